@@ -1,0 +1,112 @@
+"""Seeded synthetic inputs shared by the GPU path, the tests and the benchmark.
+
+This module holds no step of the contraction method itself. It only draws and
+prepares input tensors:
+
+* random iPEPS tensors A[p, u, l, d, r] (one physical leg p of dimension d and
+  four auxiliary legs up/left/down/right of dimension D, as in the ansatz of
+  Sec. II.A, Fig. 1(a)), averaged over the eight point-group images of the
+  square lattice because the CTMRG of Sec. II.A assumes a C4v-symmetric state;
+* closed-form test states (a product state and the iPEPS whose norm is the
+  classical 2D Ising partition function);
+* the two-site Heisenberg coupling h = S.S used as the bond observable of
+  Sec. III.
+
+All arrays are numpy float64 / complex128, C-contiguous.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+#: Seed base: workload k draws from ``numpy.random.default_rng(SEED_BASE + k)``.
+SEED_BASE = 1159600
+
+#: The eight permutations of the auxiliary legs (u, l, d, r) that form the
+#: point group of the square lattice: four rotations, then the four mirrors
+#: (left-right, up-down, main diagonal, anti-diagonal).
+D4_LEG_PERMUTATIONS = (
+    (0, 1, 2, 3), (1, 2, 3, 0), (2, 3, 0, 1), (3, 0, 1, 2),
+    (0, 3, 2, 1), (2, 1, 0, 3), (1, 0, 3, 2), (3, 2, 1, 0),
+)
+
+
+def d4_symmetrize(A: np.ndarray) -> np.ndarray:
+    """Average A[p, u, l, d, r] over the eight leg permutations of D4."""
+    acc = np.zeros_like(A)
+    for g in D4_LEG_PERMUTATIONS:
+        acc += np.transpose(A, (0, 1 + g[0], 1 + g[1], 1 + g[2], 1 + g[3]))
+    return acc / len(D4_LEG_PERMUTATIONS)
+
+
+def random_ipeps(d: int, D: int, seed: int, complex_valued: bool = False) -> np.ndarray:
+    """Seeded random C4v iPEPS tensor of shape (d, D, D, D, D), scaled to max|A| = 1.
+
+    Real entries are N(0, 1). Complex entries have real and imaginary parts
+    each N(0, 1/2), drawn as two full arrays (real first) from one generator.
+    """
+    rng = np.random.default_rng(seed)
+    shape = (d, D, D, D, D)
+    if complex_valued:
+        re = rng.standard_normal(shape)
+        im = rng.standard_normal(shape)
+        A = (re + 1j * im) * np.sqrt(0.5)
+    else:
+        A = rng.standard_normal(shape)
+    A = d4_symmetrize(A)
+    return np.ascontiguousarray(A / np.abs(A).max())
+
+
+def product_state_ipeps(phi: np.ndarray, D: int = 1) -> np.ndarray:
+    """Product state |phi>^N embedded at bond dimension D: A[p, 0, 0, 0, 0] = phi[p]."""
+    phi = np.asarray(phi)
+    A = np.zeros((phi.shape[0], D, D, D, D), dtype=phi.dtype)
+    A[:, 0, 0, 0, 0] = phi
+    return A
+
+
+def ising_ipeps(beta: float) -> np.ndarray:
+    """Real iPEPS (d = D = 2) whose norm network is the 2D Ising partition function.
+
+    A[p, u, l, d, r] = M[p, u] M[p, l] M[p, d] M[p, r] with M the symmetric
+    square root of G = [[e^{b/2}, e^{-b/2}], [e^{-b/2}, e^{b/2}]]. Each bond of
+    the double layer then carries G[p, p']^2 = exp(beta * s s'), s = +-1.
+    """
+    g = np.array([[np.exp(beta / 2), np.exp(-beta / 2)],
+                  [np.exp(-beta / 2), np.exp(beta / 2)]])
+    w, v = np.linalg.eigh(g)
+    M = (v * np.sqrt(w)) @ v.T
+    return np.einsum("pu,pl,pd,pr->puldr", M, M, M, M)
+
+
+def heisenberg_bond() -> np.ndarray:
+    """Two-site h = S^x S^x + S^y S^y + S^z S^z (S = sigma/2, J = 1) as a real 4x4.
+
+    Index order: h[(s1 s2), (s1' s2')] with s2 fastest. S^y (x) S^y is real.
+    """
+    sx = np.array([[0.0, 0.5], [0.5, 0.0]])
+    sy_sy = np.kron(np.array([[0.0, -0.5j], [0.5j, 0.0]]), np.array([[0.0, -0.5j], [0.5j, 0.0]]))
+    sz = np.array([[0.5, 0.0], [0.0, -0.5]])
+    h = np.kron(sx, sx) + sy_sy.real + np.kron(sz, sz)
+    assert np.abs(sy_sy.imag).max() == 0.0
+    return np.ascontiguousarray(h)
+
+
+def sz_sz_bond() -> np.ndarray:
+    """Two-site sigma^z sigma^z (Pauli, not spin-1/2) as a real 4x4."""
+    sz = np.diag([1.0, -1.0])
+    return np.kron(sz, sz)
+
+
+#: The benchmark workloads: (d, D, chi, moves, complex_valued).
+WORKLOADS = {
+    1: dict(d=2, D=2, chi=16, moves=30, complex_valued=False),
+    2: dict(d=2, D=4, chi=64, moves=50, complex_valued=False),
+    3: dict(d=2, D=6, chi=144, moves=50, complex_valued=False),
+    5: dict(d=2, D=5, chi=100, moves=40, complex_valued=True),
+}
+
+
+def workload_tensor(k: int) -> np.ndarray:
+    """The seeded iPEPS tensor of workload k (seed SEED_BASE + k)."""
+    w = WORKLOADS[k]
+    return random_ipeps(w["d"], w["D"], SEED_BASE + k, w["complex_valued"])

@@ -1,0 +1,81 @@
+"""Independent references used to pin the oracle (test helpers, no oracle imports).
+
+* Onsager's exact solution of the square-lattice Ising model.
+* Brute-force row-by-row contraction of finite patches of double-layer
+  tensors with a traced outer boundary.
+"""
+from __future__ import annotations
+
+import numpy as np
+from scipy.special import ellipk
+
+
+def onsager_log_z(beta: float, n: int = 512) -> float:
+    """-beta f per site: ln 2 + (1/8pi^2) int int ln[cosh^2 2b - sinh 2b (cos t1 + cos t2)].
+
+    The integrand is smooth and periodic away from the critical point, so the
+    midpoint rule on an n x n grid converges exponentially.
+    """
+    th = (np.arange(n) + 0.5) * 2 * np.pi / n
+    t1, t2 = np.meshgrid(th, th)
+    integrand = np.log(np.cosh(2 * beta) ** 2 - np.sinh(2 * beta) * (np.cos(t1) + np.cos(t2)))
+    return float(np.log(2.0) + 0.5 * np.mean(integrand))
+
+
+def onsager_nn(beta: float) -> float:
+    """<s_i s_j> on a nearest-neighbour bond: -u/2 with Onsager's internal energy u."""
+    k = 2 * np.sinh(2 * beta) / np.cosh(2 * beta) ** 2
+    u = -(1 / np.tanh(2 * beta)) * (1 + 2 / np.pi * (2 * np.tanh(2 * beta) ** 2 - 1) * ellipk(k * k))
+    return float(-u / 2)
+
+
+def _traced(D: int) -> np.ndarray:
+    v = np.zeros(D * D)
+    for k in range(D):
+        v[k + D * k] = 1.0
+    return v
+
+
+def contract_patch(site_tensor, rows: int, cols: int, D: int):
+    """Contract a rows x cols patch with every outer leg closed by delta(i, ibar).
+
+    site_tensor(r, c) returns either a 4-leg tensor t[u, l, d, r] (fully
+    contracted into the patch) or a tuple ('open', t) with t[*extra, u, l, d, r]:
+    its extra leading legs stay open in the result, in the order the sites are
+    visited (row by row, left to right). Returns an array of all open legs.
+
+    The state is psi[x_0, .., x_{cols-1}, h, *open]: the vertical bonds below
+    the processed part, the running horizontal bond h, then the open legs.
+    """
+    v = _traced(D)
+    q = D * D
+    psi = v
+    for _ in range(cols - 1):
+        psi = np.multiply.outer(psi, v)
+    psi = psi.reshape((q,) * cols)
+    n_open = 0
+    for r in range(rows):
+        psi = np.tensordot(psi, v, axes=0)               # h from the left boundary, at axis cols
+        psi = np.moveaxis(psi, psi.ndim - 1, cols)
+        for c in range(cols):
+            st = site_tensor(r, c)
+            if isinstance(st, tuple):
+                t = st[1]
+                n_extra = t.ndim - 4
+            else:
+                t = st
+                n_extra = 0
+            # contract x_c (axis c) with u and h (axis cols) with l
+            psi = np.tensordot(psi, t, axes=([c, cols], [n_extra + 0, n_extra + 1]))
+            # psi axes: [x_0..x_{c-1}, x_{c+1}..x_{cols-1}, open(n_open), extra, d, r]
+            nd = psi.ndim
+            d_ax, r_ax = nd - 2, nd - 1
+            # move d back to position c and r to position cols
+            psi = np.moveaxis(psi, d_ax, c)
+            psi = np.moveaxis(psi, psi.ndim - 1, cols)
+            # extra legs sit just after the old open legs: already in order
+            n_open += n_extra
+        psi = np.tensordot(psi, v, axes=([cols], [0]))   # close h on the right
+    for c in range(cols):
+        psi = np.tensordot(v, psi, axes=([0], [0]))      # close bottom legs
+    return psi

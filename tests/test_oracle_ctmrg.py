@@ -1,0 +1,108 @@
+"""Pins of the dense C4v CTMRG oracle (Sec. II.A, III.A): closed forms, Onsager, brute force."""
+import numpy as np
+import pytest
+
+from oracle import ctmrg, doublelayer as dl, observables as ob
+from paper_2410_11596_gb300 import inputs
+from pins import contract_patch, onsager_log_z, onsager_nn
+
+SPIN = [np.array([[0, 0.5], [0.5, 0]]), np.array([[0, -0.5j], [0.5j, 0]]), np.diag([0.5, -0.5])]
+
+
+@pytest.mark.parametrize("D", [1, 4])
+def test_product_state_energy_closed_form(D):
+    """Product state: E = sum_a <phi|S^a|phi>^2 / <phi|phi>^2, also when embedded at D = 4."""
+    phi = np.array([0.6, 0.1 + 0.8j])
+    A = inputs.product_state_ipeps(phi, D)
+    a = dl.double_layer(A)
+    r = ctmrg.run(a, 8, 4)
+    rho = ob.two_site_rdm(r.C, r.T, A)
+    n2 = np.vdot(phi, phi).real
+    closed = sum((np.vdot(phi, s @ phi).real / n2) ** 2 for s in SPIN)
+    assert ob.bond_energy(rho, inputs.heisenberg_bond()) == pytest.approx(closed, abs=1e-14)
+    sz = np.vdot(phi, np.diag([1.0, -1.0]) @ phi).real / n2
+    assert ob.bond_energy(rho, inputs.sz_sz_bond()) == pytest.approx(sz * sz, abs=1e-14)
+
+
+@pytest.mark.parametrize("beta", [0.3, 0.6])
+def test_ising_free_energy_and_bond_correlation(beta):
+    """Norm network of the Ising iPEPS = 2D Ising partition function (Onsager)."""
+    A = inputs.ising_ipeps(beta)
+    a = dl.double_layer(A)
+    r = ctmrg.run(a, 32, 120)
+    assert ob.log_kappa(r.C, r.T, a).real == pytest.approx(onsager_log_z(beta), abs=1e-9)
+    rho = ob.two_site_rdm(r.C, r.T, A)
+    assert ob.bond_energy(rho, inputs.sz_sz_bond()) == pytest.approx(onsager_nn(beta), abs=1e-9)
+
+
+def _hole(extra_dims):
+    n = int(np.prod(extra_dims))
+    return np.eye(n).reshape(tuple(extra_dims) * 2)
+
+
+@pytest.mark.parametrize("cplx", [False, True])
+@pytest.mark.parametrize("n", [0, 1, 2])
+def test_environment_equals_finite_patch_without_truncation(n, cplx):
+    """chi >= chi0 q^n: eps after n moves equals the (2n+3)^2 traced-boundary patch."""
+    A = inputs.random_ipeps(2, 2, 7, complex_valued=cplx)
+    a = dl.double_layer(A)
+    r = ctmrg.run(a, 64, n)
+    eps = ob.one_site_environment(r.C, r.T)
+    L = 2 * n + 3
+    hole = _hole((4, 4, 4, 4))
+    ex = contract_patch(lambda i, j: ("open", hole) if (i == n + 1 and j == n + 1) else a, L, L, 2)
+    e1, e2 = eps / np.linalg.norm(eps), ex / np.linalg.norm(ex)
+    np.testing.assert_allclose(e1, e2, atol=1e-13)
+
+
+@pytest.mark.parametrize("cplx", [False, True])
+@pytest.mark.parametrize("n", [0, 1])
+def test_two_site_rdm_equals_finite_patch_without_truncation(n, cplx):
+    A = inputs.random_ipeps(2, 2, 8, complex_valued=cplx)
+    a = dl.double_layer(A)
+    a_open = dl.open_double_layer(A)
+    r = ctmrg.run(a, 64, n)
+    rho = ob.two_site_rdm(r.C, r.T, A)
+    rows, cols = 2 * n + 3, 2 * n + 4
+    sites = {(n + 1, n + 1), (n + 1, n + 2)}
+    ex = contract_patch(lambda i, j: ("open", a_open) if (i, j) in sites else a, rows, cols, 2)
+    ex = ex.transpose(0, 2, 1, 3).reshape(4, 4)          # [s1, s1', s2, s2'] -> [(s1 s2), (s1' s2')]
+    np.testing.assert_allclose(rho / np.trace(rho), ex / np.trace(ex), atol=1e-13)
+
+
+def test_symmetry_error_definition():
+    """Eq. (4) for eps = H + t K (H Hermitian, K anti-Hermitian parts): S_err = t ||K|| / ||H||."""
+    rng = np.random.default_rng(1)
+    D = 2
+    e = rng.standard_normal((4,) * 4) + 1j * rng.standard_normal((4,) * 4)
+    H = 0.5 * (e + ob.dagger_env(e, D))
+    K = 0.5 * (e - ob.dagger_env(e, D))
+    assert ob.symmetry_error(H, D) < 1e-15
+    for t in (1e-6, 0.3, 2.0):
+        expect = t * np.linalg.norm(K) / np.linalg.norm(H)
+        assert ob.symmetry_error(H + t * K, D) == pytest.approx(expect, rel=1e-12)
+
+
+def test_gapped_workload1_dense_ctmrg_is_hermitian():
+    """Without multiplets at the cut the dense truncation keeps S-symmetry up to rounding."""
+    A = inputs.workload_tensor(1)
+    a = dl.double_layer(A)
+    r = ctmrg.run(a, 16, 30)
+    assert r.min_gap > 1e-9
+    assert ob.symmetry_error(ob.one_site_environment(r.C, r.T), 2) < 1e-12
+    assert ob.hermiticity_error(ob.two_site_rdm(r.C, r.T, A)) < 1e-12
+
+
+def test_keep_all_when_boundary_small():
+    A = inputs.random_ipeps(2, 2, 3)
+    r = ctmrg.run(dl.double_layer(A), 16, 1)
+    assert r.C.shape == (16, 16) and r.T.shape == (16, 4, 16)
+    assert np.isinf(r.infos[0].gap)
+
+
+def test_corner_spectrum_gauge_invariant():
+    """Normalised corner spectrum is unchanged by an orthogonal change of the boundary basis."""
+    A = inputs.random_ipeps(2, 2, 4)
+    r = ctmrg.run(dl.double_layer(A), 8, 6)
+    Q, _ = np.linalg.qr(np.random.default_rng(2).standard_normal((8, 8)))
+    np.testing.assert_allclose(ob.corner_spectrum(Q.T @ r.C @ Q), ob.corner_spectrum(r.C), atol=1e-14)
