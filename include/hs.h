@@ -1,0 +1,221 @@
+/*
+ * hs.h -- C ABI of libhs: CTMRG contraction of double-layer iPEPS tensor
+ * networks in the Hermitian (bra-ket swap) basis, on one GB300 (sm_103a).
+ *
+ * Method: arXiv 2410.11596, "Exploiting the Hermitian symmetry in tensor
+ * network algorithms". Each combined bra-ket leg of dimension D^2 is rotated
+ * into the eigenbasis of the swap S (Sec. II.B); for real tensors the double
+ * layer becomes Z2 block-sparse with an even sector of size D(D+1)/2 and an odd
+ * sector of size D(D-1)/2, and the CTMRG contractions (Sec. II.A, Fig. 1(d))
+ * become block GEMMs at about a quarter of the dense cost (Sec. II.B).
+ *
+ * Conventions used by every call
+ * ------------------------------
+ * - All pointers to tensor data are DEVICE pointers unless stated otherwise.
+ *   The caller allocates and owns every input and output buffer; the context
+ *   owns only its workspace, solver/BLAS handles and pinned staging memory.
+ * - Every call enqueues its GPU work on the context's stream. Calls that must
+ *   return host-visible results (sector sizes, status words) synchronise that
+ *   stream before returning; this is stated per call.
+ * - iPEPS tensor A: shape (d, D, D, D, D), legs (p, u, l, d, r), row-major,
+ *   float64 (HS_F64) or interleaved complex128 (HS_C128).
+ * - Combined bra-ket index of one double-layer leg: x = i + D * ibar with i
+ *   the ket (from A) and ibar the bra (from conj A) index: the ket index runs
+ *   fastest, as in the D = 2 listing of Sec. II.B.
+ * - Hermitian basis of one leg (Sec. II.B): even states (k k') for k ascending,
+ *   then (k l' + l k')/sqrt2 for k < l; odd states (k l' - l k')/sqrt2 for k < l.
+ * - Sector-ordered block storage ("FSO"): a tensor with legs split into row
+ *   legs and column legs is stored as the blocks of its block-diagonal matrix.
+ *   A fused group of legs enumerates the parity tuples of its legs grouped by
+ *   total parity (even group first), tuples in lexicographic order (first leg
+ *   most significant), and inside a tuple the local indices row-major.
+ *   Block p (p = 0 even, 1 odd) holds rows of fused parity p times columns of
+ *   fused parity p, row-major; block 1 follows block 0. In the dense basis
+ *   every leg is "all even" and the layout is the plain row-major matrix.
+ * - Errors: no call aborts, exits or prints. Each returns an hs_status; the
+ *   message of the last failure on the calling thread is hs_last_error().
+ *   There is no CPU fallback: a missing capability is an error.
+ */
+#ifndef HS_H
+#define HS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define HS_ABI_VERSION 1
+
+typedef enum {
+  HS_OK = 0,
+  HS_ERR_INVALID_ARG = -1,   /* null pointer, negative size, bad enum */
+  HS_ERR_SHAPE = -2,         /* sizes inconsistent or above a limit */
+  HS_ERR_DTYPE = -3,         /* dtype not supported by this call */
+  HS_ERR_NOT_HERMITIAN = -4, /* odd blocks above tolerance where none may exist */
+  HS_ERR_CUDA = -5,          /* a CUDA runtime call failed */
+  HS_ERR_SOLVER = -6,        /* cuSOLVER / cuBLAS failure or non-zero info */
+  HS_ERR_TIMEOUT = -7,       /* a bounded device wait gave up */
+  HS_ERR_NONFINITE = -8,     /* NaN or Inf found in a result */
+  HS_ERR_WORKSPACE = -9,     /* caller buffer smaller than required */
+  HS_ERR_UNSUPPORTED = -10   /* valid request that this build does not implement */
+} hs_status;
+
+typedef enum { HS_F64 = 0, HS_C128 = 1 } hs_dtype;
+
+/* Arithmetic of the block contractions. The eigen-decomposition, the
+ * normalisation and the traces are FP64 in every mode. */
+typedef enum {
+  HS_PREC_F64 = 0,    /* FP64 block GEMMs */
+  HS_PREC_TF32X3 = 1, /* 3-pass split TF32 on tcgen05, FP32 accumulate */
+  HS_PREC_TF32 = 2,   /* 1-pass TF32 on tcgen05, FP32 accumulate */
+  HS_PREC_BF16X3 = 3  /* 3-pass split BF16 on tcgen05, FP32 accumulate */
+} hs_precision;
+
+/* Basis of the combined legs: dense (the plain combined basis, one sector)
+ * or Hermitian (eigenbasis of S, two sectors). */
+typedef enum { HS_BASIS_DENSE = 0, HS_BASIS_HERMITIAN = 1 } hs_basis;
+
+/* Which library runs the FP64 block GEMMs (HS_PREC_F64 only). */
+typedef enum { HS_GEMM_OWN = 0, HS_GEMM_CUBLAS = 1 } hs_gemm_backend;
+
+typedef struct hs_ctx_s* hs_ctx;
+
+/* The double-layer tensor a[u, l, d, r] (Sec. II.A, Fig. 1(b)) in FSO storage
+ * with row legs (u, l) and column legs (d, r), all four legs of dimension D^2
+ * split (n_even, n_odd). Only the even-total blocks exist for real A. */
+typedef struct {
+  int D;                 /* bond dimension of A */
+  int n_even, n_odd;     /* per-leg sector sizes: (D(D+1)/2, D(D-1)/2) or (D^2, 0) */
+  hs_basis basis;
+  hs_dtype dtype;        /* HS_F64 only in this version */
+  double* data;          /* device, caller-owned */
+  size_t capacity_bytes; /* size of data */
+} hs_z2_tensor;
+
+/* The C4v environment (Sec. II.A, Fig. 1(d)): one corner C[chi, chi] and one
+ * edge T[alpha, x, beta]. Both are FP64 in FSO storage:
+ *   C: row leg beta, column leg gamma (block diagonal);
+ *   T: row legs (alpha, x), column leg beta.
+ * The boundary leg has sectors (chi_even, chi_odd). Buffers are caller-owned,
+ * sized with hs_env_bytes(). Fields other than C, T and the byte counts are
+ * written by the library. */
+typedef struct {
+  int D, chi_max;
+  int chi_even, chi_odd; /* current boundary sectors (host copy) */
+  int q_even, q_odd;     /* sectors of the double-layer legs */
+  hs_basis basis;
+  hs_precision precision;
+  hs_gemm_backend gemm_backend;
+  int moves;             /* moves done since hs_ctmrg_init */
+  double log_norm_C, log_norm_T; /* logs of the last normalisation factors */
+  double* C;             /* device, caller-owned */
+  double* T;             /* device, caller-owned */
+  size_t C_bytes, T_bytes;
+} hs_env;
+
+/* Per-move record filled by hs_ctmrg_move (host memory). */
+typedef struct {
+  int chi_even, chi_odd; /* sectors kept */
+  int n_even, n_odd;     /* sizes of the two eigenproblems (dense basis: n_odd = 0) */
+  double lam_max;        /* largest |eigenvalue| of the enlarged corner */
+  double lam_cut;        /* smallest |eigenvalue| kept */
+  double lam_next;       /* largest |eigenvalue| discarded (0 if none) */
+  double gap;            /* (lam_cut - lam_next) / lam_max, +inf if nothing discarded */
+  double log_norm_C, log_norm_T;
+  double gemm_flops;     /* sum over block GEMMs of 2 M N K in this move */
+  int flags;             /* bit 0: gap below 1e-9 (degenerate cut) */
+} hs_move_info;
+
+typedef enum { HS_RDM_TWO_SITE = 0, HS_RDM_ENV_ONE_SITE = 1 } hs_rdm_kind;
+
+/* ---- context ---------------------------------------------------------- */
+
+/* Create a context on CUDA device `device` using `stream` (a cudaStream_t;
+ * NULL selects the legacy default stream). */
+hs_status hs_create(hs_ctx* out, int device, void* stream);
+hs_status hs_destroy(hs_ctx ctx);
+/* Message of the last failure on this thread ("" if none). Never NULL. */
+const char* hs_last_error(void);
+/* Block until all work of the context has finished; reports deferred
+ * device-side errors. */
+hs_status hs_sync(hs_ctx ctx);
+int hs_abi_version(void);
+
+/* ---- double layer and Hermitian basis (Sec. II.A, II.B) --------------- */
+
+/* a[x_u, x_l, x_d, x_r] = sum_p A[p,u,l,d,r] conj(A[p,ubar,lbar,dbar,rbar])
+ * (Fig. 1(b)) in the plain combined basis, dense row-major (D^2)^4 into a_out
+ * (device, caller-owned, (D^2)^4 doubles; complex: interleaved complex128).
+ * A is device memory. Asynchronous. */
+hs_status hs_make_double_layer(hs_ctx ctx, const double* A, int d, int D, hs_dtype dtype,
+                               double* a_out);
+
+/* Bytes of an hs_z2_tensor for bond dimension D in the given basis. */
+size_t hs_z2_tensor_bytes(int D, hs_basis basis, hs_dtype dtype);
+
+/* Rotate a dense double layer (layout of hs_make_double_layer, device) into
+ * the eigenbasis of S on all four legs, a~ = (U^T)^{x4} a (Sec. II.B), and
+ * store the even-total blocks in out (FSO, fields D/n_even/n_odd/basis set
+ * here; out->data and out->capacity_bytes set by the caller). The odd-total
+ * blocks are computed too: if their largest modulus exceeds
+ * herm_tol * max|a~| the call returns HS_ERR_NOT_HERMITIAN. Synchronises. */
+hs_status hs_to_hermitian_basis(hs_ctx ctx, const double* a_dense, int D, hs_dtype dtype,
+                                double herm_tol, hs_z2_tensor* out);
+
+/* Fused form of the two calls above: from A (device, real) straight to the
+ * stored blocks of a~ in `basis` (HS_BASIS_DENSE gives the plain layout).
+ * Asynchronous. */
+hs_status hs_double_layer_hermitian(hs_ctx ctx, const double* A, int d, int D, hs_dtype dtype,
+                                    hs_basis basis, hs_z2_tensor* out);
+
+/* ---- CTMRG (Sec. II.A, Fig. 1(d)) ------------------------------------- */
+
+/* Bytes needed for env->C and env->T at bond dimension D and chi_max. */
+hs_status hs_env_bytes(int D, int chi_max, size_t* C_bytes, size_t* T_bytes);
+
+/* Traced-boundary initial environment: the open outer legs of the first
+ * corner and edge are closed with delta(i, ibar) = sum_k |k k'>, an even
+ * state, so C0 = a(delta, delta, ., .) and T0 = a(., delta, ., .) with chi0 =
+ * D^2. Sets every library-written field of env. Asynchronous. */
+hs_status hs_ctmrg_init(hs_ctx ctx, const hs_z2_tensor* a, int chi_max, hs_precision precision,
+                        hs_gemm_backend backend, hs_env* env);
+
+/* One C4v CTMRG move: enlarged corner C' = T C T a (block GEMMs), one FP64
+ * symmetric eigen-decomposition per parity block, the chi eigenvalues of
+ * largest modulus kept across both blocks (ties: larger |lambda|, then the
+ * even block, then the lower eigenvalue), C <- diag(lambda_kept),
+ * T <- P^T (T a) P, then C and T divided by their largest modulus.
+ * info (host, may be NULL) receives the move record. Synchronises once
+ * (to learn the new sector sizes). */
+hs_status hs_ctmrg_move(hs_ctx ctx, const hs_z2_tensor* a, hs_env* env, int chi,
+                        hs_move_info* info);
+
+/* Copy the environment out in the plain dense layout: C_dense[chi, chi] and
+ * T_dense[chi, D^2, chi] (device, caller-owned, FP64), with the boundary leg
+ * ordered as stored (even sector first) and the double-layer leg rotated back
+ * to the plain combined basis. Asynchronous. */
+hs_status hs_env_to_dense(hs_ctx ctx, const hs_env* env, double* C_dense, double* T_dense);
+
+/* ---- observables (Sec. III.A) ----------------------------------------- */
+
+/* HS_RDM_TWO_SITE: rho[(s1 s2), (s1' s2')] of a horizontal bond from the
+ * environment and A (device, real), not normalised, into out (device, d^4
+ * doubles); then tr_out[0] = Tr rho and tr_out[1] = Tr(rho h) with h a d^2 x
+ * d^2 real matrix (device). In the Hermitian basis only the S-even part of the
+ * open double layer meets the Z2-even environment, so rho is Hermitian by
+ * construction; the entries are computed for (row <= col) and mirrored.
+ * HS_RDM_ENV_ONE_SITE: the one-site environment eps[u, l, d, r] (Eq. (4)),
+ * (D^2)^4 doubles in the plain combined basis; h and tr_out unused.
+ * Asynchronous. */
+hs_status hs_rdm(hs_ctx ctx, const hs_env* env, const double* A, int d, int D, hs_dtype dtype,
+                 hs_rdm_kind kind, const double* h, double* out, double* tr_out);
+
+/* Workspace the context will allocate for (D, chi): reported for planning. */
+hs_status hs_workspace_query(int D, int chi, hs_precision precision, size_t* bytes);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HS_H */

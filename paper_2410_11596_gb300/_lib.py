@@ -1,0 +1,186 @@
+"""ctypes binding of libhs (include/hs.h): argument marshalling only.
+
+Every computation runs in the CUDA library; this module only converts between
+torch device tensors / Python values and the C structs of the ABI. If the
+library has not been built, loading fails with an error: there is no CPU path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+from ctypes import POINTER, c_double, c_int, c_size_t, c_void_p
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libhs.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "hs.h")
+
+HS_OK = 0
+STATUS_NAMES = {
+    0: "HS_OK", -1: "HS_ERR_INVALID_ARG", -2: "HS_ERR_SHAPE", -3: "HS_ERR_DTYPE",
+    -4: "HS_ERR_NOT_HERMITIAN", -5: "HS_ERR_CUDA", -6: "HS_ERR_SOLVER", -7: "HS_ERR_TIMEOUT",
+    -8: "HS_ERR_NONFINITE", -9: "HS_ERR_WORKSPACE", -10: "HS_ERR_UNSUPPORTED",
+}
+HS_F64, HS_C128 = 0, 1
+HS_PREC_F64, HS_PREC_TF32X3, HS_PREC_TF32, HS_PREC_BF16X3 = 0, 1, 2, 3
+HS_BASIS_DENSE, HS_BASIS_HERMITIAN = 0, 1
+HS_GEMM_OWN, HS_GEMM_CUBLAS = 0, 1
+HS_RDM_TWO_SITE, HS_RDM_ENV_ONE_SITE = 0, 1
+
+
+class HsError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Z2Tensor(ctypes.Structure):
+    _fields_ = [("D", c_int), ("n_even", c_int), ("n_odd", c_int), ("basis", c_int), ("dtype", c_int),
+                ("data", c_void_p), ("capacity_bytes", c_size_t)]
+
+
+class Env(ctypes.Structure):
+    _fields_ = [("D", c_int), ("chi_max", c_int), ("chi_even", c_int), ("chi_odd", c_int),
+                ("q_even", c_int), ("q_odd", c_int), ("basis", c_int), ("precision", c_int),
+                ("gemm_backend", c_int), ("moves", c_int), ("log_norm_C", c_double),
+                ("log_norm_T", c_double), ("C", c_void_p), ("T", c_void_p), ("C_bytes", c_size_t),
+                ("T_bytes", c_size_t)]
+
+
+class MoveInfo(ctypes.Structure):
+    _fields_ = [("chi_even", c_int), ("chi_odd", c_int), ("n_even", c_int), ("n_odd", c_int),
+                ("lam_max", c_double), ("lam_cut", c_double), ("lam_next", c_double), ("gap", c_double),
+                ("log_norm_C", c_double), ("log_norm_T", c_double), ("gemm_flops", c_double),
+                ("flags", c_int)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_PROTOS = {
+    "hs_create": (c_int, [POINTER(c_void_p), c_int, c_void_p]),
+    "hs_destroy": (c_int, [c_void_p]),
+    "hs_last_error": (ctypes.c_char_p, []),
+    "hs_sync": (c_int, [c_void_p]),
+    "hs_abi_version": (c_int, []),
+    "hs_make_double_layer": (c_int, [c_void_p, c_void_p, c_int, c_int, c_int, c_void_p]),
+    "hs_z2_tensor_bytes": (c_size_t, [c_int, c_int, c_int]),
+    "hs_to_hermitian_basis": (c_int, [c_void_p, c_void_p, c_int, c_int, c_double, POINTER(Z2Tensor)]),
+    "hs_double_layer_hermitian": (c_int, [c_void_p, c_void_p, c_int, c_int, c_int, c_int,
+                                          POINTER(Z2Tensor)]),
+    "hs_env_bytes": (c_int, [c_int, c_int, POINTER(c_size_t), POINTER(c_size_t)]),
+    "hs_ctmrg_init": (c_int, [c_void_p, POINTER(Z2Tensor), c_int, c_int, c_int, POINTER(Env)]),
+    "hs_ctmrg_move": (c_int, [c_void_p, POINTER(Z2Tensor), POINTER(Env), c_int, POINTER(MoveInfo)]),
+    "hs_env_to_dense": (c_int, [c_void_p, POINTER(Env), c_void_p, c_void_p]),
+    "hs_rdm": (c_int, [c_void_p, POINTER(Env), c_void_p, c_int, c_int, c_int, c_int, c_void_p, c_void_p,
+                       c_void_p]),
+    "hs_workspace_query": (c_int, [c_int, c_int, c_int, POINTER(c_size_t)]),
+}
+
+_lib = None
+
+
+def header_functions() -> list[str]:
+    """Names of the functions declared in include/hs.h."""
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(hs_[a-z0-9_]+)\s*\(", text)))
+
+
+def load(path: str = LIB_PATH):
+    """Load libhs.so (once) and declare the prototypes. Raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise HsError(-5, f"{path} is missing: build it with paper_2410_11596_gb300/build.py "
+                          "(there is no CPU fallback)")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in _PROTOS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def check(status: int) -> None:
+    if status != HS_OK:
+        raise HsError(status, load().hs_last_error().decode())
+
+
+def ptr(t) -> int:
+    """Device pointer of a contiguous torch tensor."""
+    assert t.is_contiguous()
+    return t.data_ptr()
+
+
+# ---- thin wrappers with the C names -----------------------------------------
+
+
+def hs_create(device: int = 0, stream: int | None = None) -> int:
+    h = c_void_p()
+    check(load().hs_create(ctypes.byref(h), device, stream))
+    return h.value
+
+
+def hs_destroy(ctx: int) -> None:
+    check(load().hs_destroy(ctx))
+
+
+def hs_sync(ctx: int) -> None:
+    check(load().hs_sync(ctx))
+
+
+def hs_z2_tensor_bytes(D: int, basis: int, dtype: int = HS_F64) -> int:
+    return load().hs_z2_tensor_bytes(D, basis, dtype)
+
+
+def hs_make_double_layer(ctx: int, A, d: int, D: int, dtype: int, a_out) -> None:
+    check(load().hs_make_double_layer(ctx, ptr(A), d, D, dtype, ptr(a_out)))
+
+
+def hs_to_hermitian_basis(ctx: int, a_dense, D: int, dtype: int, herm_tol: float, out_buf) -> Z2Tensor:
+    t = Z2Tensor(data=ptr(out_buf), capacity_bytes=out_buf.numel() * out_buf.element_size())
+    check(load().hs_to_hermitian_basis(ctx, ptr(a_dense), D, dtype, herm_tol, ctypes.byref(t)))
+    return t
+
+
+def hs_double_layer_hermitian(ctx: int, A, d: int, D: int, dtype: int, basis: int, out_buf) -> Z2Tensor:
+    t = Z2Tensor(data=ptr(out_buf), capacity_bytes=out_buf.numel() * out_buf.element_size())
+    check(load().hs_double_layer_hermitian(ctx, ptr(A), d, D, dtype, basis, ctypes.byref(t)))
+    return t
+
+
+def hs_env_bytes(D: int, chi_max: int) -> tuple[int, int]:
+    cb, tb = c_size_t(), c_size_t()
+    check(load().hs_env_bytes(D, chi_max, ctypes.byref(cb), ctypes.byref(tb)))
+    return cb.value, tb.value
+
+
+def hs_ctmrg_init(ctx: int, a: Z2Tensor, chi_max: int, precision: int, backend: int, C_buf, T_buf) -> Env:
+    env = Env(C=ptr(C_buf), T=ptr(T_buf), C_bytes=C_buf.numel() * 8, T_bytes=T_buf.numel() * 8)
+    check(load().hs_ctmrg_init(ctx, ctypes.byref(a), chi_max, precision, backend, ctypes.byref(env)))
+    return env
+
+
+def hs_ctmrg_move(ctx: int, a: Z2Tensor, env: Env, chi: int) -> MoveInfo:
+    info = MoveInfo()
+    check(load().hs_ctmrg_move(ctx, ctypes.byref(a), ctypes.byref(env), chi, ctypes.byref(info)))
+    return info
+
+
+def hs_env_to_dense(ctx: int, env: Env, C_dense, T_dense) -> None:
+    check(load().hs_env_to_dense(ctx, ctypes.byref(env), ptr(C_dense), ptr(T_dense)))
+
+
+def hs_rdm(ctx: int, env: Env, A, d: int, D: int, dtype: int, kind: int, h, out, tr_out) -> None:
+    check(load().hs_rdm(ctx, ctypes.byref(env), ptr(A), d, D, dtype, kind,
+                        ptr(h) if h is not None else None, ptr(out),
+                        ptr(tr_out) if tr_out is not None else None))
+
+
+def hs_workspace_query(D: int, chi: int, precision: int) -> int:
+    b = c_size_t()
+    check(load().hs_workspace_query(D, chi, precision, ctypes.byref(b)))
+    return b.value

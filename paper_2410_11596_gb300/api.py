@@ -1,0 +1,114 @@
+"""Python front end of libhs: allocates device buffers with torch and calls the C ABI.
+
+No arithmetic of the method happens here; every step runs in the CUDA library.
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import _lib as L
+
+BASIS = {"dense": L.HS_BASIS_DENSE, "hermitian": L.HS_BASIS_HERMITIAN}
+PRECISION = {"f64": L.HS_PREC_F64, "tf32x3": L.HS_PREC_TF32X3, "tf32": L.HS_PREC_TF32,
+             "bf16x3": L.HS_PREC_BF16X3}
+BACKEND = {"own": L.HS_GEMM_OWN, "cublas": L.HS_GEMM_CUBLAS}
+
+
+class Context:
+    """An hs_ctx bound to a CUDA device and the current torch stream."""
+
+    def __init__(self, device: int = 0, stream: torch.cuda.Stream | None = None):
+        if not torch.cuda.is_available():
+            raise L.HsError(-5, "no CUDA device: libhs has no CPU path")
+        self.device = device
+        self.stream = stream or torch.cuda.current_stream(device)
+        self.handle = L.hs_create(device, self.stream.cuda_stream)
+
+    def close(self) -> None:
+        if self.handle:
+            L.hs_destroy(self.handle)
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def sync(self) -> None:
+        L.hs_sync(self.handle)
+
+
+def to_device(A: np.ndarray, device: int = 0) -> torch.Tensor:
+    """Copy a host iPEPS tensor to the device (complex as interleaved float64)."""
+    A = np.ascontiguousarray(A)
+    if np.iscomplexobj(A):
+        A = A.astype(np.complex128).view(np.float64)
+    return torch.from_numpy(A.astype(np.float64)).to(f"cuda:{device}")
+
+
+class CTMRG:
+    """C4v CTMRG of one real iPEPS tensor on one GPU through the C ABI."""
+
+    def __init__(self, ctx: Context, A: np.ndarray | torch.Tensor, chi: int, basis: str = "hermitian",
+                 precision: str = "f64", backend: str = "own"):
+        self.ctx = ctx
+        dev = f"cuda:{ctx.device}"
+        self.A = A if isinstance(A, torch.Tensor) else to_device(A, ctx.device)
+        self.d, self.D = int(self.A.shape[0]), int(self.A.shape[1])
+        self.chi = chi
+        nbytes = L.hs_z2_tensor_bytes(self.D, BASIS[basis])
+        self.a_buf = torch.empty(nbytes // 8, dtype=torch.float64, device=dev)
+        self.a = L.hs_double_layer_hermitian(ctx.handle, self.A, self.d, self.D, L.HS_F64, BASIS[basis],
+                                             self.a_buf)
+        cb, tb = L.hs_env_bytes(self.D, chi)
+        self.C_buf = torch.empty(cb // 8, dtype=torch.float64, device=dev)
+        self.T_buf = torch.empty(tb // 8, dtype=torch.float64, device=dev)
+        self.env = L.hs_ctmrg_init(ctx.handle, self.a, chi, PRECISION[precision], BACKEND[backend],
+                                   self.C_buf, self.T_buf)
+        self.infos: list[dict] = []
+
+    def move(self) -> dict:
+        info = L.hs_ctmrg_move(self.ctx.handle, self.a, self.env, self.chi).as_dict()
+        self.infos.append(info)
+        return info
+
+    def run(self, moves: int) -> list[dict]:
+        return [self.move() for _ in range(moves)]
+
+    @property
+    def chi_now(self) -> int:
+        return self.env.chi_even + self.env.chi_odd
+
+    def dense_env(self) -> tuple[torch.Tensor, torch.Tensor]:
+        """(C[chi, chi], T[chi, D^2, chi]) in the plain combined basis."""
+        chi, q = self.chi_now, self.D * self.D
+        dev = self.A.device
+        C = torch.empty((chi, chi), dtype=torch.float64, device=dev)
+        T = torch.empty((chi, q, chi), dtype=torch.float64, device=dev)
+        L.hs_env_to_dense(self.ctx.handle, self.env, C, T)
+        return C, T
+
+    def rdm2(self, h: np.ndarray) -> tuple[torch.Tensor, float, float]:
+        """(rho, Tr rho, Tr rho h) of a horizontal bond; h a d^2 x d^2 real matrix."""
+        dev = self.A.device
+        n = self.d * self.d
+        rho = torch.empty((n, n), dtype=torch.float64, device=dev)
+        tr = torch.empty(2, dtype=torch.float64, device=dev)
+        hd = torch.from_numpy(np.ascontiguousarray(h, dtype=np.float64)).to(dev)
+        L.hs_rdm(self.ctx.handle, self.env, self.A, self.d, self.D, L.HS_F64, L.HS_RDM_TWO_SITE, hd, rho, tr)
+        t = tr.cpu().numpy()
+        return rho, float(t[0]), float(t[1])
+
+    def energy(self, h: np.ndarray) -> float:
+        _, t0, t1 = self.rdm2(h)
+        return t1 / t0
+
+    def one_site_env(self) -> torch.Tensor:
+        """eps[u, l, d, r] in the plain combined basis (Eq. (4))."""
+        q = self.D * self.D
+        eps = torch.empty((q, q, q, q), dtype=torch.float64, device=self.A.device)
+        L.hs_rdm(self.ctx.handle, self.env, self.A, self.d, self.D, L.HS_F64, L.HS_RDM_ENV_ONE_SITE,
+                 None, eps, None)
+        return eps

@@ -1,0 +1,102 @@
+// Context of libhs and the helpers shared by the C-ABI translation units.
+#pragma once
+
+#include <cublas_v2.h>
+#include <cusolverDn.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <initializer_list>
+#include <string>
+#include <vector>
+
+#include "hs_internal.cuh"
+
+namespace hs {
+
+// Records the message of the last failure on this thread and returns st.
+hs_status fail(hs_status st, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
+const char* last_error();
+
+#define HS_CUDA(x)                                                                        \
+  do {                                                                                    \
+    cudaError_t e_ = (x);                                                                 \
+    if (e_ != cudaSuccess)                                                                \
+      return ::hs::fail(HS_ERR_CUDA, "%s failed: %s (%s:%d)", #x, cudaGetErrorString(e_),   \
+                        __FILE__, __LINE__);                                              \
+  } while (0)
+#define HS_SOLVER(x)                                                                      \
+  do {                                                                                    \
+    cusolverStatus_t e_ = (x);                                                            \
+    if (e_ != CUSOLVER_STATUS_SUCCESS)                                                    \
+      return ::hs::fail(HS_ERR_SOLVER, "%s failed: cusolver status %d (%s:%d)", #x, (int)e_, \
+                        __FILE__, __LINE__);                                              \
+  } while (0)
+#define HS_BLAS(x)                                                                        \
+  do {                                                                                    \
+    cublasStatus_t e_ = (x);                                                              \
+    if (e_ != CUBLAS_STATUS_SUCCESS)                                                      \
+      return ::hs::fail(HS_ERR_SOLVER, "%s failed: cublas status %d (%s:%d)", #x, (int)e_,  \
+                        __FILE__, __LINE__);                                              \
+  } while (0)
+#define HS_TRY(x)               \
+  do {                          \
+    hs_status s_ = (x);         \
+    if (s_ != HS_OK) return s_; \
+  } while (0)
+
+// Device buffer that only grows.
+struct DBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  hs_status ensure(size_t want) {
+    if (want <= bytes) return HS_OK;
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+    if (cudaMalloc(&p, want) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(HS_ERR_CUDA, "cudaMalloc of %zu bytes failed", want);
+    }
+    bytes = want;
+    return HS_OK;
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+  }
+  double* d() const { return static_cast<double*>(p); }
+};
+
+}  // namespace hs
+
+struct hs_ctx_s {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  cusolverDnHandle_t solver = nullptr;
+  cusolverDnParams_t params = nullptr;
+  cublasHandle_t blas = nullptr;
+  // move workspace
+  hs::DBuf big1, big2, x1, pt, pp, w, lam, idx, sel, scratch, info, solver_dev;
+  std::vector<char> solver_host;
+  hs::SelectOut* h_sel = nullptr;  // pinned
+  int* h_info = nullptr;           // pinned
+  // observables workspace
+  hs::DBuf r[16];
+};
+
+namespace hs {
+
+hs_status check_ctx(hs_ctx ctx);
+Sect q_sect(int D, hs_basis b);
+Z2Mat mat(Fused r, Fused c);
+// C = A B^T on the chosen backend.
+hs_status gemm(hs_ctx ctx, hs_gemm_backend be, const GemmGroup& g, const double* A, const double* B,
+               double* C);
+hs_status permute(hs_ctx ctx, const Z2Mat& in, const Z2Mat& out, std::initializer_list<int> perm,
+                  const double* src, double* dst);
+
+}  // namespace hs

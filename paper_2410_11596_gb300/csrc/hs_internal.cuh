@@ -1,0 +1,193 @@
+// Internal declarations of libhs: sector-ordered ("FSO") block layouts, the
+// descriptors the kernels consume, and the kernel launchers.
+//
+// Z2 block structure (arXiv 2410.11596, Sec. II.B): every leg carries a
+// parity split (even, odd). A tensor is stored as a block-diagonal matrix
+// over a grouping of its legs into row legs and column legs; a group of legs
+// is "fused" by enumerating the parity tuples of its legs grouped by total
+// parity (even group first), tuples in lexicographic order (first leg most
+// significant bit), local indices row-major inside each tuple.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/hs.h"
+
+#define HS_HD __host__ __device__ __forceinline__
+
+namespace hs {
+
+// Sector sizes of one leg.
+struct Sect {
+  int n[2];
+};
+
+HS_HD Sect make_sect(int e, int o) {
+  Sect s;
+  s.n[0] = e;
+  s.n[1] = o;
+  return s;
+}
+
+// A group of up to 3 legs fused into one matrix index.
+struct Fused {
+  int k;
+  Sect leg[3];
+};
+
+HS_HD Fused fused0() {
+  Fused f;
+  f.k = 0;
+  return f;
+}
+HS_HD Fused fused1(Sect a) {
+  Fused f;
+  f.k = 1;
+  f.leg[0] = a;
+  return f;
+}
+HS_HD Fused fused2(Sect a, Sect b) {
+  Fused f;
+  f.k = 2;
+  f.leg[0] = a;
+  f.leg[1] = b;
+  return f;
+}
+
+HS_HD int tuple_parity(int t) { return __builtin_popcount((unsigned)t) & 1; }
+
+// Parity of leg j inside tuple t of a k-leg group (leg 0 = most significant).
+HS_HD int tuple_bit(int t, int k, int j) { return (t >> (k - 1 - j)) & 1; }
+
+HS_HD long long tuple_size(const Fused& f, int t) {
+  long long s = 1;
+  for (int j = 0; j < f.k; ++j) s *= f.leg[j].n[tuple_bit(t, f.k, j)];
+  return s;
+}
+
+// Number of fused indices of total parity P.
+HS_HD long long fused_size(const Fused& f, int P) {
+  long long s = 0;
+  for (int t = 0; t < (1 << f.k); ++t)
+    if (tuple_parity(t) == P) s += tuple_size(f, t);
+  return s;
+}
+
+// Offset of tuple t inside its parity group.
+HS_HD long long tuple_offset(const Fused& f, int t) {
+  long long s = 0;
+  const int P = tuple_parity(t);
+  for (int u = 0; u < t; ++u)
+    if (tuple_parity(u) == P) s += tuple_size(f, u);
+  return s;
+}
+
+// Block-diagonal Z2 matrix: block p = rows of parity p x cols of parity p.
+struct Z2Mat {
+  Fused r, c;
+};
+
+HS_HD long long z2_rows(const Z2Mat& m, int p) { return fused_size(m.r, p); }
+HS_HD long long z2_cols(const Z2Mat& m, int p) { return fused_size(m.c, p); }
+HS_HD long long z2_block_off(const Z2Mat& m, int p) {
+  return p == 0 ? 0 : z2_rows(m, 0) * z2_cols(m, 0);
+}
+HS_HD long long z2_elems(const Z2Mat& m) {
+  return z2_rows(m, 0) * z2_cols(m, 0) + z2_rows(m, 1) * z2_cols(m, 1);
+}
+
+// ---- permutation of a Z2 matrix into another grouping/order of its legs ----
+
+// One dense box: out[i0..i3] = in[...] for i_j < dim[j].
+struct Box {
+  long long out_off, in_off;
+  int dim[4];
+  long long out_stride[4], in_stride[4];
+  long long count;   // product of dims
+  long long start;   // prefix sum of counts over earlier boxes
+};
+
+constexpr int kMaxBoxes = 8;
+
+struct PermPlan {
+  int nbox;
+  long long total;
+  Box box[kMaxBoxes];
+};
+
+// Build the plan that maps matrix `in` (legs L0..L{n-1}; the first in.r.k are
+// rows) to matrix `out` whose leg j is input leg perm[j]. Both even-total.
+PermPlan make_perm_plan(const Z2Mat& in, const Z2Mat& out, const int* perm);
+
+// ---- grouped GEMM ----------------------------------------------------------
+
+// C[m, n] = alpha * sum_k A[m, k] B[n, k] (+ beta C): both operands K-major.
+struct GemmProblem {
+  int M, N, K;
+  int lda, ldb, ldc;
+  long long a_off, b_off, c_off;  // element offsets
+};
+
+constexpr int kMaxProblems = 4;
+
+struct GemmGroup {
+  int n;
+  GemmProblem p[kMaxProblems];
+};
+
+// The two block GEMMs of a Z2 product C[R|N] = A[R|K] B[N|K]^T.
+GemmGroup make_z2_gemm(const Z2Mat& A, const Z2Mat& B, const Z2Mat& C);
+double gemm_flops(const GemmGroup& g);
+
+// ---- kernel launchers (device code in k_*.cu) -------------------------------
+
+cudaError_t launch_permute_f64(const PermPlan& plan, const double* in, double* out, double scale,
+                               cudaStream_t s);
+cudaError_t launch_gemm_f64(const GemmGroup& g, const double* A, const double* B, double* C,
+                            double alpha, cudaStream_t s);
+
+// A[p,u,l,d,r] (real) -> a~ blocks in FSO [(u,l)|(d,r)]; hermitian selects the
+// rotation by U^T on every leg, otherwise the plain combined basis.
+cudaError_t launch_double_layer_blocks(const double* A, int d, int D, bool hermitian, double* out,
+                                       cudaStream_t s);
+// Dense double layer (D^2)^4 from A, real (cplx = false) or complex128.
+cudaError_t launch_double_layer_dense(const double* A, int d, int D, bool cplx, double* out,
+                                      cudaStream_t s);
+// Rotate a dense real double layer into all 16 parity blocks; writes the
+// even-total ones (FSO) and atomically maxes |odd| and |all| into maxes[0..1].
+cudaError_t launch_rotate_dense_to_blocks(const double* a, int D, double* out,
+                                          unsigned long long* maxes, cudaStream_t s);
+
+// Traced-boundary initial C0 and T0 (FSO) from the stored blocks of a.
+cudaError_t launch_ctmrg_init(const double* a_blocks, int D, bool hermitian, double* C, double* T,
+                              cudaStream_t s);
+
+struct SelectOut {
+  int chi_new[2];
+  int pad[2];
+  double lam_max, lam_cut, lam_next;
+  double log_norm_C, log_norm_T;
+};
+
+// Choose the chi eigenvalues of largest modulus across the two blocks.
+cudaError_t launch_select(const double* w0, int n0, const double* w1, int n1, int chi,
+                          int* idx /* [2][chi] */, double* lam /* new diag, FSO order */,
+                          SelectOut* out, cudaStream_t s);
+// P^T rows: block p row j = eigenvector idx[p][j] of V_p (column-major n_p x n_p).
+// The new sector sizes are read on the device from sel.
+cudaError_t launch_gather_pt(const double* V0, int n0, const double* V1, int n1, const int* idx,
+                             int chi, const SelectOut* sel, double* PT, cudaStream_t s);
+// C <- diag(lam) / max|lam| in FSO blocks (c0 x c0, c1 x c1).
+cudaError_t launch_diag_corner(const double* lam, int c0, int c1, SelectOut* sel, double* C,
+                               cudaStream_t s);
+// T <- T / max|T| over n entries; log of the factor into sel->log_norm_T.
+cudaError_t launch_normalize_max(double* T, long long n, unsigned long long* scratch,
+                                 SelectOut* sel, cudaStream_t s);
+
+// Dense views of an FSO environment (rotated back to the plain combined basis).
+cudaError_t launch_env_to_dense(const double* C, const double* T, int D, int c0, int c1,
+                                bool hermitian, double* Cd, double* Td, cudaStream_t s);
+
+}  // namespace hs

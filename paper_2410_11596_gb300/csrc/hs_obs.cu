@@ -1,0 +1,190 @@
+// Observables of a converged C4v environment (arXiv 2410.11596 Sec. III.A):
+// the two-site reduced density matrix of a bond and the one-site environment
+// eps of Eq. (4). Both are evaluated once per environment, in FP64, as a chain
+// of permutes and GEMMs over the environment expanded to the plain combined
+// basis; they need the individual bra and ket tensors, which carry no Z2
+// symmetry (Sec. II.B).
+//
+// Networks (C corner, T edge, * open site):
+//   rho:  C T T C / T * * T / C T T C        eps:  C T C / T * T / C T C
+#include "hs_ctx.cuh"
+
+using namespace hs;
+
+namespace {
+
+// Open double layer of one site with its physical legs kept:
+//   out[(s, s', m) | (c0, u, dd)] = A[s, ...] A[s', ...]
+// where m is the open auxiliary leg (right leg r if open_right, else left l)
+// and c0 the other horizontal leg; combined index x = ket + D * bra.
+__global__ void open_double_layer_kernel(const double* __restrict__ A, int d, int D, bool open_right,
+                                         double* __restrict__ out) {
+  const int q = D * D;
+  const long long total = (long long)d * d * q * q * q * q;
+  const long long D4 = (long long)D * D * D * D;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    long long r = e;
+    const int xd = (int)(r % q);
+    r /= q;
+    const int xu = (int)(r % q);
+    r /= q;
+    const int xc = (int)(r % q);
+    r /= q;
+    const int xm = (int)(r % q);
+    r /= q;
+    const int sb = (int)(r % d);
+    const int sk = (int)(r / d);
+    const int xl = open_right ? xc : xm, xr = open_right ? xm : xc;
+    const long long ik = (((long long)(xu % D) * D + xl % D) * D + xd % D) * D + xr % D;
+    const long long ib = (((long long)(xu / D) * D + xl / D) * D + xd / D) * D + xr / D;
+    out[e] = A[sk * D4 + ik] * A[sb * D4 + ib];
+  }
+}
+
+// rho[(s1 s2), (s1' s2')] = rho4[s1, s1', s2, s2']; mirror the upper triangle
+// when requested; tr[0] = Tr rho, tr[1] = Tr(rho h).
+__global__ void finish_rho_kernel(const double* __restrict__ rho4, int d, bool mirror,
+                                  const double* __restrict__ h, double* __restrict__ rho,
+                                  double* __restrict__ tr) {
+  const int n = d * d;
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+    int I = e / n, J = e % n;
+    if (mirror && I > J) {
+      const int t = I;
+      I = J;
+      J = t;
+    }
+    const int s1 = I / d, s2 = I % d, t1 = J / d, t2 = J % d;
+    rho[e] = rho4[((s1 * d + t1) * d + s2) * d + t2];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t0 = 0.0, t1 = 0.0;
+    for (int I = 0; I < n; ++I) {
+      t0 += rho[I * n + I];
+      if (h)
+        for (int J = 0; J < n; ++J) t1 += rho[I * n + J] * h[J * n + I];
+    }
+    tr[0] = t0;
+    tr[1] = t1;
+  }
+}
+
+unsigned grid_for(long long n) {
+  long long g = (n + 255) / 256;
+  if (g > 4096) g = 4096;
+  if (g < 1) g = 1;
+  return (unsigned)g;
+}
+
+// A dense tensor with up to 4 groups of legs as an all-even Z2 matrix.
+Z2Mat dense(std::initializer_list<long long> dims) {
+  Fused r = fused0(), c = fused0();
+  const int n = (int)dims.size();
+  int i = 0;
+  for (long long v : dims) {
+    if (i < n - 1)
+      r.leg[r.k++] = make_sect((int)v, 0);
+    else
+      c.leg[c.k++] = make_sect((int)v, 0);
+    ++i;
+  }
+  return mat(r, c);
+}
+
+GemmGroup dense_gemm(long long M, long long N, long long K) {
+  GemmGroup g{};
+  g.n = 1;
+  g.p[0].M = (int)M;
+  g.p[0].N = (int)N;
+  g.p[0].K = (int)K;
+  g.p[0].lda = (int)K;
+  g.p[0].ldb = (int)K;
+  g.p[0].ldc = (int)N;
+  return g;
+}
+
+}  // namespace
+
+extern "C" hs_status hs_rdm(hs_ctx ctx, const hs_env* env, const double* A, int d, int D,
+                            hs_dtype dtype, hs_rdm_kind kind, const double* h, double* out,
+                            double* tr_out) {
+  HS_TRY(check_ctx(ctx));
+  if (!env || !A || !out || d <= 0 || D != env->D) return fail(HS_ERR_INVALID_ARG, "bad arguments");
+  if (dtype != HS_F64) return fail(HS_ERR_UNSUPPORTED, "complex tensors are not supported by this build");
+  if (kind != HS_RDM_TWO_SITE && kind != HS_RDM_ENV_ONE_SITE)
+    return fail(HS_ERR_INVALID_ARG, "unknown rdm kind");
+  if (kind == HS_RDM_TWO_SITE && !tr_out) return fail(HS_ERR_INVALID_ARG, "tr_out is required");
+  cudaStream_t s = ctx->stream;
+  const hs_gemm_backend be = env->gemm_backend;
+  const long long chi = env->chi_even + env->chi_odd, q = (long long)D * D;
+  const long long c2 = chi * chi, cqc = chi * q * chi, c2q2 = c2 * q * q, c2q3 = c2q2 * q;
+  DBuf* r = ctx->r;
+  HS_TRY(r[0].ensure(c2 * 8));
+  HS_TRY(r[1].ensure(cqc * 8));
+  HS_TRY(r[2].ensure(cqc * 8));
+  HS_TRY(r[3].ensure(cqc * 8));
+  HS_TRY(r[4].ensure(cqc * 8));
+  HS_TRY(r[5].ensure(cqc * 8));
+  HS_TRY(r[6].ensure((c2q2 > c2 ? c2q2 : c2) * 8));
+  HS_TRY(r[7].ensure(c2q2 * 8));
+  HS_TRY(r[8].ensure(c2q3 * 8));
+  HS_TRY(r[9].ensure(c2q3 * 8));
+  double *Cd = r[0].d(), *Td = r[1].d(), *Tsw = r[2].d(), *E1 = r[3].d(), *E = r[4].d(),
+         *Ep = r[5].d(), *Z1 = r[6].d(), *Z1p = r[7].d(), *Z2 = r[8].d(), *Z2p = r[9].d();
+
+  // environment in the plain combined basis
+  HS_CUDA(launch_env_to_dense(env->C, env->T, D, env->chi_even, env->chi_odd,
+                              env->basis == HS_BASIS_HERMITIAN, Cd, Td, s));
+  // Tsw[(x, b) | a] = T[a, x, b]
+  HS_TRY(permute(ctx, dense({chi, q, chi}), dense({q, chi, chi}), {1, 2, 0}, Td, Tsw));
+  // half ring E[t, l, b] = C[t, a] T[a, l, a'] C[a', b]
+  HS_TRY(gemm(ctx, be, dense_gemm(chi, q * chi, chi), Cd, Tsw, E1));          // E1[t | (l, a')]
+  HS_TRY(permute(ctx, dense({chi, chi}), dense({chi, chi}), {1, 0}, Cd, Z1));  // C^T in Z1
+  HS_TRY(gemm(ctx, be, dense_gemm(chi * q, chi, chi), E1, Z1, E));             // E[(t, l) | b]
+  // Z1[l, b, u, t'] = E[t, l, b] T[t, u, t']
+  HS_TRY(permute(ctx, dense({chi, q, chi}), dense({q, chi, chi}), {1, 2, 0}, E, Ep));   // Ep[(l,b)|t]
+  HS_TRY(gemm(ctx, be, dense_gemm(q * chi, q * chi, chi), Ep, Tsw, Z1));
+  // Z2[l, u, t', d, b'] = Z1[l, b, u, t'] T[b, d, b']
+  HS_TRY(permute(ctx, dense({q, chi, q, chi}), dense({q, q, chi, chi}), {0, 2, 3, 1}, Z1, Z1p));
+  HS_TRY(gemm(ctx, be, dense_gemm(q * q * chi, q * chi, chi), Z1p, Tsw, Z2));
+
+  if (kind == HS_RDM_ENV_ONE_SITE) {
+    // Z2 plays Y2[u, l, a', r, b']; eps[u,l,r,d] = Y2[u,l,a',r,b'] H[a',d,b'], H = E
+    HS_TRY(r[12].ensure(cqc * 8));
+    HS_TRY(r[13].ensure(q * q * q * q * 8));
+    HS_TRY(permute(ctx, dense({q * q, chi, q, chi}), dense({q * q, q, chi, chi}), {0, 2, 1, 3}, Z2, Z2p));
+    HS_TRY(permute(ctx, dense({chi, q, chi}), dense({q, chi, chi}), {1, 0, 2}, E, r[12].d()));  // Hd[d|(a',b')]
+    HS_TRY(gemm(ctx, be, dense_gemm(q * q * q, q, chi * chi), Z2p, r[12].d(), r[13].d()));     // [(u,l,r)|d]
+    HS_TRY(permute(ctx, dense({q * q, q, q}), dense({q * q, q, q}), {0, 2, 1}, r[13].d(), out));
+    return HS_OK;
+  }
+
+  const long long d2 = (long long)d * d;
+  HS_TRY(r[10].ensure(d2 * q * q * q * q * 8));
+  HS_TRY(r[11].ensure(d2 * q * q * q * q * 8));
+  HS_TRY(r[12].ensure(c2 * d2 * q * 8));
+  HS_TRY(r[13].ensure(c2 * d2 * q * 8));
+  HS_TRY(r[14].ensure(c2 * d2 * q * 8));
+  HS_TRY(r[15].ensure(c2 * d2 * q * 8));
+  double *aoL = r[10].d(), *aoR = r[11].d(), *LB = r[12].d(), *RB = r[13].d(), *LBp = r[14].d(),
+         *RBp = r[15].d();
+  const long long nao = d2 * q * q * q * q;
+  open_double_layer_kernel<<<grid_for(nao), 256, 0, s>>>(A, d, D, true, aoL);
+  HS_CUDA(cudaGetLastError());
+  open_double_layer_kernel<<<grid_for(nao), 256, 0, s>>>(A, d, D, false, aoR);
+  HS_CUDA(cudaGetLastError());
+  // Z2p[(t', b') | (l, u, d)]
+  HS_TRY(permute(ctx, dense({q * q, chi, q, chi}), dense({chi, chi, q * q, q}), {1, 3, 0, 2}, Z2, Z2p));
+  // LB[(t', b') | (s, s', m)] over (l, u, d); RB over (r, u, d) of the mirror site
+  HS_TRY(gemm(ctx, be, dense_gemm(c2, d2 * q, q * q * q), Z2p, aoL, LB));
+  HS_TRY(gemm(ctx, be, dense_gemm(c2, d2 * q, q * q * q), Z2p, aoR, RB));
+  // [(s, s') | (t', b', m)]
+  HS_TRY(permute(ctx, dense({c2, d2, q}), dense({d2, c2, q}), {1, 0, 2}, LB, LBp));
+  HS_TRY(permute(ctx, dense({c2, d2, q}), dense({d2, c2, q}), {1, 0, 2}, RB, RBp));
+  HS_TRY(gemm(ctx, be, dense_gemm(d2, d2, c2 * q), LBp, RBp, Z1));  // rho4[(s1,s1') | (s2,s2')]
+  finish_rho_kernel<<<1, 256, 0, s>>>(Z1, d, env->basis == HS_BASIS_HERMITIAN, h, out, tr_out);
+  HS_CUDA(cudaGetLastError());
+  return HS_OK;
+}

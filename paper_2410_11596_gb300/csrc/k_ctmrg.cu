@@ -1,0 +1,302 @@
+// Small kernels of the C4v CTMRG move (arXiv 2410.11596 Sec. II.A, Fig. 1(d)):
+// traced-boundary initialisation, selection of the kept eigenvalues across the
+// two parity blocks, projector gather, corner/edge normalisation, and the
+// dense view of an environment.
+#include <cmath>
+
+#include "hs_internal.cuh"
+
+namespace hs {
+
+namespace {
+
+unsigned grid_for(long long n) {
+  long long g = (n + 255) / 256;
+  if (g > 4096) g = 4096;
+  if (g < 1) g = 1;
+  return (unsigned)g;
+}
+
+// Position of T[alpha, x, beta] in FSO [(alpha, x) | beta]; -1 if odd total.
+__device__ __forceinline__ long long t_pos(int pa, int ia, int px, int ix, int pb, int ib, Sect c,
+                                           Sect q) {
+  if ((pa + px + pb) & 1) return -1;
+  const Fused R = fused2(c, q);
+  const int tr = (pa << 1) | px;
+  const int P = pb;
+  const long long CP = c.n[P];
+  const long long row = tuple_offset(R, tr) + (long long)ia * q.n[px] + ix;
+  const long long off = P ? fused_size(R, 0) * (long long)c.n[0] : 0;
+  return off + row * CP + ib;
+}
+
+// Position of a[u, l, d, r] in FSO [(u, l) | (d, r)] (all legs sectors q).
+__device__ __forceinline__ long long a_pos(int pu, int iu, int pl, int il, int pd, int id, int pr,
+                                           int ir, Sect q) {
+  if ((pu + pl + pd + pr) & 1) return -1;
+  const Fused f = fused2(q, q);
+  const int tr = (pu << 1) | pl, tc = (pd << 1) | pr;
+  const int P = tuple_parity(tr);
+  const long long CP = fused_size(f, P);
+  const long long row = tuple_offset(f, tr) + (long long)iu * q.n[pl] + il;
+  const long long col = tuple_offset(f, tc) + (long long)id * q.n[pr] + ir;
+  const long long off = P ? fused_size(f, 0) * fused_size(f, 0) : 0;
+  return off + row * CP + col;
+}
+
+// Traced state k of one leg: Hermitian basis index k (even), or the plain
+// combined index k + D k (dense basis, a single all-even sector).
+__device__ __forceinline__ int traced_local(int k, int D, bool hermitian) {
+  return hermitian ? k : k * (D + 1);
+}
+
+__global__ void init_T_kernel(const double* __restrict__ a, int D, bool hermitian,
+                              double* __restrict__ T) {
+  const int q = D * D;
+  const int qe = hermitian ? D * (D + 1) / 2 : q;
+  const Sect s = make_sect(qe, q - qe);
+  const long long total = (long long)q * q * q;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int u = (int)(e % q), r = (int)((e / q) % q), dd = (int)(e / q / q);
+    const int pd = dd >= qe, pr = r >= qe, pu = u >= qe;
+    const long long pos = t_pos(pd, dd - pd * qe, pr, r - pr * qe, pu, u - pu * qe, s, s);
+    if (pos < 0) continue;
+    double acc = 0.0;
+    for (int k = 0; k < D; ++k) {
+      const long long ap = a_pos(pu, u - pu * qe, 0, traced_local(k, D, hermitian), pd, dd - pd * qe,
+                                 pr, r - pr * qe, s);
+      acc += a[ap];
+    }
+    T[pos] = acc;  // T0[alpha = d, x = r, beta = u]
+  }
+}
+
+__global__ void init_C_kernel(const double* __restrict__ a, int D, bool hermitian,
+                              double* __restrict__ C) {
+  const int q = D * D;
+  const int qe = hermitian ? D * (D + 1) / 2 : q;
+  const Sect s = make_sect(qe, q - qe);
+  const long long total = (long long)q * q;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int r = (int)(e % q), dd = (int)(e / q);
+    const int pd = dd >= qe, pr = r >= qe;
+    if (pd != pr) continue;
+    double acc = 0.0;
+    for (int k = 0; k < D; ++k)
+      for (int m = 0; m < D; ++m) {
+        const long long ap = a_pos(0, traced_local(k, D, hermitian), 0, traced_local(m, D, hermitian),
+                                   pd, dd - pd * qe, pr, r - pr * qe, s);
+        acc += a[ap];
+      }
+    const long long n = s.n[pd];
+    const long long off = pd ? (long long)qe * qe : 0;
+    C[off + (dd - pd * qe) * n + (r - pr * qe)] = acc;
+  }
+}
+
+// Merge the two ascending spectra; keep the chi of largest modulus.
+__global__ void select_kernel(const double* __restrict__ w0, int n0, const double* __restrict__ w1,
+                              int n1, int chi, int* __restrict__ idx, double* __restrict__ lam,
+                              SelectOut* out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const double* w[2] = {w0, w1};
+  int lo[2] = {0, 0}, hi[2] = {n0 - 1, n1 - 1}, cnt[2] = {0, 0};
+  const int keep = min(chi, n0 + n1);
+  double first = 0.0, last = 0.0;
+  for (int s = 0; s <= keep; ++s) {
+    int best_b = -1, best_i = -1;
+    double best = -1.0;
+    for (int b = 0; b < 2; ++b) {
+      if (lo[b] > hi[b]) continue;
+      const int cand[2] = {lo[b], hi[b]};
+      for (int c = 0; c < 2; ++c) {
+        const double v = fabs(w[b][cand[c]]);
+        if (v > best) {  // strict: earlier block, then lower index win ties
+          best = v;
+          best_b = b;
+          best_i = cand[c];
+        }
+      }
+    }
+    if (s == keep) {
+      out->lam_next = best_b < 0 ? 0.0 : best;
+      break;
+    }
+    if (s == 0) first = best;
+    last = best;
+    idx[best_b * chi + cnt[best_b]] = best_i;
+    ++cnt[best_b];
+    if (best_i == lo[best_b])
+      ++lo[best_b];
+    else
+      --hi[best_b];
+  }
+  for (int j = 0; j < cnt[0]; ++j) lam[j] = w0[idx[j]];
+  for (int j = 0; j < cnt[1]; ++j) lam[cnt[0] + j] = w1[idx[chi + j]];
+  out->chi_new[0] = cnt[0];
+  out->chi_new[1] = cnt[1];
+  out->lam_max = first;
+  out->lam_cut = last;
+}
+
+__global__ void gather_pt_kernel(const double* __restrict__ V0, int n0, const double* __restrict__ V1,
+                                 int n1, const int* __restrict__ idx, int chi,
+                                 const SelectOut* __restrict__ sel, double* __restrict__ PT) {
+  const int b = blockIdx.y, j = blockIdx.x;
+  if (j >= sel->chi_new[b]) return;
+  const int n = b ? n1 : n0;
+  const double* src = (b ? V1 : V0) + (long long)idx[b * chi + j] * n;
+  double* dst = PT + (b ? (long long)sel->chi_new[0] * n0 : 0) + (long long)j * n;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
+}
+
+__global__ void diag_corner_kernel(const double* __restrict__ lam, SelectOut* sel, double* C,
+                                   int chi) {
+  const int c0 = sel->chi_new[0], c1 = sel->chi_new[1];
+  const long long total = (long long)c0 * c0 + (long long)c1 * c1;
+  const double inv = 1.0 / sel->lam_max;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    long long r, c, base;
+    if (e < (long long)c0 * c0) {
+      r = e / c0;
+      c = e % c0;
+      base = 0;
+    } else {
+      const long long f = e - (long long)c0 * c0;
+      r = f / c1;
+      c = f % c1;
+      base = c0;
+    }
+    C[e] = (r == c) ? lam[base + r] * inv : 0.0;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) sel->log_norm_C = log(sel->lam_max);
+}
+
+__global__ void absmax_kernel(const double* __restrict__ x, long long n, unsigned long long* m) {
+  double v = 0.0;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x)
+    v = fmax(v, fabs(x[e]));
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(m, (unsigned long long)__double_as_longlong(v));
+}
+
+__global__ void scale_kernel(double* __restrict__ x, long long n, const unsigned long long* m,
+                             SelectOut* sel) {
+  const double mx = __longlong_as_double((long long)*m);
+  const double inv = 1.0 / mx;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x)
+    x[e] *= inv;
+  if (blockIdx.x == 0 && threadIdx.x == 0) sel->log_norm_T = log(mx);
+}
+
+__device__ __forceinline__ int pair_index(int k, int l, int D) {
+  return k * (2 * D - k - 1) / 2 + (l - k - 1);
+}
+
+__global__ void env_to_dense_kernel(const double* __restrict__ C, const double* __restrict__ T, int D,
+                                    int c0, int c1, bool hermitian, double* __restrict__ Cd,
+                                    double* __restrict__ Td) {
+  const int q = D * D, chi = c0 + c1;
+  const int qe = hermitian ? D * (D + 1) / 2 : q;
+  const Sect cs = make_sect(c0, c1), qs = make_sect(qe, q - qe);
+  const long long nT = (long long)chi * q * chi, nC = (long long)chi * chi;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < nT + nC;
+       e += (long long)gridDim.x * blockDim.x) {
+    if (e >= nT) {
+      const long long f = e - nT;
+      const int a = (int)(f / chi), b = (int)(f % chi);
+      const int pa = a >= c0, pb = b >= c0;
+      double v = 0.0;
+      if (pa == pb) {
+        const int n = pa ? c1 : c0;
+        v = C[(pa ? (long long)c0 * c0 : 0) + (long long)(a - pa * c0) * n + (b - pb * c0)];
+      }
+      Cd[f] = v;
+      continue;
+    }
+    const int b = (int)(e % chi), x = (int)((e / chi) % q), a = (int)(e / chi / q);
+    const int pa = a >= c0, pb = b >= c0;
+    int nX = 1, X[2];
+    double w[2];
+    if (!hermitian) {
+      X[0] = x;
+      w[0] = 1.0;
+    } else {
+      const int i = x % D, ib = x / D;
+      if (i == ib) {
+        X[0] = i;
+        w[0] = 1.0;
+      } else {
+        const int k = min(i, ib), l = max(i, ib);
+        const int m = pair_index(k, l, D);
+        const double r = 0.70710678118654752440;
+        nX = 2;
+        X[0] = D + m;
+        w[0] = r;
+        X[1] = qe + m;
+        w[1] = (i < ib) ? r : -r;  // (ket k, bra l) enters the odd state with +, (ket l, bra k) with -
+      }
+    }
+    double v = 0.0;
+    for (int t = 0; t < nX; ++t) {
+      const int px = X[t] >= qe;
+      const long long pos = t_pos(pa, a - pa * c0, px, X[t] - px * qe, pb, b - pb * c0, cs, qs);
+      if (pos >= 0) v += w[t] * T[pos];
+    }
+    Td[e] = v;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_ctmrg_init(const double* a_blocks, int D, bool hermitian, double* C, double* T,
+                              cudaStream_t s) {
+  const long long q = (long long)D * D;
+  init_T_kernel<<<grid_for(q * q * q), 256, 0, s>>>(a_blocks, D, hermitian, T);
+  init_C_kernel<<<grid_for(q * q), 256, 0, s>>>(a_blocks, D, hermitian, C);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_select(const double* w0, int n0, const double* w1, int n1, int chi, int* idx,
+                          double* lam, SelectOut* out, cudaStream_t s) {
+  select_kernel<<<1, 32, 0, s>>>(w0, n0, w1, n1, chi, idx, lam, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather_pt(const double* V0, int n0, const double* V1, int n1, const int* idx,
+                                 int chi, const SelectOut* sel, double* PT, cudaStream_t s) {
+  dim3 grid((unsigned)chi, 2);
+  gather_pt_kernel<<<grid, 256, 0, s>>>(V0, n0, V1, n1, idx, chi, sel, PT);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_diag_corner(const double* lam, int c0, int c1, SelectOut* sel, double* C,
+                               cudaStream_t s) {
+  const long long n = (long long)c0 * c0 + (long long)c1 * c1;
+  diag_corner_kernel<<<grid_for(n), 256, 0, s>>>(lam, sel, C, c0 + c1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_normalize_max(double* T, long long n, unsigned long long* scratch,
+                                 SelectOut* sel, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(scratch, 0, sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return e;
+  absmax_kernel<<<grid_for(n), 256, 0, s>>>(T, n, scratch);
+  scale_kernel<<<grid_for(n), 256, 0, s>>>(T, n, scratch, sel);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_env_to_dense(const double* C, const double* T, int D, int c0, int c1,
+                                bool hermitian, double* Cd, double* Td, cudaStream_t s) {
+  const long long chi = c0 + c1, q = (long long)D * D;
+  env_to_dense_kernel<<<grid_for(chi * q * chi + chi * chi), 256, 0, s>>>(C, T, D, c0, c1, hermitian,
+                                                                         Cd, Td);
+  return cudaGetLastError();
+}
+
+}  // namespace hs

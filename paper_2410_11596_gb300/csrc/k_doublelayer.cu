@@ -1,0 +1,204 @@
+// Double-layer tensor a = sum_s A_s (x) conj(A_s) (arXiv 2410.11596 Sec. II.A,
+// Fig. 1(b)) and its form in the eigenbasis of the bra-ket swap S (Sec. II.B).
+//
+// A basis state X of one combined leg is a combination of at most two plain
+// states (ket i, bra ibar), x = i + D*ibar:
+//   X <  D           : (k k')                   coefficient 1
+//   D <= X < q_even  : (k l' + l k')/sqrt2, k<l  lexicographic pair X - D
+//   X >= q_even      : (k l' - l k')/sqrt2, k<l  pair X - q_even
+#include <cmath>
+
+#include "hs_internal.cuh"
+
+namespace hs {
+
+namespace {
+
+struct Terms {
+  int n;
+  int ket[2], bra[2];
+  double c[2];
+};
+
+// Pair number m -> (k, l), k < l, lexicographic.
+__device__ __forceinline__ void pair_of(int m, int D, int* k, int* l) {
+  int kk = 0;
+  while (m >= D - 1 - kk) {
+    m -= D - 1 - kk;
+    ++kk;
+  }
+  *k = kk;
+  *l = kk + 1 + m;
+}
+
+__device__ __forceinline__ Terms basis_terms(int X, int D, bool hermitian) {
+  Terms t;
+  if (!hermitian) {
+    t.n = 1;
+    t.ket[0] = X % D;
+    t.bra[0] = X / D;
+    t.c[0] = 1.0;
+    return t;
+  }
+  const int qe = D * (D + 1) / 2;
+  if (X < D) {
+    t.n = 1;
+    t.ket[0] = X;
+    t.bra[0] = X;
+    t.c[0] = 1.0;
+    return t;
+  }
+  int k, l;
+  const bool odd = X >= qe;
+  pair_of(odd ? X - qe : X - D, D, &k, &l);
+  const double r = 0.70710678118654752440;
+  t.n = 2;
+  t.ket[0] = k;
+  t.bra[0] = l;
+  t.c[0] = r;
+  t.ket[1] = l;
+  t.bra[1] = k;
+  t.c[1] = odd ? -r : r;
+  return t;
+}
+
+// FSO position of element (X_u, X_l, X_d, X_r) of a [(u,l)|(d,r)] matrix whose
+// legs all have sectors (qe, qo); returns -1 for odd-total elements.
+__device__ __forceinline__ long long fso4(int Xu, int Xl, int Xd, int Xr, int qe, int qo) {
+  const Sect s = make_sect(qe, qo);
+  const Fused f = fused2(s, s);
+  const int pu = Xu >= qe, pl = Xl >= qe, pd = Xd >= qe, pr = Xr >= qe;
+  if ((pu + pl + pd + pr) & 1) return -1;
+  const int iu = Xu - pu * qe, il = Xl - pl * qe, id = Xd - pd * qe, ir = Xr - pr * qe;
+  const int tr = (pu << 1) | pl, tc = (pd << 1) | pr;
+  const int P = tuple_parity(tr);
+  const long long CP = fused_size(f, P);
+  const long long row = tuple_offset(f, tr) + (long long)iu * s.n[pl] + il;
+  const long long col = tuple_offset(f, tc) + (long long)id * s.n[pr] + ir;
+  const long long off = P ? fused_size(f, 0) * fused_size(f, 0) : 0;
+  return off + row * CP + col;
+}
+
+__global__ void double_layer_blocks_kernel(const double* __restrict__ A, int d, int D,
+                                           bool hermitian, double* __restrict__ out) {
+  const int q = D * D;
+  const int qe = hermitian ? D * (D + 1) / 2 : q;
+  const int qo = q - qe;
+  const long long total = (long long)q * q * q * q;
+  const long long D4 = (long long)D * D * D * D;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int Xr = (int)(e % q), Xd = (int)((e / q) % q), Xl = (int)((e / q / q) % q),
+              Xu = (int)(e / q / q / q);
+    const long long pos = fso4(Xu, Xl, Xd, Xr, qe, qo);
+    if (pos < 0) continue;
+    const Terms tu = basis_terms(Xu, D, hermitian), tl = basis_terms(Xl, D, hermitian),
+                td = basis_terms(Xd, D, hermitian), tr = basis_terms(Xr, D, hermitian);
+    double acc = 0.0;
+    for (int a = 0; a < tu.n; ++a)
+      for (int b = 0; b < tl.n; ++b)
+        for (int c = 0; c < td.n; ++c)
+          for (int g = 0; g < tr.n; ++g) {
+            const double coef = tu.c[a] * tl.c[b] * td.c[c] * tr.c[g];
+            const long long ik = (((long long)tu.ket[a] * D + tl.ket[b]) * D + td.ket[c]) * D + tr.ket[g];
+            const long long ib = (((long long)tu.bra[a] * D + tl.bra[b]) * D + td.bra[c]) * D + tr.bra[g];
+            double s = 0.0;
+            for (int p = 0; p < d; ++p) s += A[p * D4 + ik] * A[p * D4 + ib];
+            acc += coef * s;
+          }
+    out[pos] = acc;
+  }
+}
+
+__global__ void double_layer_dense_kernel(const double* __restrict__ A, int d, int D, bool cplx,
+                                          double* __restrict__ out) {
+  const int q = D * D;
+  const long long total = (long long)q * q * q * q;
+  const long long D4 = (long long)D * D * D * D;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int xr = (int)(e % q), xd = (int)((e / q) % q), xl = (int)((e / q / q) % q),
+              xu = (int)(e / q / q / q);
+    const long long ik = (((long long)(xu % D) * D + xl % D) * D + xd % D) * D + xr % D;
+    const long long ib = (((long long)(xu / D) * D + xl / D) * D + xd / D) * D + xr / D;
+    if (!cplx) {
+      double s = 0.0;
+      for (int p = 0; p < d; ++p) s += A[p * D4 + ik] * A[p * D4 + ib];
+      out[e] = s;
+    } else {
+      double re = 0.0, im = 0.0;
+      for (int p = 0; p < d; ++p) {
+        const double ar = A[2 * (p * D4 + ik)], ai = A[2 * (p * D4 + ik) + 1];
+        const double br = A[2 * (p * D4 + ib)], bi = -A[2 * (p * D4 + ib) + 1];
+        re += ar * br - ai * bi;
+        im += ar * bi + ai * br;
+      }
+      out[2 * e] = re;
+      out[2 * e + 1] = im;
+    }
+  }
+}
+
+__global__ void rotate_dense_kernel(const double* __restrict__ a, int D, double* __restrict__ out,
+                                    unsigned long long* maxes) {
+  const int q = D * D;
+  const int qe = D * (D + 1) / 2, qo = q - qe;
+  const long long total = (long long)q * q * q * q;
+  double mall = 0.0, modd = 0.0;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int Xr = (int)(e % q), Xd = (int)((e / q) % q), Xl = (int)((e / q / q) % q),
+              Xu = (int)(e / q / q / q);
+    const Terms tu = basis_terms(Xu, D, true), tl = basis_terms(Xl, D, true),
+                td = basis_terms(Xd, D, true), tr = basis_terms(Xr, D, true);
+    double acc = 0.0;
+    for (int i = 0; i < tu.n; ++i)
+      for (int j = 0; j < tl.n; ++j)
+        for (int k = 0; k < td.n; ++k)
+          for (int m = 0; m < tr.n; ++m) {
+            const long long x = (((long long)(tu.ket[i] + D * tu.bra[i]) * q + (tl.ket[j] + D * tl.bra[j])) * q +
+                                 (td.ket[k] + D * td.bra[k])) * q + (tr.ket[m] + D * tr.bra[m]);
+            acc += tu.c[i] * tl.c[j] * td.c[k] * tr.c[m] * a[x];
+          }
+    const long long pos = fso4(Xu, Xl, Xd, Xr, qe, qo);
+    mall = fmax(mall, fabs(acc));
+    if (pos < 0)
+      modd = fmax(modd, fabs(acc));
+    else
+      out[pos] = acc;
+  }
+  atomicMax(&maxes[0], (unsigned long long)__double_as_longlong(modd));
+  atomicMax(&maxes[1], (unsigned long long)__double_as_longlong(mall));
+}
+
+unsigned grid_for(long long n) {
+  long long g = (n + 255) / 256;
+  if (g > 4096) g = 4096;
+  if (g < 1) g = 1;
+  return (unsigned)g;
+}
+
+}  // namespace
+
+cudaError_t launch_double_layer_blocks(const double* A, int d, int D, bool hermitian, double* out,
+                                       cudaStream_t s) {
+  const long long q = (long long)D * D;
+  double_layer_blocks_kernel<<<grid_for(q * q * q * q), 256, 0, s>>>(A, d, D, hermitian, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_double_layer_dense(const double* A, int d, int D, bool cplx, double* out,
+                                      cudaStream_t s) {
+  const long long q = (long long)D * D;
+  double_layer_dense_kernel<<<grid_for(q * q * q * q), 256, 0, s>>>(A, d, D, cplx, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rotate_dense_to_blocks(const double* a, int D, double* out,
+                                          unsigned long long* maxes, cudaStream_t s) {
+  const long long q = (long long)D * D;
+  rotate_dense_kernel<<<grid_for(q * q * q * q), 256, 0, s>>>(a, D, out, maxes);
+  return cudaGetLastError();
+}
+
+}  // namespace hs

@@ -1,0 +1,67 @@
+"""The C-ABI library builds, loads and exports every entry point of include/hs.h (no GPU needed)."""
+import ctypes
+import os
+
+import pytest
+
+from paper_2410_11596_gb300 import _lib as L, build
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not os.path.exists(L.LIB_PATH) or any(
+            os.path.getmtime(s) > os.path.getmtime(L.LIB_PATH) for s in build.sources()):
+        build.build()
+    return L.load()
+
+
+def test_every_declared_function_is_exported(lib):
+    names = L.header_functions()
+    assert len(names) >= 12
+    for name in names:
+        assert hasattr(lib, name), name
+        assert isinstance(getattr(lib, name), ctypes._CFuncPtr)
+
+
+def test_binding_covers_header():
+    assert set(L.header_functions()) == set(L._PROTOS)
+
+
+def test_abi_version(lib):
+    assert lib.hs_abi_version() == 1
+
+
+@pytest.mark.parametrize("D", [1, 2, 3, 4, 5, 6, 7])
+def test_z2_tensor_bytes_closed_form(lib, D):
+    """Stored entries of a~: q_e^4 + 6 q_e^2 q_o^2 + q_o^4 (even-total blocks only)."""
+    qe, qo = D * (D + 1) // 2, D * (D - 1) // 2
+    assert L.hs_z2_tensor_bytes(D, L.HS_BASIS_HERMITIAN) == 8 * (qe ** 4 + 6 * qe ** 2 * qo ** 2 + qo ** 4)
+    assert L.hs_z2_tensor_bytes(D, L.HS_BASIS_DENSE) == 8 * D ** 8
+
+
+def test_d6_storage_fraction(lib):
+    """D = 6: 840456 of 1679616 entries stored (50.04%), the twofold memory saving of Sec. I."""
+    assert L.hs_z2_tensor_bytes(6, L.HS_BASIS_HERMITIAN) // 8 == 840456
+
+
+def test_env_bytes(lib):
+    assert L.hs_env_bytes(6, 144) == (144 * 144 * 8, 144 * 36 * 144 * 8)
+    assert L.hs_env_bytes(6, 8) == (36 * 36 * 8, 36 * 36 * 36 * 8)   # at least chi0 = D^2
+
+
+def test_errors_are_reported_not_raised_in_c(lib):
+    with pytest.raises(L.HsError) as e:
+        L.hs_env_bytes(0, 10)
+    assert e.value.status == -1
+    assert "bad arguments" in str(e.value)
+    assert lib.hs_destroy(None) == 0
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    with pytest.raises(L.HsError):
+        saved = L._lib
+        L._lib = None
+        try:
+            L.load(str(tmp_path / "nope.so"))
+        finally:
+            L._lib = saved
