@@ -212,6 +212,43 @@ hs_status hs_env_to_dense(hs_ctx ctx, const hs_env* env, double* C_dense, double
 hs_status hs_rdm(hs_ctx ctx, const hs_env* env, const double* A, int d, int D, hs_dtype dtype,
                  hs_rdm_kind kind, const double* h, double* out, double* tr_out);
 
+/* ---- profiling ------------------------------------------------------- */
+
+/* Phases of hs_ctmrg_move timed with CUDA events on the context stream. */
+typedef enum {
+  HS_PHASE_GEMM = 0,      /* block GEMMs (own kernels or cuBLAS) */
+  HS_PHASE_PERMUTE = 1,   /* leg permutations between block layouts */
+  HS_PHASE_EIG = 2,       /* per-block symmetric eigen-decompositions */
+  HS_PHASE_SELECT = 3,    /* choice of kept states, projector gather, new corner */
+  HS_PHASE_NORMALIZE = 4, /* max-abs normalisation of the edge */
+  HS_PHASE_GEMM_TC = 5,   /* block GEMMs on the tensor cores (TF32/BF16 modes) */
+  HS_PHASE_COUNT = 6
+} hs_phase;
+
+/* Turn per-phase timing on (1) or off (0); either way the counters reset.
+ * Timing adds events between phases but changes no computation. */
+hs_status hs_profile_enable(hs_ctx ctx, int enable);
+
+/* Read the counters accumulated since the last reset: phase_ms[i] and
+ * phase_flops[i] (host, n_phases entries: milliseconds of device time and
+ * algorithmic flops, sum of 2 M N K over the block GEMMs, per phase) and
+ * launches (number of this library's own kernel launches; library calls such
+ * as cuSOLVER and cuBLAS are not counted). Any output pointer may be NULL. */
+hs_status hs_profile_read(hs_ctx ctx, double* phase_ms, double* phase_flops, int n_phases,
+                          long long* launches);
+
+/* ---- block GEMM primitive (Sec. II.B) --------------------------------- */
+
+/* C[M, N] = A[M, K] B[N, K]^T for row-major FP64 device matrices with leading
+ * dimensions lda >= K, ldb >= K, ldc >= N: the dense GEMM that the Z2 block
+ * contraction performs inside one parity block. HS_PREC_F64 runs the FP64
+ * kernel; the TF32/BF16 modes split A and B into hi/lo parts (padded copies in
+ * the context workspace) and run the tcgen05 tensor-core kernel with FP32
+ * accumulation, writing FP64. Asynchronous; a timed-out device wait is
+ * reported by the next hs_sync as HS_ERR_TIMEOUT. */
+hs_status hs_gemm(hs_ctx ctx, hs_precision precision, int M, int N, int K, const double* A, int lda,
+                  const double* B, int ldb, double* C, int ldc);
+
 /* Workspace the context will allocate for (D, chi): reported for planning. */
 hs_status hs_workspace_query(int D, int chi, hs_precision precision, size_t* bytes);
 

@@ -75,7 +75,13 @@ _PROTOS = {
     "hs_rdm": (c_int, [c_void_p, POINTER(Env), c_void_p, c_int, c_int, c_int, c_int, c_void_p, c_void_p,
                        c_void_p]),
     "hs_workspace_query": (c_int, [c_int, c_int, c_int, POINTER(c_size_t)]),
+    "hs_profile_enable": (c_int, [c_void_p, c_int]),
+    "hs_profile_read": (c_int, [c_void_p, POINTER(c_double), POINTER(c_double), c_int,
+                                POINTER(ctypes.c_longlong)]),
+    "hs_gemm": (c_int, [c_void_p, c_int, c_int, c_int, c_int, c_void_p, c_int, c_void_p, c_int, c_void_p, c_int]),
 }
+
+PHASES = ("gemm", "permute", "eig", "select", "normalize", "gemm_tc")
 
 _lib = None
 
@@ -184,3 +190,23 @@ def hs_workspace_query(D: int, chi: int, precision: int) -> int:
     b = c_size_t()
     check(load().hs_workspace_query(D, chi, precision, ctypes.byref(b)))
     return b.value
+
+
+def hs_profile_enable(ctx: int, enable: bool) -> None:
+    check(load().hs_profile_enable(ctx, 1 if enable else 0))
+
+
+def hs_profile_read(ctx: int) -> dict:
+    ms = (c_double * len(PHASES))()
+    fl = (c_double * len(PHASES))()
+    n = ctypes.c_longlong()
+    check(load().hs_profile_read(ctx, ms, fl, len(PHASES), ctypes.byref(n)))
+    return {"phase_ms": dict(zip(PHASES, list(ms))), "phase_flops": dict(zip(PHASES, list(fl))),
+            "launches": n.value}
+
+
+def hs_gemm(ctx: int, precision: int, A, B, C) -> None:
+    """C = A B^T for contiguous row-major FP64 device tensors."""
+    M, K = A.shape
+    N = B.shape[0]
+    check(load().hs_gemm(ctx, precision, M, N, K, ptr(A), K, ptr(B), K, ptr(C), N))

@@ -1,6 +1,8 @@
 // C ABI of libhs (include/hs.h): context, workspace, the C4v CTMRG move of
 // arXiv 2410.11596 (Sec. II.A, Fig. 1(d)) in the Hermitian Z2 basis
 // (Sec. II.B).
+#include <utility>
+
 #include "hs_ctx.cuh"
 
 using namespace hs;
@@ -34,10 +36,11 @@ Sect q_sect(int D, hs_basis b) {
   return b == HS_BASIS_HERMITIAN ? make_sect(D * (D + 1) / 2, D * (D - 1) / 2) : make_sect(q, 0);
 }
 
-Z2Mat mat(Fused r, Fused c) {
+Z2Mat mat(Fused r, Fused c, int pad) {
   Z2Mat m;
   m.r = r;
   m.c = c;
+  m.pad = pad;
   return m;
 }
 
@@ -58,6 +61,7 @@ hs_status gemm(hs_ctx ctx, hs_gemm_backend be, const GemmGroup& g, const double*
     return HS_OK;
   }
   HS_CUDA(launch_gemm_f64(g, A, B, C, 1.0, ctx->stream));
+  if (g.n > 0) ctx->launches += 1;
   return HS_OK;
 }
 
@@ -68,8 +72,49 @@ hs_status permute(hs_ctx ctx, const Z2Mat& in, const Z2Mat& out, std::initialize
   for (int v : perm) p[i++] = v;
   const PermPlan plan = make_perm_plan(in, out, p);
   HS_CUDA(launch_permute_f64(plan, src, dst, 1.0, ctx->stream));
+  if (plan.nbox > 0) ctx->launches += 1;
   return HS_OK;
 }
+
+namespace {
+int take_event(hs_ctx c) {
+  if (c->next_event >= (int)c->events.size()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return -1;
+    c->events.push_back(e);
+  }
+  return c->next_event++;
+}
+}  // namespace
+
+PhaseScope::PhaseScope(hs_ctx c, int phase) : c_(c), phase_(phase), e0_(-1) {
+  if (!c_->prof) return;
+  e0_ = take_event(c_);
+  if (e0_ >= 0) cudaEventRecord(c_->events[e0_], c_->stream);
+}
+
+PhaseScope::~PhaseScope() {
+  if (!c_->prof || e0_ < 0) return;
+  const int e1 = take_event(c_);
+  if (e1 < 0) return;
+  cudaEventRecord(c_->events[e1], c_->stream);
+  c_->recs.push_back({phase_, e0_, e1});
+}
+
+void harvest_profile(hs_ctx ctx) {
+  for (const auto& r : ctx->recs) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, ctx->events[r.e0], ctx->events[r.e1]) == cudaSuccess)
+      ctx->phase_ms[r.phase] += ms;
+  }
+  cudaGetLastError();
+  ctx->recs.clear();
+  ctx->next_event = 0;
+}
+
+int tc_pad(hs_precision p) { return p == HS_PREC_BF16X3 ? 64 : 32; }
+int tc_elem_bytes(hs_precision p) { return p == HS_PREC_BF16X3 ? 2 : 4; }
+int tc_mode(hs_precision p) { return p == HS_PREC_BF16X3 ? 2 : 1; }
 
 namespace {
 
@@ -99,6 +144,56 @@ hs_status eig_block(hs_ctx ctx, double* A, int n, double* w, int slot) {
 }
 
 }  // namespace
+
+// C[R|N] = X[R|K] a[N|K]^T on the tensor cores. X is produced here from `src`
+// (layout Xsrc) by the permutation `perm`, written straight into the split,
+// K-padded operand buffers; a is the split copy made by hs_ctmrg_init.
+hs_status tc_a_gemm(hs_ctx ctx, hs_precision prec, const Z2Mat& Xsrc, const Z2Mat& X,
+                    std::initializer_list<int> perm, const double* src, const Z2Mat& Am, const Z2Mat& Cm,
+                    double* C) {
+  const int pad = tc_pad(prec), eb = tc_elem_bytes(prec);
+  const Z2Mat Xp = mat(X.r, X.c, pad), Amp = mat(Am.r, Am.c, pad);
+  const size_t nb = (size_t)z2_elems(Xp) * eb;
+  if (nb > ctx->tc_x_hi.bytes) return fail(HS_ERR_WORKSPACE, "tensor-core operand buffer too small");
+  {
+    PhaseScope ps(ctx, HS_PHASE_PERMUTE);
+    int pm[4] = {0, 0, 0, 0}, i = 0;
+    for (int v : perm) pm[i++] = v;
+    HS_CUDA(cudaMemsetAsync(ctx->tc_x_hi.p, 0, nb, ctx->stream));
+    HS_CUDA(cudaMemsetAsync(ctx->tc_x_lo.p, 0, nb, ctx->stream));
+    const PermPlan plan = make_perm_plan(Xsrc, Xp, pm);
+    HS_CUDA(launch_permute_split(plan, src, ctx->tc_x_hi.p, ctx->tc_x_lo.p, tc_mode(prec), ctx->stream));
+    if (plan.nbox > 0) ctx->launches += 1;
+  }
+  TcProblem pr[2];
+  int n = 0;
+  for (int p = 0; p < 2; ++p) {
+    TcProblem& t = pr[n];
+    t.M = (int)z2_rows(Xp, p);
+    t.N = (int)z2_rows(Amp, p);
+    t.Kp = (int)z2_ld(Xp, p);
+    if (t.M == 0 || t.N == 0) continue;
+    if (z2_cols(Xp, p) == 0) {  // empty contraction: the block is zero
+      HS_CUDA(cudaMemset2DAsync(C + z2_block_off(Cm, p), sizeof(double) * z2_ld(Cm, p), 0,
+                                sizeof(double) * t.N, t.M, ctx->stream));
+      continue;
+    }
+    t.ldc = (int)z2_ld(Cm, p);
+    t.a_hi = static_cast<char*>(ctx->tc_x_hi.p) + z2_block_off(Xp, p) * eb;
+    t.a_lo = static_cast<char*>(ctx->tc_x_lo.p) + z2_block_off(Xp, p) * eb;
+    t.b_hi = static_cast<char*>(ctx->tc_a_hi.p) + z2_block_off(Amp, p) * eb;
+    t.b_lo = static_cast<char*>(ctx->tc_a_lo.p) + z2_block_off(Amp, p) * eb;
+    t.c = C + z2_block_off(Cm, p);
+    ++n;
+  }
+  {
+    PhaseScope ps(ctx, HS_PHASE_GEMM_TC);
+    HS_CUDA(launch_gemm_tc(prec, pr, n, static_cast<int*>(ctx->tc_err.p), ctx->stream));
+    if (n > 0) ctx->launches += 1;
+  }
+  return HS_OK;
+}
+
 }  // namespace hs
 
 // ---------------------------------------------------------------------------
@@ -135,16 +230,21 @@ hs_status hs_create(hs_ctx* out, int device, void* stream) {
     return fail(HS_ERR_SOLVER, "cuBLAS initialisation failed");
   }
   if (cudaMallocHost(&c->h_sel, sizeof(SelectOut)) != cudaSuccess ||
-      cudaMallocHost(&c->h_info, 4 * sizeof(int)) != cudaSuccess) {
+      cudaMallocHost(&c->h_info, 4 * sizeof(int)) != cudaSuccess ||
+      cudaMallocHost(&c->h_tc_err, sizeof(int)) != cudaSuccess) {
     cudaGetLastError();
     hs_destroy(c);
     return fail(HS_ERR_CUDA, "pinned allocation failed");
   }
   hs_status st;
   if ((st = c->sel.ensure(sizeof(SelectOut))) != HS_OK || (st = c->info.ensure(4 * sizeof(int))) != HS_OK ||
-      (st = c->scratch.ensure(64)) != HS_OK) {
+      (st = c->scratch.ensure(64)) != HS_OK || (st = c->tc_err.ensure(64)) != HS_OK) {
     hs_destroy(c);
     return st;
+  }
+  if (cudaMemset(c->tc_err.p, 0, 64) != cudaSuccess) {
+    hs_destroy(c);
+    return fail(HS_ERR_CUDA, "cudaMemset failed");
   }
   *out = c;
   return HS_OK;
@@ -154,12 +254,16 @@ hs_status hs_destroy(hs_ctx ctx) {
   if (!ctx) return HS_OK;
   cudaSetDevice(ctx->device);
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
-  DBuf* bufs[] = {&ctx->big1, &ctx->big2, &ctx->x1, &ctx->pt, &ctx->pp, &ctx->w, &ctx->lam,
-                  &ctx->idx, &ctx->sel, &ctx->scratch, &ctx->info, &ctx->solver_dev};
+  DBuf* bufs[] = {&ctx->big1,    &ctx->big2,    &ctx->x1,      &ctx->pt,      &ctx->pp,
+                  &ctx->w,       &ctx->lam,     &ctx->idx,     &ctx->sel,     &ctx->scratch,
+                  &ctx->info,    &ctx->solver_dev, &ctx->tc_a_hi, &ctx->tc_a_lo, &ctx->tc_x_hi,
+                  &ctx->tc_x_lo, &ctx->tc_b_hi, &ctx->tc_b_lo, &ctx->tc_err};
   for (DBuf* b : bufs) b->release();
   for (DBuf& b : ctx->r) b.release();
+  for (cudaEvent_t e : ctx->events) cudaEventDestroy(e);
   if (ctx->h_sel) cudaFreeHost(ctx->h_sel);
   if (ctx->h_info) cudaFreeHost(ctx->h_info);
+  if (ctx->h_tc_err) cudaFreeHost(ctx->h_tc_err);
   if (ctx->params) cusolverDnDestroyParams(ctx->params);
   if (ctx->solver) cusolverDnDestroy(ctx->solver);
   if (ctx->blas) cublasDestroy(ctx->blas);
@@ -169,7 +273,13 @@ hs_status hs_destroy(hs_ctx ctx) {
 
 hs_status hs_sync(hs_ctx ctx) {
   HS_TRY(check_ctx(ctx));
+  HS_CUDA(cudaMemcpyAsync(ctx->h_tc_err, ctx->tc_err.p, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   HS_CUDA(cudaStreamSynchronize(ctx->stream));
+  if (*ctx->h_tc_err != 0) {
+    const int code = *ctx->h_tc_err;
+    HS_CUDA(cudaMemsetAsync(ctx->tc_err.p, 0, sizeof(int), ctx->stream));
+    return fail(HS_ERR_TIMEOUT, "a bounded wait in the tensor-core GEMM gave up (code %d)", code);
+  }
   return HS_OK;
 }
 
@@ -259,8 +369,9 @@ hs_status hs_ctmrg_init(hs_ctx ctx, const hs_z2_tensor* a, int chi_max, hs_preci
                         hs_gemm_backend backend, hs_env* env) {
   HS_TRY(check_ctx(ctx));
   if (!a || !env || !a->data || !env->C || !env->T) return fail(HS_ERR_INVALID_ARG, "bad arguments");
-  if (precision != HS_PREC_F64)
-    return fail(HS_ERR_UNSUPPORTED, "precision %d is not implemented in this build", (int)precision);
+  if (precision != HS_PREC_F64 && precision != HS_PREC_TF32X3 && precision != HS_PREC_TF32 &&
+      precision != HS_PREC_BF16X3)
+    return fail(HS_ERR_INVALID_ARG, "unknown precision %d", (int)precision);
   const int D = a->D, q = D * D;
   if (chi_max < 1) return fail(HS_ERR_SHAPE, "chi_max must be positive");
   size_t cb, tb;
@@ -305,6 +416,24 @@ hs_status hs_ctmrg_init(hs_ctx ctx, const hs_z2_tensor* a, int chi_max, hs_preci
   HS_TRY(ctx->lam.ensure(c * sizeof(double)));
   HS_TRY(ctx->idx.ensure(2 * c * sizeof(int)));
   HS_TRY(eig_workspace(ctx, (int)(c * q)));
+  if (precision != HS_PREC_F64) {
+    // split, padded copy of the double layer: the B operand of both a-GEMMs
+    const int pad = tc_pad(precision), eb = tc_elem_bytes(precision);
+    const Z2Mat Am = mat(fused2(qs, qs), fused2(qs, qs)), Amp = mat(fused2(qs, qs), fused2(qs, qs), pad);
+    const size_t nb = (size_t)z2_elems(Amp) * eb;
+    HS_TRY(ctx->tc_a_hi.ensure(nb));
+    HS_TRY(ctx->tc_a_lo.ensure(nb));
+    HS_CUDA(cudaMemsetAsync(ctx->tc_a_hi.p, 0, nb, ctx->stream));
+    HS_CUDA(cudaMemsetAsync(ctx->tc_a_lo.p, 0, nb, ctx->stream));
+    const int ident[4] = {0, 1, 2, 3};
+    HS_CUDA(launch_permute_split(make_perm_plan(Am, Amp, ident), a->data, ctx->tc_a_hi.p, ctx->tc_a_lo.p,
+                                 tc_mode(precision), ctx->stream));
+    ctx->tc_a_src = a->data;
+    ctx->tc_a_prec = precision;
+    const size_t xb = (c * c * ((size_t)q * q + pad)) * eb;
+    HS_TRY(ctx->tc_x_hi.ensure(xb));
+    HS_TRY(ctx->tc_x_lo.ensure(xb));
+  }
   return HS_OK;
 }
 
@@ -317,6 +446,9 @@ hs_status hs_ctmrg_move(hs_ctx ctx, const hs_z2_tensor* a, hs_env* env, int chi,
   if (chi < 1 || chi > env->chi_max) return fail(HS_ERR_SHAPE, "chi %d outside [1, %d]", chi, env->chi_max);
   cudaStream_t s = ctx->stream;
   const hs_gemm_backend be = env->gemm_backend;
+  const bool tc = env->precision != HS_PREC_F64;
+  if (tc && (ctx->tc_a_src != a->data || ctx->tc_a_prec != (int)env->precision))
+    return fail(HS_ERR_INVALID_ARG, "the double layer changed since hs_ctmrg_init (tensor-core copy is stale)");
   const Sect q = make_sect(env->q_even, env->q_odd);
   const Sect c = make_sect(env->chi_even, env->chi_odd);
   double* B1 = ctx->big1.d();
@@ -334,11 +466,28 @@ hs_status hs_ctmrg_move(hs_ctx ctx, const hs_z2_tensor* a, hs_env* env, int chi,
   GemmGroup g1 = make_z2_gemm(Tcr, Cm, X1), g2 = make_z2_gemm(X1, Tcr, X2),
             g3 = make_z2_gemm(X2p, Am, X3);
   flops += gemm_flops(g1) + gemm_flops(g2) + gemm_flops(g3);
-  HS_TRY(gemm(ctx, be, g1, env->T, env->C, ctx->x1.d()));
-  HS_TRY(gemm(ctx, be, g2, ctx->x1.d(), env->T, B1));
-  HS_TRY(permute(ctx, X2, X2p, {0, 2, 3, 1}, B1, B2));  // (a,x,e,y) -> (a,e,y,x)
-  HS_TRY(gemm(ctx, be, g3, B2, a->data, B1));
-  HS_TRY(permute(ctx, X3, Cp, {0, 2, 1, 3}, B1, B2));   // (a,e,d,r) -> (a,d,e,r)
+  ctx->phase_flops[HS_PHASE_GEMM] += gemm_flops(g1) + gemm_flops(g2);
+  ctx->phase_flops[tc ? HS_PHASE_GEMM_TC : HS_PHASE_GEMM] += gemm_flops(g3);
+  {
+    PhaseScope ps(ctx, HS_PHASE_GEMM);
+    HS_TRY(gemm(ctx, be, g1, env->T, env->C, ctx->x1.d()));
+    HS_TRY(gemm(ctx, be, g2, ctx->x1.d(), env->T, B1));
+  }
+  if (tc) {
+    HS_TRY(tc_a_gemm(ctx, env->precision, X2, X2p, {0, 2, 3, 1}, B1, Am, X3, B2));
+    std::swap(B1, B2);  // X3 now in B1, as on the FP64 path
+  } else {
+    {
+      PhaseScope ps(ctx, HS_PHASE_PERMUTE);
+      HS_TRY(permute(ctx, X2, X2p, {0, 2, 3, 1}, B1, B2));  // (a,x,e,y) -> (a,e,y,x)
+    }
+    PhaseScope ps(ctx, HS_PHASE_GEMM);
+    HS_TRY(gemm(ctx, be, g3, B2, a->data, B1));
+  }
+  {
+    PhaseScope ps(ctx, HS_PHASE_PERMUTE);
+    HS_TRY(permute(ctx, X3, Cp, {0, 2, 1, 3}, B1, B2));   // (a,e,d,r) -> (a,d,e,r)
+  }
 
   // one FP64 eigen-decomposition per parity block
   const int n0 = (int)z2_rows(Cp, 0), n1 = (int)z2_rows(Cp, 1);
@@ -347,11 +496,18 @@ hs_status hs_ctmrg_move(hs_ctx ctx, const hs_z2_tensor* a, hs_env* env, int chi,
   double* w0 = ctx->w.d();
   double* w1 = w0 + n0;
   HS_CUDA(cudaMemsetAsync(ctx->info.p, 0, 2 * sizeof(int), s));
-  HS_TRY(eig_block(ctx, V0, n0, w0, 0));
-  HS_TRY(eig_block(ctx, V1, n1, w1, 1));
+  {
+    PhaseScope ps(ctx, HS_PHASE_EIG);
+    HS_TRY(eig_block(ctx, V0, n0, w0, 0));
+    HS_TRY(eig_block(ctx, V1, n1, w1, 1));
+  }
   SelectOut* dsel = static_cast<SelectOut*>(ctx->sel.p);
   int* didx = static_cast<int*>(ctx->idx.p);
-  HS_CUDA(launch_select(w0, n0, w1, n1, chi, didx, ctx->lam.d(), dsel, s));
+  {
+    PhaseScope ps(ctx, HS_PHASE_SELECT);
+    HS_CUDA(launch_select(w0, n0, w1, n1, chi, didx, ctx->lam.d(), dsel, s));
+    ctx->launches += 1;
+  }
   HS_CUDA(cudaMemcpyAsync(ctx->h_sel, dsel, sizeof(SelectOut), cudaMemcpyDeviceToHost, s));
   HS_CUDA(cudaMemcpyAsync(ctx->h_info, ctx->info.p, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
   HS_CUDA(cudaStreamSynchronize(s));
@@ -370,23 +526,65 @@ hs_status hs_ctmrg_move(hs_ctx ctx, const hs_z2_tensor* a, hs_env* env, int chi,
   const Z2Mat Zm = mat(fused2(cn, c), fused2(q, q));
   const Z2Mat Zp = mat(fused2(cn, q), fused2(c, q));
   const Z2Mat Tn = mat(fused2(cn, q), fused1(cn));
-  HS_CUDA(launch_gather_pt(V0, n0, V1, n1, didx, chi, dsel, ctx->pt.d(), s));
-  HS_TRY(permute(ctx, PT, Pp, {2, 0, 1}, ctx->pt.d(), ctx->pp.d()));  // (a',a,d) -> (d,a',a)
+  {
+    PhaseScope ps(ctx, HS_PHASE_SELECT);
+    HS_CUDA(launch_gather_pt(V0, n0, V1, n1, didx, chi, dsel, ctx->pt.d(), s));
+    ctx->launches += 1;
+  }
   GemmGroup g4 = make_z2_gemm(Pp, Tcr, Y), g5 = make_z2_gemm(Yp, Am, Zm), g6 = make_z2_gemm(Zp, PT, Tn);
   flops += gemm_flops(g4) + gemm_flops(g5) + gemm_flops(g6);
-  HS_TRY(gemm(ctx, be, g4, ctx->pp.d(), env->T, B1));
-  HS_TRY(permute(ctx, Y, Yp, {1, 2, 0, 3}, B1, B2));    // (d,a',b,x) -> (a',b,d,x)
-  HS_TRY(gemm(ctx, be, g5, B2, a->data, B1));
-  HS_TRY(permute(ctx, Zm, Zp, {0, 3, 1, 2}, B1, B2));   // (a',b,u,r) -> (a',r,b,u)
-  HS_TRY(gemm(ctx, be, g6, B2, ctx->pt.d(), env->T));
+  ctx->phase_flops[HS_PHASE_GEMM] += gemm_flops(g4) + gemm_flops(g6);
+  ctx->phase_flops[tc ? HS_PHASE_GEMM_TC : HS_PHASE_GEMM] += gemm_flops(g5);
+  {
+    PhaseScope ps(ctx, HS_PHASE_PERMUTE);
+    HS_TRY(permute(ctx, PT, Pp, {2, 0, 1}, ctx->pt.d(), ctx->pp.d()));  // (a',a,d) -> (d,a',a)
+  }
+  {
+    PhaseScope ps(ctx, HS_PHASE_GEMM);
+    HS_TRY(gemm(ctx, be, g4, ctx->pp.d(), env->T, B1));
+  }
+  if (tc) {
+    HS_TRY(tc_a_gemm(ctx, env->precision, Y, Yp, {1, 2, 0, 3}, B1, Am, Zm, B2));
+    std::swap(B1, B2);  // Z now in B1
+  } else {
+    {
+      PhaseScope ps(ctx, HS_PHASE_PERMUTE);
+      HS_TRY(permute(ctx, Y, Yp, {1, 2, 0, 3}, B1, B2));    // (d,a',b,x) -> (a',b,d,x)
+    }
+    PhaseScope ps(ctx, HS_PHASE_GEMM);
+    HS_TRY(gemm(ctx, be, g5, B2, a->data, B1));
+  }
+  {
+    PhaseScope ps(ctx, HS_PHASE_PERMUTE);
+    HS_TRY(permute(ctx, Zm, Zp, {0, 3, 1, 2}, B1, B2));   // (a',b,u,r) -> (a',r,b,u)
+  }
+  {
+    PhaseScope ps(ctx, HS_PHASE_GEMM);
+    HS_TRY(gemm(ctx, be, g6, B2, ctx->pt.d(), env->T));
+  }
 
   // C <- diag(lambda)/max|lambda|, T <- T/max|T|
-  HS_CUDA(launch_diag_corner(ctx->lam.d(), cn.n[0], cn.n[1], dsel, env->C, s));
-  HS_CUDA(launch_normalize_max(env->T, z2_elems(Tn), static_cast<unsigned long long*>(ctx->scratch.p),
-                               dsel, s));
+  {
+    PhaseScope ps(ctx, HS_PHASE_SELECT);
+    HS_CUDA(launch_diag_corner(ctx->lam.d(), cn.n[0], cn.n[1], dsel, env->C, s));
+    ctx->launches += 1;
+  }
+  {
+    PhaseScope ps(ctx, HS_PHASE_NORMALIZE);
+    HS_CUDA(launch_normalize_max(env->T, z2_elems(Tn), static_cast<unsigned long long*>(ctx->scratch.p),
+                                 dsel, s));
+    ctx->launches += 2;
+  }
   HS_CUDA(cudaMemcpyAsync(&ctx->h_sel->log_norm_C, &dsel->log_norm_C, 2 * sizeof(double),
                           cudaMemcpyDeviceToHost, s));
+  HS_CUDA(cudaMemcpyAsync(ctx->h_tc_err, ctx->tc_err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
   HS_CUDA(cudaStreamSynchronize(s));
+  harvest_profile(ctx);
+  if (*ctx->h_tc_err != 0) {
+    const int code = *ctx->h_tc_err;
+    HS_CUDA(cudaMemsetAsync(ctx->tc_err.p, 0, sizeof(int), s));
+    return fail(HS_ERR_TIMEOUT, "a bounded wait in the tensor-core GEMM gave up (code %d)", code);
+  }
   env->chi_even = cn.n[0];
   env->chi_odd = cn.n[1];
   env->log_norm_C = ctx->h_sel->log_norm_C;
@@ -409,6 +607,70 @@ hs_status hs_ctmrg_move(hs_ctx ctx, const hs_z2_tensor* a, hs_env* env, int chi,
     info->gemm_flops = flops;
     info->flags = (discarded && info->gap < 1e-9) ? 1 : 0;
   }
+  return HS_OK;
+}
+
+hs_status hs_profile_enable(hs_ctx ctx, int enable) {
+  HS_TRY(check_ctx(ctx));
+  HS_CUDA(cudaStreamSynchronize(ctx->stream));
+  harvest_profile(ctx);
+  ctx->prof = enable != 0;
+  for (double& v : ctx->phase_ms) v = 0;
+  for (double& v : ctx->phase_flops) v = 0;
+  ctx->launches = 0;
+  return HS_OK;
+}
+
+hs_status hs_profile_read(hs_ctx ctx, double* phase_ms, double* phase_flops, int n_phases,
+                          long long* launches) {
+  HS_TRY(check_ctx(ctx));
+  if (n_phases < 0) return fail(HS_ERR_INVALID_ARG, "negative phase count");
+  for (int i = 0; i < n_phases; ++i) {
+    if (phase_ms) phase_ms[i] = i < HS_PHASE_COUNT ? ctx->phase_ms[i] : 0.0;
+    if (phase_flops) phase_flops[i] = i < HS_PHASE_COUNT ? ctx->phase_flops[i] : 0.0;
+  }
+  if (launches) *launches = ctx->launches;
+  return HS_OK;
+}
+
+hs_status hs_gemm(hs_ctx ctx, hs_precision precision, int M, int N, int K, const double* A, int lda,
+                  const double* B, int ldb, double* C, int ldc) {
+  HS_TRY(check_ctx(ctx));
+  if (M < 0 || N < 0 || K < 0 || lda < K || ldb < K || ldc < N || (M * N > 0 && (!A || !B || !C)))
+    return fail(HS_ERR_INVALID_ARG, "bad arguments");
+  if (M == 0 || N == 0) return HS_OK;
+  if (precision == HS_PREC_F64) {
+    GemmGroup g{};
+    g.n = 1;
+    g.p[0] = GemmProblem{M, N, K, lda, ldb, ldc, 0, 0, 0};
+    HS_CUDA(launch_gemm_f64(g, A, B, C, 1.0, ctx->stream));
+    return HS_OK;
+  }
+  if (precision != HS_PREC_TF32X3 && precision != HS_PREC_TF32 && precision != HS_PREC_BF16X3)
+    return fail(HS_ERR_INVALID_ARG, "unknown precision %d", (int)precision);
+  if (K == 0) {
+    HS_CUDA(cudaMemset2DAsync(C, sizeof(double) * ldc, 0, sizeof(double) * N, M, ctx->stream));
+    return HS_OK;
+  }
+  const int pad = tc_pad(precision), eb = tc_elem_bytes(precision);
+  const long long Kp = ((long long)K + pad - 1) / pad * pad;
+  HS_TRY(ctx->tc_x_hi.ensure((size_t)M * Kp * eb));
+  HS_TRY(ctx->tc_x_lo.ensure((size_t)M * Kp * eb));
+  HS_TRY(ctx->tc_b_hi.ensure((size_t)N * Kp * eb));
+  HS_TRY(ctx->tc_b_lo.ensure((size_t)N * Kp * eb));
+  HS_CUDA(launch_split_pad(A, M, K, lda, ctx->tc_x_hi.p, ctx->tc_x_lo.p, Kp, tc_mode(precision), ctx->stream));
+  HS_CUDA(launch_split_pad(B, N, K, ldb, ctx->tc_b_hi.p, ctx->tc_b_lo.p, Kp, tc_mode(precision), ctx->stream));
+  TcProblem t;
+  t.M = M;
+  t.N = N;
+  t.Kp = (int)Kp;
+  t.ldc = ldc;
+  t.a_hi = ctx->tc_x_hi.p;
+  t.a_lo = ctx->tc_x_lo.p;
+  t.b_hi = ctx->tc_b_hi.p;
+  t.b_lo = ctx->tc_b_lo.p;
+  t.c = C;
+  HS_CUDA(launch_gemm_tc(precision, &t, 1, static_cast<int*>(ctx->tc_err.p), ctx->stream));
   return HS_OK;
 }
 

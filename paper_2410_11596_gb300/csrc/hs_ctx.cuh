@@ -86,17 +86,54 @@ struct hs_ctx_s {
   int* h_info = nullptr;           // pinned
   // observables workspace
   hs::DBuf r[16];
+  // tensor-core operands: split double layer (cached per source/precision),
+  // split A operand of the current GEMM, split B for hs_gemm, error word
+  hs::DBuf tc_a_hi, tc_a_lo, tc_x_hi, tc_x_lo, tc_b_hi, tc_b_lo, tc_err;
+  const double* tc_a_src = nullptr;
+  int tc_a_prec = -1;
+  int* h_tc_err = nullptr;  // pinned
+  // profiling: events between phases, harvested after the move's last sync
+  bool prof = false;
+  std::vector<cudaEvent_t> events;
+  int next_event = 0;
+  struct Rec {
+    int phase, e0, e1;
+  };
+  std::vector<Rec> recs;
+  double phase_ms[HS_PHASE_COUNT] = {0, 0, 0, 0, 0, 0};
+  double phase_flops[HS_PHASE_COUNT] = {0, 0, 0, 0, 0, 0};
+  long long launches = 0;
 };
 
 namespace hs {
 
 hs_status check_ctx(hs_ctx ctx);
 Sect q_sect(int D, hs_basis b);
-Z2Mat mat(Fused r, Fused c);
+Z2Mat mat(Fused r, Fused c, int pad = 1);
 // C = A B^T on the chosen backend.
 hs_status gemm(hs_ctx ctx, hs_gemm_backend be, const GemmGroup& g, const double* A, const double* B,
                double* C);
 hs_status permute(hs_ctx ctx, const Z2Mat& in, const Z2Mat& out, std::initializer_list<int> perm,
                   const double* src, double* dst);
+
+// Tensor-core precisions: elements per 128-byte row (the K padding unit),
+// bytes per element, split mode of the permute/split kernels.
+int tc_pad(hs_precision p);
+int tc_elem_bytes(hs_precision p);
+int tc_mode(hs_precision p);
+
+// Records a CUDA event pair around a phase when profiling is on.
+class PhaseScope {
+ public:
+  PhaseScope(hs_ctx c, int phase);
+  ~PhaseScope();
+
+ private:
+  hs_ctx c_;
+  int phase_, e0_;
+};
+
+// Accumulates the recorded phases (call after the stream has synchronised).
+void harvest_profile(hs_ctx ctx);
 
 }  // namespace hs

@@ -85,17 +85,26 @@ HS_HD long long tuple_offset(const Fused& f, int t) {
 }
 
 // Block-diagonal Z2 matrix: block p = rows of parity p x cols of parity p.
+// Each block's row stride is its column count rounded up to `pad` elements
+// (pad = 1: tightly packed; the tensor-core operands use 32 so that rows are
+// whole 128-byte swizzle atoms and 16-byte aligned for TMA).
 struct Z2Mat {
   Fused r, c;
+  int pad;
 };
 
 HS_HD long long z2_rows(const Z2Mat& m, int p) { return fused_size(m.r, p); }
 HS_HD long long z2_cols(const Z2Mat& m, int p) { return fused_size(m.c, p); }
+HS_HD long long z2_ld(const Z2Mat& m, int p) {
+  const long long c = z2_cols(m, p);
+  const long long a = m.pad > 1 ? m.pad : 1;
+  return (c + a - 1) / a * a;
+}
 HS_HD long long z2_block_off(const Z2Mat& m, int p) {
-  return p == 0 ? 0 : z2_rows(m, 0) * z2_cols(m, 0);
+  return p == 0 ? 0 : z2_rows(m, 0) * z2_ld(m, 0);
 }
 HS_HD long long z2_elems(const Z2Mat& m) {
-  return z2_rows(m, 0) * z2_cols(m, 0) + z2_rows(m, 1) * z2_cols(m, 1);
+  return z2_rows(m, 0) * z2_ld(m, 0) + z2_rows(m, 1) * z2_ld(m, 1);
 }
 
 // ---- permutation of a Z2 matrix into another grouping/order of its legs ----
@@ -145,6 +154,33 @@ double gemm_flops(const GemmGroup& g);
 
 cudaError_t launch_permute_f64(const PermPlan& plan, const double* in, double* out, double scale,
                                cudaStream_t s);
+// Same permutation, writing the operand split for the tensor cores:
+// mode 1: hi = tf32(x), lo = fp32(x - hi) as float; mode 2: bf16 hi/lo pair.
+// The padded columns of `out` must have been zeroed by the caller.
+cudaError_t launch_permute_split(const PermPlan& plan, const double* in, void* hi, void* lo, int mode,
+                                 cudaStream_t s);
+
+// Split a row-major FP64 matrix [rows, cols] (row stride ld_src) into padded
+// hi/lo operands [rows, ld_dst] (zeros in columns cols..ld_dst-1); mode as above.
+cudaError_t launch_split_pad(const double* src, long long rows, int cols, long long ld_src, void* hi,
+                             void* lo, long long ld_dst, int mode, cudaStream_t s);
+
+// ---- tensor-core (tcgen05) block GEMM ------------------------------------------
+
+// One block problem: C[M, N] (FP64, row stride ldc) = A[M, Kp] B[N, Kp]^T with
+// A and B given as hi/lo splits (FP32 for TF32, BF16 for BF16), rows Kp apart.
+struct TcProblem {
+  int M, N, Kp, ldc;
+  const void* a_hi;
+  const void* a_lo;
+  const void* b_hi;
+  const void* b_lo;
+  double* c;
+};
+
+// precision: HS_PREC_TF32X3, HS_PREC_TF32 or HS_PREC_BF16X3. err receives a
+// non-zero code if a bounded wait inside the kernel gave up.
+cudaError_t launch_gemm_tc(int precision, const TcProblem* probs, int nprob, int* err, cudaStream_t s);
 cudaError_t launch_gemm_f64(const GemmGroup& g, const double* A, const double* B, double* C,
                             double alpha, cudaStream_t s);
 

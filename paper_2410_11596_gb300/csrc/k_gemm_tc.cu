@@ -1,0 +1,396 @@
+// Tensor-core block GEMM for the CTMRG contractions on sm_103a (tcgen05 + TMEM
+// + TMA). Inside one parity block the contraction is a dense GEMM
+// (arXiv 2410.11596 Sec. II.B: "product of block diagonal matrices"), so it
+// runs on the 5th-generation tensor cores:
+//
+//   C[M, N] (FP64) = A[M, K] B[N, K]^T,  A and B split as x = hi + lo
+//     TF32x3 : acc_main += A_hi B_hi ; acc_corr += A_hi B_lo + A_lo B_hi  (tf32 hi, fp32 lo)
+//     TF32   : acc_main += A_hi B_hi
+//     BF16x3 : as TF32x3 with a bf16 hi/lo split
+//   C = (double)acc_main + (double)acc_corr
+//
+// CTA tile 128 x 128, K step 128 bytes (one 128-byte swizzle atom per row).
+// Warp 0 lane 0 issues the TMA loads, warp 1 lane 0 issues tcgen05.mma, all
+// four warps drain TMEM in the epilogue (warp w owns TMEM lanes 32w..32w+31).
+// Operand tiles are loaded by TMA with 128-byte swizzle into a multi-stage
+// ring guarded by mbarriers (full: TMA bytes landed; empty: MMAs that read the
+// stage have completed, signalled by tcgen05.commit).
+//
+// Every wait is bounded. A wait that gives up sets *err and an abort flag in
+// shared memory; the other roles then stop, the kernel drains what it issued
+// (again with bounded waits), frees its TMEM and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <cstdint>
+#include <mutex>
+
+#include "hs_internal.cuh"
+
+namespace hs {
+
+namespace {
+
+constexpr int BM = 128, BN = 128, NT = 128;
+constexpr int ROW_BYTES = 128;
+constexpr int TILE_BYTES = BM * ROW_BYTES;  // BN == BM
+constexpr long long WAIT_LIMIT = 20000000;  // try_wait rounds before giving up (seconds)
+
+struct Maps {
+  CUtensorMap a[2][2];  // [problem][hi, lo]
+  CUtensorMap b[2][2];
+};
+
+struct Prob {
+  int M, N, Kp, ldc;
+  double* c;
+  int tile_start, tiles_n;
+};
+
+struct Group {
+  int n;
+  Prob p[2];
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait; on timeout records the code and raises the abort flag.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag,
+                                          int* err, int code) {
+  for (long long i = 0; i < WAIT_LIMIT; ++i) {
+    if (mbar_try(bar, parity)) return true;
+    if (*abort_flag) return false;
+  }
+  *abort_flag = 1;
+  atomicExch(err, code);
+  return false;
+}
+
+// Drain wait after an abort: bounded, never raises anything.
+__device__ __forceinline__ void mbar_drain(uint32_t bar, uint32_t parity) {
+  for (long long i = 0; i < WAIT_LIMIT; ++i)
+    if (mbar_try(bar, parity)) return;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int c0, int c1,
+                                            uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+      "[%4];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(bar)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row core
+// groups 1024 bytes apart (rows are 128 bytes), descriptor version 1.
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr & 0x3FFFF) >> 4);
+  d |= (uint64_t)1 << 16;            // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;  // stride byte offset
+  d |= (uint64_t)1 << 46;            // version
+  d |= (uint64_t)2 << 61;            // 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor of kind::tf32 / kind::f16: D = f32, A/B format
+// (2 = tf32, 1 = bf16), both K-major, N = BN, M = BM.
+__host__ __device__ constexpr uint32_t idesc(uint32_t fmt) {
+  return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+}
+
+template <int EB>
+__device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t acc) {
+  if (EB == 4) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::
+            "r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc(2)), "r"(acc));
+  } else {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::
+            "r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc(1)), "r"(acc));
+  }
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+               : "memory");
+}
+
+__device__ __forceinline__ void fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+      "%14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+        "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+        "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+        "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+template <int NPASS, int EB>
+struct Cfg {
+  static constexpr int TILES = NPASS == 1 ? 2 : 4;  // A_hi, B_hi (+ A_lo, B_lo)
+  static constexpr int STAGE_BYTES = TILES * TILE_BYTES;
+  static constexpr int STAGES = NPASS == 1 ? 6 : 3;
+  static constexpr uint32_t TMEM_COLS = NPASS == 1 ? BN : 2 * BN;
+  static constexpr int K_PER_TILE = ROW_BYTES / EB;  // elements per 128-byte row
+  static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 + 256;
+};
+
+template <int NPASS, int EB>
+__global__ void __launch_bounds__(NT, 1) gemm_tc_kernel(const __grid_constant__ Maps maps, const Group g,
+                                                        int* __restrict__ err) {
+  using K = Cfg<NPASS, EB>;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + K::STAGES * K::STAGE_BYTES);
+  uint64_t* empty = full + K::STAGES;
+  uint64_t* accum = empty + K::STAGES;
+  uint64_t* drain = accum + 1;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  int t = blockIdx.x;
+  const int pi = (g.n > 1 && t >= g.p[1].tile_start) ? 1 : 0;
+  const Prob P = g.p[pi];
+  t -= P.tile_start;
+  const int m0 = (t / P.tiles_n) * BM, n0 = (t % P.tiles_n) * BN;
+  const int ktiles = P.Kp / K::K_PER_TILE;
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(K::TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (threadIdx.x == 32) {
+    for (int s = 0; s < K::STAGES; ++s) {
+      mbar_init(smem_u32(&full[s]), 1);
+      mbar_init(smem_u32(&empty[s]), 1);
+    }
+    mbar_init(smem_u32(accum), 1);
+    mbar_init(smem_u32(drain), 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // ---- TMA producer ----
+    const CUtensorMap* mA0 = &maps.a[pi][0];
+    const CUtensorMap* mA1 = &maps.a[pi][1];
+    const CUtensorMap* mB0 = &maps.b[pi][0];
+    const CUtensorMap* mB1 = &maps.b[pi][1];
+    int issued = 0;
+    for (int kt = 0; kt < ktiles; ++kt) {
+      const int s = kt % K::STAGES, n = kt / K::STAGES;
+      if (n > 0 && !mbar_wait(smem_u32(&empty[s]), (n - 1) & 1, abort_flag, err, 1)) break;
+      if (*abort_flag) break;
+      const uint32_t fb = smem_u32(&full[s]);
+      mbar_expect_tx(fb, K::STAGE_BYTES);
+      const uint32_t st = smem_u32(smem + s * K::STAGE_BYTES);
+      const int kc = kt * K::K_PER_TILE;
+      tma_load_2d(st, mA0, kc, m0, fb);
+      tma_load_2d(st + TILE_BYTES, mB0, kc, n0, fb);
+      if (NPASS == 3) {
+        tma_load_2d(st + 2 * TILE_BYTES, mA1, kc, m0, fb);
+        tma_load_2d(st + 3 * TILE_BYTES, mB1, kc, n0, fb);
+      }
+      issued = kt + 1;
+    }
+    if (*abort_flag) {
+      // let every issued copy land before the CTA can exit
+      for (int kt = 0; kt < issued; ++kt) mbar_drain(smem_u32(&full[kt % K::STAGES]), (kt / K::STAGES) & 1);
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---- MMA issuer ----
+    bool any = false;
+    for (int kt = 0; kt < ktiles; ++kt) {
+      const int s = kt % K::STAGES, n = kt / K::STAGES;
+      if (!mbar_wait(smem_u32(&full[s]), n & 1, abort_flag, err, 2)) break;
+      fence_after();
+      const uint32_t st = smem_u32(smem + s * K::STAGE_BYTES);
+      const uint64_t a_hi = sdesc(st), b_hi = sdesc(st + TILE_BYTES);
+      const uint64_t a_lo = sdesc(st + 2 * TILE_BYTES), b_lo = sdesc(st + 3 * TILE_BYTES);
+#pragma unroll
+      for (int kk = 0; kk < ROW_BYTES / 32; ++kk) {
+        const uint64_t off = (uint64_t)((kk * 32) >> 4);
+        const uint32_t acc = (kt | kk) != 0;
+        mma<EB>(tmem, a_hi + off, b_hi + off, acc);
+        if (NPASS == 3) {
+          mma<EB>(tmem + BN, a_hi + off, b_lo + off, acc);
+          mma<EB>(tmem + BN, a_lo + off, b_hi + off, 1);
+        }
+      }
+      any = true;
+      mma_commit(smem_u32(&empty[s]));
+    }
+    if (*abort_flag) {
+      if (any) {
+        mma_commit(smem_u32(drain));
+        mbar_drain(smem_u32(drain), 0);
+      }
+    } else {
+      mma_commit(smem_u32(accum));
+    }
+  }
+
+  // ---- epilogue: TMEM -> registers -> FP64 global ----
+  bool ok = mbar_wait(smem_u32(accum), 0, abort_flag, err, 3);
+  __syncwarp();
+  ok = __all_sync(0xffffffffu, ok);
+  fence_after();
+  if (ok) {
+    const int row = m0 + warp * 32 + lane;
+    double* crow = P.c + (long long)row * P.ldc;
+    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+    for (int c = 0; c < BN; c += 32) {
+      if (n0 + c >= P.N) break;  // warp-uniform
+      uint32_t r0[32], r1[32];
+      tmem_ld32(tmem + lane_base + c, r0);
+      if (NPASS == 3) tmem_ld32(tmem + lane_base + BN + c, r1);
+      tmem_wait_ld();
+      if (row < P.M) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const int col = n0 + c + j;
+          if (col < P.N) {
+            double v = (double)__uint_as_float(r0[j]);
+            if (NPASS == 3) v += (double)__uint_as_float(r1[j]);
+            crow[col] = v;
+          }
+        }
+      }
+    }
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(K::TMEM_COLS)
+                 : "memory");
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
+// 2-D map over a row-major [rows, Kp] operand, box = 128 rows x 128 bytes.
+bool make_map(CUtensorMap* m, const void* base, int rows, int Kp, int eb) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)Kp, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)Kp * eb};
+  const cuuint32_t box[2] = {(cuuint32_t)(ROW_BYTES / eb), (cuuint32_t)BM};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult r = fn(m, eb == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                        const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+template <int NPASS, int EB>
+cudaError_t run(const TcProblem* probs, int nprob, int* err, cudaStream_t s) {
+  using K = Cfg<NPASS, EB>;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(gemm_tc_kernel<NPASS, EB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         K::SMEM);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  Maps maps;
+  memset(&maps, 0, sizeof maps);
+  Group g{};
+  int tiles = 0;
+  for (int i = 0; i < nprob; ++i) {
+    const TcProblem& p = probs[i];
+    if (p.M <= 0 || p.N <= 0) continue;
+    if (p.Kp <= 0 || p.Kp % K::K_PER_TILE != 0) return cudaErrorInvalidValue;
+    const int j = g.n;
+    if (!make_map(&maps.a[j][0], p.a_hi, p.M, p.Kp, EB) || !make_map(&maps.b[j][0], p.b_hi, p.N, p.Kp, EB))
+      return cudaErrorInvalidValue;
+    if (NPASS == 3 &&
+        (!make_map(&maps.a[j][1], p.a_lo, p.M, p.Kp, EB) || !make_map(&maps.b[j][1], p.b_lo, p.N, p.Kp, EB)))
+      return cudaErrorInvalidValue;
+    Prob& q = g.p[j];
+    q.M = p.M;
+    q.N = p.N;
+    q.Kp = p.Kp;
+    q.ldc = p.ldc;
+    q.c = p.c;
+    q.tiles_n = (p.N + BN - 1) / BN;
+    q.tile_start = tiles;
+    tiles += ((p.M + BM - 1) / BM) * q.tiles_n;
+    ++g.n;
+  }
+  if (tiles == 0) return cudaSuccess;
+  gemm_tc_kernel<NPASS, EB><<<tiles, NT, K::SMEM, s>>>(maps, g, err);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_gemm_tc(int precision, const TcProblem* probs, int nprob, int* err, cudaStream_t s) {
+  if (nprob > 2) return cudaErrorInvalidValue;
+  switch (precision) {
+    case HS_PREC_TF32X3:
+      return run<3, 4>(probs, nprob, err, s);
+    case HS_PREC_TF32:
+      return run<1, 4>(probs, nprob, err, s);
+    case HS_PREC_BF16X3:
+      return run<3, 2>(probs, nprob, err, s);
+    default:
+      return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace hs

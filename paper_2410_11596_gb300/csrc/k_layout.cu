@@ -1,5 +1,7 @@
 // Host-side planning of FSO permutations and block GEMMs (Z2 bookkeeping,
 // arXiv 2410.11596 Sec. II.B), plus the generic permute kernel.
+#include <cuda_bf16.h>
+
 #include "hs_internal.cuh"
 
 namespace hs {
@@ -12,7 +14,7 @@ void leg_strides(const Z2Mat& m, const int* par, long long* stride, long long* o
   for (int j = 0; j < m.r.k; ++j) tr = (tr << 1) | par[j];
   for (int j = 0; j < m.c.k; ++j) tc = (tc << 1) | par[m.r.k + j];
   const int P = tuple_parity(tr);
-  const long long CP = fused_size(m.c, P);
+  const long long CP = z2_ld(m, P);
   *off = z2_block_off(m, P) + tuple_offset(m.r, tr) * CP + tuple_offset(m.c, tc);
   long long s = CP;
   for (int j = m.r.k - 1; j >= 0; --j) {
@@ -77,9 +79,9 @@ GemmGroup make_z2_gemm(const Z2Mat& A, const Z2Mat& B, const Z2Mat& C) {
     q.K = (int)z2_cols(A, p);
     q.N = (int)z2_rows(B, p);
     if (q.M == 0 || q.N == 0) continue;
-    q.lda = q.K;
-    q.ldb = (int)z2_cols(B, p);
-    q.ldc = (int)z2_cols(C, p);
+    q.lda = (int)z2_ld(A, p);
+    q.ldb = (int)z2_ld(B, p);
+    q.ldc = (int)z2_ld(C, p);
     q.a_off = z2_block_off(A, p);
     q.b_off = z2_block_off(B, p);
     q.c_off = z2_block_off(C, p);
@@ -114,6 +116,87 @@ __global__ void permute_f64_kernel(PermPlan plan, const double* __restrict__ in,
                          i2 * b.out_stride[2] + i3 * b.out_stride[3];
     out[oo] = scale * in[io];
   }
+}
+
+template <int MODE>
+__global__ void permute_split_kernel(PermPlan plan, const double* __restrict__ in, void* __restrict__ hi,
+                                     void* __restrict__ lo) {
+  const Box& b = plan.box[blockIdx.y];
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < b.count; e += stride) {
+    long long r = e;
+    const int i3 = (int)(r % b.dim[3]);
+    r /= b.dim[3];
+    const int i2 = (int)(r % b.dim[2]);
+    r /= b.dim[2];
+    const int i1 = (int)(r % b.dim[1]);
+    const int i0 = (int)(r / b.dim[1]);
+    const long long io = b.in_off + i0 * b.in_stride[0] + i1 * b.in_stride[1] + i2 * b.in_stride[2] +
+                         i3 * b.in_stride[3];
+    const long long oo = b.out_off + i0 * b.out_stride[0] + i1 * b.out_stride[1] +
+                         i2 * b.out_stride[2] + i3 * b.out_stride[3];
+    const double x = in[io];
+    if (MODE == 1) {
+      float h;
+      asm("cvt.rna.tf32.f32 %0, %1;" : "=f"(h) : "f"((float)x));
+      static_cast<float*>(hi)[oo] = h;
+      static_cast<float*>(lo)[oo] = (float)(x - (double)h);
+    } else {
+      const __nv_bfloat16 h = __float2bfloat16_rn((float)x);
+      static_cast<__nv_bfloat16*>(hi)[oo] = h;
+      static_cast<__nv_bfloat16*>(lo)[oo] = __float2bfloat16_rn((float)(x - (double)__bfloat162float(h)));
+    }
+  }
+}
+
+cudaError_t launch_permute_split(const PermPlan& plan, const double* in, void* hi, void* lo, int mode,
+                                 cudaStream_t s) {
+  if (plan.nbox == 0) return cudaSuccess;
+  long long maxc = 0;
+  for (int i = 0; i < plan.nbox; ++i) maxc = plan.box[i].count > maxc ? plan.box[i].count : maxc;
+  long long gx = (maxc + 255) / 256;
+  if (gx > 2048) gx = 2048;
+  dim3 grid((unsigned)gx, (unsigned)plan.nbox);
+  if (mode == 1)
+    permute_split_kernel<1><<<grid, 256, 0, s>>>(plan, in, hi, lo);
+  else
+    permute_split_kernel<2><<<grid, 256, 0, s>>>(plan, in, hi, lo);
+  return cudaGetLastError();
+}
+
+template <int MODE>
+__global__ void split_pad_kernel(const double* __restrict__ src, long long rows, int cols, long long ld_src,
+                                 void* __restrict__ hi, void* __restrict__ lo, long long ld_dst) {
+  const long long total = rows * ld_dst;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long r = e / ld_dst;
+    const int c = (int)(e % ld_dst);
+    const double x = c < cols ? src[r * ld_src + c] : 0.0;
+    if (MODE == 1) {
+      float h;
+      asm("cvt.rna.tf32.f32 %0, %1;" : "=f"(h) : "f"((float)x));
+      static_cast<float*>(hi)[e] = h;
+      static_cast<float*>(lo)[e] = (float)(x - (double)h);
+    } else {
+      const __nv_bfloat16 h = __float2bfloat16_rn((float)x);
+      static_cast<__nv_bfloat16*>(hi)[e] = h;
+      static_cast<__nv_bfloat16*>(lo)[e] = __float2bfloat16_rn((float)(x - (double)__bfloat162float(h)));
+    }
+  }
+}
+
+cudaError_t launch_split_pad(const double* src, long long rows, int cols, long long ld_src, void* hi,
+                             void* lo, long long ld_dst, int mode, cudaStream_t s) {
+  const long long total = rows * ld_dst;
+  if (total == 0) return cudaSuccess;
+  long long gx = (total + 255) / 256;
+  if (gx > 4096) gx = 4096;
+  if (mode == 1)
+    split_pad_kernel<1><<<(unsigned)gx, 256, 0, s>>>(src, rows, cols, ld_src, hi, lo, ld_dst);
+  else
+    split_pad_kernel<2><<<(unsigned)gx, 256, 0, s>>>(src, rows, cols, ld_src, hi, lo, ld_dst);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_permute_f64(const PermPlan& plan, const double* in, double* out, double scale,

@@ -1,0 +1,85 @@
+"""Tensor-core (tcgen05) block GEMM and the mixed-precision CTMRG against FP64 references.
+
+Tolerances follow the arithmetic: with x = hi + lo, a 3-pass split drops the
+lo*lo term and rounds lo to the tensor-core type, so each product carries a
+relative error of about 2^-21 (TF32: 10+10 mantissa bits) or 2^-16 (BF16:
+7+8 bits), plus FP32 accumulation over K; one-pass TF32 carries 2^-10.
+The bound used is |C - C_ref| <= tol * sum_k |A_ik| |B_jk|.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from gpu_util import ensure_library, golden  # noqa: E402
+from paper_2410_11596_gb300 import _lib as L, inputs  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+TOL = {L.HS_PREC_F64: 1e-14, L.HS_PREC_TF32X3: 2 ** -18, L.HS_PREC_TF32: 2 ** -9, L.HS_PREC_BF16X3: 2 ** -14}
+NAMES = {L.HS_PREC_F64: "f64", L.HS_PREC_TF32X3: "tf32x3", L.HS_PREC_TF32: "tf32", L.HS_PREC_BF16X3: "bf16x3"}
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    ensure_library()
+    from paper_2410_11596_gb300.api import Context
+    c = Context(0)
+    yield c
+    c.close()
+
+
+@pytest.mark.parametrize("prec", [L.HS_PREC_TF32X3, L.HS_PREC_TF32, L.HS_PREC_BF16X3, L.HS_PREC_F64])
+@pytest.mark.parametrize("M,N,K", [(128, 128, 32), (10, 5, 3), (300, 200, 100), (129, 257, 70), (1000, 666, 666),
+                                   (2592, 144, 72)])
+def test_block_gemm_matches_fp64(ctx, prec, M, N, K):
+    rng = np.random.default_rng(M * 7 + N * 3 + K)
+    A = rng.standard_normal((M, K))
+    B = rng.standard_normal((N, K))
+    Ad, Bd = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    C = torch.full((M, N), np.nan, dtype=torch.float64, device="cuda")
+    L.hs_gemm(ctx.handle, prec, Ad, Bd, C)
+    ctx.sync()
+    ref = A @ B.T
+    bound = TOL[prec] * (np.abs(A) @ np.abs(B).T) + 1e-300
+    err = np.abs(C.cpu().numpy() - ref)
+    assert np.isfinite(err).all()
+    assert (err <= bound).all(), (NAMES[prec], float((err / bound).max()))
+
+
+def test_tensor_core_is_more_accurate_with_three_passes(ctx):
+    rng = np.random.default_rng(5)
+    A = rng.standard_normal((256, 512))
+    B = rng.standard_normal((256, 512))
+    ref = A @ B.T
+    errs = {}
+    for prec in (L.HS_PREC_TF32, L.HS_PREC_TF32X3):
+        C = torch.empty((256, 256), dtype=torch.float64, device="cuda")
+        L.hs_gemm(ctx.handle, prec, torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), C)
+        errs[prec] = np.abs(C.cpu().numpy() - ref).max()
+    assert errs[L.HS_PREC_TF32X3] < errs[L.HS_PREC_TF32] / 100
+
+
+@pytest.mark.parametrize("precision,tol_e", [("tf32x3", 1e-7), ("bf16x3", 1e-4), ("tf32", 1e-2)])
+def test_mixed_precision_ctmrg_energy(ctx, precision, tol_e):
+    """Block GEMMs of the corner and edge on tcgen05; eig, traces FP64. |dE| vs the FP64 oracle."""
+    from paper_2410_11596_gb300.api import CTMRG
+    g = golden(2)
+    c = CTMRG(ctx, inputs.workload_tensor(2), g["chi"], basis="hermitian", precision=precision)
+    c.run(50)
+    e = c.energy(inputs.heisenberg_bond())
+    dE = abs(e - g["checkpoints"]["50"]["energy"])
+    print(f"{precision}: |dE| = {dE:.3e}")
+    assert dE <= tol_e
+
+
+def test_full_size_tf32x3_energy(ctx):
+    """D=6, chi=144 (the benchmark workload), 50 moves: |dE| <= 1e-7 against the stored oracle run."""
+    from paper_2410_11596_gb300.api import CTMRG
+    g = golden(3)
+    c = CTMRG(ctx, inputs.workload_tensor(3), g["chi"], basis="hermitian", precision="tf32x3")
+    c.run(50)
+    e = c.energy(inputs.heisenberg_bond())
+    dE = abs(e - g["checkpoints"]["50"]["energy"])
+    print(f"D=6 chi=144 tf32x3: |dE| = {dE:.3e}")
+    assert dE <= 1e-7
