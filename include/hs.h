@@ -249,6 +249,28 @@ hs_status hs_profile_read(hs_ctx ctx, double* phase_ms, double* phase_flops, int
 hs_status hs_gemm(hs_ctx ctx, hs_precision precision, int M, int N, int K, const double* A, int lda,
                   const double* B, int ldb, double* C, int ldc);
 
+/* ---- block GEMM without allocation ------------------------------------ */
+
+/* The tensor-core block GEMM of hs_gemm (TF32X3, TF32 or BF16X3; C = A B^T,
+ * FP64 row-major device matrices) for callers that must not allocate device
+ * memory: applications whose own memory manager owns all device memory,
+ * latency-critical loops that cannot take the synchronisation cudaMalloc and
+ * cudaFree may imply, and plugins that may not change the device memory
+ * footprint. The paper has no counterpart; this is a service of the library.
+ * It takes no context and allocates nothing: its scratch (the split, padded
+ * operands) is a static device array of 16 MiB that every GPU which loads the
+ * library holds until exit, so 2 (M + N) Kp e <= 16 MiB is required (Kp = K
+ * rounded up to 32 for TF32 modes or 64 for BF16X3; e = 4 or 2 bytes);
+ * larger requests return HS_ERR_SHAPE. The first call on each device looks the
+ * array's device address up (cudaGetSymbolAddress) with that device current;
+ * make that first call before any stream capture. All calls share the array:
+ * calls whose GPU work overlaps race, so order them on one stream.
+ * status_out (device int, required) is set to 0 and receives a non-zero code
+ * if a bounded wait in the kernel gave up. stream is a cudaStream_t (NULL:
+ * legacy default stream). Asynchronous. */
+hs_status hs_gemm_static(hs_precision precision, int M, int N, int K, const double* A, int lda,
+                         const double* B, int ldb, double* C, int ldc, int* status_out, void* stream);
+
 /* Workspace the context will allocate for (D, chi): reported for planning. */
 hs_status hs_workspace_query(int D, int chi, hs_precision precision, size_t* bytes);
 

@@ -79,6 +79,8 @@ _PROTOS = {
     "hs_profile_read": (c_int, [c_void_p, POINTER(c_double), POINTER(c_double), c_int,
                                 POINTER(ctypes.c_longlong)]),
     "hs_gemm": (c_int, [c_void_p, c_int, c_int, c_int, c_int, c_void_p, c_int, c_void_p, c_int, c_void_p, c_int]),
+    "hs_gemm_static": (c_int, [c_int, c_int, c_int, c_int, c_void_p, c_int, c_void_p, c_int, c_void_p, c_int,
+                               c_void_p, c_void_p]),
 }
 
 PHASES = ("gemm", "permute", "eig", "select", "normalize", "gemm_tc")
@@ -210,3 +212,10 @@ def hs_gemm(ctx: int, precision: int, A, B, C) -> None:
     M, K = A.shape
     N = B.shape[0]
     check(load().hs_gemm(ctx, precision, M, N, K, ptr(A), K, ptr(B), K, ptr(C), N))
+
+
+def hs_gemm_static(precision: int, A, B, C, status, stream: int | None = None) -> None:
+    """C = A B^T through the allocation-free entry point; status is a device int32 tensor."""
+    M, K = A.shape
+    N = B.shape[0]
+    check(load().hs_gemm_static(precision, M, N, K, ptr(A), K, ptr(B), K, ptr(C), N, ptr(status), stream))
