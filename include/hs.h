@@ -77,6 +77,17 @@ typedef enum {
  * or Hermitian (eigenbasis of S, two sectors). */
 typedef enum { HS_BASIS_DENSE = 0, HS_BASIS_HERMITIAN = 1 } hs_basis;
 
+/* How the projector of each parity block is computed (Sec. II.A: truncation
+ * by an eigenvalue decomposition of the enlarged corner).
+ * HS_EIG_F64: FP64 symmetric eigen-decomposition; C_new = diag(lambda_kept).
+ * HS_EIG_F32_PROJECTED: FP32 eigen-decomposition chooses the kept states
+ *   (by their FP32 eigenvalues) and their vectors; in FP64 the vectors are
+ *   re-orthonormalised (two Loewdin steps, P <- (3/2 I - 1/2 P^T P)-updated)
+ *   and the new corner is the FP64 projection C_new = P^T C' P (symmetric,
+ *   not diagonal). Meant for the mixed-precision modes, whose C' carries FP32
+ *   rounding already. */
+typedef enum { HS_EIG_F64 = 0, HS_EIG_F32_PROJECTED = 1 } hs_eig_mode;
+
 /* Which library runs the FP64 block GEMMs (HS_PREC_F64 only). */
 typedef enum { HS_GEMM_OWN = 0, HS_GEMM_CUBLAS = 1 } hs_gemm_backend;
 
@@ -113,6 +124,7 @@ typedef struct {
   double* C;             /* device, caller-owned */
   double* T;             /* device, caller-owned */
   size_t C_bytes, T_bytes;
+  hs_eig_mode eig_mode;  /* set to HS_EIG_F64 by hs_ctmrg_init; the caller may change it between moves */
 } hs_env;
 
 /* Per-move record filled by hs_ctmrg_move (host memory). */

@@ -26,6 +26,7 @@ HS_PREC_F64, HS_PREC_TF32X3, HS_PREC_TF32, HS_PREC_BF16X3 = 0, 1, 2, 3
 HS_BASIS_DENSE, HS_BASIS_HERMITIAN = 0, 1
 HS_GEMM_OWN, HS_GEMM_CUBLAS = 0, 1
 HS_RDM_TWO_SITE, HS_RDM_ENV_ONE_SITE = 0, 1
+HS_EIG_F64, HS_EIG_F32_PROJECTED = 0, 1
 
 
 class HsError(RuntimeError):
@@ -44,7 +45,7 @@ class Env(ctypes.Structure):
                 ("q_even", c_int), ("q_odd", c_int), ("basis", c_int), ("precision", c_int),
                 ("gemm_backend", c_int), ("moves", c_int), ("log_norm_C", c_double),
                 ("log_norm_T", c_double), ("C", c_void_p), ("T", c_void_p), ("C_bytes", c_size_t),
-                ("T_bytes", c_size_t)]
+                ("T_bytes", c_size_t), ("eig_mode", c_int)]
 
 
 class MoveInfo(ctypes.Structure):

@@ -13,6 +13,7 @@ BASIS = {"dense": L.HS_BASIS_DENSE, "hermitian": L.HS_BASIS_HERMITIAN}
 PRECISION = {"f64": L.HS_PREC_F64, "tf32x3": L.HS_PREC_TF32X3, "tf32": L.HS_PREC_TF32,
              "bf16x3": L.HS_PREC_BF16X3}
 BACKEND = {"own": L.HS_GEMM_OWN, "cublas": L.HS_GEMM_CUBLAS}
+EIG = {"f64": L.HS_EIG_F64, "f32p": L.HS_EIG_F32_PROJECTED}
 
 
 class Context:
@@ -52,7 +53,7 @@ class CTMRG:
     """C4v CTMRG of one real iPEPS tensor on one GPU through the C ABI."""
 
     def __init__(self, ctx: Context, A: np.ndarray | torch.Tensor, chi: int, basis: str = "hermitian",
-                 precision: str = "f64", backend: str = "own"):
+                 precision: str = "f64", backend: str = "own", eig: str = "f64"):
         self.ctx = ctx
         dev = f"cuda:{ctx.device}"
         self.A = A if isinstance(A, torch.Tensor) else to_device(A, ctx.device)
@@ -67,6 +68,7 @@ class CTMRG:
         self.T_buf = torch.empty(tb // 8, dtype=torch.float64, device=dev)
         self.env = L.hs_ctmrg_init(ctx.handle, self.a, chi, PRECISION[precision], BACKEND[backend],
                                    self.C_buf, self.T_buf)
+        self.env.eig_mode = EIG[eig]
         self.infos: list[dict] = []
 
     def move(self) -> dict:
@@ -80,6 +82,12 @@ class CTMRG:
     @property
     def chi_now(self) -> int:
         return self.env.chi_even + self.env.chi_odd
+
+    def corner_spectrum(self) -> np.ndarray:
+        """Singular values of C divided by the largest (host-side post-processing of C)."""
+        C, _ = self.dense_env()
+        sv = np.linalg.svd(C.cpu().numpy(), compute_uv=False)
+        return sv / sv[0]
 
     def dense_env(self) -> tuple[torch.Tensor, torch.Tensor]:
         """(C[chi, chi], T[chi, D^2, chi]) in the plain combined basis."""

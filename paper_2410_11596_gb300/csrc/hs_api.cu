@@ -133,6 +133,26 @@ hs_status eig_workspace(hs_ctx ctx, int nmax) {
   return HS_OK;
 }
 
+hs_status eig32_workspace(hs_ctx ctx, int nmax) {
+  size_t dev = 0, host = 0;
+  HS_SOLVER(cusolverDnXsyevd_bufferSize(ctx->solver, ctx->params, CUSOLVER_EIG_MODE_VECTOR,
+                                        CUBLAS_FILL_MODE_LOWER, nmax, CUDA_R_32F, nullptr, nmax,
+                                        CUDA_R_32F, nullptr, CUDA_R_32F, &dev, &host));
+  HS_TRY(ctx->solver32_dev.ensure(dev + 256));
+  if (ctx->solver32_host.size() < host + 1) ctx->solver32_host.resize(host + 1);
+  return HS_OK;
+}
+
+// In-place FP32 symmetric eigen-decomposition of one n x n block.
+hs_status eig32_block(hs_ctx ctx, float* A, int n, float* w, int slot) {
+  if (n == 0) return HS_OK;
+  HS_SOLVER(cusolverDnXsyevd(ctx->solver, ctx->params, CUSOLVER_EIG_MODE_VECTOR,
+                             CUBLAS_FILL_MODE_LOWER, n, CUDA_R_32F, A, n, CUDA_R_32F, w, CUDA_R_32F,
+                             ctx->solver32_dev.p, ctx->solver32_dev.bytes, ctx->solver32_host.data(),
+                             ctx->solver32_host.size(), static_cast<int*>(ctx->info.p) + slot));
+  return HS_OK;
+}
+
 // In-place FP64 symmetric eigen-decomposition of one n x n block.
 hs_status eig_block(hs_ctx ctx, double* A, int n, double* w, int slot) {
   if (n == 0) return HS_OK;
@@ -191,6 +211,79 @@ hs_status tc_a_gemm(hs_ctx ctx, hs_precision prec, const Z2Mat& Xsrc, const Z2Ma
     HS_CUDA(launch_gemm_tc(prec, pr, n, static_cast<int*>(ctx->tc_err.p), ctx->stream));
     if (n > 0) ctx->launches += 1;
   }
+  return HS_OK;
+}
+
+// FP32-eigenvector projector (HS_EIG_F32_PROJECTED): gather the kept FP32
+// eigenvectors as PT (rows) and P (columns), make them orthonormal in FP64 by
+// two Loewdin steps PT <- (3/2 I - 1/2 PT PT^T) PT, then set the new corner to
+// the FP64 projection C = PT C' PT^T of each block and normalise it.
+hs_status project_f32(hs_ctx ctx, const float* V0f, int n0, const float* V1f, int n1, const int* didx, int chi,
+                      SelectOut* dsel, Sect c, Sect q, Sect cn, const double* C0, const double* C1, hs_env* env,
+                      double* flops) {
+  cudaStream_t s = ctx->stream;
+  const int k[2] = {cn.n[0], cn.n[1]};
+  const int n[2] = {n0, n1};
+  const double* Cp[2] = {C0, C1};
+  const long long npt = (long long)k[0] * n[0] + (long long)k[1] * n[1];
+  HS_TRY(ctx->pcol.ensure(npt * sizeof(double)));
+  HS_TRY(ctx->pt2.ensure(npt * sizeof(double)));
+  HS_TRY(ctx->wproj.ensure(npt * sizeof(double)));
+  HS_TRY(ctx->gram.ensure(((long long)k[0] * k[0] + (long long)k[1] * k[1] + 1) * sizeof(double)));
+  double* PT = ctx->pt.d();
+  double* PT2 = ctx->pt2.d();
+  double* P = ctx->pcol.d();
+  double* G = ctx->gram.d();
+  double* W = ctx->wproj.d();
+  {
+    PhaseScope ps(ctx, HS_PHASE_SELECT);
+    HS_CUDA(launch_gather_p32(V0f, n0, V1f, n1, didx, chi, dsel, PT, P, s));
+    ctx->launches += 1;
+  }
+  const long long ptoff[2] = {0, (long long)k[0] * n[0]};
+  const long long goff[2] = {0, (long long)k[0] * k[0]};
+  auto group = [&](auto fill) {
+    GemmGroup g{};
+    for (int p = 0; p < 2; ++p) {
+      if (k[p] == 0 || n[p] == 0) continue;
+      g.p[g.n++] = fill(p);
+    }
+    return g;
+  };
+  const Z2Mat PTm = mat(fused1(cn), fused2(c, q)), Pm = mat(fused2(c, q), fused1(cn));
+  PhaseScope ps(ctx, HS_PHASE_GEMM);
+  for (int step = 0; step < 2; ++step) {
+    // G = PT PT^T
+    GemmGroup gg = group([&](int p) {
+      return GemmProblem{k[p], k[p], n[p], n[p], n[p], k[p], ptoff[p], ptoff[p], goff[p]};
+    });
+    HS_CUDA(launch_gemm_f64(gg, PT, PT, G, 1.0, s));
+    HS_CUDA(launch_lowdin(G, k[0], k[1], s));
+    // PT2 = M PT, i.e. C = M (P)^T with P the column layout
+    GemmGroup gm = group([&](int p) {
+      return GemmProblem{k[p], n[p], k[p], k[p], k[p], n[p], goff[p], ptoff[p], ptoff[p]};
+    });
+    HS_CUDA(launch_gemm_f64(gm, G, P, PT2, 1.0, s));
+    *flops += gemm_flops(gg) + gemm_flops(gm);
+    ctx->phase_flops[HS_PHASE_GEMM] += gemm_flops(gg) + gemm_flops(gm);
+    HS_TRY(permute(ctx, PTm, Pm, {1, 2, 0}, PT2, P));  // columns of the updated vectors
+    HS_CUDA(cudaMemcpyAsync(PT, PT2, npt * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    ctx->launches += 3;
+  }
+  // W = PT C' (C' symmetric), C_new = W PT^T, block by block into env->C
+  GemmGroup gw = group([&](int p) {
+    return GemmProblem{k[p], n[p], n[p], n[p], n[p], n[p], ptoff[p], (long long)(Cp[p] - C0), ptoff[p]};
+  });
+  HS_CUDA(launch_gemm_f64(gw, PT, C0, W, 1.0, s));
+  GemmGroup gc = group([&](int p) {
+    return GemmProblem{k[p], k[p], n[p], n[p], n[p], k[p], ptoff[p], ptoff[p], goff[p]};
+  });
+  HS_CUDA(launch_gemm_f64(gc, W, PT, env->C, 1.0, s));
+  *flops += gemm_flops(gw) + gemm_flops(gc);
+  ctx->phase_flops[HS_PHASE_GEMM] += gemm_flops(gw) + gemm_flops(gc);
+  HS_CUDA(launch_normalize_max_to(env->C, goff[1] + (long long)k[1] * k[1],
+                                  static_cast<unsigned long long*>(ctx->scratch.p) + 2, &dsel->log_norm_C, s));
+  ctx->launches += 4;
   return HS_OK;
 }
 
@@ -260,6 +353,8 @@ hs_status hs_destroy(hs_ctx ctx) {
                   &ctx->tc_x_lo, &ctx->tc_b_hi, &ctx->tc_b_lo, &ctx->tc_err};
   for (DBuf* b : bufs) b->release();
   for (DBuf& b : ctx->r) b.release();
+  DBuf* more[] = {&ctx->c32, &ctx->w32, &ctx->pcol, &ctx->pt2, &ctx->gram, &ctx->wproj, &ctx->solver32_dev};
+  for (DBuf* b : more) b->release();
   for (cudaEvent_t e : ctx->events) cudaEventDestroy(e);
   if (ctx->h_sel) cudaFreeHost(ctx->h_sel);
   if (ctx->h_info) cudaFreeHost(ctx->h_info);
@@ -390,6 +485,7 @@ hs_status hs_ctmrg_init(hs_ctx ctx, const hs_z2_tensor* a, int chi_max, hs_preci
   env->precision = precision;
   env->gemm_backend = backend;
   env->moves = 0;
+  env->eig_mode = HS_EIG_F64;
   HS_CUDA(launch_ctmrg_init(a->data, D, herm, env->C, env->T, ctx->stream));
   // normalise like every later move
   const Z2Mat Cm = mat(fused1(qs), fused1(qs)), Tm = mat(fused2(qs, qs), fused1(qs));
@@ -496,10 +592,28 @@ hs_status hs_ctmrg_move(hs_ctx ctx, const hs_z2_tensor* a, hs_env* env, int chi,
   double* w0 = ctx->w.d();
   double* w1 = w0 + n0;
   HS_CUDA(cudaMemsetAsync(ctx->info.p, 0, 2 * sizeof(int), s));
-  {
+  const bool f32eig = env->eig_mode == HS_EIG_F32_PROJECTED;
+  if (env->eig_mode != HS_EIG_F64 && !f32eig) return fail(HS_ERR_INVALID_ARG, "unknown eig mode");
+  float* V0f = nullptr;
+  float* V1f = nullptr;
+  if (!f32eig) {
     PhaseScope ps(ctx, HS_PHASE_EIG);
     HS_TRY(eig_block(ctx, V0, n0, w0, 0));
     HS_TRY(eig_block(ctx, V1, n1, w1, 1));
+  } else {
+    const long long nn = (long long)n0 * n0 + (long long)n1 * n1;
+    HS_TRY(ctx->c32.ensure(nn * sizeof(float)));
+    HS_TRY(ctx->w32.ensure((size_t)(n0 + n1) * sizeof(float)));
+    HS_TRY(eig32_workspace(ctx, n0 > n1 ? n0 : n1));
+    V0f = static_cast<float*>(ctx->c32.p);
+    V1f = V0f + (long long)n0 * n0;
+    float* w32 = static_cast<float*>(ctx->w32.p);
+    PhaseScope ps(ctx, HS_PHASE_EIG);
+    HS_CUDA(launch_cast_f64_f32(V0, V0f, nn, s));
+    HS_TRY(eig32_block(ctx, V0f, n0, w32, 0));
+    HS_TRY(eig32_block(ctx, V1f, n1, w32 + n0, 1));
+    HS_CUDA(launch_cast_f32_f64(w32, w0, n0 + n1, s));
+    ctx->launches += 2;
   }
   SelectOut* dsel = static_cast<SelectOut*>(ctx->sel.p);
   int* didx = static_cast<int*>(ctx->idx.p);
@@ -526,10 +640,12 @@ hs_status hs_ctmrg_move(hs_ctx ctx, const hs_z2_tensor* a, hs_env* env, int chi,
   const Z2Mat Zm = mat(fused2(cn, c), fused2(q, q));
   const Z2Mat Zp = mat(fused2(cn, q), fused2(c, q));
   const Z2Mat Tn = mat(fused2(cn, q), fused1(cn));
-  {
+  if (!f32eig) {
     PhaseScope ps(ctx, HS_PHASE_SELECT);
     HS_CUDA(launch_gather_pt(V0, n0, V1, n1, didx, chi, dsel, ctx->pt.d(), s));
     ctx->launches += 1;
+  } else {
+    HS_TRY(project_f32(ctx, V0f, n0, V1f, n1, didx, chi, dsel, c, q, cn, V0, V1, env, &flops));
   }
   GemmGroup g4 = make_z2_gemm(Pp, Tcr, Y), g5 = make_z2_gemm(Yp, Am, Zm), g6 = make_z2_gemm(Zp, PT, Tn);
   flops += gemm_flops(g4) + gemm_flops(g5) + gemm_flops(g6);
@@ -564,7 +680,7 @@ hs_status hs_ctmrg_move(hs_ctx ctx, const hs_z2_tensor* a, hs_env* env, int chi,
   }
 
   // C <- diag(lambda)/max|lambda|, T <- T/max|T|
-  {
+  if (!f32eig) {
     PhaseScope ps(ctx, HS_PHASE_SELECT);
     HS_CUDA(launch_diag_corner(ctx->lam.d(), cn.n[0], cn.n[1], dsel, env->C, s));
     ctx->launches += 1;

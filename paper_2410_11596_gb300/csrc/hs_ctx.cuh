@@ -92,6 +92,10 @@ struct hs_ctx_s {
   const double* tc_a_src = nullptr;
   int tc_a_prec = -1;
   int* h_tc_err = nullptr;  // pinned
+  // FP32-eigenvector mode: FP32 copy of C', FP32 eigenvalues, P (columns),
+  // updated PT, Gram/Loewdin matrices, W = PT C'
+  hs::DBuf c32, w32, pcol, pt2, gram, wproj, solver32_dev;
+  std::vector<char> solver32_host;
   // profiling: events between phases, harvested after the move's last sync
   bool prof = false;
   std::vector<cudaEvent_t> events;

@@ -222,6 +222,17 @@ cudaError_t launch_diag_corner(const double* lam, int c0, int c1, SelectOut* sel
 cudaError_t launch_normalize_max(double* T, long long n, unsigned long long* scratch,
                                  SelectOut* sel, cudaStream_t s);
 
+// FP32-eigenvector mode: casts, gather of the kept vectors into PT (rows) and
+// P (columns, FP64), the Loewdin update M = 1.5 I - 0.5 G of each block of G,
+// and a max-abs normalisation that writes its log to *log_out.
+cudaError_t launch_cast_f64_f32(const double* src, float* dst, long long n, cudaStream_t s);
+cudaError_t launch_cast_f32_f64(const float* src, double* dst, long long n, cudaStream_t s);
+cudaError_t launch_gather_p32(const float* V0, int n0, const float* V1, int n1, const int* idx, int chi,
+                              const SelectOut* sel, double* PT, double* P, cudaStream_t s);
+cudaError_t launch_lowdin(double* G, int k0, int k1, cudaStream_t s);
+cudaError_t launch_normalize_max_to(double* x, long long n, unsigned long long* scratch, double* log_out,
+                                    cudaStream_t s);
+
 // Dense views of an FSO environment (rotated back to the plain combined basis).
 cudaError_t launch_env_to_dense(const double* C, const double* T, int D, int c0, int c1,
                                 bool hermitian, double* Cd, double* Td, cudaStream_t s);

@@ -194,6 +194,61 @@ __global__ void scale_kernel(double* __restrict__ x, long long n, const unsigned
   if (blockIdx.x == 0 && threadIdx.x == 0) sel->log_norm_T = log(mx);
 }
 
+__global__ void cast_f64_f32_kernel(const double* __restrict__ a, float* __restrict__ b, long long n) {
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+    b[e] = (float)a[e];
+}
+
+__global__ void cast_f32_f64_kernel(const float* __restrict__ a, double* __restrict__ b, long long n) {
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+    b[e] = (double)a[e];
+}
+
+// Row j of block b of PT, and column j of block b of P (n_b x c_b row-major).
+__global__ void gather_p32_kernel(const float* __restrict__ V0, int n0, const float* __restrict__ V1, int n1,
+                                  const int* __restrict__ idx, int chi, const SelectOut* __restrict__ sel,
+                                  double* __restrict__ PT, double* __restrict__ P) {
+  const int b = blockIdx.y, j = blockIdx.x;
+  const int cb = sel->chi_new[b];
+  if (j >= cb) return;
+  const int n = b ? n1 : n0;
+  const float* src = (b ? V1 : V0) + (long long)idx[b * chi + j] * n;
+  const long long off = b ? (long long)sel->chi_new[0] * n0 : 0;
+  double* prow = PT + off + (long long)j * n;
+  double* pcol = P + off + j;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double v = (double)src[i];
+    prow[i] = v;
+    pcol[(long long)i * cb] = v;
+  }
+}
+
+__global__ void lowdin_kernel(double* __restrict__ G, int k0, int k1) {
+  const long long total = (long long)k0 * k0 + (long long)k1 * k1;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    long long r, c;
+    if (e < (long long)k0 * k0) {
+      r = e / k0;
+      c = e % k0;
+    } else {
+      const long long f = e - (long long)k0 * k0;
+      r = f / k1;
+      c = f % k1;
+    }
+    G[e] = (r == c ? 1.5 : 0.0) - 0.5 * G[e];
+  }
+}
+
+__global__ void scale_to_kernel(double* __restrict__ x, long long n, const unsigned long long* m, double* log_out) {
+  const double mx = __longlong_as_double((long long)*m);
+  const double inv = 1.0 / mx;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x)
+    x[e] *= inv;
+  if (blockIdx.x == 0 && threadIdx.x == 0) *log_out = log(mx);
+}
+
 __device__ __forceinline__ int pair_index(int k, int l, int D) {
   return k * (2 * D - k - 1) / 2 + (l - k - 1);
 }
@@ -288,6 +343,38 @@ cudaError_t launch_normalize_max(double* T, long long n, unsigned long long* scr
   if (e != cudaSuccess) return e;
   absmax_kernel<<<grid_for(n), 256, 0, s>>>(T, n, scratch);
   scale_kernel<<<grid_for(n), 256, 0, s>>>(T, n, scratch, sel);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cast_f64_f32(const double* src, float* dst, long long n, cudaStream_t s) {
+  cast_f64_f32_kernel<<<grid_for(n), 256, 0, s>>>(src, dst, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cast_f32_f64(const float* src, double* dst, long long n, cudaStream_t s) {
+  cast_f32_f64_kernel<<<grid_for(n), 256, 0, s>>>(src, dst, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather_p32(const float* V0, int n0, const float* V1, int n1, const int* idx, int chi,
+                              const SelectOut* sel, double* PT, double* P, cudaStream_t s) {
+  dim3 grid((unsigned)chi, 2);
+  gather_p32_kernel<<<grid, 256, 0, s>>>(V0, n0, V1, n1, idx, chi, sel, PT, P);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lowdin(double* G, int k0, int k1, cudaStream_t s) {
+  const long long n = (long long)k0 * k0 + (long long)k1 * k1;
+  lowdin_kernel<<<grid_for(n), 256, 0, s>>>(G, k0, k1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_normalize_max_to(double* x, long long n, unsigned long long* scratch, double* log_out,
+                                    cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(scratch, 0, sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return e;
+  absmax_kernel<<<grid_for(n), 256, 0, s>>>(x, n, scratch);
+  scale_to_kernel<<<grid_for(n), 256, 0, s>>>(x, n, scratch, log_out);
   return cudaGetLastError();
 }
 

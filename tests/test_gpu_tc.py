@@ -83,3 +83,20 @@ def test_full_size_tf32x3_energy(ctx):
     dE = abs(e - g["checkpoints"]["50"]["energy"])
     print(f"D=6 chi=144 tf32x3: |dE| = {dE:.3e}")
     assert dE <= 1e-7
+
+
+@pytest.mark.parametrize("k,precision,eig,tol_e", [(2, "f64", "f32p", 1e-9), (2, "tf32x3", "f32p", 1e-7),
+                                                   (3, "tf32x3", "f32p", 1e-7)])
+def test_fp32_projected_eig(ctx, k, precision, eig, tol_e):
+    """FP32 eigenvectors re-orthonormalised and projected in FP64: |dE| vs the FP64 oracle."""
+    from paper_2410_11596_gb300.api import CTMRG
+    g = golden(k)
+    c = CTMRG(ctx, inputs.workload_tensor(k), g["chi"], basis="hermitian", precision=precision, eig=eig)
+    c.run(50)
+    e = c.energy(inputs.heisenberg_bond())
+    dE = abs(e - g["checkpoints"]["50"]["energy"])
+    spec = c.corner_spectrum()
+    ds = np.abs(spec - np.array(g["checkpoints"]["50"]["corner_spectrum"])).max()
+    print(f"w{k} {precision}+{eig}: |dE| = {dE:.3e}, max |d spectrum| = {ds:.3e}")
+    assert dE <= tol_e
+    assert ds <= 1e-5
