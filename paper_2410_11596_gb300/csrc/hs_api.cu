@@ -123,43 +123,75 @@ size_t a_elems(int D, hs_basis b) {
   return (size_t)z2_elems(mat(fused2(q, q), fused2(q, q)));
 }
 
-hs_status eig_workspace(hs_ctx ctx, int nmax) {
+// One cuSOLVER handle with its stream-bound workspaces.
+struct Solver {
+  cusolverDnHandle_t h;
+  cusolverDnParams_t prm;
+  DBuf* dev;
+  std::vector<char>* host;
+};
+
+Solver solver_of(hs_ctx ctx, int which, bool f32) {
+  if (which == 0) return {ctx->solver, ctx->params, f32 ? &ctx->solver32_dev : &ctx->solver_dev,
+                          f32 ? &ctx->solver32_host : &ctx->solver_host};
+  return {ctx->solver2, ctx->params2, f32 ? &ctx->solver2_32_dev : &ctx->solver2_dev,
+          f32 ? &ctx->solver2_32_host : &ctx->solver2_host};
+}
+
+hs_status eig_ws(const Solver& sv, int nmax, bool f32) {
   size_t dev = 0, host = 0;
-  HS_SOLVER(cusolverDnXsyevd_bufferSize(ctx->solver, ctx->params, CUSOLVER_EIG_MODE_VECTOR,
-                                        CUBLAS_FILL_MODE_LOWER, nmax, CUDA_R_64F, nullptr, nmax,
-                                        CUDA_R_64F, nullptr, CUDA_R_64F, &dev, &host));
-  HS_TRY(ctx->solver_dev.ensure(dev + 256));
-  if (ctx->solver_host.size() < host + 1) ctx->solver_host.resize(host + 1);
+  const cudaDataType t = f32 ? CUDA_R_32F : CUDA_R_64F;
+  HS_SOLVER(cusolverDnXsyevd_bufferSize(sv.h, sv.prm, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, nmax, t,
+                                        nullptr, nmax, t, nullptr, t, &dev, &host));
+  HS_TRY(sv.dev->ensure(dev + 256));
+  if (sv.host->size() < host + 1) sv.host->resize(host + 1);
   return HS_OK;
+}
+
+hs_status eig_workspace(hs_ctx ctx, int nmax) {
+  HS_TRY(eig_ws(solver_of(ctx, 0, false), nmax, false));
+  return eig_ws(solver_of(ctx, 1, false), nmax, false);
 }
 
 hs_status eig32_workspace(hs_ctx ctx, int nmax) {
-  size_t dev = 0, host = 0;
-  HS_SOLVER(cusolverDnXsyevd_bufferSize(ctx->solver, ctx->params, CUSOLVER_EIG_MODE_VECTOR,
-                                        CUBLAS_FILL_MODE_LOWER, nmax, CUDA_R_32F, nullptr, nmax,
-                                        CUDA_R_32F, nullptr, CUDA_R_32F, &dev, &host));
-  HS_TRY(ctx->solver32_dev.ensure(dev + 256));
-  if (ctx->solver32_host.size() < host + 1) ctx->solver32_host.resize(host + 1);
+  HS_TRY(eig_ws(solver_of(ctx, 0, true), nmax, true));
+  return eig_ws(solver_of(ctx, 1, true), nmax, true);
+}
+
+// In-place symmetric eigen-decomposition (vectors) of one n x n block on
+// solver `which`; FP32 when f32, else FP64.
+hs_status eig_any(hs_ctx ctx, int which, bool f32, void* A, int n, void* w, int slot) {
+  if (n == 0) return HS_OK;
+  const Solver sv = solver_of(ctx, which, f32);
+  const cudaDataType t = f32 ? CUDA_R_32F : CUDA_R_64F;
+  HS_SOLVER(cusolverDnXsyevd(sv.h, sv.prm, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, n, t, A, n, t, w, t,
+                             sv.dev->p, sv.dev->bytes, sv.host->data(), sv.host->size(),
+                             static_cast<int*>(ctx->info.p) + slot));
   return HS_OK;
 }
 
-// In-place FP32 symmetric eigen-decomposition of one n x n block.
-hs_status eig32_block(hs_ctx ctx, float* A, int n, float* w, int slot) {
-  if (n == 0) return HS_OK;
-  HS_SOLVER(cusolverDnXsyevd(ctx->solver, ctx->params, CUSOLVER_EIG_MODE_VECTOR,
-                             CUBLAS_FILL_MODE_LOWER, n, CUDA_R_32F, A, n, CUDA_R_32F, w, CUDA_R_32F,
-                             ctx->solver32_dev.p, ctx->solver32_dev.bytes, ctx->solver32_host.data(),
-                             ctx->solver32_host.size(), static_cast<int*>(ctx->info.p) + slot));
-  return HS_OK;
-}
-
-// In-place FP64 symmetric eigen-decomposition of one n x n block.
-hs_status eig_block(hs_ctx ctx, double* A, int n, double* w, int slot) {
-  if (n == 0) return HS_OK;
-  HS_SOLVER(cusolverDnXsyevd(ctx->solver, ctx->params, CUSOLVER_EIG_MODE_VECTOR,
-                             CUBLAS_FILL_MODE_LOWER, n, CUDA_R_64F, A, n, CUDA_R_64F, w, CUDA_R_64F,
-                             ctx->solver_dev.p, ctx->solver_dev.bytes, ctx->solver_host.data(),
-                             ctx->solver_host.size(), static_cast<int*>(ctx->info.p) + slot));
+// Both parity blocks: block 0 on the context stream, block 1 on the second
+// stream from a helper thread (cuSOLVER's syevd blocks its calling thread).
+hs_status eig_pair(hs_ctx ctx, bool f32, void* A0, int n0, void* w0, void* A1, int n1, void* w1) {
+  if (n0 == 0 || n1 == 0) {
+    HS_TRY(eig_any(ctx, 0, f32, A0, n0, w0, 0));
+    return eig_any(ctx, 0, f32, A1, n1, w1, 1);
+  }
+  HS_CUDA(cudaEventRecord(ctx->ev_fork, ctx->stream));
+  HS_CUDA(cudaStreamWaitEvent(ctx->stream2, ctx->ev_fork, 0));
+  hs_status st1 = HS_OK;
+  std::string err1;
+  std::thread th([&] {
+    cudaSetDevice(ctx->device);
+    st1 = eig_any(ctx, 1, f32, A1, n1, w1, 1);
+    if (st1 != HS_OK) err1 = last_error();
+  });
+  const hs_status st0 = eig_any(ctx, 0, f32, A0, n0, w0, 0);
+  th.join();
+  HS_CUDA(cudaEventRecord(ctx->ev_join, ctx->stream2));
+  HS_CUDA(cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0));
+  if (st0 != HS_OK) return st0;
+  if (st1 != HS_OK) return fail(st1, "%s", err1.c_str());
   return HS_OK;
 }
 
@@ -316,6 +348,16 @@ hs_status hs_create(hs_ctx* out, int device, void* stream) {
     hs_destroy(c);
     return fail(HS_ERR_SOLVER, "cuSOLVER initialisation failed");
   }
+  if (cudaStreamCreateWithFlags(&c->stream2, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+      cusolverDnCreate(&c->solver2) != CUSOLVER_STATUS_SUCCESS ||
+      cusolverDnSetStream(c->solver2, c->stream2) != CUSOLVER_STATUS_SUCCESS ||
+      cusolverDnCreateParams(&c->params2) != CUSOLVER_STATUS_SUCCESS) {
+    cudaGetLastError();
+    hs_destroy(c);
+    return fail(HS_ERR_SOLVER, "second solver initialisation failed");
+  }
   if (cublasCreate(&c->blas) != CUBLAS_STATUS_SUCCESS ||
       cublasSetStream(c->blas, c->stream) != CUBLAS_STATUS_SUCCESS ||
       cublasSetMathMode(c->blas, CUBLAS_DEFAULT_MATH) != CUBLAS_STATUS_SUCCESS) {
@@ -359,6 +401,14 @@ hs_status hs_destroy(hs_ctx ctx) {
   if (ctx->h_sel) cudaFreeHost(ctx->h_sel);
   if (ctx->h_info) cudaFreeHost(ctx->h_info);
   if (ctx->h_tc_err) cudaFreeHost(ctx->h_tc_err);
+  if (ctx->stream2) cudaStreamSynchronize(ctx->stream2);
+  DBuf* s2b[] = {&ctx->solver2_dev, &ctx->solver2_32_dev};
+  for (DBuf* b : s2b) b->release();
+  if (ctx->params2) cusolverDnDestroyParams(ctx->params2);
+  if (ctx->solver2) cusolverDnDestroy(ctx->solver2);
+  if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+  if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
+  if (ctx->stream2) cudaStreamDestroy(ctx->stream2);
   if (ctx->params) cusolverDnDestroyParams(ctx->params);
   if (ctx->solver) cusolverDnDestroy(ctx->solver);
   if (ctx->blas) cublasDestroy(ctx->blas);
@@ -598,8 +648,7 @@ hs_status hs_ctmrg_move(hs_ctx ctx, const hs_z2_tensor* a, hs_env* env, int chi,
   float* V1f = nullptr;
   if (!f32eig) {
     PhaseScope ps(ctx, HS_PHASE_EIG);
-    HS_TRY(eig_block(ctx, V0, n0, w0, 0));
-    HS_TRY(eig_block(ctx, V1, n1, w1, 1));
+    HS_TRY(eig_pair(ctx, false, V0, n0, w0, V1, n1, w1));
   } else {
     const long long nn = (long long)n0 * n0 + (long long)n1 * n1;
     HS_TRY(ctx->c32.ensure(nn * sizeof(float)));
@@ -610,8 +659,7 @@ hs_status hs_ctmrg_move(hs_ctx ctx, const hs_z2_tensor* a, hs_env* env, int chi,
     float* w32 = static_cast<float*>(ctx->w32.p);
     PhaseScope ps(ctx, HS_PHASE_EIG);
     HS_CUDA(launch_cast_f64_f32(V0, V0f, nn, s));
-    HS_TRY(eig32_block(ctx, V0f, n0, w32, 0));
-    HS_TRY(eig32_block(ctx, V1f, n1, w32 + n0, 1));
+    HS_TRY(eig_pair(ctx, true, V0f, n0, w32, V1f, n1, w32 + n0));
     HS_CUDA(launch_cast_f32_f64(w32, w0, n0 + n1, s));
     ctx->launches += 2;
   }

@@ -9,6 +9,7 @@
 #include <cstdio>
 #include <cstring>
 #include <initializer_list>
+#include <thread>
 #include <string>
 #include <vector>
 
@@ -96,6 +97,14 @@ struct hs_ctx_s {
   // updated PT, Gram/Loewdin matrices, W = PT C'
   hs::DBuf c32, w32, pcol, pt2, gram, wproj, solver32_dev;
   std::vector<char> solver32_host;
+  // second solver: the odd block's eigen-decomposition runs on its own
+  // stream and handle, driven from a helper thread, beside the even block's
+  cudaStream_t stream2 = nullptr;
+  cusolverDnHandle_t solver2 = nullptr;
+  cusolverDnParams_t params2 = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  hs::DBuf solver2_dev, solver2_32_dev;
+  std::vector<char> solver2_host, solver2_32_host;
   // profiling: events between phases, harvested after the move's last sync
   bool prof = false;
   std::vector<cudaEvent_t> events;
