@@ -103,6 +103,9 @@ typedef struct {
   hs_dtype dtype;        /* HS_F64 only in this version */
   double* data;          /* device, caller-owned */
   size_t capacity_bytes; /* size of data */
+  /* HOTRG tensors: sectors of the vertical legs (u, d) and of the horizontal
+   * legs (l, r). The double-layer calls set both to (n_even, n_odd). */
+  int v_even, v_odd, h_even, h_odd;
 } hs_z2_tensor;
 
 /* The C4v environment (Sec. II.A, Fig. 1(d)): one corner C[chi, chi] and one
@@ -141,6 +144,15 @@ typedef struct {
 } hs_move_info;
 
 typedef enum { HS_RDM_TWO_SITE = 0, HS_RDM_ENV_ONE_SITE = 1 } hs_rdm_kind;
+
+/* Per-step record of hs_hotrg_step (host memory). */
+typedef struct {
+  int h_even, h_odd;     /* sectors kept on the truncated legs */
+  int side;              /* 0: left Gram matrix supplied the isometry, 1: right */
+  double discarded_left, discarded_right; /* discarded eigenvalue weight of each Gram matrix */
+  double log_norm;       /* log of the max-abs normalisation of the new tensor */
+  double trace;          /* sum_{u,l} T[u,l,u,l] of the new (normalised) tensor */
+} hs_hotrg_info;
 
 /* ---- context ---------------------------------------------------------- */
 
@@ -209,6 +221,26 @@ hs_status hs_ctmrg_move(hs_ctx ctx, const hs_z2_tensor* a, hs_env* env, int chi,
  * ordered as stored (even sector first) and the double-layer leg rotated back
  * to the plain combined basis. Asynchronous. */
 hs_status hs_env_to_dense(hs_ctx ctx, const hs_env* env, double* C_dense, double* T_dense);
+
+/* ---- HOTRG (Sec. II.A, Ref. xie12) ------------------------------------ */
+
+/* Bytes of a HOTRG tensor buffer for bond dimension D and chi: max(D^2, chi)^4 doubles. */
+size_t hs_hotrg_tensor_bytes(int D, int chi);
+
+/* Start a HOTRG run: copy the double layer a (FSO) into t (caller-owned,
+ * t->data with hs_hotrg_tensor_bytes) and divide it by its largest modulus;
+ * *log_norm (host) receives the log of that factor. Synchronises. */
+hs_status hs_hotrg_init(hs_ctx ctx, const hs_z2_tensor* a, hs_z2_tensor* t, double* log_norm);
+
+/* One HOTRG coarse-graining step on t (in place). direction 0 stacks two
+ * tensors vertically and truncates the fused horizontal legs to chi;
+ * direction 1 does the same on the tensor turned by 90 degrees (horizontal
+ * stacking). The isometry is the top-chi eigenvector set of the left or the
+ * right Gram matrix of the fused leg, whichever discards less weight (ties:
+ * left); one FP64 eigen-decomposition per parity block, states kept across
+ * both blocks by eigenvalue. The new tensor is divided by its largest
+ * modulus. info (host, may be NULL) receives the step record. Synchronises. */
+hs_status hs_hotrg_step(hs_ctx ctx, hs_z2_tensor* t, int chi, int direction, hs_hotrg_info* info);
 
 /* ---- observables (Sec. III.A) ----------------------------------------- */
 

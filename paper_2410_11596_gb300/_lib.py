@@ -37,7 +37,16 @@ class HsError(RuntimeError):
 
 class Z2Tensor(ctypes.Structure):
     _fields_ = [("D", c_int), ("n_even", c_int), ("n_odd", c_int), ("basis", c_int), ("dtype", c_int),
-                ("data", c_void_p), ("capacity_bytes", c_size_t)]
+                ("data", c_void_p), ("capacity_bytes", c_size_t), ("v_even", c_int), ("v_odd", c_int),
+                ("h_even", c_int), ("h_odd", c_int)]
+
+
+class HotrgInfo(ctypes.Structure):
+    _fields_ = [("h_even", c_int), ("h_odd", c_int), ("side", c_int), ("discarded_left", c_double),
+                ("discarded_right", c_double), ("log_norm", c_double), ("trace", c_double)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class Env(ctypes.Structure):
@@ -80,6 +89,9 @@ _PROTOS = {
     "hs_profile_read": (c_int, [c_void_p, POINTER(c_double), POINTER(c_double), c_int,
                                 POINTER(ctypes.c_longlong)]),
     "hs_gemm": (c_int, [c_void_p, c_int, c_int, c_int, c_int, c_void_p, c_int, c_void_p, c_int, c_void_p, c_int]),
+    "hs_hotrg_tensor_bytes": (c_size_t, [c_int, c_int]),
+    "hs_hotrg_init": (c_int, [c_void_p, POINTER(Z2Tensor), POINTER(Z2Tensor), POINTER(c_double)]),
+    "hs_hotrg_step": (c_int, [c_void_p, POINTER(Z2Tensor), c_int, c_int, POINTER(HotrgInfo)]),
     "hs_gemm_static": (c_int, [c_int, c_int, c_int, c_int, c_void_p, c_int, c_void_p, c_int, c_void_p, c_int,
                                c_void_p, c_void_p]),
 }
@@ -220,3 +232,20 @@ def hs_gemm_static(precision: int, A, B, C, status, stream: int | None = None) -
     M, K = A.shape
     N = B.shape[0]
     check(load().hs_gemm_static(precision, M, N, K, ptr(A), K, ptr(B), K, ptr(C), N, ptr(status), stream))
+
+
+def hs_hotrg_tensor_bytes(D: int, chi: int) -> int:
+    return load().hs_hotrg_tensor_bytes(D, chi)
+
+
+def hs_hotrg_init(ctx: int, a: Z2Tensor, t_buf) -> tuple[Z2Tensor, float]:
+    t = Z2Tensor(data=ptr(t_buf), capacity_bytes=t_buf.numel() * t_buf.element_size())
+    ln = c_double()
+    check(load().hs_hotrg_init(ctx, ctypes.byref(a), ctypes.byref(t), ctypes.byref(ln)))
+    return t, ln.value
+
+
+def hs_hotrg_step(ctx: int, t: Z2Tensor, chi: int, direction: int) -> dict:
+    info = HotrgInfo()
+    check(load().hs_hotrg_step(ctx, ctypes.byref(t), chi, direction, ctypes.byref(info)))
+    return info.as_dict()

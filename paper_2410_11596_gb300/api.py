@@ -120,3 +120,38 @@ class CTMRG:
         L.hs_rdm(self.ctx.handle, self.env, self.A, self.d, self.D, L.HS_F64, L.HS_RDM_ENV_ONE_SITE,
                  None, eps, None)
         return eps
+
+
+class HOTRG:
+    """HOTRG of one real iPEPS double layer on one GPU through the C ABI."""
+
+    def __init__(self, ctx: Context, A: np.ndarray | torch.Tensor, chi: int, basis: str = "hermitian"):
+        self.ctx = ctx
+        dev = f"cuda:{ctx.device}"
+        self.A = A if isinstance(A, torch.Tensor) else to_device(A, ctx.device)
+        self.d, self.D = int(self.A.shape[0]), int(self.A.shape[1])
+        self.chi = chi
+        nbytes = L.hs_z2_tensor_bytes(self.D, BASIS[basis])
+        self.a_buf = torch.empty(nbytes // 8, dtype=torch.float64, device=dev)
+        self.a = L.hs_double_layer_hermitian(ctx.handle, self.A, self.d, self.D, L.HS_F64, BASIS[basis],
+                                             self.a_buf)
+        self.t_buf = torch.empty(L.hs_hotrg_tensor_bytes(self.D, chi) // 8, dtype=torch.float64, device=dev)
+        self.t, ln0 = L.hs_hotrg_init(ctx.handle, self.a, self.t_buf)
+        self.log_norms = [ln0]
+        self.infos: list[dict] = []
+
+    def step(self) -> dict:
+        direction = len(self.infos) % 2          # vertical, horizontal, vertical, ...
+        info = L.hs_hotrg_step(self.ctx.handle, self.t, self.chi, direction)
+        self.infos.append(info)
+        self.log_norms.append(info["log_norm"])
+        return info
+
+    def run(self, steps: int) -> list[dict]:
+        return [self.step() for _ in range(steps)]
+
+    def log_z_per_site(self) -> float:
+        """ln Z / N = ln c_0 + sum_k ln(c_k) / 2^k + ln Tr(T_n) / 2^n (scalars returned by the library)."""
+        n = len(self.infos)
+        val = self.log_norms[0] + sum(self.log_norms[k] / 2.0 ** k for k in range(1, n + 1))
+        return float(val + np.log(self.infos[-1]["trace"]) / 2.0 ** n)

@@ -67,7 +67,7 @@ hs_status gemm(hs_ctx ctx, hs_gemm_backend be, const GemmGroup& g, const double*
 
 hs_status permute(hs_ctx ctx, const Z2Mat& in, const Z2Mat& out, std::initializer_list<int> perm,
                   const double* src, double* dst) {
-  int p[4] = {0, 0, 0, 0};
+  int p[kMaxLegs] = {0};
   int i = 0;
   for (int v : perm) p[i++] = v;
   const PermPlan plan = make_perm_plan(in, out, p);
@@ -148,7 +148,7 @@ hs_status eig_ws(const Solver& sv, int nmax, bool f32) {
   return HS_OK;
 }
 
-hs_status eig_workspace(hs_ctx ctx, int nmax) {
+hs_status eig_workspace_impl(hs_ctx ctx, int nmax) {
   HS_TRY(eig_ws(solver_of(ctx, 0, false), nmax, false));
   return eig_ws(solver_of(ctx, 1, false), nmax, false);
 }
@@ -172,7 +172,7 @@ hs_status eig_any(hs_ctx ctx, int which, bool f32, void* A, int n, void* w, int 
 
 // Both parity blocks: block 0 on the context stream, block 1 on the second
 // stream from a helper thread (cuSOLVER's syevd blocks its calling thread).
-hs_status eig_pair(hs_ctx ctx, bool f32, void* A0, int n0, void* w0, void* A1, int n1, void* w1) {
+hs_status eig_pair_impl(hs_ctx ctx, bool f32, void* A0, int n0, void* w0, void* A1, int n1, void* w1) {
   if (n0 == 0 || n1 == 0) {
     HS_TRY(eig_any(ctx, 0, f32, A0, n0, w0, 0));
     return eig_any(ctx, 0, f32, A1, n1, w1, 1);
@@ -197,6 +197,11 @@ hs_status eig_pair(hs_ctx ctx, bool f32, void* A0, int n0, void* w0, void* A1, i
 
 }  // namespace
 
+hs_status eig_pair(hs_ctx ctx, bool f32, void* A0, int n0, void* w0, void* A1, int n1, void* w1) {
+  return eig_pair_impl(ctx, f32, A0, n0, w0, A1, n1, w1);
+}
+hs_status eig_workspace(hs_ctx ctx, int nmax) { return eig_workspace_impl(ctx, nmax); }
+
 // C[R|N] = X[R|K] a[N|K]^T on the tensor cores. X is produced here from `src`
 // (layout Xsrc) by the permutation `perm`, written straight into the split,
 // K-padded operand buffers; a is the split copy made by hs_ctmrg_init.
@@ -209,7 +214,7 @@ hs_status tc_a_gemm(hs_ctx ctx, hs_precision prec, const Z2Mat& Xsrc, const Z2Ma
   if (nb > ctx->tc_x_hi.bytes) return fail(HS_ERR_WORKSPACE, "tensor-core operand buffer too small");
   {
     PhaseScope ps(ctx, HS_PHASE_PERMUTE);
-    int pm[4] = {0, 0, 0, 0}, i = 0;
+    int pm[kMaxLegs] = {0}, i = 0;
     for (int v : perm) pm[i++] = v;
     HS_CUDA(cudaMemsetAsync(ctx->tc_x_hi.p, 0, nb, ctx->stream));
     HS_CUDA(cudaMemsetAsync(ctx->tc_x_lo.p, 0, nb, ctx->stream));
@@ -395,6 +400,7 @@ hs_status hs_destroy(hs_ctx ctx) {
                   &ctx->tc_x_lo, &ctx->tc_b_hi, &ctx->tc_b_lo, &ctx->tc_err};
   for (DBuf* b : bufs) b->release();
   for (DBuf& b : ctx->r) b.release();
+  for (DBuf& b : ctx->hb) b.release();
   DBuf* more[] = {&ctx->c32, &ctx->w32, &ctx->pcol, &ctx->pt2, &ctx->gram, &ctx->wproj, &ctx->solver32_dev};
   for (DBuf* b : more) b->release();
   for (cudaEvent_t e : ctx->events) cudaEventDestroy(e);
@@ -465,6 +471,8 @@ hs_status hs_to_hermitian_basis(hs_ctx ctx, const double* a_dense, int D, hs_dty
   out->D = D;
   out->n_even = q.n[0];
   out->n_odd = q.n[1];
+  out->v_even = out->h_even = q.n[0];
+  out->v_odd = out->h_odd = q.n[1];
   out->basis = HS_BASIS_HERMITIAN;
   out->dtype = dtype;
   if (!(mo <= herm_tol * ma))
@@ -489,6 +497,8 @@ hs_status hs_double_layer_hermitian(hs_ctx ctx, const double* A, int d, int D, h
   out->D = D;
   out->n_even = q.n[0];
   out->n_odd = q.n[1];
+  out->v_even = out->h_even = q.n[0];
+  out->v_odd = out->h_odd = q.n[1];
   out->basis = basis;
   out->dtype = dtype;
   return HS_OK;
@@ -571,7 +581,7 @@ hs_status hs_ctmrg_init(hs_ctx ctx, const hs_z2_tensor* a, int chi_max, hs_preci
     HS_TRY(ctx->tc_a_lo.ensure(nb));
     HS_CUDA(cudaMemsetAsync(ctx->tc_a_hi.p, 0, nb, ctx->stream));
     HS_CUDA(cudaMemsetAsync(ctx->tc_a_lo.p, 0, nb, ctx->stream));
-    const int ident[4] = {0, 1, 2, 3};
+    const int ident[kMaxLegs] = {0, 1, 2, 3, 0, 0};
     HS_CUDA(launch_permute_split(make_perm_plan(Am, Amp, ident), a->data, ctx->tc_a_hi.p, ctx->tc_a_lo.p,
                                  tc_mode(precision), ctx->stream));
     ctx->tc_a_src = a->data;

@@ -105,6 +105,8 @@ struct hs_ctx_s {
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   hs::DBuf solver2_dev, solver2_32_dev;
   std::vector<char> solver2_host, solver2_32_host;
+  // HOTRG workspace
+  hs::DBuf hb[16];
   // profiling: events between phases, harvested after the move's last sync
   bool prof = false;
   std::vector<cudaEvent_t> events;
@@ -128,6 +130,11 @@ hs_status gemm(hs_ctx ctx, hs_gemm_backend be, const GemmGroup& g, const double*
                double* C);
 hs_status permute(hs_ctx ctx, const Z2Mat& in, const Z2Mat& out, std::initializer_list<int> perm,
                   const double* src, double* dst);
+
+// Eigen-decompositions of the two parity blocks (block 1 on the second
+// stream); FP32 when f32. Shared with the HOTRG step.
+hs_status eig_pair(hs_ctx ctx, bool f32, void* A0, int n0, void* w0, void* A1, int n1, void* w1);
+hs_status eig_workspace(hs_ctx ctx, int nmax);
 
 // Tensor-core precisions: elements per 128-byte row (the K padding unit),
 // bytes per element, split mode of the permute/split kernels.

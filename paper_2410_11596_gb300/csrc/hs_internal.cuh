@@ -31,10 +31,11 @@ HS_HD Sect make_sect(int e, int o) {
   return s;
 }
 
-// A group of up to 3 legs fused into one matrix index.
+// A group of up to 4 legs fused into one matrix index.
+constexpr int kMaxFused = 4;
 struct Fused {
   int k;
-  Sect leg[3];
+  Sect leg[kMaxFused];
 };
 
 HS_HD Fused fused0() {
@@ -53,6 +54,23 @@ HS_HD Fused fused2(Sect a, Sect b) {
   f.k = 2;
   f.leg[0] = a;
   f.leg[1] = b;
+  return f;
+}
+HS_HD Fused fused3(Sect a, Sect b, Sect c) {
+  Fused f;
+  f.k = 3;
+  f.leg[0] = a;
+  f.leg[1] = b;
+  f.leg[2] = c;
+  return f;
+}
+HS_HD Fused fused4(Sect a, Sect b, Sect c, Sect d) {
+  Fused f;
+  f.k = 4;
+  f.leg[0] = a;
+  f.leg[1] = b;
+  f.leg[2] = c;
+  f.leg[3] = d;
   return f;
 }
 
@@ -109,16 +127,18 @@ HS_HD long long z2_elems(const Z2Mat& m) {
 
 // ---- permutation of a Z2 matrix into another grouping/order of its legs ----
 
-// One dense box: out[i0..i3] = in[...] for i_j < dim[j].
+// One dense box: out[i0..i5] = in[...] for i_j < dim[j] (up to 6 legs; the
+// leading unused dimensions have extent 1).
+constexpr int kMaxLegs = 6;
 struct Box {
   long long out_off, in_off;
-  int dim[4];
-  long long out_stride[4], in_stride[4];
+  int dim[kMaxLegs];
+  long long out_stride[kMaxLegs], in_stride[kMaxLegs];
   long long count;   // product of dims
   long long start;   // prefix sum of counts over earlier boxes
 };
 
-constexpr int kMaxBoxes = 8;
+constexpr int kMaxBoxes = 32;  // even-parity tuples of 6 legs
 
 struct PermPlan {
   int nbox;
@@ -205,6 +225,7 @@ struct SelectOut {
   int pad[2];
   double lam_max, lam_cut, lam_next;
   double log_norm_C, log_norm_T;
+  double discarded;  // sum of |lambda| over the states not kept
 };
 
 // Choose the chi eigenvalues of largest modulus across the two blocks.
@@ -232,6 +253,10 @@ cudaError_t launch_gather_p32(const float* V0, int n0, const float* V1, int n1, 
 cudaError_t launch_lowdin(double* G, int k0, int k1, cudaStream_t s);
 cudaError_t launch_normalize_max_to(double* x, long long n, unsigned long long* scratch, double* log_out,
                                     cudaStream_t s);
+
+// Sum of the diagonals of a block-diagonal FSO matrix with square blocks
+// (n0 x n0 then n1 x n1) into *out.
+cudaError_t launch_block_trace(const double* x, int n0, int n1, double* out, cudaStream_t s);
 
 // Dense views of an FSO environment (rotated back to the plain combined basis).
 cudaError_t launch_env_to_dense(const double* C, const double* T, int D, int c0, int c1,

@@ -135,6 +135,11 @@ __global__ void select_kernel(const double* __restrict__ w0, int n0, const doubl
   }
   for (int j = 0; j < cnt[0]; ++j) lam[j] = w0[idx[j]];
   for (int j = 0; j < cnt[1]; ++j) lam[cnt[0] + j] = w1[idx[chi + j]];
+  double all = 0.0, kept = 0.0;
+  for (int i = 0; i < n0; ++i) all += fabs(w0[i]);
+  for (int i = 0; i < n1; ++i) all += fabs(w1[i]);
+  for (int j = 0; j < cnt[0] + cnt[1]; ++j) kept += fabs(lam[j]);
+  out->discarded = all - kept;
   out->chi_new[0] = cnt[0];
   out->chi_new[1] = cnt[1];
   out->lam_max = first;
@@ -375,6 +380,25 @@ cudaError_t launch_normalize_max_to(double* x, long long n, unsigned long long* 
   if (e != cudaSuccess) return e;
   absmax_kernel<<<grid_for(n), 256, 0, s>>>(x, n, scratch);
   scale_to_kernel<<<grid_for(n), 256, 0, s>>>(x, n, scratch, log_out);
+  return cudaGetLastError();
+}
+
+__global__ void block_trace_kernel(const double* __restrict__ x, int n0, int n1, double* out) {
+  double v = 0.0;
+  for (int i = threadIdx.x; i < n0 + n1; i += blockDim.x)
+    v += i < n0 ? x[(long long)i * n0 + i] : x[(long long)n0 * n0 + (long long)(i - n0) * n1 + (i - n0)];
+  __shared__ double red[256];
+  red[threadIdx.x] = v;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = red[0];
+}
+
+cudaError_t launch_block_trace(const double* x, int n0, int n1, double* out, cudaStream_t s) {
+  block_trace_kernel<<<1, 256, 0, s>>>(x, n0, n1, out);
   return cudaGetLastError();
 }
 

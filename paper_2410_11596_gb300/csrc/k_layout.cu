@@ -38,20 +38,20 @@ PermPlan make_perm_plan(const Z2Mat& in, const Z2Mat& out, const int* perm) {
   long long start = 0;
   for (int bits = 0; bits < (1 << n); ++bits) {
     if (tuple_parity(bits)) continue;
-    int pout[4] = {0, 0, 0, 0}, pin[4] = {0, 0, 0, 0};
+    int pout[kMaxLegs] = {0}, pin[kMaxLegs] = {0};
     for (int j = 0; j < n; ++j) {
       pout[j] = (bits >> (n - 1 - j)) & 1;
       pin[perm[j]] = pout[j];
     }
-    long long ostr[4], istr_leg[4], ooff, ioff;
+    long long ostr[kMaxLegs], istr_leg[kMaxLegs], ooff, ioff;
     leg_strides(out, pout, ostr, &ooff);
     leg_strides(in, pin, istr_leg, &ioff);
     Box b{};
     b.out_off = ooff;
     b.in_off = ioff;
     b.count = 1;
-    const int pad = 4 - n;
-    for (int j = 0; j < 4; ++j) {
+    const int pad = kMaxLegs - n;
+    for (int j = 0; j < kMaxLegs; ++j) {
       b.dim[j] = 1;
       b.out_stride[j] = 0;
       b.in_stride[j] = 0;
@@ -103,17 +103,16 @@ __global__ void permute_f64_kernel(PermPlan plan, const double* __restrict__ in,
   const Box& b = plan.box[blockIdx.y];
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < b.count; e += stride) {
-    long long r = e;
-    const int i3 = (int)(r % b.dim[3]);
-    r /= b.dim[3];
-    const int i2 = (int)(r % b.dim[2]);
-    r /= b.dim[2];
-    const int i1 = (int)(r % b.dim[1]);
-    const int i0 = (int)(r / b.dim[1]);
-    const long long io = b.in_off + i0 * b.in_stride[0] + i1 * b.in_stride[1] + i2 * b.in_stride[2] +
-                         i3 * b.in_stride[3];
-    const long long oo = b.out_off + i0 * b.out_stride[0] + i1 * b.out_stride[1] +
-                         i2 * b.out_stride[2] + i3 * b.out_stride[3];
+    long long r = e, io = b.in_off, oo = b.out_off;
+#pragma unroll
+    for (int j = kMaxLegs - 1; j > 0; --j) {
+      const int ij = (int)(r % b.dim[j]);
+      r /= b.dim[j];
+      io += ij * b.in_stride[j];
+      oo += ij * b.out_stride[j];
+    }
+    io += r * b.in_stride[0];
+    oo += r * b.out_stride[0];
     out[oo] = scale * in[io];
   }
 }
@@ -124,17 +123,16 @@ __global__ void permute_split_kernel(PermPlan plan, const double* __restrict__ i
   const Box& b = plan.box[blockIdx.y];
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < b.count; e += stride) {
-    long long r = e;
-    const int i3 = (int)(r % b.dim[3]);
-    r /= b.dim[3];
-    const int i2 = (int)(r % b.dim[2]);
-    r /= b.dim[2];
-    const int i1 = (int)(r % b.dim[1]);
-    const int i0 = (int)(r / b.dim[1]);
-    const long long io = b.in_off + i0 * b.in_stride[0] + i1 * b.in_stride[1] + i2 * b.in_stride[2] +
-                         i3 * b.in_stride[3];
-    const long long oo = b.out_off + i0 * b.out_stride[0] + i1 * b.out_stride[1] +
-                         i2 * b.out_stride[2] + i3 * b.out_stride[3];
+    long long r = e, io = b.in_off, oo = b.out_off;
+#pragma unroll
+    for (int j = kMaxLegs - 1; j > 0; --j) {
+      const int ij = (int)(r % b.dim[j]);
+      r /= b.dim[j];
+      io += ij * b.in_stride[j];
+      oo += ij * b.out_stride[j];
+    }
+    io += r * b.in_stride[0];
+    oo += r * b.out_stride[0];
     const double x = in[io];
     if (MODE == 1) {
       float h;

@@ -1,0 +1,59 @@
+"""GPU HOTRG in the Hermitian basis vs the dense FP64 oracle HOTRG and Onsager (Sec. II.A)."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from gpu_util import ensure_library  # noqa: E402
+from oracle import doublelayer as dl, hotrg as oh  # noqa: E402
+from paper_2410_11596_gb300 import inputs  # noqa: E402
+from pins import onsager_log_z  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    ensure_library()
+    from paper_2410_11596_gb300.api import Context
+    c = Context(0)
+    yield c
+    c.close()
+
+
+@pytest.mark.parametrize("beta", [0.3, 0.6])
+def test_ising_log_z(ctx, beta):
+    from paper_2410_11596_gb300.api import HOTRG
+    A = inputs.ising_ipeps(beta)
+    h = HOTRG(ctx, A, 16)
+    h.run(30)
+    ref = oh.log_z_per_site(oh.run(dl.double_layer(A), 16, 30))
+    assert h.log_z_per_site() == pytest.approx(ref, abs=1e-10)
+    assert h.log_z_per_site() == pytest.approx(onsager_log_z(beta), abs=2e-9)
+
+
+@pytest.mark.parametrize("basis", ["hermitian", "dense"])
+@pytest.mark.parametrize("chi,steps", [(6, 6), (8, 9)])
+def test_random_tensor_matches_oracle(ctx, basis, chi, steps):
+    """ln Z per site and the normalised Gram spectra of every step vs the oracle."""
+    from paper_2410_11596_gb300.api import HOTRG
+    A = inputs.workload_tensor(1)
+    h = HOTRG(ctx, A, chi, basis=basis)
+    h.run(steps)
+    r = oh.run(dl.double_layer(A), chi, steps)
+    assert h.log_z_per_site() == pytest.approx(oh.log_z_per_site(r), rel=1e-11, abs=1e-12)
+    kept = [i["h_even"] + i["h_odd"] for i in h.infos]
+    assert kept == [min(chi, len(w)) for w in r.spectra]
+    if basis == "hermitian":
+        assert all(i["h_odd"] > 0 for i in h.infos[1:])
+
+
+def test_sector_bookkeeping(ctx):
+    from paper_2410_11596_gb300.api import HOTRG
+    h = HOTRG(ctx, inputs.workload_tensor(2), 12)      # D = 4: q = 16 = 10 + 6
+    info = h.step()
+    assert (h.t.v_even, h.t.v_odd) == (10, 6)           # vertical legs untouched by a vertical step
+    assert (h.t.h_even, h.t.h_odd) == (info["h_even"], info["h_odd"])
+    assert info["h_even"] + info["h_odd"] == 12
+    info = h.step()                                     # horizontal step truncates the vertical legs
+    assert (h.t.v_even + h.t.v_odd) == 12
