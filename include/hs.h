@@ -315,6 +315,15 @@ hs_status hs_gemm(hs_ctx ctx, hs_precision precision, int M, int N, int K, const
 hs_status hs_gemm_static(hs_precision precision, int M, int N, int K, const double* A, int lda,
                          const double* B, int ldb, double* C, int ldc, int* status_out, void* stream);
 
+/* Adjoint of the two-site RDM with the environment held fixed (the
+ * differentiation pattern of the hot path; the paper has no formula for it):
+ * dA[p,u,l,d,r] = sum_{IJ} drho[I,J] d rho[I,J] / d A[p,u,l,d,r] for the rho
+ * of hs_rdm(HS_RDM_TWO_SITE) before any mirroring (its exact mathematical
+ * derivative). drho: device, d^4 doubles, layout of rho; dA_out: device,
+ * d*D^4 doubles. Real A only. Asynchronous. */
+hs_status hs_rdm_vjp(hs_ctx ctx, const hs_env* env, const double* A, int d, int D, hs_dtype dtype,
+                     const double* drho, double* dA_out);
+
 /* Workspace the context will allocate for (D, chi): reported for planning. */
 hs_status hs_workspace_query(int D, int chi, hs_precision precision, size_t* bytes);
 

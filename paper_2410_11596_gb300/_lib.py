@@ -89,6 +89,7 @@ _PROTOS = {
     "hs_profile_read": (c_int, [c_void_p, POINTER(c_double), POINTER(c_double), c_int,
                                 POINTER(ctypes.c_longlong)]),
     "hs_gemm": (c_int, [c_void_p, c_int, c_int, c_int, c_int, c_void_p, c_int, c_void_p, c_int, c_void_p, c_int]),
+    "hs_rdm_vjp": (c_int, [c_void_p, POINTER(Env), c_void_p, c_int, c_int, c_int, c_void_p, c_void_p]),
     "hs_hotrg_tensor_bytes": (c_size_t, [c_int, c_int]),
     "hs_hotrg_init": (c_int, [c_void_p, POINTER(Z2Tensor), POINTER(Z2Tensor), POINTER(c_double)]),
     "hs_hotrg_step": (c_int, [c_void_p, POINTER(Z2Tensor), c_int, c_int, POINTER(HotrgInfo)]),
@@ -249,3 +250,7 @@ def hs_hotrg_step(ctx: int, t: Z2Tensor, chi: int, direction: int) -> dict:
     info = HotrgInfo()
     check(load().hs_hotrg_step(ctx, ctypes.byref(t), chi, direction, ctypes.byref(info)))
     return info.as_dict()
+
+
+def hs_rdm_vjp(ctx: int, env: Env, A, d: int, D: int, drho, dA) -> None:
+    check(load().hs_rdm_vjp(ctx, ctypes.byref(env), ptr(A), d, D, HS_F64, ptr(drho), ptr(dA)))

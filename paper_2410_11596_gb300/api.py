@@ -113,6 +113,20 @@ class CTMRG:
         _, t0, t1 = self.rdm2(h)
         return t1 / t0
 
+    def rdm2_of(self, A: torch.Tensor, h: torch.Tensor) -> tuple[torch.Tensor, torch.Tensor]:
+        """(rho, [Tr rho, Tr rho h]) for another tensor A with this (fixed) environment."""
+        n = self.d * self.d
+        rho = torch.empty((n, n), dtype=torch.float64, device=A.device)
+        tr = torch.empty(2, dtype=torch.float64, device=A.device)
+        L.hs_rdm(self.ctx.handle, self.env, A.contiguous(), self.d, self.D, L.HS_F64, L.HS_RDM_TWO_SITE,
+                 h.contiguous(), rho, tr)
+        return rho, tr
+
+    def rdm2_vjp(self, A: torch.Tensor, drho: torch.Tensor) -> torch.Tensor:
+        dA = torch.empty_like(A)
+        L.hs_rdm_vjp(self.ctx.handle, self.env, A.contiguous(), self.d, self.D, drho.contiguous(), dA)
+        return dA
+
     def one_site_env(self) -> torch.Tensor:
         """eps[u, l, d, r] in the plain combined basis (Eq. (4))."""
         q = self.D * self.D
@@ -155,3 +169,31 @@ class HOTRG:
         n = len(self.infos)
         val = self.log_norms[0] + sum(self.log_norms[k] / 2.0 ** k for k in range(1, n + 1))
         return float(val + np.log(self.infos[-1]["trace"]) / 2.0 ** n)
+
+
+class EnergyFn(torch.autograd.Function):
+    """E(A) = Tr(rho(A) h) / Tr rho(A) with the environment of `ctm` held fixed.
+
+    forward: hs_rdm; backward: d E / d rho = h^T / Tr rho - (Tr rho h / (Tr rho)^2) I,
+    then the hand-written adjoint hs_rdm_vjp.
+    """
+
+    @staticmethod
+    def forward(fctx, A: torch.Tensor, ctm: "CTMRG", h: torch.Tensor):
+        rho, tr = ctm.rdm2_of(A.detach(), h)
+        fctx.ctm = ctm
+        fctx.save_for_backward(A.detach(), h, tr)
+        return tr[1] / tr[0]
+
+    @staticmethod
+    def backward(fctx, g):
+        A, h, tr = fctx.saved_tensors
+        n = h.shape[0]
+        drho = g * (h.t() / tr[0] - (tr[1] / tr[0] ** 2) * torch.eye(n, dtype=h.dtype, device=h.device))
+        return fctx.ctm.rdm2_vjp(A, drho), None, None
+
+
+def bond_energy(ctm: CTMRG, A: torch.Tensor, h: np.ndarray | torch.Tensor) -> torch.Tensor:
+    """Differentiable bond energy with the environment of ctm held fixed."""
+    hd = h if isinstance(h, torch.Tensor) else torch.from_numpy(np.ascontiguousarray(h, dtype=np.float64))
+    return EnergyFn.apply(A, ctm, hd.to(A.device))

@@ -42,6 +42,51 @@ __global__ void open_double_layer_kernel(const double* __restrict__ A, int d, in
   }
 }
 
+// dA from the cotangents of the two open double layers (layouts of
+// open_double_layer_kernel: left site open on r, right site open on l). A
+// appears in each as the ket factor (index s) and as the bra factor (s'):
+//   dA[p, u, l, d, r] = sum over the other factor's indices of dao * A.
+__global__ void open_double_layer_vjp_kernel(const double* __restrict__ daoL, const double* __restrict__ daoR,
+                                             const double* __restrict__ A, int d, int D, double* __restrict__ dA) {
+  const int q = D * D;
+  const long long D4 = (long long)D * D * D * D;
+  const long long nA = d * D4;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < nA;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int p = (int)(e / D4);
+    long long t = e % D4;
+    const int ir = (int)(t % D);
+    t /= D;
+    const int id = (int)(t % D);
+    t /= D;
+    const int il = (int)(t % D);
+    const int iu = (int)(t / D);
+    double acc = 0.0;
+    for (int s2 = 0; s2 < d; ++s2)
+      for (long long o = 0; o < D4; ++o) {
+        long long oo = o;
+        const int jr = (int)(oo % D);
+        oo /= D;
+        const int jd = (int)(oo % D);
+        oo /= D;
+        const int jl = (int)(oo % D);
+        const int ju = (int)(oo / D);
+        const double a_other = A[s2 * D4 + o];
+        // this element as the ket factor: combined index = mine + D * other
+        const int ku = iu + D * ju, kl = il + D * jl, kd = id + D * jd, kr = ir + D * jr;
+        // this element as the bra factor: combined index = other + D * mine
+        const int bu = ju + D * iu, bl = jl + D * il, bd = jd + D * id, br = jr + D * ir;
+        // left site: [(s, s', m = r) | (l, u, d)]; right site: [(s, s', m = l) | (r, u, d)]
+        const long long kL = ((((((long long)p * d + s2) * q + kr) * q + kl) * q + ku) * q + kd);
+        const long long bL = ((((((long long)s2 * d + p) * q + br) * q + bl) * q + bu) * q + bd);
+        const long long kR = ((((((long long)p * d + s2) * q + kl) * q + kr) * q + ku) * q + kd);
+        const long long bR = ((((((long long)s2 * d + p) * q + bl) * q + br) * q + bu) * q + bd);
+        acc += (daoL[kL] + daoL[bL] + daoR[kR] + daoR[bR]) * a_other;
+      }
+    dA[e] = acc;
+  }
+}
+
 // rho[(s1 s2), (s1' s2')] = rho4[s1, s1', s2, s2']; mirror the upper triangle
 // when requested; tr[0] = Tr rho, tr[1] = Tr(rho h).
 __global__ void finish_rho_kernel(const double* __restrict__ rho4, int d, bool mirror,
@@ -107,15 +152,13 @@ GemmGroup dense_gemm(long long M, long long N, long long K) {
 
 }  // namespace
 
-extern "C" hs_status hs_rdm(hs_ctx ctx, const hs_env* env, const double* A, int d, int D,
-                            hs_dtype dtype, hs_rdm_kind kind, const double* h, double* out,
-                            double* tr_out) {
-  HS_TRY(check_ctx(ctx));
-  if (!env || !A || !out || d <= 0 || D != env->D) return fail(HS_ERR_INVALID_ARG, "bad arguments");
-  if (dtype != HS_F64) return fail(HS_ERR_UNSUPPORTED, "complex tensors are not supported by this build");
-  if (kind != HS_RDM_TWO_SITE && kind != HS_RDM_ENV_ONE_SITE)
-    return fail(HS_ERR_INVALID_ARG, "unknown rdm kind");
-  if (kind == HS_RDM_TWO_SITE && !tr_out) return fail(HS_ERR_INVALID_ARG, "tr_out is required");
+// Shared forward chain of the two-site network up to the half-network blocks:
+// on return r[8] = Z2 [(l,u,t')|(d,b')], r[9] = Z2p [(t',b')|(l,u,d)],
+// r[10]/r[11] = open double layers of the left/right site, r[12]/r[13] =
+// LB/RB [(t',b')|(s,s',m)], r[14]/r[15] = LBp/RBp [(s,s')|(t',b',m)],
+// r[6] = rho4 [(s1,s1')|(s2,s2')]. kind selects how far it goes.
+hs_status rdm_chain(hs_ctx ctx, const hs_env* env, const double* A, int d, int D, hs_rdm_kind kind,
+                    double* eps_out) {
   cudaStream_t s = ctx->stream;
   const hs_gemm_backend be = env->gemm_backend;
   const long long chi = env->chi_even + env->chi_odd, q = (long long)D * D;
@@ -157,7 +200,7 @@ extern "C" hs_status hs_rdm(hs_ctx ctx, const hs_env* env, const double* A, int 
     HS_TRY(permute(ctx, dense({q * q, chi, q, chi}), dense({q * q, q, chi, chi}), {0, 2, 1, 3}, Z2, Z2p));
     HS_TRY(permute(ctx, dense({chi, q, chi}), dense({q, chi, chi}), {1, 0, 2}, E, r[12].d()));  // Hd[d|(a',b')]
     HS_TRY(gemm(ctx, be, dense_gemm(q * q * q, q, chi * chi), Z2p, r[12].d(), r[13].d()));     // [(u,l,r)|d]
-    HS_TRY(permute(ctx, dense({q * q, q, q}), dense({q * q, q, q}), {0, 2, 1}, r[13].d(), out));
+    HS_TRY(permute(ctx, dense({q * q, q, q}), dense({q * q, q, q}), {0, 2, 1}, r[13].d(), eps_out));
     return HS_OK;
   }
 
@@ -184,7 +227,71 @@ extern "C" hs_status hs_rdm(hs_ctx ctx, const hs_env* env, const double* A, int 
   HS_TRY(permute(ctx, dense({c2, d2, q}), dense({d2, c2, q}), {1, 0, 2}, LB, LBp));
   HS_TRY(permute(ctx, dense({c2, d2, q}), dense({d2, c2, q}), {1, 0, 2}, RB, RBp));
   HS_TRY(gemm(ctx, be, dense_gemm(d2, d2, c2 * q), LBp, RBp, Z1));  // rho4[(s1,s1') | (s2,s2')]
-  finish_rho_kernel<<<1, 256, 0, s>>>(Z1, d, env->basis == HS_BASIS_HERMITIAN, h, out, tr_out);
+  return HS_OK;
+}
+
+extern "C" hs_status hs_rdm(hs_ctx ctx, const hs_env* env, const double* A, int d, int D,
+                            hs_dtype dtype, hs_rdm_kind kind, const double* h, double* out,
+                            double* tr_out) {
+  HS_TRY(check_ctx(ctx));
+  if (!env || !A || !out || d <= 0 || D != env->D) return fail(HS_ERR_INVALID_ARG, "bad arguments");
+  if (dtype != HS_F64) return fail(HS_ERR_UNSUPPORTED, "complex tensors are not supported by this build");
+  if (kind != HS_RDM_TWO_SITE && kind != HS_RDM_ENV_ONE_SITE)
+    return fail(HS_ERR_INVALID_ARG, "unknown rdm kind");
+  if (kind == HS_RDM_TWO_SITE && !tr_out) return fail(HS_ERR_INVALID_ARG, "tr_out is required");
+  HS_TRY(rdm_chain(ctx, env, A, d, D, kind, out));
+  if (kind == HS_RDM_ENV_ONE_SITE) return HS_OK;
+  finish_rho_kernel<<<1, 256, 0, ctx->stream>>>(ctx->r[6].d(), d, env->basis == HS_BASIS_HERMITIAN, h, out,
+                                                tr_out);
+  HS_CUDA(cudaGetLastError());
+  return HS_OK;
+}
+
+extern "C" hs_status hs_rdm_vjp(hs_ctx ctx, const hs_env* env, const double* A, int d, int D, hs_dtype dtype,
+                                const double* drho, double* dA_out) {
+  HS_TRY(check_ctx(ctx));
+  if (!env || !A || !drho || !dA_out || d <= 0 || D != env->D) return fail(HS_ERR_INVALID_ARG, "bad arguments");
+  if (dtype != HS_F64) return fail(HS_ERR_UNSUPPORTED, "complex tensors are not supported by this build");
+  HS_TRY(rdm_chain(ctx, env, A, d, D, HS_RDM_TWO_SITE, nullptr));
+  cudaStream_t s = ctx->stream;
+  const hs_gemm_backend be = env->gemm_backend;
+  const long long chi = env->chi_even + env->chi_odd, q = (long long)D * D, c2 = chi * chi,
+                  d2 = (long long)d * d;
+  DBuf* r = ctx->r;
+  double *Z2 = r[8].d(), *Z2p = r[9].d(), *LB = r[12].d(), *RB = r[13].d();
+  // rho[(s1 s2), (s1' s2')] = rho4[s1, s1', s2, s2']: cotangent of rho4 and its transpose
+  HS_TRY(ctx->hb[0].ensure(2 * d2 * d2 * 8));
+  double* drho4 = ctx->hb[0].d();
+  double* drho4T = drho4 + d2 * d2;
+  HS_TRY(permute(ctx, dense({d, d, d, d}), dense({d, d, d, d}), {0, 2, 1, 3}, drho, drho4));
+  HS_TRY(permute(ctx, dense({d2, d2}), dense({d2, d2}), {1, 0}, drho4, drho4T));
+  // RBq/LBq[(t', b', m) | (s, s')]
+  HS_TRY(ctx->hb[1].ensure(c2 * d2 * q * 8));
+  HS_TRY(ctx->hb[2].ensure(c2 * d2 * q * 8));
+  HS_TRY(ctx->hb[3].ensure(c2 * d2 * q * 8));
+  HS_TRY(ctx->hb[4].ensure(c2 * d2 * q * 8));
+  double *LBq = ctx->hb[1].d(), *RBq = ctx->hb[2].d(), *dLB = ctx->hb[3].d(), *dRB = ctx->hb[4].d();
+  HS_TRY(permute(ctx, dense({c2, d2, q}), dense({c2, q, d2}), {0, 2, 1}, LB, LBq));
+  HS_TRY(permute(ctx, dense({c2, d2, q}), dense({c2, q, d2}), {0, 2, 1}, RB, RBq));
+  // dLB[(s1,s1') | (t',b',m)] = drho4 RB ; dRB[(s2,s2') | (t',b',m)] = drho4^T LB
+  HS_TRY(gemm(ctx, be, dense_gemm(d2, c2 * q, d2), drho4, RBq, dLB));
+  HS_TRY(gemm(ctx, be, dense_gemm(d2, c2 * q, d2), drho4T, LBq, dRB));
+  // [(s, s', m) | (t', b')]
+  HS_TRY(ctx->hb[5].ensure(c2 * d2 * q * 8));
+  HS_TRY(ctx->hb[6].ensure(c2 * d2 * q * 8));
+  double *dLBm = ctx->hb[5].d(), *dRBm = ctx->hb[6].d();
+  HS_TRY(permute(ctx, dense({d2, c2, q}), dense({d2, q, c2}), {0, 2, 1}, dLB, dLBm));
+  HS_TRY(permute(ctx, dense({d2, c2, q}), dense({d2, q, c2}), {0, 2, 1}, dRB, dRBm));
+  // Z2t[(l, u, d) | (t', b')] from Z2[(l,u), t', d, b']
+  HS_TRY(permute(ctx, dense({q * q, chi, q, chi}), dense({q * q, q, chi, chi}), {0, 2, 1, 3}, Z2, Z2p));
+  // cotangents of the open double layers: dao[(s, s', m) | (c0, u, d)]
+  const long long nao = d2 * q * q * q * q;
+  HS_TRY(ctx->hb[7].ensure(nao * 8));
+  HS_TRY(ctx->hb[8].ensure(nao * 8));
+  HS_TRY(gemm(ctx, be, dense_gemm(d2 * q, q * q * q, c2), dLBm, Z2p, ctx->hb[7].d()));
+  HS_TRY(gemm(ctx, be, dense_gemm(d2 * q, q * q * q, c2), dRBm, Z2p, ctx->hb[8].d()));
+  const long long nA = (long long)d * D * D * D * D;
+  open_double_layer_vjp_kernel<<<grid_for(nA), 256, 0, s>>>(ctx->hb[7].d(), ctx->hb[8].d(), A, d, D, dA_out);
   HS_CUDA(cudaGetLastError());
   return HS_OK;
 }

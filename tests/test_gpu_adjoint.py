@@ -1,0 +1,59 @@
+"""Hand-written adjoint of the RDM/energy contraction (hs_rdm_vjp) behind torch.autograd."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from gpu_util import ensure_library  # noqa: E402
+from oracle import adjoint, ctmrg as oc, doublelayer as dl  # noqa: E402
+from paper_2410_11596_gb300 import inputs  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    ensure_library()
+    from paper_2410_11596_gb300.api import Context
+    c = Context(0)
+    yield c
+    c.close()
+
+
+@pytest.mark.parametrize("k,chi,moves,basis", [(1, 16, 12, "hermitian"), (2, 32, 15, "hermitian"),
+                                               (1, 16, 12, "dense")])
+def test_energy_gradient(ctx, k, chi, moves, basis):
+    from paper_2410_11596_gb300.api import CTMRG, bond_energy
+    A = inputs.workload_tensor(k)
+    h = inputs.heisenberg_bond()
+    ctm = CTMRG(ctx, A, chi, basis=basis)
+    ctm.run(moves)
+    At = torch.from_numpy(A.copy()).cuda().requires_grad_(True)
+    e = bond_energy(ctm, At, h)
+    e.backward()
+    g = At.grad.cpu().numpy()
+    # (1) dense gradient: torch autograd on the oracle's own environment
+    r = oc.run(dl.double_layer(A), chi, moves)
+    g_ref = adjoint.energy_gradient(r.C, r.T, A, h)
+    assert np.abs(g - g_ref).max() <= 1e-8 * np.abs(g_ref).max()
+    # (2) central differences, h = 1e-6, on 64 seeded coordinates, environment fixed
+    rng = np.random.default_rng(100 + k)
+    eps = 1e-6
+    hd = torch.from_numpy(h).cuda()
+    Ad = torch.from_numpy(A).cuda()
+    for flat in rng.choice(A.size, size=min(64, A.size), replace=False):
+        dv = torch.zeros(A.size, dtype=torch.float64, device="cuda")
+        dv[flat] = eps
+        dv = dv.reshape(A.shape)
+        _, tp = ctm.rdm2_of(Ad + dv, hd)
+        _, tm = ctm.rdm2_of(Ad - dv, hd)
+        fd = float(tp[1] / tp[0] - tm[1] / tm[0]) / (2 * eps)
+        assert g.reshape(-1)[flat] == pytest.approx(fd, rel=1e-5, abs=1e-8)
+    # (3) four random directional derivatives
+    for _ in range(4):
+        v = rng.standard_normal(A.shape)
+        vd = torch.from_numpy(v).cuda()
+        _, tp = ctm.rdm2_of(Ad + eps * vd, hd)
+        _, tm = ctm.rdm2_of(Ad - eps * vd, hd)
+        fd = float(tp[1] / tp[0] - tm[1] / tm[0]) / (2 * eps)
+        assert float(np.sum(g * v)) == pytest.approx(fd, rel=1e-6, abs=1e-9)
