@@ -60,7 +60,8 @@ hs_status gemm(hs_ctx ctx, hs_gemm_backend be, const GemmGroup& g, const double*
     }
     return HS_OK;
   }
-  HS_CUDA(launch_gemm_f64(g, A, B, C, 1.0, ctx->stream));
+  HS_TRY(ctx->splitk.ensure(kSplitKElems * sizeof(double)));
+  HS_CUDA(launch_gemm_f64(g, A, B, C, 1.0, ctx->stream, ctx->splitk.d(), kSplitKElems));
   if (g.n > 0) ctx->launches += 1;
   return HS_OK;
 }
@@ -202,53 +203,66 @@ hs_status eig_pair(hs_ctx ctx, bool f32, void* A0, int n0, void* w0, void* A1, i
 }
 hs_status eig_workspace(hs_ctx ctx, int nmax) { return eig_workspace_impl(ctx, nmax); }
 
-// C[R|N] = X[R|K] a[N|K]^T on the tensor cores. X is produced here from `src`
-// (layout Xsrc) by the permutation `perm`, written straight into the split,
-// K-padded operand buffers; a is the split copy made by hs_ctmrg_init.
-hs_status tc_a_gemm(hs_ctx ctx, hs_precision prec, const Z2Mat& Xsrc, const Z2Mat& X,
-                    std::initializer_list<int> perm, const double* src, const Z2Mat& Am, const Z2Mat& Cm,
-                    double* C) {
+// Write the operand `layout` (legs = src legs permuted by perm) of a
+// tensor-core GEMM as split, K-padded hi/lo arrays.
+hs_status tc_split(hs_ctx ctx, hs_precision prec, const Z2Mat& src_layout, const Z2Mat& layout,
+                   std::initializer_list<int> perm, const double* src, DBuf& hi, DBuf& lo) {
   const int pad = tc_pad(prec), eb = tc_elem_bytes(prec);
-  const Z2Mat Xp = mat(X.r, X.c, pad), Amp = mat(Am.r, Am.c, pad);
-  const size_t nb = (size_t)z2_elems(Xp) * eb;
-  if (nb > ctx->tc_x_hi.bytes) return fail(HS_ERR_WORKSPACE, "tensor-core operand buffer too small");
-  {
-    PhaseScope ps(ctx, HS_PHASE_PERMUTE);
-    int pm[kMaxLegs] = {0}, i = 0;
-    for (int v : perm) pm[i++] = v;
-    HS_CUDA(cudaMemsetAsync(ctx->tc_x_hi.p, 0, nb, ctx->stream));
-    HS_CUDA(cudaMemsetAsync(ctx->tc_x_lo.p, 0, nb, ctx->stream));
-    const PermPlan plan = make_perm_plan(Xsrc, Xp, pm);
-    HS_CUDA(launch_permute_split(plan, src, ctx->tc_x_hi.p, ctx->tc_x_lo.p, tc_mode(prec), ctx->stream));
-    if (plan.nbox > 0) ctx->launches += 1;
-  }
+  const Z2Mat P = mat(layout.r, layout.c, pad);
+  const size_t nb = (size_t)z2_elems(P) * eb;
+  HS_TRY(hi.ensure(nb));
+  HS_TRY(lo.ensure(nb));
+  PhaseScope ps(ctx, HS_PHASE_PERMUTE);
+  int pm[kMaxLegs] = {0}, i = 0;
+  for (int v : perm) pm[i++] = v;
+  HS_CUDA(cudaMemsetAsync(hi.p, 0, nb, ctx->stream));
+  HS_CUDA(cudaMemsetAsync(lo.p, 0, nb, ctx->stream));
+  const PermPlan plan = make_perm_plan(src_layout, P, pm);
+  HS_CUDA(launch_permute_split(plan, src, hi.p, lo.p, tc_mode(prec), ctx->stream));
+  if (plan.nbox > 0) ctx->launches += 1;
+  return HS_OK;
+}
+
+// C[R|N] = A[R|K] B[N|K]^T on the tensor cores from split operands (logical
+// layouts A, B; buffers padded as written by tc_split), FP64 C in layout Cm.
+hs_status tc_run(hs_ctx ctx, hs_precision prec, const Z2Mat& A, const DBuf& ahi, const DBuf& alo,
+                 const Z2Mat& B, const DBuf& bhi, const DBuf& blo, const Z2Mat& Cm, double* C) {
+  const int pad = tc_pad(prec), eb = tc_elem_bytes(prec);
+  const Z2Mat Ap = mat(A.r, A.c, pad), Bp = mat(B.r, B.c, pad);
   TcProblem pr[2];
   int n = 0;
   for (int p = 0; p < 2; ++p) {
     TcProblem& t = pr[n];
-    t.M = (int)z2_rows(Xp, p);
-    t.N = (int)z2_rows(Amp, p);
-    t.Kp = (int)z2_ld(Xp, p);
+    t.M = (int)z2_rows(Ap, p);
+    t.N = (int)z2_rows(Bp, p);
+    t.Kp = (int)z2_ld(Ap, p);
     if (t.M == 0 || t.N == 0) continue;
-    if (z2_cols(Xp, p) == 0) {  // empty contraction: the block is zero
+    if (z2_cols(Ap, p) == 0) {  // empty contraction: the block is zero
       HS_CUDA(cudaMemset2DAsync(C + z2_block_off(Cm, p), sizeof(double) * z2_ld(Cm, p), 0,
                                 sizeof(double) * t.N, t.M, ctx->stream));
       continue;
     }
     t.ldc = (int)z2_ld(Cm, p);
-    t.a_hi = static_cast<char*>(ctx->tc_x_hi.p) + z2_block_off(Xp, p) * eb;
-    t.a_lo = static_cast<char*>(ctx->tc_x_lo.p) + z2_block_off(Xp, p) * eb;
-    t.b_hi = static_cast<char*>(ctx->tc_a_hi.p) + z2_block_off(Amp, p) * eb;
-    t.b_lo = static_cast<char*>(ctx->tc_a_lo.p) + z2_block_off(Amp, p) * eb;
+    t.a_hi = static_cast<const char*>(ahi.p) + z2_block_off(Ap, p) * eb;
+    t.a_lo = static_cast<const char*>(alo.p) + z2_block_off(Ap, p) * eb;
+    t.b_hi = static_cast<const char*>(bhi.p) + z2_block_off(Bp, p) * eb;
+    t.b_lo = static_cast<const char*>(blo.p) + z2_block_off(Bp, p) * eb;
     t.c = C + z2_block_off(Cm, p);
     ++n;
   }
-  {
-    PhaseScope ps(ctx, HS_PHASE_GEMM_TC);
-    HS_CUDA(launch_gemm_tc(prec, pr, n, static_cast<int*>(ctx->tc_err.p), ctx->stream));
-    if (n > 0) ctx->launches += 1;
-  }
+  PhaseScope ps(ctx, HS_PHASE_GEMM_TC);
+  HS_CUDA(launch_gemm_tc(prec, pr, n, static_cast<int*>(ctx->tc_err.p), ctx->stream));
+  if (n > 0) ctx->launches += 1;
   return HS_OK;
+}
+
+// C[R|N] = X[R|K] a[N|K]^T with X written from `src` (layout Xsrc) by `perm`
+// and a the split copy of the double layer made by hs_ctmrg_init.
+hs_status tc_a_gemm(hs_ctx ctx, hs_precision prec, const Z2Mat& Xsrc, const Z2Mat& X,
+                    std::initializer_list<int> perm, const double* src, const Z2Mat& Am, const Z2Mat& Cm,
+                    double* C) {
+  HS_TRY(tc_split(ctx, prec, Xsrc, X, perm, src, ctx->tc_x_hi, ctx->tc_x_lo));
+  return tc_run(ctx, prec, X, ctx->tc_x_hi, ctx->tc_x_lo, Am, ctx->tc_a_hi, ctx->tc_a_lo, Cm, C);
 }
 
 // FP32-eigenvector projector (HS_EIG_F32_PROJECTED): gather the kept FP32
@@ -294,13 +308,14 @@ hs_status project_f32(hs_ctx ctx, const float* V0f, int n0, const float* V1f, in
     GemmGroup gg = group([&](int p) {
       return GemmProblem{k[p], k[p], n[p], n[p], n[p], k[p], ptoff[p], ptoff[p], goff[p]};
     });
-    HS_CUDA(launch_gemm_f64(gg, PT, PT, G, 1.0, s));
+    HS_TRY(ctx->splitk.ensure(kSplitKElems * sizeof(double)));
+    HS_CUDA(launch_gemm_f64(gg, PT, PT, G, 1.0, s, ctx->splitk.d(), kSplitKElems));
     HS_CUDA(launch_lowdin(G, k[0], k[1], s));
     // PT2 = M PT, i.e. C = M (P)^T with P the column layout
     GemmGroup gm = group([&](int p) {
       return GemmProblem{k[p], n[p], k[p], k[p], k[p], n[p], goff[p], ptoff[p], ptoff[p]};
     });
-    HS_CUDA(launch_gemm_f64(gm, G, P, PT2, 1.0, s));
+    HS_CUDA(launch_gemm_f64(gm, G, P, PT2, 1.0, s, ctx->splitk.d(), kSplitKElems));
     *flops += gemm_flops(gg) + gemm_flops(gm);
     ctx->phase_flops[HS_PHASE_GEMM] += gemm_flops(gg) + gemm_flops(gm);
     HS_TRY(permute(ctx, PTm, Pm, {1, 2, 0}, PT2, P));  // columns of the updated vectors
@@ -311,11 +326,11 @@ hs_status project_f32(hs_ctx ctx, const float* V0f, int n0, const float* V1f, in
   GemmGroup gw = group([&](int p) {
     return GemmProblem{k[p], n[p], n[p], n[p], n[p], n[p], ptoff[p], (long long)(Cp[p] - C0), ptoff[p]};
   });
-  HS_CUDA(launch_gemm_f64(gw, PT, C0, W, 1.0, s));
+  HS_CUDA(launch_gemm_f64(gw, PT, C0, W, 1.0, s, ctx->splitk.d(), kSplitKElems));
   GemmGroup gc = group([&](int p) {
     return GemmProblem{k[p], k[p], n[p], n[p], n[p], k[p], ptoff[p], ptoff[p], goff[p]};
   });
-  HS_CUDA(launch_gemm_f64(gc, W, PT, env->C, 1.0, s));
+  HS_CUDA(launch_gemm_f64(gc, W, PT, env->C, 1.0, s, ctx->splitk.d(), kSplitKElems));
   *flops += gemm_flops(gw) + gemm_flops(gc);
   ctx->phase_flops[HS_PHASE_GEMM] += gemm_flops(gw) + gemm_flops(gc);
   HS_CUDA(launch_normalize_max_to(env->C, goff[1] + (long long)k[1] * k[1],
@@ -401,7 +416,8 @@ hs_status hs_destroy(hs_ctx ctx) {
   for (DBuf* b : bufs) b->release();
   for (DBuf& b : ctx->r) b.release();
   for (DBuf& b : ctx->hb) b.release();
-  DBuf* more[] = {&ctx->c32, &ctx->w32, &ctx->pcol, &ctx->pt2, &ctx->gram, &ctx->wproj, &ctx->solver32_dev};
+  DBuf* more[] = {&ctx->c32,  &ctx->w32,   &ctx->pcol,         &ctx->pt2,
+                  &ctx->gram, &ctx->wproj, &ctx->solver32_dev, &ctx->splitk};
   for (DBuf* b : more) b->release();
   for (cudaEvent_t e : ctx->events) cudaEventDestroy(e);
   if (ctx->h_sel) cudaFreeHost(ctx->h_sel);
@@ -622,12 +638,21 @@ hs_status hs_ctmrg_move(hs_ctx ctx, const hs_z2_tensor* a, hs_env* env, int chi,
   GemmGroup g1 = make_z2_gemm(Tcr, Cm, X1), g2 = make_z2_gemm(X1, Tcr, X2),
             g3 = make_z2_gemm(X2p, Am, X3);
   flops += gemm_flops(g1) + gemm_flops(g2) + gemm_flops(g3);
-  ctx->phase_flops[HS_PHASE_GEMM] += gemm_flops(g1) + gemm_flops(g2);
-  ctx->phase_flops[tc ? HS_PHASE_GEMM_TC : HS_PHASE_GEMM] += gemm_flops(g3);
-  {
+  ctx->phase_flops[HS_PHASE_GEMM] += gemm_flops(g1);
+  ctx->phase_flops[tc ? HS_PHASE_GEMM_TC : HS_PHASE_GEMM] += gemm_flops(g2) + gemm_flops(g3);
+  if (!tc) {
     PhaseScope ps(ctx, HS_PHASE_GEMM);
     HS_TRY(gemm(ctx, be, g1, env->T, env->C, ctx->x1.d()));
     HS_TRY(gemm(ctx, be, g2, ctx->x1.d(), env->T, B1));
+  } else {
+    {
+      PhaseScope ps(ctx, HS_PHASE_GEMM);
+      HS_TRY(gemm(ctx, be, g1, env->T, env->C, ctx->x1.d()));
+    }
+    // the split edge serves as B of G2 here and of G4 below
+    HS_TRY(tc_split(ctx, env->precision, Tcr, Tcr, {0, 1, 2}, env->T, ctx->tc_b_hi, ctx->tc_b_lo));
+    HS_TRY(tc_split(ctx, env->precision, X1, X1, {0, 1, 2}, ctx->x1.d(), ctx->tc_x_hi, ctx->tc_x_lo));
+    HS_TRY(tc_run(ctx, env->precision, X1, ctx->tc_x_hi, ctx->tc_x_lo, Tcr, ctx->tc_b_hi, ctx->tc_b_lo, X2, B1));
   }
   if (tc) {
     HS_TRY(tc_a_gemm(ctx, env->precision, X2, X2p, {0, 2, 3, 1}, B1, Am, X3, B2));
@@ -707,15 +732,17 @@ hs_status hs_ctmrg_move(hs_ctx ctx, const hs_z2_tensor* a, hs_env* env, int chi,
   }
   GemmGroup g4 = make_z2_gemm(Pp, Tcr, Y), g5 = make_z2_gemm(Yp, Am, Zm), g6 = make_z2_gemm(Zp, PT, Tn);
   flops += gemm_flops(g4) + gemm_flops(g5) + gemm_flops(g6);
-  ctx->phase_flops[HS_PHASE_GEMM] += gemm_flops(g4) + gemm_flops(g6);
-  ctx->phase_flops[tc ? HS_PHASE_GEMM_TC : HS_PHASE_GEMM] += gemm_flops(g5);
+  ctx->phase_flops[tc ? HS_PHASE_GEMM_TC : HS_PHASE_GEMM] += gemm_flops(g4) + gemm_flops(g5) + gemm_flops(g6);
   {
     PhaseScope ps(ctx, HS_PHASE_PERMUTE);
     HS_TRY(permute(ctx, PT, Pp, {2, 0, 1}, ctx->pt.d(), ctx->pp.d()));  // (a',a,d) -> (d,a',a)
   }
-  {
+  if (!tc) {
     PhaseScope ps(ctx, HS_PHASE_GEMM);
     HS_TRY(gemm(ctx, be, g4, ctx->pp.d(), env->T, B1));
+  } else {
+    HS_TRY(tc_split(ctx, env->precision, Pp, Pp, {0, 1, 2}, ctx->pp.d(), ctx->tc_x_hi, ctx->tc_x_lo));
+    HS_TRY(tc_run(ctx, env->precision, Pp, ctx->tc_x_hi, ctx->tc_x_lo, Tcr, ctx->tc_b_hi, ctx->tc_b_lo, Y, B1));
   }
   if (tc) {
     HS_TRY(tc_a_gemm(ctx, env->precision, Y, Yp, {1, 2, 0, 3}, B1, Am, Zm, B2));
@@ -728,13 +755,17 @@ hs_status hs_ctmrg_move(hs_ctx ctx, const hs_z2_tensor* a, hs_env* env, int chi,
     PhaseScope ps(ctx, HS_PHASE_GEMM);
     HS_TRY(gemm(ctx, be, g5, B2, a->data, B1));
   }
-  {
-    PhaseScope ps(ctx, HS_PHASE_PERMUTE);
-    HS_TRY(permute(ctx, Zm, Zp, {0, 3, 1, 2}, B1, B2));   // (a',b,u,r) -> (a',r,b,u)
-  }
-  {
+  if (!tc) {
+    {
+      PhaseScope ps(ctx, HS_PHASE_PERMUTE);
+      HS_TRY(permute(ctx, Zm, Zp, {0, 3, 1, 2}, B1, B2));   // (a',b,u,r) -> (a',r,b,u)
+    }
     PhaseScope ps(ctx, HS_PHASE_GEMM);
     HS_TRY(gemm(ctx, be, g6, B2, ctx->pt.d(), env->T));
+  } else {
+    HS_TRY(tc_split(ctx, env->precision, Zm, Zp, {0, 3, 1, 2}, B1, ctx->tc_x_hi, ctx->tc_x_lo));
+    HS_TRY(tc_split(ctx, env->precision, PT, PT, {0, 1, 2}, ctx->pt.d(), ctx->tc_b_hi, ctx->tc_b_lo));
+    HS_TRY(tc_run(ctx, env->precision, Zp, ctx->tc_x_hi, ctx->tc_x_lo, PT, ctx->tc_b_hi, ctx->tc_b_lo, Tn, env->T));
   }
 
   // C <- diag(lambda)/max|lambda|, T <- T/max|T|

@@ -48,6 +48,9 @@ const char* last_error();
     if (s_ != HS_OK) return s_; \
   } while (0)
 
+// Split-K workspace of the FP64 GEMM, in doubles (32 MB).
+constexpr long long kSplitKElems = 4ll << 20;
+
 // Device buffer that only grows.
 struct DBuf {
   void* p = nullptr;
@@ -107,6 +110,8 @@ struct hs_ctx_s {
   std::vector<char> solver2_host, solver2_32_host;
   // HOTRG workspace
   hs::DBuf hb[16];
+  // split-K partial sums of the FP64 GEMM
+  hs::DBuf splitk;
   // profiling: events between phases, harvested after the move's last sync
   bool prof = false;
   std::vector<cudaEvent_t> events;

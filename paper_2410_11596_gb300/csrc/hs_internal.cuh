@@ -201,8 +201,10 @@ struct TcProblem {
 // precision: HS_PREC_TF32X3, HS_PREC_TF32 or HS_PREC_BF16X3. err receives a
 // non-zero code if a bounded wait inside the kernel gave up.
 cudaError_t launch_gemm_tc(int precision, const TcProblem* probs, int nprob, int* err, cudaStream_t s);
+// part/part_elems: optional workspace for split-K partial sums (used when the
+// output tiles alone cannot fill the GPU); nullptr disables splitting.
 cudaError_t launch_gemm_f64(const GemmGroup& g, const double* A, const double* B, double* C,
-                            double alpha, cudaStream_t s);
+                            double alpha, cudaStream_t s, double* part = nullptr, long long part_elems = 0);
 
 // A[p,u,l,d,r] (real) -> a~ blocks in FSO [(u,l)|(d,r)]; hermitian selects the
 // rotation by U^T on every leg, otherwise the plain combined basis.

@@ -10,10 +10,21 @@ constexpr int BM = 64, BN = 64, BK = 16, NT = 256;
 
 __device__ __forceinline__ int cdiv(int a, int b) { return (a + b - 1) / b; }
 
+// With nsplit > 1 every tile is computed as nsplit partial sums over
+// consecutive K ranges, written to `part` (problem i at part_off[i], split s
+// at s * M * N, row-major M x N) and summed by splitk_reduce_kernel in a fixed
+// order (deterministic).
+struct SplitK {
+  int nsplit;
+  long long part_off[kMaxProblems];
+};
+
 __global__ void __launch_bounds__(NT) gemm_f64_nt_kernel(GemmGroup g, const double* __restrict__ A,
                                                          const double* __restrict__ B,
-                                                         double* __restrict__ C, double alpha) {
-  int t = blockIdx.x;
+                                                         double* __restrict__ C, double alpha, SplitK sk,
+                                                         double* __restrict__ part) {
+  int t = blockIdx.x / sk.nsplit;
+  const int split = blockIdx.x % sk.nsplit;
   int pi = 0;
   for (; pi < g.n; ++pi) {
     const int tiles = cdiv(g.p[pi].M, BM) * cdiv(g.p[pi].N, BN);
@@ -24,6 +35,9 @@ __global__ void __launch_bounds__(NT) gemm_f64_nt_kernel(GemmGroup g, const doub
   const GemmProblem P = g.p[pi];
   const int tn_count = cdiv(P.N, BN);
   const int m0 = (t / tn_count) * BM, n0 = (t % tn_count) * BN;
+  const int kchunk = cdiv(cdiv(P.K, sk.nsplit), BK) * BK;
+  const int kbeg = split * kchunk;
+  const int kend = min(P.K, kbeg + kchunk);
   const double* Ap = A + P.a_off;
   const double* Bp = B + P.b_off;
   double* Cp = C + P.c_off;
@@ -37,15 +51,15 @@ __global__ void __launch_bounds__(NT) gemm_f64_nt_kernel(GemmGroup g, const doub
 #pragma unroll
     for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
 
-  for (int k0 = 0; k0 < P.K; k0 += BK) {
+  for (int k0 = kbeg; k0 < kend; k0 += BK) {
 #pragma unroll
     for (int i = 0; i < (BM * BK) / NT; ++i) {
       const int idx = threadIdx.x + i * NT;
       const int r = idx / BK, c = idx % BK;
       const int gm = m0 + r, gk = k0 + c;
-      As[c][r] = (gm < P.M && gk < P.K) ? Ap[(long long)gm * P.lda + gk] : 0.0;
+      As[c][r] = (gm < P.M && gk < kend) ? Ap[(long long)gm * P.lda + gk] : 0.0;
       const int gn = n0 + r;
-      Bs[c][r] = (gn < P.N && gk < P.K) ? Bp[(long long)gn * P.ldb + gk] : 0.0;
+      Bs[c][r] = (gn < P.N && gk < kend) ? Bp[(long long)gn * P.ldb + gk] : 0.0;
     }
     __syncthreads();
 #pragma unroll
@@ -62,6 +76,12 @@ __global__ void __launch_bounds__(NT) gemm_f64_nt_kernel(GemmGroup g, const doub
     }
     __syncthreads();
   }
+  double* out = Cp;
+  long long ld = P.ldc;
+  if (sk.nsplit > 1) {
+    out = part + sk.part_off[pi] + (long long)split * P.M * P.N;
+    ld = P.N;
+  }
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
     const int gm = m0 + ty + 16 * i;
@@ -69,19 +89,65 @@ __global__ void __launch_bounds__(NT) gemm_f64_nt_kernel(GemmGroup g, const doub
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const int gn = n0 + tx + 16 * j;
-      if (gn < P.N) Cp[(long long)gm * P.ldc + gn] = alpha * acc[i][j];
+      if (gn < P.N) out[(long long)gm * ld + gn] = alpha * acc[i][j];
+    }
+  }
+}
+
+__global__ void splitk_reduce_kernel(GemmGroup g, SplitK sk, const double* __restrict__ part,
+                                     double* __restrict__ C) {
+  for (int pi = 0; pi < g.n; ++pi) {
+    const GemmProblem P = g.p[pi];
+    const long long mn = (long long)P.M * P.N;
+    const double* src = part + sk.part_off[pi];
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < mn;
+         e += (long long)gridDim.x * blockDim.x) {
+      double v = 0.0;
+      for (int s = 0; s < sk.nsplit; ++s) v += src[s * mn + e];
+      C[P.c_off + (e / P.N) * P.ldc + (e % P.N)] = v;
     }
   }
 }
 }  // namespace
 
 cudaError_t launch_gemm_f64(const GemmGroup& g, const double* A, const double* B, double* C,
-                            double alpha, cudaStream_t s) {
+                            double alpha, cudaStream_t s, double* part, long long part_elems) {
   long long tiles = 0;
-  for (int i = 0; i < g.n; ++i)
+  int kmax = 0;
+  for (int i = 0; i < g.n; ++i) {
     tiles += (long long)((g.p[i].M + BM - 1) / BM) * ((g.p[i].N + BN - 1) / BN);
+    kmax = g.p[i].K > kmax ? g.p[i].K : kmax;
+  }
   if (tiles == 0) return cudaSuccess;
-  gemm_f64_nt_kernel<<<(unsigned)tiles, NT, 0, s>>>(g, A, B, C, alpha);
+  // split K when the output tiles cannot fill the GPU (3 resident CTAs on each
+  // of its 152 SMs) and each split still gets several K steps
+  constexpr long long kTarget = 3 * 152;
+  SplitK sk{};
+  sk.nsplit = 1;
+  if (part && tiles < kTarget) {
+    int ns = (int)((kTarget + tiles - 1) / tiles);
+    ns = ns < kmax / (4 * BK) ? ns : kmax / (4 * BK);
+    ns = ns < 64 ? ns : 64;
+    long long need = 0;
+    for (int i = 0; i < g.n; ++i) need += (long long)g.p[i].M * g.p[i].N;
+    while (ns > 1 && need * ns > part_elems) --ns;
+    if (ns > 1) {
+      sk.nsplit = ns;
+      long long off = 0;
+      for (int i = 0; i < g.n; ++i) {
+        sk.part_off[i] = off;
+        off += (long long)g.p[i].M * g.p[i].N * ns;
+      }
+    }
+  }
+  gemm_f64_nt_kernel<<<(unsigned)(tiles * sk.nsplit), NT, 0, s>>>(g, A, B, C, alpha, sk, part);
+  if (sk.nsplit > 1) {
+    long long mn = 0;
+    for (int i = 0; i < g.n; ++i) mn = (long long)g.p[i].M * g.p[i].N > mn ? (long long)g.p[i].M * g.p[i].N : mn;
+    long long gx = (mn + 255) / 256;
+    if (gx > 4096) gx = 4096;
+    splitk_reduce_kernel<<<(unsigned)gx, 256, 0, s>>>(g, sk, part, C);
+  }
   return cudaGetLastError();
 }
 
