@@ -47,7 +47,7 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--precision", default="tf32x3", choices=["f64", "tf32x3", "tf32", "bf16x3"])
-    p.add_argument("--eig", default="f32p", choices=["f64", "f32p"],
+    p.add_argument("--eig", default="f32p", choices=["f64", "f32p", "subspace"],
                    help="f64: FP64 syevd per block; f32p: FP32 syevd + FP64 re-orthonormalised projection")
     p.add_argument("--no-dense", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
@@ -300,7 +300,7 @@ def run_ours(args):
     # the same Z2 path with the FP64 eigen-decomposition, for comparison
     alt = None
     if not args.no_dense:
-        other = "f64" if args.eig == "f32p" else "f32p"
+        other = "f64" if args.eig != "f64" else "f32p"
         ca = CTMRG(ctx, A, w["chi"], basis="hermitian", precision=args.precision, backend="own", eig=other)
         ca.run(args.warmup)
         msa = timed_moves(torch, ca, ctx, args.steps, flush)
@@ -365,14 +365,18 @@ def run_ours(args):
                 "warmup": args.warmup, "ms_per_step": 1e3 * sec / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None,
                 "dtype": ("f64" if args.precision == "f64" else f"{args.precision} GEMM (fp32 accumulate)") +
-                         (" + f64 eig" if args.eig == "f64" else " + f32 eig, f64 projection"),
+                         {"f64": " + f64 eig", "f32p": " + f32 eig, f64 projection",
+                          "subspace": " + subspace eig (f32 Ritz), f64 projection"}[args.eig],
                 "data": "synthetic",
                 "config": {"workload": "real C4v iPEPS d=2 D=6 chi=144 (q=36: 21 even/15 odd), seeded N(0,1), "
                                        "D4-symmetrised, max|A|=1", "D": 6, "chi": 144, "basis": "hermitian",
                            "precision": args.precision,
-                           "eig": ("cuSOLVER Xsyevd FP64 per parity block" if args.eig == "f64" else
-                                   "cuSOLVER Xsyevd FP32 per parity block, FP64 Loewdin re-orthonormalisation "
-                                   "and FP64 projection C = P^T C' P"),
+                           "eig": {"f64": "cuSOLVER Xsyevd FP64 per parity block",
+                                   "f32p": "cuSOLVER Xsyevd FP32 per parity block, FP64 Loewdin "
+                                           "re-orthonormalisation and FP64 projection C = P^T C' P",
+                                   "subspace": "warm-started block subspace iteration per parity block "
+                                               "(tcgen05 products, FP64 Cholesky-QR, Rayleigh-Ritz m=k+24), "
+                                               "FP64 Loewdin re-orthonormalisation and projection"}[args.eig],
                            "l2": "flushed (512 MB write) between timed moves", "parallelism": f"replicas{world}"},
                 "speedup_vs_dense_f64": (value / world) / dense["moves_per_s"] if dense else None,
                 "dense_f64": dense, "z2_other_eig": alt, "abs_dE_vs_oracle_50_moves": dE,

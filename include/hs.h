@@ -85,8 +85,19 @@ typedef enum { HS_BASIS_DENSE = 0, HS_BASIS_HERMITIAN = 1 } hs_basis;
  *   re-orthonormalised (two Loewdin steps, P <- (3/2 I - 1/2 P^T P)-updated)
  *   and the new corner is the FP64 projection C_new = P^T C' P (symmetric,
  *   not diagonal). Meant for the mixed-precision modes, whose C' carries FP32
- *   rounding already. */
-typedef enum { HS_EIG_F64 = 0, HS_EIG_F32_PROJECTED = 1 } hs_eig_mode;
+ *   rounding already.
+ * HS_EIG_SUBSPACE: as HS_EIG_F32_PROJECTED, but the kept vectors come from a
+ *   warm-started block subspace iteration on each parity block (tensor-core
+ *   products H X, FP64 Cholesky-QR, Rayleigh-Ritz of size m = k + 24 with an
+ *   FP32 eigensolver) seeded with the previous move's subspace (kept plus
+ *   oversampled vectors). Converged when every Ritz pair that can be kept
+ *   has residual |H x - theta x| <= tol max|theta| (tol = 1e-6 with FP64
+ *   products, 1e-5 with tensor-core products, above their rounding floor);
+ *   otherwise, on the first move, or when the sector sizes changed, the move
+ *   falls back to HS_EIG_F32_PROJECTED. Kept vectors carry
+ *   a canonical sign (largest entry positive) so that the gauge, and with it
+ *   the warm start, is stationary at the fixed point. */
+typedef enum { HS_EIG_F64 = 0, HS_EIG_F32_PROJECTED = 1, HS_EIG_SUBSPACE = 2 } hs_eig_mode;
 
 /* Which library runs the FP64 block GEMMs (HS_PREC_F64 only). */
 typedef enum { HS_GEMM_OWN = 0, HS_GEMM_CUBLAS = 1 } hs_gemm_backend;
@@ -140,7 +151,13 @@ typedef struct {
   double gap;            /* (lam_cut - lam_next) / lam_max, +inf if nothing discarded */
   double log_norm_C, log_norm_T;
   double gemm_flops;     /* sum over block GEMMs of 2 M N K in this move */
-  int flags;             /* bit 0: gap below 1e-9 (degenerate cut) */
+  int flags;             /* bit 0: gap below 1e-9 (degenerate cut); bit 1: the subspace
+                            eigensolver converged (no fallback); bit 2: it fell back */
+  int subspace_iters;    /* Rayleigh-Ritz rounds of the subspace eigensolver (0 if unused) */
+  int subspace_reason;   /* 0 converged, 1 no warm start, 2 sector sizes changed, 3 subspace too
+                            large, 4 Cholesky or eigensolver failure, 5 not converged, 6 selection at
+                            the edge of the subspace; -1 not used */
+  double subspace_resid; /* largest residual / max|theta| over the candidates in the last round */
 } hs_move_info;
 
 typedef enum { HS_RDM_TWO_SITE = 0, HS_RDM_ENV_ONE_SITE = 1 } hs_rdm_kind;

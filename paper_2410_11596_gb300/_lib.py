@@ -26,7 +26,7 @@ HS_PREC_F64, HS_PREC_TF32X3, HS_PREC_TF32, HS_PREC_BF16X3 = 0, 1, 2, 3
 HS_BASIS_DENSE, HS_BASIS_HERMITIAN = 0, 1
 HS_GEMM_OWN, HS_GEMM_CUBLAS = 0, 1
 HS_RDM_TWO_SITE, HS_RDM_ENV_ONE_SITE = 0, 1
-HS_EIG_F64, HS_EIG_F32_PROJECTED = 0, 1
+HS_EIG_F64, HS_EIG_F32_PROJECTED, HS_EIG_SUBSPACE = 0, 1, 2
 
 
 class HsError(RuntimeError):
@@ -61,7 +61,8 @@ class MoveInfo(ctypes.Structure):
     _fields_ = [("chi_even", c_int), ("chi_odd", c_int), ("n_even", c_int), ("n_odd", c_int),
                 ("lam_max", c_double), ("lam_cut", c_double), ("lam_next", c_double), ("gap", c_double),
                 ("log_norm_C", c_double), ("log_norm_T", c_double), ("gemm_flops", c_double),
-                ("flags", c_int)]
+                ("flags", c_int), ("subspace_iters", c_int), ("subspace_reason", c_int),
+                ("subspace_resid", c_double)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -1,6 +1,7 @@
 // C ABI of libhs (include/hs.h): context, workspace, the C4v CTMRG move of
 // arXiv 2410.11596 (Sec. II.A, Fig. 1(d)) in the Hermitian Z2 basis
 // (Sec. II.B).
+#include <algorithm>
 #include <utility>
 
 #include "hs_ctx.cuh"
@@ -265,13 +266,12 @@ hs_status tc_a_gemm(hs_ctx ctx, hs_precision prec, const Z2Mat& Xsrc, const Z2Ma
   return tc_run(ctx, prec, X, ctx->tc_x_hi, ctx->tc_x_lo, Am, ctx->tc_a_hi, ctx->tc_a_lo, Cm, C);
 }
 
-// FP32-eigenvector projector (HS_EIG_F32_PROJECTED): gather the kept FP32
-// eigenvectors as PT (rows) and P (columns), make them orthonormal in FP64 by
-// two Loewdin steps PT <- (3/2 I - 1/2 PT PT^T) PT, then set the new corner to
-// the FP64 projection C = PT C' PT^T of each block and normalise it.
-hs_status project_f32(hs_ctx ctx, const float* V0f, int n0, const float* V1f, int n1, const int* didx, int chi,
-                      SelectOut* dsel, Sect c, Sect q, Sect cn, const double* C0, const double* C1, hs_env* env,
-                      double* flops) {
+// Canonical sign, FP64 re-orthonormalisation and projection of the kept rows
+// PT (already gathered): the largest entry of each row is made positive, two
+// Loewdin steps PT <- (3/2 I - 1/2 PT PT^T) PT, then the new corner is the
+// FP64 projection C = PT C' PT^T of each block, normalised by its largest entry.
+hs_status finish_projector(hs_ctx ctx, int n0, int n1, SelectOut* dsel, Sect c, Sect q, Sect cn, const double* C0,
+                           const double* C1, hs_env* env, double* flops) {
   cudaStream_t s = ctx->stream;
   const int k[2] = {cn.n[0], cn.n[1]};
   const int n[2] = {n0, n1};
@@ -281,16 +281,12 @@ hs_status project_f32(hs_ctx ctx, const float* V0f, int n0, const float* V1f, in
   HS_TRY(ctx->pt2.ensure(npt * sizeof(double)));
   HS_TRY(ctx->wproj.ensure(npt * sizeof(double)));
   HS_TRY(ctx->gram.ensure(((long long)k[0] * k[0] + (long long)k[1] * k[1] + 1) * sizeof(double)));
+  HS_TRY(ctx->splitk.ensure(kSplitKElems * sizeof(double)));
   double* PT = ctx->pt.d();
   double* PT2 = ctx->pt2.d();
   double* P = ctx->pcol.d();
   double* G = ctx->gram.d();
   double* W = ctx->wproj.d();
-  {
-    PhaseScope ps(ctx, HS_PHASE_SELECT);
-    HS_CUDA(launch_gather_p32(V0f, n0, V1f, n1, didx, chi, dsel, PT, P, s));
-    ctx->launches += 1;
-  }
   const long long ptoff[2] = {0, (long long)k[0] * n[0]};
   const long long goff[2] = {0, (long long)k[0] * k[0]};
   auto group = [&](auto fill) {
@@ -302,13 +298,18 @@ hs_status project_f32(hs_ctx ctx, const float* V0f, int n0, const float* V1f, in
     return g;
   };
   const Z2Mat PTm = mat(fused1(cn), fused2(c, q)), Pm = mat(fused2(c, q), fused1(cn));
+  {
+    PhaseScope ps(ctx, HS_PHASE_SELECT);
+    for (int p = 0; p < 2; ++p) HS_CUDA(launch_row_sign(PT + ptoff[p], k[p], n[p], s));
+    HS_TRY(permute(ctx, PTm, Pm, {1, 2, 0}, PT, P));
+    ctx->launches += 2;
+  }
   PhaseScope ps(ctx, HS_PHASE_GEMM);
   for (int step = 0; step < 2; ++step) {
     // G = PT PT^T
     GemmGroup gg = group([&](int p) {
       return GemmProblem{k[p], k[p], n[p], n[p], n[p], k[p], ptoff[p], ptoff[p], goff[p]};
     });
-    HS_TRY(ctx->splitk.ensure(kSplitKElems * sizeof(double)));
     HS_CUDA(launch_gemm_f64(gg, PT, PT, G, 1.0, s, ctx->splitk.d(), kSplitKElems));
     HS_CUDA(launch_lowdin(G, k[0], k[1], s));
     // PT2 = M PT, i.e. C = M (P)^T with P the column layout
@@ -336,6 +337,194 @@ hs_status project_f32(hs_ctx ctx, const float* V0f, int n0, const float* V1f, in
   HS_CUDA(launch_normalize_max_to(env->C, goff[1] + (long long)k[1] * k[1],
                                   static_cast<unsigned long long*>(ctx->scratch.p) + 2, &dsel->log_norm_C, s));
   ctx->launches += 4;
+  return HS_OK;
+}
+
+// FP32-eigenvector projector (HS_EIG_F32_PROJECTED): gather the kept FP32
+// eigenvectors, then finish_projector.
+hs_status project_f32(hs_ctx ctx, const float* V0f, int n0, const float* V1f, int n1, const int* didx, int chi,
+                      SelectOut* dsel, Sect c, Sect q, Sect cn, const double* C0, const double* C1, hs_env* env,
+                      double* flops) {
+  const long long npt = (long long)cn.n[0] * n0 + (long long)cn.n[1] * n1;
+  HS_TRY(ctx->pcol.ensure(npt * sizeof(double)));
+  {
+    PhaseScope ps(ctx, HS_PHASE_SELECT);
+    HS_CUDA(launch_gather_p32(V0f, n0, V1f, n1, didx, chi, dsel, ctx->pt.d(), ctx->pcol.d(), ctx->stream));
+    ctx->launches += 1;
+  }
+  return finish_projector(ctx, n0, n1, dsel, c, q, cn, C0, C1, env, flops);
+}
+
+// ---- warm-started subspace eigensolver (HS_EIG_SUBSPACE) ----
+
+Z2Mat dense2(long long r, long long c) { return mat(fused1(make_sect((int)r, 0)), fused1(make_sect((int)c, 0))); }
+
+// Orthonormalise the m rows of X (m x n) in FP64: two passes of Cholesky-QR,
+// X <- L^{-1} X with X X^T = L L^T. Non-positive pivots raise *bad (device).
+hs_status cholqr2(hs_ctx ctx, double* X, int m, int n, double* Xc, int* bad) {
+  HS_TRY(ctx->schol.ensure(2 * (size_t)m * m * sizeof(double)));
+  double* G = ctx->schol.d();
+  double* Li = G + (long long)m * m;
+  for (int pass = 0; pass < 2; ++pass) {
+    HS_TRY(gemm(ctx, HS_GEMM_OWN, GemmGroup{1, {GemmProblem{m, m, n, n, n, m, 0, 0, 0}}}, X, X, G));
+    HS_CUDA(launch_chol_inv(G, m, Li, bad, ctx->stream));
+    HS_TRY(permute(ctx, dense2(m, n), dense2(n, m), {1, 0}, X, Xc));
+    HS_TRY(gemm(ctx, HS_GEMM_OWN, GemmGroup{1, {GemmProblem{m, n, m, m, m, n, 0, 0, 0}}}, Li, Xc, X));
+    ctx->launches += 1;
+  }
+  return HS_OK;
+}
+
+// Subspace iteration on both parity blocks H_b (n_b x n_b, FP64 in place in
+// the C' buffer), warm-started from the previous move's kept rows. On success
+// (*done) w[0 .. m0+m1) holds the Ritz values of block 0 then block 1
+// (ascending per block), sxr[b] the matching Ritz vectors as rows, and
+// m_out the subspace sizes; otherwise the caller falls back.
+hs_status subspace_projector(hs_ctx ctx, hs_env* env, int chi, int n0, int n1, double* H0, double* H1, double* w,
+                             int* m_out, bool* done, int* iters, double* flops, int* reason, double* resid) {
+  *done = false;
+  *iters = 0;
+  *resid = 0.0;
+  const int n[2] = {n0, n1};
+  double* H[2] = {H0, H1};
+  *reason = 1;
+  if (!(ctx->ws_valid && ctx->ws_env == env)) return HS_OK;
+  *reason = 2;
+  if (!(ctx->ws_n[0] == n0 && ctx->ws_n[1] == n1)) return HS_OK;
+  constexpr int kOver = 24, kMaxIt = 4;
+  cudaStream_t s = ctx->stream;
+  const bool tc = env->precision != HS_PREC_F64;
+  // residual tolerance relative to max|theta|: above the rounding floor of
+  // the products H X (about 2e-6 with 3-pass TF32 at n ~ 2600)
+  const double kTol = tc ? 1e-5 : 1e-6;
+  const hs_precision prec = env->precision;
+  int m[2];
+  for (int b = 0; b < 2; ++b) {
+    m[b] = n[b] == 0 ? 0 : (ctx->ws_k[b] + kOver < n[b] ? ctx->ws_k[b] + kOver : n[b]);
+    *reason = 3;
+    if (m[b] > max_subspace()) return HS_OK;
+  }
+  int* bad = static_cast<int*>(ctx->info.p) + 2;
+  HS_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), s));
+  HS_TRY(eig32_workspace(ctx, m[0] > m[1] ? m[0] : m[1]));
+  const long long wsoff[2] = {0, (long long)ctx->ws_m[0] * ctx->ws_n[0]};
+  for (int b = 0; b < 2; ++b) {
+    if (m[b] == 0) continue;
+    const size_t mn = (size_t)m[b] * n[b] * sizeof(double);
+    HS_TRY(ctx->sx[b].ensure(mn));
+    HS_TRY(ctx->sz[b].ensure(mn));
+    HS_TRY(ctx->sxc[b].ensure(mn));
+    HS_TRY(ctx->szc[b].ensure(mn));
+    HS_TRY(ctx->sxr[b].ensure(mn));
+    HS_TRY(ctx->szr[b].ensure(mn));
+    HS_TRY(ctx->sbm[b].ensure((size_t)m[b] * m[b] * sizeof(double)));
+    HS_TRY(ctx->sbw[b].ensure((size_t)m[b] * m[b] * sizeof(float)));
+    HS_TRY(ctx->sres[b].ensure((size_t)m[b] * sizeof(double)));
+    const int kb = ctx->ws_m[b] < m[b] ? ctx->ws_m[b] : m[b];
+    if (kb > 0)
+      HS_CUDA(cudaMemcpyAsync(ctx->sx[b].p, ctx->ws_pt.d() + wsoff[b], (size_t)kb * n[b] * sizeof(double),
+                              cudaMemcpyDeviceToDevice, s));
+    HS_CUDA(launch_fill_random_rows(ctx->sx[b].d(), kb, m[b], n[b], 0x5eed0000ull + 2 * (unsigned long long)ctx->ws_moves + b,
+                                    s));
+    HS_TRY(cholqr2(ctx, ctx->sx[b].d(), m[b], n[b], ctx->sxc[b].d(), bad));
+    if (tc) HS_TRY(tc_split(ctx, prec, dense2(n[b], n[b]), dense2(n[b], n[b]), {0, 1}, H[b], ctx->sH_hi[b], ctx->sH_lo[b]));
+  }
+  HS_TRY(ctx->sth.ensure((size_t)(m[0] + m[1] + 2) * sizeof(float)));
+  float* th = static_cast<float*>(ctx->sth.p);
+  std::vector<float> hth(m[0] + m[1]);
+  std::vector<double> hres(m[0] + m[1]);
+  int hbad = 0;
+  for (int it = 0; it < kMaxIt; ++it) {
+    *iters = it + 1;
+    for (int b = 0; b < 2; ++b) {
+      if (m[b] == 0) continue;
+      // Z = X H (H symmetric), Rayleigh matrix B = Z X^T
+      if (tc) {
+        HS_TRY(tc_split(ctx, prec, dense2(m[b], n[b]), dense2(m[b], n[b]), {0, 1}, ctx->sx[b].d(), ctx->sx_hi, ctx->sx_lo));
+        HS_TRY(tc_run(ctx, prec, dense2(m[b], n[b]), ctx->sx_hi, ctx->sx_lo, dense2(n[b], n[b]), ctx->sH_hi[b],
+                      ctx->sH_lo[b], dense2(m[b], n[b]), ctx->sz[b].d()));
+        ctx->phase_flops[HS_PHASE_GEMM_TC] += 2.0 * m[b] * (double)n[b] * n[b];
+      } else {
+        HS_TRY(gemm(ctx, HS_GEMM_OWN, GemmGroup{1, {GemmProblem{m[b], n[b], n[b], n[b], n[b], n[b], 0, 0, 0}}},
+                    ctx->sx[b].d(), H[b], ctx->sz[b].d()));
+        ctx->phase_flops[HS_PHASE_GEMM] += 2.0 * m[b] * (double)n[b] * n[b];
+      }
+      *flops += 2.0 * m[b] * (double)n[b] * n[b];
+      HS_TRY(gemm(ctx, HS_GEMM_OWN, GemmGroup{1, {GemmProblem{m[b], m[b], n[b], n[b], n[b], m[b], 0, 0, 0}}},
+                  ctx->sz[b].d(), ctx->sx[b].d(), ctx->sbm[b].d()));
+      HS_CUDA(launch_cast_f64_f32(ctx->sbm[b].d(), static_cast<float*>(ctx->sbw[b].p), (long long)m[b] * m[b], s));
+      ctx->launches += 1;
+    }
+    {
+      PhaseScope ps(ctx, HS_PHASE_EIG);
+      HS_CUDA(cudaMemsetAsync(ctx->info.p, 0, 2 * sizeof(int), s));
+      HS_TRY(eig_pair_impl(ctx, true, ctx->sbw[0].p, m[0], th, ctx->sbw[1].p, m[1], th + m[0]));
+    }
+    for (int b = 0; b < 2; ++b) {
+      if (m[b] == 0) continue;
+      // Ritz vectors Xr = W^T X and Zr = W^T Z (W column-major = W^T row-major)
+      HS_CUDA(launch_cast_f32_f64(static_cast<float*>(ctx->sbw[b].p), ctx->sbm[b].d(), (long long)m[b] * m[b], s));
+      HS_TRY(permute(ctx, dense2(m[b], n[b]), dense2(n[b], m[b]), {1, 0}, ctx->sx[b].d(), ctx->sxc[b].d()));
+      HS_TRY(permute(ctx, dense2(m[b], n[b]), dense2(n[b], m[b]), {1, 0}, ctx->sz[b].d(), ctx->szc[b].d()));
+      const GemmGroup gr{1, {GemmProblem{m[b], n[b], m[b], m[b], m[b], n[b], 0, 0, 0}}};
+      HS_TRY(gemm(ctx, HS_GEMM_OWN, gr, ctx->sbm[b].d(), ctx->sxc[b].d(), ctx->sxr[b].d()));
+      HS_TRY(gemm(ctx, HS_GEMM_OWN, gr, ctx->sbm[b].d(), ctx->szc[b].d(), ctx->szr[b].d()));
+      HS_CUDA(launch_residual(ctx->szr[b].d(), ctx->sxr[b].d(), th + (b ? m[0] : 0), m[b], n[b], ctx->sres[b].d(), s));
+      ctx->launches += 2;
+    }
+    int hinfo[2];
+    HS_CUDA(cudaMemcpyAsync(hth.data(), th, hth.size() * sizeof(float), cudaMemcpyDeviceToHost, s));
+    for (int b = 0; b < 2; ++b)
+      if (m[b] > 0)
+        HS_CUDA(cudaMemcpyAsync(hres.data() + (b ? m[0] : 0), ctx->sres[b].p, m[b] * sizeof(double),
+                                cudaMemcpyDeviceToHost, s));
+    HS_CUDA(cudaMemcpyAsync(hinfo, ctx->info.p, sizeof hinfo, cudaMemcpyDeviceToHost, s));
+    HS_CUDA(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+    HS_CUDA(cudaStreamSynchronize(s));
+    *reason = 4;
+    if (hbad || hinfo[0] || hinfo[1]) return HS_OK;  // fall back
+    // the states the selection can keep: the chi largest |theta| across both
+    // blocks, plus two more per block; all of them must have converged, and no
+    // block may keep states near the edge of its subspace
+    std::vector<std::pair<double, int>> cand;
+    double tmax = 0.0;
+    for (int i = 0; i < m[0] + m[1]; ++i) {
+      cand.push_back({std::fabs((double)hth[i]), i});
+      tmax = std::max(tmax, std::fabs((double)hth[i]));
+    }
+    std::sort(cand.begin(), cand.end(), [](const auto& x, const auto& y) { return x.first > y.first; });
+    const int keep = std::min(chi, m[0] + m[1]);
+    int kept[2] = {0, 0};
+    bool ok = tmax > 0.0;
+    double worst = 0.0;
+    for (int r = 0; r < (int)cand.size() && r < keep + 4; ++r) {
+      const int i = cand[r].second, b = i >= m[0] ? 1 : 0;
+      if (r < keep) ++kept[b];
+      worst = std::max(worst, tmax > 0.0 ? hres[i] / tmax : 1.0);
+    }
+    *resid = worst;
+    *reason = 5;
+    if (worst > kTol) ok = false;
+    for (int b = 0; b < 2; ++b)
+      if (m[b] < n[b] && kept[b] > m[b] - kOver / 2) {
+        ok = false;
+        *reason = 6;
+      }
+    if (ok) {
+      *reason = 0;
+      for (int b = 0; b < 2; ++b) m_out[b] = m[b];
+      HS_CUDA(launch_cast_f32_f64(th, w, m[0] + m[1], s));
+      *done = true;
+      return HS_OK;
+    }
+    if (it + 1 == kMaxIt) return HS_OK;  // fall back
+    for (int b = 0; b < 2; ++b)
+      if (m[b] > 0) {
+        HS_CUDA(cudaMemcpyAsync(ctx->sx[b].p, ctx->szr[b].p, (size_t)m[b] * n[b] * sizeof(double),
+                                cudaMemcpyDeviceToDevice, s));
+        HS_TRY(cholqr2(ctx, ctx->sx[b].d(), m[b], n[b], ctx->sxc[b].d(), bad));
+      }
+  }
   return HS_OK;
 }
 
@@ -562,6 +751,7 @@ hs_status hs_ctmrg_init(hs_ctx ctx, const hs_z2_tensor* a, int chi_max, hs_preci
   env->gemm_backend = backend;
   env->moves = 0;
   env->eig_mode = HS_EIG_F64;
+  ctx->ws_valid = false;  // no warm start for the subspace eigensolver yet
   HS_CUDA(launch_ctmrg_init(a->data, D, herm, env->C, env->T, ctx->stream));
   // normalise like every later move
   const Z2Mat Cm = mat(fused1(qs), fused1(qs)), Tm = mat(fused2(qs, qs), fused1(qs));
@@ -677,11 +867,29 @@ hs_status hs_ctmrg_move(hs_ctx ctx, const hs_z2_tensor* a, hs_env* env, int chi,
   double* w0 = ctx->w.d();
   double* w1 = w0 + n0;
   HS_CUDA(cudaMemsetAsync(ctx->info.p, 0, 2 * sizeof(int), s));
-  const bool f32eig = env->eig_mode == HS_EIG_F32_PROJECTED;
-  if (env->eig_mode != HS_EIG_F64 && !f32eig) return fail(HS_ERR_INVALID_ARG, "unknown eig mode");
+  if (env->eig_mode != HS_EIG_F64 && env->eig_mode != HS_EIG_F32_PROJECTED && env->eig_mode != HS_EIG_SUBSPACE)
+    return fail(HS_ERR_INVALID_ARG, "unknown eig mode");
+  // subspace eigensolver first (when a warm start exists); its Ritz values
+  // replace the spectra, ns0/ns1 are the sizes passed to the selection
+  bool sub_done = false;
+  int sub_iters = 0, ns0 = n0, ns1 = n1, sub_reason = -1;
+  double sub_resid = 0.0;
+  if (env->eig_mode == HS_EIG_SUBSPACE) {
+    int msub[2] = {0, 0};
+    HS_TRY(subspace_projector(ctx, env, chi, n0, n1, V0, V1, w0, msub, &sub_done, &sub_iters, &flops, &sub_reason,
+                              &sub_resid));
+    if (sub_done) {
+      ns0 = msub[0];
+      ns1 = msub[1];
+      w1 = w0 + ns0;
+    }
+  }
+  const bool f32eig = env->eig_mode == HS_EIG_F32_PROJECTED || (env->eig_mode == HS_EIG_SUBSPACE && !sub_done);
   float* V0f = nullptr;
   float* V1f = nullptr;
-  if (!f32eig) {
+  if (sub_done) {
+    // Ritz pairs ready
+  } else if (!f32eig) {
     PhaseScope ps(ctx, HS_PHASE_EIG);
     HS_TRY(eig_pair(ctx, false, V0, n0, w0, V1, n1, w1));
   } else {
@@ -702,7 +910,7 @@ hs_status hs_ctmrg_move(hs_ctx ctx, const hs_z2_tensor* a, hs_env* env, int chi,
   int* didx = static_cast<int*>(ctx->idx.p);
   {
     PhaseScope ps(ctx, HS_PHASE_SELECT);
-    HS_CUDA(launch_select(w0, n0, w1, n1, chi, didx, ctx->lam.d(), dsel, s));
+    HS_CUDA(launch_select(w0, ns0, w1, ns1, chi, didx, ctx->lam.d(), dsel, s));
     ctx->launches += 1;
   }
   HS_CUDA(cudaMemcpyAsync(ctx->h_sel, dsel, sizeof(SelectOut), cudaMemcpyDeviceToHost, s));
@@ -723,12 +931,57 @@ hs_status hs_ctmrg_move(hs_ctx ctx, const hs_z2_tensor* a, hs_env* env, int chi,
   const Z2Mat Zm = mat(fused2(cn, c), fused2(q, q));
   const Z2Mat Zp = mat(fused2(cn, q), fused2(c, q));
   const Z2Mat Tn = mat(fused2(cn, q), fused1(cn));
-  if (!f32eig) {
+  if (sub_done) {
+    const long long npt = (long long)cn.n[0] * n0 + (long long)cn.n[1] * n1;
+    HS_TRY(ctx->pcol.ensure(npt * sizeof(double)));
+    {
+      PhaseScope ps(ctx, HS_PHASE_SELECT);
+      HS_CUDA(launch_gather_rows(ctx->sxr[0].d(), n0, ctx->sxr[1].d(), n1, didx, chi, dsel, ctx->pt.d(),
+                                 ctx->pcol.d(), s));
+      ctx->launches += 1;
+    }
+    HS_TRY(finish_projector(ctx, n0, n1, dsel, c, q, cn, V0, V1, env, &flops));
+  } else if (!f32eig) {
     PhaseScope ps(ctx, HS_PHASE_SELECT);
     HS_CUDA(launch_gather_pt(V0, n0, V1, n1, didx, chi, dsel, ctx->pt.d(), s));
     ctx->launches += 1;
   } else {
     HS_TRY(project_f32(ctx, V0f, n0, V1f, n1, didx, chi, dsel, c, q, cn, V0, V1, env, &flops));
+  }
+  if (env->eig_mode == HS_EIG_SUBSPACE) {
+    // the next move starts from the whole subspace of each block: the Ritz
+    // vectors of this move, or after a fallback the m largest-|lambda| FP32
+    // eigenvectors, m = kept + 24 (at most the block size)
+    int mnext[2];
+    for (int b = 0; b < 2; ++b) {
+      const int nb = b ? n1 : n0;
+      mnext[b] = cn.n[b] + 24 < nb ? cn.n[b] + 24 : nb;
+      if (sub_done) mnext[b] = b ? ns1 : ns0;
+    }
+    const long long nws = (long long)mnext[0] * n0 + (long long)mnext[1] * n1;
+    HS_TRY(ctx->ws_pt.ensure((nws + 1) * sizeof(double)));
+    HS_TRY(ctx->sres[0].ensure(((size_t)mnext[0] + mnext[1] + 1) * sizeof(double)));
+    double* dst[2] = {ctx->ws_pt.d(), ctx->ws_pt.d() + (long long)mnext[0] * n0};
+    for (int b = 0; b < 2; ++b) {
+      const int nb = b ? n1 : n0;
+      if (mnext[b] == 0) continue;
+      if (sub_done) {
+        HS_CUDA(cudaMemcpyAsync(dst[b], ctx->sxr[b].p, (size_t)mnext[b] * nb * sizeof(double),
+                                cudaMemcpyDeviceToDevice, s));
+      } else if (f32eig) {
+        const float* wb = static_cast<float*>(ctx->w32.p) + (b ? n0 : 0);
+        HS_CUDA(launch_top_rows(wb, b ? V1f : V0f, nb, mnext[b], static_cast<int*>(ctx->sres[0].p), dst[b], s));
+      }
+    }
+    ctx->ws_env = env;
+    ctx->ws_valid = sub_done || f32eig;
+    ctx->ws_k[0] = cn.n[0];
+    ctx->ws_k[1] = cn.n[1];
+    ctx->ws_m[0] = mnext[0];
+    ctx->ws_m[1] = mnext[1];
+    ctx->ws_n[0] = n0;
+    ctx->ws_n[1] = n1;
+    ctx->ws_moves += 1;
   }
   GemmGroup g4 = make_z2_gemm(Pp, Tcr, Y), g5 = make_z2_gemm(Yp, Am, Zm), g6 = make_z2_gemm(Zp, PT, Tn);
   flops += gemm_flops(g4) + gemm_flops(g5) + gemm_flops(g6);
@@ -769,7 +1022,7 @@ hs_status hs_ctmrg_move(hs_ctx ctx, const hs_z2_tensor* a, hs_env* env, int chi,
   }
 
   // C <- diag(lambda)/max|lambda|, T <- T/max|T|
-  if (!f32eig) {
+  if (!f32eig && !sub_done) {
     PhaseScope ps(ctx, HS_PHASE_SELECT);
     HS_CUDA(launch_diag_corner(ctx->lam.d(), cn.n[0], cn.n[1], dsel, env->C, s));
     ctx->launches += 1;
@@ -810,7 +1063,11 @@ hs_status hs_ctmrg_move(hs_ctx ctx, const hs_z2_tensor* a, hs_env* env, int chi,
     info->log_norm_C = env->log_norm_C;
     info->log_norm_T = env->log_norm_T;
     info->gemm_flops = flops;
-    info->flags = (discarded && info->gap < 1e-9) ? 1 : 0;
+    info->flags = ((discarded && info->gap < 1e-9) ? 1 : 0) |
+                  (env->eig_mode == HS_EIG_SUBSPACE ? (sub_done ? 2 : 4) : 0);
+    info->subspace_iters = sub_iters;
+    info->subspace_reason = sub_reason;
+    info->subspace_resid = sub_resid;
   }
   return HS_OK;
 }

@@ -112,6 +112,14 @@ struct hs_ctx_s {
   hs::DBuf hb[16];
   // split-K partial sums of the FP64 GEMM
   hs::DBuf splitk;
+  // subspace eigensolver: warm start (previous kept rows, per block) and
+  // per-block iteration buffers
+  const void* ws_env = nullptr;
+  bool ws_valid = false;
+  int ws_k[2] = {0, 0}, ws_n[2] = {0, 0}, ws_m[2] = {0, 0};  // kept counts, block sizes, stored rows
+  long long ws_moves = 0;
+  hs::DBuf ws_pt, sx[2], sz[2], sxc[2], szc[2], sxr[2], szr[2], sbm[2], sbw[2], sres[2], sth, sH_hi[2],
+      sH_lo[2], sx_hi, sx_lo, schol;
   // profiling: events between phases, harvested after the move's last sync
   bool prof = false;
   std::vector<cudaEvent_t> events;

@@ -260,6 +260,19 @@ cudaError_t launch_normalize_max_to(double* x, long long n, unsigned long long* 
 // (n0 x n0 then n1 x n1) into *out.
 cudaError_t launch_block_trace(const double* x, int n0, int n1, double* out, cudaStream_t s);
 
+// Warm-started subspace eigensolver kernels (k_subspace.cu).
+cudaError_t launch_fill_random_rows(double* X, int r0, int m, int n, unsigned long long seed, cudaStream_t s);
+cudaError_t launch_chol_inv(const double* G, int m, double* Linv, int* status, cudaStream_t s);
+cudaError_t launch_residual(const double* Zr, const double* Xr, const float* theta, int m, int n, double* res,
+                            cudaStream_t s);
+cudaError_t launch_row_sign(double* X, int m, int n, cudaStream_t s);
+cudaError_t launch_gather_rows(const double* X0, int n0, const double* X1, int n1, const int* idx, int chi,
+                               const SelectOut* sel, double* PT, double* P, cudaStream_t s);
+int max_subspace();
+// X (m x n rows, FP64) = the m eigenvectors of largest |eigenvalue| of one
+// FP32 eigen-decomposition (ascending w, column-major V); idx is scratch (m ints).
+cudaError_t launch_top_rows(const float* w, const float* V, int n, int m, int* idx, double* X, cudaStream_t s);
+
 // Dense views of an FSO environment (rotated back to the plain combined basis).
 cudaError_t launch_env_to_dense(const double* C, const double* T, int D, int c0, int c1,
                                 bool hermitian, double* Cd, double* Td, cudaStream_t s);

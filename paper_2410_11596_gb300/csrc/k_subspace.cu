@@ -1,0 +1,230 @@
+// Kernels of the warm-started subspace eigensolver for the CTMRG projector
+// (the truncation of Sec. II.A needs only the chi eigenpairs of largest
+// modulus of each parity block of the enlarged corner, not all of them).
+#include <cmath>
+
+#include "hs_internal.cuh"
+
+namespace hs {
+
+namespace {
+
+unsigned grid_for(long long n) {
+  long long g = (n + 255) / 256;
+  if (g > 4096) g = 4096;
+  if (g < 1) g = 1;
+  return (unsigned)g;
+}
+
+// Counter-based hash (splitmix64 finaliser) -> uniform in (-1, 1).
+__device__ __forceinline__ double hash_uniform(unsigned long long x) {
+  x += 0x9E3779B97F4A7C15ull;
+  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+  x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+  x ^= x >> 31;
+  return (double)(x >> 11) * (2.0 / 9007199254740992.0) - 1.0;
+}
+
+// rows [r0, m) of X (m x n, row-major) get seeded pseudo-random entries
+__global__ void fill_random_rows_kernel(double* __restrict__ X, int r0, int m, int n, unsigned long long seed) {
+  const long long total = (long long)(m - r0) * n;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x)
+    X[(long long)r0 * n + e] = hash_uniform(seed * 0x100000001B3ull + (unsigned long long)e);
+}
+
+// In-place Cholesky G = L L^T (lower) of an m x m SPD matrix and L^{-1}, in
+// FP64, by one CTA in shared memory (m <= kMaxSub). On a non-positive pivot
+// the status word is set and Linv is left unspecified.
+constexpr int kMaxSub = 160;
+
+__global__ void __launch_bounds__(256) chol_inv_kernel(const double* __restrict__ G, int m,
+                                                       double* __restrict__ Linv, int* __restrict__ status) {
+  extern __shared__ double sh[];
+  double* L = sh;  // m x m, lower triangle used
+  for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+    const int r = e / m, c = e % m;
+    L[e] = r >= c ? 0.5 * (G[r * m + c] + G[c * m + r]) : 0.0;
+  }
+  __syncthreads();
+  __shared__ int bad;
+  if (threadIdx.x == 0) bad = 0;
+  __syncthreads();
+  for (int j = 0; j < m; ++j) {
+    if (threadIdx.x == 0) {
+      const double d = L[j * m + j];
+      if (!(d > 0.0)) bad = 1;
+      L[j * m + j] = d > 0.0 ? sqrt(d) : 1.0;
+    }
+    __syncthreads();
+    const double piv = L[j * m + j];
+    for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x) L[i * m + j] /= piv;
+    __syncthreads();
+    // trailing update of the lower triangle
+    const int rem = m - j - 1;
+    for (int e = threadIdx.x; e < rem * rem; e += blockDim.x) {
+      const int r = j + 1 + e / rem, c = j + 1 + e % rem;
+      if (c <= r) L[r * m + c] -= L[r * m + j] * L[c * m + j];
+    }
+    __syncthreads();
+  }
+  // L^{-1} by forward substitution, one column of the identity per thread,
+  // built directly in Linv (each thread reads and writes only its column)
+  for (int c = threadIdx.x; c < m; c += blockDim.x) {
+    for (int r = 0; r < m; ++r) {
+      double v = r == c ? 1.0 : 0.0;
+      for (int k = c; k < r; ++k) v -= L[r * m + k] * Linv[k * m + c];
+      Linv[r * m + c] = r < c ? 0.0 : v / L[r * m + r];
+    }
+  }
+  if (threadIdx.x == 0 && bad) *status = 1;
+}
+
+// res[i] = || Zr_i - theta_i Xr_i || for the m rows (theta from FP32 values).
+__global__ void residual_kernel(const double* __restrict__ Zr, const double* __restrict__ Xr,
+                                const float* __restrict__ theta, int m, int n, double* __restrict__ res) {
+  const int i = blockIdx.x;
+  if (i >= m) return;
+  const double t = (double)theta[i];
+  double s = 0.0;
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    const double v = Zr[(long long)i * n + j] - t * Xr[(long long)i * n + j];
+    s += v * v;
+  }
+  __shared__ double red[256];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) res[i] = sqrt(red[0]);
+}
+
+// Canonical sign: the entry of largest modulus of each row is made positive.
+__global__ void row_sign_kernel(double* __restrict__ X, int m, int n) {
+  const int i = blockIdx.x;
+  if (i >= m) return;
+  double best = -1.0, val = 0.0;
+  int bj = 0;
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    const double v = X[(long long)i * n + j];
+    if (fabs(v) > best || (fabs(v) == best && j < bj)) {
+      best = fabs(v);
+      val = v;
+      bj = j;
+    }
+  }
+  __shared__ double sb[256], sv[256];
+  __shared__ int sj[256];
+  sb[threadIdx.x] = best;
+  sv[threadIdx.x] = val;
+  sj[threadIdx.x] = bj;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      const double b2 = sb[threadIdx.x + o];
+      const int j2 = sj[threadIdx.x + o];
+      if (b2 > sb[threadIdx.x] || (b2 == sb[threadIdx.x] && j2 < sj[threadIdx.x])) {
+        sb[threadIdx.x] = b2;
+        sv[threadIdx.x] = sv[threadIdx.x + o];
+        sj[threadIdx.x] = j2;
+      }
+    }
+    __syncthreads();
+  }
+  const double sgn = sv[0] < 0.0 ? -1.0 : 1.0;
+  if (sgn < 0.0)
+    for (int j = threadIdx.x; j < n; j += blockDim.x) X[(long long)i * n + j] = -X[(long long)i * n + j];
+}
+
+// PT block b row j = X_b row idx[b][j]; P block b column j likewise.
+__global__ void gather_rows_kernel(const double* __restrict__ X0, int n0, const double* __restrict__ X1, int n1,
+                                   const int* __restrict__ idx, int chi, const SelectOut* __restrict__ sel,
+                                   double* __restrict__ PT, double* __restrict__ P) {
+  const int b = blockIdx.y, j = blockIdx.x;
+  const int cb = sel->chi_new[b];
+  if (j >= cb) return;
+  const int n = b ? n1 : n0;
+  const double* src = (b ? X1 : X0) + (long long)idx[b * chi + j] * n;
+  const long long off = b ? (long long)sel->chi_new[0] * n0 : 0;
+  double* prow = PT + off + (long long)j * n;
+  double* pcol = P + off + j;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double v = src[i];
+    prow[i] = v;
+    pcol[(long long)i * cb] = v;
+  }
+}
+
+// Indices of the m eigenvalues of largest modulus of one ascending spectrum
+// (both ends of the array), in descending modulus.
+__global__ void top_abs_kernel(const float* __restrict__ w, int n, int m, int* __restrict__ idx) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  int lo = 0, hi = n - 1;
+  for (int j = 0; j < m && lo <= hi; ++j) {
+    if (fabsf(w[lo]) > fabsf(w[hi])) idx[j] = lo++;
+    else idx[j] = hi--;
+  }
+}
+
+// row j of X (FP64, m x n) = column idx[j] of V (FP32, column-major n x n)
+__global__ void rows_from_columns_kernel(const float* __restrict__ V, int n, const int* __restrict__ idx,
+                                         double* __restrict__ X) {
+  const int j = blockIdx.x;
+  const float* src = V + (long long)idx[j] * n;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) X[(long long)j * n + i] = (double)src[i];
+}
+
+}  // namespace
+
+cudaError_t launch_top_rows(const float* w, const float* V, int n, int m, int* idx, double* X, cudaStream_t s) {
+  if (m <= 0) return cudaSuccess;
+  top_abs_kernel<<<1, 32, 0, s>>>(w, n, m, idx);
+  rows_from_columns_kernel<<<m, 256, 0, s>>>(V, n, idx, X);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fill_random_rows(double* X, int r0, int m, int n, unsigned long long seed, cudaStream_t s) {
+  if (r0 >= m) return cudaSuccess;
+  fill_random_rows_kernel<<<grid_for((long long)(m - r0) * n), 256, 0, s>>>(X, r0, m, n, seed);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_chol_inv(const double* G, int m, double* Linv, int* status, cudaStream_t s) {
+  if (m <= 0 || m > kMaxSub) return cudaErrorInvalidValue;
+  const size_t smem = (size_t)m * m * sizeof(double);
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(chol_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         kMaxSub * kMaxSub * (int)sizeof(double));
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  chol_inv_kernel<<<1, 256, smem, s>>>(G, m, Linv, status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_residual(const double* Zr, const double* Xr, const float* theta, int m, int n, double* res,
+                            cudaStream_t s) {
+  if (m <= 0) return cudaSuccess;
+  residual_kernel<<<m, 256, 0, s>>>(Zr, Xr, theta, m, n, res);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_row_sign(double* X, int m, int n, cudaStream_t s) {
+  if (m <= 0) return cudaSuccess;
+  row_sign_kernel<<<m, 256, 0, s>>>(X, m, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather_rows(const double* X0, int n0, const double* X1, int n1, const int* idx, int chi,
+                               const SelectOut* sel, double* PT, double* P, cudaStream_t s) {
+  dim3 grid((unsigned)chi, 2);
+  gather_rows_kernel<<<grid, 256, 0, s>>>(X0, n0, X1, n1, idx, chi, sel, PT, P);
+  return cudaGetLastError();
+}
+
+int max_subspace() { return kMaxSub; }
+
+}  // namespace hs
