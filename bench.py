@@ -47,7 +47,7 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--precision", default="tf32x3", choices=["f64", "tf32x3", "tf32", "bf16x3"])
-    p.add_argument("--eig", default="f32p", choices=["f64", "f32p", "subspace"],
+    p.add_argument("--eig", default="subspace", choices=["f64", "f32p", "subspace"],
                    help="f64: FP64 syevd per block; f32p: FP32 syevd + FP64 re-orthonormalised projection")
     p.add_argument("--no-dense", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
@@ -274,14 +274,24 @@ def run_ours(args):
         sec = float(t.item())
     value = world * args.steps / sec
 
-    # |dE| against the oracle after 50 moves
+    # |dE| against the oracle after 50 moves, then the same path at steady
+    # state (moves 51-60, every warm start in place)
     dE = None
+    steady = None
     if not args.no_check:
         done = args.warmup + args.steps
         if done < 50:
             c.run(50 - done)
         ref = golden_energy(50)
         dE = abs(c.energy(h) - ref) if ref is not None else None
+        L.hs_profile_enable(ctx.handle, True)
+        mss = timed_moves(torch, c, ctx, args.steps, flush)
+        ps = L.hs_profile_read(ctx.handle)
+        L.hs_profile_enable(ctx.handle, False)
+        steady = {"moves": "51-%d" % (50 + args.steps), "moves_per_s": args.steps / (np.sum(mss) / 1e3),
+                  "ms_per_step": float(np.mean(mss)),
+                  "time_split_ms": {k: v / args.steps for k, v in ps["phase_ms"].items()},
+                  "subspace_converged": int(sum(1 for i in c.infos[-args.steps:] if i.get("flags", 0) & 2))}
 
     # dense FP64 path (cuBLAS DGEMM + cuSOLVER on the full chi*D^2 corner)
     dense = None
@@ -358,7 +368,8 @@ def run_ours(args):
     roof = {"bound": bound, "kernel": kname, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": (achieved / peak) if achieved else None, "traffic": traffic, "peak_source": psrc,
             "share_of_move": k_ms / total_ms,
-            "note": "the move is dominated by cuSOLVER's per-block eigen-decomposition (time_split_ms.eig)"}
+            "note": "per-phase device time of the move is in time_split_ms (timed moves) and "
+                    "steady_state.time_split_ms (moves 51-60)"}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "moves/s", "n_gpus": world, "steps": args.steps,
@@ -380,6 +391,7 @@ def run_ours(args):
                            "l2": "flushed (512 MB write) between timed moves", "parallelism": f"replicas{world}"},
                 "speedup_vs_dense_f64": (value / world) / dense["moves_per_s"] if dense else None,
                 "dense_f64": dense, "z2_other_eig": alt, "abs_dE_vs_oracle_50_moves": dE,
+                "steady_state": steady,
                 "time_split_ms": {k: v / args.steps for k, v in prof["phase_ms"].items()},
                 "wall_s_timed_region": t_wall,
                 "roofline": roof, "cpu_baseline": cpu,

@@ -266,6 +266,9 @@ hs_status tc_a_gemm(hs_ctx ctx, hs_precision prec, const Z2Mat& Xsrc, const Z2Ma
   return tc_run(ctx, prec, X, ctx->tc_x_hi, ctx->tc_x_lo, Am, ctx->tc_a_hi, ctx->tc_a_lo, Cm, C);
 }
 
+// A dense r x c matrix as a one-block Z2 layout.
+Z2Mat dense2(long long r, long long c) { return mat(fused1(make_sect((int)r, 0)), fused1(make_sect((int)c, 0))); }
+
 // Canonical sign, FP64 re-orthonormalisation and projection of the kept rows
 // PT (already gathered): the largest entry of each row is made positive, two
 // Loewdin steps PT <- (3/2 I - 1/2 PT PT^T) PT, then the new corner is the
@@ -323,17 +326,35 @@ hs_status finish_projector(hs_ctx ctx, int n0, int n1, SelectOut* dsel, Sect c, 
     HS_CUDA(cudaMemcpyAsync(PT, PT2, npt * sizeof(double), cudaMemcpyDeviceToDevice, s));
     ctx->launches += 3;
   }
-  // W = PT C' (C' symmetric), C_new = W PT^T, block by block into env->C
+  // W = PT C' (C' symmetric), C_new = W PT^T, block by block into env->C.
+  // With tensor-core precisions W runs on tcgen05 from the split C' blocks.
   GemmGroup gw = group([&](int p) {
     return GemmProblem{k[p], n[p], n[p], n[p], n[p], n[p], ptoff[p], (long long)(Cp[p] - C0), ptoff[p]};
   });
-  HS_CUDA(launch_gemm_f64(gw, PT, C0, W, 1.0, s, ctx->splitk.d(), kSplitKElems));
+  const hs_precision prec = env->precision;
+  if (prec == HS_PREC_F64) {
+    HS_CUDA(launch_gemm_f64(gw, PT, C0, W, 1.0, s, ctx->splitk.d(), kSplitKElems));
+  } else {
+    for (int p = 0; p < 2; ++p) {
+      if (k[p] == 0 || n[p] == 0) continue;
+      if (!ctx->sH_fresh || ctx->sH_n[p] != n[p]) {
+        HS_TRY(tc_split(ctx, prec, dense2(n[p], n[p]), dense2(n[p], n[p]), {0, 1}, Cp[p], ctx->sH_hi[p],
+                        ctx->sH_lo[p]));
+        ctx->sH_n[p] = n[p];
+      }
+      HS_TRY(tc_split(ctx, prec, dense2(k[p], n[p]), dense2(k[p], n[p]), {0, 1}, PT + ptoff[p], ctx->sx_hi,
+                      ctx->sx_lo));
+      HS_TRY(tc_run(ctx, prec, dense2(k[p], n[p]), ctx->sx_hi, ctx->sx_lo, dense2(n[p], n[p]), ctx->sH_hi[p],
+                    ctx->sH_lo[p], dense2(k[p], n[p]), W + ptoff[p]));
+      ctx->phase_flops[HS_PHASE_GEMM_TC] += 2.0 * k[p] * (double)n[p] * n[p];
+    }
+  }
   GemmGroup gc = group([&](int p) {
     return GemmProblem{k[p], k[p], n[p], n[p], n[p], k[p], ptoff[p], ptoff[p], goff[p]};
   });
   HS_CUDA(launch_gemm_f64(gc, W, PT, env->C, 1.0, s, ctx->splitk.d(), kSplitKElems));
   *flops += gemm_flops(gw) + gemm_flops(gc);
-  ctx->phase_flops[HS_PHASE_GEMM] += gemm_flops(gw) + gemm_flops(gc);
+  ctx->phase_flops[HS_PHASE_GEMM] += (prec == HS_PREC_F64 ? gemm_flops(gw) : 0.0) + gemm_flops(gc);
   HS_CUDA(launch_normalize_max_to(env->C, goff[1] + (long long)k[1] * k[1],
                                   static_cast<unsigned long long*>(ctx->scratch.p) + 2, &dsel->log_norm_C, s));
   ctx->launches += 4;
@@ -357,7 +378,6 @@ hs_status project_f32(hs_ctx ctx, const float* V0f, int n0, const float* V1f, in
 
 // ---- warm-started subspace eigensolver (HS_EIG_SUBSPACE) ----
 
-Z2Mat dense2(long long r, long long c) { return mat(fused1(make_sect((int)r, 0)), fused1(make_sect((int)c, 0))); }
 
 // Orthonormalise the m rows of X (m x n) in FP64: two passes of Cholesky-QR,
 // X <- L^{-1} X with X X^T = L L^T. Non-positive pivots raise *bad (device).
@@ -427,8 +447,12 @@ hs_status subspace_projector(hs_ctx ctx, hs_env* env, int chi, int n0, int n1, d
     HS_CUDA(launch_fill_random_rows(ctx->sx[b].d(), kb, m[b], n[b], 0x5eed0000ull + 2 * (unsigned long long)ctx->ws_moves + b,
                                     s));
     HS_TRY(cholqr2(ctx, ctx->sx[b].d(), m[b], n[b], ctx->sxc[b].d(), bad));
-    if (tc) HS_TRY(tc_split(ctx, prec, dense2(n[b], n[b]), dense2(n[b], n[b]), {0, 1}, H[b], ctx->sH_hi[b], ctx->sH_lo[b]));
+    if (tc) {
+      HS_TRY(tc_split(ctx, prec, dense2(n[b], n[b]), dense2(n[b], n[b]), {0, 1}, H[b], ctx->sH_hi[b], ctx->sH_lo[b]));
+      ctx->sH_n[b] = n[b];
+    }
   }
+  if (tc) ctx->sH_fresh = true;
   HS_TRY(ctx->sth.ensure((size_t)(m[0] + m[1] + 2) * sizeof(float)));
   float* th = static_cast<float*>(ctx->sth.p);
   std::vector<float> hth(m[0] + m[1]);
@@ -809,6 +833,7 @@ hs_status hs_ctmrg_move(hs_ctx ctx, const hs_z2_tensor* a, hs_env* env, int chi,
   cudaStream_t s = ctx->stream;
   const hs_gemm_backend be = env->gemm_backend;
   const bool tc = env->precision != HS_PREC_F64;
+  ctx->sH_fresh = false;
   if (tc && (ctx->tc_a_src != a->data || ctx->tc_a_prec != (int)env->precision))
     return fail(HS_ERR_INVALID_ARG, "the double layer changed since hs_ctmrg_init (tensor-core copy is stale)");
   const Sect q = make_sect(env->q_even, env->q_odd);

@@ -118,6 +118,8 @@ struct hs_ctx_s {
   bool ws_valid = false;
   int ws_k[2] = {0, 0}, ws_n[2] = {0, 0}, ws_m[2] = {0, 0};  // kept counts, block sizes, stored rows
   long long ws_moves = 0;
+  bool sH_fresh = false;  // sH_hi/lo hold the split blocks of this move's C'
+  int sH_n[2] = {0, 0};
   hs::DBuf ws_pt, sx[2], sz[2], sxc[2], szc[2], sxr[2], szr[2], sbm[2], sbw[2], sres[2], sth, sH_hi[2],
       sH_lo[2], sx_hi, sx_lo, schol;
   // profiling: events between phases, harvested after the move's last sync
