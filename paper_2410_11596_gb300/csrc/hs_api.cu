@@ -251,8 +251,9 @@ hs_status tc_run(hs_ctx ctx, hs_precision prec, const Z2Mat& A, const DBuf& ahi,
     t.c = C + z2_block_off(Cm, p);
     ++n;
   }
+  HS_TRY(ctx->splitk.ensure(kSplitKElems * sizeof(double)));
   PhaseScope ps(ctx, HS_PHASE_GEMM_TC);
-  HS_CUDA(launch_gemm_tc(prec, pr, n, static_cast<int*>(ctx->tc_err.p), ctx->stream));
+  HS_CUDA(launch_gemm_tc(prec, pr, n, static_cast<int*>(ctx->tc_err.p), ctx->stream, ctx->splitk.d(), kSplitKElems));
   if (n > 0) ctx->launches += 1;
   return HS_OK;
 }
@@ -395,6 +396,36 @@ hs_status cholqr2(hs_ctx ctx, double* X, int m, int n, double* Xc, int* bad) {
   return HS_OK;
 }
 
+// C[M x N] = A[M x K] B[N x K]^T for dense FP64 row-major operands: on the
+// tensor cores (operands split into sx / sy) in the TF32/BF16 precisions,
+// with the FP64 kernel otherwise.
+hs_status dense_gemm_any(hs_ctx ctx, hs_precision prec, int M, int N, int K, const double* A, const double* B,
+                         double* C) {
+  if (prec == HS_PREC_F64)
+    return gemm(ctx, HS_GEMM_OWN, GemmGroup{1, {GemmProblem{M, N, K, K, K, N, 0, 0, 0}}}, A, B, C);
+  HS_TRY(tc_split(ctx, prec, dense2(M, K), dense2(M, K), {0, 1}, A, ctx->sx_hi, ctx->sx_lo));
+  HS_TRY(tc_split(ctx, prec, dense2(N, K), dense2(N, K), {0, 1}, B, ctx->sy_hi, ctx->sy_lo));
+  HS_TRY(tc_run(ctx, prec, dense2(M, K), ctx->sx_hi, ctx->sx_lo, dense2(N, K), ctx->sy_hi, ctx->sy_lo,
+                dense2(M, N), C));
+  ctx->phase_flops[HS_PHASE_GEMM_TC] += 2.0 * M * (double)N * K;
+  return HS_OK;
+}
+
+// Loewdin orthonormalisation of the m rows of X (n long), for rows already
+// close to orthonormal: X <- (3/2 I - 1/2 X X^T) X, `steps` times.
+hs_status lowdin_rows(hs_ctx ctx, hs_precision prec, double* X, int m, int n, double* Xc, int steps) {
+  HS_TRY(ctx->schol.ensure(2 * (size_t)m * m * sizeof(double)));
+  double* G = ctx->schol.d();
+  for (int st = 0; st < steps; ++st) {
+    HS_TRY(dense_gemm_any(ctx, prec, m, m, n, X, X, G));
+    HS_CUDA(launch_lowdin(G, m, 0, ctx->stream));
+    HS_TRY(permute(ctx, dense2(m, n), dense2(n, m), {1, 0}, X, Xc));
+    HS_TRY(dense_gemm_any(ctx, prec, m, n, m, G, Xc, X));
+    ctx->launches += 1;
+  }
+  return HS_OK;
+}
+
 // Subspace iteration on both parity blocks H_b (n_b x n_b, FP64 in place in
 // the C' buffer), warm-started from the previous move's kept rows. On success
 // (*done) w[0 .. m0+m1) holds the Ritz values of block 0 then block 1
@@ -446,7 +477,12 @@ hs_status subspace_projector(hs_ctx ctx, hs_env* env, int chi, int n0, int n1, d
                               cudaMemcpyDeviceToDevice, s));
     HS_CUDA(launch_fill_random_rows(ctx->sx[b].d(), kb, m[b], n[b], 0x5eed0000ull + 2 * (unsigned long long)ctx->ws_moves + b,
                                     s));
-    HS_TRY(cholqr2(ctx, ctx->sx[b].d(), m[b], n[b], ctx->sxc[b].d(), bad));
+    if (kb == m[b]) {
+      // the previous move's Ritz / eigen-vectors: orthonormal up to FP32 rounding
+      HS_TRY(lowdin_rows(ctx, prec, ctx->sx[b].d(), m[b], n[b], ctx->sxc[b].d(), tc ? 1 : 2));
+    } else {
+      HS_TRY(cholqr2(ctx, ctx->sx[b].d(), m[b], n[b], ctx->sxc[b].d(), bad));
+    }
     if (tc) {
       HS_TRY(tc_split(ctx, prec, dense2(n[b], n[b]), dense2(n[b], n[b]), {0, 1}, H[b], ctx->sH_hi[b], ctx->sH_lo[b]));
       ctx->sH_n[b] = n[b];
@@ -474,8 +510,7 @@ hs_status subspace_projector(hs_ctx ctx, hs_env* env, int chi, int n0, int n1, d
         ctx->phase_flops[HS_PHASE_GEMM] += 2.0 * m[b] * (double)n[b] * n[b];
       }
       *flops += 2.0 * m[b] * (double)n[b] * n[b];
-      HS_TRY(gemm(ctx, HS_GEMM_OWN, GemmGroup{1, {GemmProblem{m[b], m[b], n[b], n[b], n[b], m[b], 0, 0, 0}}},
-                  ctx->sz[b].d(), ctx->sx[b].d(), ctx->sbm[b].d()));
+      HS_TRY(dense_gemm_any(ctx, prec, m[b], m[b], n[b], ctx->sz[b].d(), ctx->sx[b].d(), ctx->sbm[b].d()));
       HS_CUDA(launch_cast_f64_f32(ctx->sbm[b].d(), static_cast<float*>(ctx->sbw[b].p), (long long)m[b] * m[b], s));
       ctx->launches += 1;
     }
@@ -490,9 +525,8 @@ hs_status subspace_projector(hs_ctx ctx, hs_env* env, int chi, int n0, int n1, d
       HS_CUDA(launch_cast_f32_f64(static_cast<float*>(ctx->sbw[b].p), ctx->sbm[b].d(), (long long)m[b] * m[b], s));
       HS_TRY(permute(ctx, dense2(m[b], n[b]), dense2(n[b], m[b]), {1, 0}, ctx->sx[b].d(), ctx->sxc[b].d()));
       HS_TRY(permute(ctx, dense2(m[b], n[b]), dense2(n[b], m[b]), {1, 0}, ctx->sz[b].d(), ctx->szc[b].d()));
-      const GemmGroup gr{1, {GemmProblem{m[b], n[b], m[b], m[b], m[b], n[b], 0, 0, 0}}};
-      HS_TRY(gemm(ctx, HS_GEMM_OWN, gr, ctx->sbm[b].d(), ctx->sxc[b].d(), ctx->sxr[b].d()));
-      HS_TRY(gemm(ctx, HS_GEMM_OWN, gr, ctx->sbm[b].d(), ctx->szc[b].d(), ctx->szr[b].d()));
+      HS_TRY(dense_gemm_any(ctx, prec, m[b], n[b], m[b], ctx->sbm[b].d(), ctx->sxc[b].d(), ctx->sxr[b].d()));
+      HS_TRY(dense_gemm_any(ctx, prec, m[b], n[b], m[b], ctx->sbm[b].d(), ctx->szc[b].d(), ctx->szr[b].d()));
       HS_CUDA(launch_residual(ctx->szr[b].d(), ctx->sxr[b].d(), th + (b ? m[0] : 0), m[b], n[b], ctx->sres[b].d(), s));
       ctx->launches += 2;
     }
@@ -544,9 +578,12 @@ hs_status subspace_projector(hs_ctx ctx, hs_env* env, int chi, int n0, int n1, d
     if (it + 1 == kMaxIt) return HS_OK;  // fall back
     for (int b = 0; b < 2; ++b)
       if (m[b] > 0) {
+        // power step on the Ritz basis: rows of Zr = theta_i x_i + residual are
+        // nearly orthogonal; normalise them and orthonormalise (Loewdin)
         HS_CUDA(cudaMemcpyAsync(ctx->sx[b].p, ctx->szr[b].p, (size_t)m[b] * n[b] * sizeof(double),
                                 cudaMemcpyDeviceToDevice, s));
-        HS_TRY(cholqr2(ctx, ctx->sx[b].d(), m[b], n[b], ctx->sxc[b].d(), bad));
+        HS_CUDA(launch_row_normalize(ctx->sx[b].d(), m[b], n[b], s));
+        HS_TRY(lowdin_rows(ctx, prec, ctx->sx[b].d(), m[b], n[b], ctx->sxc[b].d(), 2));
       }
   }
   return HS_OK;
@@ -629,8 +666,14 @@ hs_status hs_destroy(hs_ctx ctx) {
   for (DBuf* b : bufs) b->release();
   for (DBuf& b : ctx->r) b.release();
   for (DBuf& b : ctx->hb) b.release();
-  DBuf* more[] = {&ctx->c32,  &ctx->w32,   &ctx->pcol,         &ctx->pt2,
-                  &ctx->gram, &ctx->wproj, &ctx->solver32_dev, &ctx->splitk};
+  DBuf* more[] = {&ctx->c32,  &ctx->w32,   &ctx->pcol,         &ctx->pt2,   &ctx->gram,
+                  &ctx->wproj, &ctx->solver32_dev, &ctx->splitk, &ctx->ws_pt, &ctx->sth,
+                  &ctx->sx_hi, &ctx->sx_lo, &ctx->sy_hi, &ctx->sy_lo, &ctx->schol};
+  for (int b = 0; b < 2; ++b) {
+    DBuf* per[] = {&ctx->sx[b], &ctx->sz[b], &ctx->sxc[b], &ctx->szc[b], &ctx->sxr[b], &ctx->szr[b],
+                   &ctx->sbm[b], &ctx->sbw[b], &ctx->sres[b], &ctx->sH_hi[b], &ctx->sH_lo[b]};
+    for (DBuf* x : per) x->release();
+  }
   for (DBuf* b : more) b->release();
   for (cudaEvent_t e : ctx->events) cudaEventDestroy(e);
   if (ctx->h_sel) cudaFreeHost(ctx->h_sel);

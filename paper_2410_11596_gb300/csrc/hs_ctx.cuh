@@ -121,7 +121,7 @@ struct hs_ctx_s {
   bool sH_fresh = false;  // sH_hi/lo hold the split blocks of this move's C'
   int sH_n[2] = {0, 0};
   hs::DBuf ws_pt, sx[2], sz[2], sxc[2], szc[2], sxr[2], szr[2], sbm[2], sbw[2], sres[2], sth, sH_hi[2],
-      sH_lo[2], sx_hi, sx_lo, schol;
+      sH_lo[2], sx_hi, sx_lo, sy_hi, sy_lo, schol;
   // profiling: events between phases, harvested after the move's last sync
   bool prof = false;
   std::vector<cudaEvent_t> events;

@@ -200,7 +200,10 @@ struct TcProblem {
 
 // precision: HS_PREC_TF32X3, HS_PREC_TF32 or HS_PREC_BF16X3. err receives a
 // non-zero code if a bounded wait inside the kernel gave up.
-cudaError_t launch_gemm_tc(int precision, const TcProblem* probs, int nprob, int* err, cudaStream_t s);
+// part/part_elems: optional FP64 workspace for split-K partials (used when a
+// problem's output tiles cannot fill the GPU); nullptr disables splitting.
+cudaError_t launch_gemm_tc(int precision, const TcProblem* probs, int nprob, int* err, cudaStream_t s,
+                           double* part = nullptr, long long part_elems = 0);
 // part/part_elems: optional workspace for split-K partial sums (used when the
 // output tiles alone cannot fill the GPU); nullptr disables splitting.
 cudaError_t launch_gemm_f64(const GemmGroup& g, const double* A, const double* B, double* C,
@@ -269,6 +272,7 @@ cudaError_t launch_row_sign(double* X, int m, int n, cudaStream_t s);
 cudaError_t launch_gather_rows(const double* X0, int n0, const double* X1, int n1, const int* idx, int chi,
                                const SelectOut* sel, double* PT, double* P, cudaStream_t s);
 int max_subspace();
+cudaError_t launch_row_normalize(double* X, int m, int n, cudaStream_t s);
 // X (m x n rows, FP64) = the m eigenvectors of largest |eigenvalue| of one
 // FP32 eigen-decomposition (ascending w, column-major V); idx is scratch (m ints).
 cudaError_t launch_top_rows(const float* w, const float* V, int n, int m, int* idx, double* X, cudaStream_t s);

@@ -37,19 +37,24 @@ constexpr int TILE_BYTES = BM * ROW_BYTES;  // BN == BM
 constexpr long long WAIT_LIMIT = 20000000;  // try_wait rounds before giving up (seconds)
 
 struct Maps {
-  CUtensorMap a[2][2];  // [problem][hi, lo]
+  CUtensorMap a[2][2];  // [operand pair][hi, lo]
   CUtensorMap b[2][2];
 };
 
+// One launch unit: a K range [k0, k0 + Kp) of an operand pair (map); with
+// split-K every range writes its own FP64 partial (c, row stride ldc) and a
+// reduction kernel sums them.
+constexpr int kMaxUnits = 16;
 struct Prob {
   int M, N, Kp, ldc;
+  int k0, map;
   double* c;
   int tile_start, tiles_n;
 };
 
 struct Group {
   int n;
-  Prob p[2];
+  Prob p[kMaxUnits];
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -185,8 +190,10 @@ __global__ void __launch_bounds__(NT, 1) gemm_tc_kernel(const __grid_constant__ 
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   int t = blockIdx.x;
-  const int pi = (g.n > 1 && t >= g.p[1].tile_start) ? 1 : 0;
+  int pi = 0;
+  while (pi + 1 < g.n && t >= g.p[pi + 1].tile_start) ++pi;
   const Prob P = g.p[pi];
+  const int mi = P.map;
   t -= P.tile_start;
   const int m0 = (t / P.tiles_n) * BM, n0 = (t % P.tiles_n) * BN;
   const int ktiles = P.Kp / K::K_PER_TILE;
@@ -214,10 +221,10 @@ __global__ void __launch_bounds__(NT, 1) gemm_tc_kernel(const __grid_constant__ 
 
   if (warp == 0 && lane == 0) {
     // ---- TMA producer ----
-    const CUtensorMap* mA0 = &maps.a[pi][0];
-    const CUtensorMap* mA1 = &maps.a[pi][1];
-    const CUtensorMap* mB0 = &maps.b[pi][0];
-    const CUtensorMap* mB1 = &maps.b[pi][1];
+    const CUtensorMap* mA0 = &maps.a[mi][0];
+    const CUtensorMap* mA1 = &maps.a[mi][1];
+    const CUtensorMap* mB0 = &maps.b[mi][0];
+    const CUtensorMap* mB1 = &maps.b[mi][1];
     int issued = 0;
     for (int kt = 0; kt < ktiles; ++kt) {
       const int s = kt % K::STAGES, n = kt / K::STAGES;
@@ -226,7 +233,7 @@ __global__ void __launch_bounds__(NT, 1) gemm_tc_kernel(const __grid_constant__ 
       const uint32_t fb = smem_u32(&full[s]);
       mbar_expect_tx(fb, K::STAGE_BYTES);
       const uint32_t st = smem_u32(smem + s * K::STAGE_BYTES);
-      const int kc = kt * K::K_PER_TILE;
+      const int kc = P.k0 + kt * K::K_PER_TILE;
       tma_load_2d(st, mA0, kc, m0, fb);
       tma_load_2d(st + TILE_BYTES, mB0, kc, n0, fb);
       if (NPASS == 3) {
@@ -277,6 +284,13 @@ __global__ void __launch_bounds__(NT, 1) gemm_tc_kernel(const __grid_constant__ 
   __syncwarp();
   ok = __all_sync(0xffffffffu, ok);
   fence_after();
+  if (ok && ktiles == 0) {
+    // empty K range: the accumulator was never written, the product is zero
+    const int row = m0 + warp * 32 + lane;
+    if (row < P.M)
+      for (int c = 0; c < BN && n0 + c < P.N; ++c) P.c[(long long)row * P.ldc + n0 + c] = 0.0;
+    ok = false;
+  }
   if (ok) {
     const int row = m0 + warp * 32 + lane;
     double* crow = P.c + (long long)row * P.ldc;
@@ -337,8 +351,19 @@ bool make_map(CUtensorMap* m, const void* base, int rows, int Kp, int eb) {
   return r == CUDA_SUCCESS;
 }
 
+__global__ void tc_splitk_reduce_kernel(const double* __restrict__ part, int nsplit, int M, int N,
+                                        double* __restrict__ C, int ldc) {
+  const long long mn = (long long)M * N;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < mn;
+       e += (long long)gridDim.x * blockDim.x) {
+    double v = 0.0;
+    for (int s = 0; s < nsplit; ++s) v += part[s * mn + e];
+    C[(e / N) * ldc + (e % N)] = v;
+  }
+}
+
 template <int NPASS, int EB>
-cudaError_t run(const TcProblem* probs, int nprob, int* err, cudaStream_t s) {
+cudaError_t run(const TcProblem* probs, int nprob, int* err, cudaStream_t s, double* part, long long part_elems) {
   using K = Cfg<NPASS, EB>;
   static bool attr = false;
   if (!attr) {
@@ -350,44 +375,90 @@ cudaError_t run(const TcProblem* probs, int nprob, int* err, cudaStream_t s) {
   Maps maps;
   memset(&maps, 0, sizeof maps);
   Group g{};
-  int tiles = 0;
+  int tiles = 0, nmap = 0;
+  struct Red {
+    const double* part;
+    int nsplit, M, N, ldc;
+    double* c;
+  } red[2];
+  int nred = 0;
+  long long part_used = 0;
   for (int i = 0; i < nprob; ++i) {
     const TcProblem& p = probs[i];
     if (p.M <= 0 || p.N <= 0) continue;
     if (p.Kp <= 0 || p.Kp % K::K_PER_TILE != 0) return cudaErrorInvalidValue;
-    const int j = g.n;
+    const int j = nmap++;
     if (!make_map(&maps.a[j][0], p.a_hi, p.M, p.Kp, EB) || !make_map(&maps.b[j][0], p.b_hi, p.N, p.Kp, EB))
       return cudaErrorInvalidValue;
     if (NPASS == 3 &&
         (!make_map(&maps.a[j][1], p.a_lo, p.M, p.Kp, EB) || !make_map(&maps.b[j][1], p.b_lo, p.N, p.Kp, EB)))
       return cudaErrorInvalidValue;
-    Prob& q = g.p[j];
-    q.M = p.M;
-    q.N = p.N;
-    q.Kp = p.Kp;
-    q.ldc = p.ldc;
-    q.c = p.c;
-    q.tiles_n = (p.N + BN - 1) / BN;
-    q.tile_start = tiles;
-    tiles += ((p.M + BM - 1) / BM) * q.tiles_n;
-    ++g.n;
+    const int tiles_n = (p.N + BN - 1) / BN;
+    const int ptiles = ((p.M + BM - 1) / BM) * tiles_n;
+    const int ktiles = p.Kp / K::K_PER_TILE;
+    // split K when this problem's tiles cannot fill the 152 SMs and each
+    // split keeps at least 4 K steps; partials go to `part`
+    int ns = 1;
+    if (part && ptiles < 152) {
+      ns = (152 + ptiles - 1) / ptiles;
+      ns = ns < ktiles / 4 ? ns : ktiles / 4;
+      ns = ns < 8 ? ns : 8;
+      const long long need = (long long)ns * p.M * p.N;
+      if (ns < 2 || part_used + need > part_elems || g.n + ns > kMaxUnits) ns = 1;
+    }
+    const int kper = (ktiles + ns - 1) / ns;
+    ns = (ktiles + kper - 1) / kper;  // no empty K range
+    for (int sidx = 0; sidx < ns; ++sidx) {
+      const int kb = sidx * kper, ke = (kb + kper < ktiles) ? kb + kper : ktiles;
+      if (g.n >= kMaxUnits) return cudaErrorInvalidValue;
+      Prob& q = g.p[g.n++];
+      q.M = p.M;
+      q.N = p.N;
+      q.k0 = kb * K::K_PER_TILE;
+      q.Kp = (ke > kb ? ke - kb : 0) * K::K_PER_TILE;
+      q.map = j;
+      if (ns > 1) {
+        q.c = part + part_used + (long long)sidx * p.M * p.N;
+        q.ldc = p.N;
+      } else {
+        q.c = p.c;
+        q.ldc = p.ldc;
+      }
+      q.tiles_n = tiles_n;
+      q.tile_start = tiles;
+      tiles += ptiles;
+    }
+    if (ns > 1) {
+      red[nred++] = {part + part_used, ns, p.M, p.N, p.ldc, p.c};
+      part_used += (long long)ns * p.M * p.N;
+    }
   }
   if (tiles == 0) return cudaSuccess;
   gemm_tc_kernel<NPASS, EB><<<tiles, NT, K::SMEM, s>>>(maps, g, err);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  for (int r = 0; r < nred; ++r) {
+    const long long mn = (long long)red[r].M * red[r].N;
+    long long gx = (mn + 255) / 256;
+    if (gx > 4096) gx = 4096;
+    tc_splitk_reduce_kernel<<<(unsigned)gx, 256, 0, s>>>(red[r].part, red[r].nsplit, red[r].M, red[r].N, red[r].c,
+                                                        red[r].ldc);
+  }
   return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t launch_gemm_tc(int precision, const TcProblem* probs, int nprob, int* err, cudaStream_t s) {
+cudaError_t launch_gemm_tc(int precision, const TcProblem* probs, int nprob, int* err, cudaStream_t s,
+                           double* part, long long part_elems) {
   if (nprob > 2) return cudaErrorInvalidValue;
   switch (precision) {
     case HS_PREC_TF32X3:
-      return run<3, 4>(probs, nprob, err, s);
+      return run<3, 4>(probs, nprob, err, s, part, part_elems);
     case HS_PREC_TF32:
-      return run<1, 4>(probs, nprob, err, s);
+      return run<1, 4>(probs, nprob, err, s, part, part_elems);
     case HS_PREC_BF16X3:
-      return run<3, 2>(probs, nprob, err, s);
+      return run<3, 2>(probs, nprob, err, s, part, part_elems);
     default:
       return cudaErrorInvalidValue;
   }

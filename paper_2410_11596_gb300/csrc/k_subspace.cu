@@ -176,7 +176,34 @@ __global__ void rows_from_columns_kernel(const float* __restrict__ V, int n, con
   for (int i = threadIdx.x; i < n; i += blockDim.x) X[(long long)j * n + i] = (double)src[i];
 }
 
+// Each row of X (m x n) scaled to unit Euclidean norm (zero rows untouched).
+__global__ void row_normalize_kernel(double* __restrict__ X, int m, int n) {
+  const int i = blockIdx.x;
+  if (i >= m) return;
+  double s = 0.0;
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    const double v = X[(long long)i * n + j];
+    s += v * v;
+  }
+  __shared__ double red[256];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  const double nrm = sqrt(red[0]);
+  if (nrm > 0.0)
+    for (int j = threadIdx.x; j < n; j += blockDim.x) X[(long long)i * n + j] /= nrm;
+}
+
 }  // namespace
+
+cudaError_t launch_row_normalize(double* X, int m, int n, cudaStream_t s) {
+  if (m <= 0) return cudaSuccess;
+  row_normalize_kernel<<<m, 256, 0, s>>>(X, m, n);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_top_rows(const float* w, const float* V, int n, int m, int* idx, double* X, cudaStream_t s) {
   if (m <= 0) return cudaSuccess;
