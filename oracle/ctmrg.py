@@ -10,26 +10,37 @@ all four corners C[chi, chi] and all four edges T[chi, D^2, chi] are equal.
 Index conventions (all tensors here are plain dense arrays):
   a[u, l, d, r]          double layer, legs up/left/down/right (double_layer()).
   T[alpha, x, beta]      edge: alpha and beta are the two boundary bonds, x the
-                         bond into the bulk. As the left edge, alpha points down,
-                         beta up and x right. C4v makes T[alpha, x, beta] =
-                         T[beta, x, alpha].
-  C[beta, gamma]         corner, symmetric.
+                         bond into the bulk. Boundary tensors are oriented
+                         clockwise around the lattice: alpha is the incoming
+                         end, beta the outgoing one. As the left edge, alpha
+                         points down, beta up and x right; as the top edge,
+                         alpha is the left end and x points down.
+  C[beta, gamma]         corner, incoming leg beta, outgoing leg gamma.
   C'[(alpha,d),(eps,r)]  enlarged upper-left corner: left edge T, corner C, top
-                         edge T and the bulk a; rows are the lower open pair
-                         (boundary bond alpha, bulk leg d), columns the right
-                         open pair (eps, r).
+                         edge T and the bulk a; rows are the incoming pair
+                         (boundary bond alpha, bulk leg d), columns the
+                         outgoing pair (eps, r).
+For real tensors C4v makes T[alpha, x, beta] = T[beta, x, alpha] and C
+symmetric, and the orientation plays no role.
 
 Readings of points the paper leaves open (each is a convention; the
 gauge-invariant results do not depend on it):
   * initial environment: traced boundary. The open outer legs of the first
     corner and edge are closed with the bra-ket identity delta(i, ibar), which
     is an even state of S;
-  * truncation: keep the chi eigenvalues of largest modulus (ties: lower index
-    in the eigensolver's ascending order). If chi*D^2 <= chi all states are kept;
-  * complex tensors: C' is complex symmetric (C'^T = C'), so its eigenvectors
-    are normalised with the bilinear form (z^T z = 1) instead of the Hermitian
-    one; the projector P = Z_kept has P^T P = I, keeps C and T symmetric, and
-    inserts the spectral projector P P^T on every boundary bond;
+  * truncation, real tensors: keep the chi eigenvalues of largest modulus of
+    the symmetric C' (ties: lower index in the eigensolver's ascending order);
+    P = V_kept, C_new = diag(lambda_kept), T_new = P^T (T a) P. If
+    chi*D^2 <= chi all states are kept;
+  * truncation, complex tensors: C' is complex symmetric but its eigenvalues
+    come in complex-conjugate pairs of equal modulus, so "keep the chi largest"
+    is not well defined for them. The move uses the singular value
+    decomposition C' = U S V^dagger instead: keep the chi largest singular
+    values, insert U_k U_k^dagger on every boundary bond, i.e. renormalise each
+    boundary tensor as U_k^dagger (incoming leg) ... U_k (outgoing leg):
+    C_new = U_k^dagger C' U_k, T_new = U_k^dagger (T a) U_k. This keeps the
+    orientation and reduces to the real rule for real tensors (singular values
+    |lambda|, U = V up to signs);
   * normalisation: C and T are divided by their largest modulus after every
     move.
 """
@@ -69,19 +80,6 @@ def enlarged_corner(C: np.ndarray, T: np.ndarray, a: np.ndarray) -> np.ndarray:
     return X3.transpose(0, 2, 1, 3).reshape(chi * q, chi * q)
 
 
-def complex_symmetric_eig(Cp: np.ndarray):
-    """Cp = Z diag(lam) Z^T with Z^T Z = I for a complex symmetric Cp.
-
-    Eigenvectors of a complex symmetric matrix with distinct eigenvalues are
-    orthogonal under the bilinear form z^T z'; each is scaled to z^T z = 1.
-    Then Z_k Z_k^T is the spectral projector on the kept eigenvectors, and the
-    untruncated case inserts exactly Z Z^T = I on every bond.
-    """
-    lam, Z = np.linalg.eig(Cp)
-    Z = Z / np.sqrt(np.einsum("ij,ij->j", Z, Z))[None, :]
-    return lam, Z
-
-
 @dataclass
 class MoveInfo:
     """Per-move record: eigenvalues kept and the relative gap at the cut."""
@@ -95,24 +93,22 @@ class MoveInfo:
 
 
 def truncate(Cp: np.ndarray, chi: int):
-    """Projector and new corner spectrum from the enlarged corner (Sec. II.A).
+    """Projector and kept spectrum of the enlarged corner (Sec. II.A).
 
     Real: eigh of the symmetric C' (symmetric by C4v; its symmetric part is
-    taken explicitly), keep the chi eigenvalues of largest modulus, P = V[:, kept].
-    Complex: C' is complex symmetric; its eigenvectors scaled to z^T z = 1
-    (complex_symmetric_eig) give P = Z[:, kept], so that P^T P = I and the
-    corner stays symmetric, C_new = P^T C' P = diag(lam_kept).
-    Returns (P, lam_kept, info) with lam_kept in descending modulus.
+    taken explicitly), keep the chi eigenvalues of largest modulus,
+    P = V[:, kept]; returns those eigenvalues in descending modulus.
+    Complex: SVD C' = U S V^dagger, keep the chi largest singular values,
+    P = U[:, :chi]; returns those singular values.
+    Returns (P, kept, info).
     """
     n = Cp.shape[0]
     keep = min(chi, n)
     if np.iscomplexobj(Cp):
-        w, Z = complex_symmetric_eig(0.5 * (Cp + Cp.T))
-        order = np.argsort(-np.abs(w), kind="stable")
-        lam = w[order]
-        P = Z[:, order[:keep]]
-        kept = lam[:keep]
-        mags = np.abs(lam)
+        U, sv, _ = np.linalg.svd(Cp)
+        P = U[:, :keep]
+        kept = sv[:keep]
+        mags = sv
     else:
         w, V = np.linalg.eigh(0.5 * (Cp + Cp.T))
         order = np.argsort(-np.abs(w), kind="stable")
@@ -127,14 +123,15 @@ def truncate(Cp: np.ndarray, chi: int):
 
 
 def renormalize_edge(T: np.ndarray, a: np.ndarray, P: np.ndarray) -> np.ndarray:
-    """T_new[a', r, b'] = sum P[(alpha,d),a'] T[alpha,x,beta] a[u,x,d,r] P[(beta,u),b'].
+    """T_new[a', r, b'] = sum conj(P[(alpha,d),a']) T[alpha,x,beta] a[u,x,d,r] P[(beta,u),b'].
 
-    Contracted as Y = P^T T (over alpha), Z = Y a (over d and x), T_new = Z P
-    (over beta and u).
+    In the left-edge frame (alpha, d) is the incoming pair and (beta, u) the
+    outgoing one. Contracted as Y = P^dagger T (over alpha), Z = Y a (over d
+    and x), T_new = Z P (over beta and u). For real P this is P^T (T a) P.
     """
     chi, q = T.shape[0], T.shape[1]
     P3 = P.reshape(chi, q, P.shape[1])                   # [alpha, d, a']
-    Y = np.tensordot(P3, T, axes=([0], [0]))             # [d, a', x, beta]
+    Y = np.tensordot(P3.conj(), T, axes=([0], [0]))      # [d, a', x, beta]
     Z = np.tensordot(Y, a, axes=([0, 2], [2, 1]))        # [a', beta, u, r]
     Tn = np.tensordot(Z, P3, axes=([1, 2], [0, 1]))      # [a', r, b']
     return Tn
@@ -144,7 +141,10 @@ def move(C: np.ndarray, T: np.ndarray, a: np.ndarray, chi: int):
     """One C4v CTMRG move: enlarge, truncate, renormalise, normalise."""
     Cp = enlarged_corner(C, T, a)
     P, lam, info = truncate(Cp, chi)
-    Cn = np.diag(lam)
+    if np.iscomplexobj(Cp):
+        Cn = P.conj().T @ Cp @ P
+    else:
+        Cn = np.diag(lam)
     Tn = renormalize_edge(T, a, P)
     nC = np.abs(Cn).max()
     nT = np.abs(Tn).max()

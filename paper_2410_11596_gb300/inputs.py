@@ -103,6 +103,8 @@ WORKLOADS = {
     2: dict(d=2, D=4, chi=64, moves=50, complex_valued=False),
     3: dict(d=2, D=6, chi=144, moves=50, complex_valued=False),
     5: dict(d=2, D=5, chi=100, moves=40, complex_valued=True),
+    # small complex case for parity tests (the oracle finishes it in seconds)
+    6: dict(d=2, D=3, chi=27, moves=30, complex_valued=True),
 }
 
 

@@ -106,3 +106,58 @@ def test_corner_spectrum_gauge_invariant():
     r = ctmrg.run(dl.double_layer(A), 8, 6)
     Q, _ = np.linalg.qr(np.random.default_rng(2).standard_normal((8, 8)))
     np.testing.assert_allclose(ob.corner_spectrum(Q.T @ r.C @ Q), ob.corner_spectrum(r.C), atol=1e-14)
+
+
+def test_correlation_length_decoupled_chains_closed_form():
+    """a[u,l,d,r] = M[u,d] M[l,r]: every row is an independent 1D chain with
+    transfer matrix M and the boundary is an exact product state (chi = 1), so the
+    column transfer matrix T-a-T is (v1^T M v1) M and xi = -1/ln|mu2/mu1|."""
+    rng = np.random.default_rng(5)
+    for q in (4, 9):  # q = D^2: the traced-boundary init pairs bra and ket
+        X = rng.standard_normal((q, q))
+        M = X @ X.T + 0.5 * np.eye(q)
+        a = np.einsum("ud,lr->uldr", M, M)
+        r = ctmrg.run(a, 1, 30)
+        mu = np.sort(np.abs(np.linalg.eigvalsh(M)))[::-1]
+        assert ob.correlation_length(r.T, a) == pytest.approx(-1.0 / np.log(mu[1] / mu[0]), rel=1e-12)
+
+
+def test_correlation_length_ising_approaches_onsager():
+    """High-temperature 2D Ising (K = beta = 0.2 < K_c): the axis correlation length is
+    1/(ln coth K - 2K). At finite chi CTMRG underestimates it and the error shrinks with chi."""
+    beta = 0.2
+    exact = 1.0 / (np.log(1.0 / np.tanh(beta)) - 2.0 * beta)
+    a = dl.double_layer(inputs.ising_ipeps(beta))
+    errs = []
+    for chi in (8, 16):
+        r = ctmrg.run(a, chi, 120)
+        errs.append(exact - ob.correlation_length(r.T, a))
+    assert 0.0 < errs[1] < errs[0] < 0.02 * exact
+
+
+def test_complex_rule_reduces_to_real_rule():
+    """The SVD truncation used for complex tensors, fed a real tensor as complex,
+    keeps the same states as the eigenvalue rule (singular values = |lambda|,
+    U = V up to signs): same energy and corner spectrum after truncating moves."""
+    A = inputs.random_ipeps(2, 3, seed=7)
+    a = dl.double_layer(A)
+    rr = ctmrg.run(a, 12, 20)
+    rc = ctmrg.run(a.astype(complex), 12, 20)
+    assert rr.min_gap > 1e-6
+    h = inputs.heisenberg_bond()
+    er = ob.bond_energy(ob.two_site_rdm(rr.C, rr.T, A), h)
+    ec = ob.bond_energy(ob.two_site_rdm(rc.C, rc.T, A.astype(complex)), h)
+    assert ec == pytest.approx(er, abs=1e-13)
+    np.testing.assert_allclose(ob.corner_spectrum(rc.C), ob.corner_spectrum(rr.C), atol=1e-12)
+
+
+@pytest.mark.parametrize("D,chi", [(2, 8), (3, 12)])
+def test_complex_truncation_preserves_hermiticity(D, chi):
+    """Complex A (Sec. II.C): the truncated environment keeps the bra-ket
+    symmetry, so rho is Hermitian and S_err (Eq. (4)) vanishes to rounding."""
+    A = inputs.random_ipeps(2, D, seed=11, complex_valued=True)
+    a = dl.double_layer(A)
+    r = ctmrg.run(a, chi, 30)
+    assert r.min_gap > 1e-6
+    assert ob.hermiticity_error(ob.two_site_rdm(r.C, r.T, A)) < 1e-11
+    assert ob.symmetry_error(ob.one_site_environment(r.C, r.T), D) < 1e-11
