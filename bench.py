@@ -52,6 +52,8 @@ def parse():
     p.add_argument("--no-dense", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-check", action="store_true", help="skip the |dE| run to 50 moves")
+    p.add_argument("--no-complex", action="store_true",
+                   help="skip the complex-tensor line (graded path, D=5 chi=100, 40 moves)")
     p.add_argument("--profile-region", action="store_true",
                    help="profiling runs only: W warm-up moves, then K moves inside cudaProfilerStart/Stop "
                         "(for ncu --profile-from-start off); prints a short JSON line, no bench line")
@@ -349,6 +351,29 @@ def run_ours(args):
         alt = {"eig": other, "moves_per_s": args.steps / (np.sum(msa) / 1e3), "ms_per_step": float(np.mean(msa))}
         del ca
 
+    # complex tensors (Sec. II.C): the graded path on the complex workload, FP64,
+    # every move timed; |dE| against the stored oracle energy after 40 moves
+    cplx = None
+    if not args.no_complex and rank == 0:
+        from paper_2410_11596_gb300 import inputs as _inp
+        w5 = _inp.WORKLOADS[5]
+        cc = CTMRG(ctx, _inp.workload_tensor(5), w5["chi"], precision="f64", eig="f64")
+        msc = timed_moves(torch, cc, ctx, w5["moves"], flush)
+        ref5 = None
+        try:
+            with open(os.path.join(ROOT, "tests", "golden", "ctmrg_w5.json")) as f:
+                ref5 = json.load(f)["checkpoints"][str(w5["moves"])]["energy"]
+        except Exception:
+            pass
+        e5 = cc.energy(h)
+        cplx = {"workload": "complex C4v iPEPS d=2 D=5 chi=100 (q=25: 15 even/10 odd), seeded, Re/Im ~ N(0,1/2)",
+                "path": "graded real storage (Re of even-total, Im of odd-total entries), sign rule of Eq. (2)-(3), "
+                        "FP64 block GEMMs, SVD truncation via FP64 eig of M M^T (n = 2500)",
+                "moves": w5["moves"], "moves_per_s_all": w5["moves"] / (np.sum(msc) / 1e3),
+                "moves_per_s_last10": 10 / (np.sum(msc[-10:]) / 1e3),
+                "abs_dE_vs_oracle": abs(e5 - ref5) if ref5 is not None else None}
+        del cc
+
     # end to end through the public API: host A -> device, double layer, move, corner -> host
     import ctypes  # noqa: F401
     A_host = torch.from_numpy(np.ascontiguousarray(A)).pin_memory()
@@ -424,6 +449,7 @@ def run_ours(args):
                            "moves_timed": f"{args.warmup + 1}-{args.warmup + args.steps}"},
                 "speedup_vs_dense_f64": (value / world) / dense["moves_per_s"] if dense else None,
                 "dense_f64": dense, "z2_other_eig": alt, "abs_dE_vs_oracle_50_moves": dE,
+                "complex_graded": cplx,
                 "steady_state": steady,
                 "time_split_ms": {k: v / args.steps for k, v in prof["phase_ms"].items()},
                 "wall_s_timed_region": t_wall,

@@ -46,7 +46,7 @@
 extern "C" {
 #endif
 
-#define HS_ABI_VERSION 1
+#define HS_ABI_VERSION 2
 
 typedef enum {
   HS_OK = 0,
@@ -106,7 +106,15 @@ typedef struct hs_ctx_s* hs_ctx;
 
 /* The double-layer tensor a[u, l, d, r] (Sec. II.A, Fig. 1(b)) in FSO storage
  * with row legs (u, l) and column legs (d, r), all four legs of dimension D^2
- * split (n_even, n_odd). Only the even-total blocks exist for real A. */
+ * split (n_even, n_odd). Only the even-total blocks exist for real A.
+ *
+ * Complex A (dtype HS_C128, Hermitian basis only; Sec. II.C): every block of a
+ * in the eigenbasis of S is purely real (even total parity) or purely
+ * imaginary (odd). Such "graded" tensors, and the environment built from
+ * them, are stored as ONE dense row-major real matrix over the same row and
+ * column leg groups, rows and columns each in FSO order (even group first);
+ * an entry of odd total parity holds the imaginary part, an even one the real
+ * part. Products follow the sign rule of Eq. (2)-(3). */
 typedef struct {
   int D;                 /* bond dimension of A */
   int n_even, n_odd;     /* per-leg sector sizes: (D(D+1)/2, D(D-1)/2) or (D^2, 0) */
@@ -123,6 +131,9 @@ typedef struct {
  * edge T[alpha, x, beta]. Both are FP64 in FSO storage:
  *   C: row leg beta, column leg gamma (block diagonal);
  *   T: row legs (alpha, x), column leg beta.
+ * Complex environments (dtype HS_C128) are graded (see hs_z2_tensor) and
+ * oriented: boundary tensors run clockwise, alpha/beta of T and the row/column
+ * of C are the incoming/outgoing legs, and C is not symmetric.
  * The boundary leg has sectors (chi_even, chi_odd). Buffers are caller-owned,
  * sized with hs_env_bytes(). Fields other than C, T and the byte counts are
  * written by the library. */
@@ -139,6 +150,7 @@ typedef struct {
   double* T;             /* device, caller-owned */
   size_t C_bytes, T_bytes;
   hs_eig_mode eig_mode;  /* set to HS_EIG_F64 by hs_ctmrg_init; the caller may change it between moves */
+  hs_dtype dtype;        /* HS_F64, or HS_C128 for a complex double layer (graded storage, below) */
 } hs_env;
 
 /* Per-move record filled by hs_ctmrg_move (host memory). */
@@ -207,7 +219,8 @@ hs_status hs_to_hermitian_basis(hs_ctx ctx, const double* a_dense, int D, hs_dty
 
 /* Fused form of the two calls above: from A (device, real) straight to the
  * stored blocks of a~ in `basis` (HS_BASIS_DENSE gives the plain layout).
- * Asynchronous. */
+ * dtype HS_C128 (A interleaved complex128, Hermitian basis only) writes the
+ * graded a~ (Sec. II.C). Asynchronous. */
 hs_status hs_double_layer_hermitian(hs_ctx ctx, const double* A, int d, int D, hs_dtype dtype,
                                     hs_basis basis, hs_z2_tensor* out);
 
@@ -228,15 +241,23 @@ hs_status hs_ctmrg_init(hs_ctx ctx, const hs_z2_tensor* a, int chi_max, hs_preci
  * largest modulus kept across both blocks (ties: larger |lambda|, then the
  * even block, then the lower eigenvalue), C <- diag(lambda_kept),
  * T <- P^T (T a) P, then C and T divided by their largest modulus.
+ * Complex environments (HS_C128): graded block GEMMs (FP64), then the chi
+ * largest singular values of C' = U S V^dagger, found as the top
+ * eigenvectors of H = M M^T with C' = J M J (J = diag(1, i) by parity; one
+ * eigen-decomposition of size chi*D^2, FP64 for HS_EIG_F64, FP32 followed by
+ * two FP64 Loewdin steps otherwise); C <- U^dagger C' U,
+ * T <- U^dagger (T a) U; the new boundary sectors are (chi, 0). lam_* in info
+ * are singular values. FP64 block GEMMs only: the precision is ignored.
  * info (host, may be NULL) receives the move record. Synchronises once
  * (to learn the new sector sizes). */
 hs_status hs_ctmrg_move(hs_ctx ctx, const hs_z2_tensor* a, hs_env* env, int chi,
                         hs_move_info* info);
 
 /* Copy the environment out in the plain dense layout: C_dense[chi, chi] and
- * T_dense[chi, D^2, chi] (device, caller-owned, FP64), with the boundary leg
- * ordered as stored (even sector first) and the double-layer leg rotated back
- * to the plain combined basis. Asynchronous. */
+ * T_dense[chi, D^2, chi] (device, caller-owned, FP64; interleaved complex128
+ * for HS_C128 environments), with the boundary leg ordered as stored (even
+ * sector first) and the double-layer leg rotated back to the plain combined
+ * basis. Asynchronous. */
 hs_status hs_env_to_dense(hs_ctx ctx, const hs_env* env, double* C_dense, double* T_dense);
 
 /* ---- HOTRG (Sec. II.A, Ref. xie12) ------------------------------------ */

@@ -54,7 +54,7 @@ class Env(ctypes.Structure):
                 ("q_even", c_int), ("q_odd", c_int), ("basis", c_int), ("precision", c_int),
                 ("gemm_backend", c_int), ("moves", c_int), ("log_norm_C", c_double),
                 ("log_norm_T", c_double), ("C", c_void_p), ("T", c_void_p), ("C_bytes", c_size_t),
-                ("T_bytes", c_size_t), ("eig_mode", c_int)]
+                ("T_bytes", c_size_t), ("eig_mode", c_int), ("dtype", c_int)]
 
 
 class MoveInfo(ctypes.Structure):

@@ -50,18 +50,29 @@ def to_device(A: np.ndarray, device: int = 0) -> torch.Tensor:
 
 
 class CTMRG:
-    """C4v CTMRG of one real iPEPS tensor on one GPU through the C ABI."""
+    """C4v CTMRG of one iPEPS tensor on one GPU through the C ABI.
+
+    A complex A (numpy complex array, or a torch tensor of interleaved float64
+    with complex_valued=True) runs the graded path of Sec. II.C in the
+    Hermitian basis; a real one the Z2 block path of Sec. II.B.
+    """
 
     def __init__(self, ctx: Context, A: np.ndarray | torch.Tensor, chi: int, basis: str = "hermitian",
-                 precision: str = "f64", backend: str = "own", eig: str = "f64"):
+                 precision: str = "f64", backend: str = "own", eig: str = "f64", complex_valued: bool | None = None):
         self.ctx = ctx
         dev = f"cuda:{ctx.device}"
+        if complex_valued is None:
+            complex_valued = isinstance(A, np.ndarray) and np.iscomplexobj(A)
+        self.complex = bool(complex_valued)
+        self.dtype = L.HS_C128 if self.complex else L.HS_F64
         self.A = A if isinstance(A, torch.Tensor) else to_device(A, ctx.device)
         self.d, self.D = int(self.A.shape[0]), int(self.A.shape[1])
         self.chi = chi
-        nbytes = L.hs_z2_tensor_bytes(self.D, BASIS[basis])
+        nbytes = L.hs_z2_tensor_bytes(self.D, BASIS[basis], self.dtype)
+        if nbytes == 0:
+            raise ValueError("complex tensors need the Hermitian basis")
         self.a_buf = torch.empty(nbytes // 8, dtype=torch.float64, device=dev)
-        self.a = L.hs_double_layer_hermitian(ctx.handle, self.A, self.d, self.D, L.HS_F64, BASIS[basis],
+        self.a = L.hs_double_layer_hermitian(ctx.handle, self.A, self.d, self.D, self.dtype, BASIS[basis],
                                              self.a_buf)
         cb, tb = L.hs_env_bytes(self.D, chi)
         self.C_buf = torch.empty(cb // 8, dtype=torch.float64, device=dev)
@@ -90,28 +101,40 @@ class CTMRG:
         return sv / sv[0]
 
     def dense_env(self) -> tuple[torch.Tensor, torch.Tensor]:
-        """(C[chi, chi], T[chi, D^2, chi]) in the plain combined basis."""
+        """(C[chi, chi], T[chi, D^2, chi]) in the plain combined basis (complex128 for complex A)."""
         chi, q = self.chi_now, self.D * self.D
         dev = self.A.device
+        if self.complex:
+            C = torch.empty((chi, chi, 2), dtype=torch.float64, device=dev)
+            T = torch.empty((chi, q, chi, 2), dtype=torch.float64, device=dev)
+            L.hs_env_to_dense(self.ctx.handle, self.env, C, T)
+            return torch.view_as_complex(C), torch.view_as_complex(T)
         C = torch.empty((chi, chi), dtype=torch.float64, device=dev)
         T = torch.empty((chi, q, chi), dtype=torch.float64, device=dev)
         L.hs_env_to_dense(self.ctx.handle, self.env, C, T)
         return C, T
 
-    def rdm2(self, h: np.ndarray) -> tuple[torch.Tensor, float, float]:
-        """(rho, Tr rho, Tr rho h) of a horizontal bond; h a d^2 x d^2 real matrix."""
+    def rdm2(self, h: np.ndarray):
+        """(rho, Tr rho, Tr rho h) of a horizontal bond; h a d^2 x d^2 real matrix.
+        For complex A, rho is complex128 and the traces are complex."""
         dev = self.A.device
         n = self.d * self.d
+        hd = torch.from_numpy(np.ascontiguousarray(np.real(h), dtype=np.float64)).to(dev)
+        if self.complex:
+            rho = torch.empty((n, n, 2), dtype=torch.float64, device=dev)
+            tr = torch.empty(4, dtype=torch.float64, device=dev)
+            L.hs_rdm(self.ctx.handle, self.env, self.A, self.d, self.D, L.HS_C128, L.HS_RDM_TWO_SITE, hd, rho, tr)
+            t = tr.cpu().numpy()
+            return torch.view_as_complex(rho), complex(t[0], t[1]), complex(t[2], t[3])
         rho = torch.empty((n, n), dtype=torch.float64, device=dev)
         tr = torch.empty(2, dtype=torch.float64, device=dev)
-        hd = torch.from_numpy(np.ascontiguousarray(h, dtype=np.float64)).to(dev)
         L.hs_rdm(self.ctx.handle, self.env, self.A, self.d, self.D, L.HS_F64, L.HS_RDM_TWO_SITE, hd, rho, tr)
         t = tr.cpu().numpy()
         return rho, float(t[0]), float(t[1])
 
     def energy(self, h: np.ndarray) -> float:
         _, t0, t1 = self.rdm2(h)
-        return t1 / t0
+        return float(np.real(t1 / t0))
 
     def rdm2_of(self, A: torch.Tensor, h: torch.Tensor) -> tuple[torch.Tensor, torch.Tensor]:
         """(rho, [Tr rho, Tr rho h]) for another tensor A with this (fixed) environment."""

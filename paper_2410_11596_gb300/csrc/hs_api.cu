@@ -202,6 +202,8 @@ hs_status eig_pair_impl(hs_ctx ctx, bool f32, void* A0, int n0, void* w0, void* 
 hs_status eig_pair(hs_ctx ctx, bool f32, void* A0, int n0, void* w0, void* A1, int n1, void* w1) {
   return eig_pair_impl(ctx, f32, A0, n0, w0, A1, n1, w1);
 }
+hs_status eig_single(hs_ctx ctx, bool f32, void* A, int n, void* w) { return eig_any(ctx, 0, f32, A, n, w, 0); }
+hs_status eig_workspace32(hs_ctx ctx, int nmax) { return eig32_workspace(ctx, nmax); }
 hs_status eig_workspace(hs_ctx ctx, int nmax) { return eig_workspace_impl(ctx, nmax); }
 
 // Write the operand `layout` (legs = src legs permuted by perm) of a
@@ -271,11 +273,13 @@ hs_status tc_a_gemm(hs_ctx ctx, hs_precision prec, const Z2Mat& Xsrc, const Z2Ma
 Z2Mat dense2(long long r, long long c) { return mat(fused1(make_sect((int)r, 0)), fused1(make_sect((int)c, 0))); }
 
 // Canonical sign, FP64 re-orthonormalisation and projection of the kept rows
-// PT (already gathered): the largest entry of each row is made positive, two
-// Loewdin steps PT <- (3/2 I - 1/2 PT PT^T) PT, then the new corner is the
-// FP64 projection C = PT C' PT^T of each block, normalised by its largest entry.
+// PT (already gathered): the largest entry of each row is made positive,
+// `lowdin` Loewdin steps PT <- (3/2 I - 1/2 PT PT^T) PT in FP64 (each step
+// squares the departure from orthonormality: 1e-6 -> 1e-12 -> rounding), then
+// the new corner is the projection C = PT C' PT^T of each block (FP64, or on
+// the tensor cores in the TF32/BF16 precisions), normalised by its largest entry.
 hs_status finish_projector(hs_ctx ctx, int n0, int n1, SelectOut* dsel, Sect c, Sect q, Sect cn, const double* C0,
-                           const double* C1, hs_env* env, double* flops) {
+                           const double* C1, hs_env* env, double* flops, int lowdin) {
   cudaStream_t s = ctx->stream;
   const int k[2] = {cn.n[0], cn.n[1]};
   const int n[2] = {n0, n1};
@@ -308,8 +312,8 @@ hs_status finish_projector(hs_ctx ctx, int n0, int n1, SelectOut* dsel, Sect c, 
     HS_TRY(permute(ctx, PTm, Pm, {1, 2, 0}, PT, P));
     ctx->launches += 2;
   }
-  PhaseScope ps(ctx, HS_PHASE_GEMM);
-  for (int step = 0; step < 2; ++step) {
+  for (int step = 0; step < lowdin; ++step) {
+    PhaseScope ps(ctx, HS_PHASE_GEMM);
     // G = PT PT^T
     GemmGroup gg = group([&](int p) {
       return GemmProblem{k[p], k[p], n[p], n[p], n[p], k[p], ptoff[p], ptoff[p], goff[p]};
@@ -328,13 +332,21 @@ hs_status finish_projector(hs_ctx ctx, int n0, int n1, SelectOut* dsel, Sect c, 
     ctx->launches += 3;
   }
   // W = PT C' (C' symmetric), C_new = W PT^T, block by block into env->C.
-  // With tensor-core precisions W runs on tcgen05 from the split C' blocks.
-  GemmGroup gw = group([&](int p) {
-    return GemmProblem{k[p], n[p], n[p], n[p], n[p], n[p], ptoff[p], (long long)(Cp[p] - C0), ptoff[p]};
-  });
+  // With tensor-core precisions both products run on tcgen05 (C' split once
+  // per move, PT and W split here); otherwise both run on the FP64 kernel.
   const hs_precision prec = env->precision;
   if (prec == HS_PREC_F64) {
+    PhaseScope ps(ctx, HS_PHASE_GEMM);
+    GemmGroup gw = group([&](int p) {
+      return GemmProblem{k[p], n[p], n[p], n[p], n[p], n[p], ptoff[p], (long long)(Cp[p] - C0), ptoff[p]};
+    });
+    GemmGroup gc = group([&](int p) {
+      return GemmProblem{k[p], k[p], n[p], n[p], n[p], k[p], ptoff[p], ptoff[p], goff[p]};
+    });
     HS_CUDA(launch_gemm_f64(gw, PT, C0, W, 1.0, s, ctx->splitk.d(), kSplitKElems));
+    HS_CUDA(launch_gemm_f64(gc, W, PT, env->C, 1.0, s, ctx->splitk.d(), kSplitKElems));
+    *flops += gemm_flops(gw) + gemm_flops(gc);
+    ctx->phase_flops[HS_PHASE_GEMM] += gemm_flops(gw) + gemm_flops(gc);
   } else {
     for (int p = 0; p < 2; ++p) {
       if (k[p] == 0 || n[p] == 0) continue;
@@ -347,15 +359,15 @@ hs_status finish_projector(hs_ctx ctx, int n0, int n1, SelectOut* dsel, Sect c, 
                       ctx->sx_lo));
       HS_TRY(tc_run(ctx, prec, dense2(k[p], n[p]), ctx->sx_hi, ctx->sx_lo, dense2(n[p], n[p]), ctx->sH_hi[p],
                     ctx->sH_lo[p], dense2(k[p], n[p]), W + ptoff[p]));
-      ctx->phase_flops[HS_PHASE_GEMM_TC] += 2.0 * k[p] * (double)n[p] * n[p];
+      HS_TRY(tc_split(ctx, prec, dense2(k[p], n[p]), dense2(k[p], n[p]), {0, 1}, W + ptoff[p], ctx->sy_hi,
+                      ctx->sy_lo));
+      HS_TRY(tc_run(ctx, prec, dense2(k[p], n[p]), ctx->sy_hi, ctx->sy_lo, dense2(k[p], n[p]), ctx->sx_hi,
+                    ctx->sx_lo, dense2(k[p], k[p]), env->C + goff[p]));
+      const double f = 2.0 * k[p] * (double)n[p] * n[p] + 2.0 * k[p] * (double)k[p] * n[p];
+      *flops += f;
+      ctx->phase_flops[HS_PHASE_GEMM_TC] += f;
     }
   }
-  GemmGroup gc = group([&](int p) {
-    return GemmProblem{k[p], k[p], n[p], n[p], n[p], k[p], ptoff[p], ptoff[p], goff[p]};
-  });
-  HS_CUDA(launch_gemm_f64(gc, W, PT, env->C, 1.0, s, ctx->splitk.d(), kSplitKElems));
-  *flops += gemm_flops(gw) + gemm_flops(gc);
-  ctx->phase_flops[HS_PHASE_GEMM] += (prec == HS_PREC_F64 ? gemm_flops(gw) : 0.0) + gemm_flops(gc);
   HS_CUDA(launch_normalize_max_to(env->C, goff[1] + (long long)k[1] * k[1],
                                   static_cast<unsigned long long*>(ctx->scratch.p) + 2, &dsel->log_norm_C, s));
   ctx->launches += 4;
@@ -374,7 +386,7 @@ hs_status project_f32(hs_ctx ctx, const float* V0f, int n0, const float* V1f, in
     HS_CUDA(launch_gather_p32(V0f, n0, V1f, n1, didx, chi, dsel, ctx->pt.d(), ctx->pcol.d(), ctx->stream));
     ctx->launches += 1;
   }
-  return finish_projector(ctx, n0, n1, dsel, c, q, cn, C0, C1, env, flops);
+  return finish_projector(ctx, n0, n1, dsel, c, q, cn, C0, C1, env, flops, 2);
 }
 
 // ---- warm-started subspace eigensolver (HS_EIG_SUBSPACE) ----
@@ -515,9 +527,12 @@ hs_status subspace_projector(hs_ctx ctx, hs_env* env, int chi, int n0, int n1, d
       ctx->launches += 1;
     }
     {
+      // Rayleigh-Ritz: both m x m FP32 problems by one-CTA Jacobi kernels
       PhaseScope ps(ctx, HS_PHASE_EIG);
       HS_CUDA(cudaMemsetAsync(ctx->info.p, 0, 2 * sizeof(int), s));
-      HS_TRY(eig_pair_impl(ctx, true, ctx->sbw[0].p, m[0], th, ctx->sbw[1].p, m[1], th + m[0]));
+      HS_CUDA(launch_jacobi_eig_pair(static_cast<float*>(ctx->sbw[0].p), m[0], th, static_cast<float*>(ctx->sbw[1].p),
+                                     m[1], th + m[0], static_cast<int*>(ctx->info.p), s));
+      ctx->launches += 1;
     }
     for (int b = 0; b < 2; ++b) {
       if (m[b] == 0) continue;
@@ -707,7 +722,9 @@ hs_status hs_sync(hs_ctx ctx) {
 }
 
 size_t hs_z2_tensor_bytes(int D, hs_basis basis, hs_dtype dtype) {
-  if (D <= 0 || dtype != HS_F64) return 0;
+  if (D <= 0) return 0;
+  if (dtype == HS_C128) return basis == HS_BASIS_HERMITIAN ? graded_tensor_bytes(D) : 0;
+  if (dtype != HS_F64) return 0;
   return a_elems(D, basis) * sizeof(double);
 }
 
@@ -757,14 +774,18 @@ hs_status hs_double_layer_hermitian(hs_ctx ctx, const double* A, int d, int D, h
                                     hs_basis basis, hs_z2_tensor* out) {
   HS_TRY(check_ctx(ctx));
   if (!A || !out || !out->data || d <= 0 || D <= 0) return fail(HS_ERR_INVALID_ARG, "bad arguments");
-  if (dtype != HS_F64)
-    return fail(HS_ERR_UNSUPPORTED, "complex double layers are not supported by this build");
+  if (dtype != HS_F64 && dtype != HS_C128) return fail(HS_ERR_DTYPE, "unknown dtype");
   if (basis != HS_BASIS_DENSE && basis != HS_BASIS_HERMITIAN)
     return fail(HS_ERR_INVALID_ARG, "unknown basis");
+  if (dtype == HS_C128 && basis != HS_BASIS_HERMITIAN)
+    return fail(HS_ERR_UNSUPPORTED, "complex double layers are stored in the Hermitian basis only");
   const size_t need = hs_z2_tensor_bytes(D, basis, dtype);
   if (out->capacity_bytes < need)
     return fail(HS_ERR_WORKSPACE, "output holds %zu bytes, %zu needed", out->capacity_bytes, need);
-  HS_CUDA(launch_double_layer_blocks(A, d, D, basis == HS_BASIS_HERMITIAN, out->data, ctx->stream));
+  if (dtype == HS_C128)
+    HS_TRY(graded_double_layer(ctx, A, d, D, out));
+  else
+    HS_CUDA(launch_double_layer_blocks(A, d, D, basis == HS_BASIS_HERMITIAN, out->data, ctx->stream));
   const Sect q = q_sect(D, basis);
   out->D = D;
   out->n_even = q.n[0];
@@ -818,7 +839,12 @@ hs_status hs_ctmrg_init(hs_ctx ctx, const hs_z2_tensor* a, int chi_max, hs_preci
   env->gemm_backend = backend;
   env->moves = 0;
   env->eig_mode = HS_EIG_F64;
+  env->dtype = a->dtype;
   ctx->ws_valid = false;  // no warm start for the subspace eigensolver yet
+  if (a->dtype == HS_C128) {
+    if (!herm) return fail(HS_ERR_UNSUPPORTED, "complex double layers are stored in the Hermitian basis only");
+    return graded_init(ctx, a, chi_max, env);
+  }
   HS_CUDA(launch_ctmrg_init(a->data, D, herm, env->C, env->T, ctx->stream));
   // normalise like every later move
   const Z2Mat Cm = mat(fused1(qs), fused1(qs)), Tm = mat(fused2(qs, qs), fused1(qs));
@@ -873,6 +899,8 @@ hs_status hs_ctmrg_move(hs_ctx ctx, const hs_z2_tensor* a, hs_env* env, int chi,
   if (a->D != env->D || a->basis != env->basis)
     return fail(HS_ERR_SHAPE, "tensor and environment disagree on D or basis");
   if (chi < 1 || chi > env->chi_max) return fail(HS_ERR_SHAPE, "chi %d outside [1, %d]", chi, env->chi_max);
+  if (env->dtype != a->dtype) return fail(HS_ERR_DTYPE, "tensor and environment disagree on dtype");
+  if (env->dtype == HS_C128) return graded_move(ctx, a, env, chi, info);
   cudaStream_t s = ctx->stream;
   const hs_gemm_backend be = env->gemm_backend;
   const bool tc = env->precision != HS_PREC_F64;
@@ -896,19 +924,18 @@ hs_status hs_ctmrg_move(hs_ctx ctx, const hs_z2_tensor* a, hs_env* env, int chi,
   GemmGroup g1 = make_z2_gemm(Tcr, Cm, X1), g2 = make_z2_gemm(X1, Tcr, X2),
             g3 = make_z2_gemm(X2p, Am, X3);
   flops += gemm_flops(g1) + gemm_flops(g2) + gemm_flops(g3);
-  ctx->phase_flops[HS_PHASE_GEMM] += gemm_flops(g1);
-  ctx->phase_flops[tc ? HS_PHASE_GEMM_TC : HS_PHASE_GEMM] += gemm_flops(g2) + gemm_flops(g3);
+  ctx->phase_flops[tc ? HS_PHASE_GEMM_TC : HS_PHASE_GEMM] += gemm_flops(g1) + gemm_flops(g2) + gemm_flops(g3);
   if (!tc) {
     PhaseScope ps(ctx, HS_PHASE_GEMM);
     HS_TRY(gemm(ctx, be, g1, env->T, env->C, ctx->x1.d()));
     HS_TRY(gemm(ctx, be, g2, ctx->x1.d(), env->T, B1));
   } else {
-    {
-      PhaseScope ps(ctx, HS_PHASE_GEMM);
-      HS_TRY(gemm(ctx, be, g1, env->T, env->C, ctx->x1.d()));
-    }
-    // the split edge serves as B of G2 here and of G4 below
+    // the split edge serves as A of G1, B of G2 here and B of G4 below; the
+    // corner (symmetric) is its own K-major B operand
     HS_TRY(tc_split(ctx, env->precision, Tcr, Tcr, {0, 1, 2}, env->T, ctx->tc_b_hi, ctx->tc_b_lo));
+    HS_TRY(tc_split(ctx, env->precision, Cm, Cm, {0, 1}, env->C, ctx->sy_hi, ctx->sy_lo));
+    HS_TRY(tc_run(ctx, env->precision, Tcr, ctx->tc_b_hi, ctx->tc_b_lo, Cm, ctx->sy_hi, ctx->sy_lo, X1,
+                  ctx->x1.d()));
     HS_TRY(tc_split(ctx, env->precision, X1, X1, {0, 1, 2}, ctx->x1.d(), ctx->tc_x_hi, ctx->tc_x_lo));
     HS_TRY(tc_run(ctx, env->precision, X1, ctx->tc_x_hi, ctx->tc_x_lo, Tcr, ctx->tc_b_hi, ctx->tc_b_lo, X2, B1));
   }
@@ -1008,7 +1035,9 @@ hs_status hs_ctmrg_move(hs_ctx ctx, const hs_z2_tensor* a, hs_env* env, int chi,
                                  ctx->pcol.d(), s));
       ctx->launches += 1;
     }
-    HS_TRY(finish_projector(ctx, n0, n1, dsel, c, q, cn, V0, V1, env, &flops));
+    // converged Ritz vectors are orthonormal to ~1e-6 (FP32 Rayleigh-Ritz):
+    // one FP64 Loewdin step brings them to ~1e-12
+    HS_TRY(finish_projector(ctx, n0, n1, dsel, c, q, cn, V0, V1, env, &flops, 1));
   } else if (!f32eig) {
     PhaseScope ps(ctx, HS_PHASE_SELECT);
     HS_CUDA(launch_gather_pt(V0, n0, V1, n1, didx, chi, dsel, ctx->pt.d(), s));
@@ -1207,6 +1236,11 @@ hs_status hs_gemm(hs_ctx ctx, hs_precision precision, int M, int N, int K, const
 hs_status hs_env_to_dense(hs_ctx ctx, const hs_env* env, double* C_dense, double* T_dense) {
   HS_TRY(check_ctx(ctx));
   if (!env || !C_dense || !T_dense) return fail(HS_ERR_INVALID_ARG, "bad arguments");
+  if (env->dtype == HS_C128) {
+    HS_CUDA(launch_env_to_dense_graded(env->C, env->T, env->D, env->chi_even, env->chi_odd, C_dense, T_dense,
+                                       ctx->stream));
+    return HS_OK;
+  }
   HS_CUDA(launch_env_to_dense(env->C, env->T, env->D, env->chi_even, env->chi_odd,
                               env->basis == HS_BASIS_HERMITIAN, C_dense, T_dense, ctx->stream));
   return HS_OK;

@@ -110,6 +110,12 @@ struct hs_ctx_s {
   std::vector<char> solver2_host, solver2_32_host;
   // HOTRG workspace
   hs::DBuf hb[16];
+  // complex (graded) CTMRG: private copy of a~ followed by its conjugate, and scratch
+  hs::DBuf ga;
+  const double* ga_src = nullptr;
+  hs::DBuf gb[12];
+  // complex observables (planar real / imaginary parts)
+  hs::DBuf zr[24];
   // split-K partial sums of the FP64 GEMM
   hs::DBuf splitk;
   // subspace eigensolver: warm start (previous kept rows, per block) and
@@ -150,6 +156,21 @@ hs_status permute(hs_ctx ctx, const Z2Mat& in, const Z2Mat& out, std::initialize
 // stream); FP32 when f32. Shared with the HOTRG step.
 hs_status eig_pair(hs_ctx ctx, bool f32, void* A0, int n0, void* w0, void* A1, int n1, void* w1);
 hs_status eig_workspace(hs_ctx ctx, int nmax);
+// One symmetric eigen-decomposition (vectors in place, column-major) on the
+// context stream; FP32 when f32 (workspace from eig_workspace32).
+hs_status eig_single(hs_ctx ctx, bool f32, void* A, int n, void* w);
+hs_status eig_workspace32(hs_ctx ctx, int nmax);
+// C[M x N] = A[M x K] B[N x K]^T, dense row-major FP64 (tensor cores in the
+// TF32/BF16 precisions, else the FP64 kernel).
+hs_status dense_gemm_any(hs_ctx ctx, hs_precision prec, int M, int N, int K, const double* A, const double* B,
+                         double* C);
+// Complex (graded) CTMRG, hs_graded.cu.
+hs_status graded_double_layer(hs_ctx ctx, const double* A, int d, int D, hs_z2_tensor* out);
+size_t graded_tensor_bytes(int D);
+hs_status graded_init(hs_ctx ctx, const hs_z2_tensor* a, int chi_max, hs_env* env);
+hs_status graded_move(hs_ctx ctx, const hs_z2_tensor* a, hs_env* env, int chi, hs_move_info* info);
+// Loewdin re-orthonormalisation of the m rows of X (n long), `steps` times.
+hs_status lowdin_rows(hs_ctx ctx, hs_precision prec, double* X, int m, int n, double* Xc, int steps);
 
 // Tensor-core precisions: elements per 128-byte row (the K padding unit),
 // bytes per element, split mode of the permute/split kernels.

@@ -136,6 +136,9 @@ struct Box {
   long long out_stride[kMaxLegs], in_stride[kMaxLegs];
   long long count;   // product of dims
   long long start;   // prefix sum of counts over earlier boxes
+  // division by dim[j] of 32-bit indices (fast_div in hs_bits.cuh)
+  unsigned mag[kMaxLegs];
+  unsigned char sh1[kMaxLegs], sh2[kMaxLegs];
 };
 
 constexpr int kMaxBoxes = 32;  // even-parity tuples of 6 legs
@@ -149,6 +152,35 @@ struct PermPlan {
 // Build the plan that maps matrix `in` (legs L0..L{n-1}; the first in.r.k are
 // rows) to matrix `out` whose leg j is input leg perm[j]. Both even-total.
 PermPlan make_perm_plan(const Z2Mat& in, const Z2Mat& out, const int* perm);
+
+// ---- graded dense matrices (complex tensors, Sec. II.C) ----------------------
+//
+// For complex A the double layer in the eigenbasis of S is not block sparse,
+// but each block is purely real (even total parity) or purely imaginary (odd):
+// Sec. II.C. A graded matrix stores all four parity blocks as one dense
+// row-major real matrix, rows and columns each in FSO order (even group
+// first); an entry of odd total parity holds the imaginary part of the
+// complex value, an even one the real part. The product of two graded
+// matrices is graded (the rule f of Eq. (2)-(3)): with x = i^[p(r)!=p(k)] x~,
+//   C~[r, k] = sum_j s A~[r, j] B~[j, k],  s = -1 iff p(j) != p(r) = p(k).
+struct GMat {
+  Fused r, c;
+  int pad;
+};
+
+HS_HD long long g_rows(const GMat& m) { return fused_size(m.r, 0) + fused_size(m.r, 1); }
+HS_HD long long g_cols(const GMat& m) { return fused_size(m.c, 0) + fused_size(m.c, 1); }
+HS_HD long long g_ld(const GMat& m) {
+  const long long a = m.pad > 1 ? m.pad : 1;
+  return (g_cols(m) + a - 1) / a * a;
+}
+HS_HD long long g_elems(const GMat& m) { return g_rows(m) * g_ld(m); }
+HS_HD long long g_row0(const GMat& m, int p) { return p ? fused_size(m.r, 0) : 0; }
+HS_HD long long g_col0(const GMat& m, int p) { return p ? fused_size(m.c, 0) : 0; }
+
+// Permutation plan between two graded matrices (all parity tuples; at most
+// five legs). Returns false if the tuples do not fit the plan.
+bool make_graded_perm_plan(const GMat& in, const GMat& out, const int* perm, PermPlan* plan);
 
 // ---- grouped GEMM ----------------------------------------------------------
 
@@ -168,6 +200,11 @@ struct GemmGroup {
 
 // The two block GEMMs of a Z2 product C[R|N] = A[R|K] B[N|K]^T.
 GemmGroup make_z2_gemm(const Z2Mat& A, const Z2Mat& B, const Z2Mat& C);
+// The four sub-GEMMs of a graded product C~[R|N] = A~[R|K] B~[N|K]^T: the
+// output block (pr, pc) is A~'s row block pr times B~'s row block pc over the
+// whole K; the diagonal blocks (pr == pc) read the conjugate copy of B~ (its
+// odd-total entries negated), stored `bconj_off` elements after B~.
+GemmGroup make_graded_gemm(const GMat& A, const GMat& B, const GMat& C, long long bconj_off);
 double gemm_flops(const GemmGroup& g);
 
 // ---- kernel launchers (device code in k_*.cu) -------------------------------
@@ -206,8 +243,10 @@ cudaError_t launch_gemm_tc(int precision, const TcProblem* probs, int nprob, int
                            double* part = nullptr, long long part_elems = 0);
 // part/part_elems: optional workspace for split-K partial sums (used when the
 // output tiles alone cannot fill the GPU); nullptr disables splitting.
+// accumulate: C += alpha A B^T instead of C = alpha A B^T.
 cudaError_t launch_gemm_f64(const GemmGroup& g, const double* A, const double* B, double* C,
-                            double alpha, cudaStream_t s, double* part = nullptr, long long part_elems = 0);
+                            double alpha, cudaStream_t s, double* part = nullptr, long long part_elems = 0,
+                            bool accumulate = false);
 
 // A[p,u,l,d,r] (real) -> a~ blocks in FSO [(u,l)|(d,r)]; hermitian selects the
 // rotation by U^T on every leg, otherwise the plain combined basis.
@@ -272,10 +311,41 @@ cudaError_t launch_row_sign(double* X, int m, int n, cudaStream_t s);
 cudaError_t launch_gather_rows(const double* X0, int n0, const double* X1, int n1, const int* idx, int chi,
                                const SelectOut* sel, double* PT, double* P, cudaStream_t s);
 int max_subspace();
+// Two small symmetric FP32 eigen-decompositions (one CTA each; m <= max_subspace()),
+// output as syevd: ascending eigenvalues, vectors as columns (column-major, in place);
+// *status = 1 if a matrix did not converge.
+cudaError_t launch_jacobi_eig_pair(float* A0, int m0, float* w0, float* A1, int m1, float* w1, int* status,
+                                   cudaStream_t s);
 cudaError_t launch_row_normalize(double* X, int m, int n, cudaStream_t s);
 // X (m x n rows, FP64) = the m eigenvectors of largest |eigenvalue| of one
 // FP32 eigen-decomposition (ascending w, column-major V); idx is scratch (m ints).
 cudaError_t launch_top_rows(const float* w, const float* V, int n, int m, int* idx, double* X, cudaStream_t s);
+
+// ---- graded (complex) kernels, k_graded.cu --------------------------------
+
+// dst = src with a sign on part of a graded matrix (rows split r0 | r1,
+// columns c0 | c1, row stride ld; dst may equal src):
+//   mode 0: negate entries of odd total parity (complex conjugation);
+//   mode 1: negate the odd-odd block (C~ -> M with C = J M J, J = diag(1, i)).
+cudaError_t launch_graded_sign(const double* src, double* dst, long long r0, long long r1, long long c0,
+                               long long c1, long long ld, int mode, cudaStream_t s);
+// a~ of a complex A (interleaved complex128) as a graded [(u,l)|(d,r)] matrix.
+cudaError_t launch_double_layer_graded(const double* A, int d, int D, double* out, cudaStream_t s);
+// Traced-boundary C0 [d | r] and T0 [(alpha, x) | beta] (graded, chi0 = D^2
+// with the sectors of one double-layer leg) from the graded a~.
+cudaError_t launch_ctmrg_init_graded(const double* a, int D, double* C, double* T, cudaStream_t s);
+// Truncation from the ascending eigenvalues w (n) of H = M M^T with vectors V
+// (column-major n x n): keep k = min(chi, n) largest, singular values
+// sqrt(w); PT rows = the kept vectors in descending order; sel->chi_new =
+// {k, 0}; lam_* from the singular values. FP32 variant reads float w and V.
+cudaError_t launch_graded_select(const double* w, const double* V, int n, int chi, double* PT, SelectOut* sel,
+                                 cudaStream_t s);
+cudaError_t launch_graded_select32(const float* w, const float* V, int n, int chi, double* PT, SelectOut* sel,
+                                   cudaStream_t s);
+// Complex dense views (interleaved complex128, plain combined basis) of a
+// graded environment with boundary sectors (c0, c1).
+cudaError_t launch_env_to_dense_graded(const double* C, const double* T, int D, int c0, int c1, double* Cd,
+                                       double* Td, cudaStream_t s);
 
 // Dense views of an FSO environment (rotated back to the plain combined basis).
 cudaError_t launch_env_to_dense(const double* C, const double* T, int D, int c0, int c1,

@@ -150,7 +150,165 @@ GemmGroup dense_gemm(long long M, long long N, long long K) {
   return g;
 }
 
+// Complex A (interleaved complex128): open double layer with planar output
+//   out[(s, s', m) | (k0, k1, k2)] = A[s, kets] conj(A[s', bras]),
+// where (m, k0, k1, k2) are the legs legs[0..3] (0 u, 1 l, 2 d, 3 r) and each
+// combined index is x = ket + D * bra.
+__global__ void open_double_layer_c_kernel(const double* __restrict__ A, int d, int D, int4 legs,
+                                           double* __restrict__ re, double* __restrict__ im) {
+  const int q = D * D;
+  const long long total = (long long)d * d * q * q * q * q;
+  const long long D4 = (long long)D * D * D * D;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    long long r = e;
+    int x[4];
+    const int x2 = (int)(r % q);
+    r /= q;
+    const int x1 = (int)(r % q);
+    r /= q;
+    const int x0 = (int)(r % q);
+    r /= q;
+    const int xm = (int)(r % q);
+    r /= q;
+    const int sb = (int)(r % d);
+    const int sk = (int)(r / d);
+    x[legs.x] = xm;
+    x[legs.y] = x0;
+    x[legs.z] = x1;
+    x[legs.w] = x2;
+    const long long ik = (((long long)(x[0] % D) * D + x[1] % D) * D + x[2] % D) * D + x[3] % D;
+    const long long ib = (((long long)(x[0] / D) * D + x[1] / D) * D + x[2] / D) * D + x[3] / D;
+    const double kr = A[2 * (sk * D4 + ik)], ki = A[2 * (sk * D4 + ik) + 1];
+    const double br = A[2 * (sb * D4 + ib)], bi = A[2 * (sb * D4 + ib) + 1];
+    re[e] = kr * br + ki * bi;
+    im[e] = ki * br - kr * bi;
+  }
+}
+
+// Complex rho[(s1 s2), (s1' s2')] = rho4[s1, s1', s2, s2'] (planar in,
+// interleaved out); tr[0..1] = Tr rho, tr[2..3] = Tr(rho h) for real h.
+__global__ void finish_rho_c_kernel(const double* __restrict__ re4, const double* __restrict__ im4, int d,
+                                    const double* __restrict__ h, double* __restrict__ rho, double* __restrict__ tr) {
+  const int n = d * d;
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+    const int I = e / n, J = e % n;
+    const int s1 = I / d, s2 = I % d, t1 = J / d, t2 = J % d;
+    const int src = ((s1 * d + t1) * d + s2) * d + t2;
+    rho[2 * e] = re4[src];
+    rho[2 * e + 1] = im4[src];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0, c = 0.0, f = 0.0;
+    for (int I = 0; I < n; ++I) {
+      a += rho[2 * (I * n + I)];
+      b += rho[2 * (I * n + I) + 1];
+      if (h)
+        for (int J = 0; J < n; ++J) {
+          c += rho[2 * (I * n + J)] * h[J * n + I];
+          f += rho[2 * (I * n + J) + 1] * h[J * n + I];
+        }
+    }
+    tr[0] = a;
+    tr[1] = b;
+    tr[2] = c;
+    tr[3] = f;
+  }
+}
+
+struct ZBuf {
+  double* re;
+  double* im;
+};
+
+ZBuf zbuf(hs_ctx ctx, int i, long long n) {
+  if (ctx->zr[2 * i].ensure(n * 8) != HS_OK || ctx->zr[2 * i + 1].ensure(n * 8) != HS_OK) return {nullptr, nullptr};
+  return {ctx->zr[2 * i].d(), ctx->zr[2 * i + 1].d()};
+}
+
+// complex C = A B^T from planar parts: four FP64 GEMMs, two accumulating
+hs_status zgemm(hs_ctx ctx, const GemmGroup& g, ZBuf A, ZBuf B, ZBuf C) {
+  cudaStream_t s = ctx->stream;
+  HS_TRY(ctx->splitk.ensure(kSplitKElems * sizeof(double)));
+  double* part = ctx->splitk.d();
+  HS_CUDA(launch_gemm_f64(g, A.re, B.re, C.re, 1.0, s, part, kSplitKElems, false));
+  HS_CUDA(launch_gemm_f64(g, A.im, B.im, C.re, -1.0, s, part, kSplitKElems, true));
+  HS_CUDA(launch_gemm_f64(g, A.re, B.im, C.im, 1.0, s, part, kSplitKElems, false));
+  HS_CUDA(launch_gemm_f64(g, A.im, B.re, C.im, 1.0, s, part, kSplitKElems, true));
+  ctx->launches += 4;
+  return HS_OK;
+}
+
+hs_status zpermute(hs_ctx ctx, const Z2Mat& in, const Z2Mat& out, std::initializer_list<int> perm, ZBuf src,
+                   ZBuf dst) {
+  HS_TRY(permute(ctx, in, out, perm, src.re, dst.re));
+  return permute(ctx, in, out, perm, src.im, dst.im);
+}
+
 }  // namespace
+
+// Two-site rho of a complex (graded, oriented) environment: the network of
+// the oracle's clockwise ring, in complex arithmetic on planar FP64 parts.
+// Chain (C, T dense from the graded environment; boundary tensors clockwise):
+//   H[a,x,b] = C[a,c] T[c,x,e] C[e,b]
+//   L[b,d1,l1,u1,t] = T[b,d1,c] H[c,l1,e] T[e,u1,t]  (also the right chain R[t,u2,r2,d2,b])
+//   LB[(b,t)|(s1,s1',m)] = L a1 over (d1,l1,u1); RB[(t,b)|(s2,s2',m)] = L a2 over (u2,r2,d2)
+//   rho4[(s1,s1')|(s2,s2')] = sum_{b,t,m} LB RB
+hs_status rdm_complex(hs_ctx ctx, const hs_env* env, const double* A, int d, int D, const double* h, double* out,
+                      double* tr_out) {
+  cudaStream_t s = ctx->stream;
+  const long long chi = env->chi_even + env->chi_odd, q = (long long)D * D, d2 = (long long)d * d;
+  const long long c2 = chi * chi, cqc = chi * q * chi, c2q2 = c2 * q * q, c2q3 = c2q2 * q;
+  // interleaved dense environment, then planar
+  HS_TRY(ctx->r[0].ensure(2 * c2 * 8));
+  HS_TRY(ctx->r[1].ensure(2 * cqc * 8));
+  HS_CUDA(launch_env_to_dense_graded(env->C, env->T, D, env->chi_even, env->chi_odd, ctx->r[0].d(), ctx->r[1].d(),
+                                     s));
+  ZBuf Cz = zbuf(ctx, 0, c2), Tz = zbuf(ctx, 1, cqc), Ctz = zbuf(ctx, 2, c2), Tqz = zbuf(ctx, 3, cqc),
+       H1 = zbuf(ctx, 4, cqc), Hz = zbuf(ctx, 5, cqc), Hq = zbuf(ctx, 6, cqc), L1 = zbuf(ctx, 7, c2q2),
+       L2 = zbuf(ctx, 8, c2q3), L2p = zbuf(ctx, 9, c2q3);
+  if (!L2p.re) return fail(HS_ERR_CUDA, "workspace allocation failed");
+  {
+    // de-interleave: permute [n | 2] -> [2 | n]
+    HS_TRY(ctx->r[2].ensure(2 * cqc * 8));
+    HS_TRY(permute(ctx, dense({c2, 2}), dense({2, c2}), {1, 0}, ctx->r[0].d(), ctx->r[2].d()));
+    HS_CUDA(cudaMemcpyAsync(Cz.re, ctx->r[2].d(), c2 * 8, cudaMemcpyDeviceToDevice, s));
+    HS_CUDA(cudaMemcpyAsync(Cz.im, ctx->r[2].d() + c2, c2 * 8, cudaMemcpyDeviceToDevice, s));
+    HS_TRY(permute(ctx, dense({cqc, 2}), dense({2, cqc}), {1, 0}, ctx->r[1].d(), ctx->r[2].d()));
+    HS_CUDA(cudaMemcpyAsync(Tz.re, ctx->r[2].d(), cqc * 8, cudaMemcpyDeviceToDevice, s));
+    HS_CUDA(cudaMemcpyAsync(Tz.im, ctx->r[2].d() + cqc, cqc * 8, cudaMemcpyDeviceToDevice, s));
+  }
+  HS_TRY(zpermute(ctx, dense({chi, chi}), dense({chi, chi}), {1, 0}, Cz, Ctz));                 // C^T
+  HS_TRY(zpermute(ctx, dense({chi, q, chi}), dense({q, chi, chi}), {1, 2, 0}, Tz, Tqz));       // Tq[(x,e)|c]
+  HS_TRY(zgemm(ctx, dense_gemm(chi, q * chi, chi), Cz, Tqz, H1));                               // H1[a|(x,e)]
+  HS_TRY(zgemm(ctx, dense_gemm(chi * q, chi, chi), H1, Ctz, Hz));                               // H[(a,x)|b]
+  HS_TRY(zpermute(ctx, dense({chi, q, chi}), dense({q, chi, chi}), {1, 2, 0}, Hz, Hq));        // Hq[(l,e)|c]
+  HS_TRY(zgemm(ctx, dense_gemm(chi * q, q * chi, chi), Tz, Hq, L1));                            // L1[(b,d1)|(l1,e)]
+  HS_TRY(zgemm(ctx, dense_gemm(chi * q * q, q * chi, chi), L1, Tqz, L2));                       // L2[(b,d1,l1)|(u1,t)]
+  HS_TRY(zpermute(ctx, dense({chi, q, q, q, chi}), dense({chi, chi, q, q, q}), {0, 4, 1, 2, 3}, L2, L2p));
+  // open double layers: a1[(s,s',r) | (d,l,u)], a2[(s,s',l) | (u,r,d)]
+  const long long nao = d2 * q * q * q * q;
+  ZBuf a1 = zbuf(ctx, 10, nao), a2 = zbuf(ctx, 11, nao);
+  if (!a2.re) return fail(HS_ERR_CUDA, "workspace allocation failed");
+  open_double_layer_c_kernel<<<grid_for(nao), 256, 0, s>>>(A, d, D, make_int4(3, 2, 1, 0), a1.re, a1.im);
+  HS_CUDA(cudaGetLastError());
+  open_double_layer_c_kernel<<<grid_for(nao), 256, 0, s>>>(A, d, D, make_int4(1, 0, 3, 2), a2.re, a2.im);
+  HS_CUDA(cudaGetLastError());
+  ctx->launches += 2;
+  ZBuf LB = zbuf(ctx, 1, c2 * d2 * q), RB = zbuf(ctx, 2, c2 * d2 * q);  // reuse (T, C^T no longer needed)
+  ZBuf LBp = zbuf(ctx, 4, c2 * d2 * q), RBp = zbuf(ctx, 5, c2 * d2 * q), R4 = zbuf(ctx, 0, d2 * d2);
+  if (!R4.re) return fail(HS_ERR_CUDA, "workspace allocation failed");
+  HS_TRY(zgemm(ctx, dense_gemm(c2, d2 * q, q * q * q), L2p, a1, LB));                           // LB[(b,t)|(s,s',m)]
+  HS_TRY(zgemm(ctx, dense_gemm(c2, d2 * q, q * q * q), L2p, a2, RB));                           // RB[(t,b)|(s,s',m)]
+  HS_TRY(zpermute(ctx, dense({chi, chi, d, d, q}), dense({d, d, chi, chi, q}), {2, 3, 0, 1, 4}, LB, LBp));
+  HS_TRY(zpermute(ctx, dense({chi, chi, d, d, q}), dense({d, d, chi, chi, q}), {2, 3, 1, 0, 4}, RB, RBp));
+  HS_TRY(zgemm(ctx, dense_gemm(d2, d2, c2 * q), LBp, RBp, R4));                                 // rho4
+  finish_rho_c_kernel<<<1, 256, 0, s>>>(R4.re, R4.im, d, h, out, tr_out);
+  HS_CUDA(cudaGetLastError());
+  ctx->launches += 1;
+  return HS_OK;
+}
 
 // Shared forward chain of the two-site network up to the half-network blocks:
 // on return r[8] = Z2 [(l,u,t')|(d,b')], r[9] = Z2p [(t',b')|(l,u,d)],
@@ -235,10 +393,15 @@ extern "C" hs_status hs_rdm(hs_ctx ctx, const hs_env* env, const double* A, int 
                             double* tr_out) {
   HS_TRY(check_ctx(ctx));
   if (!env || !A || !out || d <= 0 || D != env->D) return fail(HS_ERR_INVALID_ARG, "bad arguments");
-  if (dtype != HS_F64) return fail(HS_ERR_UNSUPPORTED, "complex tensors are not supported by this build");
+  if (dtype != HS_F64 && dtype != HS_C128) return fail(HS_ERR_DTYPE, "unknown dtype");
   if (kind != HS_RDM_TWO_SITE && kind != HS_RDM_ENV_ONE_SITE)
     return fail(HS_ERR_INVALID_ARG, "unknown rdm kind");
   if (kind == HS_RDM_TWO_SITE && !tr_out) return fail(HS_ERR_INVALID_ARG, "tr_out is required");
+  if ((dtype == HS_C128) != (env->dtype == HS_C128)) return fail(HS_ERR_DTYPE, "A and environment disagree on dtype");
+  if (dtype == HS_C128) {
+    if (kind != HS_RDM_TWO_SITE) return fail(HS_ERR_UNSUPPORTED, "complex one-site environment not in this build");
+    return rdm_complex(ctx, env, A, d, D, h, out, tr_out);
+  }
   HS_TRY(rdm_chain(ctx, env, A, d, D, kind, out));
   if (kind == HS_RDM_ENV_ONE_SITE) return HS_OK;
   finish_rho_kernel<<<1, 256, 0, ctx->stream>>>(ctx->r[6].d(), d, env->basis == HS_BASIS_HERMITIAN, h, out,

@@ -312,7 +312,70 @@ __global__ void env_to_dense_kernel(const double* __restrict__ C, const double* 
   }
 }
 
+// Graded environment (complex path) -> interleaved complex dense views in the
+// plain combined basis: C[a, b] and T[a, x, b] with x = i + D * ibar; an entry
+// of odd total parity is i times the stored number.
+__global__ void env_to_dense_graded_kernel(const double* __restrict__ C, const double* __restrict__ T, int D,
+                                           int c0, int c1, double* __restrict__ Cd, double* __restrict__ Td) {
+  const int q = D * D, chi = c0 + c1;
+  const int qe = D * (D + 1) / 2, qo = q - qe;
+  const Fused fr = fused2(make_sect(c0, c1), make_sect(qe, qo));
+  const long long f0 = fused_size(fr, 0);
+  const long long nT = (long long)chi * q * chi, nC = (long long)chi * chi;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < nT + nC;
+       e += (long long)gridDim.x * blockDim.x) {
+    if (e >= nT) {
+      const long long f = e - nT;
+      const int a = (int)(f / chi), b = (int)(f % chi);
+      const double v = C[f];
+      const bool odd = (a >= c0) != (b >= c0);
+      Cd[2 * f] = odd ? 0.0 : v;
+      Cd[2 * f + 1] = odd ? v : 0.0;
+      continue;
+    }
+    const int b = (int)(e % chi), x = (int)((e / chi) % q), a = (int)(e / chi / q);
+    const int pa = a >= c0, pb = b >= c0;
+    int nX = 1, X[2];
+    double w[2];
+    const int i = x % D, ib = x / D;
+    if (i == ib) {
+      X[0] = i;
+      w[0] = 1.0;
+    } else {
+      const int k = min(i, ib), l = max(i, ib);
+      const int m = pair_index(k, l, D);
+      const double r = 0.70710678118654752440;
+      nX = 2;
+      X[0] = D + m;
+      w[0] = r;
+      X[1] = qe + m;
+      w[1] = (i < ib) ? r : -r;
+    }
+    double re = 0.0, im = 0.0;
+    for (int t = 0; t < nX; ++t) {
+      const int px = X[t] >= qe;
+      const int tt = (pa << 1) | px;
+      const long long row = ((pa ^ px) ? f0 : 0) + tuple_offset(fr, tt) +
+                            (long long)(a - pa * c0) * (px ? qo : qe) + (X[t] - px * qe);
+      const double v = w[t] * T[row * chi + b];
+      if ((pa + px + pb) & 1)
+        im += v;
+      else
+        re += v;
+    }
+    Td[2 * e] = re;
+    Td[2 * e + 1] = im;
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_env_to_dense_graded(const double* C, const double* T, int D, int c0, int c1, double* Cd,
+                                       double* Td, cudaStream_t s) {
+  const long long chi = c0 + c1, q = (long long)D * D;
+  env_to_dense_graded_kernel<<<grid_for(chi * q * chi + chi * chi), 256, 0, s>>>(C, T, D, c0, c1, Cd, Td);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_ctmrg_init(const double* a_blocks, int D, bool hermitian, double* C, double* T,
                               cudaStream_t s) {

@@ -110,6 +110,50 @@ __global__ void double_layer_blocks_kernel(const double* __restrict__ A, int d, 
   }
 }
 
+// Complex A (interleaved complex128): a~ in the eigenbasis of S as a graded
+// [(u,l)|(d,r)] matrix (Sec. II.C): the real part of every even-total entry,
+// the imaginary part of every odd-total one (the other part vanishes).
+__global__ void double_layer_graded_kernel(const double* __restrict__ A, int d, int D, double* __restrict__ out) {
+  const int q = D * D;
+  const int qe = D * (D + 1) / 2, qo = q - qe;
+  const Fused f = fused2(make_sect(qe, qo), make_sect(qe, qo));
+  const long long f0 = fused_size(f, 0);
+  const long long total = (long long)q * q * q * q;
+  const long long D4 = (long long)D * D * D * D;
+  const long long q2 = (long long)q * q;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int Xr = (int)(e % q), Xd = (int)((e / q) % q), Xl = (int)((e / q / q) % q),
+              Xu = (int)(e / q / q / q);
+    const int pu = Xu >= qe, pl = Xl >= qe, pd = Xd >= qe, pr = Xr >= qe;
+    const long long row = ((pu ^ pl) ? f0 : 0) + tuple_offset(f, (pu << 1) | pl) +
+                          (long long)(Xu - pu * qe) * (pl ? qo : qe) + (Xl - pl * qe);
+    const long long col = ((pd ^ pr) ? f0 : 0) + tuple_offset(f, (pd << 1) | pr) +
+                          (long long)(Xd - pd * qe) * (pr ? qo : qe) + (Xr - pr * qe);
+    const Terms tu = basis_terms(Xu, D, true), tl = basis_terms(Xl, D, true), td = basis_terms(Xd, D, true),
+                tr = basis_terms(Xr, D, true);
+    double re = 0.0, im = 0.0;
+    for (int a = 0; a < tu.n; ++a)
+      for (int b = 0; b < tl.n; ++b)
+        for (int c = 0; c < td.n; ++c)
+          for (int g = 0; g < tr.n; ++g) {
+            const double coef = tu.c[a] * tl.c[b] * td.c[c] * tr.c[g];
+            const long long ik = (((long long)tu.ket[a] * D + tl.ket[b]) * D + td.ket[c]) * D + tr.ket[g];
+            const long long ib = (((long long)tu.bra[a] * D + tl.bra[b]) * D + td.bra[c]) * D + tr.bra[g];
+            double sr = 0.0, si = 0.0;
+            for (int p = 0; p < d; ++p) {
+              const double kr = A[2 * (p * D4 + ik)], ki = A[2 * (p * D4 + ik) + 1];
+              const double br = A[2 * (p * D4 + ib)], bi = A[2 * (p * D4 + ib) + 1];
+              sr += kr * br + ki * bi;  // ket * conj(bra)
+              si += ki * br - kr * bi;
+            }
+            re += coef * sr;
+            im += coef * si;
+          }
+    out[row * q2 + col] = ((pu + pl + pd + pr) & 1) ? im : re;
+  }
+}
+
 __global__ void double_layer_dense_kernel(const double* __restrict__ A, int d, int D, bool cplx,
                                           double* __restrict__ out) {
   const int q = D * D;
@@ -184,6 +228,14 @@ cudaError_t launch_double_layer_blocks(const double* A, int d, int D, bool hermi
                                        cudaStream_t s) {
   const long long q = (long long)D * D;
   double_layer_blocks_kernel<<<grid_for(q * q * q * q), 256, 0, s>>>(A, d, D, hermitian, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_double_layer_graded(const double* A, int d, int D, double* out, cudaStream_t s) {
+  const long long q = (long long)D * D, total = q * q * q * q;
+  long long g = (total + 255) / 256;
+  if (g > 4096) g = 4096;
+  double_layer_graded_kernel<<<(unsigned)g, 256, 0, s>>>(A, d, D, out);
   return cudaGetLastError();
 }
 

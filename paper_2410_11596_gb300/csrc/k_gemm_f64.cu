@@ -1,6 +1,7 @@
 // Grouped FP64 GEMM (DFMA) for the block contractions in FP64 mode:
-// C[m, n] = alpha * sum_k A[m, k] B[n, k], both operands K-major (row-major
-// M x K and N x K). One CTA per 64 x 64 output tile of any problem of the group.
+// C[m, n] = alpha * sum_k A[m, k] B[n, k] (+ C[m, n] when accumulating), both
+// operands K-major (row-major M x K and N x K). One CTA per 64 x 64 output
+// tile of any problem of the group.
 #include "hs_internal.cuh"
 
 namespace hs {
@@ -21,8 +22,8 @@ struct SplitK {
 
 __global__ void __launch_bounds__(NT) gemm_f64_nt_kernel(GemmGroup g, const double* __restrict__ A,
                                                          const double* __restrict__ B,
-                                                         double* __restrict__ C, double alpha, SplitK sk,
-                                                         double* __restrict__ part) {
+                                                         double* __restrict__ C, double alpha, bool accumulate,
+                                                         SplitK sk, double* __restrict__ part) {
   int t = blockIdx.x / sk.nsplit;
   const int split = blockIdx.x % sk.nsplit;
   int pi = 0;
@@ -89,13 +90,16 @@ __global__ void __launch_bounds__(NT) gemm_f64_nt_kernel(GemmGroup g, const doub
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const int gn = n0 + tx + 16 * j;
-      if (gn < P.N) out[(long long)gm * ld + gn] = alpha * acc[i][j];
+      if (gn < P.N) {
+        double& o = out[(long long)gm * ld + gn];
+        o = (accumulate && sk.nsplit == 1) ? o + alpha * acc[i][j] : alpha * acc[i][j];
+      }
     }
   }
 }
 
 __global__ void splitk_reduce_kernel(GemmGroup g, SplitK sk, const double* __restrict__ part,
-                                     double* __restrict__ C) {
+                                     double* __restrict__ C, bool accumulate) {
   for (int pi = 0; pi < g.n; ++pi) {
     const GemmProblem P = g.p[pi];
     const long long mn = (long long)P.M * P.N;
@@ -104,14 +108,15 @@ __global__ void splitk_reduce_kernel(GemmGroup g, SplitK sk, const double* __res
          e += (long long)gridDim.x * blockDim.x) {
       double v = 0.0;
       for (int s = 0; s < sk.nsplit; ++s) v += src[s * mn + e];
-      C[P.c_off + (e / P.N) * P.ldc + (e % P.N)] = v;
+      double& o = C[P.c_off + (e / P.N) * P.ldc + (e % P.N)];
+      o = accumulate ? o + v : v;
     }
   }
 }
 }  // namespace
 
 cudaError_t launch_gemm_f64(const GemmGroup& g, const double* A, const double* B, double* C,
-                            double alpha, cudaStream_t s, double* part, long long part_elems) {
+                            double alpha, cudaStream_t s, double* part, long long part_elems, bool accumulate) {
   long long tiles = 0;
   int kmax = 0;
   for (int i = 0; i < g.n; ++i) {
@@ -140,13 +145,13 @@ cudaError_t launch_gemm_f64(const GemmGroup& g, const double* A, const double* B
       }
     }
   }
-  gemm_f64_nt_kernel<<<(unsigned)(tiles * sk.nsplit), NT, 0, s>>>(g, A, B, C, alpha, sk, part);
+  gemm_f64_nt_kernel<<<(unsigned)(tiles * sk.nsplit), NT, 0, s>>>(g, A, B, C, alpha, accumulate, sk, part);
   if (sk.nsplit > 1) {
     long long mn = 0;
     for (int i = 0; i < g.n; ++i) mn = (long long)g.p[i].M * g.p[i].N > mn ? (long long)g.p[i].M * g.p[i].N : mn;
     long long gx = (mn + 255) / 256;
     if (gx > 4096) gx = 4096;
-    splitk_reduce_kernel<<<(unsigned)gx, 256, 0, s>>>(g, sk, part, C);
+    splitk_reduce_kernel<<<(unsigned)gx, 256, 0, s>>>(g, sk, part, C, accumulate);
   }
   return cudaGetLastError();
 }

@@ -7,14 +7,24 @@
 //     TF32x3 : acc_main += A_hi B_hi ; acc_corr += A_hi B_lo + A_lo B_hi  (tf32 hi, fp32 lo)
 //     TF32   : acc_main += A_hi B_hi
 //     BF16x3 : as TF32x3 with a bf16 hi/lo split
-//   C = (double)acc_main + (double)acc_corr
+//   C = (double)acc_main + (double)acc_corr, widened on the bit patterns
+// The small cross terms get their own accumulator: folded into the main one
+// they lose their low bits to its (truncating) accumulation, about a tenth of
+// the accuracy gain of the extra passes on K = 512.
 //
 // CTA tile 128 x 128, K step 128 bytes (one 128-byte swizzle atom per row).
-// Warp 0 lane 0 issues the TMA loads, warp 1 lane 0 issues tcgen05.mma, all
-// four warps drain TMEM in the epilogue (warp w owns TMEM lanes 32w..32w+31).
-// Operand tiles are loaded by TMA with 128-byte swizzle into a multi-stage
-// ring guarded by mbarriers (full: TMA bytes landed; empty: MMAs that read the
-// stage have completed, signalled by tcgen05.commit).
+// The kernel is persistent: one CTA per SM walks the output tiles
+// (blockIdx.x, + gridDim.x, ...). Warp roles:
+//   warp 0 lane 0   TMA producer: operand tiles into a multi-stage shared ring
+//                   (128-byte swizzle), across tile boundaries;
+//   warp 1 lane 0   MMA issuer: tcgen05.mma into one of two TMEM accumulator
+//                   buffers, so that tile i+1 accumulates while tile i drains;
+//   warps 2..5      epilogue: TMEM -> registers -> FP64, staged through shared
+//                   memory so that each warp store writes 32 consecutive
+//                   doubles of one row (warp w reads TMEM lanes 32(w%4)...).
+// mbarriers: full (TMA bytes landed), empty (MMAs that read the stage are
+// done, via tcgen05.commit), tfull (accumulator ready), tempty (the four
+// epilogue warps have read the accumulator).
 //
 // Every wait is bounded. A wait that gives up sets *err and an abort flag in
 // shared memory; the other roles then stop, the kernel drains what it issued
@@ -25,13 +35,14 @@
 #include <cstdint>
 #include <mutex>
 
+#include "hs_bits.cuh"
 #include "hs_internal.cuh"
 
 namespace hs {
 
 namespace {
 
-constexpr int BM = 128, BN = 128, NT = 128;
+constexpr int BM = 128, BN = 128, NT = 192;
 constexpr int ROW_BYTES = 128;
 constexpr int TILE_BYTES = BM * ROW_BYTES;  // BN == BM
 constexpr long long WAIT_LIMIT = 20000000;  // try_wait rounds before giving up (seconds)
@@ -169,34 +180,50 @@ template <int NPASS, int EB>
 struct Cfg {
   static constexpr int TILES = NPASS == 1 ? 2 : 4;  // A_hi, B_hi (+ A_lo, B_lo)
   static constexpr int STAGE_BYTES = TILES * TILE_BYTES;
-  static constexpr int STAGES = NPASS == 1 ? 6 : 3;
-  static constexpr uint32_t TMEM_COLS = NPASS == 1 ? BN : 2 * BN;
-  static constexpr int K_PER_TILE = ROW_BYTES / EB;  // elements per 128-byte row
-  static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 + 256;
+  static constexpr int STAGES = NPASS == 1 ? 5 : 3;
+  static constexpr uint32_t ACC_COLS = NPASS == 1 ? BN : 2 * BN;  // one accumulator buffer
+  static constexpr uint32_t TMEM_COLS = 2 * ACC_COLS;              // double buffered
+  static constexpr int K_PER_TILE = ROW_BYTES / EB;                // elements per 128-byte row
+  static constexpr int STG_LD = 33;                                // staging row stride (doubles)
+  static constexpr int STG_BYTES = 4 * 32 * STG_LD * 8;            // one 32 x 32 block per epilogue warp
+  static constexpr int BAR_BYTES = 256;
+  static constexpr int SMEM = STAGES * STAGE_BYTES + STG_BYTES + BAR_BYTES + 1024;
+  static_assert(SMEM <= 232448, "shared memory per CTA");
+  static_assert(2 * STAGES + 6 <= BAR_BYTES / 8 - 2, "barrier area");
 };
+
+// Output tile t of the launch: its unit and corner.
+struct TileRef {
+  int pi, m0, n0;
+};
+
+__device__ __forceinline__ TileRef tile_of(const Group& g, int t) {
+  int pi = 0;
+  while (pi + 1 < g.n && t >= g.p[pi + 1].tile_start) ++pi;
+  t -= g.p[pi].tile_start;
+  return {pi, (t / g.p[pi].tiles_n) * BM, (t % g.p[pi].tiles_n) * BN};
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
 
 template <int NPASS, int EB>
 __global__ void __launch_bounds__(NT, 1) gemm_tc_kernel(const __grid_constant__ Maps maps, const Group g,
-                                                        int* __restrict__ err) {
+                                                        int total_tiles, int* __restrict__ err) {
   using K = Cfg<NPASS, EB>;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + K::STAGES * K::STAGE_BYTES);
+  double* stage_c = reinterpret_cast<double*>(smem + K::STAGES * K::STAGE_BYTES);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + K::STAGES * K::STAGE_BYTES + K::STG_BYTES);
   uint64_t* empty = full + K::STAGES;
-  uint64_t* accum = empty + K::STAGES;
-  uint64_t* drain = accum + 1;
+  uint64_t* tfull = empty + K::STAGES;   // [2]
+  uint64_t* tempty = tfull + 2;          // [2]
+  uint64_t* drain = tempty + 2;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  int t = blockIdx.x;
-  int pi = 0;
-  while (pi + 1 < g.n && t >= g.p[pi + 1].tile_start) ++pi;
-  const Prob P = g.p[pi];
-  const int mi = P.map;
-  t -= P.tile_start;
-  const int m0 = (t / P.tiles_n) * BM, n0 = (t % P.tiles_n) * BN;
-  const int ktiles = P.Kp / K::K_PER_TILE;
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
@@ -209,7 +236,10 @@ __global__ void __launch_bounds__(NT, 1) gemm_tc_kernel(const __grid_constant__ 
       mbar_init(smem_u32(&full[s]), 1);
       mbar_init(smem_u32(&empty[s]), 1);
     }
-    mbar_init(smem_u32(accum), 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(smem_u32(&tfull[b]), 1);
+      mbar_init(smem_u32(&tempty[b]), 4);
+    }
     mbar_init(smem_u32(drain), 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -220,106 +250,149 @@ __global__ void __launch_bounds__(NT, 1) gemm_tc_kernel(const __grid_constant__ 
   const uint32_t tmem = *tmem_slot;
 
   if (warp == 0 && lane == 0) {
-    // ---- TMA producer ----
-    const CUtensorMap* mA0 = &maps.a[mi][0];
-    const CUtensorMap* mA1 = &maps.a[mi][1];
-    const CUtensorMap* mB0 = &maps.b[mi][0];
-    const CUtensorMap* mB1 = &maps.b[mi][1];
-    int issued = 0;
-    for (int kt = 0; kt < ktiles; ++kt) {
-      const int s = kt % K::STAGES, n = kt / K::STAGES;
-      if (n > 0 && !mbar_wait(smem_u32(&empty[s]), (n - 1) & 1, abort_flag, err, 1)) break;
-      if (*abort_flag) break;
-      const uint32_t fb = smem_u32(&full[s]);
-      mbar_expect_tx(fb, K::STAGE_BYTES);
-      const uint32_t st = smem_u32(smem + s * K::STAGE_BYTES);
-      const int kc = P.k0 + kt * K::K_PER_TILE;
-      tma_load_2d(st, mA0, kc, m0, fb);
-      tma_load_2d(st + TILE_BYTES, mB0, kc, n0, fb);
-      if (NPASS == 3) {
-        tma_load_2d(st + 2 * TILE_BYTES, mA1, kc, m0, fb);
-        tma_load_2d(st + 3 * TILE_BYTES, mB1, kc, n0, fb);
+    // ---- TMA producer: every K step of every tile of this CTA ----
+    long long it = 0;
+    for (int t = blockIdx.x; t < total_tiles && !*abort_flag; t += gridDim.x) {
+      const TileRef r = tile_of(g, t);
+      const Prob& P = g.p[r.pi];
+      const CUtensorMap* mA0 = &maps.a[P.map][0];
+      const CUtensorMap* mA1 = &maps.a[P.map][1];
+      const CUtensorMap* mB0 = &maps.b[P.map][0];
+      const CUtensorMap* mB1 = &maps.b[P.map][1];
+      const int ktiles = P.Kp / K::K_PER_TILE;
+      for (int kt = 0; kt < ktiles; ++kt) {
+        const int s = (int)(it % K::STAGES);
+        const long long n = it / K::STAGES;
+        if (n > 0 && !mbar_wait(smem_u32(&empty[s]), (uint32_t)((n - 1) & 1), abort_flag, err, 1)) break;
+        if (*abort_flag) break;
+        const uint32_t fb = smem_u32(&full[s]);
+        mbar_expect_tx(fb, K::STAGE_BYTES);
+        const uint32_t st = smem_u32(smem + s * K::STAGE_BYTES);
+        const int kc = P.k0 + kt * K::K_PER_TILE;
+        tma_load_2d(st, mA0, kc, r.m0, fb);
+        tma_load_2d(st + TILE_BYTES, mB0, kc, r.n0, fb);
+        if (NPASS == 3) {
+          tma_load_2d(st + 2 * TILE_BYTES, mA1, kc, r.m0, fb);
+          tma_load_2d(st + 3 * TILE_BYTES, mB1, kc, r.n0, fb);
+        }
+        ++it;
       }
-      issued = kt + 1;
     }
     if (*abort_flag) {
-      // let every issued copy land before the CTA can exit
-      for (int kt = 0; kt < issued; ++kt) mbar_drain(smem_u32(&full[kt % K::STAGES]), (kt / K::STAGES) & 1);
+      // copies still in flight sit in the last STAGES issued steps (earlier
+      // ones were consumed); let them land before the CTA can exit
+      for (long long j = it > K::STAGES ? it - K::STAGES : 0; j < it; ++j)
+        mbar_drain(smem_u32(&full[j % K::STAGES]), (uint32_t)((j / K::STAGES) & 1));
     }
   } else if (warp == 1 && lane == 0) {
     // ---- MMA issuer ----
+    long long it = 0;
     bool any = false;
-    for (int kt = 0; kt < ktiles; ++kt) {
-      const int s = kt % K::STAGES, n = kt / K::STAGES;
-      if (!mbar_wait(smem_u32(&full[s]), n & 1, abort_flag, err, 2)) break;
+    int local = 0;
+    for (int t = blockIdx.x; t < total_tiles && !*abort_flag; t += gridDim.x, ++local) {
+      const TileRef r = tile_of(g, t);
+      const int ktiles = g.p[r.pi].Kp / K::K_PER_TILE;
+      const int buf = local & 1, use = local >> 1;
+      if (use > 0 && !mbar_wait(smem_u32(&tempty[buf]), (uint32_t)((use - 1) & 1), abort_flag, err, 4)) break;
       fence_after();
-      const uint32_t st = smem_u32(smem + s * K::STAGE_BYTES);
-      const uint64_t a_hi = sdesc(st), b_hi = sdesc(st + TILE_BYTES);
-      const uint64_t a_lo = sdesc(st + 2 * TILE_BYTES), b_lo = sdesc(st + 3 * TILE_BYTES);
-#pragma unroll
-      for (int kk = 0; kk < ROW_BYTES / 32; ++kk) {
-        const uint64_t off = (uint64_t)((kk * 32) >> 4);
-        const uint32_t acc = (kt | kk) != 0;
-        mma<EB>(tmem, a_hi + off, b_hi + off, acc);
-        if (NPASS == 3) {
-          mma<EB>(tmem + BN, a_hi + off, b_lo + off, acc);
-          mma<EB>(tmem + BN, a_lo + off, b_hi + off, 1);
+      const uint32_t d = tmem + (uint32_t)buf * K::ACC_COLS;
+      bool ok = true;
+      for (int kt = 0; kt < ktiles; ++kt) {
+        const int s = (int)(it % K::STAGES);
+        const long long n = it / K::STAGES;
+        if (!mbar_wait(smem_u32(&full[s]), (uint32_t)(n & 1), abort_flag, err, 2)) {
+          ok = false;
+          break;
         }
-      }
-      any = true;
-      mma_commit(smem_u32(&empty[s]));
-    }
-    if (*abort_flag) {
-      if (any) {
-        mma_commit(smem_u32(drain));
-        mbar_drain(smem_u32(drain), 0);
-      }
-    } else {
-      mma_commit(smem_u32(accum));
-    }
-  }
-
-  // ---- epilogue: TMEM -> registers -> FP64 global ----
-  bool ok = mbar_wait(smem_u32(accum), 0, abort_flag, err, 3);
-  __syncwarp();
-  ok = __all_sync(0xffffffffu, ok);
-  fence_after();
-  if (ok && ktiles == 0) {
-    // empty K range: the accumulator was never written, the product is zero
-    const int row = m0 + warp * 32 + lane;
-    if (row < P.M)
-      for (int c = 0; c < BN && n0 + c < P.N; ++c) P.c[(long long)row * P.ldc + n0 + c] = 0.0;
-    ok = false;
-  }
-  if (ok) {
-    const int row = m0 + warp * 32 + lane;
-    double* crow = P.c + (long long)row * P.ldc;
-    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
-    for (int c = 0; c < BN; c += 32) {
-      if (n0 + c >= P.N) break;  // warp-uniform
-      uint32_t r0[32], r1[32];
-      tmem_ld32(tmem + lane_base + c, r0);
-      if (NPASS == 3) tmem_ld32(tmem + lane_base + BN + c, r1);
-      tmem_wait_ld();
-      if (row < P.M) {
+        fence_after();
+        const uint32_t st = smem_u32(smem + s * K::STAGE_BYTES);
+        const uint64_t a_hi = sdesc(st), b_hi = sdesc(st + TILE_BYTES);
+        const uint64_t a_lo = sdesc(st + 2 * TILE_BYTES), b_lo = sdesc(st + 3 * TILE_BYTES);
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const int col = n0 + c + j;
-          if (col < P.N) {
-            double v = (double)__uint_as_float(r0[j]);
-            if (NPASS == 3) v += (double)__uint_as_float(r1[j]);
-            crow[col] = v;
+        for (int kk = 0; kk < ROW_BYTES / 32; ++kk) {
+          const uint64_t off = (uint64_t)((kk * 32) >> 4);
+          const uint32_t acc = (kt | kk) != 0;
+          mma<EB>(d, a_hi + off, b_hi + off, acc);
+          if (NPASS == 3) {
+            mma<EB>(d + BN, a_hi + off, b_lo + off, acc);
+            mma<EB>(d + BN, a_lo + off, b_hi + off, 1);
           }
         }
+        any = true;
+        mma_commit(smem_u32(&empty[s]));
+        ++it;
       }
+      if (!ok) break;
+      mma_commit(smem_u32(&tfull[buf]));  // arrives once this tile's MMAs are done
+    }
+    if (*abort_flag && any) {
+      mma_commit(smem_u32(drain));
+      mbar_drain(smem_u32(drain), 0);
+    }
+  } else if (warp >= 2) {
+    // ---- epilogue: TMEM -> registers -> shared staging -> coalesced FP64 stores ----
+    const int q = warp & 3;  // TMEM lane quarter this warp may read
+    double* stg = stage_c + q * 32 * K::STG_LD;
+    const uint32_t lane_base = (uint32_t)(q * 32) << 16;
+    int local = 0;
+    for (int t = blockIdx.x; t < total_tiles; t += gridDim.x, ++local) {
+      const TileRef r = tile_of(g, t);
+      const Prob& P = g.p[r.pi];
+      const int ktiles = P.Kp / K::K_PER_TILE;
+      const int buf = local & 1, use = local >> 1;
+      bool ok = mbar_wait(smem_u32(&tfull[buf]), (uint32_t)(use & 1), abort_flag, err, 3);
+      ok = __all_sync(0xffffffffu, ok);
+      if (!ok) break;
+      fence_after();
+      const uint32_t d = tmem + (uint32_t)buf * K::ACC_COLS + lane_base;
+      const int row0 = r.m0 + q * 32;
+      for (int c = 0; c < BN && r.n0 + c < P.N; c += 32) {
+        if (ktiles > 0) {
+          uint32_t r0[32], r1[32];
+          tmem_ld32(d + c, r0);
+          if (NPASS == 3) tmem_ld32(d + BN + c, r1);
+          tmem_wait_ld();
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            unsigned long long w;
+            if (!f32_widen_fast(r0[j], w)) w = f64_bits((double)__uint_as_float(r0[j]));  // subnormal
+            double v = f64_from_bits(w);
+            if (NPASS == 3) {
+              if (!f32_widen_fast(r1[j], w)) w = f64_bits((double)__uint_as_float(r1[j]));
+              v += f64_from_bits(w);
+            }
+            stg[lane * K::STG_LD + j] = v;
+          }
+        } else {
+          // empty K range: the accumulator was never written, the product is zero
+#pragma unroll
+          for (int j = 0; j < 32; ++j) stg[lane * K::STG_LD + j] = 0.0;
+        }
+        __syncwarp();
+        const int col = r.n0 + c + lane;
+        if (col < P.N) {
+          for (int i = 0; i < 32; ++i) {
+            const int row = row0 + i;
+            if (row >= P.M) break;
+            P.c[(long long)row * P.ldc + col] = stg[i * K::STG_LD + lane];
+          }
+        }
+        __syncwarp();
+      }
+      // this warp is done reading the accumulator buffer
+      fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&tempty[buf]));
     }
   }
   fence_before();
   __syncthreads();
   fence_after();
-  if (warp == 0)
+  if (warp == 0) {
+    __syncwarp();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(K::TMEM_COLS)
                  : "memory");
+  }
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
@@ -434,7 +507,14 @@ cudaError_t run(const TcProblem* probs, int nprob, int* err, cudaStream_t s, dou
     }
   }
   if (tiles == 0) return cudaSuccess;
-  gemm_tc_kernel<NPASS, EB><<<tiles, NT, K::SMEM, s>>>(maps, g, err);
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 148;
+  }
+  const int grid = tiles < sms ? tiles : sms;
+  gemm_tc_kernel<NPASS, EB><<<grid, NT, K::SMEM, s>>>(maps, g, tiles, err);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   for (int r = 0; r < nred; ++r) {

@@ -1,7 +1,8 @@
 // Host-side planning of FSO permutations and block GEMMs (Z2 bookkeeping,
 // arXiv 2410.11596 Sec. II.B), plus the generic permute kernel.
-#include <cuda_bf16.h>
+#include <cstdint>
 
+#include "hs_bits.cuh"
 #include "hs_internal.cuh"
 
 namespace hs {
@@ -63,12 +64,101 @@ PermPlan make_perm_plan(const Z2Mat& in, const Z2Mat& out, const int* perm) {
       b.count *= b.dim[pad + j];
     }
     if (b.count == 0) continue;
+    for (int j = 0; j < kMaxLegs; ++j) fast_div_magic((unsigned)b.dim[j], &b.mag[j], &b.sh1[j], &b.sh2[j]);
     b.start = start;
     start += b.count;
     plan.box[plan.nbox++] = b;
   }
   plan.total = start;
   return plan;
+}
+
+namespace {
+
+// Strides of each leg of a graded matrix inside the parity tuple `par`.
+void graded_leg_strides(const GMat& m, const int* par, long long* stride, long long* off) {
+  int tr = 0, tc = 0;
+  for (int j = 0; j < m.r.k; ++j) tr = (tr << 1) | par[j];
+  for (int j = 0; j < m.c.k; ++j) tc = (tc << 1) | par[m.r.k + j];
+  const long long ld = g_ld(m);
+  const long long row = g_row0(m, tuple_parity(tr)) + tuple_offset(m.r, tr);
+  const long long col = g_col0(m, tuple_parity(tc)) + tuple_offset(m.c, tc);
+  *off = row * ld + col;
+  long long s = ld;
+  for (int j = m.r.k - 1; j >= 0; --j) {
+    stride[j] = s;
+    s *= m.r.leg[j].n[par[j]];
+  }
+  s = 1;
+  for (int j = m.c.k - 1; j >= 0; --j) {
+    stride[m.r.k + j] = s;
+    s *= m.c.leg[j].n[par[m.r.k + j]];
+  }
+}
+
+Sect gleg_of(const GMat& m, int j) { return j < m.r.k ? m.r.leg[j] : m.c.leg[j - m.r.k]; }
+
+}  // namespace
+
+bool make_graded_perm_plan(const GMat& in, const GMat& out, const int* perm, PermPlan* plan_out) {
+  PermPlan plan{};
+  const int n = out.r.k + out.c.k;
+  if (n > kMaxLegs || (1 << n) > kMaxBoxes) return false;
+  long long start = 0;
+  for (int bits = 0; bits < (1 << n); ++bits) {
+    int pout[kMaxLegs] = {0}, pin[kMaxLegs] = {0};
+    for (int j = 0; j < n; ++j) {
+      pout[j] = (bits >> (n - 1 - j)) & 1;
+      pin[perm[j]] = pout[j];
+    }
+    long long ostr[kMaxLegs], istr_leg[kMaxLegs], ooff, ioff;
+    graded_leg_strides(out, pout, ostr, &ooff);
+    graded_leg_strides(in, pin, istr_leg, &ioff);
+    Box b{};
+    b.out_off = ooff;
+    b.in_off = ioff;
+    b.count = 1;
+    const int pad = kMaxLegs - n;
+    for (int j = 0; j < kMaxLegs; ++j) {
+      b.dim[j] = 1;
+      b.out_stride[j] = 0;
+      b.in_stride[j] = 0;
+    }
+    for (int j = 0; j < n; ++j) {
+      b.dim[pad + j] = gleg_of(out, j).n[pout[j]];
+      b.out_stride[pad + j] = ostr[j];
+      b.in_stride[pad + j] = istr_leg[perm[j]];
+      b.count *= b.dim[pad + j];
+    }
+    if (b.count == 0) continue;
+    for (int j = 0; j < kMaxLegs; ++j) fast_div_magic((unsigned)b.dim[j], &b.mag[j], &b.sh1[j], &b.sh2[j]);
+    b.start = start;
+    start += b.count;
+    plan.box[plan.nbox++] = b;
+  }
+  plan.total = start;
+  *plan_out = plan;
+  return true;
+}
+
+GemmGroup make_graded_gemm(const GMat& A, const GMat& B, const GMat& C, long long bconj_off) {
+  GemmGroup g{};
+  for (int pr = 0; pr < 2; ++pr)
+    for (int pc = 0; pc < 2; ++pc) {
+      GemmProblem q{};
+      q.M = (int)fused_size(A.r, pr);
+      q.N = (int)fused_size(B.r, pc);
+      q.K = (int)g_cols(A);
+      if (q.M == 0 || q.N == 0) continue;
+      q.lda = (int)g_ld(A);
+      q.ldb = (int)g_ld(B);
+      q.ldc = (int)g_ld(C);
+      q.a_off = g_row0(A, pr) * g_ld(A);
+      q.b_off = g_row0(B, pc) * g_ld(B) + (pr == pc ? bconj_off : 0);
+      q.c_off = g_row0(C, pr) * g_ld(C) + g_col0(C, pc);
+      g.p[g.n++] = q;
+    }
+  return g;
 }
 
 GemmGroup make_z2_gemm(const Z2Mat& A, const Z2Mat& B, const Z2Mat& C) {
@@ -98,12 +188,25 @@ double gemm_flops(const GemmGroup& g) {
 
 // ---- permute: one dense box per blockIdx.y, grid-stride over its elements ----
 
-__global__ void permute_f64_kernel(PermPlan plan, const double* __restrict__ in,
-                                   double* __restrict__ out, double scale) {
-  const Box& b = plan.box[blockIdx.y];
-  const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < b.count; e += stride) {
-    long long r = e, io = b.in_off, oo = b.out_off;
+// Input and output offsets of element e of box b (row-major over b.dim).
+// Boxes below 2^31 elements decode with 32-bit multiply-high divisions.
+__device__ __forceinline__ void box_offsets(const Box& b, long long e, long long& io, long long& oo) {
+  io = b.in_off;
+  oo = b.out_off;
+  if (b.count < (1ll << 31)) {
+    unsigned r = (unsigned)e;
+#pragma unroll
+    for (int j = kMaxLegs - 1; j > 0; --j) {
+      const unsigned qd = fast_div(r, b.mag[j], b.sh1[j], b.sh2[j]);
+      const unsigned ij = r - qd * (unsigned)b.dim[j];
+      r = qd;
+      io += (long long)ij * b.in_stride[j];
+      oo += (long long)ij * b.out_stride[j];
+    }
+    io += (long long)r * b.in_stride[0];
+    oo += (long long)r * b.out_stride[0];
+  } else {
+    long long r = e;
 #pragma unroll
     for (int j = kMaxLegs - 1; j > 0; --j) {
       const int ij = (int)(r % b.dim[j]);
@@ -113,7 +216,32 @@ __global__ void permute_f64_kernel(PermPlan plan, const double* __restrict__ in,
     }
     io += r * b.in_stride[0];
     oo += r * b.out_stride[0];
-    out[oo] = scale * in[io];
+  }
+}
+
+__global__ void permute_f64_kernel(PermPlan plan, const double* __restrict__ in,
+                                   double* __restrict__ out, double scale) {
+  const Box& b = plan.box[blockIdx.y];
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < b.count; e += stride) {
+    long long io, oo;
+    box_offsets(b, e, io, oo);
+    out[oo] = scale == 1.0 ? in[io] : scale * in[io];  // plain copies keep off the FP64 pipe
+  }
+}
+
+template <int MODE>
+__device__ __forceinline__ void store_split(double x, void* hi, void* lo, long long o) {
+  if (MODE == 1) {
+    uint32_t h, l;
+    split_f64(x, 11, 24, true, h, l);
+    static_cast<uint32_t*>(hi)[o] = h;
+    static_cast<uint32_t*>(lo)[o] = l;
+  } else {
+    uint32_t h, l;
+    split_f64(x, 8, 8, false, h, l);
+    static_cast<unsigned short*>(hi)[o] = (unsigned short)(h >> 16);
+    static_cast<unsigned short*>(lo)[o] = (unsigned short)(l >> 16);
   }
 }
 
@@ -123,27 +251,9 @@ __global__ void permute_split_kernel(PermPlan plan, const double* __restrict__ i
   const Box& b = plan.box[blockIdx.y];
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < b.count; e += stride) {
-    long long r = e, io = b.in_off, oo = b.out_off;
-#pragma unroll
-    for (int j = kMaxLegs - 1; j > 0; --j) {
-      const int ij = (int)(r % b.dim[j]);
-      r /= b.dim[j];
-      io += ij * b.in_stride[j];
-      oo += ij * b.out_stride[j];
-    }
-    io += r * b.in_stride[0];
-    oo += r * b.out_stride[0];
-    const double x = in[io];
-    if (MODE == 1) {
-      float h;
-      asm("cvt.rna.tf32.f32 %0, %1;" : "=f"(h) : "f"((float)x));
-      static_cast<float*>(hi)[oo] = h;
-      static_cast<float*>(lo)[oo] = (float)(x - (double)h);
-    } else {
-      const __nv_bfloat16 h = __float2bfloat16_rn((float)x);
-      static_cast<__nv_bfloat16*>(hi)[oo] = h;
-      static_cast<__nv_bfloat16*>(lo)[oo] = __float2bfloat16_rn((float)(x - (double)__bfloat162float(h)));
-    }
+    long long io, oo;
+    box_offsets(b, e, io, oo);
+    store_split<MODE>(in[io], hi, lo, oo);
   }
 }
 
@@ -170,17 +280,7 @@ __global__ void split_pad_kernel(const double* __restrict__ src, long long rows,
        e += (long long)gridDim.x * blockDim.x) {
     const long long r = e / ld_dst;
     const int c = (int)(e % ld_dst);
-    const double x = c < cols ? src[r * ld_src + c] : 0.0;
-    if (MODE == 1) {
-      float h;
-      asm("cvt.rna.tf32.f32 %0, %1;" : "=f"(h) : "f"((float)x));
-      static_cast<float*>(hi)[e] = h;
-      static_cast<float*>(lo)[e] = (float)(x - (double)h);
-    } else {
-      const __nv_bfloat16 h = __float2bfloat16_rn((float)x);
-      static_cast<__nv_bfloat16*>(hi)[e] = h;
-      static_cast<__nv_bfloat16*>(lo)[e] = __float2bfloat16_rn((float)(x - (double)__bfloat162float(h)));
-    }
+    store_split<MODE>(c < cols ? src[r * ld_src + c] : 0.0, hi, lo, e);
   }
 }
 

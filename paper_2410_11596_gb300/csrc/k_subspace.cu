@@ -197,7 +197,141 @@ __global__ void row_normalize_kernel(double* __restrict__ X, int m, int n) {
     for (int j = threadIdx.x; j < n; j += blockDim.x) X[(long long)i * n + j] /= nrm;
 }
 
+// Symmetric eigen-decomposition of one small FP32 matrix per CTA by the
+// cyclic Jacobi method (Golub and Van Loan, Sec. 8.5) with the round-robin
+// ordering, so that the m/2 rotations of a round touch disjoint rows and
+// columns and are applied together: A <- J^T A J, V <- V J. The Rayleigh
+// matrices of the warm-started subspace iteration are nearly diagonal, where
+// Jacobi converges quadratically in a few sweeps. Output as cuSOLVER's syevd:
+// eigenvalues ascending in w, eigenvectors as the columns of the column-major
+// m x m array A (overwritten). A rotation is skipped when |A_pq| <= tol
+// sqrt|A_pp A_qq|, tol = max(4e-7, sqrt(m) eps_32) (the relative criterion of
+// Demmel and Veselic, SIAM J. Matrix Anal. Appl. 13, 1992); converged after a
+// sweep without rotations.
+// After kMaxSweeps without that, *status = 1.
+constexpr int kMaxSweeps = 40;
+
+__global__ void __launch_bounds__(512) jacobi_eig_kernel(float* __restrict__ A0, int m0, float* __restrict__ w0,
+                                                         float* __restrict__ A1, int m1, float* __restrict__ w1,
+                                                         int* __restrict__ status) {
+  float* Ag = blockIdx.x ? A1 : A0;
+  float* wg = blockIdx.x ? w1 : w0;
+  const int m = blockIdx.x ? m1 : m0;
+  if (m <= 0) return;
+  extern __shared__ float shj[];
+  const int ld = m + 1;
+  float* A = shj;                 // m x ld
+  float* V = A + m * ld;          // m x ld, V[i * ld + j] = component i of vector j
+  float* cs = V + m * ld;         // cos, sin per pair
+  int* pq = reinterpret_cast<int*>(cs + 2 * ((m + 1) / 2 + 1));
+  __shared__ int nrot;
+  const int M = (m + 1) & ~1;     // even player count (index m is a dummy when m is odd)
+  const int npair = M / 2;
+  const float kRelTol = fmaxf(4e-7f, sqrtf((float)m) * 6e-8f);
+  for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+    const int i = e / m, j = e % m;
+    A[i * ld + j] = 0.5f * (Ag[i * m + j] + Ag[j * m + i]);
+    V[i * ld + j] = i == j ? 1.f : 0.f;
+  }
+  __syncthreads();
+  bool converged = false;
+  for (int sweep = 0; sweep < kMaxSweeps && !converged; ++sweep) {
+    if (threadIdx.x == 0) nrot = 0;
+    __syncthreads();
+    for (int r = 0; r < M - 1; ++r) {
+      // round-robin pairing: player M-1 fixed, the others rotate
+      for (int k = threadIdx.x; k < npair; k += blockDim.x) {
+        int p = k == 0 ? M - 1 : (r + k) % (M - 1);
+        int q = (r + M - 1 - k) % (M - 1);
+        if (k == 0) q = r;
+        if (p > q) {
+          const int t = p;
+          p = q;
+          q = t;
+        }
+        float c = 1.f, sn = 0.f;
+        if (q < m) {
+          const float apq = A[p * ld + q];
+          const float app = A[p * ld + p], aqq = A[q * ld + q];
+          // rotate unless A_pq is negligible against its diagonal pair
+          if (fabsf(apq) > 1e-30f && fabsf(apq) > kRelTol * sqrtf(fabsf(app * aqq))) {
+            const float th = (aqq - app) / (2.f * apq);
+            const float t = (th >= 0.f ? 1.f : -1.f) / (fabsf(th) + sqrtf(th * th + 1.f));
+            c = rsqrtf(t * t + 1.f);
+            sn = t * c;
+            atomicAdd(&nrot, 1);
+          }
+        }
+        pq[2 * k] = p;
+        pq[2 * k + 1] = q;
+        cs[2 * k] = c;
+        cs[2 * k + 1] = sn;
+      }
+      __syncthreads();
+      // rows p, q of A: A <- J^T A
+      for (int e = threadIdx.x; e < npair * m; e += blockDim.x) {
+        const int k = e / m, j = e % m;
+        const int p = pq[2 * k], q = pq[2 * k + 1];
+        if (q >= m) continue;
+        const float c = cs[2 * k], sn = cs[2 * k + 1];
+        const float ap = A[p * ld + j], aq = A[q * ld + j];
+        A[p * ld + j] = c * ap - sn * aq;
+        A[q * ld + j] = sn * ap + c * aq;
+      }
+      __syncthreads();
+      // columns p, q of A and V: A <- A J, V <- V J
+      for (int e = threadIdx.x; e < npair * m; e += blockDim.x) {
+        const int k = e / m, i = e % m;
+        const int p = pq[2 * k], q = pq[2 * k + 1];
+        if (q >= m) continue;
+        const float c = cs[2 * k], sn = cs[2 * k + 1];
+        const float ap = A[i * ld + p], aq = A[i * ld + q];
+        A[i * ld + p] = c * ap - sn * aq;
+        A[i * ld + q] = sn * ap + c * aq;
+        const float vp = V[i * ld + p], vq = V[i * ld + q];
+        V[i * ld + p] = c * vp - sn * vq;
+        V[i * ld + q] = sn * vp + c * vq;
+      }
+      __syncthreads();
+    }
+    converged = nrot == 0;  // a sweep without a rotation: every A_pq is negligible
+    __syncthreads();
+  }
+  if (!converged && threadIdx.x == 0) atomicExch(status, 1);
+  // ascending order by rank (ties by index); vectors as columns, column-major
+  for (int j = threadIdx.x; j < m; j += blockDim.x) {
+    const float lj = A[j * ld + j];
+    int rank = 0;
+    for (int i = 0; i < m; ++i) {
+      const float li = A[i * ld + i];
+      rank += (li < lj) || (li == lj && i < j);
+    }
+    wg[rank] = lj;
+    for (int i = 0; i < m; ++i) Ag[(long long)rank * m + i] = V[i * ld + j];
+  }
+}
+
 }  // namespace
+
+size_t jacobi_smem_bytes(int m) {
+  return (size_t)(2 * m * (m + 1) + 2 * ((m + 1) / 2 + 1)) * sizeof(float) + (size_t)((m + 1) / 2 + 1) * 2 * sizeof(int);
+}
+
+cudaError_t launch_jacobi_eig_pair(float* A0, int m0, float* w0, float* A1, int m1, float* w1, int* status,
+                                   cudaStream_t s) {
+  const int m = m0 > m1 ? m0 : m1;
+  if (m <= 0) return cudaSuccess;
+  if (m > kMaxSub) return cudaErrorInvalidValue;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(jacobi_eig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)jacobi_smem_bytes(kMaxSub));
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  jacobi_eig_kernel<<<2, 512, jacobi_smem_bytes(m), s>>>(A0, m0, w0, A1, m1, w1, status);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_row_normalize(double* X, int m, int n, cudaStream_t s) {
   if (m <= 0) return cudaSuccess;

@@ -56,3 +56,18 @@ def golden(k):
 def spectrum_from_corner(C):
     s = np.linalg.svd(C, compute_uv=False)
     return s / s[0]
+
+
+def graded_pack(t, row_sects, col_sects):
+    """Dense graded matrix of hs.h (complex tensors): all rows in FSO order (both parities),
+    all columns likewise; entries of odd total parity give their imaginary part, even ones
+    their real part."""
+    kr, kc = len(row_sects), len(col_sects)
+    R, Cc = fso_order(row_sects, kr), fso_order(col_sects, kc)
+    r = np.concatenate([R[0], R[1]], axis=0)
+    c = np.concatenate([Cc[0], Cc[1]], axis=0)
+    sub = t[tuple(r[:, j][:, None] for j in range(kr)) + tuple(c[:, j][None, :] for j in range(kc))]
+    nr0, nc0 = len(R[0]), len(Cc[0])
+    pr = (np.arange(len(r)) >= nr0)[:, None]
+    pc = (np.arange(len(c)) >= nc0)[None, :]
+    return np.where(pr != pc, np.imag(sub), np.real(sub))
