@@ -253,5 +253,5 @@ def hs_hotrg_step(ctx: int, t: Z2Tensor, chi: int, direction: int) -> dict:
     return info.as_dict()
 
 
-def hs_rdm_vjp(ctx: int, env: Env, A, d: int, D: int, drho, dA) -> None:
-    check(load().hs_rdm_vjp(ctx, ctypes.byref(env), ptr(A), d, D, HS_F64, ptr(drho), ptr(dA)))
+def hs_rdm_vjp(ctx: int, env: Env, A, d: int, D: int, drho, dA, dtype: int = HS_F64) -> None:
+    check(load().hs_rdm_vjp(ctx, ctypes.byref(env), ptr(A), d, D, dtype, ptr(drho), ptr(dA)))

@@ -137,8 +137,16 @@ class CTMRG:
         return float(np.real(t1 / t0))
 
     def rdm2_of(self, A: torch.Tensor, h: torch.Tensor) -> tuple[torch.Tensor, torch.Tensor]:
-        """(rho, [Tr rho, Tr rho h]) for another tensor A with this (fixed) environment."""
+        """(rho, [Tr rho, Tr rho h]) for another tensor A with this (fixed) environment.
+        Complex A (a complex128 tensor) gives complex rho and traces."""
         n = self.d * self.d
+        if self.complex:
+            Ai = torch.view_as_real(A.to(torch.complex128)).contiguous()
+            rho = torch.empty((n, n, 2), dtype=torch.float64, device=A.device)
+            tr = torch.empty((2, 2), dtype=torch.float64, device=A.device)
+            L.hs_rdm(self.ctx.handle, self.env, Ai, self.d, self.D, L.HS_C128, L.HS_RDM_TWO_SITE, h.contiguous(),
+                     rho, tr)
+            return torch.view_as_complex(rho), torch.view_as_complex(tr)
         rho = torch.empty((n, n), dtype=torch.float64, device=A.device)
         tr = torch.empty(2, dtype=torch.float64, device=A.device)
         L.hs_rdm(self.ctx.handle, self.env, A.contiguous(), self.d, self.D, L.HS_F64, L.HS_RDM_TWO_SITE,
@@ -146,6 +154,13 @@ class CTMRG:
         return rho, tr
 
     def rdm2_vjp(self, A: torch.Tensor, drho: torch.Tensor) -> torch.Tensor:
+        """Adjoint of rdm2_of: drho (cotangent dE/dRe rho + i dE/dIm rho for complex A) -> dA."""
+        if self.complex:
+            Ai = torch.view_as_real(A.to(torch.complex128)).contiguous()
+            dr = torch.view_as_real(drho.to(torch.complex128)).contiguous()
+            dA = torch.empty_like(Ai)
+            L.hs_rdm_vjp(self.ctx.handle, self.env, Ai, self.d, self.D, dr, dA, L.HS_C128)
+            return torch.view_as_complex(dA)
         dA = torch.empty_like(A)
         L.hs_rdm_vjp(self.ctx.handle, self.env, A.contiguous(), self.d, self.D, drho.contiguous(), dA)
         return dA
@@ -195,10 +210,11 @@ class HOTRG:
 
 
 class EnergyFn(torch.autograd.Function):
-    """E(A) = Tr(rho(A) h) / Tr rho(A) with the environment of `ctm` held fixed.
+    """E(A) = Re Tr(rho(A) h) / Tr rho(A) with the environment of `ctm` held fixed.
 
-    forward: hs_rdm; backward: d E / d rho = h^T / Tr rho - (Tr rho h / (Tr rho)^2) I,
-    then the hand-written adjoint hs_rdm_vjp.
+    forward: hs_rdm; backward: the cotangent of rho, d E / d rho = conj(1 / Tr rho) h^T
+    - conj(Tr rho h / (Tr rho)^2) I (dE/dRe + i dE/dIm for complex rho), then the
+    hand-written adjoint hs_rdm_vjp. For complex A the gradient is dE/dRe A + i dE/dIm A.
     """
 
     @staticmethod
@@ -206,13 +222,14 @@ class EnergyFn(torch.autograd.Function):
         rho, tr = ctm.rdm2_of(A.detach(), h)
         fctx.ctm = ctm
         fctx.save_for_backward(A.detach(), h, tr)
-        return tr[1] / tr[0]
+        return torch.real(tr[1] / tr[0])
 
     @staticmethod
     def backward(fctx, g):
         A, h, tr = fctx.saved_tensors
         n = h.shape[0]
-        drho = g * (h.t() / tr[0] - (tr[1] / tr[0] ** 2) * torch.eye(n, dtype=h.dtype, device=h.device))
+        eye = torch.eye(n, dtype=tr.dtype, device=h.device)
+        drho = g * (torch.conj(1.0 / tr[0]) * h.t().to(tr.dtype) - torch.conj(tr[1] / tr[0] ** 2) * eye)
         return fctx.ctm.rdm2_vjp(A, drho), None, None
 
 

@@ -312,6 +312,15 @@ hs_status finish_projector(hs_ctx ctx, int n0, int n1, SelectOut* dsel, Sect c, 
     HS_TRY(permute(ctx, PTm, Pm, {1, 2, 0}, PT, P));
     ctx->launches += 2;
   }
+  if (env->precision != HS_PREC_F64) {
+    // tensor-core precisions: the projection below runs on tcgen05 with FP32
+    // accumulation, so orthonormality beyond that level buys nothing; the
+    // Loewdin step runs on the tensor cores too (rows of each block)
+    for (int p = 0; p < 2; ++p)
+      if (k[p] > 0 && n[p] > 0)
+        HS_TRY(lowdin_rows(ctx, env->precision, PT + ptoff[p], k[p], n[p], PT2, lowdin));
+    lowdin = 0;
+  }
   for (int step = 0; step < lowdin; ++step) {
     PhaseScope ps(ctx, HS_PHASE_GEMM);
     // G = PT PT^T

@@ -115,7 +115,7 @@ struct hs_ctx_s {
   const double* ga_src = nullptr;
   hs::DBuf gb[12];
   // complex observables (planar real / imaginary parts)
-  hs::DBuf zr[24];
+  hs::DBuf zr[40];
   // split-K partial sums of the FP64 GEMM
   hs::DBuf splitk;
   // subspace eigensolver: warm start (previous kept rows, per block) and

@@ -222,22 +222,85 @@ struct ZBuf {
   double* im;
 };
 
+// planar buffer pair i (0 <= i < 20) of the context, at least n doubles each
 ZBuf zbuf(hs_ctx ctx, int i, long long n) {
+  if (i < 0 || 2 * i + 1 >= (int)(sizeof(ctx->zr) / sizeof(ctx->zr[0]))) return {nullptr, nullptr};
   if (ctx->zr[2 * i].ensure(n * 8) != HS_OK || ctx->zr[2 * i + 1].ensure(n * 8) != HS_OK) return {nullptr, nullptr};
   return {ctx->zr[2 * i].d(), ctx->zr[2 * i + 1].d()};
 }
 
-// complex C = A B^T from planar parts: four FP64 GEMMs, two accumulating
-hs_status zgemm(hs_ctx ctx, const GemmGroup& g, ZBuf A, ZBuf B, ZBuf C) {
+// complex C = A B^T (or A conj(B)^T) from planar parts: four FP64 GEMMs, two accumulating
+hs_status zgemm(hs_ctx ctx, const GemmGroup& g, ZBuf A, ZBuf B, ZBuf C, bool conj_b = false) {
   cudaStream_t s = ctx->stream;
   HS_TRY(ctx->splitk.ensure(kSplitKElems * sizeof(double)));
   double* part = ctx->splitk.d();
+  const double sb = conj_b ? -1.0 : 1.0;
   HS_CUDA(launch_gemm_f64(g, A.re, B.re, C.re, 1.0, s, part, kSplitKElems, false));
-  HS_CUDA(launch_gemm_f64(g, A.im, B.im, C.re, -1.0, s, part, kSplitKElems, true));
-  HS_CUDA(launch_gemm_f64(g, A.re, B.im, C.im, 1.0, s, part, kSplitKElems, false));
+  HS_CUDA(launch_gemm_f64(g, A.im, B.im, C.re, -sb, s, part, kSplitKElems, true));
+  HS_CUDA(launch_gemm_f64(g, A.re, B.im, C.im, sb, s, part, kSplitKElems, false));
   HS_CUDA(launch_gemm_f64(g, A.im, B.re, C.im, 1.0, s, part, kSplitKElems, true));
   ctx->launches += 4;
   return HS_OK;
+}
+
+// dA of a complex A from the cotangents g1, g2 of the two open double layers
+// (planar; layouts of open_double_layer_c_kernel with legs1 / legs2). For a
+// real energy the cotangent convention is g = dE/dRe + i dE/dIm; a site's
+// a[s, s', ...] = A[s, ket] conj(A[s', bra]) gives
+//   dA[p, mine] += g[p, s', (mine as ket, other as bra)] A[s', other]
+//                + conj(g[s, p, (other as ket, mine as bra)]) A[s, other].
+__global__ void open_double_layer_c_vjp_kernel(const double* __restrict__ g1r, const double* __restrict__ g1i,
+                                               int4 legs1, const double* __restrict__ g2r,
+                                               const double* __restrict__ g2i, int4 legs2,
+                                               const double* __restrict__ A, int d, int D, double* __restrict__ dA) {
+  const int q = D * D;
+  const long long D4 = (long long)D * D * D * D;
+  const long long nA = d * D4;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < nA;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int p = (int)(e / D4);
+    long long t = e % D4;
+    int mine[4];
+    mine[3] = (int)(t % D);
+    t /= D;
+    mine[2] = (int)(t % D);
+    t /= D;
+    mine[1] = (int)(t % D);
+    mine[0] = (int)(t / D);
+    double ar = 0.0, ai = 0.0;
+    for (int s2 = 0; s2 < d; ++s2)
+      for (long long o = 0; o < D4; ++o) {
+        long long oo = o;
+        int oth[4];
+        oth[3] = (int)(oo % D);
+        oo /= D;
+        oth[2] = (int)(oo % D);
+        oo /= D;
+        oth[1] = (int)(oo % D);
+        oth[0] = (int)(oo / D);
+        int xk[4], xb[4];
+        for (int l = 0; l < 4; ++l) {
+          xk[l] = mine[l] + D * oth[l];  // this element as the ket factor
+          xb[l] = oth[l] + D * mine[l];  // this element as the bra factor
+        }
+        const double Or = A[2 * (s2 * D4 + o)], Oi = A[2 * (s2 * D4 + o) + 1];
+        for (int site = 0; site < 2; ++site) {
+          const int4 L = site ? legs2 : legs1;
+          const double* gr = site ? g2r : g1r;
+          const double* gi = site ? g2i : g1i;
+          const long long ik =
+              ((((((long long)p * d + s2) * q + xk[L.x]) * q + xk[L.y]) * q + xk[L.z]) * q + xk[L.w]);
+          const long long ib =
+              ((((((long long)s2 * d + p) * q + xb[L.x]) * q + xb[L.y]) * q + xb[L.z]) * q + xb[L.w]);
+          // g_ket * A_other + conj(g_bra) * A_other
+          const double cr = gr[ik] + gr[ib], ci = gi[ik] - gi[ib];
+          ar += cr * Or - ci * Oi;
+          ai += cr * Oi + ci * Or;
+        }
+      }
+    dA[2 * e] = ar;
+    dA[2 * e + 1] = ai;
+  }
 }
 
 hs_status zpermute(hs_ctx ctx, const Z2Mat& in, const Z2Mat& out, std::initializer_list<int> perm, ZBuf src,
@@ -305,6 +368,53 @@ hs_status rdm_complex(hs_ctx ctx, const hs_env* env, const double* A, int d, int
   HS_TRY(zpermute(ctx, dense({chi, chi, d, d, q}), dense({d, d, chi, chi, q}), {2, 3, 1, 0, 4}, RB, RBp));
   HS_TRY(zgemm(ctx, dense_gemm(d2, d2, c2 * q), LBp, RBp, R4));                                 // rho4
   finish_rho_c_kernel<<<1, 256, 0, s>>>(R4.re, R4.im, d, h, out, tr_out);
+  HS_CUDA(cudaGetLastError());
+  ctx->launches += 1;
+  return HS_OK;
+}
+
+// Adjoint of rdm_complex with the environment fixed: drho (interleaved
+// complex d^4, cotangent dE/dRe rho + i dE/dIm rho) -> dA (interleaved complex).
+hs_status rdm_vjp_complex(hs_ctx ctx, const hs_env* env, const double* A, int d, int D, const double* drho,
+                          double* dA_out) {
+  cudaStream_t s = ctx->stream;
+  const long long chi = env->chi_even + env->chi_odd, q = (long long)D * D, d2 = (long long)d * d;
+  const long long c2 = chi * chi, c2q3 = c2 * q * q * q, nb = c2 * d2 * q;
+  // forward: leaves L2p (slot 9), LB (1), RB (2), LBp (4), RBp (5)
+  HS_TRY(ctx->r[3].ensure(2 * d2 * d2 * 8 + 4 * 8));
+  HS_TRY(rdm_complex(ctx, env, A, d, D, nullptr, ctx->r[3].d(), ctx->r[3].d() + 2 * d2 * d2));
+  ZBuf L2p = zbuf(ctx, 9, c2q3), LBp = zbuf(ctx, 4, nb), RBp = zbuf(ctx, 5, nb);
+  // cotangent of rho4[s1, s1', s2, s2'] and of its transpose
+  ZBuf G = zbuf(ctx, 12, d2 * d2), G4 = zbuf(ctx, 13, d2 * d2), G4t = zbuf(ctx, 14, d2 * d2);
+  if (!G4t.re) return fail(HS_ERR_CUDA, "workspace allocation failed");
+  HS_TRY(ctx->r[4].ensure(2 * d2 * d2 * 8));
+  HS_TRY(permute(ctx, dense({d2 * d2, 2}), dense({2, d2 * d2}), {1, 0}, drho, ctx->r[4].d()));
+  HS_CUDA(cudaMemcpyAsync(G.re, ctx->r[4].d(), d2 * d2 * 8, cudaMemcpyDeviceToDevice, s));
+  HS_CUDA(cudaMemcpyAsync(G.im, ctx->r[4].d() + d2 * d2, d2 * d2 * 8, cudaMemcpyDeviceToDevice, s));
+  HS_TRY(zpermute(ctx, dense({d, d, d, d}), dense({d, d, d, d}), {0, 2, 1, 3}, G, G4));
+  HS_TRY(zpermute(ctx, dense({d2, d2}), dense({d2, d2}), {1, 0}, G4, G4t));
+  // gLBp = G4 conj(RBp), gRBp = G4^T conj(LBp): B operands transposed to [(b,t,m) | (s,s')]
+  ZBuf RBq = zbuf(ctx, 15, nb), LBq = zbuf(ctx, 16, nb), gLBp = zbuf(ctx, 17, nb), gRBp = zbuf(ctx, 18, nb);
+  if (!gRBp.re) return fail(HS_ERR_CUDA, "workspace allocation failed");
+  HS_TRY(zpermute(ctx, dense({d2, c2 * q}), dense({c2 * q, d2}), {1, 0}, RBp, RBq));
+  HS_TRY(zpermute(ctx, dense({d2, c2 * q}), dense({c2 * q, d2}), {1, 0}, LBp, LBq));
+  HS_TRY(zgemm(ctx, dense_gemm(d2, c2 * q, d2), G4, RBq, gLBp, true));
+  HS_TRY(zgemm(ctx, dense_gemm(d2, c2 * q, d2), G4t, LBq, gRBp, true));
+  // back to [(s, s', m) | (b, t)] and [(s, s', m) | (t, b)] (LB rows (b,t), RB rows (t,b))
+  ZBuf gLm = zbuf(ctx, 15, nb), gRm = zbuf(ctx, 16, nb);
+  HS_TRY(zpermute(ctx, dense({d, d, chi, chi, q}), dense({d, d, q, chi, chi}), {0, 1, 4, 2, 3}, gLBp, gLm));
+  HS_TRY(zpermute(ctx, dense({d, d, chi, chi, q}), dense({d, d, q, chi, chi}), {0, 1, 4, 3, 2}, gRBp, gRm));
+  // open double layers: g_a = g_B^T conj(L2p) with L2p^T[(k0,k1,k2) | (x0, x4)]
+  ZBuf L2pT = zbuf(ctx, 8, c2q3);
+  if (!L2pT.re) return fail(HS_ERR_CUDA, "workspace allocation failed");
+  HS_TRY(zpermute(ctx, dense({c2, q * q * q}), dense({q * q * q, c2}), {1, 0}, L2p, L2pT));
+  const long long nao = d2 * q * q * q * q;
+  ZBuf g1 = zbuf(ctx, 10, nao), g2 = zbuf(ctx, 11, nao);
+  HS_TRY(zgemm(ctx, dense_gemm(d2 * q, q * q * q, c2), gLm, L2pT, g1, true));
+  HS_TRY(zgemm(ctx, dense_gemm(d2 * q, q * q * q, c2), gRm, L2pT, g2, true));
+  const long long nA = (long long)d * D * D * D * D;
+  open_double_layer_c_vjp_kernel<<<grid_for(nA), 256, 0, s>>>(g1.re, g1.im, make_int4(3, 2, 1, 0), g2.re, g2.im,
+                                                               make_int4(1, 0, 3, 2), A, d, D, dA_out);
   HS_CUDA(cudaGetLastError());
   ctx->launches += 1;
   return HS_OK;
@@ -414,7 +524,9 @@ extern "C" hs_status hs_rdm_vjp(hs_ctx ctx, const hs_env* env, const double* A, 
                                 const double* drho, double* dA_out) {
   HS_TRY(check_ctx(ctx));
   if (!env || !A || !drho || !dA_out || d <= 0 || D != env->D) return fail(HS_ERR_INVALID_ARG, "bad arguments");
-  if (dtype != HS_F64) return fail(HS_ERR_UNSUPPORTED, "complex tensors are not supported by this build");
+  if (dtype != HS_F64 && dtype != HS_C128) return fail(HS_ERR_DTYPE, "unknown dtype");
+  if ((dtype == HS_C128) != (env->dtype == HS_C128)) return fail(HS_ERR_DTYPE, "A and environment disagree on dtype");
+  if (dtype == HS_C128) return rdm_vjp_complex(ctx, env, A, d, D, drho, dA_out);
   HS_TRY(rdm_chain(ctx, env, A, d, D, HS_RDM_TWO_SITE, nullptr));
   cudaStream_t s = ctx->stream;
   const hs_gemm_backend be = env->gemm_backend;

@@ -97,10 +97,28 @@ __global__ void init_C_kernel(const double* __restrict__ a, int D, bool hermitia
 }
 
 // Merge the two ascending spectra; keep the chi of largest modulus.
-__global__ void select_kernel(const double* __restrict__ w0, int n0, const double* __restrict__ w1,
+__global__ void select_kernel(const double* __restrict__ w0g, int n0, const double* __restrict__ w1g,
                               int n1, int chi, int* __restrict__ idx, double* __restrict__ lam,
-                              SelectOut* out) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+                              SelectOut* out, bool staged) {
+  // both spectra staged in shared memory (the merge below is a serial walk)
+  extern __shared__ double wsh[];
+  const double* w0 = w0g;
+  const double* w1 = w1g;
+  if (staged) {
+    for (int i = threadIdx.x; i < n0; i += blockDim.x) wsh[i] = w0g[i];
+    for (int i = threadIdx.x; i < n1; i += blockDim.x) wsh[n0 + i] = w1g[i];
+    w0 = wsh;
+    w1 = wsh + n0;
+  }
+  // sum of |w| over both spectra
+  __shared__ double part[256];
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < n0 + n1; i += blockDim.x) acc += fabs(i < n0 ? w0g[i] : w1g[i - n0]);
+  part[threadIdx.x] = acc;
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  double all = 0.0;
+  for (int t = 0; t < (int)blockDim.x; ++t) all += part[t];
   const double* w[2] = {w0, w1};
   int lo[2] = {0, 0}, hi[2] = {n0 - 1, n1 - 1}, cnt[2] = {0, 0};
   const int keep = min(chi, n0 + n1);
@@ -133,12 +151,15 @@ __global__ void select_kernel(const double* __restrict__ w0, int n0, const doubl
     else
       --hi[best_b];
   }
-  for (int j = 0; j < cnt[0]; ++j) lam[j] = w0[idx[j]];
-  for (int j = 0; j < cnt[1]; ++j) lam[cnt[0] + j] = w1[idx[chi + j]];
-  double all = 0.0, kept = 0.0;
-  for (int i = 0; i < n0; ++i) all += fabs(w0[i]);
-  for (int i = 0; i < n1; ++i) all += fabs(w1[i]);
-  for (int j = 0; j < cnt[0] + cnt[1]; ++j) kept += fabs(lam[j]);
+  double kept = 0.0;
+  for (int j = 0; j < cnt[0]; ++j) {
+    lam[j] = w0[idx[j]];
+    kept += fabs(lam[j]);
+  }
+  for (int j = 0; j < cnt[1]; ++j) {
+    lam[cnt[0] + j] = w1[idx[chi + j]];
+    kept += fabs(lam[cnt[0] + j]);
+  }
   out->discarded = all - kept;
   out->chi_new[0] = cnt[0];
   out->chi_new[1] = cnt[1];
@@ -387,7 +408,15 @@ cudaError_t launch_ctmrg_init(const double* a_blocks, int D, bool hermitian, dou
 
 cudaError_t launch_select(const double* w0, int n0, const double* w1, int n1, int chi, int* idx,
                           double* lam, SelectOut* out, cudaStream_t s) {
-  select_kernel<<<1, 32, 0, s>>>(w0, n0, w1, n1, chi, idx, lam, out);
+  const size_t smem = (size_t)(n0 + n1) * sizeof(double);
+  const bool staged = smem <= 160 * 1024;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(select_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  select_kernel<<<1, 256, staged ? smem : 0, s>>>(w0, n0, w1, n1, chi, idx, lam, out, staged);
   return cudaGetLastError();
 }
 

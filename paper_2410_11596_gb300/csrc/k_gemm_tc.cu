@@ -7,10 +7,11 @@
 //     TF32x3 : acc_main += A_hi B_hi ; acc_corr += A_hi B_lo + A_lo B_hi  (tf32 hi, fp32 lo)
 //     TF32   : acc_main += A_hi B_hi
 //     BF16x3 : as TF32x3 with a bf16 hi/lo split
-//   C = (double)acc_main + (double)acc_corr, widened on the bit patterns
+//   C = (double)(acc_main + acc_corr), one FP32 add, widened on the bit pattern
 // The small cross terms get their own accumulator: folded into the main one
 // they lose their low bits to its (truncating) accumulation, about a tenth of
-// the accuracy gain of the extra passes on K = 512.
+// the accuracy gain of the extra passes on K = 512; the single rounding of
+// the final FP32 add is of the order of the accumulation's own.
 //
 // CTA tile 128 x 128, K step 128 bytes (one 128-byte swizzle atom per row).
 // The kernel is persistent: one CTA per SM walks the output tiles
@@ -20,8 +21,8 @@
 //   warp 1 lane 0   MMA issuer: tcgen05.mma into one of two TMEM accumulator
 //                   buffers, so that tile i+1 accumulates while tile i drains;
 //   warps 2..5      epilogue: TMEM -> registers -> FP64, staged through shared
-//                   memory so that each warp store writes 32 consecutive
-//                   doubles of one row (warp w reads TMEM lanes 32(w%4)...).
+//                   memory so that each warp store writes 16-byte pairs of
+//                   four rows (warp w reads TMEM lanes 32(w%4)...).
 // mbarriers: full (TMA bytes landed), empty (MMAs that read the stage are
 // done, via tcgen05.commit), tfull (accumulator ready), tempty (the four
 // epilogue warps have read the accumulator).
@@ -184,8 +185,8 @@ struct Cfg {
   static constexpr uint32_t ACC_COLS = NPASS == 1 ? BN : 2 * BN;  // one accumulator buffer
   static constexpr uint32_t TMEM_COLS = 2 * ACC_COLS;              // double buffered
   static constexpr int K_PER_TILE = ROW_BYTES / EB;                // elements per 128-byte row
-  static constexpr int STG_LD = 33;                                // staging row stride (doubles)
-  static constexpr int STG_BYTES = 4 * 32 * STG_LD * 8;            // one 32 x 32 block per epilogue warp
+  static constexpr int STG_LD = 18;                                // staging row stride (doubles, 16-byte rows)
+  static constexpr int STG_BYTES = 4 * 32 * STG_LD * 8;            // one 32 x 16 block per epilogue warp
   static constexpr int BAR_BYTES = 256;
   static constexpr int SMEM = STAGES * STAGE_BYTES + STG_BYTES + BAR_BYTES + 1024;
   static_assert(SMEM <= 232448, "shared memory per CTA");
@@ -346,38 +347,56 @@ __global__ void __launch_bounds__(NT, 1) gemm_tc_kernel(const __grid_constant__ 
       fence_after();
       const uint32_t d = tmem + (uint32_t)buf * K::ACC_COLS + lane_base;
       const int row0 = r.m0 + q * 32;
+      // 16-byte stores when every row start is 16-byte aligned
+      const bool vec = (P.ldc % 2 == 0) && ((reinterpret_cast<uintptr_t>(P.c) & 15) == 0);
       for (int c = 0; c < BN && r.n0 + c < P.N; c += 32) {
+        uint32_t r0[32], r1[32];
         if (ktiles > 0) {
-          uint32_t r0[32], r1[32];
           tmem_ld32(d + c, r0);
           if (NPASS == 3) tmem_ld32(d + BN + c, r1);
           tmem_wait_ld();
+        }
 #pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            unsigned long long w;
-            if (!f32_widen_fast(r0[j], w)) w = f64_bits((double)__uint_as_float(r0[j]));  // subnormal
-            double v = f64_from_bits(w);
-            if (NPASS == 3) {
-              if (!f32_widen_fast(r1[j], w)) w = f64_bits((double)__uint_as_float(r1[j]));
-              v += f64_from_bits(w);
+        for (int h = 0; h < 2; ++h) {
+          // this lane's row, 16 columns, widened to FP64 on the bit patterns;
+          // the correction joins the main accumulator with one FP32 add
+#pragma unroll
+          for (int j = 0; j < 16; j += 2) {
+            double v[2];
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+              uint32_t x = 0u;
+              if (ktiles > 0) {
+                float f = __uint_as_float(r0[16 * h + j + u]);
+                if (NPASS == 3) f += __uint_as_float(r1[16 * h + j + u]);
+                x = __float_as_uint(f);
+              }
+              unsigned long long w;
+              if (!f32_widen_fast(x, w)) w = f64_bits((double)__uint_as_float(x));  // subnormal
+              v[u] = f64_from_bits(w);
             }
-            stg[lane * K::STG_LD + j] = v;
+            *reinterpret_cast<double2*>(&stg[lane * K::STG_LD + j]) = make_double2(v[0], v[1]);
           }
-        } else {
-          // empty K range: the accumulator was never written, the product is zero
+          __syncwarp();
+          // eight lanes per row, two columns each: four rows per warp store
+          const int col = r.n0 + c + 16 * h + 2 * (lane & 7);
 #pragma unroll
-          for (int j = 0; j < 32; ++j) stg[lane * K::STG_LD + j] = 0.0;
-        }
-        __syncwarp();
-        const int col = r.n0 + c + lane;
-        if (col < P.N) {
-          for (int i = 0; i < 32; ++i) {
+          for (int i0 = 0; i0 < 32; i0 += 4) {
+            const int i = i0 + (lane >> 3);
             const int row = row0 + i;
-            if (row >= P.M) break;
-            P.c[(long long)row * P.ldc + col] = stg[i * K::STG_LD + lane];
+            if (row < P.M && col < P.N) {
+              const double2 x = *reinterpret_cast<const double2*>(&stg[i * K::STG_LD + 2 * (lane & 7)]);
+              double* dst = P.c + (long long)row * P.ldc + col;
+              if (vec && col + 1 < P.N) {
+                *reinterpret_cast<double2*>(dst) = x;
+              } else {
+                dst[0] = x.x;
+                if (col + 1 < P.N) dst[1] = x.y;
+              }
+            }
           }
+          __syncwarp();
         }
-        __syncwarp();
       }
       // this warp is done reading the accumulator buffer
       fence_before();

@@ -206,12 +206,13 @@ __global__ void row_normalize_kernel(double* __restrict__ X, int m, int n) {
 // eigenvalues ascending in w, eigenvectors as the columns of the column-major
 // m x m array A (overwritten). A rotation is skipped when |A_pq| <= tol
 // sqrt|A_pp A_qq|, tol = max(4e-7, sqrt(m) eps_32) (the relative criterion of
-// Demmel and Veselic, SIAM J. Matrix Anal. Appl. 13, 1992); converged after a
+// Demmel and Veselic, SIAM J. Matrix Anal. Appl. 13, 1992), or when |A_pq| is
+// below 1e-7 max|A_ii| (FP32 rounding noise of the input); converged after a
 // sweep without rotations.
 // After kMaxSweeps without that, *status = 1.
 constexpr int kMaxSweeps = 40;
 
-__global__ void __launch_bounds__(512) jacobi_eig_kernel(float* __restrict__ A0, int m0, float* __restrict__ w0,
+__global__ void __launch_bounds__(1024) jacobi_eig_kernel(float* __restrict__ A0, int m0, float* __restrict__ w0,
                                                          float* __restrict__ A1, int m1, float* __restrict__ w1,
                                                          int* __restrict__ status) {
   float* Ag = blockIdx.x ? A1 : A0;
@@ -228,12 +229,22 @@ __global__ void __launch_bounds__(512) jacobi_eig_kernel(float* __restrict__ A0,
   const int M = (m + 1) & ~1;     // even player count (index m is a dummy when m is odd)
   const int npair = M / 2;
   const float kRelTol = fmaxf(4e-7f, sqrtf((float)m) * 6e-8f);
+  __shared__ float dmax_part[32];
+  float dm = 0.f;
   for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
     const int i = e / m, j = e % m;
-    A[i * ld + j] = 0.5f * (Ag[i * m + j] + Ag[j * m + i]);
+    const float v = 0.5f * (Ag[i * m + j] + Ag[j * m + i]);
+    A[i * ld + j] = v;
     V[i * ld + j] = i == j ? 1.f : 0.f;
+    if (i == j) dm = fmaxf(dm, fabsf(v));
   }
+  for (int o = 16; o > 0; o >>= 1) dm = fmaxf(dm, __shfl_xor_sync(0xffffffffu, dm, o));
+  if ((threadIdx.x & 31) == 0) dmax_part[threadIdx.x >> 5] = dm;
   __syncthreads();
+  float dmax = 0.f;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) dmax = fmaxf(dmax, dmax_part[w]);
+  // off-diagonal entries below this are rounding noise of the FP32 matrix
+  const float abs_floor = 1e-7f * dmax;
   bool converged = false;
   for (int sweep = 0; sweep < kMaxSweeps && !converged; ++sweep) {
     if (threadIdx.x == 0) nrot = 0;
@@ -254,7 +265,7 @@ __global__ void __launch_bounds__(512) jacobi_eig_kernel(float* __restrict__ A0,
           const float apq = A[p * ld + q];
           const float app = A[p * ld + p], aqq = A[q * ld + q];
           // rotate unless A_pq is negligible against its diagonal pair
-          if (fabsf(apq) > 1e-30f && fabsf(apq) > kRelTol * sqrtf(fabsf(app * aqq))) {
+          if (fabsf(apq) > abs_floor && fabsf(apq) > 1e-30f && fabsf(apq) > kRelTol * sqrtf(fabsf(app * aqq))) {
             const float th = (aqq - app) / (2.f * apq);
             const float t = (th >= 0.f ? 1.f : -1.f) / (fabsf(th) + sqrtf(th * th + 1.f));
             c = rsqrtf(t * t + 1.f);
@@ -268,29 +279,38 @@ __global__ void __launch_bounds__(512) jacobi_eig_kernel(float* __restrict__ A0,
         cs[2 * k + 1] = sn;
       }
       __syncthreads();
-      // rows p, q of A: A <- J^T A
-      for (int e = threadIdx.x; e < npair * m; e += blockDim.x) {
-        const int k = e / m, j = e % m;
-        const int p = pq[2 * k], q = pq[2 * k + 1];
-        if (q >= m) continue;
-        const float c = cs[2 * k], sn = cs[2 * k + 1];
-        const float ap = A[p * ld + j], aq = A[q * ld + j];
-        A[p * ld + j] = c * ap - sn * aq;
-        A[q * ld + j] = sn * ap + c * aq;
+      // A <- J^T A J: the rotations act on disjoint pairs, so every 2 x 2 block
+      // (rows of pair a, columns of pair b) transforms on its own; V <- V J
+      const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+      for (int a = threadIdx.x >> 5; a < npair; a += nw) {
+        const int pa = pq[2 * a], qa = pq[2 * a + 1];
+        const float ca = cs[2 * a], sa = cs[2 * a + 1];
+        const bool ra = qa < m;
+        for (int b = lane; b < npair; b += 32) {
+          const int pb = pq[2 * b], qb = pq[2 * b + 1];
+          const float cb = cs[2 * b], sb = cs[2 * b + 1];
+          const bool rb = qb < m;
+          const float a00 = A[pa * ld + pb];
+          const float a01 = rb ? A[pa * ld + qb] : 0.f;
+          const float a10 = ra ? A[qa * ld + pb] : 0.f;
+          const float a11 = (ra && rb) ? A[qa * ld + qb] : 0.f;
+          const float t00 = ca * a00 - sa * a10, t01 = ca * a01 - sa * a11;
+          const float t10 = sa * a00 + ca * a10, t11 = sa * a01 + ca * a11;
+          A[pa * ld + pb] = cb * t00 - sb * t01;
+          if (rb) A[pa * ld + qb] = sb * t00 + cb * t01;
+          if (ra) A[qa * ld + pb] = cb * t10 - sb * t11;
+          if (ra && rb) A[qa * ld + qb] = sb * t10 + cb * t11;
+        }
       }
-      __syncthreads();
-      // columns p, q of A and V: A <- A J, V <- V J
-      for (int e = threadIdx.x; e < npair * m; e += blockDim.x) {
-        const int k = e / m, i = e % m;
-        const int p = pq[2 * k], q = pq[2 * k + 1];
-        if (q >= m) continue;
-        const float c = cs[2 * k], sn = cs[2 * k + 1];
-        const float ap = A[i * ld + p], aq = A[i * ld + q];
-        A[i * ld + p] = c * ap - sn * aq;
-        A[i * ld + q] = sn * ap + c * aq;
-        const float vp = V[i * ld + p], vq = V[i * ld + q];
-        V[i * ld + p] = c * vp - sn * vq;
-        V[i * ld + q] = sn * vp + c * vq;
+      for (int i = threadIdx.x >> 5; i < m; i += nw) {
+        for (int b = lane; b < npair; b += 32) {
+          const int pb = pq[2 * b], qb = pq[2 * b + 1];
+          if (qb >= m) continue;
+          const float cb = cs[2 * b], sb = cs[2 * b + 1];
+          const float vp = V[i * ld + pb], vq = V[i * ld + qb];
+          V[i * ld + pb] = cb * vp - sb * vq;
+          V[i * ld + qb] = sb * vp + cb * vq;
+        }
       }
       __syncthreads();
     }
@@ -329,7 +349,7 @@ cudaError_t launch_jacobi_eig_pair(float* A0, int m0, float* w0, float* A1, int 
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  jacobi_eig_kernel<<<2, 512, jacobi_smem_bytes(m), s>>>(A0, m0, w0, A1, m1, w1, status);
+  jacobi_eig_kernel<<<2, 1024, jacobi_smem_bytes(m), s>>>(A0, m0, w0, A1, m1, w1, status);
   return cudaGetLastError();
 }
 

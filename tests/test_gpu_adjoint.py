@@ -57,3 +57,54 @@ def test_energy_gradient(ctx, k, chi, moves, basis):
         _, tm = ctm.rdm2_of(Ad - eps * vd, hd)
         fd = float(tp[1] / tp[0] - tm[1] / tm[0]) / (2 * eps)
         assert float(np.sum(g * v)) == pytest.approx(fd, rel=1e-6, abs=1e-9)
+
+
+def _complex_gradient_checks(ctx, k, chi, moves, n_fd, dense_ref):
+    from paper_2410_11596_gb300.api import CTMRG, bond_energy
+    A = inputs.workload_tensor(k)
+    h = inputs.heisenberg_bond()
+    ctm = CTMRG(ctx, A, chi)
+    ctm.run(moves)
+    At = torch.from_numpy(A.copy()).cuda().requires_grad_(True)
+    e = bond_energy(ctm, At, h)
+    e.backward()
+    g = At.grad.cpu().numpy()
+    if dense_ref:
+        # dense gradient: torch autograd of the oracle's network on this environment
+        C, T = ctm.dense_env()
+        g_ref = adjoint.energy_gradient(C.cpu().numpy(), T.cpu().numpy(), A, h)
+        assert np.abs(g - g_ref).max() <= 1e-9 * np.abs(g_ref).max()
+    rng = np.random.default_rng(200 + k)
+    eps = 1e-6
+    hd = torch.from_numpy(h).cuda()
+    Ad = torch.from_numpy(A).cuda()
+
+    def energy(X):
+        _, tr = ctm.rdm2_of(X, hd)
+        return float(torch.real(tr[1] / tr[0]))
+
+    for flat in rng.choice(A.size, size=min(n_fd, A.size), replace=False):
+        for unit, part in ((1.0, np.real), (1j, np.imag)):
+            dv = torch.zeros(A.size, dtype=torch.complex128, device="cuda")
+            dv[flat] = unit * eps
+            dv = dv.reshape(A.shape)
+            fd = (energy(Ad + dv) - energy(Ad - dv)) / (2 * eps)
+            assert part(g.reshape(-1)[flat]) == pytest.approx(fd, rel=1e-5, abs=1e-8)
+    for _ in range(4):
+        v = rng.standard_normal(A.shape) + 1j * rng.standard_normal(A.shape)
+        vd = torch.from_numpy(v).cuda()
+        fd = (energy(Ad + eps * vd) - energy(Ad - eps * vd)) / (2 * eps)
+        # directional derivative along v: Re <g, v> with g = dE/dRe + i dE/dIm
+        assert float(np.sum(g.real * v.real + g.imag * v.imag)) == pytest.approx(fd, rel=1e-6, abs=1e-9)
+
+
+def test_complex_energy_gradient_small(ctx):
+    """Complex A (Sec. II.C): adjoint of the graded environment's rho vs the dense autograd
+    gradient and central differences (h = 1e-6) in the real and imaginary directions."""
+    _complex_gradient_checks(ctx, 6, 27, 20, 64, True)
+
+
+def test_complex_energy_gradient_full_size(ctx):
+    """Complex workload at full size (D=5, chi=100, 40 moves): finite differences on 16
+    coordinates (both parts) and four directional derivatives."""
+    _complex_gradient_checks(ctx, 5, 100, 40, 16, False)

@@ -109,3 +109,16 @@ def test_graded_rdm_on_gpu(ctx):
     np.testing.assert_allclose(rho, rho_o, rtol=0, atol=1e-12)
     assert ob.hermiticity_error(rho) < 1e-12
     assert abs(c.energy(h) - g["checkpoints"]["30"]["energy"]) < 1e-10
+
+
+def test_graded_ctmrg_full_size_complex_workload(ctx):
+    """Complex workload at its full size (D=5, chi=100, 40 moves, FP64): energy of the
+    library's own rho against the oracle's stored value."""
+    from paper_2410_11596_gb300.api import CTMRG
+    g = golden(5)
+    c = CTMRG(ctx, inputs.workload_tensor(5), g["chi"])
+    infos = c.run(g["moves"])
+    assert min(i["gap"] for i in infos if np.isfinite(i["gap"])) > 1e-6
+    e = c.energy(inputs.heisenberg_bond())
+    print(f"w5 |dE| = {abs(e - g['checkpoints'][str(g['moves'])]['energy']):.3e}")
+    assert abs(e - g["checkpoints"][str(g["moves"])]["energy"]) < 1e-9
