@@ -54,6 +54,10 @@ def parse():
     p.add_argument("--no-check", action="store_true", help="skip the |dE| run to 50 moves")
     p.add_argument("--no-complex", action="store_true",
                    help="skip the complex-tensor line (graded path, D=5 chi=100, 40 moves)")
+    p.add_argument("--no-dtypes", action="store_true",
+                   help="skip the per-dtype |dE| / rho error table (50 moves per dtype)")
+    p.add_argument("--no-batched", action="store_true",
+                   help="skip the batched line (32 instances, D in 3..7, chi = 4 D^2)")
     p.add_argument("--profile-region", action="store_true",
                    help="profiling runs only: W warm-up moves, then K moves inside cudaProfilerStart/Stop "
                         "(for ncu --profile-from-start off); prints a short JSON line, no bench line")
@@ -351,28 +355,91 @@ def run_ours(args):
         alt = {"eig": other, "moves_per_s": args.steps / (np.sum(msa) / 1e3), "ms_per_step": float(np.mean(msa))}
         del ca
 
+    # accuracy per dtype of the block GEMMs (same eigensolver): |dE| and the
+    # largest |d rho| of the normalised two-site RDM against the oracle after 50 moves
+    per_dtype = None
+    if not args.no_dtypes and rank == 0:
+        g3 = None
+        try:
+            with open(os.path.join(ROOT, "tests", "golden", f"ctmrg_w{WORKLOAD}.json")) as f:
+                g3 = json.load(f)["checkpoints"]["50"]
+        except Exception:
+            pass
+        if g3 is not None:
+            rho_ref = np.array(g3["rho_re"]) + 1j * np.array(g3["rho_im"])
+            per_dtype = {}
+            for prec_ in ("tf32", "bf16x3", "tf32x3", "f64"):
+                cp = CTMRG(ctx, A, w["chi"], basis="hermitian", precision=prec_, backend="own", eig=args.eig)
+                cp.run(50)
+                rho_, t0_, t1_ = cp.rdm2(h)
+                rho_ = rho_.cpu().numpy() / t0_
+                per_dtype[prec_] = {"abs_dE": abs(t1_ / t0_ - g3["energy"]),
+                                    "max_abs_drho": float(np.abs(rho_ - rho_ref).max())}
+                del cp
+
     # complex tensors (Sec. II.C): the graded path on the complex workload, FP64,
     # every move timed; |dE| against the stored oracle energy after 40 moves
     cplx = None
     if not args.no_complex and rank == 0:
         from paper_2410_11596_gb300 import inputs as _inp
         w5 = _inp.WORKLOADS[5]
-        cc = CTMRG(ctx, _inp.workload_tensor(5), w5["chi"], precision="f64", eig="f64")
-        msc = timed_moves(torch, cc, ctx, w5["moves"], flush)
         ref5 = None
         try:
             with open(os.path.join(ROOT, "tests", "golden", "ctmrg_w5.json")) as f:
                 ref5 = json.load(f)["checkpoints"][str(w5["moves"])]["energy"]
         except Exception:
             pass
-        e5 = cc.energy(h)
         cplx = {"workload": "complex C4v iPEPS d=2 D=5 chi=100 (q=25: 15 even/10 odd), seeded, Re/Im ~ N(0,1/2)",
                 "path": "graded real storage (Re of even-total, Im of odd-total entries), sign rule of Eq. (2)-(3), "
-                        "FP64 block GEMMs, SVD truncation via FP64 eig of M M^T (n = 2500)",
-                "moves": w5["moves"], "moves_per_s_all": w5["moves"] / (np.sum(msc) / 1e3),
-                "moves_per_s_last10": 10 / (np.sum(msc[-10:]) / 1e3),
-                "abs_dE_vs_oracle": abs(e5 - ref5) if ref5 is not None else None}
-        del cc
+                        "SVD truncation via the eigenvectors of M M^T (n = 2500)", "moves": w5["moves"]}
+        for label, prec_, eig_ in (("f64", "f64", "f64"), ("tf32x3_f32eig", "tf32x3", "f32p")):
+            cc = CTMRG(ctx, _inp.workload_tensor(5), w5["chi"], precision=prec_, eig=eig_)
+            msc = timed_moves(torch, cc, ctx, w5["moves"], flush)
+            e5 = cc.energy(h)
+            cplx[label] = {"gemm": prec_, "eig": {"f64": "FP64 syevd", "f32p": "FP32 syevd + FP64 Loewdin"}[eig_],
+                           "moves_per_s_all": w5["moves"] / (np.sum(msc) / 1e3),
+                           "moves_per_s_last10": 10 / (np.sum(msc[-10:]) / 1e3),
+                           "abs_dE_vs_oracle": abs(e5 - ref5) if ref5 is not None else None}
+            del cc
+
+    # many independent instances (32 real iPEPS, D uniform in 3..7, chi = 4 D^2):
+    # one batched call per move, instances on their own streams driven by a
+    # host thread pool; per-instance latency and the same moves one by one
+    batched = None
+    if not args.no_batched and rank == 0:
+        from paper_2410_11596_gb300.api import BatchedCTMRG
+        from paper_2410_11596_gb300 import inputs as _inp
+        wl = _inp.batched_workload()
+        bt = BatchedCTMRG([A_ for _, _, A_ in wl], [chi_ for _, chi_, _ in wl], device=local,
+                          precision=args.precision, eig=args.eig)
+        # past the transient (sector sizes settle, warm starts converge), then
+        # 10 batched moves and 10 more moves of the same instances one at a time
+        nwarm = max(args.warmup, 15)
+        bt.run(nwarm)
+        torch.cuda.synchronize()
+        nb = 10
+        t0 = time.perf_counter()
+        bt.run(nb)
+        torch.cuda.synchronize()
+        tb = time.perf_counter() - t0
+        lat = np.array(bt.latencies_ms[-nb:]).reshape(-1)
+        t0 = time.perf_counter()
+        for _ in range(nb):
+            for m_ in bt.members:
+                m_.move()
+        torch.cuda.synchronize()
+        ts = time.perf_counter() - t0
+        batched = {"workload": "32 real C4v iPEPS, D uniform in {3..7} (seed 1159604), chi = 4 D^2, "
+                               "seeded N(0,1), D4-symmetrised",
+                   "Ds": [int(D_) for D_, _, _ in wl], "moves_timed": nb, "warmup_moves": nwarm,
+                   "instance_moves_per_s": len(wl) * nb / tb, "wall_s": tb,
+                   "latency_ms_p50": float(np.percentile(lat, 50)), "latency_ms_p99": float(np.percentile(lat, 99)),
+                   "one_by_one_instance_moves_per_s": len(wl) * nb / ts,
+                   "threads": bt.nthreads, "note": "wall clock (host) around the batched calls (moves "
+                                                   f"{nwarm + 1}-{nwarm + nb}), then the same instances moved one "
+                                                   "at a time; each instance has its own stream and workspace"}
+        bt.close()
+        del bt
 
     # end to end through the public API: host A -> device, double layer, move, corner -> host
     import ctypes  # noqa: F401
@@ -449,7 +516,7 @@ def run_ours(args):
                            "moves_timed": f"{args.warmup + 1}-{args.warmup + args.steps}"},
                 "speedup_vs_dense_f64": (value / world) / dense["moves_per_s"] if dense else None,
                 "dense_f64": dense, "z2_other_eig": alt, "abs_dE_vs_oracle_50_moves": dE,
-                "complex_graded": cplx,
+                "per_dtype_50_moves": per_dtype, "complex_graded": cplx, "batched": batched,
                 "steady_state": steady,
                 "time_split_ms": {k: v / args.steps for k, v in prof["phase_ms"].items()},
                 "wall_s_timed_region": t_wall,

@@ -88,9 +88,10 @@ typedef enum { HS_BASIS_DENSE = 0, HS_BASIS_HERMITIAN = 1 } hs_basis;
  *   rounding already.
  * HS_EIG_SUBSPACE: as HS_EIG_F32_PROJECTED, but the kept vectors come from a
  *   warm-started block subspace iteration on each parity block (tensor-core
- *   products H X, FP64 Cholesky-QR, Rayleigh-Ritz of size m = k + 24 with an
- *   FP32 eigensolver) seeded with the previous move's subspace (kept plus
- *   oversampled vectors). Converged when every Ritz pair that can be kept
+ *   products H X; the warm rows re-orthonormalised by a Loewdin step, power
+ *   steps by Cholesky-QR twice; Rayleigh-Ritz of size m = k + 24 by an FP32
+ *   Jacobi eigensolver, at most 4 rounds, fewer when the residual stalls) seeded with the previous move's
+ *   subspace (kept plus oversampled vectors). Converged when every Ritz pair that can be kept
  *   has residual |H x - theta x| <= tol max|theta| (tol = 1e-6 with FP64
  *   products, 1e-5 with tensor-core products, above their rounding floor);
  *   otherwise, on the first move, or when the sector sizes changed, the move
@@ -247,11 +248,25 @@ hs_status hs_ctmrg_init(hs_ctx ctx, const hs_z2_tensor* a, int chi_max, hs_preci
  * eigen-decomposition of size chi*D^2, FP64 for HS_EIG_F64, FP32 followed by
  * two FP64 Loewdin steps otherwise); C <- U^dagger C' U,
  * T <- U^dagger (T a) U; the new boundary sectors are (chi, 0). lam_* in info
- * are singular values. FP64 block GEMMs only: the precision is ignored.
+ * are singular values. The graded GEMMs and H run in the environment's
+ * precision (FP64 kernel or tcgen05).
  * info (host, may be NULL) receives the move record. Synchronises once
  * (to learn the new sector sizes). */
 hs_status hs_ctmrg_move(hs_ctx ctx, const hs_z2_tensor* a, hs_env* env, int chi,
                         hs_move_info* info);
+
+/* One move of each of n independent CTMRG instances (any mix of D, chi and
+ * dtype), concurrently: instance i runs hs_ctmrg_move(ctxs[i], a[i],
+ * env[i], chi[i], &info[i]) on its own context, whose stream and workspace
+ * no other instance may share, from a pool of nthreads host threads (1 to
+ * 256), so that the GPU overlaps the instances' kernels. info (host, n
+ * records) and ms (host, n wall-clock latencies in milliseconds) may be NULL.
+ * Returns when all instances are done; on failures, every instance still
+ * runs and the first failing instance's status and message are returned.
+ * The paper has no counterpart: this is the batched execution of many
+ * independent networks. */
+hs_status hs_ctmrg_move_batched(hs_ctx* ctxs, int n, const hs_z2_tensor* const* a, hs_env* const* env,
+                                const int* chi, hs_move_info* info, double* ms, int nthreads);
 
 /* Copy the environment out in the plain dense layout: C_dense[chi, chi] and
  * T_dense[chi, D^2, chi] (device, caller-owned, FP64; interleaved complex128
@@ -293,6 +308,21 @@ hs_status hs_hotrg_step(hs_ctx ctx, hs_z2_tensor* t, int chi, int direction, hs_
  * Asynchronous. */
 hs_status hs_rdm(hs_ctx ctx, const hs_env* env, const double* A, int d, int D, hs_dtype dtype,
                  hs_rdm_kind kind, const double* h, double* out, double* tr_out);
+
+/* Correlation length of a real C4v environment: xi = -1/ln|lambda_2/lambda_1|
+ * of the column transfer matrix E[(alpha,l,beta),(alpha',r,beta')] =
+ * sum_{u,d} T[alpha,u,alpha'] a[u,l,d,r] T[beta',d,beta] (top edge left to
+ * right, bottom edge right to left), from A (device, real, the tensor the
+ * environment was built from). E is symmetric for real C4v tensors; a Lanczos
+ * iteration with full re-orthogonalisation (at most max_iter matvecs, 4 to
+ * 400; each is three GEMMs in the plain combined basis, in the environment's
+ * precision) runs until the two largest |Ritz values| change by at most
+ * tol * lambda_1. lam_out (host, 2) receives |lambda_1| and |lambda_2|;
+ * xi_out (host) xi (0 if lambda_2 = 0, +inf if degenerate). Complex
+ * environments: HS_ERR_UNSUPPORTED. Not converged: HS_ERR_TIMEOUT with the
+ * last estimates written. Synchronises. */
+hs_status hs_correlation_length(hs_ctx ctx, const hs_env* env, const double* A, int d, int D, int max_iter,
+                                double tol, double* lam_out, double* xi_out);
 
 /* ---- profiling ------------------------------------------------------- */
 

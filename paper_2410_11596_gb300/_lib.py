@@ -82,7 +82,11 @@ _PROTOS = {
     "hs_env_bytes": (c_int, [c_int, c_int, POINTER(c_size_t), POINTER(c_size_t)]),
     "hs_ctmrg_init": (c_int, [c_void_p, POINTER(Z2Tensor), c_int, c_int, c_int, POINTER(Env)]),
     "hs_ctmrg_move": (c_int, [c_void_p, POINTER(Z2Tensor), POINTER(Env), c_int, POINTER(MoveInfo)]),
+    "hs_ctmrg_move_batched": (c_int, [POINTER(c_void_p), c_int, POINTER(POINTER(Z2Tensor)), POINTER(POINTER(Env)),
+                                      POINTER(c_int), POINTER(MoveInfo), POINTER(c_double), c_int]),
     "hs_env_to_dense": (c_int, [c_void_p, POINTER(Env), c_void_p, c_void_p]),
+    "hs_correlation_length": (c_int, [c_void_p, POINTER(Env), c_void_p, c_int, c_int, c_int, c_double,
+                                      POINTER(c_double), POINTER(c_double)]),
     "hs_rdm": (c_int, [c_void_p, POINTER(Env), c_void_p, c_int, c_int, c_int, c_int, c_void_p, c_void_p,
                        c_void_p]),
     "hs_workspace_query": (c_int, [c_int, c_int, c_int, POINTER(c_size_t)]),
@@ -191,6 +195,27 @@ def hs_ctmrg_move(ctx: int, a: Z2Tensor, env: Env, chi: int) -> MoveInfo:
     info = MoveInfo()
     check(load().hs_ctmrg_move(ctx, ctypes.byref(a), ctypes.byref(env), chi, ctypes.byref(info)))
     return info
+
+
+def hs_ctmrg_move_batched(ctxs: list, a: list, env: list, chi: list, nthreads: int) -> tuple[list, list]:
+    """One move of each instance, concurrently; returns (move records, wall-clock ms per instance)."""
+    n = len(ctxs)
+    c_ctx = (c_void_p * n)(*ctxs)
+    c_a = (POINTER(Z2Tensor) * n)(*[ctypes.pointer(x) for x in a])
+    c_env = (POINTER(Env) * n)(*[ctypes.pointer(x) for x in env])
+    c_chi = (c_int * n)(*chi)
+    info = (MoveInfo * n)()
+    ms = (c_double * n)()
+    check(load().hs_ctmrg_move_batched(c_ctx, n, c_a, c_env, c_chi, info, ms, nthreads))
+    return [info[i].as_dict() for i in range(n)], [ms[i] for i in range(n)]
+
+
+def hs_correlation_length(ctx: int, env: Env, A, d: int, D: int, max_iter: int = 200,
+                          tol: float = 1e-12) -> tuple[float, float, float]:
+    lam = (c_double * 2)()
+    xi = c_double()
+    check(load().hs_correlation_length(ctx, ctypes.byref(env), ptr(A), d, D, max_iter, tol, lam, ctypes.byref(xi)))
+    return lam[0], lam[1], xi.value
 
 
 def hs_env_to_dense(ctx: int, env: Env, C_dense, T_dense) -> None:

@@ -4,6 +4,8 @@ No arithmetic of the method happens here; every step runs in the CUDA library.
 """
 from __future__ import annotations
 
+import functools
+
 import numpy as np
 import torch
 
@@ -41,6 +43,34 @@ class Context:
         L.hs_sync(self.handle)
 
 
+def _record(x, stream) -> None:
+    if isinstance(x, torch.Tensor) and x.is_cuda:
+        x.record_stream(stream)
+    elif isinstance(x, (tuple, list)):
+        for y in x:
+            _record(y, stream)
+
+
+def on_ctx_stream(fn):
+    """Run a method of an object with a `ctx` on the context's stream: the
+    context stream first waits for the caller's stream (inputs made there),
+    torch work inside (allocations, copies) is issued on the context stream,
+    and the caller's stream then waits for it (outputs handed back)."""
+    @functools.wraps(fn)
+    def wrapper(self, *args, **kwargs):
+        s = self.ctx.stream
+        caller = torch.cuda.current_stream(self.ctx.device)
+        if s == caller:
+            return fn(self, *args, **kwargs)
+        s.wait_stream(caller)
+        with torch.cuda.stream(s):
+            out = fn(self, *args, **kwargs)
+        caller.wait_stream(s)
+        _record(out, caller)
+        return out
+    return wrapper
+
+
 def to_device(A: np.ndarray, device: int = 0) -> torch.Tensor:
     """Copy a host iPEPS tensor to the device (complex as interleaved float64)."""
     A = np.ascontiguousarray(A)
@@ -60,6 +90,11 @@ class CTMRG:
     def __init__(self, ctx: Context, A: np.ndarray | torch.Tensor, chi: int, basis: str = "hermitian",
                  precision: str = "f64", backend: str = "own", eig: str = "f64", complex_valued: bool | None = None):
         self.ctx = ctx
+        self._init(A, chi, basis, precision, backend, eig, complex_valued)
+
+    @on_ctx_stream
+    def _init(self, A, chi, basis, precision, backend, eig, complex_valued):
+        ctx = self.ctx
         dev = f"cuda:{ctx.device}"
         if complex_valued is None:
             complex_valued = isinstance(A, np.ndarray) and np.iscomplexobj(A)
@@ -82,6 +117,7 @@ class CTMRG:
         self.env.eig_mode = EIG[eig]
         self.infos: list[dict] = []
 
+    @on_ctx_stream
     def move(self) -> dict:
         info = L.hs_ctmrg_move(self.ctx.handle, self.a, self.env, self.chi).as_dict()
         self.infos.append(info)
@@ -100,6 +136,7 @@ class CTMRG:
         sv = np.linalg.svd(C.cpu().numpy(), compute_uv=False)
         return sv / sv[0]
 
+    @on_ctx_stream
     def dense_env(self) -> tuple[torch.Tensor, torch.Tensor]:
         """(C[chi, chi], T[chi, D^2, chi]) in the plain combined basis (complex128 for complex A)."""
         chi, q = self.chi_now, self.D * self.D
@@ -114,6 +151,7 @@ class CTMRG:
         L.hs_env_to_dense(self.ctx.handle, self.env, C, T)
         return C, T
 
+    @on_ctx_stream
     def rdm2(self, h: np.ndarray):
         """(rho, Tr rho, Tr rho h) of a horizontal bond; h a d^2 x d^2 real matrix.
         For complex A, rho is complex128 and the traces are complex."""
@@ -136,6 +174,7 @@ class CTMRG:
         _, t0, t1 = self.rdm2(h)
         return float(np.real(t1 / t0))
 
+    @on_ctx_stream
     def rdm2_of(self, A: torch.Tensor, h: torch.Tensor) -> tuple[torch.Tensor, torch.Tensor]:
         """(rho, [Tr rho, Tr rho h]) for another tensor A with this (fixed) environment.
         Complex A (a complex128 tensor) gives complex rho and traces."""
@@ -153,6 +192,7 @@ class CTMRG:
                  h.contiguous(), rho, tr)
         return rho, tr
 
+    @on_ctx_stream
     def rdm2_vjp(self, A: torch.Tensor, drho: torch.Tensor) -> torch.Tensor:
         """Adjoint of rdm2_of: drho (cotangent dE/dRe rho + i dE/dIm rho for complex A) -> dA."""
         if self.complex:
@@ -165,6 +205,11 @@ class CTMRG:
         L.hs_rdm_vjp(self.ctx.handle, self.env, A.contiguous(), self.d, self.D, drho.contiguous(), dA)
         return dA
 
+    def correlation_length(self, max_iter: int = 200, tol: float = 1e-12) -> float:
+        """xi = -1/ln|lambda_2/lambda_1| of the column transfer matrix T-a-T (real A)."""
+        return L.hs_correlation_length(self.ctx.handle, self.env, self.A, self.d, self.D, max_iter, tol)[2]
+
+    @on_ctx_stream
     def one_site_env(self) -> torch.Tensor:
         """eps[u, l, d, r] in the plain combined basis (Eq. (4))."""
         q = self.D * self.D
@@ -179,6 +224,11 @@ class HOTRG:
 
     def __init__(self, ctx: Context, A: np.ndarray | torch.Tensor, chi: int, basis: str = "hermitian"):
         self.ctx = ctx
+        self._init(A, chi, basis)
+
+    @on_ctx_stream
+    def _init(self, A, chi, basis):
+        ctx = self.ctx
         dev = f"cuda:{ctx.device}"
         self.A = A if isinstance(A, torch.Tensor) else to_device(A, ctx.device)
         self.d, self.D = int(self.A.shape[0]), int(self.A.shape[1])
@@ -207,6 +257,40 @@ class HOTRG:
         n = len(self.infos)
         val = self.log_norms[0] + sum(self.log_norms[k] / 2.0 ** k for k in range(1, n + 1))
         return float(val + np.log(self.infos[-1]["trace"]) / 2.0 ** n)
+
+
+class BatchedCTMRG:
+    """Many independent CTMRG instances (any mix of D, chi, real or complex) moved
+    together by hs_ctmrg_move_batched: each instance has its own context and
+    stream, and a pool of host threads drives them concurrently."""
+
+    def __init__(self, tensors: list, chis: list, device: int = 0, precision: str = "tf32x3",
+                 eig: str = "subspace", nthreads: int | None = None):
+        self.members = []
+        self.contexts = []
+        for A, chi in zip(tensors, chis):
+            ctx = Context(device, torch.cuda.Stream(device))
+            self.contexts.append(ctx)
+            self.members.append(CTMRG(ctx, A, chi, precision=precision, eig=eig))
+        self.nthreads = nthreads or min(len(self.members), 32)
+        self.latencies_ms: list[list[float]] = []
+
+    def move(self) -> list[dict]:
+        infos, ms = L.hs_ctmrg_move_batched([c.handle for c in self.contexts], [m.a for m in self.members],
+                                            [m.env for m in self.members], [m.chi for m in self.members],
+                                            self.nthreads)
+        for m, i in zip(self.members, infos):
+            m.infos.append(i)
+        self.latencies_ms.append(ms)
+        return infos
+
+    def run(self, moves: int) -> None:
+        for _ in range(moves):
+            self.move()
+
+    def close(self) -> None:
+        for c in self.contexts:
+            c.close()
 
 
 class EnergyFn(torch.autograd.Function):

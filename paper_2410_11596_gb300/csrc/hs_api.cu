@@ -515,6 +515,7 @@ hs_status subspace_projector(hs_ctx ctx, hs_env* env, int chi, int n0, int n1, d
   std::vector<float> hth(m[0] + m[1]);
   std::vector<double> hres(m[0] + m[1]);
   int hbad = 0;
+  double prev_worst = INFINITY;
   for (int it = 0; it < kMaxIt; ++it) {
     *iters = it + 1;
     for (int b = 0; b < 2; ++b) {
@@ -600,14 +601,18 @@ hs_status subspace_projector(hs_ctx ctx, hs_env* env, int chi, int n0, int n1, d
       return HS_OK;
     }
     if (it + 1 == kMaxIt) return HS_OK;  // fall back
+    // hopeless attempts (far from tolerance and not closing in fast) fall back early
+    if (it >= 1 && worst > 30.0 * kTol && worst > 0.5 * prev_worst) return HS_OK;
+    prev_worst = worst;
     for (int b = 0; b < 2; ++b)
       if (m[b] > 0) {
-        // power step on the Ritz basis: rows of Zr = theta_i x_i + residual are
-        // nearly orthogonal; normalise them and orthonormalise (Loewdin)
+        // power step on the Ritz basis: rows of Zr = theta_i x_i + residual.
+        // Far from convergence they can be far from orthogonal, where the
+        // Loewdin iteration diverges: orthonormalise by Cholesky-QR twice (FP64)
         HS_CUDA(cudaMemcpyAsync(ctx->sx[b].p, ctx->szr[b].p, (size_t)m[b] * n[b] * sizeof(double),
                                 cudaMemcpyDeviceToDevice, s));
         HS_CUDA(launch_row_normalize(ctx->sx[b].d(), m[b], n[b], s));
-        HS_TRY(lowdin_rows(ctx, prec, ctx->sx[b].d(), m[b], n[b], ctx->sxc[b].d(), 2));
+        HS_TRY(cholqr2(ctx, ctx->sx[b].d(), m[b], n[b], ctx->sxc[b].d(), bad));
       }
   }
   return HS_OK;

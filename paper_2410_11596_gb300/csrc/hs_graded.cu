@@ -57,16 +57,61 @@ hs_status gconj(hs_ctx ctx, const GMat& m, double* buf) {
   return HS_OK;
 }
 
-// C~ = A~ B~^T (graded); B points at B~ followed by its conjugate.
-hs_status ggemm(hs_ctx ctx, const GMat& Am, const double* A, const GMat& Bm, const double* B, const GMat& Cm,
-                double* C, double* flops) {
+// C~ = A~ B~^T (graded); B points at B~ followed by its conjugate. FP64
+// kernel, or the tensor cores in the TF32/BF16 precisions (A, B and conj(B)
+// split into padded hi/lo operands, the four sub-products in one launch).
+hs_status ggemm(hs_ctx ctx, hs_precision prec, const GMat& Am, const double* A, const GMat& Bm, const double* B,
+                const GMat& Cm, double* C, double* flops) {
   if (g_cols(Am) != g_cols(Bm)) return fail(HS_ERR_SHAPE, "graded GEMM: K mismatch");
   const GemmGroup g = make_graded_gemm(Am, Bm, Cm, g_elems(Bm));
-  PhaseScope ps(ctx, HS_PHASE_GEMM);
-  HS_TRY(gemm(ctx, HS_GEMM_OWN, g, A, B, C));
   const double f = gemm_flops(g);
   *flops += f;
-  ctx->phase_flops[HS_PHASE_GEMM] += f;
+  if (prec == HS_PREC_F64) {
+    PhaseScope ps(ctx, HS_PHASE_GEMM);
+    HS_TRY(gemm(ctx, HS_GEMM_OWN, g, A, B, C));
+    ctx->phase_flops[HS_PHASE_GEMM] += f;
+    return HS_OK;
+  }
+  const int pad = tc_pad(prec), eb = tc_elem_bytes(prec), mode = tc_mode(prec);
+  const long long K = g_cols(Am), Kp = (K + pad - 1) / pad * pad;
+  const long long ra = g_rows(Am), rb = g_rows(Bm);
+  HS_TRY(ctx->sx_hi.ensure((size_t)ra * Kp * eb));
+  HS_TRY(ctx->sx_lo.ensure((size_t)ra * Kp * eb));
+  HS_TRY(ctx->sy_hi.ensure((size_t)2 * rb * Kp * eb));
+  HS_TRY(ctx->sy_lo.ensure((size_t)2 * rb * Kp * eb));
+  {
+    PhaseScope ps(ctx, HS_PHASE_PERMUTE);
+    HS_CUDA(launch_split_pad(A, ra, (int)K, g_ld(Am), ctx->sx_hi.p, ctx->sx_lo.p, Kp, mode, ctx->stream));
+    // B~ and its conjugate (stored g_elems(Bm) apart) split back to back
+    HS_CUDA(launch_split_pad(B, rb, (int)K, g_ld(Bm), ctx->sy_hi.p, ctx->sy_lo.p, Kp, mode, ctx->stream));
+    HS_CUDA(launch_split_pad(B + g_elems(Bm), rb, (int)K, g_ld(Bm), static_cast<char*>(ctx->sy_hi.p) + rb * Kp * eb,
+                             static_cast<char*>(ctx->sy_lo.p) + rb * Kp * eb, Kp, mode, ctx->stream));
+    ctx->launches += 3;
+  }
+  TcProblem pr[4];
+  int np = 0;
+  for (int i = 0; i < g.n; ++i) {
+    const GemmProblem& q = g.p[i];
+    TcProblem& t = pr[np++];
+    t.M = q.M;
+    t.N = q.N;
+    t.Kp = (int)Kp;
+    t.ldc = q.ldc;
+    const long long arow = q.a_off / g_ld(Am);
+    const bool conj = q.b_off >= g_elems(Bm);
+    const long long brow = (q.b_off - (conj ? g_elems(Bm) : 0)) / g_ld(Bm) + (conj ? rb : 0);
+    t.a_hi = static_cast<const char*>(ctx->sx_hi.p) + arow * Kp * eb;
+    t.a_lo = static_cast<const char*>(ctx->sx_lo.p) + arow * Kp * eb;
+    t.b_hi = static_cast<const char*>(ctx->sy_hi.p) + brow * Kp * eb;
+    t.b_lo = static_cast<const char*>(ctx->sy_lo.p) + brow * Kp * eb;
+    t.c = C + q.c_off;
+  }
+  HS_TRY(ctx->splitk.ensure(kSplitKElems * sizeof(double)));
+  PhaseScope ps(ctx, HS_PHASE_GEMM_TC);
+  HS_CUDA(launch_gemm_tc(prec, pr, np, static_cast<int*>(ctx->tc_err.p), ctx->stream, ctx->splitk.d(),
+                         kSplitKElems));
+  ctx->launches += 1;
+  ctx->phase_flops[HS_PHASE_GEMM_TC] += f;
   return HS_OK;
 }
 
@@ -133,6 +178,7 @@ hs_status graded_move(hs_ctx ctx, const hs_z2_tensor* a, hs_env* env, int chi, h
   const int k = (int)std::min<long long>(chi, n);
   const Sect cn = make_sect(k, 0);
   double flops = 0.0;
+  const hs_precision prec = env->precision;
   double* B1 = ctx->big1.d();
   double* B2 = ctx->big2.d();
   double* Tq = ctx->gb[0].d();
@@ -171,10 +217,10 @@ hs_status graded_move(hs_ctx ctx, const hs_z2_tensor* a, hs_env* env, int chi, h
   HS_TRY(gconj(ctx, Tqm, Tq));
   HS_TRY(gpermute(ctx, Cm, Cm, {1, 0}, env->C, Ct));
   HS_TRY(gconj(ctx, Cm, Ct));
-  HS_TRY(ggemm(ctx, Tm, env->T, Cm, Ct, X1m, X1, &flops));             // G1: X1 = T C
-  HS_TRY(ggemm(ctx, X1m, X1, Tqm, Tq, X2m, B1, &flops));               // G2: X2 = X1 T
+  HS_TRY(ggemm(ctx, prec, Tm, env->T, Cm, Ct, X1m, X1, &flops));             // G1: X1 = T C
+  HS_TRY(ggemm(ctx, prec, X1m, X1, Tqm, Tq, X2m, B1, &flops));               // G2: X2 = X1 T
   HS_TRY(gpermute(ctx, X2m, X2pm, {0, 3, 2, 1}, B1, B2));              // (a,x,y,e) -> (a,e,y,x)
-  HS_TRY(ggemm(ctx, X2pm, B2, Am, A2, X3m, B1, &flops));               // G3: X3 = X2p a
+  HS_TRY(ggemm(ctx, prec, X2pm, B2, Am, A2, X3m, B1, &flops));               // G3: X3 = X2p a
   HS_TRY(gpermute(ctx, X3m, Cpm, {0, 2, 1, 3}, B1, B2));               // (a,e,d,r) -> (a,d,e,r)
   double* Cp = B2;
 
@@ -185,15 +231,15 @@ hs_status graded_move(hs_ctx ctx, const hs_z2_tensor* a, hs_env* env, int chi, h
     HS_CUDA(launch_graded_sign(Cp, B1, r0, r1, r0, r1, n, 1, s));  // M in B1
     ctx->launches += 1;
   }
-  {
+  // H = M M^T (tensor cores in the TF32/BF16 precisions, which time themselves)
+  if (prec == HS_PREC_F64) {
     PhaseScope ps(ctx, HS_PHASE_GEMM);
-    GemmGroup gh{};
-    gh.n = 1;
-    gh.p[0] = GemmProblem{(int)n, (int)n, (int)n, (int)n, (int)n, (int)n, 0, 0, 0};
-    HS_TRY(gemm(ctx, HS_GEMM_OWN, gh, B1, B1, Mh));
-    flops += gemm_flops(gh);
-    ctx->phase_flops[HS_PHASE_GEMM] += gemm_flops(gh);
+    HS_TRY(dense_gemm_any(ctx, prec, (int)n, (int)n, (int)n, B1, B1, Mh));
+    ctx->phase_flops[HS_PHASE_GEMM] += 2.0 * n * (double)n * n;
+  } else {
+    HS_TRY(dense_gemm_any(ctx, prec, (int)n, (int)n, (int)n, B1, B1, Mh));
   }
+  flops += 2.0 * n * (double)n * n;
   const bool f32 = env->eig_mode != HS_EIG_F64;
   {
     PhaseScope ps(ctx, HS_PHASE_EIG);
@@ -223,20 +269,20 @@ hs_status graded_move(hs_ctx ctx, const hs_z2_tensor* a, hs_env* env, int chi, h
   double* PTc = PT + g_elems(PTm);
 
   // ---- C_new = P^dagger C' P
-  HS_TRY(ggemm(ctx, Cpm, Cp, PTm, PT, V1m, V1, &flops));               // V1 = C' P
+  HS_TRY(ggemm(ctx, prec, Cpm, Cp, PTm, PT, V1m, V1, &flops));               // V1 = C' P
   double* V1t = B1;
   HS_TRY(gpermute(ctx, V1m, V1tm, {2, 0, 1}, V1, V1t));
   HS_TRY(gconj(ctx, V1tm, V1t));
-  HS_TRY(ggemm(ctx, PTm, PTc, V1tm, V1t, Cnm, env->C, &flops));        // C_new = conj(P)^T V1
+  HS_TRY(ggemm(ctx, prec, PTm, PTc, V1tm, V1t, Cnm, env->C, &flops));        // C_new = conj(P)^T V1
 
   // ---- T_new[a', r, b'] = conj(P[(alpha,d),a']) T[alpha,x,beta] a[u,x,d,r] P[(beta,u),b']
   double* Pp = V1;
   HS_TRY(gpermute(ctx, PTm, Ppm, {2, 0, 1}, PTc, Pp));                 // (a',alpha,d) -> (d,a',alpha)
-  HS_TRY(ggemm(ctx, Ppm, Pp, Tqm, Tq, Ym, B1, &flops));                // G4: Y = conj(P') T
+  HS_TRY(ggemm(ctx, prec, Ppm, Pp, Tqm, Tq, Ym, B1, &flops));                // G4: Y = conj(P') T
   HS_TRY(gpermute(ctx, Ym, Ypm, {1, 3, 0, 2}, B1, B2));                // (d,a',x,b) -> (a',b,d,x)
-  HS_TRY(ggemm(ctx, Ypm, B2, Am, A2, Zm, B1, &flops));                 // G5: Z = Yp a
+  HS_TRY(ggemm(ctx, prec, Ypm, B2, Am, A2, Zm, B1, &flops));                 // G5: Z = Yp a
   HS_TRY(gpermute(ctx, Zm, Zpm, {0, 3, 1, 2}, B1, B2));                // (a',b,u,r) -> (a',r,b,u)
-  HS_TRY(ggemm(ctx, Zpm, B2, PTm, PT, Tnm, env->T, &flops));           // G6: T_new = Zp P
+  HS_TRY(ggemm(ctx, prec, Zpm, B2, PTm, PT, Tnm, env->T, &flops));           // G6: T_new = Zp P
 
   // ---- normalise
   {

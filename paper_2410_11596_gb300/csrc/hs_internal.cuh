@@ -235,7 +235,7 @@ struct TcProblem {
   double* c;
 };
 
-// precision: HS_PREC_TF32X3, HS_PREC_TF32 or HS_PREC_BF16X3. err receives a
+// Up to four problems per launch. precision: HS_PREC_TF32X3, HS_PREC_TF32 or HS_PREC_BF16X3. err receives a
 // non-zero code if a bounded wait inside the kernel gave up.
 // part/part_elems: optional FP64 workspace for split-K partials (used when a
 // problem's output tiles cannot fill the GPU); nullptr disables splitting.

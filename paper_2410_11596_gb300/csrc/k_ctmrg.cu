@@ -100,10 +100,14 @@ __global__ void init_C_kernel(const double* __restrict__ a, int D, bool hermitia
 __global__ void select_kernel(const double* __restrict__ w0g, int n0, const double* __restrict__ w1g,
                               int n1, int chi, int* __restrict__ idx, double* __restrict__ lam,
                               SelectOut* out, bool staged) {
-  // both spectra staged in shared memory (the merge below is a serial walk)
+  // both spectra staged in shared memory (the merge below is a serial walk),
+  // followed by the picked values and their blocks
   extern __shared__ double wsh[];
+  const int keep = min(chi, n0 + n1);
   const double* w0 = w0g;
   const double* w1 = w1g;
+  double* pv = wsh + (staged ? n0 + n1 : 0);
+  unsigned char* pb = reinterpret_cast<unsigned char*>(pv + keep);
   if (staged) {
     for (int i = threadIdx.x; i < n0; i += blockDim.x) wsh[i] = w0g[i];
     for (int i = threadIdx.x; i < n1; i += blockDim.x) wsh[n0 + i] = w1g[i];
@@ -121,8 +125,7 @@ __global__ void select_kernel(const double* __restrict__ w0g, int n0, const doub
   for (int t = 0; t < (int)blockDim.x; ++t) all += part[t];
   const double* w[2] = {w0, w1};
   int lo[2] = {0, 0}, hi[2] = {n0 - 1, n1 - 1}, cnt[2] = {0, 0};
-  const int keep = min(chi, n0 + n1);
-  double first = 0.0, last = 0.0;
+  double first = 0.0, last = 0.0, kept = 0.0;
   for (int s = 0; s <= keep; ++s) {
     int best_b = -1, best_i = -1;
     double best = -1.0;
@@ -144,22 +147,19 @@ __global__ void select_kernel(const double* __restrict__ w0g, int n0, const doub
     }
     if (s == 0) first = best;
     last = best;
+    kept += best;
     idx[best_b * chi + cnt[best_b]] = best_i;
+    pv[s] = w[best_b][best_i];
+    pb[s] = (unsigned char)best_b;
     ++cnt[best_b];
     if (best_i == lo[best_b])
       ++lo[best_b];
     else
       --hi[best_b];
   }
-  double kept = 0.0;
-  for (int j = 0; j < cnt[0]; ++j) {
-    lam[j] = w0[idx[j]];
-    kept += fabs(lam[j]);
-  }
-  for (int j = 0; j < cnt[1]; ++j) {
-    lam[cnt[0] + j] = w1[idx[chi + j]];
-    kept += fabs(lam[cnt[0] + j]);
-  }
+  // new diagonal in FSO order: block 0's picks, then block 1's, each in pick order
+  int j0 = 0, j1 = cnt[0];
+  for (int s = 0; s < keep; ++s) lam[pb[s] ? j1++ : j0++] = pv[s];
   out->discarded = all - kept;
   out->chi_new[0] = cnt[0];
   out->chi_new[1] = cnt[1];
@@ -408,15 +408,18 @@ cudaError_t launch_ctmrg_init(const double* a_blocks, int D, bool hermitian, dou
 
 cudaError_t launch_select(const double* w0, int n0, const double* w1, int n1, int chi, int* idx,
                           double* lam, SelectOut* out, cudaStream_t s) {
-  const size_t smem = (size_t)(n0 + n1) * sizeof(double);
-  const bool staged = smem <= 160 * 1024;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(select_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
-  select_kernel<<<1, 256, staged ? smem : 0, s>>>(w0, n0, w1, n1, chi, idx, lam, out, staged);
+  constexpr size_t kSmemMax = 160 * 1024;
+  const int keep = chi < n0 + n1 ? chi : n0 + n1;
+  const size_t picks = (size_t)keep * (sizeof(double) + 1);
+  size_t smem = (size_t)(n0 + n1) * sizeof(double) + picks;
+  const bool staged = smem <= kSmemMax;
+  if (!staged) smem = picks;
+  if (smem > kSmemMax) return cudaErrorInvalidValue;
+  // set once per process (thread-safe static initialisation)
+  static const cudaError_t attr_err =
+      cudaFuncSetAttribute(select_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax);
+  if (attr_err != cudaSuccess) return attr_err;
+  select_kernel<<<1, 256, smem, s>>>(w0, n0, w1, n1, chi, idx, lam, out, staged);
   return cudaGetLastError();
 }
 

@@ -20,11 +20,13 @@
 //                   (128-byte swizzle), across tile boundaries;
 //   warp 1 lane 0   MMA issuer: tcgen05.mma into one of two TMEM accumulator
 //                   buffers, so that tile i+1 accumulates while tile i drains;
-//   warps 2..5      epilogue: TMEM -> registers -> FP64, staged through shared
+//   warps 2..9      epilogue: TMEM -> registers -> FP64, staged through shared
 //                   memory so that each warp store writes 16-byte pairs of
-//                   four rows (warp w reads TMEM lanes 32(w%4)...).
+//                   eight rows; warp w reads TMEM lanes 32(w%4)... and half
+//                   of the tile's columns (two warps per SM sub-partition,
+//                   so that one hides the other's latency).
 // mbarriers: full (TMA bytes landed), empty (MMAs that read the stage are
-// done, via tcgen05.commit), tfull (accumulator ready), tempty (the four
+// done, via tcgen05.commit), tfull (accumulator ready), tempty (the eight
 // epilogue warps have read the accumulator).
 //
 // Every wait is bounded. A wait that gives up sets *err and an abort flag in
@@ -43,14 +45,17 @@ namespace hs {
 
 namespace {
 
-constexpr int BM = 128, BN = 128, NT = 192;
+constexpr int BM = 128, BN = 128;
+constexpr int kEpiWarps = 8;              // two per TMEM lane quarter, each on half the columns
+constexpr int NT = 32 * (2 + kEpiWarps);  // TMA warp, MMA warp, epilogue warps
 constexpr int ROW_BYTES = 128;
 constexpr int TILE_BYTES = BM * ROW_BYTES;  // BN == BM
 constexpr long long WAIT_LIMIT = 20000000;  // try_wait rounds before giving up (seconds)
 
+constexpr int kMaxPairs = 4;  // operand pairs of one launch (the four graded sub-products)
 struct Maps {
-  CUtensorMap a[2][2];  // [operand pair][hi, lo]
-  CUtensorMap b[2][2];
+  CUtensorMap a[kMaxPairs][2];  // [operand pair][hi, lo]
+  CUtensorMap b[kMaxPairs][2];
 };
 
 // One launch unit: a K range [k0, k0 + Kp) of an operand pair (map); with
@@ -185,8 +190,8 @@ struct Cfg {
   static constexpr uint32_t ACC_COLS = NPASS == 1 ? BN : 2 * BN;  // one accumulator buffer
   static constexpr uint32_t TMEM_COLS = 2 * ACC_COLS;              // double buffered
   static constexpr int K_PER_TILE = ROW_BYTES / EB;                // elements per 128-byte row
-  static constexpr int STG_LD = 18;                                // staging row stride (doubles, 16-byte rows)
-  static constexpr int STG_BYTES = 4 * 32 * STG_LD * 8;            // one 32 x 16 block per epilogue warp
+  static constexpr int STG_LD = 10;                                // staging row stride (doubles, 16-byte rows)
+  static constexpr int STG_BYTES = kEpiWarps * 32 * STG_LD * 8;    // one 32 x 8 block per epilogue warp
   static constexpr int BAR_BYTES = 256;
   static constexpr int SMEM = STAGES * STAGE_BYTES + STG_BYTES + BAR_BYTES + 1024;
   static_assert(SMEM <= 232448, "shared memory per CTA");
@@ -239,7 +244,7 @@ __global__ void __launch_bounds__(NT, 1) gemm_tc_kernel(const __grid_constant__ 
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(smem_u32(&tfull[b]), 1);
-      mbar_init(smem_u32(&tempty[b]), 4);
+      mbar_init(smem_u32(&tempty[b]), kEpiWarps);
     }
     mbar_init(smem_u32(drain), 1);
     *abort_flag = 0;
@@ -332,8 +337,9 @@ __global__ void __launch_bounds__(NT, 1) gemm_tc_kernel(const __grid_constant__ 
     }
   } else if (warp >= 2) {
     // ---- epilogue: TMEM -> registers -> shared staging -> coalesced FP64 stores ----
-    const int q = warp & 3;  // TMEM lane quarter this warp may read
-    double* stg = stage_c + q * 32 * K::STG_LD;
+    const int q = warp & 3;               // TMEM lane quarter this warp may read
+    const int half = (warp - 2) / 4;      // columns [64 half, 64 half + 64) of the tile
+    double* stg = stage_c + (warp - 2) * 32 * K::STG_LD;
     const uint32_t lane_base = (uint32_t)(q * 32) << 16;
     int local = 0;
     for (int t = blockIdx.x; t < total_tiles; t += gridDim.x, ++local) {
@@ -349,7 +355,7 @@ __global__ void __launch_bounds__(NT, 1) gemm_tc_kernel(const __grid_constant__ 
       const int row0 = r.m0 + q * 32;
       // 16-byte stores when every row start is 16-byte aligned
       const bool vec = (P.ldc % 2 == 0) && ((reinterpret_cast<uintptr_t>(P.c) & 15) == 0);
-      for (int c = 0; c < BN && r.n0 + c < P.N; c += 32) {
+      for (int c = 64 * half; c < 64 * half + 64 && r.n0 + c < P.N; c += 32) {
         uint32_t r0[32], r1[32];
         if (ktiles > 0) {
           tmem_ld32(d + c, r0);
@@ -357,18 +363,18 @@ __global__ void __launch_bounds__(NT, 1) gemm_tc_kernel(const __grid_constant__ 
           tmem_wait_ld();
         }
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          // this lane's row, 16 columns, widened to FP64 on the bit patterns;
+        for (int h = 0; h < 4; ++h) {
+          // this lane's row, 8 columns, widened to FP64 on the bit patterns;
           // the correction joins the main accumulator with one FP32 add
 #pragma unroll
-          for (int j = 0; j < 16; j += 2) {
+          for (int j = 0; j < 8; j += 2) {
             double v[2];
 #pragma unroll
             for (int u = 0; u < 2; ++u) {
               uint32_t x = 0u;
               if (ktiles > 0) {
-                float f = __uint_as_float(r0[16 * h + j + u]);
-                if (NPASS == 3) f += __uint_as_float(r1[16 * h + j + u]);
+                float f = __uint_as_float(r0[8 * h + j + u]);
+                if (NPASS == 3) f += __uint_as_float(r1[8 * h + j + u]);
                 x = __float_as_uint(f);
               }
               unsigned long long w;
@@ -378,14 +384,14 @@ __global__ void __launch_bounds__(NT, 1) gemm_tc_kernel(const __grid_constant__ 
             *reinterpret_cast<double2*>(&stg[lane * K::STG_LD + j]) = make_double2(v[0], v[1]);
           }
           __syncwarp();
-          // eight lanes per row, two columns each: four rows per warp store
-          const int col = r.n0 + c + 16 * h + 2 * (lane & 7);
+          // four lanes per row, two columns each: eight rows per warp store
+          const int col = r.n0 + c + 8 * h + 2 * (lane & 3);
 #pragma unroll
-          for (int i0 = 0; i0 < 32; i0 += 4) {
-            const int i = i0 + (lane >> 3);
+          for (int i0 = 0; i0 < 32; i0 += 8) {
+            const int i = i0 + (lane >> 2);
             const int row = row0 + i;
             if (row < P.M && col < P.N) {
-              const double2 x = *reinterpret_cast<const double2*>(&stg[i * K::STG_LD + 2 * (lane & 7)]);
+              const double2 x = *reinterpret_cast<const double2*>(&stg[i * K::STG_LD + 2 * (lane & 3)]);
               double* dst = P.c + (long long)row * P.ldc + col;
               if (vec && col + 1 < P.N) {
                 *reinterpret_cast<double2*>(dst) = x;
@@ -457,13 +463,10 @@ __global__ void tc_splitk_reduce_kernel(const double* __restrict__ part, int nsp
 template <int NPASS, int EB>
 cudaError_t run(const TcProblem* probs, int nprob, int* err, cudaStream_t s, double* part, long long part_elems) {
   using K = Cfg<NPASS, EB>;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(gemm_tc_kernel<NPASS, EB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  // set once per process (thread-safe static initialisation)
+  static const cudaError_t attr_err = cudaFuncSetAttribute(gemm_tc_kernel<NPASS, EB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          K::SMEM);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  if (attr_err != cudaSuccess) return attr_err;
   Maps maps;
   memset(&maps, 0, sizeof maps);
   Group g{};
@@ -526,12 +529,12 @@ cudaError_t run(const TcProblem* probs, int nprob, int* err, cudaStream_t s, dou
     }
   }
   if (tiles == 0) return cudaSuccess;
-  static int sms = 0;
-  if (sms == 0) {
-    int dev = 0;
+  static const int sms = [] {
+    int dev = 0, n = 0;
     cudaGetDevice(&dev);
-    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 148;
-  }
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 148;
+    return n;
+  }();
   const int grid = tiles < sms ? tiles : sms;
   gemm_tc_kernel<NPASS, EB><<<grid, NT, K::SMEM, s>>>(maps, g, tiles, err);
   cudaError_t e = cudaGetLastError();
@@ -550,7 +553,7 @@ cudaError_t run(const TcProblem* probs, int nprob, int* err, cudaStream_t s, dou
 
 cudaError_t launch_gemm_tc(int precision, const TcProblem* probs, int nprob, int* err, cudaStream_t s,
                            double* part, long long part_elems) {
-  if (nprob > 2) return cudaErrorInvalidValue;
+  if (nprob > kMaxPairs) return cudaErrorInvalidValue;
   switch (precision) {
     case HS_PREC_TF32X3:
       return run<3, 4>(probs, nprob, err, s, part, part_elems);

@@ -342,13 +342,10 @@ cudaError_t launch_jacobi_eig_pair(float* A0, int m0, float* w0, float* A1, int 
   const int m = m0 > m1 ? m0 : m1;
   if (m <= 0) return cudaSuccess;
   if (m > kMaxSub) return cudaErrorInvalidValue;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(jacobi_eig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  // set once per process (thread-safe static initialisation)
+  static const cudaError_t attr_err = cudaFuncSetAttribute(jacobi_eig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)jacobi_smem_bytes(kMaxSub));
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  if (attr_err != cudaSuccess) return attr_err;
   jacobi_eig_kernel<<<2, 1024, jacobi_smem_bytes(m), s>>>(A0, m0, w0, A1, m1, w1, status);
   return cudaGetLastError();
 }
@@ -375,13 +372,10 @@ cudaError_t launch_fill_random_rows(double* X, int r0, int m, int n, unsigned lo
 cudaError_t launch_chol_inv(const double* G, int m, double* Linv, int* status, cudaStream_t s) {
   if (m <= 0 || m > kMaxSub) return cudaErrorInvalidValue;
   const size_t smem = (size_t)m * m * sizeof(double);
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(chol_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  // set once per process (thread-safe static initialisation)
+  static const cudaError_t attr_err = cudaFuncSetAttribute(chol_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          kMaxSub * kMaxSub * (int)sizeof(double));
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  if (attr_err != cudaSuccess) return attr_err;
   chol_inv_kernel<<<1, 256, smem, s>>>(G, m, Linv, status);
   return cudaGetLastError();
 }

@@ -108,6 +108,15 @@ WORKLOADS = {
 }
 
 
+def batched_workload(n: int = 32, seed: int | None = None) -> list[tuple[int, int, np.ndarray]]:
+    """n independent real iPEPS instances: D uniform in {3, ..., 7} from
+    rng(SEED_BASE + 4), chi = 4 D^2, instance i seeded SEED_BASE + 4000 + i.
+    Returns (D, chi, A) per instance."""
+    rng = np.random.default_rng(SEED_BASE + 4 if seed is None else seed)
+    Ds = rng.integers(3, 8, size=n)
+    return [(int(D), 4 * int(D) * int(D), random_ipeps(2, int(D), SEED_BASE + 4000 + i)) for i, D in enumerate(Ds)]
+
+
 def workload_tensor(k: int) -> np.ndarray:
     """The seeded iPEPS tensor of workload k (seed SEED_BASE + k)."""
     w = WORKLOADS[k]

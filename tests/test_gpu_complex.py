@@ -45,14 +45,16 @@ def _env_observables(c, A):
     return C, T, rho
 
 
-@pytest.mark.parametrize("eig,tol_e,tol_s", [("f64", 1e-10, 1e-9), ("f32p", 1e-6, 1e-5)])
-def test_graded_ctmrg_matches_oracle(ctx, eig, tol_e, tol_s):
+@pytest.mark.parametrize("precision,eig,tol_e,tol_s", [("f64", "f64", 1e-10, 1e-9), ("f64", "f32p", 1e-6, 1e-5),
+                                                      ("tf32x3", "f64", 1e-7, 1e-5), ("tf32x3", "f32p", 1e-6, 1e-5)])
+def test_graded_ctmrg_matches_oracle(ctx, precision, eig, tol_e, tol_s):
     """Small complex workload (D=3, chi=27): energy and corner spectrum at every
-    checkpoint against the oracle's SVD rule (oriented C4v CTMRG)."""
+    checkpoint against the oracle's SVD rule (oriented C4v CTMRG), with the graded
+    GEMMs in FP64 or on the tensor cores (TF32x3)."""
     from paper_2410_11596_gb300.api import CTMRG
     g = golden(6)
     A = inputs.workload_tensor(6)
-    c = CTMRG(ctx, A, g["chi"], eig=eig)
+    c = CTMRG(ctx, A, g["chi"], precision=precision, eig=eig)
     h = inputs.heisenberg_bond()
     done = 0
     for m in sorted(int(k) for k in g["checkpoints"]):
