@@ -305,6 +305,9 @@ hs_status hs_hotrg_step(hs_ctx ctx, hs_z2_tensor* t, int chi, int direction, hs_
  * construction; the entries are computed for (row <= col) and mirrored.
  * HS_RDM_ENV_ONE_SITE: the one-site environment eps[u, l, d, r] (Eq. (4)),
  * (D^2)^4 doubles in the plain combined basis; h and tr_out unused.
+ * HS_C128 (complex A, interleaved; graded environment): rho, eps and the
+ * traces are interleaved complex128 (tr_out: Re/Im of Tr rho, then of
+ * Tr(rho h)), computed in complex arithmetic on the clockwise boundary ring.
  * Asynchronous. */
 hs_status hs_rdm(hs_ctx ctx, const hs_env* env, const double* A, int d, int D, hs_dtype dtype,
                  hs_rdm_kind kind, const double* h, double* out, double* tr_out);

@@ -211,8 +211,13 @@ class CTMRG:
 
     @on_ctx_stream
     def one_site_env(self) -> torch.Tensor:
-        """eps[u, l, d, r] in the plain combined basis (Eq. (4))."""
+        """eps[u, l, d, r] in the plain combined basis (Eq. (4)); complex128 for complex A."""
         q = self.D * self.D
+        if self.complex:
+            eps = torch.empty((q, q, q, q, 2), dtype=torch.float64, device=self.A.device)
+            L.hs_rdm(self.ctx.handle, self.env, self.A, self.d, self.D, L.HS_C128, L.HS_RDM_ENV_ONE_SITE,
+                     None, eps, None)
+            return torch.view_as_complex(eps)
         eps = torch.empty((q, q, q, q), dtype=torch.float64, device=self.A.device)
         L.hs_rdm(self.ctx.handle, self.env, self.A, self.d, self.D, L.HS_F64, L.HS_RDM_ENV_ONE_SITE,
                  None, eps, None)

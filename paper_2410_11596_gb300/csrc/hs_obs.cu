@@ -318,8 +318,8 @@ hs_status zpermute(hs_ctx ctx, const Z2Mat& in, const Z2Mat& out, std::initializ
 //   L[b,d1,l1,u1,t] = T[b,d1,c] H[c,l1,e] T[e,u1,t]  (also the right chain R[t,u2,r2,d2,b])
 //   LB[(b,t)|(s1,s1',m)] = L a1 over (d1,l1,u1); RB[(t,b)|(s2,s2',m)] = L a2 over (u2,r2,d2)
 //   rho4[(s1,s1')|(s2,s2')] = sum_{b,t,m} LB RB
-hs_status rdm_complex(hs_ctx ctx, const hs_env* env, const double* A, int d, int D, const double* h, double* out,
-                      double* tr_out) {
+hs_status rdm_complex(hs_ctx ctx, const hs_env* env, const double* A, int d, int D, hs_rdm_kind kind,
+                      const double* h, double* out, double* tr_out) {
   cudaStream_t s = ctx->stream;
   const long long chi = env->chi_even + env->chi_odd, q = (long long)D * D, d2 = (long long)d * d;
   const long long c2 = chi * chi, cqc = chi * q * chi, c2q2 = c2 * q * q, c2q3 = c2q2 * q;
@@ -347,6 +347,26 @@ hs_status rdm_complex(hs_ctx ctx, const hs_env* env, const double* A, int d, int
   HS_TRY(zgemm(ctx, dense_gemm(chi, q * chi, chi), Cz, Tqz, H1));                               // H1[a|(x,e)]
   HS_TRY(zgemm(ctx, dense_gemm(chi * q, chi, chi), H1, Ctz, Hz));                               // H[(a,x)|b]
   HS_TRY(zpermute(ctx, dense({chi, q, chi}), dense({q, chi, chi}), {1, 2, 0}, Hz, Hq));        // Hq[(l,e)|c]
+  if (kind == HS_RDM_ENV_ONE_SITE) {
+    // eps[u,l,d,r] = H[a,u,b] T[b,r,b'] H[b',d,a'] T[a',l,a] (the clockwise ring of Eq. (4))
+    ZBuf Y1 = zbuf(ctx, 7, c2q2), Y2 = zbuf(ctx, 8, c2q3), Y2p = zbuf(ctx, 9, c2q3), Tl = zbuf(ctx, 10, cqc),
+         E3 = zbuf(ctx, 11, q * q * q * q);
+    if (!E3.re) return fail(HS_ERR_CUDA, "workspace allocation failed");
+    HS_TRY(zgemm(ctx, dense_gemm(chi * q, q * chi, chi), Hz, Tqz, Y1));                        // [(a,u)|(r,b')]
+    HS_TRY(zgemm(ctx, dense_gemm(chi * q * q, q * chi, chi), Y1, Hq, Y2));                     // [(a,u,r)|(d,a')]
+    HS_TRY(zpermute(ctx, dense({chi, q, q, q, chi}), dense({q, q, q, chi, chi}), {1, 2, 3, 4, 0}, Y2, Y2p));
+    HS_TRY(zpermute(ctx, dense({chi, q, chi}), dense({q, chi, chi}), {1, 0, 2}, Tz, Tl));      // Tl[l|(a',a)]
+    HS_TRY(zgemm(ctx, dense_gemm(q * q * q, q, chi * chi), Y2p, Tl, E3));                       // [(u,r,d)|l]
+    // eps[u,l,d,r] (interleaved complex): permute each part, then interleave
+    ZBuf Eo = zbuf(ctx, 12, q * q * q * q);
+    if (!Eo.re) return fail(HS_ERR_CUDA, "workspace allocation failed");
+    HS_TRY(zpermute(ctx, dense({q, q, q, q}), dense({q, q, q, q}), {0, 3, 2, 1}, E3, Eo));
+    const long long n4 = q * q * q * q;
+    HS_TRY(ctx->r[2].ensure(2 * n4 * 8));
+    HS_CUDA(cudaMemcpyAsync(ctx->r[2].d(), Eo.re, n4 * 8, cudaMemcpyDeviceToDevice, s));
+    HS_CUDA(cudaMemcpyAsync(ctx->r[2].d() + n4, Eo.im, n4 * 8, cudaMemcpyDeviceToDevice, s));
+    return permute(ctx, dense({2, n4}), dense({n4, 2}), {1, 0}, ctx->r[2].d(), out);
+  }
   HS_TRY(zgemm(ctx, dense_gemm(chi * q, q * chi, chi), Tz, Hq, L1));                            // L1[(b,d1)|(l1,e)]
   HS_TRY(zgemm(ctx, dense_gemm(chi * q * q, q * chi, chi), L1, Tqz, L2));                       // L2[(b,d1,l1)|(u1,t)]
   HS_TRY(zpermute(ctx, dense({chi, q, q, q, chi}), dense({chi, chi, q, q, q}), {0, 4, 1, 2, 3}, L2, L2p));
@@ -382,7 +402,7 @@ hs_status rdm_vjp_complex(hs_ctx ctx, const hs_env* env, const double* A, int d,
   const long long c2 = chi * chi, c2q3 = c2 * q * q * q, nb = c2 * d2 * q;
   // forward: leaves L2p (slot 9), LB (1), RB (2), LBp (4), RBp (5)
   HS_TRY(ctx->r[3].ensure(2 * d2 * d2 * 8 + 4 * 8));
-  HS_TRY(rdm_complex(ctx, env, A, d, D, nullptr, ctx->r[3].d(), ctx->r[3].d() + 2 * d2 * d2));
+  HS_TRY(rdm_complex(ctx, env, A, d, D, HS_RDM_TWO_SITE, nullptr, ctx->r[3].d(), ctx->r[3].d() + 2 * d2 * d2));
   ZBuf L2p = zbuf(ctx, 9, c2q3), LBp = zbuf(ctx, 4, nb), RBp = zbuf(ctx, 5, nb);
   // cotangent of rho4[s1, s1', s2, s2'] and of its transpose
   ZBuf G = zbuf(ctx, 12, d2 * d2), G4 = zbuf(ctx, 13, d2 * d2), G4t = zbuf(ctx, 14, d2 * d2);
@@ -508,10 +528,7 @@ extern "C" hs_status hs_rdm(hs_ctx ctx, const hs_env* env, const double* A, int 
     return fail(HS_ERR_INVALID_ARG, "unknown rdm kind");
   if (kind == HS_RDM_TWO_SITE && !tr_out) return fail(HS_ERR_INVALID_ARG, "tr_out is required");
   if ((dtype == HS_C128) != (env->dtype == HS_C128)) return fail(HS_ERR_DTYPE, "A and environment disagree on dtype");
-  if (dtype == HS_C128) {
-    if (kind != HS_RDM_TWO_SITE) return fail(HS_ERR_UNSUPPORTED, "complex one-site environment not in this build");
-    return rdm_complex(ctx, env, A, d, D, h, out, tr_out);
-  }
+  if (dtype == HS_C128) return rdm_complex(ctx, env, A, d, D, kind, h, out, tr_out);
   HS_TRY(rdm_chain(ctx, env, A, d, D, kind, out));
   if (kind == HS_RDM_ENV_ONE_SITE) return HS_OK;
   finish_rho_kernel<<<1, 256, 0, ctx->stream>>>(ctx->r[6].d(), d, env->basis == HS_BASIS_HERMITIAN, h, out,

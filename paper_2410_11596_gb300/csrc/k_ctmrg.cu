@@ -415,10 +415,12 @@ cudaError_t launch_select(const double* w0, int n0, const double* w1, int n1, in
   const bool staged = smem <= kSmemMax;
   if (!staged) smem = picks;
   if (smem > kSmemMax) return cudaErrorInvalidValue;
-  // set once per process (thread-safe static initialisation)
-  static const cudaError_t attr_err =
-      cudaFuncSetAttribute(select_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax);
-  if (attr_err != cudaSuccess) return attr_err;
+  if (smem > 48 * 1024) {
+    // opt in beyond the default 48 KB only when needed (once per process)
+    static const cudaError_t attr_err =
+        cudaFuncSetAttribute(select_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax);
+    if (attr_err != cudaSuccess) return attr_err;
+  }
   select_kernel<<<1, 256, smem, s>>>(w0, n0, w1, n1, chi, idx, lam, out, staged);
   return cudaGetLastError();
 }

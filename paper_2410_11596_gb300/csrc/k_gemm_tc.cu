@@ -475,7 +475,7 @@ cudaError_t run(const TcProblem* probs, int nprob, int* err, cudaStream_t s, dou
     const double* part;
     int nsplit, M, N, ldc;
     double* c;
-  } red[2];
+  } red[kMaxPairs];  // one reduction per split problem (at most one per operand pair)
   int nred = 0;
   long long part_used = 0;
   for (int i = 0; i < nprob; ++i) {
@@ -524,6 +524,7 @@ cudaError_t run(const TcProblem* probs, int nprob, int* err, cudaStream_t s, dou
       tiles += ptiles;
     }
     if (ns > 1) {
+      if (nred >= kMaxPairs) return cudaErrorInvalidValue;
       red[nred++] = {part + part_used, ns, p.M, p.N, p.ldc, p.c};
       part_used += (long long)ns * p.M * p.N;
     }

@@ -225,7 +225,7 @@ __global__ void __launch_bounds__(1024) jacobi_eig_kernel(float* __restrict__ A0
   float* V = A + m * ld;          // m x ld, V[i * ld + j] = component i of vector j
   float* cs = V + m * ld;         // cos, sin per pair
   int* pq = reinterpret_cast<int*>(cs + 2 * ((m + 1) / 2 + 1));
-  __shared__ int nrot;
+  __shared__ int nrot, rrot;
   const int M = (m + 1) & ~1;     // even player count (index m is a dummy when m is odd)
   const int npair = M / 2;
   const float kRelTol = fmaxf(4e-7f, sqrtf((float)m) * 6e-8f);
@@ -250,6 +250,8 @@ __global__ void __launch_bounds__(1024) jacobi_eig_kernel(float* __restrict__ A0
     if (threadIdx.x == 0) nrot = 0;
     __syncthreads();
     for (int r = 0; r < M - 1; ++r) {
+      if (threadIdx.x == 0) rrot = 0;
+      __syncthreads();
       // round-robin pairing: player M-1 fixed, the others rotate
       for (int k = threadIdx.x; k < npair; k += blockDim.x) {
         int p = k == 0 ? M - 1 : (r + k) % (M - 1);
@@ -270,7 +272,7 @@ __global__ void __launch_bounds__(1024) jacobi_eig_kernel(float* __restrict__ A0
             const float t = (th >= 0.f ? 1.f : -1.f) / (fabsf(th) + sqrtf(th * th + 1.f));
             c = rsqrtf(t * t + 1.f);
             sn = t * c;
-            atomicAdd(&nrot, 1);
+            atomicAdd(&rrot, 1);
           }
         }
         pq[2 * k] = p;
@@ -279,6 +281,8 @@ __global__ void __launch_bounds__(1024) jacobi_eig_kernel(float* __restrict__ A0
         cs[2 * k + 1] = sn;
       }
       __syncthreads();
+      if (rrot == 0) continue;  // nothing rotates in this round (block-uniform)
+      if (threadIdx.x == 0) nrot += rrot;
       // A <- J^T A J: the rotations act on disjoint pairs, so every 2 x 2 block
       // (rows of pair a, columns of pair b) transforms on its own; V <- V J
       const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;

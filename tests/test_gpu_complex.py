@@ -124,3 +124,29 @@ def test_graded_ctmrg_full_size_complex_workload(ctx):
     e = c.energy(inputs.heisenberg_bond())
     print(f"w5 |dE| = {abs(e - g['checkpoints'][str(g['moves'])]['energy']):.3e}")
     assert abs(e - g["checkpoints"][str(g["moves"])]["energy"]) < 1e-9
+
+
+def test_graded_one_site_env_and_symmetry_error(ctx):
+    """eps of Eq. (4) from the library for a complex environment equals the oracle's
+    network on that environment, and its S_err vanishes to rounding."""
+    from paper_2410_11596_gb300.api import CTMRG
+    A = inputs.workload_tensor(6)
+    c = CTMRG(ctx, A, 27)
+    c.run(20)
+    eps = c.one_site_env().cpu().numpy()
+    C, T = c.dense_env()
+    ref = ob.one_site_environment(C.cpu().numpy(), T.cpu().numpy())
+    assert np.abs(eps - ref).max() <= 1e-12 * np.abs(ref).max()
+    assert ob.symmetry_error(eps, 3) < 1e-12
+
+
+def test_graded_ctmrg_full_size_tensor_cores(ctx):
+    """Complex workload at full size with the graded GEMMs on tcgen05 (TF32x3; four
+    split-K sub-products per launch) and the FP32 eigensolver: energy vs the oracle."""
+    from paper_2410_11596_gb300.api import CTMRG
+    g = golden(5)
+    c = CTMRG(ctx, inputs.workload_tensor(5), g["chi"], precision="tf32x3", eig="f32p")
+    c.run(g["moves"])
+    e = c.energy(inputs.heisenberg_bond())
+    print(f"w5 tf32x3 |dE| = {abs(e - g['checkpoints'][str(g['moves'])]['energy']):.3e}")
+    assert abs(e - g["checkpoints"][str(g["moves"])]["energy"]) < 1e-6
