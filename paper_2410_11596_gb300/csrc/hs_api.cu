@@ -218,8 +218,18 @@ hs_status tc_split(hs_ctx ctx, hs_precision prec, const Z2Mat& src_layout, const
   PhaseScope ps(ctx, HS_PHASE_PERMUTE);
   int pm[kMaxLegs] = {0}, i = 0;
   for (int v : perm) pm[i++] = v;
-  HS_CUDA(cudaMemsetAsync(hi.p, 0, nb, ctx->stream));
-  HS_CUDA(cudaMemsetAsync(lo.p, 0, nb, ctx->stream));
+  // the split writes every entry of the layout but none of the K padding:
+  // zero the buffers only when the last split into them had another layout
+  unsigned long long key = 0x9E3779B97F4A7C15ull ^ (unsigned long long)eb;
+  for (int p = 0; p < 2; ++p)
+    for (long long v : {z2_rows(P, p), z2_cols(P, p), z2_ld(P, p)})
+      key = (key ^ (unsigned long long)v) * 0x100000001B3ull;
+  key |= 1;
+  if (hi.zkey != key || lo.zkey != key) {
+    HS_CUDA(cudaMemsetAsync(hi.p, 0, nb, ctx->stream));
+    HS_CUDA(cudaMemsetAsync(lo.p, 0, nb, ctx->stream));
+    hi.zkey = lo.zkey = key;
+  }
   const PermPlan plan = make_perm_plan(src_layout, P, pm);
   HS_CUDA(launch_permute_split(plan, src, hi.p, lo.p, tc_mode(prec), ctx->stream));
   if (plan.nbox > 0) ctx->launches += 1;
@@ -447,6 +457,104 @@ hs_status lowdin_rows(hs_ctx ctx, hs_precision prec, double* X, int m, int n, do
   return HS_OK;
 }
 
+// Chebyshev-filtered power step on block b after a Rayleigh-Ritz step that
+// did not converge (Ritz vectors in sxr[b], their products with H in szr[b],
+// FP32 Ritz values theta, kept_b of them in the selection). The spectrum of
+// C' falls off slowly past the cut, so plain power steps gain little there;
+// a Chebyshev polynomial T_deg(H / a) damps |lambda| <= a and amplifies the
+// states just above the cut by T_deg(|lambda| / a) (Zhou and Saad, 2007).
+// a is an interior Ritz magnitude of the window, an estimate of the largest
+// |lambda| outside it. The filter also grows the top of the spectrum by
+// orders of magnitude more than the cut, which would swamp the rows in
+// rounding; so the Ritz pairs with |theta| >= kLock a are locked: they take
+// one plain power step (their rows of Zr) and their span is projected out
+// after every product of the filtered rows. X receives the locked rows, then
+// the filtered ones (not normalised). Returns false in *used when no interior
+// magnitude exists (the caller then takes a plain step).
+hs_status cheb_filter_block(hs_ctx ctx, hs_precision prec, int b, int m, int n, const double* H,
+                            const float* theta, int kept_b, double* X, bool* used) {
+  constexpr int kDeg = 6;
+  constexpr double kLock = 16.0, kEdge = 0.3;
+  *used = false;
+  cudaStream_t s = ctx->stream;
+  const bool tc = prec != HS_PREC_F64;
+  std::vector<int> ord(m);
+  for (int i = 0; i < m; ++i) ord[i] = i;
+  std::stable_sort(ord.begin(), ord.end(),
+                   [&](int x, int y) { return std::fabs((double)theta[x]) > std::fabs((double)theta[y]); });
+  int r = kept_b + 2 + (int)(kEdge * (m - kept_b - 2));
+  r = std::max(0, std::min(r, m - 1));
+  const double a = std::fabs((double)theta[ord[r]]);
+  if (!(a > 0.0) || r <= kept_b) return HS_OK;
+  std::vector<int> idx;
+  idx.reserve(m);
+  for (int i = 0; i < m; ++i)
+    if (std::fabs((double)theta[i]) >= kLock * a) idx.push_back(i);
+  const int mL = (int)idx.size(), mU = m - mL;
+  for (int i = 0; i < m; ++i)
+    if (std::fabs((double)theta[i]) < kLock * a) idx.push_back(i);
+  HS_TRY(ctx->sf_idx.ensure((size_t)m * sizeof(int)));
+  int* didx = static_cast<int*>(ctx->sf_idx.p);
+  HS_CUDA(cudaMemcpyAsync(didx, idx.data(), (size_t)m * sizeof(int), cudaMemcpyHostToDevice, s));
+  const size_t mn = (size_t)m * n * sizeof(double);
+  for (auto* buf : {&ctx->sf_y[0], &ctx->sf_y[1], &ctx->sf_y[2], &ctx->sf_z, &ctx->sf_t, &ctx->sf_q, &ctx->sf_qt})
+    HS_TRY(buf->ensure(mn));
+  HS_TRY(ctx->sf_s.ensure((size_t)m * m * sizeof(double)));
+  const double* Xr = ctx->sxr[b].d();
+  const double* Zr = ctx->szr[b].d();
+  // locked rows: one power step
+  HS_CUDA(launch_gather_rows_idx(Zr, didx, mL, n, X, s));
+  ctx->launches += 1;
+  if (mU > 0) {
+    double* Q = ctx->sf_q.d();
+    double* Qt = ctx->sf_qt.d();
+    double* Z = ctx->sf_z.d();
+    double* T = ctx->sf_t.d();
+    double* S = ctx->sf_s.d();
+    double* Y[3] = {ctx->sf_y[0].d(), ctx->sf_y[1].d(), ctx->sf_y[2].d()};
+    if (mL > 0) {
+      HS_CUDA(launch_gather_rows_idx(Xr, didx, mL, n, Q, s));
+      HS_TRY(permute(ctx, dense2(mL, n), dense2(n, mL), {1, 0}, Q, Qt));
+      ctx->launches += 1;
+    }
+    HS_CUDA(launch_gather_rows_idx(Xr, didx + mL, mU, n, Y[0], s));
+    HS_CUDA(launch_gather_rows_idx(Zr, didx + mL, mU, n, Z, s));
+    ctx->launches += 2;
+    const long long cnt = (long long)mU * n;
+    // Z <- Z - (Z Q^T) Q: the part of Z outside the locked span (into T, then combined)
+    auto project = [&]() -> hs_status {
+      if (mL == 0) return HS_OK;
+      HS_TRY(dense_gemm_any(ctx, prec, mU, mL, n, Z, Q, S));
+      HS_TRY(dense_gemm_any(ctx, prec, mU, n, mL, S, Qt, T));
+      return HS_OK;
+    };
+    HS_TRY(project());
+    HS_CUDA(launch_cheb_step(Y[1], Z, mL > 0 ? T : nullptr, nullptr, cnt, 1.0 / a, 0.0, s));
+    ctx->launches += 1;
+    int prev = 0, cur = 1;
+    for (int j = 2; j <= kDeg; ++j) {
+      const int next = 3 - prev - cur;
+      if (tc) {
+        HS_TRY(tc_split(ctx, prec, dense2(mU, n), dense2(mU, n), {0, 1}, Y[cur], ctx->sx_hi, ctx->sx_lo));
+        HS_TRY(tc_run(ctx, prec, dense2(mU, n), ctx->sx_hi, ctx->sx_lo, dense2(n, n), ctx->sH_hi[b], ctx->sH_lo[b],
+                      dense2(mU, n), Z));
+        ctx->phase_flops[HS_PHASE_GEMM_TC] += 2.0 * mU * (double)n * n;
+      } else {
+        HS_TRY(gemm(ctx, HS_GEMM_OWN, GemmGroup{1, {GemmProblem{mU, n, n, n, n, n, 0, 0, 0}}}, Y[cur], H, Z));
+        ctx->phase_flops[HS_PHASE_GEMM] += 2.0 * mU * (double)n * n;
+      }
+      HS_TRY(project());
+      HS_CUDA(launch_cheb_step(Y[next], Z, mL > 0 ? T : nullptr, Y[prev], cnt, 2.0 / a, -1.0, s));
+      ctx->launches += 1;
+      prev = cur;
+      cur = next;
+    }
+    HS_CUDA(cudaMemcpyAsync(X + (long long)mL * n, Y[cur], (size_t)cnt * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  }
+  *used = true;
+  return HS_OK;
+}
+
 // Subspace iteration on both parity blocks H_b (n_b x n_b, FP64 in place in
 // the C' buffer), warm-started from the previous move's kept rows. On success
 // (*done) w[0 .. m0+m1) holds the Ritz values of block 0 then block 1
@@ -463,7 +571,7 @@ hs_status subspace_projector(hs_ctx ctx, hs_env* env, int chi, int n0, int n1, d
   if (!(ctx->ws_valid && ctx->ws_env == env)) return HS_OK;
   *reason = 2;
   if (!(ctx->ws_n[0] == n0 && ctx->ws_n[1] == n1)) return HS_OK;
-  constexpr int kOver = 24, kMaxIt = 4;
+  constexpr int kOver = 24, kMaxIt = 5;
   cudaStream_t s = ctx->stream;
   const bool tc = env->precision != HS_PREC_F64;
   // residual tolerance relative to max|theta|: above the rounding floor of
@@ -606,11 +714,16 @@ hs_status subspace_projector(hs_ctx ctx, hs_env* env, int chi, int n0, int n1, d
     prev_worst = worst;
     for (int b = 0; b < 2; ++b)
       if (m[b] > 0) {
-        // power step on the Ritz basis: rows of Zr = theta_i x_i + residual.
-        // Far from convergence they can be far from orthogonal, where the
-        // Loewdin iteration diverges: orthonormalise by Cholesky-QR twice (FP64)
-        HS_CUDA(cudaMemcpyAsync(ctx->sx[b].p, ctx->szr[b].p, (size_t)m[b] * n[b] * sizeof(double),
-                                cudaMemcpyDeviceToDevice, s));
+        // next basis: a Chebyshev-filtered step where possible, else a plain
+        // power step (rows of Zr = theta_i x_i + residual). Far from
+        // convergence the rows can be far from orthogonal, where the Loewdin
+        // iteration diverges: orthonormalise by Cholesky-QR twice (FP64)
+        bool filtered = false;
+        HS_TRY(cheb_filter_block(ctx, prec, b, m[b], n[b], H[b], hth.data() + (b ? m[0] : 0), kept[b],
+                                 ctx->sx[b].d(), &filtered));
+        if (!filtered)
+          HS_CUDA(cudaMemcpyAsync(ctx->sx[b].p, ctx->szr[b].p, (size_t)m[b] * n[b] * sizeof(double),
+                                  cudaMemcpyDeviceToDevice, s));
         HS_CUDA(launch_row_normalize(ctx->sx[b].d(), m[b], n[b], s));
         HS_TRY(cholqr2(ctx, ctx->sx[b].d(), m[b], n[b], ctx->sxc[b].d(), bad));
       }
@@ -1231,6 +1344,7 @@ hs_status hs_gemm(hs_ctx ctx, hs_precision precision, int M, int N, int K, const
   HS_TRY(ctx->tc_x_lo.ensure((size_t)M * Kp * eb));
   HS_TRY(ctx->tc_b_hi.ensure((size_t)N * Kp * eb));
   HS_TRY(ctx->tc_b_lo.ensure((size_t)N * Kp * eb));
+  ctx->tc_x_hi.zkey = ctx->tc_x_lo.zkey = ctx->tc_b_hi.zkey = ctx->tc_b_lo.zkey = 0;
   HS_CUDA(launch_split_pad(A, M, K, lda, ctx->tc_x_hi.p, ctx->tc_x_lo.p, Kp, tc_mode(precision), ctx->stream));
   HS_CUDA(launch_split_pad(B, N, K, ldb, ctx->tc_b_hi.p, ctx->tc_b_lo.p, Kp, tc_mode(precision), ctx->stream));
   TcProblem t;

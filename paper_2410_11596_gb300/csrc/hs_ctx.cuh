@@ -55,11 +55,15 @@ constexpr long long kSplitKElems = 4ll << 20;
 struct DBuf {
   void* p = nullptr;
   size_t bytes = 0;
+  // key of the padded split layout whose pad entries are known to be zero
+  // (0: unknown). Only tc_split sets it; every other writer clears it.
+  unsigned long long zkey = 0;
   hs_status ensure(size_t want) {
     if (want <= bytes) return HS_OK;
     if (p) cudaFree(p);
     p = nullptr;
     bytes = 0;
+    zkey = 0;
     if (cudaMalloc(&p, want) != cudaSuccess) {
       cudaGetLastError();
       return fail(HS_ERR_CUDA, "cudaMalloc of %zu bytes failed", want);
@@ -71,6 +75,7 @@ struct DBuf {
     if (p) cudaFree(p);
     p = nullptr;
     bytes = 0;
+    zkey = 0;
   }
   double* d() const { return static_cast<double*>(p); }
 };
@@ -128,6 +133,10 @@ struct hs_ctx_s {
   int sH_n[2] = {0, 0};
   hs::DBuf ws_pt, sx[2], sz[2], sxc[2], szc[2], sxr[2], szr[2], sbm[2], sbw[2], sres[2], sth, sH_hi[2],
       sH_lo[2], sx_hi, sx_lo, sy_hi, sy_lo, schol;
+  // Chebyshev filter of the subspace eigensolver: three recurrence terms, the
+  // product, the projection and its coefficients, the locked rows (and their
+  // transpose), and the row order
+  hs::DBuf sf_y[3], sf_z, sf_t, sf_s, sf_q, sf_qt, sf_idx;
   // profiling: events between phases, harvested after the move's last sync
   bool prof = false;
   std::vector<cudaEvent_t> events;

@@ -79,6 +79,7 @@ hs_status ggemm(hs_ctx ctx, hs_precision prec, const GMat& Am, const double* A, 
   HS_TRY(ctx->sx_lo.ensure((size_t)ra * Kp * eb));
   HS_TRY(ctx->sy_hi.ensure((size_t)2 * rb * Kp * eb));
   HS_TRY(ctx->sy_lo.ensure((size_t)2 * rb * Kp * eb));
+  ctx->sx_hi.zkey = ctx->sx_lo.zkey = ctx->sy_hi.zkey = ctx->sy_lo.zkey = 0;
   {
     PhaseScope ps(ctx, HS_PHASE_PERMUTE);
     HS_CUDA(launch_split_pad(A, ra, (int)K, g_ld(Am), ctx->sx_hi.p, ctx->sx_lo.p, Kp, mode, ctx->stream));

@@ -317,6 +317,11 @@ int max_subspace();
 cudaError_t launch_jacobi_eig_pair(float* A0, int m0, float* w0, float* A1, int m1, float* w1, int* status,
                                    cudaStream_t s);
 cudaError_t launch_row_normalize(double* X, int m, int n, cudaStream_t s);
+// out row i = X row idx[i] for i < m (idx on the device; rows of n).
+cudaError_t launch_gather_rows_idx(const double* X, const int* idx, int m, int n, double* out, cudaStream_t s);
+// Y = alpha (Z - T) + beta Yold over count entries; T and Yold may be null.
+cudaError_t launch_cheb_step(double* Y, const double* Z, const double* T, const double* Yold, long long count,
+                             double alpha, double beta, cudaStream_t s);
 // X (m x n rows, FP64) = the m eigenvectors of largest |eigenvalue| of one
 // FP32 eigen-decomposition (ascending w, column-major V); idx is scratch (m ints).
 cudaError_t launch_top_rows(const float* w, const float* V, int n, int m, int* idx, double* X, cudaStream_t s);

@@ -101,7 +101,9 @@ __global__ void select_kernel(const double* __restrict__ w0g, int n0, const doub
                               int n1, int chi, int* __restrict__ idx, double* __restrict__ lam,
                               SelectOut* out, bool staged) {
   // both spectra staged in shared memory (the merge below is a serial walk),
-  // followed by the picked values and their blocks
+  // followed by the picked values and their blocks. The walk compares
+  // magnitudes as integers (IEEE bit patterns without the sign order like
+  // |x| for finite values): FP64 compares would run on the slow FP64 pipe.
   extern __shared__ double wsh[];
   const int keep = min(chi, n0 + n1);
   const double* w0 = w0g;
@@ -116,55 +118,71 @@ __global__ void select_kernel(const double* __restrict__ w0g, int n0, const doub
   }
   // sum of |w| over both spectra
   __shared__ double part[256];
+  __shared__ unsigned long long first_bits, last_bits;
   double acc = 0.0;
   for (int i = threadIdx.x; i < n0 + n1; i += blockDim.x) acc += fabs(i < n0 ? w0g[i] : w1g[i - n0]);
   part[threadIdx.x] = acc;
   __syncthreads();
-  if (threadIdx.x != 0) return;
-  double all = 0.0;
-  for (int t = 0; t < (int)blockDim.x; ++t) all += part[t];
-  const double* w[2] = {w0, w1};
-  int lo[2] = {0, 0}, hi[2] = {n0 - 1, n1 - 1}, cnt[2] = {0, 0};
-  double first = 0.0, last = 0.0, kept = 0.0;
-  for (int s = 0; s <= keep; ++s) {
-    int best_b = -1, best_i = -1;
-    double best = -1.0;
-    for (int b = 0; b < 2; ++b) {
-      if (lo[b] > hi[b]) continue;
-      const int cand[2] = {lo[b], hi[b]};
-      for (int c = 0; c < 2; ++c) {
-        const double v = fabs(w[b][cand[c]]);
-        if (v > best) {  // strict: earlier block, then lower index win ties
-          best = v;
-          best_b = b;
-          best_i = cand[c];
-        }
+  if (threadIdx.x == 0) {
+    constexpr unsigned long long kMag = 0x7FFFFFFFFFFFFFFFull;
+    const unsigned long long* u0 = reinterpret_cast<const unsigned long long*>(w0);
+    const unsigned long long* u1 = reinterpret_cast<const unsigned long long*>(w1);
+    int lo0 = 0, hi0 = n0 - 1, lo1 = 0, hi1 = n1 - 1, cnt0 = 0, cnt1 = 0;
+    unsigned long long fb = 0, lb = 0;
+    for (int s = 0; s <= keep; ++s) {
+      // candidates in tie order: block 0 low end, block 0 high end, block 1 low, block 1 high
+      int best_b = -1, best_i = -1;
+      unsigned long long best = 0;
+      bool any = false;
+      if (lo0 <= hi0) {
+        const unsigned long long a = u0[lo0] & kMag, c = u0[hi0] & kMag;
+        best = a; best_b = 0; best_i = lo0; any = true;
+        if (c > best) { best = c; best_i = hi0; }
       }
+      if (lo1 <= hi1) {
+        const unsigned long long a = u1[lo1] & kMag, c = u1[hi1] & kMag;
+        if (!any || a > best) { best = a; best_b = 1; best_i = lo1; any = true; }
+        if (c > best) { best = c; best_b = 1; best_i = hi1; }
+      }
+      if (s == keep) {
+        out->lam_next = any ? __longlong_as_double((long long)best) : 0.0;
+        break;
+      }
+      if (s == 0) fb = best;
+      lb = best;
+      if (best_b == 0) {
+        idx[cnt0++] = best_i;
+        pv[s] = w0[best_i];
+        if (best_i == lo0) ++lo0; else --hi0;
+      } else {
+        idx[chi + cnt1++] = best_i;
+        pv[s] = w1[best_i];
+        if (best_i == lo1) ++lo1; else --hi1;
+      }
+      pb[s] = (unsigned char)best_b;
     }
-    if (s == keep) {
-      out->lam_next = best_b < 0 ? 0.0 : best;
-      break;
-    }
-    if (s == 0) first = best;
-    last = best;
-    kept += best;
-    idx[best_b * chi + cnt[best_b]] = best_i;
-    pv[s] = w[best_b][best_i];
-    pb[s] = (unsigned char)best_b;
-    ++cnt[best_b];
-    if (best_i == lo[best_b])
-      ++lo[best_b];
-    else
-      --hi[best_b];
+    // new diagonal in FSO order: block 0's picks, then block 1's, each in pick order
+    int j0 = 0, j1 = cnt0;
+    for (int s = 0; s < keep; ++s) lam[pb[s] ? j1++ : j0++] = pv[s];
+    out->chi_new[0] = cnt0;
+    out->chi_new[1] = cnt1;
+    first_bits = fb;
+    last_bits = lb;
   }
-  // new diagonal in FSO order: block 0's picks, then block 1's, each in pick order
-  int j0 = 0, j1 = cnt[0];
-  for (int s = 0; s < keep; ++s) lam[pb[s] ? j1++ : j0++] = pv[s];
-  out->discarded = all - kept;
-  out->chi_new[0] = cnt[0];
-  out->chi_new[1] = cnt[1];
-  out->lam_max = first;
-  out->lam_cut = last;
+  __syncthreads();
+  // discarded weight: sum |w| minus the kept magnitudes (parallel)
+  double k = 0.0;
+  for (int s = threadIdx.x; s < keep; s += blockDim.x) k += fabs(pv[s]);
+  __syncthreads();
+  part[threadIdx.x] -= k;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double disc = 0.0;
+    for (int t = 0; t < (int)blockDim.x; ++t) disc += part[t];
+    out->discarded = disc;
+    out->lam_max = __longlong_as_double((long long)first_bits);
+    out->lam_cut = __longlong_as_double((long long)last_bits);
+  }
 }
 
 __global__ void gather_pt_kernel(const double* __restrict__ V0, int n0, const double* __restrict__ V1,

@@ -197,6 +197,27 @@ __global__ void row_normalize_kernel(double* __restrict__ X, int m, int n) {
     for (int j = threadIdx.x; j < n; j += blockDim.x) X[(long long)i * n + j] /= nrm;
 }
 
+// out row i = X row idx[i], i < m (rows of n doubles).
+__global__ void gather_rows_idx_kernel(const double* __restrict__ X, const int* __restrict__ idx, int n,
+                                       double* __restrict__ out) {
+  const long long src = (long long)idx[blockIdx.x] * n, dst = (long long)blockIdx.x * n;
+  for (int j = threadIdx.x; j < n; j += blockDim.x) out[dst + j] = X[src + j];
+}
+
+// One term of the Chebyshev three-term recurrence on rows:
+// Y = alpha (Z - T) + beta Yold, T and Yold optional (null: zero).
+__global__ void cheb_step_kernel(double* __restrict__ Y, const double* __restrict__ Z, const double* __restrict__ T,
+                                 const double* __restrict__ Yold, long long count, double alpha, double beta) {
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < count;
+       e += (long long)gridDim.x * blockDim.x) {
+    double v = Z[e];
+    if (T) v -= T[e];
+    v *= alpha;
+    if (Yold) v += beta * Yold[e];
+    Y[e] = v;
+  }
+}
+
 // Symmetric eigen-decomposition of one small FP32 matrix per CTA by the
 // cyclic Jacobi method (Golub and Van Loan, Sec. 8.5) with the round-robin
 // ordering, so that the m/2 rotations of a round touch disjoint rows and
@@ -357,6 +378,19 @@ cudaError_t launch_jacobi_eig_pair(float* A0, int m0, float* w0, float* A1, int 
 cudaError_t launch_row_normalize(double* X, int m, int n, cudaStream_t s) {
   if (m <= 0) return cudaSuccess;
   row_normalize_kernel<<<m, 256, 0, s>>>(X, m, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather_rows_idx(const double* X, const int* idx, int m, int n, double* out, cudaStream_t s) {
+  if (m <= 0) return cudaSuccess;
+  gather_rows_idx_kernel<<<m, 256, 0, s>>>(X, idx, n, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cheb_step(double* Y, const double* Z, const double* T, const double* Yold, long long count,
+                             double alpha, double beta, cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  cheb_step_kernel<<<grid_for(count), 256, 0, s>>>(Y, Z, T, Yold, count, alpha, beta);
   return cudaGetLastError();
 }
 
