@@ -168,8 +168,9 @@ typedef struct {
                             eigensolver converged (no fallback); bit 2: it fell back */
   int subspace_iters;    /* Rayleigh-Ritz rounds of the subspace eigensolver (0 if unused) */
   int subspace_reason;   /* 0 converged, 1 no warm start, 2 sector sizes changed, 3 subspace too
-                            large, 4 Cholesky or eigensolver failure, 5 not converged, 6 selection at
-                            the edge of the subspace; -1 not used */
+                            large, 4 Cholesky failure (non-positive pivot), 5 not converged, 6 selection
+                            at the edge of the subspace, 7 Rayleigh-Ritz eigensolver failure; -1 not
+                            used */
   double subspace_resid; /* largest residual / max|theta| over the candidates in the last round */
 } hs_move_info;
 

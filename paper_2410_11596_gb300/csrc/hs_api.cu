@@ -411,19 +411,32 @@ hs_status project_f32(hs_ctx ctx, const float* V0f, int n0, const float* V1f, in
 // ---- warm-started subspace eigensolver (HS_EIG_SUBSPACE) ----
 
 
-// Orthonormalise the m rows of X (m x n) in FP64: two passes of Cholesky-QR,
-// X <- L^{-1} X with X X^T = L L^T. Non-positive pivots raise *bad (device).
-hs_status cholqr2(hs_ctx ctx, double* X, int m, int n, double* Xc, int* bad) {
-  HS_TRY(ctx->schol.ensure(2 * (size_t)m * m * sizeof(double)));
-  double* G = ctx->schol.d();
-  double* Li = G + (long long)m * m;
-  for (int pass = 0; pass < 2; ++pass) {
-    HS_TRY(gemm(ctx, HS_GEMM_OWN, GemmGroup{1, {GemmProblem{m, m, n, n, n, m, 0, 0, 0}}}, X, X, G));
-    HS_CUDA(launch_chol_inv(G, m, Li, bad, ctx->stream));
-    HS_TRY(permute(ctx, dense2(m, n), dense2(n, m), {1, 0}, X, Xc));
-    HS_TRY(gemm(ctx, HS_GEMM_OWN, GemmGroup{1, {GemmProblem{m, n, m, m, m, n, 0, 0, 0}}}, Li, Xc, X));
-    ctx->launches += 1;
-  }
+// Orthonormalise the rows of X_b (m_b x n_b) of both parity blocks (m_b = 0
+// skips one): one Cholesky-QR pass with FP64 products, X <- L^{-1} X with
+// X X^T = L L^T, leaves an orthogonality error of about eps cond(X)^2
+// (Yamamoto et al., 2015), which one Loewdin step in the move's GEMM
+// precision squares away. The two factorisations share one launch.
+// Non-positive pivots raise *bad (device).
+hs_status orthonormalise_rows(hs_ctx ctx, hs_precision prec, double* const X[2], const int m[2], const int n[2],
+                              double* const Xc[2], int* bad) {
+  const int mm = std::max(m[0], m[1]);
+  if (mm == 0) return HS_OK;
+  HS_TRY(ctx->schol.ensure(4 * (size_t)mm * mm * sizeof(double)));
+  double* G[2] = {ctx->schol.d(), ctx->schol.d() + 2LL * mm * mm};
+  double* Li[2] = {G[0] + (long long)mm * mm, G[1] + (long long)mm * mm};
+  for (int b = 0; b < 2; ++b)
+    if (m[b] > 0)
+      HS_TRY(gemm(ctx, HS_GEMM_OWN, GemmGroup{1, {GemmProblem{m[b], m[b], n[b], n[b], n[b], m[b], 0, 0, 0}}}, X[b],
+                  X[b], G[b]));
+  HS_CUDA(launch_chol_inv(G[0], m[0], Li[0], G[1], m[1], Li[1], bad, ctx->stream));
+  ctx->launches += 1;
+  for (int b = 0; b < 2; ++b)
+    if (m[b] > 0) {
+      HS_TRY(permute(ctx, dense2(m[b], n[b]), dense2(n[b], m[b]), {1, 0}, X[b], Xc[b]));
+      HS_TRY(gemm(ctx, HS_GEMM_OWN, GemmGroup{1, {GemmProblem{m[b], n[b], m[b], m[b], m[b], n[b], 0, 0, 0}}},
+                  Li[b], Xc[b], X[b]));
+      HS_TRY(lowdin_rows(ctx, prec, X[b], m[b], n[b], Xc[b], 1));
+    }
   return HS_OK;
 }
 
@@ -467,14 +480,14 @@ hs_status lowdin_rows(hs_ctx ctx, hs_precision prec, double* X, int m, int n, do
 // |lambda| outside it. The filter also grows the top of the spectrum by
 // orders of magnitude more than the cut, which would swamp the rows in
 // rounding; so the Ritz pairs with |theta| >= kLock a are locked: they take
-// one plain power step (their rows of Zr) and their span is projected out
-// after every product of the filtered rows. X receives the locked rows, then
+// two plain power steps and their span is projected out after every product
+// of the filtered rows. X receives the locked rows, then
 // the filtered ones (not normalised). Returns false in *used when no interior
 // magnitude exists (the caller then takes a plain step).
 hs_status cheb_filter_block(hs_ctx ctx, hs_precision prec, int b, int m, int n, const double* H,
                             const float* theta, int kept_b, double* X, bool* used) {
-  constexpr int kDeg = 6;
-  constexpr double kLock = 16.0, kEdge = 0.3;
+  constexpr int kDeg = 8;
+  constexpr double kLock = 8.0, kEdge = 0.3;
   *used = false;
   cudaStream_t s = ctx->stream;
   const bool tc = prec != HS_PREC_F64;
@@ -502,9 +515,27 @@ hs_status cheb_filter_block(hs_ctx ctx, hs_precision prec, int b, int m, int n, 
   HS_TRY(ctx->sf_s.ensure((size_t)m * m * sizeof(double)));
   const double* Xr = ctx->sxr[b].d();
   const double* Zr = ctx->szr[b].d();
-  // locked rows: one power step
-  HS_CUDA(launch_gather_rows_idx(Zr, didx, mL, n, X, s));
-  ctx->launches += 1;
+  // product of mr rows of Y (m x n) with H into Z
+  auto hprod = [&](const double* Y, int mr, double* Z) -> hs_status {
+    if (tc) {
+      HS_TRY(tc_split(ctx, prec, dense2(mr, n), dense2(mr, n), {0, 1}, Y, ctx->sx_hi, ctx->sx_lo));
+      HS_TRY(tc_run(ctx, prec, dense2(mr, n), ctx->sx_hi, ctx->sx_lo, dense2(n, n), ctx->sH_hi[b], ctx->sH_lo[b],
+                    dense2(mr, n), Z));
+      ctx->phase_flops[HS_PHASE_GEMM_TC] += 2.0 * mr * (double)n * n;
+    } else {
+      HS_TRY(gemm(ctx, HS_GEMM_OWN, GemmGroup{1, {GemmProblem{mr, n, n, n, n, n, 0, 0, 0}}}, Y, H, Z));
+      ctx->phase_flops[HS_PHASE_GEMM] += 2.0 * mr * (double)n * n;
+    }
+    return HS_OK;
+  };
+  // locked rows: two power steps (the first is their rows of Zr); the ratio
+  // to the largest |lambda| outside the window is at most 1 / kLock per step
+  if (mL > 0) {
+    HS_CUDA(launch_gather_rows_idx(Zr, didx, mL, n, ctx->sf_z.d(), s));
+    HS_CUDA(launch_row_normalize(ctx->sf_z.d(), mL, n, s));
+    HS_TRY(hprod(ctx->sf_z.d(), mL, X));
+    ctx->launches += 2;
+  }
   if (mU > 0) {
     double* Q = ctx->sf_q.d();
     double* Qt = ctx->sf_qt.d();
@@ -534,15 +565,7 @@ hs_status cheb_filter_block(hs_ctx ctx, hs_precision prec, int b, int m, int n, 
     int prev = 0, cur = 1;
     for (int j = 2; j <= kDeg; ++j) {
       const int next = 3 - prev - cur;
-      if (tc) {
-        HS_TRY(tc_split(ctx, prec, dense2(mU, n), dense2(mU, n), {0, 1}, Y[cur], ctx->sx_hi, ctx->sx_lo));
-        HS_TRY(tc_run(ctx, prec, dense2(mU, n), ctx->sx_hi, ctx->sx_lo, dense2(n, n), ctx->sH_hi[b], ctx->sH_lo[b],
-                      dense2(mU, n), Z));
-        ctx->phase_flops[HS_PHASE_GEMM_TC] += 2.0 * mU * (double)n * n;
-      } else {
-        HS_TRY(gemm(ctx, HS_GEMM_OWN, GemmGroup{1, {GemmProblem{mU, n, n, n, n, n, 0, 0, 0}}}, Y[cur], H, Z));
-        ctx->phase_flops[HS_PHASE_GEMM] += 2.0 * mU * (double)n * n;
-      }
+      HS_TRY(hprod(Y[cur], mU, Z));
       HS_TRY(project());
       HS_CUDA(launch_cheb_step(Y[next], Z, mL > 0 ? T : nullptr, Y[prev], cnt, 2.0 / a, -1.0, s));
       ctx->launches += 1;
@@ -610,7 +633,10 @@ hs_status subspace_projector(hs_ctx ctx, hs_env* env, int chi, int n0, int n1, d
       // the previous move's Ritz / eigen-vectors: orthonormal up to FP32 rounding
       HS_TRY(lowdin_rows(ctx, prec, ctx->sx[b].d(), m[b], n[b], ctx->sxc[b].d(), tc ? 1 : 2));
     } else {
-      HS_TRY(cholqr2(ctx, ctx->sx[b].d(), m[b], n[b], ctx->sxc[b].d(), bad));
+      double* const Xo[2] = {ctx->sx[b].d(), nullptr};
+      double* const Xco[2] = {ctx->sxc[b].d(), nullptr};
+      const int mo[2] = {m[b], 0}, no[2] = {n[b], 0};
+      HS_TRY(orthonormalise_rows(ctx, prec, Xo, mo, no, Xco, bad));
     }
     if (tc) {
       HS_TRY(tc_split(ctx, prec, dense2(n[b], n[b]), dense2(n[b], n[b]), {0, 1}, H[b], ctx->sH_hi[b], ctx->sH_lo[b]));
@@ -672,7 +698,7 @@ hs_status subspace_projector(hs_ctx ctx, hs_env* env, int chi, int n0, int n1, d
     HS_CUDA(cudaMemcpyAsync(hinfo, ctx->info.p, sizeof hinfo, cudaMemcpyDeviceToHost, s));
     HS_CUDA(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
     HS_CUDA(cudaStreamSynchronize(s));
-    *reason = 4;
+    *reason = hbad ? 4 : 7;
     if (hbad || hinfo[0] || hinfo[1]) return HS_OK;  // fall back
     // the states the selection can keep: the chi largest |theta| across both
     // blocks, plus two more per block; all of them must have converged, and no
@@ -715,9 +741,7 @@ hs_status subspace_projector(hs_ctx ctx, hs_env* env, int chi, int n0, int n1, d
     for (int b = 0; b < 2; ++b)
       if (m[b] > 0) {
         // next basis: a Chebyshev-filtered step where possible, else a plain
-        // power step (rows of Zr = theta_i x_i + residual). Far from
-        // convergence the rows can be far from orthogonal, where the Loewdin
-        // iteration diverges: orthonormalise by Cholesky-QR twice (FP64)
+        // power step (rows of Zr = theta_i x_i + residual)
         bool filtered = false;
         HS_TRY(cheb_filter_block(ctx, prec, b, m[b], n[b], H[b], hth.data() + (b ? m[0] : 0), kept[b],
                                  ctx->sx[b].d(), &filtered));
@@ -725,8 +749,14 @@ hs_status subspace_projector(hs_ctx ctx, hs_env* env, int chi, int n0, int n1, d
           HS_CUDA(cudaMemcpyAsync(ctx->sx[b].p, ctx->szr[b].p, (size_t)m[b] * n[b] * sizeof(double),
                                   cudaMemcpyDeviceToDevice, s));
         HS_CUDA(launch_row_normalize(ctx->sx[b].d(), m[b], n[b], s));
-        HS_TRY(cholqr2(ctx, ctx->sx[b].d(), m[b], n[b], ctx->sxc[b].d(), bad));
       }
+    {
+      // far from convergence the rows can be far from orthogonal (the Loewdin
+      // iteration alone diverges there): Cholesky-QR first
+      double* const Xo[2] = {ctx->sx[0].d(), ctx->sx[1].d()};
+      double* const Xco[2] = {ctx->sxc[0].d(), ctx->sxc[1].d()};
+      HS_TRY(orthonormalise_rows(ctx, prec, Xo, m, n, Xco, bad));
+    }
   }
   return HS_OK;
 }

@@ -304,7 +304,10 @@ cudaError_t launch_block_trace(const double* x, int n0, int n1, double* out, cud
 
 // Warm-started subspace eigensolver kernels (k_subspace.cu).
 cudaError_t launch_fill_random_rows(double* X, int r0, int m, int n, unsigned long long seed, cudaStream_t s);
-cudaError_t launch_chol_inv(const double* G, int m, double* Linv, int* status, cudaStream_t s);
+// Cholesky factor inverses L_b^{-1} of two SPD matrices G_b (m_b <= max_subspace(),
+// m_b = 0 skips one), one CTA each; *status = 1 on a non-positive pivot.
+cudaError_t launch_chol_inv(const double* G0, int m0, double* Linv0, const double* G1, int m1, double* Linv1,
+                            int* status, cudaStream_t s);
 cudaError_t launch_residual(const double* Zr, const double* Xr, const float* theta, int m, int n, double* res,
                             cudaStream_t s);
 cudaError_t launch_row_sign(double* X, int m, int n, cudaStream_t s);

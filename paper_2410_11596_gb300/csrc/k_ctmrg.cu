@@ -200,7 +200,11 @@ __global__ void diag_corner_kernel(const double* __restrict__ lam, SelectOut* se
                                    int chi) {
   const int c0 = sel->chi_new[0], c1 = sel->chi_new[1];
   const long long total = (long long)c0 * c0 + (long long)c1 * c1;
-  const double inv = 1.0 / sel->lam_max;
+  // one FP64 division per block (it is a long sequence on the FP64 pipe)
+  __shared__ double s_inv;
+  if (threadIdx.x == 0) s_inv = 1.0 / sel->lam_max;
+  __syncthreads();
+  const double inv = s_inv;
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
        e += (long long)gridDim.x * blockDim.x) {
     long long r, c, base;
@@ -231,7 +235,11 @@ __global__ void absmax_kernel(const double* __restrict__ x, long long n, unsigne
 __global__ void scale_kernel(double* __restrict__ x, long long n, const unsigned long long* m,
                              SelectOut* sel) {
   const double mx = __longlong_as_double((long long)*m);
-  const double inv = 1.0 / mx;
+  // one FP64 division per block (it is a long sequence on the FP64 pipe)
+  __shared__ double s_inv;
+  if (threadIdx.x == 0) s_inv = 1.0 / mx;
+  __syncthreads();
+  const double inv = s_inv;
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n;
        e += (long long)gridDim.x * blockDim.x)
     x[e] *= inv;
@@ -286,7 +294,10 @@ __global__ void lowdin_kernel(double* __restrict__ G, int k0, int k1) {
 
 __global__ void scale_to_kernel(double* __restrict__ x, long long n, const unsigned long long* m, double* log_out) {
   const double mx = __longlong_as_double((long long)*m);
-  const double inv = 1.0 / mx;
+  __shared__ double s_inv;
+  if (threadIdx.x == 0) s_inv = 1.0 / mx;
+  __syncthreads();
+  const double inv = s_inv;
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n;
        e += (long long)gridDim.x * blockDim.x)
     x[e] *= inv;

@@ -449,6 +449,37 @@ bool make_map(CUtensorMap* m, const void* base, int rows, int Kp, int eb) {
   return r == CUDA_SUCCESS;
 }
 
+// make_map through a small per-thread cache: encoding a map is a driver call
+// of a few microseconds, and the same operands recur every move. A map
+// depends only on (base, rows, Kp, eb), the key, so an entry never goes stale.
+bool make_map_cached(CUtensorMap* m, const void* base, int rows, int Kp, int eb) {
+  struct Entry {
+    const void* base;
+    int rows, Kp, eb;
+    CUtensorMap map;
+  };
+  constexpr int kEntries = 128;
+  thread_local Entry cache[kEntries] = {};
+  unsigned long long h = reinterpret_cast<unsigned long long>(base) >> 7;
+  h = (h ^ (unsigned long long)rows * 0x9E3779B97F4A7C15ull ^ (unsigned long long)Kp * 0xC2B2AE3D27D4EB4Full ^
+       (unsigned long long)eb) * 0x100000001B3ull;
+  Entry& e = cache[(h >> 32) % kEntries];
+  if (e.base == base && e.rows == rows && e.Kp == Kp && e.eb == eb && base != nullptr) {
+    *m = e.map;
+    return true;
+  }
+  if (!make_map(&e.map, base, rows, Kp, eb)) {
+    e.base = nullptr;
+    return false;
+  }
+  e.base = base;
+  e.rows = rows;
+  e.Kp = Kp;
+  e.eb = eb;
+  *m = e.map;
+  return true;
+}
+
 __global__ void tc_splitk_reduce_kernel(const double* __restrict__ part, int nsplit, int M, int N,
                                         double* __restrict__ C, int ldc) {
   const long long mn = (long long)M * N;
@@ -483,10 +514,11 @@ cudaError_t run(const TcProblem* probs, int nprob, int* err, cudaStream_t s, dou
     if (p.M <= 0 || p.N <= 0) continue;
     if (p.Kp <= 0 || p.Kp % K::K_PER_TILE != 0) return cudaErrorInvalidValue;
     const int j = nmap++;
-    if (!make_map(&maps.a[j][0], p.a_hi, p.M, p.Kp, EB) || !make_map(&maps.b[j][0], p.b_hi, p.N, p.Kp, EB))
+    if (!make_map_cached(&maps.a[j][0], p.a_hi, p.M, p.Kp, EB) ||
+        !make_map_cached(&maps.b[j][0], p.b_hi, p.N, p.Kp, EB))
       return cudaErrorInvalidValue;
-    if (NPASS == 3 &&
-        (!make_map(&maps.a[j][1], p.a_lo, p.M, p.Kp, EB) || !make_map(&maps.b[j][1], p.b_lo, p.N, p.Kp, EB)))
+    if (NPASS == 3 && (!make_map_cached(&maps.a[j][1], p.a_lo, p.M, p.Kp, EB) ||
+                       !make_map_cached(&maps.b[j][1], p.b_lo, p.N, p.Kp, EB)))
       return cudaErrorInvalidValue;
     const int tiles_n = (p.N + BN - 1) / BN;
     const int ptiles = ((p.M + BM - 1) / BM) * tiles_n;

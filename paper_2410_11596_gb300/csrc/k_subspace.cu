@@ -33,49 +33,61 @@ __global__ void fill_random_rows_kernel(double* __restrict__ X, int r0, int m, i
     X[(long long)r0 * n + e] = hash_uniform(seed * 0x100000001B3ull + (unsigned long long)e);
 }
 
-// In-place Cholesky G = L L^T (lower) of an m x m SPD matrix and L^{-1}, in
-// FP64, by one CTA in shared memory (m <= kMaxSub). On a non-positive pivot
-// the status word is set and Linv is left unspecified.
+// Cholesky G = L L^T (lower) of an m x m SPD matrix and L^{-1}, in FP64, by
+// one CTA in shared memory (m <= kMaxSub). Right-looking: step j takes the
+// pivot, scales column j of L and row j of L^{-1}, then applies the rank-1
+// updates of both (forward substitution of L X = I carried along the
+// factorisation). One m x (m+1) array holds both triangles: L[i][c] at
+// (i, c) and L^{-1}[i][c] at (c, i + 1), c <= i. On a non-positive pivot the
+// status word is set and Linv is left unspecified.
 constexpr int kMaxSub = 160;
 
-__global__ void __launch_bounds__(256) chol_inv_kernel(const double* __restrict__ G, int m,
-                                                       double* __restrict__ Linv, int* __restrict__ status) {
+__global__ void __launch_bounds__(1024) chol_inv_kernel(const double* __restrict__ G0, int m0,
+                                                        double* __restrict__ Linv0, const double* __restrict__ G1,
+                                                        int m1, double* __restrict__ Linv1, int* __restrict__ status) {
+  // one CTA per matrix (blockIdx.x)
+  const double* G = blockIdx.x ? G1 : G0;
+  double* Linv = blockIdx.x ? Linv1 : Linv0;
+  const int m = blockIdx.x ? m1 : m0;
+  if (m <= 0) return;
   extern __shared__ double sh[];
-  double* L = sh;  // m x m, lower triangle used
-  for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
-    const int r = e / m, c = e % m;
-    L[e] = r >= c ? 0.5 * (G[r * m + c] + G[c * m + r]) : 0.0;
+  const int ld = m + 1;
+  double* A = sh;
+  for (int e = threadIdx.x; e < m * ld; e += blockDim.x) {
+    const int i = e / ld, c = e - (e / ld) * ld;
+    A[e] = c <= i ? 0.5 * (G[i * m + c] + G[c * m + i]) : (c == i + 1 ? 1.0 : 0.0);
   }
-  __syncthreads();
   __shared__ int bad;
+  __shared__ double s_rp;
   if (threadIdx.x == 0) bad = 0;
   __syncthreads();
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5, ny = blockDim.x >> 5;
   for (int j = 0; j < m; ++j) {
+    // the pivot's square root and reciprocal once (FP64 square roots and
+    // divisions are long sequences on the FP64 pipe)
     if (threadIdx.x == 0) {
-      const double d = L[j * m + j];
-      if (!(d > 0.0)) bad = 1;
-      L[j * m + j] = d > 0.0 ? sqrt(d) : 1.0;
+      const double d = A[j * ld + j];
+      const bool ok = d > 0.0;
+      const double piv = ok ? sqrt(d) : 1.0;
+      A[j * ld + j] = piv;
+      s_rp = 1.0 / piv;
+      if (!ok) bad = 1;
     }
     __syncthreads();
-    const double piv = L[j * m + j];
-    for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x) L[i * m + j] /= piv;
+    const double rp = s_rp;
+    for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x) A[i * ld + j] *= rp;
+    for (int c = threadIdx.x; c <= j; c += blockDim.x) A[c * ld + j + 1] *= rp;
     __syncthreads();
-    // trailing update of the lower triangle
-    const int rem = m - j - 1;
-    for (int e = threadIdx.x; e < rem * rem; e += blockDim.x) {
-      const int r = j + 1 + e / rem, c = j + 1 + e % rem;
-      if (c <= r) L[r * m + c] -= L[r * m + j] * L[c * m + j];
+    for (int r = j + 1 + ty; r < m; r += ny) {
+      const double lrj = A[r * ld + j];
+      for (int c = j + 1 + tx; c <= r; c += 32) A[r * ld + c] -= lrj * A[c * ld + j];
+      for (int c = tx; c <= j; c += 32) A[c * ld + r + 1] -= lrj * A[c * ld + j + 1];
     }
     __syncthreads();
   }
-  // L^{-1} by forward substitution, one column of the identity per thread,
-  // built directly in Linv (each thread reads and writes only its column)
-  for (int c = threadIdx.x; c < m; c += blockDim.x) {
-    for (int r = 0; r < m; ++r) {
-      double v = r == c ? 1.0 : 0.0;
-      for (int k = c; k < r; ++k) v -= L[r * m + k] * Linv[k * m + c];
-      Linv[r * m + c] = r < c ? 0.0 : v / L[r * m + r];
-    }
+  for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+    const int i = e / m, c = e - (e / m) * m;
+    Linv[e] = c <= i ? A[c * ld + i + 1] : 0.0;
   }
   if (threadIdx.x == 0 && bad) *status = 1;
 }
@@ -193,8 +205,10 @@ __global__ void row_normalize_kernel(double* __restrict__ X, int m, int n) {
     __syncthreads();
   }
   const double nrm = sqrt(red[0]);
-  if (nrm > 0.0)
-    for (int j = threadIdx.x; j < n; j += blockDim.x) X[(long long)i * n + j] /= nrm;
+  if (nrm > 0.0) {
+    const double inv = 1.0 / nrm;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) X[(long long)i * n + j] *= inv;
+  }
 }
 
 // out row i = X row idx[i], i < m (rows of n doubles).
@@ -233,6 +247,10 @@ __global__ void cheb_step_kernel(double* __restrict__ Y, const double* __restric
 // After kMaxSweeps without that, *status = 1.
 constexpr int kMaxSweeps = 40;
 
+// Blocks (a, b), a <= b, of the 2 x 2 block grid that thread `t` updates in
+// every round, packed a << 16 | b (at most kBlkPerThread per thread).
+constexpr int kBlkPerThread = 4;
+
 __global__ void __launch_bounds__(1024) jacobi_eig_kernel(float* __restrict__ A0, int m0, float* __restrict__ w0,
                                                          float* __restrict__ A1, int m1, float* __restrict__ w1,
                                                          int* __restrict__ status) {
@@ -243,10 +261,9 @@ __global__ void __launch_bounds__(1024) jacobi_eig_kernel(float* __restrict__ A0
   extern __shared__ float shj[];
   const int ld = m + 1;
   float* A = shj;                 // m x ld
-  float* V = A + m * ld;          // m x ld, V[i * ld + j] = component i of vector j
-  float* cs = V + m * ld;         // cos, sin per pair
-  int* pq = reinterpret_cast<int*>(cs + 2 * ((m + 1) / 2 + 1));
-  __shared__ int nrot, rrot;
+  float* Vt = A + m * ld;         // m x ld, Vt[j * ld + i] = component i of vector j
+  float2* cs = reinterpret_cast<float2*>(Vt + m * ld);  // (cos, sin) per pair
+  int2* pq = reinterpret_cast<int2*>(cs + ((m + 1) / 2 + 1));
   const int M = (m + 1) & ~1;     // even player count (index m is a dummy when m is odd)
   const int npair = M / 2;
   const float kRelTol = fmaxf(4e-7f, sqrtf((float)m) * 6e-8f);
@@ -256,23 +273,41 @@ __global__ void __launch_bounds__(1024) jacobi_eig_kernel(float* __restrict__ A0
     const int i = e / m, j = e % m;
     const float v = 0.5f * (Ag[i * m + j] + Ag[j * m + i]);
     A[i * ld + j] = v;
-    V[i * ld + j] = i == j ? 1.f : 0.f;
+    Vt[i * ld + j] = i == j ? 1.f : 0.f;
     if (i == j) dm = fmaxf(dm, fabsf(v));
   }
   for (int o = 16; o > 0; o >>= 1) dm = fmaxf(dm, __shfl_xor_sync(0xffffffffu, dm, o));
   if ((threadIdx.x & 31) == 0) dmax_part[threadIdx.x >> 5] = dm;
+  // this thread's blocks of the upper block triangle, in row-major order
+  int blk[kBlkPerThread];
+  int nblk = 0;
+  {
+    int a = 0, off = 0;  // off: flat index of block (a, a); row a holds blocks b = a .. npair-1
+#pragma unroll
+    for (int t = 0; t < kBlkPerThread; ++t) {
+      const int f = threadIdx.x + t * blockDim.x;
+      blk[t] = -1;
+      if (f < npair * (npair + 1) / 2) {
+        while (f >= off + (npair - a)) {
+          off += npair - a;
+          ++a;
+        }
+        blk[t] = (a << 16) | (a + f - off);
+        nblk = t + 1;
+      }
+    }
+  }
   __syncthreads();
   float dmax = 0.f;
   for (int w = 0; w < (int)(blockDim.x >> 5); ++w) dmax = fmaxf(dmax, dmax_part[w]);
   // off-diagonal entries below this are rounding noise of the FP32 matrix
   const float abs_floor = 1e-7f * dmax;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   bool converged = false;
   for (int sweep = 0; sweep < kMaxSweeps && !converged; ++sweep) {
-    if (threadIdx.x == 0) nrot = 0;
-    __syncthreads();
+    int nrot = 0;  // rotations in this sweep (the same in every thread)
     for (int r = 0; r < M - 1; ++r) {
-      if (threadIdx.x == 0) rrot = 0;
-      __syncthreads();
+      int rotates = 0;
       // round-robin pairing: player M-1 fixed, the others rotate
       for (int k = threadIdx.x; k < npair; k += blockDim.x) {
         int p = k == 0 ? M - 1 : (r + k) % (M - 1);
@@ -293,54 +328,58 @@ __global__ void __launch_bounds__(1024) jacobi_eig_kernel(float* __restrict__ A0
             const float t = (th >= 0.f ? 1.f : -1.f) / (fabsf(th) + sqrtf(th * th + 1.f));
             c = rsqrtf(t * t + 1.f);
             sn = t * c;
-            atomicAdd(&rrot, 1);
+            rotates = 1;
           }
         }
-        pq[2 * k] = p;
-        pq[2 * k + 1] = q;
-        cs[2 * k] = c;
-        cs[2 * k + 1] = sn;
+        pq[k] = make_int2(p, q);
+        cs[k] = make_float2(c, sn);
       }
-      __syncthreads();
+      const int rrot = __syncthreads_count(rotates);
       if (rrot == 0) continue;  // nothing rotates in this round (block-uniform)
-      if (threadIdx.x == 0) nrot += rrot;
+      nrot += rrot;
       // A <- J^T A J: the rotations act on disjoint pairs, so every 2 x 2 block
-      // (rows of pair a, columns of pair b) transforms on its own; V <- V J
-      const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-      for (int a = threadIdx.x >> 5; a < npair; a += nw) {
-        const int pa = pq[2 * a], qa = pq[2 * a + 1];
-        const float ca = cs[2 * a], sa = cs[2 * a + 1];
-        const bool ra = qa < m;
-        for (int b = lane; b < npair; b += 32) {
-          const int pb = pq[2 * b], qb = pq[2 * b + 1];
-          const float cb = cs[2 * b], sb = cs[2 * b + 1];
-          const bool rb = qb < m;
-          const float a00 = A[pa * ld + pb];
-          const float a01 = rb ? A[pa * ld + qb] : 0.f;
-          const float a10 = ra ? A[qa * ld + pb] : 0.f;
-          const float a11 = (ra && rb) ? A[qa * ld + qb] : 0.f;
-          const float t00 = ca * a00 - sa * a10, t01 = ca * a01 - sa * a11;
-          const float t10 = sa * a00 + ca * a10, t11 = sa * a01 + ca * a11;
-          A[pa * ld + pb] = cb * t00 - sb * t01;
-          if (rb) A[pa * ld + qb] = sb * t00 + cb * t01;
-          if (ra) A[qa * ld + pb] = cb * t10 - sb * t11;
-          if (ra && rb) A[qa * ld + qb] = sb * t10 + cb * t11;
+      // (rows of pair a, columns of pair b) transforms on its own; A stays
+      // symmetric, so only blocks a <= b are computed and mirrored
+#pragma unroll
+      for (int t = 0; t < kBlkPerThread; ++t) {
+        if (t >= nblk) break;
+        const int a = blk[t] >> 16, b = blk[t] & 0xffff;
+        const int2 ia = pq[a], ib = pq[b];
+        const float2 ra_ = cs[a], rb_ = cs[b];
+        const bool ra = ia.y < m, rb = ib.y < m;
+        const float a00 = A[ia.x * ld + ib.x];
+        const float a01 = rb ? A[ia.x * ld + ib.y] : 0.f;
+        const float a10 = ra ? A[ia.y * ld + ib.x] : 0.f;
+        const float a11 = (ra && rb) ? A[ia.y * ld + ib.y] : 0.f;
+        const float t00 = ra_.x * a00 - ra_.y * a10, t01 = ra_.x * a01 - ra_.y * a11;
+        const float t10 = ra_.y * a00 + ra_.x * a10, t11 = ra_.y * a01 + ra_.x * a11;
+        const float n00 = rb_.x * t00 - rb_.y * t01, n01 = rb_.y * t00 + rb_.x * t01;
+        const float n10 = rb_.x * t10 - rb_.y * t11, n11 = rb_.y * t10 + rb_.x * t11;
+        A[ia.x * ld + ib.x] = n00;
+        if (rb) A[ia.x * ld + ib.y] = n01;
+        if (ra) A[ia.y * ld + ib.x] = n10;
+        if (ra && rb) A[ia.y * ld + ib.y] = n11;
+        if (a != b) {
+          A[ib.x * ld + ia.x] = n00;
+          if (rb) A[ib.y * ld + ia.x] = n01;
+          if (ra) A[ib.x * ld + ia.y] = n10;
+          if (ra && rb) A[ib.y * ld + ia.y] = n11;
         }
       }
-      for (int i = threadIdx.x >> 5; i < m; i += nw) {
-        for (int b = lane; b < npair; b += 32) {
-          const int pb = pq[2 * b], qb = pq[2 * b + 1];
-          if (qb >= m) continue;
-          const float cb = cs[2 * b], sb = cs[2 * b + 1];
-          const float vp = V[i * ld + pb], vq = V[i * ld + qb];
-          V[i * ld + pb] = cb * vp - sb * vq;
-          V[i * ld + qb] = sb * vp + cb * vq;
+      // V <- V J on the rows of Vt: one pair per warp, lanes along the vector
+      for (int b = warp; b < npair; b += nw) {
+        const int2 ib = pq[b];
+        const float2 rb_ = cs[b];
+        if (ib.y >= m || (rb_.x == 1.f && rb_.y == 0.f)) continue;  // warp-uniform
+        for (int i = lane; i < m; i += 32) {
+          const float vp = Vt[ib.x * ld + i], vq = Vt[ib.y * ld + i];
+          Vt[ib.x * ld + i] = rb_.x * vp - rb_.y * vq;
+          Vt[ib.y * ld + i] = rb_.y * vp + rb_.x * vq;
         }
       }
       __syncthreads();
     }
     converged = nrot == 0;  // a sweep without a rotation: every A_pq is negligible
-    __syncthreads();
   }
   if (!converged && threadIdx.x == 0) atomicExch(status, 1);
   // ascending order by rank (ties by index); vectors as columns, column-major
@@ -352,7 +391,7 @@ __global__ void __launch_bounds__(1024) jacobi_eig_kernel(float* __restrict__ A0
       rank += (li < lj) || (li == lj && i < j);
     }
     wg[rank] = lj;
-    for (int i = 0; i < m; ++i) Ag[(long long)rank * m + i] = V[i * ld + j];
+    for (int i = 0; i < m; ++i) Ag[(long long)rank * m + i] = Vt[j * ld + i];
   }
 }
 
@@ -366,6 +405,8 @@ cudaError_t launch_jacobi_eig_pair(float* A0, int m0, float* w0, float* A1, int 
                                    cudaStream_t s) {
   const int m = m0 > m1 ? m0 : m1;
   if (m <= 0) return cudaSuccess;
+  // m <= kMaxSub keeps the (m/2)(m/2 + 1)/2 blocks of a round within kBlkPerThread per thread
+  static_assert((kMaxSub / 2 + 1) * (kMaxSub / 2 + 2) / 2 <= kBlkPerThread * 1024, "block grid too large");
   if (m > kMaxSub) return cudaErrorInvalidValue;
   // set once per process (thread-safe static initialisation)
   static const cudaError_t attr_err = cudaFuncSetAttribute(jacobi_eig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -407,14 +448,17 @@ cudaError_t launch_fill_random_rows(double* X, int r0, int m, int n, unsigned lo
   return cudaGetLastError();
 }
 
-cudaError_t launch_chol_inv(const double* G, int m, double* Linv, int* status, cudaStream_t s) {
-  if (m <= 0 || m > kMaxSub) return cudaErrorInvalidValue;
-  const size_t smem = (size_t)m * m * sizeof(double);
+cudaError_t launch_chol_inv(const double* G0, int m0, double* Linv0, const double* G1, int m1, double* Linv1,
+                            int* status, cudaStream_t s) {
+  if (m0 < 0 || m1 < 0 || m0 > kMaxSub || m1 > kMaxSub) return cudaErrorInvalidValue;
+  if (m0 == 0 && m1 == 0) return cudaSuccess;
+  const int mm = m0 > m1 ? m0 : m1;
+  const size_t smem = (size_t)mm * (mm + 1) * sizeof(double);
   // set once per process (thread-safe static initialisation)
   static const cudaError_t attr_err = cudaFuncSetAttribute(chol_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         kMaxSub * kMaxSub * (int)sizeof(double));
+                                         kMaxSub * (kMaxSub + 1) * (int)sizeof(double));
   if (attr_err != cudaSuccess) return attr_err;
-  chol_inv_kernel<<<1, 256, smem, s>>>(G, m, Linv, status);
+  chol_inv_kernel<<<2, 1024, smem, s>>>(G0, m0, Linv0, G1, m1, Linv1, status);
   return cudaGetLastError();
 }
 
