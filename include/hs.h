@@ -345,6 +345,12 @@ typedef enum {
  * Timing adds events between phases but changes no computation. */
 hs_status hs_profile_enable(hs_ctx ctx, int enable);
 
+/* Restrict the per-phase timing to the phases whose bit is set in mask
+ * (bit i = phase i; all phases by default). Each timed phase adds two events
+ * to the stream, so timing fewer phases perturbs a launch-bound move less.
+ * Errors: HS_ERR_INVALID_ARG for a bad context. */
+hs_status hs_profile_phases(hs_ctx ctx, unsigned mask);
+
 /* Read the counters accumulated since the last reset: phase_ms[i] and
  * phase_flops[i] (host, n_phases entries: milliseconds of device time and
  * algorithmic flops, sum of 2 M N K over the block GEMMs, per phase) and

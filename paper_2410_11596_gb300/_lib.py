@@ -9,7 +9,7 @@ from __future__ import annotations
 import ctypes
 import os
 import re
-from ctypes import POINTER, c_double, c_int, c_size_t, c_void_p
+from ctypes import POINTER, c_double, c_int, c_size_t, c_uint, c_void_p
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libhs.so")
@@ -91,6 +91,7 @@ _PROTOS = {
                        c_void_p]),
     "hs_workspace_query": (c_int, [c_int, c_int, c_int, POINTER(c_size_t)]),
     "hs_profile_enable": (c_int, [c_void_p, c_int]),
+    "hs_profile_phases": (c_int, [c_void_p, c_uint]),
     "hs_profile_read": (c_int, [c_void_p, POINTER(c_double), POINTER(c_double), c_int,
                                 POINTER(ctypes.c_longlong)]),
     "hs_gemm": (c_int, [c_void_p, c_int, c_int, c_int, c_int, c_void_p, c_int, c_void_p, c_int, c_void_p, c_int]),
@@ -236,6 +237,12 @@ def hs_workspace_query(D: int, chi: int, precision: int) -> int:
 
 def hs_profile_enable(ctx: int, enable: bool) -> None:
     check(load().hs_profile_enable(ctx, 1 if enable else 0))
+
+
+def hs_profile_phases(ctx: int, phases=None) -> None:
+    """Time only the named phases (None: all of them)."""
+    mask = 0xFFFFFFFF if phases is None else sum(1 << PHASES.index(p) for p in phases)
+    check(load().hs_profile_phases(ctx, mask))
 
 
 def hs_profile_read(ctx: int) -> dict:

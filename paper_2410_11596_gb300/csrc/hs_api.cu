@@ -90,7 +90,7 @@ int take_event(hs_ctx c) {
 }  // namespace
 
 PhaseScope::PhaseScope(hs_ctx c, int phase) : c_(c), phase_(phase), e0_(-1) {
-  if (!c_->prof) return;
+  if (!c_->prof || !((c_->prof_mask >> phase) & 1u)) return;
   e0_ = take_event(c_);
   if (e0_ >= 0) cudaEventRecord(c_->events[e0_], c_->stream);
 }
@@ -1334,6 +1334,12 @@ hs_status hs_profile_enable(hs_ctx ctx, int enable) {
   for (double& v : ctx->phase_ms) v = 0;
   for (double& v : ctx->phase_flops) v = 0;
   ctx->launches = 0;
+  return HS_OK;
+}
+
+hs_status hs_profile_phases(hs_ctx ctx, unsigned mask) {
+  HS_TRY(check_ctx(ctx));
+  ctx->prof_mask = mask;
   return HS_OK;
 }
 

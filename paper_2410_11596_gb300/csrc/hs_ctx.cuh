@@ -139,6 +139,7 @@ struct hs_ctx_s {
   hs::DBuf sf_y[3], sf_z, sf_t, sf_s, sf_q, sf_qt, sf_idx;
   // profiling: events between phases, harvested after the move's last sync
   bool prof = false;
+  unsigned prof_mask = ~0u;  // phases that record events when prof is on
   std::vector<cudaEvent_t> events;
   int next_event = 0;
   struct Rec {

@@ -53,10 +53,12 @@ constexpr int TILE_BYTES = BM * ROW_BYTES;  // BN == BM
 constexpr long long WAIT_LIMIT = 20000000;  // try_wait rounds before giving up (seconds)
 
 constexpr int kMaxPairs = 4;  // operand pairs of one launch (the four graded sub-products)
-struct Maps {
-  CUtensorMap a[kMaxPairs][2];  // [operand pair][hi, lo]
-  CUtensorMap b[kMaxPairs][2];
+template <int NM>
+struct MapsN {
+  CUtensorMap a[NM][2];  // [operand pair][hi, lo]
+  CUtensorMap b[NM][2];
 };
+using Maps = MapsN<kMaxPairs>;
 
 // One launch unit: a K range [k0, k0 + Kp) of an operand pair (map); with
 // split-K every range writes its own FP64 partial (c, row stride ldc) and a
@@ -214,8 +216,8 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
-template <int NPASS, int EB>
-__global__ void __launch_bounds__(NT, 1) gemm_tc_kernel(const __grid_constant__ Maps maps, const Group g,
+template <int NPASS, int EB, int NM>
+__global__ void __launch_bounds__(NT, 1) gemm_tc_kernel(const __grid_constant__ MapsN<NM> maps, const Group g,
                                                         int total_tiles, int* __restrict__ err) {
   using K = Cfg<NPASS, EB>;
   extern __shared__ uint8_t smem_raw[];
@@ -491,13 +493,29 @@ __global__ void tc_splitk_reduce_kernel(const double* __restrict__ part, int nsp
   }
 }
 
+// Launch with the tensor maps of the first NM operand pairs only: the maps
+// are kernel parameters (512 bytes per pair), and a smaller parameter block
+// launches faster.
+template <int NPASS, int EB, int NM>
+cudaError_t launch_tc(const Maps& all, const Group& g, int grid, int tiles, int* err, cudaStream_t s) {
+  using K = Cfg<NPASS, EB>;
+  // set once per process and instantiation (thread-safe static initialisation)
+  static const cudaError_t attr_err = cudaFuncSetAttribute(gemm_tc_kernel<NPASS, EB, NM>,
+                                                           cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM);
+  if (attr_err != cudaSuccess) return attr_err;
+  MapsN<NM> maps;
+  for (int j = 0; j < NM; ++j)
+    for (int h = 0; h < 2; ++h) {
+      maps.a[j][h] = all.a[j][h];
+      maps.b[j][h] = all.b[j][h];
+    }
+  gemm_tc_kernel<NPASS, EB, NM><<<grid, NT, K::SMEM, s>>>(maps, g, tiles, err);
+  return cudaGetLastError();
+}
+
 template <int NPASS, int EB>
 cudaError_t run(const TcProblem* probs, int nprob, int* err, cudaStream_t s, double* part, long long part_elems) {
   using K = Cfg<NPASS, EB>;
-  // set once per process (thread-safe static initialisation)
-  static const cudaError_t attr_err = cudaFuncSetAttribute(gemm_tc_kernel<NPASS, EB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         K::SMEM);
-  if (attr_err != cudaSuccess) return attr_err;
   Maps maps;
   memset(&maps, 0, sizeof maps);
   Group g{};
@@ -569,8 +587,9 @@ cudaError_t run(const TcProblem* probs, int nprob, int* err, cudaStream_t s, dou
     return n;
   }();
   const int grid = tiles < sms ? tiles : sms;
-  gemm_tc_kernel<NPASS, EB><<<grid, NT, K::SMEM, s>>>(maps, g, tiles, err);
-  cudaError_t e = cudaGetLastError();
+  cudaError_t e = nmap <= 1   ? launch_tc<NPASS, EB, 1>(maps, g, grid, tiles, err, s)
+                  : nmap <= 2 ? launch_tc<NPASS, EB, 2>(maps, g, grid, tiles, err, s)
+                              : launch_tc<NPASS, EB, kMaxPairs>(maps, g, grid, tiles, err, s);
   if (e != cudaSuccess) return e;
   for (int r = 0; r < nred; ++r) {
     const long long mn = (long long)red[r].M * red[r].N;

@@ -1,6 +1,7 @@
 // Host-side planning of FSO permutations and block GEMMs (Z2 bookkeeping,
 // arXiv 2410.11596 Sec. II.B), plus the generic permute kernel.
 #include <cstdint>
+#include <type_traits>
 
 #include "hs_bits.cuh"
 #include "hs_internal.cuh"
@@ -219,8 +220,17 @@ __device__ __forceinline__ void box_offsets(const Box& b, long long e, long long
   }
 }
 
-__global__ void permute_f64_kernel(PermPlan plan, const double* __restrict__ in,
-                                   double* __restrict__ out, double scale) {
+// The kernels take the plan's boxes by value in a parameter block sized to
+// the plan (NB boxes of 192 bytes): a full 32-box plan is a 6 KB parameter
+// block, which makes every launch of the common 2- and 8-box plans slower.
+template <int NB>
+struct PlanArg {
+  Box box[NB];
+};
+
+template <int NB>
+__global__ void permute_f64_kernel(PlanArg<NB> plan, const double* __restrict__ in, double* __restrict__ out,
+                                   double scale) {
   const Box& b = plan.box[blockIdx.y];
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < b.count; e += stride) {
@@ -245,8 +255,8 @@ __device__ __forceinline__ void store_split(double x, void* hi, void* lo, long l
   }
 }
 
-template <int MODE>
-__global__ void permute_split_kernel(PermPlan plan, const double* __restrict__ in, void* __restrict__ hi,
+template <int MODE, int NB>
+__global__ void permute_split_kernel(PlanArg<NB> plan, const double* __restrict__ in, void* __restrict__ hi,
                                      void* __restrict__ lo) {
   const Box& b = plan.box[blockIdx.y];
   const long long stride = (long long)gridDim.x * blockDim.x;
@@ -265,10 +275,21 @@ cudaError_t launch_permute_split(const PermPlan& plan, const double* in, void* h
   long long gx = (maxc + 255) / 256;
   if (gx > 2048) gx = 2048;
   dim3 grid((unsigned)gx, (unsigned)plan.nbox);
-  if (mode == 1)
-    permute_split_kernel<1><<<grid, 256, 0, s>>>(plan, in, hi, lo);
+  auto go = [&](auto nb) {
+    constexpr int NB = decltype(nb)::value;
+    PlanArg<NB> arg;
+    for (int i = 0; i < plan.nbox; ++i) arg.box[i] = plan.box[i];
+    if (mode == 1)
+      permute_split_kernel<1, NB><<<grid, 256, 0, s>>>(arg, in, hi, lo);
+    else
+      permute_split_kernel<2, NB><<<grid, 256, 0, s>>>(arg, in, hi, lo);
+  };
+  if (plan.nbox <= 2)
+    go(std::integral_constant<int, 2>{});
+  else if (plan.nbox <= 8)
+    go(std::integral_constant<int, 8>{});
   else
-    permute_split_kernel<2><<<grid, 256, 0, s>>>(plan, in, hi, lo);
+    go(std::integral_constant<int, kMaxBoxes>{});
   return cudaGetLastError();
 }
 
@@ -305,7 +326,18 @@ cudaError_t launch_permute_f64(const PermPlan& plan, const double* in, double* o
   long long gx = (maxc + 255) / 256;
   if (gx > 2048) gx = 2048;
   dim3 grid((unsigned)gx, (unsigned)plan.nbox);
-  permute_f64_kernel<<<grid, 256, 0, s>>>(plan, in, out, scale);
+  auto go = [&](auto nb) {
+    constexpr int NB = decltype(nb)::value;
+    PlanArg<NB> arg;
+    for (int i = 0; i < plan.nbox; ++i) arg.box[i] = plan.box[i];
+    permute_f64_kernel<NB><<<grid, 256, 0, s>>>(arg, in, out, scale);
+  };
+  if (plan.nbox <= 2)
+    go(std::integral_constant<int, 2>{});
+  else if (plan.nbox <= 8)
+    go(std::integral_constant<int, 8>{});
+  else
+    go(std::integral_constant<int, kMaxBoxes>{});
   return cudaGetLastError();
 }
 
