@@ -484,6 +484,8 @@ hs_status lowdin_rows(hs_ctx ctx, hs_precision prec, double* X, int m, int n, do
 // of the filtered rows. X receives the locked rows, then
 // the filtered ones (not normalised). Returns false in *used when no interior
 // magnitude exists (the caller then takes a plain step).
+constexpr int kMaxSubRows = 256;  // bound on the subspace rows (max_subspace() is smaller)
+
 hs_status cheb_filter_block(hs_ctx ctx, hs_precision prec, int b, int m, int n, const double* H,
                             const float* theta, int kept_b, double* X, bool* used) {
   constexpr int kDeg = 8;
@@ -506,9 +508,15 @@ hs_status cheb_filter_block(hs_ctx ctx, hs_precision prec, int b, int m, int n, 
   const int mL = (int)idx.size(), mU = m - mL;
   for (int i = 0; i < m; ++i)
     if (std::fabs((double)theta[i]) < kLock * a) idx.push_back(i);
-  HS_TRY(ctx->sf_idx.ensure((size_t)m * sizeof(int)));
-  int* didx = static_cast<int*>(ctx->sf_idx.p);
-  HS_CUDA(cudaMemcpyAsync(didx, idx.data(), (size_t)m * sizeof(int), cudaMemcpyHostToDevice, s));
+  // per-block regions of the pinned and device index buffers: the copy is
+  // asynchronous, so block 1 must not overwrite block 0's staging
+  HS_TRY(ctx->sf_idx.ensure(2 * (size_t)kMaxSubRows * sizeof(int)));
+  HS_TRY(ctx->h_idx.ensure(2 * (size_t)kMaxSubRows * sizeof(int)));
+  if (m > kMaxSubRows) return fail(HS_ERR_INVALID_ARG, "subspace of %d rows", m);
+  int* didx = static_cast<int*>(ctx->sf_idx.p) + b * kMaxSubRows;
+  int* hidx = static_cast<int*>(ctx->h_idx.p) + b * kMaxSubRows;
+  std::copy(idx.begin(), idx.end(), hidx);
+  HS_CUDA(cudaMemcpyAsync(didx, hidx, (size_t)m * sizeof(int), cudaMemcpyHostToDevice, s));
   const size_t mn = (size_t)m * n * sizeof(double);
   for (auto* buf : {&ctx->sf_y[0], &ctx->sf_y[1], &ctx->sf_y[2], &ctx->sf_z, &ctx->sf_t, &ctx->sf_q, &ctx->sf_qt})
     HS_TRY(buf->ensure(mn));
@@ -646,27 +654,36 @@ hs_status subspace_projector(hs_ctx ctx, hs_env* env, int chi, int n0, int n1, d
   if (tc) ctx->sH_fresh = true;
   HS_TRY(ctx->sth.ensure((size_t)(m[0] + m[1] + 2) * sizeof(float)));
   float* th = static_cast<float*>(ctx->sth.p);
-  std::vector<float> hth(m[0] + m[1]);
-  std::vector<double> hres(m[0] + m[1]);
-  int hbad = 0;
+  // pinned read-back of the Ritz values, residuals and status words (a copy
+  // into pageable memory would block the host before the stream drains)
+  const int mt = m[0] + m[1];
+  HS_TRY(ctx->h_sub.ensure((size_t)mt * (sizeof(double) + sizeof(float)) + 4 * sizeof(int)));
+  double* hres = static_cast<double*>(ctx->h_sub.p);
+  float* hth = reinterpret_cast<float*>(hres + mt);
+  int* hstat = reinterpret_cast<int*>(hth + mt);  // Jacobi status of both blocks, Cholesky status
   double prev_worst = INFINITY;
   for (int it = 0; it < kMaxIt; ++it) {
     *iters = it + 1;
     for (int b = 0; b < 2; ++b) {
       if (m[b] == 0) continue;
-      // Z = X H (H symmetric), Rayleigh matrix B = Z X^T
+      // Z = X H (H symmetric), Rayleigh matrix B = X Z^T (symmetric; the
+      // tensor-core path reuses the split X as the A operand of both)
       if (tc) {
         HS_TRY(tc_split(ctx, prec, dense2(m[b], n[b]), dense2(m[b], n[b]), {0, 1}, ctx->sx[b].d(), ctx->sx_hi, ctx->sx_lo));
         HS_TRY(tc_run(ctx, prec, dense2(m[b], n[b]), ctx->sx_hi, ctx->sx_lo, dense2(n[b], n[b]), ctx->sH_hi[b],
                       ctx->sH_lo[b], dense2(m[b], n[b]), ctx->sz[b].d()));
-        ctx->phase_flops[HS_PHASE_GEMM_TC] += 2.0 * m[b] * (double)n[b] * n[b];
+        HS_TRY(tc_split(ctx, prec, dense2(m[b], n[b]), dense2(m[b], n[b]), {0, 1}, ctx->sz[b].d(), ctx->sy_hi, ctx->sy_lo));
+        HS_TRY(tc_run(ctx, prec, dense2(m[b], n[b]), ctx->sx_hi, ctx->sx_lo, dense2(m[b], n[b]), ctx->sy_hi,
+                      ctx->sy_lo, dense2(m[b], m[b]), ctx->sbm[b].d()));
+        ctx->phase_flops[HS_PHASE_GEMM_TC] += 2.0 * m[b] * (double)n[b] * n[b] + 2.0 * m[b] * (double)m[b] * n[b];
       } else {
         HS_TRY(gemm(ctx, HS_GEMM_OWN, GemmGroup{1, {GemmProblem{m[b], n[b], n[b], n[b], n[b], n[b], 0, 0, 0}}},
                     ctx->sx[b].d(), H[b], ctx->sz[b].d()));
-        ctx->phase_flops[HS_PHASE_GEMM] += 2.0 * m[b] * (double)n[b] * n[b];
+        HS_TRY(gemm(ctx, HS_GEMM_OWN, GemmGroup{1, {GemmProblem{m[b], m[b], n[b], n[b], n[b], m[b], 0, 0, 0}}},
+                    ctx->sx[b].d(), ctx->sz[b].d(), ctx->sbm[b].d()));
+        ctx->phase_flops[HS_PHASE_GEMM] += 2.0 * m[b] * (double)n[b] * n[b] + 2.0 * m[b] * (double)m[b] * n[b];
       }
       *flops += 2.0 * m[b] * (double)n[b] * n[b];
-      HS_TRY(dense_gemm_any(ctx, prec, m[b], m[b], n[b], ctx->sz[b].d(), ctx->sx[b].d(), ctx->sbm[b].d()));
       HS_CUDA(launch_cast_f64_f32(ctx->sbm[b].d(), static_cast<float*>(ctx->sbw[b].p), (long long)m[b] * m[b], s));
       ctx->launches += 1;
     }
@@ -682,24 +699,40 @@ hs_status subspace_projector(hs_ctx ctx, hs_env* env, int chi, int n0, int n1, d
       if (m[b] == 0) continue;
       // Ritz vectors Xr = W^T X and Zr = W^T Z (W column-major = W^T row-major)
       HS_CUDA(launch_cast_f32_f64(static_cast<float*>(ctx->sbw[b].p), ctx->sbm[b].d(), (long long)m[b] * m[b], s));
-      HS_TRY(permute(ctx, dense2(m[b], n[b]), dense2(n[b], m[b]), {1, 0}, ctx->sx[b].d(), ctx->sxc[b].d()));
-      HS_TRY(permute(ctx, dense2(m[b], n[b]), dense2(n[b], m[b]), {1, 0}, ctx->sz[b].d(), ctx->szc[b].d()));
-      HS_TRY(dense_gemm_any(ctx, prec, m[b], n[b], m[b], ctx->sbm[b].d(), ctx->sxc[b].d(), ctx->sxr[b].d()));
-      HS_TRY(dense_gemm_any(ctx, prec, m[b], n[b], m[b], ctx->sbm[b].d(), ctx->szc[b].d(), ctx->szr[b].d()));
+      ctx->launches += 1;
+      if (tc) {
+        // W split once; X^T and Z^T written straight into the split B operand
+        HS_TRY(tc_split(ctx, prec, dense2(m[b], m[b]), dense2(m[b], m[b]), {0, 1}, ctx->sbm[b].d(), ctx->sx_hi,
+                        ctx->sx_lo));
+        HS_TRY(tc_split(ctx, prec, dense2(m[b], n[b]), dense2(n[b], m[b]), {1, 0}, ctx->sx[b].d(), ctx->sy_hi,
+                        ctx->sy_lo));
+        HS_TRY(tc_run(ctx, prec, dense2(m[b], m[b]), ctx->sx_hi, ctx->sx_lo, dense2(n[b], m[b]), ctx->sy_hi,
+                      ctx->sy_lo, dense2(m[b], n[b]), ctx->sxr[b].d()));
+        HS_TRY(tc_split(ctx, prec, dense2(m[b], n[b]), dense2(n[b], m[b]), {1, 0}, ctx->sz[b].d(), ctx->sy_hi,
+                        ctx->sy_lo));
+        HS_TRY(tc_run(ctx, prec, dense2(m[b], m[b]), ctx->sx_hi, ctx->sx_lo, dense2(n[b], m[b]), ctx->sy_hi,
+                      ctx->sy_lo, dense2(m[b], n[b]), ctx->szr[b].d()));
+        ctx->phase_flops[HS_PHASE_GEMM_TC] += 4.0 * m[b] * (double)m[b] * n[b];
+      } else {
+        HS_TRY(permute(ctx, dense2(m[b], n[b]), dense2(n[b], m[b]), {1, 0}, ctx->sx[b].d(), ctx->sxc[b].d()));
+        HS_TRY(permute(ctx, dense2(m[b], n[b]), dense2(n[b], m[b]), {1, 0}, ctx->sz[b].d(), ctx->szc[b].d()));
+        HS_TRY(dense_gemm_any(ctx, prec, m[b], n[b], m[b], ctx->sbm[b].d(), ctx->sxc[b].d(), ctx->sxr[b].d()));
+        HS_TRY(dense_gemm_any(ctx, prec, m[b], n[b], m[b], ctx->sbm[b].d(), ctx->szc[b].d(), ctx->szr[b].d()));
+      }
       HS_CUDA(launch_residual(ctx->szr[b].d(), ctx->sxr[b].d(), th + (b ? m[0] : 0), m[b], n[b], ctx->sres[b].d(), s));
-      ctx->launches += 2;
+      ctx->launches += 1;
     }
-    int hinfo[2];
-    HS_CUDA(cudaMemcpyAsync(hth.data(), th, hth.size() * sizeof(float), cudaMemcpyDeviceToHost, s));
+    HS_CUDA(cudaMemcpyAsync(hth, th, (size_t)mt * sizeof(float), cudaMemcpyDeviceToHost, s));
     for (int b = 0; b < 2; ++b)
       if (m[b] > 0)
-        HS_CUDA(cudaMemcpyAsync(hres.data() + (b ? m[0] : 0), ctx->sres[b].p, m[b] * sizeof(double),
+        HS_CUDA(cudaMemcpyAsync(hres + (b ? m[0] : 0), ctx->sres[b].p, m[b] * sizeof(double),
                                 cudaMemcpyDeviceToHost, s));
-    HS_CUDA(cudaMemcpyAsync(hinfo, ctx->info.p, sizeof hinfo, cudaMemcpyDeviceToHost, s));
-    HS_CUDA(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+    // info[0], info[1]: Jacobi status; info[2]: Cholesky status (bad)
+    HS_CUDA(cudaMemcpyAsync(hstat, ctx->info.p, 3 * sizeof(int), cudaMemcpyDeviceToHost, s));
     HS_CUDA(cudaStreamSynchronize(s));
+    const int hbad = hstat[2];
     *reason = hbad ? 4 : 7;
-    if (hbad || hinfo[0] || hinfo[1]) return HS_OK;  // fall back
+    if (hbad || hstat[0] || hstat[1]) return HS_OK;  // fall back
     // the states the selection can keep: the chi largest |theta| across both
     // blocks, plus two more per block; all of them must have converged, and no
     // block may keep states near the edge of its subspace
@@ -743,7 +776,7 @@ hs_status subspace_projector(hs_ctx ctx, hs_env* env, int chi, int n0, int n1, d
         // next basis: a Chebyshev-filtered step where possible, else a plain
         // power step (rows of Zr = theta_i x_i + residual)
         bool filtered = false;
-        HS_TRY(cheb_filter_block(ctx, prec, b, m[b], n[b], H[b], hth.data() + (b ? m[0] : 0), kept[b],
+        HS_TRY(cheb_filter_block(ctx, prec, b, m[b], n[b], H[b], hth + (b ? m[0] : 0), kept[b],
                                  ctx->sx[b].d(), &filtered));
         if (!filtered)
           HS_CUDA(cudaMemcpyAsync(ctx->sx[b].p, ctx->szr[b].p, (size_t)m[b] * n[b] * sizeof(double),
@@ -851,6 +884,8 @@ hs_status hs_destroy(hs_ctx ctx) {
   if (ctx->h_sel) cudaFreeHost(ctx->h_sel);
   if (ctx->h_info) cudaFreeHost(ctx->h_info);
   if (ctx->h_tc_err) cudaFreeHost(ctx->h_tc_err);
+  ctx->h_sub.release();
+  ctx->h_idx.release();
   if (ctx->stream2) cudaStreamSynchronize(ctx->stream2);
   DBuf* s2b[] = {&ctx->solver2_dev, &ctx->solver2_32_dev};
   for (DBuf* b : s2b) b->release();

@@ -80,6 +80,30 @@ struct DBuf {
   double* d() const { return static_cast<double*>(p); }
 };
 
+// Pinned host buffer, grown on demand (device-to-host copies into pageable
+// memory block the host until the stream drains).
+struct PinnedBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  hs_status ensure(size_t want) {
+    if (want <= bytes) return HS_OK;
+    if (p) cudaFreeHost(p);
+    p = nullptr;
+    bytes = 0;
+    if (cudaMallocHost(&p, want) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(HS_ERR_CUDA, "cudaMallocHost of %zu bytes failed", want);
+    }
+    bytes = want;
+    return HS_OK;
+  }
+  void release() {
+    if (p) cudaFreeHost(p);
+    p = nullptr;
+    bytes = 0;
+  }
+};
+
 }  // namespace hs
 
 struct hs_ctx_s {
@@ -137,6 +161,9 @@ struct hs_ctx_s {
   // product, the projection and its coefficients, the locked rows (and their
   // transpose), and the row order
   hs::DBuf sf_y[3], sf_z, sf_t, sf_s, sf_q, sf_qt, sf_idx;
+  // pinned staging: Ritz values, residuals and status words (device to
+  // host), the filter's row order (host to device)
+  hs::PinnedBuf h_sub, h_idx;
   // profiling: events between phases, harvested after the move's last sync
   bool prof = false;
   unsigned prof_mask = ~0u;  // phases that record events when prof is on

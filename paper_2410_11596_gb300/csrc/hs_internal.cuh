@@ -139,6 +139,7 @@ struct Box {
   // division by dim[j] of 32-bit indices (fast_div in hs_bits.cuh)
   unsigned mag[kMaxLegs];
   unsigned char sh1[kMaxLegs], sh2[kMaxLegs];
+  int lo;            // first non-trivial dim: dims [0, lo) have extent 1
 };
 
 constexpr int kMaxBoxes = 32;  // even-parity tuples of 6 legs

@@ -66,6 +66,7 @@ PermPlan make_perm_plan(const Z2Mat& in, const Z2Mat& out, const int* perm) {
     }
     if (b.count == 0) continue;
     for (int j = 0; j < kMaxLegs; ++j) fast_div_magic((unsigned)b.dim[j], &b.mag[j], &b.sh1[j], &b.sh2[j]);
+    b.lo = n > 0 ? kMaxLegs - n : kMaxLegs - 1;
     b.start = start;
     start += b.count;
     plan.box[plan.nbox++] = b;
@@ -133,6 +134,7 @@ bool make_graded_perm_plan(const GMat& in, const GMat& out, const int* perm, Per
     }
     if (b.count == 0) continue;
     for (int j = 0; j < kMaxLegs; ++j) fast_div_magic((unsigned)b.dim[j], &b.mag[j], &b.sh1[j], &b.sh2[j]);
+    b.lo = n > 0 ? kMaxLegs - n : kMaxLegs - 1;
     b.start = start;
     start += b.count;
     plan.box[plan.nbox++] = b;
@@ -195,17 +197,17 @@ __device__ __forceinline__ void box_offsets(const Box& b, long long e, long long
   io = b.in_off;
   oo = b.out_off;
   if (b.count < (1ll << 31)) {
+    // only the box's own dims (the leading extent-1 dims add nothing)
     unsigned r = (unsigned)e;
-#pragma unroll
-    for (int j = kMaxLegs - 1; j > 0; --j) {
+    for (int j = kMaxLegs - 1; j > b.lo; --j) {
       const unsigned qd = fast_div(r, b.mag[j], b.sh1[j], b.sh2[j]);
       const unsigned ij = r - qd * (unsigned)b.dim[j];
       r = qd;
       io += (long long)ij * b.in_stride[j];
       oo += (long long)ij * b.out_stride[j];
     }
-    io += (long long)r * b.in_stride[0];
-    oo += (long long)r * b.out_stride[0];
+    io += (long long)r * b.in_stride[b.lo];
+    oo += (long long)r * b.out_stride[b.lo];
   } else {
     long long r = e;
 #pragma unroll
