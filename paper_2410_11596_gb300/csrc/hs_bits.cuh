@@ -85,6 +85,7 @@ HS_HD uint32_t round_to_float(unsigned long long A, int k, int bits, uint32_t si
   // sig in [2^(bits-1), 2^bits]; a carry to 2^bits lands in the exponent field
   const int fe = k + top + 127;
   if (fe <= 0) return (fe == 0 && sig == (1ull << bits)) ? (sign | 0x00800000u) : sign;  // rounds up to 2^-126
+  if (fe >= 255) return sign | 0x7F800000u;
   const uint32_t v = ((uint32_t)fe << 23) + ((uint32_t)(sig - (1ull << (bits - 1))) << (24 - bits));
   return v >= 0x7F800000u ? (sign | 0x7F800000u) : (sign | v);
 }
@@ -108,6 +109,10 @@ HS_HD void split_f64(double x, int hb, int lb, bool hi_away, uint32_t& hi, uint3
     hi = lo = sign;
     return;
   }
+  if (fe >= 255) {  // beyond the single range
+    hi = lo = sign | 0x7F800000u;
+    return;
+  }
   const unsigned long long M = (b & ((1ull << 52) - 1)) | (1ull << 52);  // |x| = M 2^(e-1075)
   const int drop = 53 - hb;
   const unsigned long long half = 1ull << (drop - 1), rem = M & ((1ull << drop) - 1);
@@ -122,6 +127,73 @@ HS_HD void split_f64(double x, int hb, int lb, bool hi_away, uint32_t& hi, uint3
   }
   lo = round_to_float(R < 0 ? (unsigned long long)(-R) : (unsigned long long)R, e - 1075, lb,
                       R < 0 ? (sign ^ 0x80000000u) : sign);
+}
+
+// split_f64(x, 11, 24, true, hi, lo) (TF32 hi with ties away, FP32 lo) in
+// 32-bit integer operations: the rounding bit of hi is bit 41 of the
+// significand M, and the remainder M mod 2^42 (minus 2^42 when hi rounded
+// up) has at most 42 bits, held as two words. Bit-identical to split_f64.
+HS_HD void split_tf32x3(double x, uint32_t& hi, uint32_t& lo) {
+  const unsigned long long b = f64_bits(x);
+  const uint32_t hw = (uint32_t)(b >> 32), lw = (uint32_t)b;
+  const uint32_t sign = hw & 0x80000000u;
+  const int e = (int)((hw >> 20) & 0x7FFu);
+  if (e == 0x7FF) {
+    hi = lo = 0x7FC00000u;
+    return;
+  }
+  const int fe = e - 896;
+  if (fe <= 0) {
+    hi = lo = sign;
+    return;
+  }
+  if (fe >= 255) {
+    hi = lo = sign | 0x7F800000u;
+    return;
+  }
+  const uint32_t m20 = hw & 0xFFFFFu;
+  const uint32_t up = (m20 >> 9) & 1u;             // ties away: round up on the top dropped bit
+  const uint32_t sh = 1024u + (m20 >> 10) + up;    // 11 significant bits, may carry to 2^11
+  const uint32_t hv = ((uint32_t)fe << 23) + ((sh - 1024u) << 13);
+  hi = hv >= 0x7F800000u ? (sign | 0x7F800000u) : (sign | hv);
+  // remainder A = |M - sh 2^42| as (ah, al), sign of lo
+  uint32_t ah = m20 & 0x3FFu, al = lw;
+  uint32_t sgn = sign;
+  if (up) {
+    const uint32_t borrow = al != 0u;
+    al = 0u - al;
+    ah = 1024u - ah - borrow;
+    sgn ^= 0x80000000u;
+  } else if (ah == 0u && al == 0u) {
+    lo = 0u;
+    return;
+  }
+  int top;
+#if defined(__CUDA_ARCH__)
+  top = ah ? 63 - __clz((int)ah) : 31 - __clz((int)al);
+#else
+  top = ah ? 63 - __builtin_clz(ah) : 31 - __builtin_clz(al);
+#endif
+  const int drop = top - 23;
+  uint32_t sig;
+  if (drop > 0) {  // drop <= 19
+    sig = (al >> drop) | (ah << (32 - drop));
+    const uint32_t rem = al & ((1u << drop) - 1u), half = 1u << (drop - 1);
+    if (rem > half || (rem == half && (sig & 1u))) ++sig;
+  } else {
+    sig = al << (-drop);
+  }
+  const int fl = e - 948 + top;  // (e - 1075) + top + 127
+  if (fl <= 0) {
+    lo = (fl == 0 && sig == (1u << 24)) ? (sgn | 0x00800000u) : sgn;
+    return;
+  }
+  if (fl >= 255) {
+    lo = sgn | 0x7F800000u;
+    return;
+  }
+  const uint32_t v = ((uint32_t)fl << 23) + (sig - (1u << 23));
+  lo = v >= 0x7F800000u ? (sgn | 0x7F800000u) : (sgn | v);
 }
 
 // The FP64 value of the IEEE single bit pattern f (exact). Subnormal singles

@@ -140,7 +140,13 @@ struct Box {
   unsigned mag[kMaxLegs];
   unsigned char sh1[kMaxLegs], sh2[kMaxLegs];
   int lo;            // first non-trivial dim: dims [0, lo) have extent 1
+  // chunked traversal: rows (all dims but the innermost) x nch chunks of
+  // kPermVec innermost elements; division by nch as for the dims
+  int fits32;        // every offset of the box and rows * nch below 2^31
+  unsigned rows, nch, magc;
+  unsigned char sh1c, sh2c;
 };
+constexpr int kPermVec = 4;
 
 constexpr int kMaxBoxes = 32;  // even-parity tuples of 6 legs
 

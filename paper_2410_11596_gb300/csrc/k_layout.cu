@@ -32,6 +32,25 @@ void leg_strides(const Z2Mat& m, const int* par, long long* stride, long long* o
 
 Sect leg_of(const Z2Mat& m, int j) { return j < m.r.k ? m.r.leg[j] : m.c.leg[j - m.r.k]; }
 
+// Chunked-traversal fields of a box (dims, strides, offsets and count set).
+void set_chunks(Box& b) {
+  const long long inner = b.dim[kMaxLegs - 1];
+  long long in_max = b.in_off, out_max = b.out_off;
+  for (int j = 0; j < kMaxLegs; ++j) {
+    in_max += (long long)(b.dim[j] - 1) * b.in_stride[j];
+    out_max += (long long)(b.dim[j] - 1) * b.out_stride[j];
+  }
+  const long long rows = inner > 0 ? b.count / inner : 0;
+  const long long nch = (inner + kPermVec - 1) / kPermVec;
+  const long long lim = 1ll << 31;
+  b.fits32 = inner > 0 && in_max < lim && out_max < lim && rows * nch < lim && b.count < lim;
+  for (int j = 0; j < kMaxLegs; ++j)
+    if (b.in_stride[j] >= lim || b.out_stride[j] >= lim) b.fits32 = 0;
+  b.rows = (unsigned)rows;
+  b.nch = (unsigned)(nch > 0 ? nch : 1);
+  fast_div_magic(b.nch, &b.magc, &b.sh1c, &b.sh2c);
+}
+
 }  // namespace
 
 PermPlan make_perm_plan(const Z2Mat& in, const Z2Mat& out, const int* perm) {
@@ -67,6 +86,7 @@ PermPlan make_perm_plan(const Z2Mat& in, const Z2Mat& out, const int* perm) {
     if (b.count == 0) continue;
     for (int j = 0; j < kMaxLegs; ++j) fast_div_magic((unsigned)b.dim[j], &b.mag[j], &b.sh1[j], &b.sh2[j]);
     b.lo = n > 0 ? kMaxLegs - n : kMaxLegs - 1;
+    set_chunks(b);
     b.start = start;
     start += b.count;
     plan.box[plan.nbox++] = b;
@@ -135,6 +155,7 @@ bool make_graded_perm_plan(const GMat& in, const GMat& out, const int* perm, Per
     if (b.count == 0) continue;
     for (int j = 0; j < kMaxLegs; ++j) fast_div_magic((unsigned)b.dim[j], &b.mag[j], &b.sh1[j], &b.sh2[j]);
     b.lo = n > 0 ? kMaxLegs - n : kMaxLegs - 1;
+    set_chunks(b);
     b.start = start;
     start += b.count;
     plan.box[plan.nbox++] = b;
@@ -222,6 +243,36 @@ __device__ __forceinline__ void box_offsets(const Box& b, long long e, long long
   }
 }
 
+// 32-bit start offsets of row `row` of box b (fits32): every dim but the
+// innermost, decoded once per chunk of kPermVec innermost elements.
+__device__ __forceinline__ void row_offsets32(const Box& b, unsigned row, unsigned& io, unsigned& oo) {
+  io = (unsigned)b.in_off;
+  oo = (unsigned)b.out_off;
+  unsigned r = row;
+  for (int j = kMaxLegs - 2; j > b.lo; --j) {
+    const unsigned qd = fast_div(r, b.mag[j], b.sh1[j], b.sh2[j]);
+    const unsigned ij = r - qd * (unsigned)b.dim[j];
+    r = qd;
+    io += ij * (unsigned)b.in_stride[j];
+    oo += ij * (unsigned)b.out_stride[j];
+  }
+  if (b.lo < kMaxLegs - 1) {
+    io += r * (unsigned)b.in_stride[b.lo];
+    oo += r * (unsigned)b.out_stride[b.lo];
+  }
+}
+
+// Threads a box needs: one per chunk (fits32) or per element.
+long long max_work(const PermPlan& plan) {
+  long long w = 0;
+  for (int i = 0; i < plan.nbox; ++i) {
+    const Box& b = plan.box[i];
+    const long long t = b.fits32 ? (long long)b.rows * b.nch : b.count;
+    w = t > w ? t : w;
+  }
+  return w;
+}
+
 // The kernels take the plan's boxes by value in a parameter block sized to
 // the plan (NB boxes of 192 bytes): a full 32-box plan is a 6 KB parameter
 // block, which makes every launch of the common 2- and 8-box plans slower.
@@ -230,15 +281,41 @@ struct PlanArg {
   Box box[NB];
 };
 
+// Each thread moves a chunk of kPermVec consecutive innermost elements (one
+// index decode per chunk, loads issued before the stores); boxes beyond the
+// 32-bit range go element by element.
 template <int NB>
 __global__ void permute_f64_kernel(PlanArg<NB> plan, const double* __restrict__ in, double* __restrict__ out,
                                    double scale) {
   const Box& b = plan.box[blockIdx.y];
+  const bool plain = scale == 1.0;  // plain copies keep off the FP64 pipe
+  if (b.fits32) {
+    const unsigned inner = (unsigned)b.dim[kMaxLegs - 1];
+    const unsigned istr = (unsigned)b.in_stride[kMaxLegs - 1], ostr = (unsigned)b.out_stride[kMaxLegs - 1];
+    const unsigned total = b.rows * b.nch;
+    for (unsigned c = blockIdx.x * blockDim.x + threadIdx.x; c < total; c += gridDim.x * blockDim.x) {
+      const unsigned row = fast_div(c, b.magc, b.sh1c, b.sh2c);
+      const unsigned i0 = (c - row * b.nch) * kPermVec;
+      unsigned io, oo;
+      row_offsets32(b, row, io, oo);
+      io += i0 * istr;
+      oo += i0 * ostr;
+      const unsigned nv = inner - i0 < (unsigned)kPermVec ? inner - i0 : (unsigned)kPermVec;
+      double v[kPermVec];
+#pragma unroll
+      for (int k = 0; k < kPermVec; ++k)
+        if ((unsigned)k < nv) v[k] = in[io + k * istr];
+#pragma unroll
+      for (int k = 0; k < kPermVec; ++k)
+        if ((unsigned)k < nv) out[oo + k * ostr] = plain ? v[k] : scale * v[k];
+    }
+    return;
+  }
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < b.count; e += stride) {
     long long io, oo;
     box_offsets(b, e, io, oo);
-    out[oo] = scale == 1.0 ? in[io] : scale * in[io];  // plain copies keep off the FP64 pipe
+    out[oo] = plain ? in[io] : scale * in[io];
   }
 }
 
@@ -246,7 +323,7 @@ template <int MODE>
 __device__ __forceinline__ void store_split(double x, void* hi, void* lo, long long o) {
   if (MODE == 1) {
     uint32_t h, l;
-    split_f64(x, 11, 24, true, h, l);
+    split_tf32x3(x, h, l);
     static_cast<uint32_t*>(hi)[o] = h;
     static_cast<uint32_t*>(lo)[o] = l;
   } else {
@@ -261,6 +338,28 @@ template <int MODE, int NB>
 __global__ void permute_split_kernel(PlanArg<NB> plan, const double* __restrict__ in, void* __restrict__ hi,
                                      void* __restrict__ lo) {
   const Box& b = plan.box[blockIdx.y];
+  if (b.fits32) {
+    const unsigned inner = (unsigned)b.dim[kMaxLegs - 1];
+    const unsigned istr = (unsigned)b.in_stride[kMaxLegs - 1], ostr = (unsigned)b.out_stride[kMaxLegs - 1];
+    const unsigned total = b.rows * b.nch;
+    for (unsigned c = blockIdx.x * blockDim.x + threadIdx.x; c < total; c += gridDim.x * blockDim.x) {
+      const unsigned row = fast_div(c, b.magc, b.sh1c, b.sh2c);
+      const unsigned i0 = (c - row * b.nch) * kPermVec;
+      unsigned io, oo;
+      row_offsets32(b, row, io, oo);
+      io += i0 * istr;
+      oo += i0 * ostr;
+      const unsigned nv = inner - i0 < (unsigned)kPermVec ? inner - i0 : (unsigned)kPermVec;
+      double v[kPermVec];
+#pragma unroll
+      for (int k = 0; k < kPermVec; ++k)
+        if ((unsigned)k < nv) v[k] = in[io + k * istr];
+#pragma unroll
+      for (int k = 0; k < kPermVec; ++k)
+        if ((unsigned)k < nv) store_split<MODE>(v[k], hi, lo, (long long)(oo + k * ostr));
+    }
+    return;
+  }
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < b.count; e += stride) {
     long long io, oo;
@@ -272,8 +371,7 @@ __global__ void permute_split_kernel(PlanArg<NB> plan, const double* __restrict_
 cudaError_t launch_permute_split(const PermPlan& plan, const double* in, void* hi, void* lo, int mode,
                                  cudaStream_t s) {
   if (plan.nbox == 0) return cudaSuccess;
-  long long maxc = 0;
-  for (int i = 0; i < plan.nbox; ++i) maxc = plan.box[i].count > maxc ? plan.box[i].count : maxc;
+  const long long maxc = max_work(plan);
   long long gx = (maxc + 255) / 256;
   if (gx > 2048) gx = 2048;
   dim3 grid((unsigned)gx, (unsigned)plan.nbox);
@@ -323,8 +421,7 @@ cudaError_t launch_split_pad(const double* src, long long rows, int cols, long l
 cudaError_t launch_permute_f64(const PermPlan& plan, const double* in, double* out, double scale,
                                cudaStream_t s) {
   if (plan.nbox == 0) return cudaSuccess;
-  long long maxc = 0;
-  for (int i = 0; i < plan.nbox; ++i) maxc = plan.box[i].count > maxc ? plan.box[i].count : maxc;
+  const long long maxc = max_work(plan);
   long long gx = (maxc + 255) / 256;
   if (gx > 2048) gx = 2048;
   dim3 grid((unsigned)gx, (unsigned)plan.nbox);

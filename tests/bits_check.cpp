@@ -93,6 +93,26 @@ int main() {
       return 1;
     }
   }
+  // 2b. the 32-bit TF32 split is bit-identical to the general one, over
+  // random significands at every exponent (both ends of the single range
+  // included) and on ties
+  std::uniform_int_distribution<unsigned long long> um(0, (1ull << 52) - 1);
+  for (int e = 0; e < 2047; ++e)
+    for (int i = 0; i < 600; ++i) {
+      unsigned long long m = um(rng);
+      if (i % 5 == 1) m = (m >> 42) << 42 | (1ull << 41);        // exact tie of hi
+      if (i % 5 == 2) m &= ~((1ull << 41) - 1);                  // zero remainder
+      if (i % 5 == 3) m = (m >> 42) << 42 | (m & 0xFFFull);      // tiny remainder
+      const unsigned long long bb = (unsigned long long)(i & 1) << 63 | (unsigned long long)e << 52 | m;
+      const double x = f64_from_bits(bb);
+      uint32_t h1, l1, h2, l2;
+      split_f64(x, 11, 24, true, h1, l1);
+      split_tf32x3(x, h2, l2);
+      if (h1 != h2 || l1 != l2) {
+        std::printf("tf32x3 split of %.17g: %08x %08x vs %08x %08x\n", x, h2, l2, h1, l1);
+        return 1;
+      }
+    }
   // zero, tiny, NaN
   uint32_t h, l;
   split_f64(0.0, 11, 24, true, h, l);
