@@ -67,12 +67,35 @@ hs_status gemm(hs_ctx ctx, hs_gemm_backend be, const GemmGroup& g, const double*
   return HS_OK;
 }
 
+// make_perm_plan through the context's cache, keyed by the two layouts and
+// the permutation.
+const PermPlan& cached_plan(hs_ctx ctx, const Z2Mat& in, const Z2Mat& out, const int* perm) {
+  int key[2 * (2 + 2 * 2 * kMaxFused) + 2 + kMaxLegs];
+  int k = 0;
+  for (const Z2Mat* m : {&in, &out}) {
+    for (const Fused* f : {&m->r, &m->c}) {
+      key[k++] = f->k;
+      for (int j = 0; j < kMaxFused; ++j) {
+        key[k++] = j < f->k ? f->leg[j].n[0] : 0;
+        key[k++] = j < f->k ? f->leg[j].n[1] : 0;
+      }
+    }
+    key[k++] = m->pad;
+  }
+  for (int j = 0; j < kMaxLegs; ++j) key[k++] = perm[j];
+  std::string ks(reinterpret_cast<const char*>(key), k * sizeof(int));
+  auto it = ctx->plan_cache.find(ks);
+  if (it != ctx->plan_cache.end()) return it->second;
+  if (ctx->plan_cache.size() > 4096) ctx->plan_cache.clear();  // bound the cache
+  return ctx->plan_cache.emplace(std::move(ks), make_perm_plan(in, out, perm)).first->second;
+}
+
 hs_status permute(hs_ctx ctx, const Z2Mat& in, const Z2Mat& out, std::initializer_list<int> perm,
                   const double* src, double* dst) {
   int p[kMaxLegs] = {0};
   int i = 0;
   for (int v : perm) p[i++] = v;
-  const PermPlan plan = make_perm_plan(in, out, p);
+  const PermPlan& plan = cached_plan(ctx, in, out, p);
   HS_CUDA(launch_permute_f64(plan, src, dst, 1.0, ctx->stream));
   if (plan.nbox > 0) ctx->launches += 1;
   return HS_OK;
@@ -230,7 +253,7 @@ hs_status tc_split(hs_ctx ctx, hs_precision prec, const Z2Mat& src_layout, const
     HS_CUDA(cudaMemsetAsync(lo.p, 0, nb, ctx->stream));
     hi.zkey = lo.zkey = key;
   }
-  const PermPlan plan = make_perm_plan(src_layout, P, pm);
+  const PermPlan& plan = cached_plan(ctx, src_layout, P, pm);
   HS_CUDA(launch_permute_split(plan, src, hi.p, lo.p, tc_mode(prec), ctx->stream));
   if (plan.nbox > 0) ctx->launches += 1;
   return HS_OK;

@@ -9,8 +9,9 @@
 #include <cstdio>
 #include <cstring>
 #include <initializer_list>
-#include <thread>
 #include <string>
+#include <thread>
+#include <unordered_map>
 #include <vector>
 
 #include "hs_internal.cuh"
@@ -164,6 +165,9 @@ struct hs_ctx_s {
   // pinned staging: Ritz values, residuals and status words (device to
   // host), the filter's row order (host to device)
   hs::PinnedBuf h_sub, h_idx;
+  // permute plans by layout pair and permutation (building one takes a few
+  // microseconds of host time, and every move repeats the same few dozen)
+  std::unordered_map<std::string, hs::PermPlan> plan_cache;
   // profiling: events between phases, harvested after the move's last sync
   bool prof = false;
   unsigned prof_mask = ~0u;  // phases that record events when prof is on
