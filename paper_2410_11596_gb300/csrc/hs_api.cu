@@ -341,17 +341,15 @@ hs_status finish_projector(hs_ctx ctx, int n0, int n1, SelectOut* dsel, Sect c, 
   const Z2Mat PTm = mat(fused1(cn), fused2(c, q)), Pm = mat(fused2(c, q), fused1(cn));
   {
     PhaseScope ps(ctx, HS_PHASE_SELECT);
-    for (int p = 0; p < 2; ++p) HS_CUDA(launch_row_sign(PT + ptoff[p], k[p], n[p], s));
+    HS_CUDA(launch_row_sign_pair(PT, k[0], n[0], k[1], n[1], s));
     HS_TRY(permute(ctx, PTm, Pm, {1, 2, 0}, PT, P));
     ctx->launches += 2;
   }
   if (env->precision != HS_PREC_F64) {
     // tensor-core precisions: the projection below runs on tcgen05 with FP32
     // accumulation, so orthonormality beyond that level buys nothing; the
-    // Loewdin step runs on the tensor cores too (rows of each block)
-    for (int p = 0; p < 2; ++p)
-      if (k[p] > 0 && n[p] > 0)
-        HS_TRY(lowdin_rows(ctx, env->precision, PT + ptoff[p], k[p], n[p], PT2, lowdin));
+    // Loewdin steps run on the tensor cores too (both blocks per launch)
+    HS_TRY(lowdin_rows_pair(ctx, env->precision, PT, k, n, PT2, lowdin));
     lowdin = 0;
   }
   for (int step = 0; step < lowdin; ++step) {
@@ -390,21 +388,17 @@ hs_status finish_projector(hs_ctx ctx, int n0, int n1, SelectOut* dsel, Sect c, 
     *flops += gemm_flops(gw) + gemm_flops(gc);
     ctx->phase_flops[HS_PHASE_GEMM] += gemm_flops(gw) + gemm_flops(gc);
   } else {
+    // both blocks per launch: W = PT C' (C' split once per move), C_new = W PT^T
+    if (!ctx->sH_fresh || ctx->sH_n[0] != n[0] || ctx->sH_n[1] != n[1]) {
+      if (Cp[1] != Cp[0] + (long long)n[0] * n[0]) return fail(HS_ERR_INVALID_ARG, "corner blocks not stacked");
+      HS_TRY(split_corner(ctx, prec, Cp[0], n[0], n[1]));
+    }
+    const Z2Mat PL = zd(k[0], k[1], n[0], n[1]), HL = zd(n[0], n[1], n[0], n[1]), CL = zd(k[0], k[1], k[0], k[1]);
+    HS_TRY(tc_split(ctx, prec, PL, PL, {0, 1}, PT, ctx->sx_hi, ctx->sx_lo));
+    HS_TRY(tc_run(ctx, prec, PL, ctx->sx_hi, ctx->sx_lo, HL, ctx->sH_hi, ctx->sH_lo, PL, W));
+    HS_TRY(tc_split(ctx, prec, PL, PL, {0, 1}, W, ctx->sy_hi, ctx->sy_lo));
+    HS_TRY(tc_run(ctx, prec, PL, ctx->sy_hi, ctx->sy_lo, PL, ctx->sx_hi, ctx->sx_lo, CL, env->C));
     for (int p = 0; p < 2; ++p) {
-      if (k[p] == 0 || n[p] == 0) continue;
-      if (!ctx->sH_fresh || ctx->sH_n[p] != n[p]) {
-        HS_TRY(tc_split(ctx, prec, dense2(n[p], n[p]), dense2(n[p], n[p]), {0, 1}, Cp[p], ctx->sH_hi[p],
-                        ctx->sH_lo[p]));
-        ctx->sH_n[p] = n[p];
-      }
-      HS_TRY(tc_split(ctx, prec, dense2(k[p], n[p]), dense2(k[p], n[p]), {0, 1}, PT + ptoff[p], ctx->sx_hi,
-                      ctx->sx_lo));
-      HS_TRY(tc_run(ctx, prec, dense2(k[p], n[p]), ctx->sx_hi, ctx->sx_lo, dense2(n[p], n[p]), ctx->sH_hi[p],
-                    ctx->sH_lo[p], dense2(k[p], n[p]), W + ptoff[p]));
-      HS_TRY(tc_split(ctx, prec, dense2(k[p], n[p]), dense2(k[p], n[p]), {0, 1}, W + ptoff[p], ctx->sy_hi,
-                      ctx->sy_lo));
-      HS_TRY(tc_run(ctx, prec, dense2(k[p], n[p]), ctx->sy_hi, ctx->sy_lo, dense2(k[p], n[p]), ctx->sx_hi,
-                    ctx->sx_lo, dense2(k[p], k[p]), env->C + goff[p]));
       const double f = 2.0 * k[p] * (double)n[p] * n[p] + 2.0 * k[p] * (double)k[p] * n[p];
       *flops += f;
       ctx->phase_flops[HS_PHASE_GEMM_TC] += f;
@@ -544,14 +538,14 @@ hs_status cheb_filter_block(hs_ctx ctx, hs_precision prec, int b, int m, int n, 
   for (auto* buf : {&ctx->sf_y[0], &ctx->sf_y[1], &ctx->sf_y[2], &ctx->sf_z, &ctx->sf_t, &ctx->sf_q, &ctx->sf_qt})
     HS_TRY(buf->ensure(mn));
   HS_TRY(ctx->sf_s.ensure((size_t)m * m * sizeof(double)));
-  const double* Xr = ctx->sxr[b].d();
-  const double* Zr = ctx->szr[b].d();
+  const double* Xr = ctx->sxr.d(b);
+  const double* Zr = ctx->szr.d(b);
+  const DBuf hhi = tc ? sH_block(ctx, prec, true, b) : DBuf{}, hlo = tc ? sH_block(ctx, prec, false, b) : DBuf{};
   // product of mr rows of Y (m x n) with H into Z
   auto hprod = [&](const double* Y, int mr, double* Z) -> hs_status {
     if (tc) {
       HS_TRY(tc_split(ctx, prec, dense2(mr, n), dense2(mr, n), {0, 1}, Y, ctx->sx_hi, ctx->sx_lo));
-      HS_TRY(tc_run(ctx, prec, dense2(mr, n), ctx->sx_hi, ctx->sx_lo, dense2(n, n), ctx->sH_hi[b], ctx->sH_lo[b],
-                    dense2(mr, n), Z));
+      HS_TRY(tc_run(ctx, prec, dense2(mr, n), ctx->sx_hi, ctx->sx_lo, dense2(n, n), hhi, hlo, dense2(mr, n), Z));
       ctx->phase_flops[HS_PHASE_GEMM_TC] += 2.0 * mr * (double)n * n;
     } else {
       HS_TRY(gemm(ctx, HS_GEMM_OWN, GemmGroup{1, {GemmProblem{mr, n, n, n, n, n, 0, 0, 0}}}, Y, H, Z));
@@ -609,6 +603,63 @@ hs_status cheb_filter_block(hs_ctx ctx, hs_precision prec, int b, int m, int n, 
   return HS_OK;
 }
 
+// A block-diagonal pair as one Z2 layout: block p is r_p x c_p (stacked).
+Z2Mat zd(long long r0, long long r1, long long c0, long long c1, int pad) {
+  return mat(fused1(make_sect((int)r0, (int)r1)), fused1(make_sect((int)c0, (int)c1)), pad);
+}
+
+// A view of part of a buffer (never grown or freed through the view).
+DBuf view(const DBuf& b, long long byte_off) {
+  DBuf v;
+  v.p = static_cast<char*>(b.p) + byte_off;
+  v.bytes = 0;
+  return v;
+}
+
+// The split C' block b (dense n_b x n_b) inside the stacked split sH_hi/lo.
+DBuf sH_block(hs_ctx ctx, hs_precision prec, bool hi, int b) {
+  const Z2Mat P = zd(ctx->sH_n[0], ctx->sH_n[1], ctx->sH_n[0], ctx->sH_n[1], tc_pad(prec));
+  return view(hi ? ctx->sH_hi : ctx->sH_lo, z2_block_off(P, b) * tc_elem_bytes(prec));
+}
+
+// Both C' blocks (stacked: block 1 right after block 0) split once per move.
+hs_status split_corner(hs_ctx ctx, hs_precision prec, const double* H0, int n0, int n1) {
+  HS_TRY(tc_split(ctx, prec, zd(n0, n1, n0, n1), zd(n0, n1, n0, n1), {0, 1}, H0, ctx->sH_hi, ctx->sH_lo));
+  ctx->sH_n[0] = n0;
+  ctx->sH_n[1] = n1;
+  ctx->sH_fresh = true;
+  return HS_OK;
+}
+
+// `steps` Loewdin steps X <- (3/2 I - 1/2 X X^T) X on the rows of both blocks
+// of a stacked pair (m_b rows of n_b), each product one tensor-core launch
+// for both blocks; with FP64 products block by block.
+hs_status lowdin_rows_pair(hs_ctx ctx, hs_precision prec, double* X, const int m[2], const int n[2], double* Xc,
+                           int steps) {
+  if (prec == HS_PREC_F64) {
+    for (int b = 0; b < 2; ++b)
+      if (m[b] > 0 && n[b] > 0)
+        HS_TRY(lowdin_rows(ctx, prec, X + (b ? (long long)m[0] * n[0] : 0), m[b], n[b], Xc, steps));
+    return HS_OK;
+  }
+  const Z2Mat XL = zd(m[0], m[1], n[0], n[1]), GL = zd(m[0], m[1], m[0], m[1]), XT = zd(n[0], n[1], m[0], m[1]);
+  HS_TRY(ctx->schol.ensure(((size_t)m[0] * m[0] + (size_t)m[1] * m[1] + 1) * sizeof(double)));
+  double* G = ctx->schol.d();
+  for (int st = 0; st < steps; ++st) {
+    // G = X X^T (the split X serves as both operands)
+    HS_TRY(tc_split(ctx, prec, XL, XL, {0, 1}, X, ctx->sx_hi, ctx->sx_lo));
+    HS_TRY(tc_run(ctx, prec, XL, ctx->sx_hi, ctx->sx_lo, XL, ctx->sx_hi, ctx->sx_lo, GL, G));
+    HS_CUDA(launch_lowdin(G, m[0], m[1], ctx->stream));
+    // X <- G X: G split as A, X^T written straight into the split B operand
+    HS_TRY(tc_split(ctx, prec, GL, GL, {0, 1}, G, ctx->sy_hi, ctx->sy_lo));
+    HS_TRY(tc_split(ctx, prec, XL, XT, {1, 0}, X, ctx->sx_hi, ctx->sx_lo));
+    HS_TRY(tc_run(ctx, prec, GL, ctx->sy_hi, ctx->sy_lo, XT, ctx->sx_hi, ctx->sx_lo, XL, X));
+    ctx->launches += 1;
+    for (int b = 0; b < 2; ++b) ctx->phase_flops[HS_PHASE_GEMM_TC] += 4.0 * m[b] * (double)m[b] * n[b];
+  }
+  return HS_OK;
+}
+
 // Subspace iteration on both parity blocks H_b (n_b x n_b, FP64 in place in
 // the C' buffer), warm-started from the previous move's kept rows. On success
 // (*done) w[0 .. m0+m1) holds the Ritz values of block 0 then block 1
@@ -641,40 +692,46 @@ hs_status subspace_projector(hs_ctx ctx, hs_env* env, int chi, int n0, int n1, d
   int* bad = static_cast<int*>(ctx->info.p) + 2;
   HS_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), s));
   HS_TRY(eig32_workspace(ctx, m[0] > m[1] ? m[0] : m[1]));
+  // stacked buffers: block 1 after block 0
+  const long long mn0 = (long long)m[0] * n[0], mn1 = (long long)m[1] * n[1];
+  for (Stacked* t : {&ctx->sx, &ctx->sz, &ctx->sxc, &ctx->szc, &ctx->sxr, &ctx->szr})
+    HS_TRY(t->ensure(mn0, mn1, sizeof(double)));
+  HS_TRY(ctx->sbm.ensure((long long)m[0] * m[0], (long long)m[1] * m[1], sizeof(double)));
+  HS_TRY(ctx->sbw.ensure((long long)m[0] * m[0], (long long)m[1] * m[1], sizeof(float)));
+  HS_TRY(ctx->sres.ensure(m[0], m[1], sizeof(double)));
+  const Z2Mat XL = zd(m[0], m[1], n[0], n[1]), XT = zd(n[0], n[1], m[0], m[1]), BL = zd(m[0], m[1], m[0], m[1]),
+              HL = zd(n[0], n[1], n[0], n[1]);
+  // warm start: the previous move's rows (same stacking when the subspace
+  // sizes are unchanged), random rows where the subspace grew
   const long long wsoff[2] = {0, (long long)ctx->ws_m[0] * ctx->ws_n[0]};
-  for (int b = 0; b < 2; ++b) {
-    if (m[b] == 0) continue;
-    const size_t mn = (size_t)m[b] * n[b] * sizeof(double);
-    HS_TRY(ctx->sx[b].ensure(mn));
-    HS_TRY(ctx->sz[b].ensure(mn));
-    HS_TRY(ctx->sxc[b].ensure(mn));
-    HS_TRY(ctx->szc[b].ensure(mn));
-    HS_TRY(ctx->sxr[b].ensure(mn));
-    HS_TRY(ctx->szr[b].ensure(mn));
-    HS_TRY(ctx->sbm[b].ensure((size_t)m[b] * m[b] * sizeof(double)));
-    HS_TRY(ctx->sbw[b].ensure((size_t)m[b] * m[b] * sizeof(float)));
-    HS_TRY(ctx->sres[b].ensure((size_t)m[b] * sizeof(double)));
-    const int kb = ctx->ws_m[b] < m[b] ? ctx->ws_m[b] : m[b];
-    if (kb > 0)
-      HS_CUDA(cudaMemcpyAsync(ctx->sx[b].p, ctx->ws_pt.d() + wsoff[b], (size_t)kb * n[b] * sizeof(double),
-                              cudaMemcpyDeviceToDevice, s));
-    HS_CUDA(launch_fill_random_rows(ctx->sx[b].d(), kb, m[b], n[b], 0x5eed0000ull + 2 * (unsigned long long)ctx->ws_moves + b,
-                                    s));
-    if (kb == m[b]) {
-      // the previous move's Ritz / eigen-vectors: orthonormal up to FP32 rounding
-      HS_TRY(lowdin_rows(ctx, prec, ctx->sx[b].d(), m[b], n[b], ctx->sxc[b].d(), tc ? 1 : 2));
-    } else {
-      double* const Xo[2] = {ctx->sx[b].d(), nullptr};
-      double* const Xco[2] = {ctx->sxc[b].d(), nullptr};
-      const int mo[2] = {m[b], 0}, no[2] = {n[b], 0};
-      HS_TRY(orthonormalise_rows(ctx, prec, Xo, mo, no, Xco, bad));
-    }
-    if (tc) {
-      HS_TRY(tc_split(ctx, prec, dense2(n[b], n[b]), dense2(n[b], n[b]), {0, 1}, H[b], ctx->sH_hi[b], ctx->sH_lo[b]));
-      ctx->sH_n[b] = n[b];
+  const int kb[2] = {std::min(ctx->ws_m[0], m[0]), std::min(ctx->ws_m[1], m[1])};
+  bool all_warm = true;
+  if (kb[0] == m[0] && kb[1] == m[1] && ctx->ws_m[0] == m[0]) {
+    HS_CUDA(cudaMemcpyAsync(ctx->sx.d(0), ctx->ws_pt.d(), (size_t)(mn0 + mn1) * sizeof(double),
+                            cudaMemcpyDeviceToDevice, s));
+  } else {
+    for (int b = 0; b < 2; ++b) {
+      if (m[b] == 0) continue;
+      if (kb[b] > 0)
+        HS_CUDA(cudaMemcpyAsync(ctx->sx.d(b), ctx->ws_pt.d() + wsoff[b], (size_t)kb[b] * n[b] * sizeof(double),
+                                cudaMemcpyDeviceToDevice, s));
+      HS_CUDA(launch_fill_random_rows(ctx->sx.d(b), kb[b], m[b], n[b],
+                                      0x5eed0000ull + 2 * (unsigned long long)ctx->ws_moves + b, s));
+      if (kb[b] < m[b]) all_warm = false;
     }
   }
-  if (tc) ctx->sH_fresh = true;
+  if (all_warm) {
+    // the previous move's Ritz / eigen-vectors: orthonormal up to FP32 rounding
+    HS_TRY(lowdin_rows_pair(ctx, prec, ctx->sx.d(0), m, n, ctx->sxc.d(0), tc ? 1 : 2));
+  } else {
+    double* const Xo[2] = {ctx->sx.d(0), ctx->sx.d(1)};
+    double* const Xco[2] = {ctx->sxc.d(0), ctx->sxc.d(1)};
+    HS_TRY(orthonormalise_rows(ctx, prec, Xo, m, n, Xco, bad));
+  }
+  if (tc) {
+    if (H1 != H0 + (long long)n0 * n0) return fail(HS_ERR_INVALID_ARG, "corner blocks not stacked");
+    HS_TRY(split_corner(ctx, prec, H0, n0, n1));
+  }
   HS_TRY(ctx->sth.ensure((size_t)(m[0] + m[1] + 2) * sizeof(float)));
   float* th = static_cast<float*>(ctx->sth.p);
   // pinned read-back of the Ritz values, residuals and status words (a copy
@@ -687,69 +744,63 @@ hs_status subspace_projector(hs_ctx ctx, hs_env* env, int chi, int n0, int n1, d
   double prev_worst = INFINITY;
   for (int it = 0; it < kMaxIt; ++it) {
     *iters = it + 1;
-    for (int b = 0; b < 2; ++b) {
-      if (m[b] == 0) continue;
-      // Z = X H (H symmetric), Rayleigh matrix B = X Z^T (symmetric; the
-      // tensor-core path reuses the split X as the A operand of both)
-      if (tc) {
-        HS_TRY(tc_split(ctx, prec, dense2(m[b], n[b]), dense2(m[b], n[b]), {0, 1}, ctx->sx[b].d(), ctx->sx_hi, ctx->sx_lo));
-        HS_TRY(tc_run(ctx, prec, dense2(m[b], n[b]), ctx->sx_hi, ctx->sx_lo, dense2(n[b], n[b]), ctx->sH_hi[b],
-                      ctx->sH_lo[b], dense2(m[b], n[b]), ctx->sz[b].d()));
-        HS_TRY(tc_split(ctx, prec, dense2(m[b], n[b]), dense2(m[b], n[b]), {0, 1}, ctx->sz[b].d(), ctx->sy_hi, ctx->sy_lo));
-        HS_TRY(tc_run(ctx, prec, dense2(m[b], n[b]), ctx->sx_hi, ctx->sx_lo, dense2(m[b], n[b]), ctx->sy_hi,
-                      ctx->sy_lo, dense2(m[b], m[b]), ctx->sbm[b].d()));
+    // Z = X H (H symmetric), Rayleigh matrix B = X Z^T (symmetric); with
+    // tensor cores each product is one launch for both blocks and the split
+    // X serves as the A operand of both
+    if (tc) {
+      HS_TRY(tc_split(ctx, prec, XL, XL, {0, 1}, ctx->sx.d(0), ctx->sx_hi, ctx->sx_lo));
+      HS_TRY(tc_run(ctx, prec, XL, ctx->sx_hi, ctx->sx_lo, HL, ctx->sH_hi, ctx->sH_lo, XL, ctx->sz.d(0)));
+      HS_TRY(tc_split(ctx, prec, XL, XL, {0, 1}, ctx->sz.d(0), ctx->sy_hi, ctx->sy_lo));
+      HS_TRY(tc_run(ctx, prec, XL, ctx->sx_hi, ctx->sx_lo, XL, ctx->sy_hi, ctx->sy_lo, BL, ctx->sbm.d(0)));
+      for (int b = 0; b < 2; ++b)
         ctx->phase_flops[HS_PHASE_GEMM_TC] += 2.0 * m[b] * (double)n[b] * n[b] + 2.0 * m[b] * (double)m[b] * n[b];
-      } else {
+    } else {
+      for (int b = 0; b < 2; ++b) {
+        if (m[b] == 0) continue;
         HS_TRY(gemm(ctx, HS_GEMM_OWN, GemmGroup{1, {GemmProblem{m[b], n[b], n[b], n[b], n[b], n[b], 0, 0, 0}}},
-                    ctx->sx[b].d(), H[b], ctx->sz[b].d()));
+                    ctx->sx.d(b), H[b], ctx->sz.d(b)));
         HS_TRY(gemm(ctx, HS_GEMM_OWN, GemmGroup{1, {GemmProblem{m[b], m[b], n[b], n[b], n[b], m[b], 0, 0, 0}}},
-                    ctx->sx[b].d(), ctx->sz[b].d(), ctx->sbm[b].d()));
+                    ctx->sx.d(b), ctx->sz.d(b), ctx->sbm.d(b)));
         ctx->phase_flops[HS_PHASE_GEMM] += 2.0 * m[b] * (double)n[b] * n[b] + 2.0 * m[b] * (double)m[b] * n[b];
       }
-      *flops += 2.0 * m[b] * (double)n[b] * n[b];
-      HS_CUDA(launch_cast_f64_f32(ctx->sbm[b].d(), static_cast<float*>(ctx->sbw[b].p), (long long)m[b] * m[b], s));
-      ctx->launches += 1;
     }
+    for (int b = 0; b < 2; ++b) *flops += 2.0 * m[b] * (double)n[b] * n[b];
+    HS_CUDA(launch_cast_f64_f32(ctx->sbm.d(0), ctx->sbw.as<float>(0),
+                                (long long)m[0] * m[0] + (long long)m[1] * m[1], s));
+    ctx->launches += 1;
     {
       // Rayleigh-Ritz: both m x m FP32 problems by one-CTA Jacobi kernels
       PhaseScope ps(ctx, HS_PHASE_EIG);
       HS_CUDA(cudaMemsetAsync(ctx->info.p, 0, 2 * sizeof(int), s));
-      HS_CUDA(launch_jacobi_eig_pair(static_cast<float*>(ctx->sbw[0].p), m[0], th, static_cast<float*>(ctx->sbw[1].p),
-                                     m[1], th + m[0], static_cast<int*>(ctx->info.p), s));
+      HS_CUDA(launch_jacobi_eig_pair(ctx->sbw.as<float>(0), m[0], th, ctx->sbw.as<float>(1), m[1], th + m[0],
+                                     static_cast<int*>(ctx->info.p), s));
       ctx->launches += 1;
     }
-    for (int b = 0; b < 2; ++b) {
-      if (m[b] == 0) continue;
-      // Ritz vectors Xr = W^T X and Zr = W^T Z (W column-major = W^T row-major)
-      HS_CUDA(launch_cast_f32_f64(static_cast<float*>(ctx->sbw[b].p), ctx->sbm[b].d(), (long long)m[b] * m[b], s));
-      ctx->launches += 1;
-      if (tc) {
-        // W split once; X^T and Z^T written straight into the split B operand
-        HS_TRY(tc_split(ctx, prec, dense2(m[b], m[b]), dense2(m[b], m[b]), {0, 1}, ctx->sbm[b].d(), ctx->sx_hi,
-                        ctx->sx_lo));
-        HS_TRY(tc_split(ctx, prec, dense2(m[b], n[b]), dense2(n[b], m[b]), {1, 0}, ctx->sx[b].d(), ctx->sy_hi,
-                        ctx->sy_lo));
-        HS_TRY(tc_run(ctx, prec, dense2(m[b], m[b]), ctx->sx_hi, ctx->sx_lo, dense2(n[b], m[b]), ctx->sy_hi,
-                      ctx->sy_lo, dense2(m[b], n[b]), ctx->sxr[b].d()));
-        HS_TRY(tc_split(ctx, prec, dense2(m[b], n[b]), dense2(n[b], m[b]), {1, 0}, ctx->sz[b].d(), ctx->sy_hi,
-                        ctx->sy_lo));
-        HS_TRY(tc_run(ctx, prec, dense2(m[b], m[b]), ctx->sx_hi, ctx->sx_lo, dense2(n[b], m[b]), ctx->sy_hi,
-                      ctx->sy_lo, dense2(m[b], n[b]), ctx->szr[b].d()));
-        ctx->phase_flops[HS_PHASE_GEMM_TC] += 4.0 * m[b] * (double)m[b] * n[b];
-      } else {
-        HS_TRY(permute(ctx, dense2(m[b], n[b]), dense2(n[b], m[b]), {1, 0}, ctx->sx[b].d(), ctx->sxc[b].d()));
-        HS_TRY(permute(ctx, dense2(m[b], n[b]), dense2(n[b], m[b]), {1, 0}, ctx->sz[b].d(), ctx->szc[b].d()));
-        HS_TRY(dense_gemm_any(ctx, prec, m[b], n[b], m[b], ctx->sbm[b].d(), ctx->sxc[b].d(), ctx->sxr[b].d()));
-        HS_TRY(dense_gemm_any(ctx, prec, m[b], n[b], m[b], ctx->sbm[b].d(), ctx->szc[b].d(), ctx->szr[b].d()));
+    // Ritz vectors Xr = W^T X and Zr = W^T Z (W column-major = W^T row-major)
+    HS_CUDA(launch_cast_f32_f64(ctx->sbw.as<float>(0), ctx->sbm.d(0),
+                                (long long)m[0] * m[0] + (long long)m[1] * m[1], s));
+    ctx->launches += 1;
+    if (tc) {
+      // W split once; X^T and Z^T written straight into the split B operand
+      HS_TRY(tc_split(ctx, prec, BL, BL, {0, 1}, ctx->sbm.d(0), ctx->sx_hi, ctx->sx_lo));
+      HS_TRY(tc_split(ctx, prec, XL, XT, {1, 0}, ctx->sx.d(0), ctx->sy_hi, ctx->sy_lo));
+      HS_TRY(tc_run(ctx, prec, BL, ctx->sx_hi, ctx->sx_lo, XT, ctx->sy_hi, ctx->sy_lo, XL, ctx->sxr.d(0)));
+      HS_TRY(tc_split(ctx, prec, XL, XT, {1, 0}, ctx->sz.d(0), ctx->sy_hi, ctx->sy_lo));
+      HS_TRY(tc_run(ctx, prec, BL, ctx->sx_hi, ctx->sx_lo, XT, ctx->sy_hi, ctx->sy_lo, XL, ctx->szr.d(0)));
+      for (int b = 0; b < 2; ++b) ctx->phase_flops[HS_PHASE_GEMM_TC] += 4.0 * m[b] * (double)m[b] * n[b];
+    } else {
+      for (int b = 0; b < 2; ++b) {
+        if (m[b] == 0) continue;
+        HS_TRY(permute(ctx, dense2(m[b], n[b]), dense2(n[b], m[b]), {1, 0}, ctx->sx.d(b), ctx->sxc.d(b)));
+        HS_TRY(permute(ctx, dense2(m[b], n[b]), dense2(n[b], m[b]), {1, 0}, ctx->sz.d(b), ctx->szc.d(b)));
+        HS_TRY(dense_gemm_any(ctx, prec, m[b], n[b], m[b], ctx->sbm.d(b), ctx->sxc.d(b), ctx->sxr.d(b)));
+        HS_TRY(dense_gemm_any(ctx, prec, m[b], n[b], m[b], ctx->sbm.d(b), ctx->szc.d(b), ctx->szr.d(b)));
       }
-      HS_CUDA(launch_residual(ctx->szr[b].d(), ctx->sxr[b].d(), th + (b ? m[0] : 0), m[b], n[b], ctx->sres[b].d(), s));
-      ctx->launches += 1;
     }
+    HS_CUDA(launch_residual_pair(ctx->szr.d(0), ctx->sxr.d(0), th, m[0], n[0], m[1], n[1], ctx->sres.d(0), s));
+    ctx->launches += 1;
     HS_CUDA(cudaMemcpyAsync(hth, th, (size_t)mt * sizeof(float), cudaMemcpyDeviceToHost, s));
-    for (int b = 0; b < 2; ++b)
-      if (m[b] > 0)
-        HS_CUDA(cudaMemcpyAsync(hres + (b ? m[0] : 0), ctx->sres[b].p, m[b] * sizeof(double),
-                                cudaMemcpyDeviceToHost, s));
+    HS_CUDA(cudaMemcpyAsync(hres, ctx->sres.d(0), (size_t)mt * sizeof(double), cudaMemcpyDeviceToHost, s));
     // info[0], info[1]: Jacobi status; info[2]: Cholesky status (bad)
     HS_CUDA(cudaMemcpyAsync(hstat, ctx->info.p, 3 * sizeof(int), cudaMemcpyDeviceToHost, s));
     HS_CUDA(cudaStreamSynchronize(s));
@@ -799,18 +850,18 @@ hs_status subspace_projector(hs_ctx ctx, hs_env* env, int chi, int n0, int n1, d
         // next basis: a Chebyshev-filtered step where possible, else a plain
         // power step (rows of Zr = theta_i x_i + residual)
         bool filtered = false;
-        HS_TRY(cheb_filter_block(ctx, prec, b, m[b], n[b], H[b], hth + (b ? m[0] : 0), kept[b],
-                                 ctx->sx[b].d(), &filtered));
+        HS_TRY(cheb_filter_block(ctx, prec, b, m[b], n[b], H[b], hth + (b ? m[0] : 0), kept[b], ctx->sx.d(b),
+                                 &filtered));
         if (!filtered)
-          HS_CUDA(cudaMemcpyAsync(ctx->sx[b].p, ctx->szr[b].p, (size_t)m[b] * n[b] * sizeof(double),
+          HS_CUDA(cudaMemcpyAsync(ctx->sx.d(b), ctx->szr.d(b), (size_t)m[b] * n[b] * sizeof(double),
                                   cudaMemcpyDeviceToDevice, s));
-        HS_CUDA(launch_row_normalize(ctx->sx[b].d(), m[b], n[b], s));
+        HS_CUDA(launch_row_normalize(ctx->sx.d(b), m[b], n[b], s));
       }
     {
       // far from convergence the rows can be far from orthogonal (the Loewdin
       // iteration alone diverges there): Cholesky-QR first
-      double* const Xo[2] = {ctx->sx[0].d(), ctx->sx[1].d()};
-      double* const Xco[2] = {ctx->sxc[0].d(), ctx->sxc[1].d()};
+      double* const Xo[2] = {ctx->sx.d(0), ctx->sx.d(1)};
+      double* const Xco[2] = {ctx->sxc.d(0), ctx->sxc.d(1)};
       HS_TRY(orthonormalise_rows(ctx, prec, Xo, m, n, Xco, bad));
     }
   }
@@ -897,11 +948,13 @@ hs_status hs_destroy(hs_ctx ctx) {
   DBuf* more[] = {&ctx->c32,  &ctx->w32,   &ctx->pcol,         &ctx->pt2,   &ctx->gram,
                   &ctx->wproj, &ctx->solver32_dev, &ctx->splitk, &ctx->ws_pt, &ctx->sth,
                   &ctx->sx_hi, &ctx->sx_lo, &ctx->sy_hi, &ctx->sy_lo, &ctx->schol};
-  for (int b = 0; b < 2; ++b) {
-    DBuf* per[] = {&ctx->sx[b], &ctx->sz[b], &ctx->sxc[b], &ctx->szc[b], &ctx->sxr[b], &ctx->szr[b],
-                   &ctx->sbm[b], &ctx->sbw[b], &ctx->sres[b], &ctx->sH_hi[b], &ctx->sH_lo[b]};
-    for (DBuf* x : per) x->release();
-  }
+  for (Stacked* t : {&ctx->sx, &ctx->sz, &ctx->sxc, &ctx->szc, &ctx->sxr, &ctx->szr, &ctx->sbm, &ctx->sbw, &ctx->sres})
+    t->release();
+  ctx->sH_hi.release();
+  ctx->sH_lo.release();
+  for (auto* t : {&ctx->sf_y[0], &ctx->sf_y[1], &ctx->sf_y[2], &ctx->sf_z, &ctx->sf_t, &ctx->sf_s, &ctx->sf_q,
+                  &ctx->sf_qt, &ctx->sf_idx})
+    t->release();
   for (DBuf* b : more) b->release();
   for (cudaEvent_t e : ctx->events) cudaEventDestroy(e);
   if (ctx->h_sel) cudaFreeHost(ctx->h_sel);
@@ -1246,7 +1299,7 @@ hs_status hs_ctmrg_move(hs_ctx ctx, const hs_z2_tensor* a, hs_env* env, int chi,
     HS_TRY(ctx->pcol.ensure(npt * sizeof(double)));
     {
       PhaseScope ps(ctx, HS_PHASE_SELECT);
-      HS_CUDA(launch_gather_rows(ctx->sxr[0].d(), n0, ctx->sxr[1].d(), n1, didx, chi, dsel, ctx->pt.d(),
+      HS_CUDA(launch_gather_rows(ctx->sxr.d(0), n0, ctx->sxr.d(1), n1, didx, chi, dsel, ctx->pt.d(),
                                  ctx->pcol.d(), s));
       ctx->launches += 1;
     }
@@ -1272,17 +1325,17 @@ hs_status hs_ctmrg_move(hs_ctx ctx, const hs_z2_tensor* a, hs_env* env, int chi,
     }
     const long long nws = (long long)mnext[0] * n0 + (long long)mnext[1] * n1;
     HS_TRY(ctx->ws_pt.ensure((nws + 1) * sizeof(double)));
-    HS_TRY(ctx->sres[0].ensure(((size_t)mnext[0] + mnext[1] + 1) * sizeof(double)));
+    HS_TRY(ctx->sf_idx.ensure(((size_t)mnext[0] + mnext[1] + 1) * sizeof(int)));
     double* dst[2] = {ctx->ws_pt.d(), ctx->ws_pt.d() + (long long)mnext[0] * n0};
-    for (int b = 0; b < 2; ++b) {
-      const int nb = b ? n1 : n0;
-      if (mnext[b] == 0) continue;
-      if (sub_done) {
-        HS_CUDA(cudaMemcpyAsync(dst[b], ctx->sxr[b].p, (size_t)mnext[b] * nb * sizeof(double),
-                                cudaMemcpyDeviceToDevice, s));
-      } else if (f32eig) {
+    if (sub_done) {
+      // the Ritz vectors, stacked exactly as the warm start wants them
+      HS_CUDA(cudaMemcpyAsync(dst[0], ctx->sxr.d(0), (size_t)nws * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    } else if (f32eig) {
+      for (int b = 0; b < 2; ++b) {
+        const int nb = b ? n1 : n0;
+        if (mnext[b] == 0) continue;
         const float* wb = static_cast<float*>(ctx->w32.p) + (b ? n0 : 0);
-        HS_CUDA(launch_top_rows(wb, b ? V1f : V0f, nb, mnext[b], static_cast<int*>(ctx->sres[0].p), dst[b], s));
+        HS_CUDA(launch_top_rows(wb, b ? V1f : V0f, nb, mnext[b], static_cast<int*>(ctx->sf_idx.p), dst[b], s));
       }
     }
     ctx->ws_env = env;

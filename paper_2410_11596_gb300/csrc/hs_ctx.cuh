@@ -81,6 +81,24 @@ struct DBuf {
   double* d() const { return static_cast<double*>(p); }
 };
 
+// The two parity blocks of one subspace quantity back to back in one
+// allocation (block 1 starts at off[1] elements).
+struct Stacked {
+  DBuf buf;
+  long long off[2] = {0, 0};
+  hs_status ensure(long long e0, long long e1, size_t esize) {
+    off[0] = 0;
+    off[1] = e0;
+    return buf.ensure((size_t)(e0 + e1 + 2) * esize);
+  }
+  double* d(int b) const { return buf.d() + off[b]; }
+  template <class T>
+  T* as(int b) const {
+    return static_cast<T*>(buf.p) + off[b];
+  }
+  void release() { buf.release(); }
+};
+
 // Pinned host buffer, grown on demand (device-to-host copies into pageable
 // memory block the host until the stream drains).
 struct PinnedBuf {
@@ -156,8 +174,11 @@ struct hs_ctx_s {
   long long ws_moves = 0;
   bool sH_fresh = false;  // sH_hi/lo hold the split blocks of this move's C'
   int sH_n[2] = {0, 0};
-  hs::DBuf ws_pt, sx[2], sz[2], sxc[2], szc[2], sxr[2], szr[2], sbm[2], sbw[2], sres[2], sth, sH_hi[2],
-      sH_lo[2], sx_hi, sx_lo, sy_hi, sy_lo, schol;
+  // per-block subspace quantities stacked (block 1 after block 0), so that
+  // one launch covers both parity blocks; sH_hi/lo hold the split C' blocks in
+  // their padded Z2 layout
+  hs::Stacked sx, sz, sxc, szc, sxr, szr, sbm, sbw, sres;
+  hs::DBuf ws_pt, sth, sH_hi, sH_lo, sx_hi, sx_lo, sy_hi, sy_lo, schol;
   // Chebyshev filter of the subspace eigensolver: three recurrence terms, the
   // product, the projection and its coefficients, the locked rows (and their
   // transpose), and the row order
@@ -212,6 +233,14 @@ hs_status graded_init(hs_ctx ctx, const hs_z2_tensor* a, int chi_max, hs_env* en
 hs_status graded_move(hs_ctx ctx, const hs_z2_tensor* a, hs_env* env, int chi, hs_move_info* info);
 // Loewdin re-orthonormalisation of the m rows of X (n long), `steps` times.
 hs_status lowdin_rows(hs_ctx ctx, hs_precision prec, double* X, int m, int n, double* Xc, int steps);
+// Stacked parity-block pairs (block 1 right after block 0): the pair as one
+// Z2 layout, views into buffers, the split C' blocks, batched Loewdin steps.
+Z2Mat zd(long long r0, long long r1, long long c0, long long c1, int pad = 1);
+DBuf view(const DBuf& b, long long byte_off);
+DBuf sH_block(hs_ctx ctx, hs_precision prec, bool hi, int b);
+hs_status split_corner(hs_ctx ctx, hs_precision prec, const double* H0, int n0, int n1);
+hs_status lowdin_rows_pair(hs_ctx ctx, hs_precision prec, double* X, const int m[2], const int n[2], double* Xc,
+                           int steps);
 
 // Tensor-core precisions: elements per 128-byte row (the K padding unit),
 // bytes per element, split mode of the permute/split kernels.

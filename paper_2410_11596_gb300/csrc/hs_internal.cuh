@@ -318,6 +318,11 @@ cudaError_t launch_chol_inv(const double* G0, int m0, double* Linv0, const doubl
 cudaError_t launch_residual(const double* Zr, const double* Xr, const float* theta, int m, int n, double* res,
                             cudaStream_t s);
 cudaError_t launch_row_sign(double* X, int m, int n, cudaStream_t s);
+// Over a stacked pair: m0 rows of n0 entries, then m1 rows of n1 (theta and
+// res stacked likewise).
+cudaError_t launch_row_sign_pair(double* X, int m0, int n0, int m1, int n1, cudaStream_t s);
+cudaError_t launch_residual_pair(const double* Zr, const double* Xr, const float* theta, int m0, int n0, int m1,
+                                 int n1, double* res, cudaStream_t s);
 cudaError_t launch_gather_rows(const double* X0, int n0, const double* X1, int n1, const int* idx, int chi,
                                const SelectOut* sel, double* PT, double* P, cudaStream_t s);
 int max_subspace();

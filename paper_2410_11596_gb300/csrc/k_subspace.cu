@@ -150,6 +150,83 @@ __global__ void row_sign_kernel(double* __restrict__ X, int m, int n) {
     for (int j = threadIdx.x; j < n; j += blockDim.x) X[(long long)i * n + j] = -X[(long long)i * n + j];
 }
 
+// Row i of a stacked pair (m0 rows of n0 entries, then rows of n1 entries):
+// offset of its first entry and its length.
+__device__ __forceinline__ void pair_row(int i, int m0, int n0, int n1, long long& off, int& n) {
+  if (i < m0) {
+    off = (long long)i * n0;
+    n = n0;
+  } else {
+    off = (long long)m0 * n0 + (long long)(i - m0) * n1;
+    n = n1;
+  }
+}
+
+// row_sign_kernel over both blocks of a stacked pair (one CTA per row). The
+// magnitudes compare as integers (IEEE bits without the sign) and the sign
+// flips as a bit: FP64 compares and negations would take the FP64 pipe.
+__global__ void row_sign_pair_kernel(double* __restrict__ X, int m0, int n0, int n1) {
+  long long off;
+  int n;
+  pair_row(blockIdx.x, m0, n0, n1, off, n);
+  unsigned long long* u = reinterpret_cast<unsigned long long*>(X + off);
+  constexpr unsigned long long kMag = 0x7FFFFFFFFFFFFFFFull;
+  unsigned long long best = 0, val = 0;
+  int bj = 0x7FFFFFFF;
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    const unsigned long long v = u[j], a = v & kMag;
+    if (a > best || (a == best && j < bj)) {
+      best = a;
+      val = v;
+      bj = j;
+    }
+  }
+  __shared__ unsigned long long sb[256], sv[256];
+  __shared__ int sj[256];
+  sb[threadIdx.x] = best;
+  sv[threadIdx.x] = val;
+  sj[threadIdx.x] = bj;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      const unsigned long long b2 = sb[threadIdx.x + o];
+      const int j2 = sj[threadIdx.x + o];
+      if (b2 > sb[threadIdx.x] || (b2 == sb[threadIdx.x] && j2 < sj[threadIdx.x])) {
+        sb[threadIdx.x] = b2;
+        sv[threadIdx.x] = sv[threadIdx.x + o];
+        sj[threadIdx.x] = j2;
+      }
+    }
+    __syncthreads();
+  }
+  if ((sv[0] >> 63) && sb[0] != 0)
+    for (int j = threadIdx.x; j < n; j += blockDim.x) u[j] ^= 0x8000000000000000ull;
+}
+
+// residual_kernel over both blocks of a stacked pair (theta and res stacked).
+__global__ void residual_pair_kernel(const double* __restrict__ Zr, const double* __restrict__ Xr,
+                                     const float* __restrict__ theta, int m0, int n0, int n1,
+                                     double* __restrict__ res) {
+  const int i = blockIdx.x;
+  long long off;
+  int n;
+  pair_row(i, m0, n0, n1, off, n);
+  const double t = (double)theta[i];
+  double s = 0.0;
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    const double v = Zr[off + j] - t * Xr[off + j];
+    s += v * v;
+  }
+  __shared__ double red[256];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) res[i] = sqrt(red[0]);
+}
+
 // PT block b row j = X_b row idx[b][j]; P block b column j likewise.
 __global__ void gather_rows_kernel(const double* __restrict__ X0, int n0, const double* __restrict__ X1, int n1,
                                    const int* __restrict__ idx, int chi, const SelectOut* __restrict__ sel,
@@ -466,6 +543,19 @@ cudaError_t launch_residual(const double* Zr, const double* Xr, const float* the
                             cudaStream_t s) {
   if (m <= 0) return cudaSuccess;
   residual_kernel<<<m, 256, 0, s>>>(Zr, Xr, theta, m, n, res);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_row_sign_pair(double* X, int m0, int n0, int m1, int n1, cudaStream_t s) {
+  if (m0 + m1 <= 0) return cudaSuccess;
+  row_sign_pair_kernel<<<m0 + m1, 256, 0, s>>>(X, m0, n0, n1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_residual_pair(const double* Zr, const double* Xr, const float* theta, int m0, int n0, int m1,
+                                 int n1, double* res, cudaStream_t s) {
+  if (m0 + m1 <= 0) return cudaSuccess;
+  residual_pair_kernel<<<m0 + m1, 256, 0, s>>>(Zr, Xr, theta, m0, n0, n1, res);
   return cudaGetLastError();
 }
 
