@@ -145,8 +145,19 @@ struct Box {
   int fits32;        // every offset of the box and rows * nch below 2^31
   unsigned rows, nch, magc;
   unsigned char sh1c, sh2c;
+  // tiled transpose (fits32 boxes whose input-contiguous dim ji is not the
+  // innermost output dim): kPermTile x kPermTile tiles over (dim ji, the
+  // innermost dim), the other dims a batch (nbd dims, outermost first);
+  // ji < 0: not tiled
+  int ji, nbd;
+  unsigned ntile_i, ntile_o, nbatch, magto, magti;
+  unsigned char sh1to, sh2to, sh1ti, sh2ti;
+  int bdim[kMaxLegs];
+  unsigned bin_stride[kMaxLegs], bout_stride[kMaxLegs], bmag[kMaxLegs];
+  unsigned char bsh1[kMaxLegs], bsh2[kMaxLegs];
 };
 constexpr int kPermVec = 4;
+constexpr int kPermTile = 32;
 
 constexpr int kMaxBoxes = 32;  // even-parity tuples of 6 legs
 

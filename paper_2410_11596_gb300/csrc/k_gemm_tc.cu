@@ -36,6 +36,7 @@
 #include <cudaTypedefs.h>
 
 #include <cstdint>
+#include <algorithm>
 #include <mutex>
 
 #include "hs_bits.cuh"
@@ -482,14 +483,26 @@ bool make_map_cached(CUtensorMap* m, const void* base, int rows, int Kp, int eb)
   return true;
 }
 
-__global__ void tc_splitk_reduce_kernel(const double* __restrict__ part, int nsplit, int M, int N,
-                                        double* __restrict__ C, int ldc) {
-  const long long mn = (long long)M * N;
+// Split-K sums of every split problem of one launch (blockIdx.y = problem),
+// partials added in split order (deterministic).
+struct SplitRed {
+  const double* part;
+  int nsplit, M, N, ldc;
+  double* c;
+};
+struct SplitReds {
+  SplitRed r[kMaxPairs];
+};
+
+__global__ void tc_splitk_reduce_kernel(const SplitReds reds) {
+  const SplitRed& r = reds.r[blockIdx.y];
+  const long long mn = (long long)r.M * r.N;
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < mn;
        e += (long long)gridDim.x * blockDim.x) {
     double v = 0.0;
-    for (int s = 0; s < nsplit; ++s) v += part[s * mn + e];
-    C[(e / N) * ldc + (e % N)] = v;
+    for (int s = 0; s < r.nsplit; ++s) v += r.part[s * mn + e];
+    const long long row = e / r.N;
+    r.c[row * r.ldc + (e - row * r.N)] = v;
   }
 }
 
@@ -520,11 +533,8 @@ cudaError_t run(const TcProblem* probs, int nprob, int* err, cudaStream_t s, dou
   memset(&maps, 0, sizeof maps);
   Group g{};
   int tiles = 0, nmap = 0;
-  struct Red {
-    const double* part;
-    int nsplit, M, N, ldc;
-    double* c;
-  } red[kMaxPairs];  // one reduction per split problem (at most one per operand pair)
+  SplitReds reds{};  // one reduction per split problem (at most one per operand pair)
+  SplitRed* red = reds.r;
   int nred = 0;
   long long part_used = 0;
   for (int i = 0; i < nprob; ++i) {
@@ -591,12 +601,12 @@ cudaError_t run(const TcProblem* probs, int nprob, int* err, cudaStream_t s, dou
                   : nmap <= 2 ? launch_tc<NPASS, EB, 2>(maps, g, grid, tiles, err, s)
                               : launch_tc<NPASS, EB, kMaxPairs>(maps, g, grid, tiles, err, s);
   if (e != cudaSuccess) return e;
-  for (int r = 0; r < nred; ++r) {
-    const long long mn = (long long)red[r].M * red[r].N;
+  if (nred > 0) {
+    long long mn = 0;
+    for (int r = 0; r < nred; ++r) mn = std::max(mn, (long long)red[r].M * red[r].N);
     long long gx = (mn + 255) / 256;
     if (gx > 4096) gx = 4096;
-    tc_splitk_reduce_kernel<<<(unsigned)gx, 256, 0, s>>>(red[r].part, red[r].nsplit, red[r].M, red[r].N, red[r].c,
-                                                        red[r].ldc);
+    tc_splitk_reduce_kernel<<<dim3((unsigned)gx, (unsigned)nred), 256, 0, s>>>(reds);
   }
   return cudaGetLastError();
 }

@@ -49,6 +49,32 @@ void set_chunks(Box& b) {
   b.rows = (unsigned)rows;
   b.nch = (unsigned)(nch > 0 ? nch : 1);
   fast_div_magic(b.nch, &b.magc, &b.sh1c, &b.sh2c);
+  // tiled transpose when the input's contiguous dim is another one and both
+  // extents fill whole tiles (for smaller extents the chunked traversal,
+  // whose loads stay within L2-resident lines, is faster than staging tiles
+  // that are mostly empty)
+  b.ji = -1;
+  b.nbd = 0;
+  const int jo = kMaxLegs - 1;
+  if (!b.fits32 || b.out_stride[jo] != 1 || b.in_stride[jo] == 1 || b.dim[jo] < kPermTile) return;
+  int ji = -1;
+  for (int j = b.lo; j < jo; ++j)
+    if (b.in_stride[j] == 1 && b.dim[j] >= kPermTile) ji = j;
+  if (ji < 0) return;
+  b.ji = ji;
+  b.ntile_i = (unsigned)((b.dim[ji] + kPermTile - 1) / kPermTile);
+  b.ntile_o = (unsigned)((b.dim[jo] + kPermTile - 1) / kPermTile);
+  b.nbatch = (unsigned)(b.count / ((long long)b.dim[ji] * b.dim[jo]));
+  fast_div_magic(b.ntile_o, &b.magto, &b.sh1to, &b.sh2to);
+  fast_div_magic(b.ntile_i, &b.magti, &b.sh1ti, &b.sh2ti);
+  for (int j = b.lo; j < jo; ++j) {
+    if (j == ji) continue;
+    const int k = b.nbd++;
+    b.bdim[k] = b.dim[j];
+    b.bin_stride[k] = (unsigned)b.in_stride[j];
+    b.bout_stride[k] = (unsigned)b.out_stride[j];
+    fast_div_magic((unsigned)b.dim[j], &b.bmag[k], &b.bsh1[k], &b.bsh2[k]);
+  }
 }
 
 }  // namespace
@@ -262,15 +288,58 @@ __device__ __forceinline__ void row_offsets32(const Box& b, unsigned row, unsign
   }
 }
 
-// Threads a box needs: one per chunk (fits32) or per element.
+// Threads a box needs: a CTA of 256 per tile (tiled), one per chunk
+// (fits32) or one per element.
 long long max_work(const PermPlan& plan) {
   long long w = 0;
   for (int i = 0; i < plan.nbox; ++i) {
     const Box& b = plan.box[i];
-    const long long t = b.fits32 ? (long long)b.rows * b.nch : b.count;
+    const long long t = b.ji >= 0   ? 256LL * b.nbatch * b.ntile_i * b.ntile_o
+                        : b.fits32 ? (long long)b.rows * b.nch
+                                   : b.count;
     w = t > w ? t : w;
   }
   return w;
+}
+
+// Tiled transpose of box b: each CTA stages a tile (rows along the innermost
+// output dim, columns along the input's contiguous dim) in shared memory, so
+// both the loads and the stores run along contiguous addresses. `store`
+// writes one value at an output offset.
+template <class Store>
+__device__ __forceinline__ void permute_tiled(const Box& b, const double* __restrict__ in, Store store) {
+  __shared__ double tile[kPermTile][kPermTile + 1];
+  constexpr int jo = kMaxLegs - 1;
+  const unsigned di = (unsigned)b.dim[b.ji], dout = (unsigned)b.dim[jo];
+  const unsigned is_o = (unsigned)b.in_stride[jo], os_i = (unsigned)b.out_stride[b.ji];
+  const unsigned ntiles = b.nbatch * b.ntile_i * b.ntile_o;
+  for (unsigned t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const unsigned t1 = fast_div(t, b.magto, b.sh1to, b.sh2to);
+    const unsigned to = t - t1 * b.ntile_o;
+    unsigned r = fast_div(t1, b.magti, b.sh1ti, b.sh2ti);
+    const unsigned ti = t1 - r * b.ntile_i;
+    unsigned io = (unsigned)b.in_off, oo = (unsigned)b.out_off;
+    for (int k = b.nbd - 1; k >= 0; --k) {
+      const unsigned q = fast_div(r, b.bmag[k], b.bsh1[k], b.bsh2[k]);
+      const unsigned ik = r - q * (unsigned)b.bdim[k];
+      r = q;
+      io += ik * b.bin_stride[k];
+      oo += ik * b.bout_stride[k];
+    }
+    const unsigned i0 = ti * kPermTile, o0 = to * kPermTile;
+    const unsigned ni = di - i0 < (unsigned)kPermTile ? di - i0 : (unsigned)kPermTile;
+    const unsigned no = dout - o0 < (unsigned)kPermTile ? dout - o0 : (unsigned)kPermTile;
+    for (unsigned e = threadIdx.x; e < kPermTile * kPermTile; e += blockDim.x) {
+      const unsigned rr = e / kPermTile, cc = e % kPermTile;  // rr along the output dim, cc along the input's
+      if (rr < no && cc < ni) tile[rr][cc] = in[io + (o0 + rr) * is_o + i0 + cc];
+    }
+    __syncthreads();
+    for (unsigned e = threadIdx.x; e < kPermTile * kPermTile; e += blockDim.x) {
+      const unsigned rr = e / kPermTile, cc = e % kPermTile;  // rr along the input's dim, cc along the output's
+      if (rr < ni && cc < no) store(oo + (i0 + rr) * os_i + o0 + cc, tile[cc][rr]);
+    }
+    __syncthreads();
+  }
 }
 
 // The kernels take the plan's boxes by value in a parameter block sized to
@@ -289,6 +358,10 @@ __global__ void permute_f64_kernel(PlanArg<NB> plan, const double* __restrict__ 
                                    double scale) {
   const Box& b = plan.box[blockIdx.y];
   const bool plain = scale == 1.0;  // plain copies keep off the FP64 pipe
+  if (b.ji >= 0) {
+    permute_tiled(b, in, [&](unsigned o, double v) { out[o] = plain ? v : scale * v; });
+    return;
+  }
   if (b.fits32) {
     const unsigned inner = (unsigned)b.dim[kMaxLegs - 1];
     const unsigned istr = (unsigned)b.in_stride[kMaxLegs - 1], ostr = (unsigned)b.out_stride[kMaxLegs - 1];
@@ -338,6 +411,10 @@ template <int MODE, int NB>
 __global__ void permute_split_kernel(PlanArg<NB> plan, const double* __restrict__ in, void* __restrict__ hi,
                                      void* __restrict__ lo) {
   const Box& b = plan.box[blockIdx.y];
+  if (b.ji >= 0) {
+    permute_tiled(b, in, [&](unsigned o, double v) { store_split<MODE>(v, hi, lo, (long long)o); });
+    return;
+  }
   if (b.fits32) {
     const unsigned inner = (unsigned)b.dim[kMaxLegs - 1];
     const unsigned istr = (unsigned)b.in_stride[kMaxLegs - 1], ostr = (unsigned)b.out_stride[kMaxLegs - 1];
