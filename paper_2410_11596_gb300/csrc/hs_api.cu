@@ -231,8 +231,22 @@ hs_status eig_workspace(hs_ctx ctx, int nmax) { return eig_workspace_impl(ctx, n
 
 // Write the operand `layout` (legs = src legs permuted by perm) of a
 // tensor-core GEMM as split, K-padded hi/lo arrays.
+hs_status tc_split_any(hs_ctx ctx, hs_precision prec, const Z2Mat& src_layout, const Z2Mat& layout,
+                       std::initializer_list<int> perm, const void* src, bool src_f32, DBuf& hi, DBuf& lo);
+
 hs_status tc_split(hs_ctx ctx, hs_precision prec, const Z2Mat& src_layout, const Z2Mat& layout,
                    std::initializer_list<int> perm, const double* src, DBuf& hi, DBuf& lo) {
+  return tc_split_any(ctx, prec, src_layout, layout, perm, src, false, hi, lo);
+}
+
+// As tc_split, from an FP32 source (an FP32 tensor-core GEMM output).
+hs_status tc_split_f32(hs_ctx ctx, hs_precision prec, const Z2Mat& src_layout, const Z2Mat& layout,
+                       std::initializer_list<int> perm, const float* src, DBuf& hi, DBuf& lo) {
+  return tc_split_any(ctx, prec, src_layout, layout, perm, src, true, hi, lo);
+}
+
+hs_status tc_split_any(hs_ctx ctx, hs_precision prec, const Z2Mat& src_layout, const Z2Mat& layout,
+                       std::initializer_list<int> perm, const void* src, bool src_f32, DBuf& hi, DBuf& lo) {
   const int pad = tc_pad(prec), eb = tc_elem_bytes(prec);
   const Z2Mat P = mat(layout.r, layout.c, pad);
   const size_t nb = (size_t)z2_elems(P) * eb;
@@ -254,7 +268,10 @@ hs_status tc_split(hs_ctx ctx, hs_precision prec, const Z2Mat& src_layout, const
     hi.zkey = lo.zkey = key;
   }
   const PermPlan& plan = cached_plan(ctx, src_layout, P, pm);
-  HS_CUDA(launch_permute_split(plan, src, hi.p, lo.p, tc_mode(prec), ctx->stream));
+  if (src_f32)
+    HS_CUDA(launch_permute_split_f32(plan, static_cast<const float*>(src), hi.p, lo.p, tc_mode(prec), ctx->stream));
+  else
+    HS_CUDA(launch_permute_split(plan, static_cast<const double*>(src), hi.p, lo.p, tc_mode(prec), ctx->stream));
   if (plan.nbox > 0) ctx->launches += 1;
   return HS_OK;
 }
@@ -262,8 +279,10 @@ hs_status tc_split(hs_ctx ctx, hs_precision prec, const Z2Mat& src_layout, const
 // C[R|N] = A[R|K] B[N|K]^T on the tensor cores from split operands (logical
 // layouts A, B; buffers padded as written by tc_split), FP64 C in layout Cm.
 hs_status tc_run(hs_ctx ctx, hs_precision prec, const Z2Mat& A, const DBuf& ahi, const DBuf& alo,
-                 const Z2Mat& B, const DBuf& bhi, const DBuf& blo, const Z2Mat& Cm, double* C) {
+                 const Z2Mat& B, const DBuf& bhi, const DBuf& blo, const Z2Mat& Cm, double* C, bool out_f32 = false) {
   const int pad = tc_pad(prec), eb = tc_elem_bytes(prec);
+  const size_t ce = out_f32 ? sizeof(float) : sizeof(double);
+  char* Cb = reinterpret_cast<char*>(C);
   const Z2Mat Ap = mat(A.r, A.c, pad), Bp = mat(B.r, B.c, pad);
   TcProblem pr[2];
   int n = 0;
@@ -274,8 +293,7 @@ hs_status tc_run(hs_ctx ctx, hs_precision prec, const Z2Mat& A, const DBuf& ahi,
     t.Kp = (int)z2_ld(Ap, p);
     if (t.M == 0 || t.N == 0) continue;
     if (z2_cols(Ap, p) == 0) {  // empty contraction: the block is zero
-      HS_CUDA(cudaMemset2DAsync(C + z2_block_off(Cm, p), sizeof(double) * z2_ld(Cm, p), 0,
-                                sizeof(double) * t.N, t.M, ctx->stream));
+      HS_CUDA(cudaMemset2DAsync(Cb + z2_block_off(Cm, p) * ce, ce * z2_ld(Cm, p), 0, ce * t.N, t.M, ctx->stream));
       continue;
     }
     t.ldc = (int)z2_ld(Cm, p);
@@ -283,7 +301,8 @@ hs_status tc_run(hs_ctx ctx, hs_precision prec, const Z2Mat& A, const DBuf& ahi,
     t.a_lo = static_cast<const char*>(alo.p) + z2_block_off(Ap, p) * eb;
     t.b_hi = static_cast<const char*>(bhi.p) + z2_block_off(Bp, p) * eb;
     t.b_lo = static_cast<const char*>(blo.p) + z2_block_off(Bp, p) * eb;
-    t.c = C + z2_block_off(Cm, p);
+    t.c = reinterpret_cast<double*>(Cb + z2_block_off(Cm, p) * ce);
+    t.out_f32 = out_f32 ? 1 : 0;
     ++n;
   }
   HS_TRY(ctx->splitk.ensure(kSplitKElems * sizeof(double)));
@@ -297,9 +316,9 @@ hs_status tc_run(hs_ctx ctx, hs_precision prec, const Z2Mat& A, const DBuf& ahi,
 // and a the split copy of the double layer made by hs_ctmrg_init.
 hs_status tc_a_gemm(hs_ctx ctx, hs_precision prec, const Z2Mat& Xsrc, const Z2Mat& X,
                     std::initializer_list<int> perm, const double* src, const Z2Mat& Am, const Z2Mat& Cm,
-                    double* C) {
-  HS_TRY(tc_split(ctx, prec, Xsrc, X, perm, src, ctx->tc_x_hi, ctx->tc_x_lo));
-  return tc_run(ctx, prec, X, ctx->tc_x_hi, ctx->tc_x_lo, Am, ctx->tc_a_hi, ctx->tc_a_lo, Cm, C);
+                    double* C, bool f32 = false) {
+  HS_TRY(tc_split_any(ctx, prec, Xsrc, X, perm, src, f32, ctx->tc_x_hi, ctx->tc_x_lo));
+  return tc_run(ctx, prec, X, ctx->tc_x_hi, ctx->tc_x_lo, Am, ctx->tc_a_hi, ctx->tc_a_lo, Cm, C, f32);
 }
 
 // A dense r x c matrix as a one-block Z2 layout.
@@ -390,7 +409,9 @@ hs_status finish_projector(hs_ctx ctx, int n0, int n1, SelectOut* dsel, Sect c, 
   } else {
     // both blocks per launch: W = PT C' (C' split once per move), C_new = W PT^T
     if (!ctx->sH_fresh || ctx->sH_n[0] != n[0] || ctx->sH_n[1] != n[1]) {
-      if (Cp[1] != Cp[0] + (long long)n[0] * n[0]) return fail(HS_ERR_INVALID_ARG, "corner blocks not stacked");
+      const size_t es = ctx->cp_f32 ? sizeof(float) : sizeof(double);
+      if (reinterpret_cast<const char*>(Cp[1]) != reinterpret_cast<const char*>(Cp[0]) + (size_t)n[0] * n[0] * es)
+        return fail(HS_ERR_INVALID_ARG, "corner blocks not stacked");
       HS_TRY(split_corner(ctx, prec, Cp[0], n[0], n[1]));
     }
     const Z2Mat PL = zd(k[0], k[1], n[0], n[1]), HL = zd(n[0], n[1], n[0], n[1]), CL = zd(k[0], k[1], k[0], k[1]);
@@ -624,7 +645,8 @@ DBuf sH_block(hs_ctx ctx, hs_precision prec, bool hi, int b) {
 
 // Both C' blocks (stacked: block 1 right after block 0) split once per move.
 hs_status split_corner(hs_ctx ctx, hs_precision prec, const double* H0, int n0, int n1) {
-  HS_TRY(tc_split(ctx, prec, zd(n0, n1, n0, n1), zd(n0, n1, n0, n1), {0, 1}, H0, ctx->sH_hi, ctx->sH_lo));
+  HS_TRY(tc_split_any(ctx, prec, zd(n0, n1, n0, n1), zd(n0, n1, n0, n1), {0, 1}, H0, ctx->cp_f32, ctx->sH_hi,
+                      ctx->sH_lo));
   ctx->sH_n[0] = n0;
   ctx->sH_n[1] = n1;
   ctx->sH_fresh = true;
@@ -729,7 +751,9 @@ hs_status subspace_projector(hs_ctx ctx, hs_env* env, int chi, int n0, int n1, d
     HS_TRY(orthonormalise_rows(ctx, prec, Xo, m, n, Xco, bad));
   }
   if (tc) {
-    if (H1 != H0 + (long long)n0 * n0) return fail(HS_ERR_INVALID_ARG, "corner blocks not stacked");
+    const size_t es = ctx->cp_f32 ? sizeof(float) : sizeof(double);
+    if (reinterpret_cast<const char*>(H1) != reinterpret_cast<const char*>(H0) + (size_t)n0 * n0 * es)
+      return fail(HS_ERR_INVALID_ARG, "corner blocks not stacked");
     HS_TRY(split_corner(ctx, prec, H0, n0, n1));
   }
   HS_TRY(ctx->sth.ensure((size_t)(m[0] + m[1] + 2) * sizeof(float)));
@@ -1173,6 +1197,10 @@ hs_status hs_ctmrg_move(hs_ctx ctx, const hs_z2_tensor* a, hs_env* env, int chi,
   const hs_gemm_backend be = env->gemm_backend;
   const bool tc = env->precision != HS_PREC_F64;
   ctx->sH_fresh = false;
+  // with tensor-core GEMMs the corner chain stays in FP32 (the accumulators'
+  // values, so nothing is lost), except for the FP64 eigensolver
+  ctx->cp_f32 = tc && env->eig_mode != HS_EIG_F64;
+  const bool f32c = ctx->cp_f32;
   if (tc && (ctx->tc_a_src != a->data || ctx->tc_a_prec != (int)env->precision))
     return fail(HS_ERR_INVALID_ARG, "the double layer changed since hs_ctmrg_init (tensor-core copy is stale)");
   const Sect q = make_sect(env->q_even, env->q_odd);
@@ -1205,10 +1233,11 @@ hs_status hs_ctmrg_move(hs_ctx ctx, const hs_z2_tensor* a, hs_env* env, int chi,
     HS_TRY(tc_run(ctx, env->precision, Tcr, ctx->tc_b_hi, ctx->tc_b_lo, Cm, ctx->sy_hi, ctx->sy_lo, X1,
                   ctx->x1.d()));
     HS_TRY(tc_split(ctx, env->precision, X1, X1, {0, 1, 2}, ctx->x1.d(), ctx->tc_x_hi, ctx->tc_x_lo));
-    HS_TRY(tc_run(ctx, env->precision, X1, ctx->tc_x_hi, ctx->tc_x_lo, Tcr, ctx->tc_b_hi, ctx->tc_b_lo, X2, B1));
+    HS_TRY(tc_run(ctx, env->precision, X1, ctx->tc_x_hi, ctx->tc_x_lo, Tcr, ctx->tc_b_hi, ctx->tc_b_lo, X2, B1,
+                  f32c));
   }
   if (tc) {
-    HS_TRY(tc_a_gemm(ctx, env->precision, X2, X2p, {0, 2, 3, 1}, B1, Am, X3, B2));
+    HS_TRY(tc_a_gemm(ctx, env->precision, X2, X2p, {0, 2, 3, 1}, B1, Am, X3, B2, f32c));
     std::swap(B1, B2);  // X3 now in B1, as on the FP64 path
   } else {
     {
@@ -1220,13 +1249,22 @@ hs_status hs_ctmrg_move(hs_ctx ctx, const hs_z2_tensor* a, hs_env* env, int chi,
   }
   {
     PhaseScope ps(ctx, HS_PHASE_PERMUTE);
-    HS_TRY(permute(ctx, X3, Cp, {0, 2, 1, 3}, B1, B2));   // (a,e,d,r) -> (a,d,e,r)
+    if (f32c) {
+      const int pm[kMaxLegs] = {0, 2, 1, 3, 0, 0};
+      HS_CUDA(launch_permute_f32(cached_plan(ctx, X3, Cp, pm), reinterpret_cast<const float*>(B1),
+                                 reinterpret_cast<float*>(B2), s));
+      ctx->launches += 1;
+    } else {
+      HS_TRY(permute(ctx, X3, Cp, {0, 2, 1, 3}, B1, B2));  // (a,e,d,r) -> (a,d,e,r)
+    }
   }
 
-  // one FP64 eigen-decomposition per parity block
+  // one eigen-decomposition per parity block (C' blocks stacked in B2: FP32
+  // values when f32c, else FP64)
   const int n0 = (int)z2_rows(Cp, 0), n1 = (int)z2_rows(Cp, 1);
   double* V0 = B2;
-  double* V1 = B2 + (long long)n0 * n0;
+  double* V1 = f32c ? reinterpret_cast<double*>(reinterpret_cast<float*>(B2) + (long long)n0 * n0)
+                    : B2 + (long long)n0 * n0;
   double* w0 = ctx->w.d();
   double* w1 = w0 + n0;
   HS_CUDA(cudaMemsetAsync(ctx->info.p, 0, 2 * sizeof(int), s));
@@ -1264,7 +1302,10 @@ hs_status hs_ctmrg_move(hs_ctx ctx, const hs_z2_tensor* a, hs_env* env, int chi,
     V1f = V0f + (long long)n0 * n0;
     float* w32 = static_cast<float*>(ctx->w32.p);
     PhaseScope ps(ctx, HS_PHASE_EIG);
-    HS_CUDA(launch_cast_f64_f32(V0, V0f, nn, s));
+    if (f32c)
+      HS_CUDA(cudaMemcpyAsync(V0f, V0, nn * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    else
+      HS_CUDA(launch_cast_f64_f32(V0, V0f, nn, s));
     HS_TRY(eig_pair(ctx, true, V0f, n0, w32, V1f, n1, w32 + n0));
     HS_CUDA(launch_cast_f32_f64(w32, w0, n0 + n1, s));
     ctx->launches += 2;
@@ -1360,10 +1401,12 @@ hs_status hs_ctmrg_move(hs_ctx ctx, const hs_z2_tensor* a, hs_env* env, int chi,
     HS_TRY(gemm(ctx, be, g4, ctx->pp.d(), env->T, B1));
   } else {
     HS_TRY(tc_split(ctx, env->precision, Pp, Pp, {0, 1, 2}, ctx->pp.d(), ctx->tc_x_hi, ctx->tc_x_lo));
-    HS_TRY(tc_run(ctx, env->precision, Pp, ctx->tc_x_hi, ctx->tc_x_lo, Tcr, ctx->tc_b_hi, ctx->tc_b_lo, Y, B1));
+    // Y and Z stay FP32 (the accumulators' values): they only feed splits
+    HS_TRY(tc_run(ctx, env->precision, Pp, ctx->tc_x_hi, ctx->tc_x_lo, Tcr, ctx->tc_b_hi, ctx->tc_b_lo, Y, B1,
+                  true));
   }
   if (tc) {
-    HS_TRY(tc_a_gemm(ctx, env->precision, Y, Yp, {1, 2, 0, 3}, B1, Am, Zm, B2));
+    HS_TRY(tc_a_gemm(ctx, env->precision, Y, Yp, {1, 2, 0, 3}, B1, Am, Zm, B2, true));
     std::swap(B1, B2);  // Z now in B1
   } else {
     {
@@ -1381,7 +1424,8 @@ hs_status hs_ctmrg_move(hs_ctx ctx, const hs_z2_tensor* a, hs_env* env, int chi,
     PhaseScope ps(ctx, HS_PHASE_GEMM);
     HS_TRY(gemm(ctx, be, g6, B2, ctx->pt.d(), env->T));
   } else {
-    HS_TRY(tc_split(ctx, env->precision, Zm, Zp, {0, 3, 1, 2}, B1, ctx->tc_x_hi, ctx->tc_x_lo));
+    HS_TRY(tc_split_f32(ctx, env->precision, Zm, Zp, {0, 3, 1, 2}, reinterpret_cast<const float*>(B1), ctx->tc_x_hi,
+                        ctx->tc_x_lo));
     HS_TRY(tc_split(ctx, env->precision, PT, PT, {0, 1, 2}, ctx->pt.d(), ctx->tc_b_hi, ctx->tc_b_lo));
     HS_TRY(tc_run(ctx, env->precision, Zp, ctx->tc_x_hi, ctx->tc_x_lo, PT, ctx->tc_b_hi, ctx->tc_b_lo, Tn, env->T));
   }

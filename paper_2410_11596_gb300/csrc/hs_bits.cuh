@@ -196,6 +196,46 @@ HS_HD void split_tf32x3(double x, uint32_t& hi, uint32_t& lo) {
   lo = v >= 0x7F800000u ? (sgn | 0x7F800000u) : (sgn | v);
 }
 
+// The splits of an FP32 value v (bit pattern u), equal to split_f64 of
+// (double)v: the remainder v - hi is exact in FP32 (v has 24 significant
+// bits, hi the top 11 or 8), so one FP32 subtraction gives it; hi rounds on
+// the bit pattern (adding half an ulp of the kept bits to the magnitude
+// rounds ties away, the carry moving into the exponent). Values below the
+// single normal range give zeros, as in split_f64.
+HS_HD void split_f32_tf32x3(uint32_t u, uint32_t& hi, uint32_t& lo) {
+  const uint32_t sign = u & 0x80000000u, ex = u & 0x7F800000u;
+  if (ex == 0x7F800000u) {
+    hi = lo = (u & 0x007FFFFFu) ? 0x7FC00000u : u;  // NaN, infinity
+    if (u & 0x007FFFFFu) return;
+    lo = u;
+    return;
+  }
+  if (ex == 0u) {
+    hi = lo = sign;
+    return;
+  }
+  hi = (u + 0x1000u) & 0xFFFFE000u;  // 10 explicit bits, ties away (may carry to infinity)
+  float fv, d;
+  {
+    uint32_t uu = u;
+    std::memcpy(&fv, &uu, 4);
+  }
+  if ((hi & 0x7F800000u) == 0x7F800000u) {
+    // rounded up to 2^128: v - 2^128 = (v - 2^127) - 2^127, both steps exact
+    const float t = sign ? -1.7014118346046923e38f : 1.7014118346046923e38f;
+    d = (fv - t) - t;
+  } else {
+    float fh;
+    uint32_t hh = hi;
+    std::memcpy(&fh, &hh, 4);
+    d = fv - fh;  // exact
+  }
+  uint32_t ld;
+  std::memcpy(&ld, &d, 4);
+  lo = (ld & 0x7F800000u) == 0u ? (ld & 0x80000000u) : ld;  // below the normal range: signed zero
+  if ((ld & 0x7FFFFFFFu) == 0u) lo = 0u;
+}
+
 // The FP64 value of the IEEE single bit pattern f (exact). Subnormal singles
 // are widened by the FP64 conversion (`slow` is called for them).
 HS_HD bool f32_widen_fast(uint32_t f, unsigned long long& out) {

@@ -173,6 +173,9 @@ struct hs_ctx_s {
   int ws_k[2] = {0, 0}, ws_n[2] = {0, 0}, ws_m[2] = {0, 0};  // kept counts, block sizes, stored rows
   long long ws_moves = 0;
   bool sH_fresh = false;  // sH_hi/lo hold the split blocks of this move's C'
+  // this move's enlarged corner C' (and the GEMM outputs before it) are FP32
+  // (the tensor-core accumulators' values) rather than FP64
+  bool cp_f32 = false;
   int sH_n[2] = {0, 0};
   // per-block subspace quantities stacked (block 1 after block 0), so that
   // one launch covers both parity blocks; sH_hi/lo hold the split C' blocks in
@@ -238,6 +241,7 @@ hs_status lowdin_rows(hs_ctx ctx, hs_precision prec, double* X, int m, int n, do
 Z2Mat zd(long long r0, long long r1, long long c0, long long c1, int pad = 1);
 DBuf view(const DBuf& b, long long byte_off);
 DBuf sH_block(hs_ctx ctx, hs_precision prec, bool hi, int b);
+// H0 holds FP32 values when ctx->cp_f32 is set.
 hs_status split_corner(hs_ctx ctx, hs_precision prec, const double* H0, int n0, int n1);
 hs_status lowdin_rows_pair(hs_ctx ctx, hs_precision prec, double* X, const int m[2], const int n[2], double* Xc,
                            int steps);

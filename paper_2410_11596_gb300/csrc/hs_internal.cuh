@@ -150,6 +150,11 @@ struct Box {
   // innermost dim), the other dims a batch (nbd dims, outermost first);
   // ji < 0: not tiled
   int ji, nbd;
+  // plane mode (plane > 0): both extents small, a CTA stages `plane` whole
+  // (dim ji x innermost dim) planes at a time; psz = their product
+  int plane;
+  unsigned psz, magp, magpi, magpo;
+  unsigned char sh1p, sh2p, sh1pi, sh2pi, sh1po, sh2po;
   unsigned ntile_i, ntile_o, nbatch, magto, magti;
   unsigned char sh1to, sh2to, sh1ti, sh2ti;
   int bdim[kMaxLegs];
@@ -158,6 +163,7 @@ struct Box {
 };
 constexpr int kPermVec = 4;
 constexpr int kPermTile = 32;
+constexpr int kPermPlaneElems = 2048;  // staged elements per plane-mode step
 
 constexpr int kMaxBoxes = 32;  // even-parity tuples of 6 legs
 
@@ -232,6 +238,10 @@ cudaError_t launch_permute_f64(const PermPlan& plan, const double* in, double* o
 // Same permutation, writing the operand split for the tensor cores:
 // mode 1: hi = tf32(x), lo = fp32(x - hi) as float; mode 2: bf16 hi/lo pair.
 // The padded columns of `out` must have been zeroed by the caller.
+// FP32 sources (values that came out of the tensor-core GEMMs' FP32 accumulators).
+cudaError_t launch_permute_f32(const PermPlan& plan, const float* in, float* out, cudaStream_t s);
+cudaError_t launch_permute_split_f32(const PermPlan& plan, const float* in, void* hi, void* lo, int mode,
+                                     cudaStream_t s);
 cudaError_t launch_permute_split(const PermPlan& plan, const double* in, void* hi, void* lo, int mode,
                                  cudaStream_t s);
 
@@ -250,7 +260,8 @@ struct TcProblem {
   const void* a_lo;
   const void* b_hi;
   const void* b_lo;
-  double* c;
+  double* c;        // FP64 output, or FP32 (c read as float*, ldc in floats) when out_f32
+  int out_f32 = 0;  // the accumulators are FP32, so an FP32 output loses nothing (one split-K sum rounds once)
 };
 
 // Up to four problems per launch. precision: HS_PREC_TF32X3, HS_PREC_TF32 or HS_PREC_BF16X3. err receives a

@@ -68,6 +68,7 @@ constexpr int kMaxUnits = 16;
 struct Prob {
   int M, N, Kp, ldc;
   int k0, map;
+  int f32;  // output FP32 (c read as float*)
   double* c;
   int tile_start, tiles_n;
 };
@@ -356,14 +357,55 @@ __global__ void __launch_bounds__(NT, 1) gemm_tc_kernel(const __grid_constant__ 
       fence_after();
       const uint32_t d = tmem + (uint32_t)buf * K::ACC_COLS + lane_base;
       const int row0 = r.m0 + q * 32;
-      // 16-byte stores when every row start is 16-byte aligned
-      const bool vec = (P.ldc % 2 == 0) && ((reinterpret_cast<uintptr_t>(P.c) & 15) == 0);
+      // 16-byte stores (FP64) / 8-byte stores (FP32) when every row start is aligned
+      const bool vec = P.f32 ? (P.ldc % 2 == 0) && ((reinterpret_cast<uintptr_t>(P.c) & 7) == 0)
+                             : (P.ldc % 2 == 0) && ((reinterpret_cast<uintptr_t>(P.c) & 15) == 0);
       for (int c = 64 * half; c < 64 * half + 64 && r.n0 + c < P.N; c += 32) {
         uint32_t r0[32], r1[32];
         if (ktiles > 0) {
           tmem_ld32(d + c, r0);
           if (NPASS == 3) tmem_ld32(d + BN + c, r1);
           tmem_wait_ld();
+        }
+        if (P.f32) {
+          // FP32 output: the accumulator sums as they are, staged as above
+          float* stf = reinterpret_cast<float*>(stg);
+#pragma unroll
+          for (int h = 0; h < 4; ++h) {
+#pragma unroll
+            for (int j = 0; j < 8; j += 2) {
+              float v[2];
+#pragma unroll
+              for (int u = 0; u < 2; ++u) {
+                float f = 0.f;
+                if (ktiles > 0) {
+                  f = __uint_as_float(r0[8 * h + j + u]);
+                  if (NPASS == 3) f += __uint_as_float(r1[8 * h + j + u]);
+                }
+                v[u] = f;
+              }
+              *reinterpret_cast<float2*>(&stf[lane * 2 * K::STG_LD + j]) = make_float2(v[0], v[1]);
+            }
+            __syncwarp();
+            const int col = r.n0 + c + 8 * h + 2 * (lane & 3);
+#pragma unroll
+            for (int i0 = 0; i0 < 32; i0 += 8) {
+              const int i = i0 + (lane >> 2);
+              const int row = row0 + i;
+              if (row < P.M && col < P.N) {
+                const float2 x = *reinterpret_cast<const float2*>(&stf[i * 2 * K::STG_LD + 2 * (lane & 3)]);
+                float* dst = reinterpret_cast<float*>(P.c) + (long long)row * P.ldc + col;
+                if (vec && col + 1 < P.N) {
+                  *reinterpret_cast<float2*>(dst) = x;
+                } else {
+                  dst[0] = x.x;
+                  if (col + 1 < P.N) dst[1] = x.y;
+                }
+              }
+            }
+            __syncwarp();
+          }
+          continue;
         }
 #pragma unroll
         for (int h = 0; h < 4; ++h) {
@@ -489,6 +531,7 @@ struct SplitRed {
   const double* part;
   int nsplit, M, N, ldc;
   double* c;
+  int f32;  // write FP32 (c read as float*)
 };
 struct SplitReds {
   SplitRed r[kMaxPairs];
@@ -502,7 +545,10 @@ __global__ void tc_splitk_reduce_kernel(const SplitReds reds) {
     double v = 0.0;
     for (int s = 0; s < r.nsplit; ++s) v += r.part[s * mn + e];
     const long long row = e / r.N;
-    r.c[row * r.ldc + (e - row * r.N)] = v;
+    if (r.f32)
+      reinterpret_cast<float*>(r.c)[row * r.ldc + (e - row * r.N)] = (float)v;
+    else
+      r.c[row * r.ldc + (e - row * r.N)] = v;
   }
 }
 
@@ -578,6 +624,7 @@ cudaError_t run(const TcProblem* probs, int nprob, int* err, cudaStream_t s, dou
       } else {
         q.c = p.c;
         q.ldc = p.ldc;
+        q.f32 = p.out_f32;
       }
       q.tiles_n = tiles_n;
       q.tile_start = tiles;
@@ -585,7 +632,7 @@ cudaError_t run(const TcProblem* probs, int nprob, int* err, cudaStream_t s, dou
     }
     if (ns > 1) {
       if (nred >= kMaxPairs) return cudaErrorInvalidValue;
-      red[nred++] = {part + part_used, ns, p.M, p.N, p.ldc, p.c};
+      red[nred++] = {part + part_used, ns, p.M, p.N, p.ldc, p.c, p.out_f32};
       part_used += (long long)ns * p.M * p.N;
     }
   }

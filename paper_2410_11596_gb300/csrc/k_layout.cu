@@ -1,5 +1,6 @@
 // Host-side planning of FSO permutations and block GEMMs (Z2 bookkeeping,
 // arXiv 2410.11596 Sec. II.B), plus the generic permute kernel.
+#include <algorithm>
 #include <cstdint>
 #include <type_traits>
 
@@ -55,13 +56,27 @@ void set_chunks(Box& b) {
   // that are mostly empty)
   b.ji = -1;
   b.nbd = 0;
+  b.plane = 0;
   const int jo = kMaxLegs - 1;
-  if (!b.fits32 || b.out_stride[jo] != 1 || b.in_stride[jo] == 1 || b.dim[jo] < kPermTile) return;
+  if (!b.fits32 || b.out_stride[jo] != 1 || b.in_stride[jo] == 1 || b.dim[jo] < 2) return;
   int ji = -1;
   for (int j = b.lo; j < jo; ++j)
-    if (b.in_stride[j] == 1 && b.dim[j] >= kPermTile) ji = j;
+    if (b.in_stride[j] == 1 && b.dim[j] >= 2) ji = j;
   if (ji < 0) return;
-  b.ji = ji;
+  const long long psz = (long long)b.dim[ji] * b.dim[jo];
+  if (b.dim[ji] >= kPermTile && b.dim[jo] >= kPermTile) {
+    b.ji = ji;  // tiled
+  } else if (psz <= kPermPlaneElems / 2) {
+    // whole planes, several per step
+    b.ji = ji;
+    b.plane = (int)std::min<long long>(16, kPermPlaneElems / psz);
+    b.psz = (unsigned)psz;
+    fast_div_magic(b.psz, &b.magp, &b.sh1p, &b.sh2p);
+    fast_div_magic((unsigned)b.dim[ji], &b.magpi, &b.sh1pi, &b.sh2pi);
+    fast_div_magic((unsigned)b.dim[jo], &b.magpo, &b.sh1po, &b.sh2po);
+  } else {
+    return;
+  }
   b.ntile_i = (unsigned)((b.dim[ji] + kPermTile - 1) / kPermTile);
   b.ntile_o = (unsigned)((b.dim[jo] + kPermTile - 1) / kPermTile);
   b.nbatch = (unsigned)(b.count / ((long long)b.dim[ji] * b.dim[jo]));
@@ -294,9 +309,10 @@ long long max_work(const PermPlan& plan) {
   long long w = 0;
   for (int i = 0; i < plan.nbox; ++i) {
     const Box& b = plan.box[i];
-    const long long t = b.ji >= 0   ? 256LL * b.nbatch * b.ntile_i * b.ntile_o
-                        : b.fits32 ? (long long)b.rows * b.nch
-                                   : b.count;
+    const long long t = b.plane > 0 ? 256LL * ((b.nbatch + b.plane - 1) / b.plane)
+                        : b.ji >= 0  ? 256LL * b.nbatch * b.ntile_i * b.ntile_o
+                        : b.fits32   ? (long long)b.rows * b.nch
+                                     : b.count;
     w = t > w ? t : w;
   }
   return w;
@@ -306,9 +322,9 @@ long long max_work(const PermPlan& plan) {
 // output dim, columns along the input's contiguous dim) in shared memory, so
 // both the loads and the stores run along contiguous addresses. `store`
 // writes one value at an output offset.
-template <class Store>
-__device__ __forceinline__ void permute_tiled(const Box& b, const double* __restrict__ in, Store store) {
-  __shared__ double tile[kPermTile][kPermTile + 1];
+template <class T, class Store>
+__device__ __forceinline__ void permute_tiled(const Box& b, const T* __restrict__ in, Store store) {
+  __shared__ T tile[kPermTile][kPermTile + 1];
   constexpr int jo = kMaxLegs - 1;
   const unsigned di = (unsigned)b.dim[b.ji], dout = (unsigned)b.dim[jo];
   const unsigned is_o = (unsigned)b.in_stride[jo], os_i = (unsigned)b.out_stride[b.ji];
@@ -342,6 +358,50 @@ __device__ __forceinline__ void permute_tiled(const Box& b, const double* __rest
   }
 }
 
+// Offsets of batch item r of box b (its dims other than ji and the innermost).
+__device__ __forceinline__ void batch_offsets(const Box& b, unsigned r, unsigned& io, unsigned& oo) {
+  io = (unsigned)b.in_off;
+  oo = (unsigned)b.out_off;
+  for (int k = b.nbd - 1; k >= 0; --k) {
+    const unsigned q = fast_div(r, b.bmag[k], b.bsh1[k], b.bsh2[k]);
+    const unsigned ik = r - q * (unsigned)b.bdim[k];
+    r = q;
+    io += ik * b.bin_stride[k];
+    oo += ik * b.bout_stride[k];
+  }
+}
+
+// Plane-mode transpose of box b: a CTA stages b.plane whole (dim ji x
+// innermost dim) planes in shared memory, read in input order and written in
+// output order, both along contiguous runs.
+template <class T, class Store>
+__device__ __forceinline__ void permute_planes(const Box& b, const T* __restrict__ in, Store store) {
+  __shared__ T buf[kPermPlaneElems];
+  __shared__ unsigned s_io[16], s_oo[16];
+  constexpr int jo = kMaxLegs - 1;
+  const unsigned pi = (unsigned)b.dim[b.ji], po = (unsigned)b.dim[jo];
+  const unsigned is_o = (unsigned)b.in_stride[jo], os_i = (unsigned)b.out_stride[b.ji];
+  const unsigned P = (unsigned)b.plane, groups = (b.nbatch + P - 1) / P;
+  for (unsigned g = blockIdx.x; g < groups; g += gridDim.x) {
+    const unsigned b0 = g * P, np = b.nbatch - b0 < P ? b.nbatch - b0 : P;
+    if (threadIdx.x < np) batch_offsets(b, b0 + threadIdx.x, s_io[threadIdx.x], s_oo[threadIdx.x]);
+    __syncthreads();
+    const unsigned tot = np * b.psz;
+    for (unsigned e = threadIdx.x; e < tot; e += blockDim.x) {  // input order: i fastest
+      const unsigned p = fast_div(e, b.magp, b.sh1p, b.sh2p), rem = e - p * b.psz;
+      const unsigned o = fast_div(rem, b.magpi, b.sh1pi, b.sh2pi), i = rem - o * pi;
+      buf[e] = in[s_io[p] + o * is_o + i];
+    }
+    __syncthreads();
+    for (unsigned e = threadIdx.x; e < tot; e += blockDim.x) {  // output order: o fastest
+      const unsigned p = fast_div(e, b.magp, b.sh1p, b.sh2p), rem = e - p * b.psz;
+      const unsigned i = fast_div(rem, b.magpo, b.sh1po, b.sh2po), o = rem - i * po;
+      store(s_oo[p] + i * os_i + o, buf[p * b.psz + o * pi + i]);
+    }
+    __syncthreads();
+  }
+}
+
 // The kernels take the plan's boxes by value in a parameter block sized to
 // the plan (NB boxes of 192 bytes): a full 32-box plan is a 6 KB parameter
 // block, which makes every launch of the common 2- and 8-box plans slower.
@@ -352,14 +412,23 @@ struct PlanArg {
 
 // Each thread moves a chunk of kPermVec consecutive innermost elements (one
 // index decode per chunk, loads issued before the stores); boxes beyond the
-// 32-bit range go element by element.
-template <int NB>
-__global__ void permute_f64_kernel(PlanArg<NB> plan, const double* __restrict__ in, double* __restrict__ out,
-                                   double scale) {
+// 32-bit range go element by element. T: double or float (scale 1 only).
+template <int NB, class T, bool SCALE>
+__global__ void permute_kernel(PlanArg<NB> plan, const T* __restrict__ in, T* __restrict__ out, double scale) {
   const Box& b = plan.box[blockIdx.y];
-  const bool plain = scale == 1.0;  // plain copies keep off the FP64 pipe
+  // plain copies (SCALE false) keep off the FP64 pipe entirely
+  auto put = [&](unsigned long long o, T v) {
+    if (SCALE)
+      out[o] = (T)(scale * v);
+    else
+      out[o] = v;
+  };
+  if (b.plane > 0) {
+    permute_planes(b, in, [&](unsigned o, T v) { put(o, v); });
+    return;
+  }
   if (b.ji >= 0) {
-    permute_tiled(b, in, [&](unsigned o, double v) { out[o] = plain ? v : scale * v; });
+    permute_tiled(b, in, [&](unsigned o, T v) { put(o, v); });
     return;
   }
   if (b.fits32) {
@@ -374,13 +443,13 @@ __global__ void permute_f64_kernel(PlanArg<NB> plan, const double* __restrict__ 
       io += i0 * istr;
       oo += i0 * ostr;
       const unsigned nv = inner - i0 < (unsigned)kPermVec ? inner - i0 : (unsigned)kPermVec;
-      double v[kPermVec];
+      T v[kPermVec];
 #pragma unroll
       for (int k = 0; k < kPermVec; ++k)
         if ((unsigned)k < nv) v[k] = in[io + k * istr];
 #pragma unroll
       for (int k = 0; k < kPermVec; ++k)
-        if ((unsigned)k < nv) out[oo + k * ostr] = plain ? v[k] : scale * v[k];
+        if ((unsigned)k < nv) put(oo + k * ostr, v[k]);
     }
     return;
   }
@@ -388,7 +457,26 @@ __global__ void permute_f64_kernel(PlanArg<NB> plan, const double* __restrict__ 
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < b.count; e += stride) {
     long long io, oo;
     box_offsets(b, e, io, oo);
-    out[oo] = plain ? in[io] : scale * in[io];
+    put((unsigned long long)oo, in[io]);
+  }
+}
+
+// An FP32 value: TF32x3 through one FP32 subtraction (split_f32_tf32x3);
+// BF16x3 through the general split of its exact FP64 value.
+template <int MODE>
+__device__ __forceinline__ void store_split(float x, void* hi, void* lo, long long o) {
+  if (MODE == 1) {
+    uint32_t h, l;
+    split_f32_tf32x3(__float_as_uint(x), h, l);
+    static_cast<uint32_t*>(hi)[o] = h;
+    static_cast<uint32_t*>(lo)[o] = l;
+  } else {
+    uint32_t h, l;
+    unsigned long long w;
+    if (!f32_widen_fast(__float_as_uint(x), w)) w = 0ull;  // subnormal: below the split's range anyway
+    split_f64(f64_from_bits(w), 8, 8, false, h, l);
+    static_cast<unsigned short*>(hi)[o] = (unsigned short)(h >> 16);
+    static_cast<unsigned short*>(lo)[o] = (unsigned short)(l >> 16);
   }
 }
 
@@ -407,12 +495,16 @@ __device__ __forceinline__ void store_split(double x, void* hi, void* lo, long l
   }
 }
 
-template <int MODE, int NB>
-__global__ void permute_split_kernel(PlanArg<NB> plan, const double* __restrict__ in, void* __restrict__ hi,
+template <int MODE, int NB, class T>
+__global__ void permute_split_kernel(PlanArg<NB> plan, const T* __restrict__ in, void* __restrict__ hi,
                                      void* __restrict__ lo) {
   const Box& b = plan.box[blockIdx.y];
+  if (b.plane > 0) {
+    permute_planes(b, in, [&](unsigned o, T v) { store_split<MODE>(v, hi, lo, (long long)o); });
+    return;
+  }
   if (b.ji >= 0) {
-    permute_tiled(b, in, [&](unsigned o, double v) { store_split<MODE>(v, hi, lo, (long long)o); });
+    permute_tiled(b, in, [&](unsigned o, T v) { store_split<MODE>(v, hi, lo, (long long)o); });
     return;
   }
   if (b.fits32) {
@@ -427,7 +519,7 @@ __global__ void permute_split_kernel(PlanArg<NB> plan, const double* __restrict_
       io += i0 * istr;
       oo += i0 * ostr;
       const unsigned nv = inner - i0 < (unsigned)kPermVec ? inner - i0 : (unsigned)kPermVec;
-      double v[kPermVec];
+      T v[kPermVec];
 #pragma unroll
       for (int k = 0; k < kPermVec; ++k)
         if ((unsigned)k < nv) v[k] = in[io + k * istr];
@@ -445,8 +537,8 @@ __global__ void permute_split_kernel(PlanArg<NB> plan, const double* __restrict_
   }
 }
 
-cudaError_t launch_permute_split(const PermPlan& plan, const double* in, void* hi, void* lo, int mode,
-                                 cudaStream_t s) {
+template <class T>
+cudaError_t launch_permute_split_t(const PermPlan& plan, const T* in, void* hi, void* lo, int mode, cudaStream_t s) {
   if (plan.nbox == 0) return cudaSuccess;
   const long long maxc = max_work(plan);
   long long gx = (maxc + 255) / 256;
@@ -457,9 +549,9 @@ cudaError_t launch_permute_split(const PermPlan& plan, const double* in, void* h
     PlanArg<NB> arg;
     for (int i = 0; i < plan.nbox; ++i) arg.box[i] = plan.box[i];
     if (mode == 1)
-      permute_split_kernel<1, NB><<<grid, 256, 0, s>>>(arg, in, hi, lo);
+      permute_split_kernel<1, NB, T><<<grid, 256, 0, s>>>(arg, in, hi, lo);
     else
-      permute_split_kernel<2, NB><<<grid, 256, 0, s>>>(arg, in, hi, lo);
+      permute_split_kernel<2, NB, T><<<grid, 256, 0, s>>>(arg, in, hi, lo);
   };
   if (plan.nbox <= 2)
     go(std::integral_constant<int, 2>{});
@@ -468,6 +560,16 @@ cudaError_t launch_permute_split(const PermPlan& plan, const double* in, void* h
   else
     go(std::integral_constant<int, kMaxBoxes>{});
   return cudaGetLastError();
+}
+
+cudaError_t launch_permute_split(const PermPlan& plan, const double* in, void* hi, void* lo, int mode,
+                                 cudaStream_t s) {
+  return launch_permute_split_t(plan, in, hi, lo, mode, s);
+}
+
+cudaError_t launch_permute_split_f32(const PermPlan& plan, const float* in, void* hi, void* lo, int mode,
+                                     cudaStream_t s) {
+  return launch_permute_split_t(plan, in, hi, lo, mode, s);
 }
 
 template <int MODE>
@@ -495,8 +597,8 @@ cudaError_t launch_split_pad(const double* src, long long rows, int cols, long l
   return cudaGetLastError();
 }
 
-cudaError_t launch_permute_f64(const PermPlan& plan, const double* in, double* out, double scale,
-                               cudaStream_t s) {
+template <class T>
+cudaError_t launch_permute_t(const PermPlan& plan, const T* in, T* out, double scale, cudaStream_t s) {
   if (plan.nbox == 0) return cudaSuccess;
   const long long maxc = max_work(plan);
   long long gx = (maxc + 255) / 256;
@@ -506,7 +608,10 @@ cudaError_t launch_permute_f64(const PermPlan& plan, const double* in, double* o
     constexpr int NB = decltype(nb)::value;
     PlanArg<NB> arg;
     for (int i = 0; i < plan.nbox; ++i) arg.box[i] = plan.box[i];
-    permute_f64_kernel<NB><<<grid, 256, 0, s>>>(arg, in, out, scale);
+    if (scale != 1.0)
+      permute_kernel<NB, T, true><<<grid, 256, 0, s>>>(arg, in, out, scale);
+    else
+      permute_kernel<NB, T, false><<<grid, 256, 0, s>>>(arg, in, out, scale);
   };
   if (plan.nbox <= 2)
     go(std::integral_constant<int, 2>{});
@@ -515,6 +620,15 @@ cudaError_t launch_permute_f64(const PermPlan& plan, const double* in, double* o
   else
     go(std::integral_constant<int, kMaxBoxes>{});
   return cudaGetLastError();
+}
+
+cudaError_t launch_permute_f64(const PermPlan& plan, const double* in, double* out, double scale,
+                               cudaStream_t s) {
+  return launch_permute_t(plan, in, out, scale, s);
+}
+
+cudaError_t launch_permute_f32(const PermPlan& plan, const float* in, float* out, cudaStream_t s) {
+  return launch_permute_t(plan, in, out, 1.0, s);
 }
 
 }  // namespace hs

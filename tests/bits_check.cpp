@@ -113,6 +113,26 @@ int main() {
         return 1;
       }
     }
+  // 2c. the split of an FP32 value through one FP32 subtraction equals the
+  // general split of the same value, at every single exponent
+  std::uniform_int_distribution<uint32_t> u23(0, (1u << 23) - 1);
+  for (uint32_t e = 1; e < 255; ++e)
+    for (int i = 0; i < 4000; ++i) {
+      uint32_t m = u23(rng);
+      if (i % 7 == 1) m = (m & ~0x1FFFu) | 0x1000u;  // exact tie of hi
+      if (i % 7 == 2) m &= ~0x1FFFu;                 // zero remainder
+      if (i % 7 == 3) m = 0x7FFFFFu;                  // carry into the exponent
+      const uint32_t uu = (uint32_t)(i & 1) << 31 | e << 23 | m;
+      float fv;
+      std::memcpy(&fv, &uu, 4);
+      uint32_t h1, l1, h2, l2;
+      split_f64((double)fv, 11, 24, true, h1, l1);
+      split_f32_tf32x3(uu, h2, l2);
+      if (h1 != h2 || l1 != l2) {
+        std::printf("f32 tf32x3 split of %08x: %08x %08x vs %08x %08x\n", uu, h2, l2, h1, l1);
+        return 1;
+      }
+    }
   // zero, tiny, NaN
   uint32_t h, l;
   split_f64(0.0, 11, 24, true, h, l);
