@@ -682,6 +682,141 @@ hs_status lowdin_rows_pair(hs_ctx ctx, hs_precision prec, double* X, const int m
   return HS_OK;
 }
 
+// cheb_filter_block for both parity blocks at once (tensor-core precisions):
+// the locked rows, the filtered rows and every product stacked over the
+// blocks, so that each split, product and projection is one launch for both.
+// Each block has its own interior magnitude a_b and lock; a block without an
+// interior magnitude locks every row (two plain power steps). Writes the
+// new basis into ctx->sx (not normalised).
+hs_status cheb_filter_pair(hs_ctx ctx, hs_precision prec, const int m[2], const int n[2], const float* theta,
+                           const int kept[2]) {
+  constexpr int kDeg = 8;
+  constexpr double kLock = 8.0, kEdge = 0.3;
+  cudaStream_t s = ctx->stream;
+  double a[2] = {0.0, 0.0};
+  int mL[2] = {0, 0}, mU[2] = {0, 0};
+  std::vector<int> idxL[2], idxU[2];
+  for (int b = 0; b < 2; ++b) {
+    if (m[b] == 0) continue;
+    const float* th = theta + (b ? m[0] : 0);
+    std::vector<int> ord(m[b]);
+    for (int i = 0; i < m[b]; ++i) ord[i] = i;
+    std::stable_sort(ord.begin(), ord.end(),
+                     [&](int x, int y) { return std::fabs((double)th[x]) > std::fabs((double)th[y]); });
+    int r = kept[b] + 2 + (int)(kEdge * (m[b] - kept[b] - 2));
+    r = std::max(0, std::min(r, m[b] - 1));
+    a[b] = std::fabs((double)th[ord[r]]);
+    const bool filt = a[b] > 0.0 && r > kept[b];
+    for (int i = 0; i < m[b]; ++i) {
+      if (!filt || std::fabs((double)th[i]) >= kLock * a[b])
+        idxL[b].push_back(i);
+      else
+        idxU[b].push_back(i);
+    }
+    mL[b] = (int)idxL[b].size();
+    mU[b] = (int)idxU[b].size();
+    if (!filt) a[b] = 1.0;  // unused (no filtered rows)
+  }
+  // row orders to the device through pinned staging: locked rows of both
+  // blocks, then unlocked rows of both blocks
+  const int ntot = m[0] + m[1];
+  HS_TRY(ctx->sf_idx.ensure(((size_t)ntot + 4) * sizeof(int)));
+  HS_TRY(ctx->h_idx.ensure(((size_t)ntot + 4) * sizeof(int)));
+  int* hidx = static_cast<int*>(ctx->h_idx.p);
+  int k = 0;
+  for (int b = 0; b < 2; ++b)
+    for (int i : idxL[b]) hidx[k++] = i;
+  for (int b = 0; b < 2; ++b)
+    for (int i : idxU[b]) hidx[k++] = i;
+  int* didx = static_cast<int*>(ctx->sf_idx.p);
+  HS_CUDA(cudaMemcpyAsync(didx, hidx, (size_t)ntot * sizeof(int), cudaMemcpyHostToDevice, s));
+  const int* dL = didx;
+  const int* dU = didx + mL[0] + mL[1];
+  const long long mn = (long long)m[0] * n[0] + (long long)m[1] * n[1];
+  for (auto* buf : {&ctx->sf_y[0], &ctx->sf_y[1], &ctx->sf_y[2], &ctx->sf_z, &ctx->sf_t, &ctx->sf_q, &ctx->sf_xl})
+    HS_TRY(buf->ensure((size_t)(mn + 2) * sizeof(double)));
+  HS_TRY(ctx->sf_s.ensure(((size_t)m[0] * m[0] + (size_t)m[1] * m[1] + 2) * sizeof(double)));
+  const Z2Mat LL = zd(mL[0], mL[1], n[0], n[1]), UL = zd(mU[0], mU[1], n[0], n[1]), HL = zd(n[0], n[1], n[0], n[1]),
+              LT = zd(n[0], n[1], mL[0], mL[1]), SL = zd(mU[0], mU[1], mL[0], mL[1]);
+  const long long xoff1 = (long long)m[0] * n[0];
+  auto hprod = [&](const Z2Mat& RL, const double* Y, double* Z) -> hs_status {
+    HS_TRY(tc_split(ctx, prec, RL, RL, {0, 1}, Y, ctx->sx_hi, ctx->sx_lo));
+    HS_TRY(tc_run(ctx, prec, RL, ctx->sx_hi, ctx->sx_lo, HL, ctx->sH_hi, ctx->sH_lo, RL, Z));
+    for (int b = 0; b < 2; ++b)
+      ctx->phase_flops[HS_PHASE_GEMM_TC] += 2.0 * z2_rows(RL, b) * (double)n[b] * n[b];
+    return HS_OK;
+  };
+  double* XL = ctx->sf_xl.d();
+  // locked rows: two power steps (the first is their rows of Zr)
+  if (mL[0] + mL[1] > 0) {
+    double* Zl = ctx->sf_z.d();
+    HS_CUDA(launch_gather_rows_idx_pair(ctx->szr.d(0), xoff1, n[0], n[1], dL, mL[0], mL[1], Zl,
+                                        (long long)mL[0] * n[0], s));
+    for (int b = 0; b < 2; ++b)
+      HS_CUDA(launch_row_normalize(Zl + (b ? (long long)mL[0] * n[0] : 0), mL[b], n[b], s));
+    HS_TRY(hprod(LL, Zl, XL));
+    ctx->launches += 3;
+  }
+  double* Y[3] = {ctx->sf_y[0].d(), ctx->sf_y[1].d(), ctx->sf_y[2].d()};
+  int cur = 0;
+  if (mU[0] + mU[1] > 0) {
+    double* Q = ctx->sf_q.d();
+    double* Z = ctx->sf_z.d();
+    double* T = ctx->sf_t.d();
+    double* S = ctx->sf_s.d();
+    const bool proj = mL[0] + mL[1] > 0;
+    if (proj) {
+      // the locked span, split once in both orientations (B of S = Z Q^T and of T = S Q)
+      HS_CUDA(launch_gather_rows_idx_pair(ctx->sxr.d(0), xoff1, n[0], n[1], dL, mL[0], mL[1], Q,
+                                          (long long)mL[0] * n[0], s));
+      HS_TRY(tc_split(ctx, prec, LL, LL, {0, 1}, Q, ctx->sf_qh, ctx->sf_ql));
+      HS_TRY(tc_split(ctx, prec, LL, LT, {1, 0}, Q, ctx->sf_qth, ctx->sf_qtl));
+      ctx->launches += 1;
+    }
+    const long long uoff1 = (long long)mU[0] * n[0];
+    HS_CUDA(launch_gather_rows_idx_pair(ctx->sxr.d(0), xoff1, n[0], n[1], dU, mU[0], mU[1], Y[0], uoff1, s));
+    HS_CUDA(launch_gather_rows_idx_pair(ctx->szr.d(0), xoff1, n[0], n[1], dU, mU[0], mU[1], Z, uoff1, s));
+    ctx->launches += 2;
+    const long long cnt = uoff1 + (long long)mU[1] * n[1];
+    // Z <- Z - (Z Q^T) Q: the part of Z outside the locked span (T holds the second term)
+    auto project = [&]() -> hs_status {
+      if (!proj) return HS_OK;
+      HS_TRY(tc_split(ctx, prec, UL, UL, {0, 1}, Z, ctx->sx_hi, ctx->sx_lo));
+      HS_TRY(tc_run(ctx, prec, UL, ctx->sx_hi, ctx->sx_lo, LL, ctx->sf_qh, ctx->sf_ql, SL, S));
+      HS_TRY(tc_split(ctx, prec, SL, SL, {0, 1}, S, ctx->sy_hi, ctx->sy_lo));
+      HS_TRY(tc_run(ctx, prec, SL, ctx->sy_hi, ctx->sy_lo, LT, ctx->sf_qth, ctx->sf_qtl, UL, T));
+      return HS_OK;
+    };
+    HS_TRY(project());
+    HS_CUDA(launch_cheb_step_pair(Y[1], Z, proj ? T : nullptr, nullptr, cnt, uoff1, 1.0 / a[0], 1.0 / a[1], 0.0, s));
+    ctx->launches += 1;
+    int prev = 0;
+    cur = 1;
+    for (int j = 2; j <= kDeg; ++j) {
+      const int next = 3 - prev - cur;
+      HS_TRY(hprod(UL, Y[cur], Z));
+      HS_TRY(project());
+      HS_CUDA(launch_cheb_step_pair(Y[next], Z, proj ? T : nullptr, Y[prev], cnt, uoff1, 2.0 / a[0], 2.0 / a[1], -1.0,
+                                    s));
+      ctx->launches += 1;
+      prev = cur;
+      cur = next;
+    }
+  }
+  // assemble the new basis per block: locked rows, then filtered rows
+  for (int b = 0; b < 2; ++b) {
+    if (m[b] == 0) continue;
+    double* Xb = ctx->sx.d(b);
+    if (mL[b] > 0)
+      HS_CUDA(cudaMemcpyAsync(Xb, XL + (b ? (long long)mL[0] * n[0] : 0), (size_t)mL[b] * n[b] * sizeof(double),
+                              cudaMemcpyDeviceToDevice, s));
+    if (mU[b] > 0)
+      HS_CUDA(cudaMemcpyAsync(Xb + (long long)mL[b] * n[b], Y[cur] + (b ? (long long)mU[0] * n[0] : 0),
+                              (size_t)mU[b] * n[b] * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  }
+  return HS_OK;
+}
+
 // Subspace iteration on both parity blocks H_b (n_b x n_b, FP64 in place in
 // the C' buffer), warm-started from the previous move's kept rows. On success
 // (*done) w[0 .. m0+m1) holds the Ritz values of block 0 then block 1
@@ -869,18 +1004,25 @@ hs_status subspace_projector(hs_ctx ctx, hs_env* env, int chi, int n0, int n1, d
     // hopeless attempts (far from tolerance and not closing in fast) fall back early
     if (it >= 1 && worst > 30.0 * kTol && worst > 0.5 * prev_worst) return HS_OK;
     prev_worst = worst;
-    for (int b = 0; b < 2; ++b)
-      if (m[b] > 0) {
-        // next basis: a Chebyshev-filtered step where possible, else a plain
-        // power step (rows of Zr = theta_i x_i + residual)
-        bool filtered = false;
-        HS_TRY(cheb_filter_block(ctx, prec, b, m[b], n[b], H[b], hth + (b ? m[0] : 0), kept[b], ctx->sx.d(b),
-                                 &filtered));
-        if (!filtered)
-          HS_CUDA(cudaMemcpyAsync(ctx->sx.d(b), ctx->szr.d(b), (size_t)m[b] * n[b] * sizeof(double),
-                                  cudaMemcpyDeviceToDevice, s));
-        HS_CUDA(launch_row_normalize(ctx->sx.d(b), m[b], n[b], s));
-      }
+    if (tc) {
+      // next basis: Chebyshev-filtered steps, both blocks per launch
+      HS_TRY(cheb_filter_pair(ctx, prec, m, n, hth, kept));
+      for (int b = 0; b < 2; ++b)
+        if (m[b] > 0) HS_CUDA(launch_row_normalize(ctx->sx.d(b), m[b], n[b], s));
+    } else {
+      for (int b = 0; b < 2; ++b)
+        if (m[b] > 0) {
+          // next basis: a Chebyshev-filtered step where possible, else a plain
+          // power step (rows of Zr = theta_i x_i + residual)
+          bool filtered = false;
+          HS_TRY(cheb_filter_block(ctx, prec, b, m[b], n[b], H[b], hth + (b ? m[0] : 0), kept[b], ctx->sx.d(b),
+                                   &filtered));
+          if (!filtered)
+            HS_CUDA(cudaMemcpyAsync(ctx->sx.d(b), ctx->szr.d(b), (size_t)m[b] * n[b] * sizeof(double),
+                                    cudaMemcpyDeviceToDevice, s));
+          HS_CUDA(launch_row_normalize(ctx->sx.d(b), m[b], n[b], s));
+        }
+    }
     {
       // far from convergence the rows can be far from orthogonal (the Loewdin
       // iteration alone diverges there): Cholesky-QR first
@@ -977,7 +1119,7 @@ hs_status hs_destroy(hs_ctx ctx) {
   ctx->sH_hi.release();
   ctx->sH_lo.release();
   for (auto* t : {&ctx->sf_y[0], &ctx->sf_y[1], &ctx->sf_y[2], &ctx->sf_z, &ctx->sf_t, &ctx->sf_s, &ctx->sf_q,
-                  &ctx->sf_qt, &ctx->sf_idx})
+                  &ctx->sf_qt, &ctx->sf_idx, &ctx->sf_xl, &ctx->sf_qh, &ctx->sf_ql, &ctx->sf_qth, &ctx->sf_qtl})
     t->release();
   for (DBuf* b : more) b->release();
   for (cudaEvent_t e : ctx->events) cudaEventDestroy(e);

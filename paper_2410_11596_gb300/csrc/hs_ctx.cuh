@@ -185,7 +185,7 @@ struct hs_ctx_s {
   // Chebyshev filter of the subspace eigensolver: three recurrence terms, the
   // product, the projection and its coefficients, the locked rows (and their
   // transpose), and the row order
-  hs::DBuf sf_y[3], sf_z, sf_t, sf_s, sf_q, sf_qt, sf_idx;
+  hs::DBuf sf_y[3], sf_z, sf_t, sf_s, sf_q, sf_qt, sf_idx, sf_xl, sf_qh, sf_ql, sf_qth, sf_qtl;
   // pinned staging: Ritz values, residuals and status words (device to
   // host), the filter's row order (host to device)
   hs::PinnedBuf h_sub, h_idx;

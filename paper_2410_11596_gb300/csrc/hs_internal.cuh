@@ -356,6 +356,13 @@ cudaError_t launch_jacobi_eig_pair(float* A0, int m0, float* w0, float* A1, int 
 cudaError_t launch_row_normalize(double* X, int m, int n, cudaStream_t s);
 // out row i = X row idx[i] for i < m (idx on the device; rows of n).
 cudaError_t launch_gather_rows_idx(const double* X, const int* idx, int m, int n, double* out, cudaStream_t s);
+// Stacked pairs (block 1 at the given element offsets): gather of cnt_b rows
+// of block b by idx (cnt0 entries for block 0, then cnt1), and the
+// Chebyshev term with alpha0 on the first count0 entries, alpha1 after.
+cudaError_t launch_gather_rows_idx_pair(const double* X, long long src_off1, int n0, int n1, const int* idx,
+                                        int cnt0, int cnt1, double* out, long long dst_off1, cudaStream_t s);
+cudaError_t launch_cheb_step_pair(double* Y, const double* Z, const double* T, const double* Yold, long long count,
+                                  long long count0, double alpha0, double alpha1, double beta, cudaStream_t s);
 // Y = alpha (Z - T) + beta Yold over count entries; T and Yold may be null.
 cudaError_t launch_cheb_step(double* Y, const double* Z, const double* T, const double* Yold, long long count,
                              double alpha, double beta, cudaStream_t s);

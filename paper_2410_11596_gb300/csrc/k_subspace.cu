@@ -309,6 +309,32 @@ __global__ void cheb_step_kernel(double* __restrict__ Y, const double* __restric
   }
 }
 
+// Stacked pair gather: out block b row i = X block b row idx[...]; CTA j <
+// cnt0 takes block 0 (idx[j]), the rest block 1 (idx[j], rows of n1).
+__global__ void gather_rows_idx_pair_kernel(const double* __restrict__ X, long long src_off1, int n0, int n1,
+                                            const int* __restrict__ idx, int cnt0, double* __restrict__ out,
+                                            long long dst_off1) {
+  const int j = blockIdx.x, b = j >= cnt0;
+  const int n = b ? n1 : n0;
+  const long long src = (b ? src_off1 : 0) + (long long)idx[j] * n;
+  const long long dst = (b ? dst_off1 : 0) + (long long)(j - (b ? cnt0 : 0)) * n;
+  for (int k = threadIdx.x; k < n; k += blockDim.x) out[dst + k] = X[src + k];
+}
+
+// cheb_step_kernel over a stacked pair: entries below count0 use alpha0.
+__global__ void cheb_step_pair_kernel(double* __restrict__ Y, const double* __restrict__ Z,
+                                      const double* __restrict__ T, const double* __restrict__ Yold, long long count,
+                                      long long count0, double alpha0, double alpha1, double beta) {
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < count;
+       e += (long long)gridDim.x * blockDim.x) {
+    double v = Z[e];
+    if (T) v -= T[e];
+    v *= e < count0 ? alpha0 : alpha1;
+    if (Yold) v += beta * Yold[e];
+    Y[e] = v;
+  }
+}
+
 // Symmetric eigen-decomposition of one small FP32 matrix per CTA by the
 // cyclic Jacobi method (Golub and Van Loan, Sec. 8.5) with the round-robin
 // ordering, so that the m/2 rotations of a round touch disjoint rows and
@@ -509,6 +535,20 @@ cudaError_t launch_cheb_step(double* Y, const double* Z, const double* T, const 
                              double alpha, double beta, cudaStream_t s) {
   if (count <= 0) return cudaSuccess;
   cheb_step_kernel<<<grid_for(count), 256, 0, s>>>(Y, Z, T, Yold, count, alpha, beta);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather_rows_idx_pair(const double* X, long long src_off1, int n0, int n1, const int* idx,
+                                        int cnt0, int cnt1, double* out, long long dst_off1, cudaStream_t s) {
+  if (cnt0 + cnt1 <= 0) return cudaSuccess;
+  gather_rows_idx_pair_kernel<<<cnt0 + cnt1, 256, 0, s>>>(X, src_off1, n0, n1, idx, cnt0, out, dst_off1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cheb_step_pair(double* Y, const double* Z, const double* T, const double* Yold, long long count,
+                                  long long count0, double alpha0, double alpha1, double beta, cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  cheb_step_pair_kernel<<<grid_for(count), 256, 0, s>>>(Y, Z, T, Yold, count, count0, alpha0, alpha1, beta);
   return cudaGetLastError();
 }
 
