@@ -462,12 +462,30 @@ hs_status orthonormalise_rows(hs_ctx ctx, hs_precision prec, double* const X[2],
   HS_TRY(ctx->schol.ensure(4 * (size_t)mm * mm * sizeof(double)));
   double* G[2] = {ctx->schol.d(), ctx->schol.d() + 2LL * mm * mm};
   double* Li[2] = {G[0] + (long long)mm * mm, G[1] + (long long)mm * mm};
-  for (int b = 0; b < 2; ++b)
-    if (m[b] > 0)
-      HS_TRY(gemm(ctx, HS_GEMM_OWN, GemmGroup{1, {GemmProblem{m[b], m[b], n[b], n[b], n[b], m[b], 0, 0, 0}}}, X[b],
-                  X[b], G[b]));
+  // stacked pairs (block 1 right after block 0 in X and Xc) run both
+  // blocks in one launch per step
+  const long long mn0 = (long long)m[0] * n[0];
+  const bool stacked = m[0] > 0 && m[1] > 0 && X[1] == X[0] + mn0 && Xc[1] == Xc[0] + mn0;
+  if (stacked) {
+    GemmGroup gg{2, {GemmProblem{m[0], m[0], n[0], n[0], n[0], m[0], 0, 0, 0},
+                     GemmProblem{m[1], m[1], n[1], n[1], n[1], m[1], mn0, mn0, G[1] - G[0]}}};
+    HS_TRY(gemm(ctx, HS_GEMM_OWN, gg, X[0], X[0], G[0]));
+  } else {
+    for (int b = 0; b < 2; ++b)
+      if (m[b] > 0)
+        HS_TRY(gemm(ctx, HS_GEMM_OWN, GemmGroup{1, {GemmProblem{m[b], m[b], n[b], n[b], n[b], m[b], 0, 0, 0}}},
+                    X[b], X[b], G[b]));
+  }
   HS_CUDA(launch_chol_inv(G[0], m[0], Li[0], G[1], m[1], Li[1], bad, ctx->stream));
   ctx->launches += 1;
+  if (stacked) {
+    HS_TRY(permute(ctx, zd(m[0], m[1], n[0], n[1]), zd(n[0], n[1], m[0], m[1]), {1, 0}, X[0], Xc[0]));
+    GemmGroup gl{2, {GemmProblem{m[0], n[0], m[0], m[0], m[0], n[0], 0, 0, 0},
+                     GemmProblem{m[1], n[1], m[1], m[1], m[1], n[1], Li[1] - Li[0], mn0, mn0}}};
+    HS_TRY(gemm(ctx, HS_GEMM_OWN, gl, Li[0], Xc[0], X[0]));
+    HS_TRY(lowdin_rows_pair(ctx, prec, X[0], m, n, Xc[0], 1));
+    return HS_OK;
+  }
   for (int b = 0; b < 2; ++b)
     if (m[b] > 0) {
       HS_TRY(permute(ctx, dense2(m[b], n[b]), dense2(n[b], m[b]), {1, 0}, X[b], Xc[b]));
