@@ -27,6 +27,7 @@ unsigned grid_for(long long n) {
 // out[j] = <V_j, w> for the m rows of V (n long); one block per row
 __global__ void multi_dot_kernel(const double* __restrict__ V, int m, long long n, const double* __restrict__ w,
                                  double* __restrict__ out) {
+  hs_pdl_enter();
   const int j = blockIdx.x;
   if (j >= m) return;
   double s = 0.0;
@@ -44,6 +45,7 @@ __global__ void multi_dot_kernel(const double* __restrict__ V, int m, long long 
 // w -= sum_j c[j] V_j
 __global__ void multi_axpy_kernel(const double* __restrict__ V, int m, long long n, const double* __restrict__ c,
                                   double* __restrict__ w) {
+  hs_pdl_enter();
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     double s = 0.0;
     for (int j = 0; j < m; ++j) s += c[j] * V[j * n + i];
@@ -53,12 +55,14 @@ __global__ void multi_axpy_kernel(const double* __restrict__ V, int m, long long
 
 // dst = src * f
 __global__ void scale_copy_kernel(const double* __restrict__ src, double f, long long n, double* __restrict__ dst) {
+  hs_pdl_enter();
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     dst[i] = src[i] * f;
 }
 
 // seeded start vector (splitmix64 -> uniform in (-1, 1))
 __global__ void start_vector_kernel(double* __restrict__ v, long long n) {
+  hs_pdl_enter();
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     unsigned long long x = (unsigned long long)i + 0x9E3779B97F4A7C15ull * 7;
     x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
@@ -152,16 +156,16 @@ extern "C" hs_status hs_correlation_length(hs_ctx ctx, const hs_env* env, const 
     return dense_gemm_any(ctx, prec, (int)(chi * q), (int)chi, (int)(chi * q), W2, TB, out);     // [(a,l)|b]
   };
   auto norm = [&](const double* x) -> double {
-    multi_dot_kernel<<<1, 256, 0, s>>>(x, 1, n, x, coef);
+    hs_launch(multi_dot_kernel, 1, 256, 0, s, x, 1, n, x, coef);
     double h = 0.0;
     cudaMemcpyAsync(&h, coef, 8, cudaMemcpyDeviceToHost, s);
     cudaStreamSynchronize(s);
     return std::sqrt(h);
   };
-  start_vector_kernel<<<grid_for(n), 256, 0, s>>>(w, n);
+  hs_launch(start_vector_kernel, grid_for(n), 256, 0, s, w, n);
   HS_CUDA(cudaGetLastError());
   double nb = norm(w);
-  scale_copy_kernel<<<grid_for(n), 256, 0, s>>>(w, 1.0 / nb, n, V);
+  hs_launch(scale_copy_kernel, grid_for(n), 256, 0, s, w, 1.0 / nb, n, V);
   std::vector<double> alpha, beta;
   std::vector<double> c(mmax + 1);
   double l1 = 0.0, l2 = 0.0, l1_old = -1.0, l2_old = -1.0;
@@ -171,12 +175,12 @@ extern "C" hs_status hs_correlation_length(hs_ctx ctx, const hs_env* env, const 
     // full re-orthogonalisation against V_0..V_j, twice (classical Gram-Schmidt)
     double a_j = 0.0;
     for (int pass = 0; pass < 2; ++pass) {
-      multi_dot_kernel<<<j + 1, 256, 0, s>>>(V, j + 1, n, w, coef);
+      hs_launch(multi_dot_kernel, j + 1, 256, 0, s, V, j + 1, n, w, coef);
       HS_CUDA(cudaMemcpyAsync(c.data(), coef, (j + 1) * 8, cudaMemcpyDeviceToHost, s));
       HS_CUDA(cudaStreamSynchronize(s));
       if (pass == 0) a_j = c[j];
       else a_j += c[j];
-      multi_axpy_kernel<<<grid_for(n), 256, 0, s>>>(V, j + 1, n, coef, w);
+      hs_launch(multi_axpy_kernel, grid_for(n), 256, 0, s, V, j + 1, n, coef, w);
     }
     alpha.push_back(a_j);
     const double b = norm(w);
@@ -202,7 +206,7 @@ extern "C" hs_status hs_correlation_length(hs_ctx ctx, const hs_env* env, const 
       break;
     }
     beta.push_back(b);
-    scale_copy_kernel<<<grid_for(n), 256, 0, s>>>(w, 1.0 / b, n, V + (long long)(j + 1) * n);
+    hs_launch(scale_copy_kernel, grid_for(n), 256, 0, s, w, 1.0 / b, n, V + (long long)(j + 1) * n);
   }
   HS_CUDA(cudaGetLastError());
   lam_out[0] = l1;

@@ -11,6 +11,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <utility>
 #include <cuda_runtime.h>
 
 #include "../../include/hs.h"
@@ -20,6 +21,36 @@
 namespace hs {
 
 // Sector sizes of one leg.
+// Programmatic dependent launch. Every kernel of the library is launched by
+// hs_launch with programmatic stream serialisation allowed and opens with
+// hs_pdl_enter(): it first waits until the previous kernel in the stream has
+// completed and its writes are visible (griddepcontrol.wait, before any
+// global memory access), then lets the next kernel be scheduled
+// (griddepcontrol.launch_dependents). The next kernel's launch and prologue
+// so overlap this kernel's run, while the data order stays that of the stream.
+__device__ __forceinline__ void hs_pdl_enter() {
+#if defined(__CUDA_ARCH__)
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+#endif
+}
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t hs_launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                             Args&&... args) {
+  cudaLaunchAttribute attr;
+  attr.id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr.val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cfg.attrs = &attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
 struct Sect {
   int n[2];
 };

@@ -19,6 +19,7 @@ namespace {
 // and c0 the other horizontal leg; combined index x = ket + D * bra.
 __global__ void open_double_layer_kernel(const double* __restrict__ A, int d, int D, bool open_right,
                                          double* __restrict__ out) {
+  hs_pdl_enter();
   const int q = D * D;
   const long long total = (long long)d * d * q * q * q * q;
   const long long D4 = (long long)D * D * D * D;
@@ -48,6 +49,7 @@ __global__ void open_double_layer_kernel(const double* __restrict__ A, int d, in
 //   dA[p, u, l, d, r] = sum over the other factor's indices of dao * A.
 __global__ void open_double_layer_vjp_kernel(const double* __restrict__ daoL, const double* __restrict__ daoR,
                                              const double* __restrict__ A, int d, int D, double* __restrict__ dA) {
+  hs_pdl_enter();
   const int q = D * D;
   const long long D4 = (long long)D * D * D * D;
   const long long nA = d * D4;
@@ -92,6 +94,7 @@ __global__ void open_double_layer_vjp_kernel(const double* __restrict__ daoL, co
 __global__ void finish_rho_kernel(const double* __restrict__ rho4, int d, bool mirror,
                                   const double* __restrict__ h, double* __restrict__ rho,
                                   double* __restrict__ tr) {
+  hs_pdl_enter();
   const int n = d * d;
   for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
     int I = e / n, J = e % n;
@@ -156,6 +159,7 @@ GemmGroup dense_gemm(long long M, long long N, long long K) {
 // combined index is x = ket + D * bra.
 __global__ void open_double_layer_c_kernel(const double* __restrict__ A, int d, int D, int4 legs,
                                            double* __restrict__ re, double* __restrict__ im) {
+  hs_pdl_enter();
   const int q = D * D;
   const long long total = (long long)d * d * q * q * q * q;
   const long long D4 = (long long)D * D * D * D;
@@ -190,6 +194,7 @@ __global__ void open_double_layer_c_kernel(const double* __restrict__ A, int d, 
 // interleaved out); tr[0..1] = Tr rho, tr[2..3] = Tr(rho h) for real h.
 __global__ void finish_rho_c_kernel(const double* __restrict__ re4, const double* __restrict__ im4, int d,
                                     const double* __restrict__ h, double* __restrict__ rho, double* __restrict__ tr) {
+  hs_pdl_enter();
   const int n = d * d;
   for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
     const int I = e / n, J = e % n;
@@ -253,6 +258,7 @@ __global__ void open_double_layer_c_vjp_kernel(const double* __restrict__ g1r, c
                                                int4 legs1, const double* __restrict__ g2r,
                                                const double* __restrict__ g2i, int4 legs2,
                                                const double* __restrict__ A, int d, int D, double* __restrict__ dA) {
+  hs_pdl_enter();
   const int q = D * D;
   const long long D4 = (long long)D * D * D * D;
   const long long nA = d * D4;
@@ -374,9 +380,9 @@ hs_status rdm_complex(hs_ctx ctx, const hs_env* env, const double* A, int d, int
   const long long nao = d2 * q * q * q * q;
   ZBuf a1 = zbuf(ctx, 10, nao), a2 = zbuf(ctx, 11, nao);
   if (!a2.re) return fail(HS_ERR_CUDA, "workspace allocation failed");
-  open_double_layer_c_kernel<<<grid_for(nao), 256, 0, s>>>(A, d, D, make_int4(3, 2, 1, 0), a1.re, a1.im);
+  hs_launch(open_double_layer_c_kernel, grid_for(nao), 256, 0, s, A, d, D, make_int4(3, 2, 1, 0), a1.re, a1.im);
   HS_CUDA(cudaGetLastError());
-  open_double_layer_c_kernel<<<grid_for(nao), 256, 0, s>>>(A, d, D, make_int4(1, 0, 3, 2), a2.re, a2.im);
+  hs_launch(open_double_layer_c_kernel, grid_for(nao), 256, 0, s, A, d, D, make_int4(1, 0, 3, 2), a2.re, a2.im);
   HS_CUDA(cudaGetLastError());
   ctx->launches += 2;
   ZBuf LB = zbuf(ctx, 1, c2 * d2 * q), RB = zbuf(ctx, 2, c2 * d2 * q);  // reuse (T, C^T no longer needed)
@@ -387,7 +393,7 @@ hs_status rdm_complex(hs_ctx ctx, const hs_env* env, const double* A, int d, int
   HS_TRY(zpermute(ctx, dense({chi, chi, d, d, q}), dense({d, d, chi, chi, q}), {2, 3, 0, 1, 4}, LB, LBp));
   HS_TRY(zpermute(ctx, dense({chi, chi, d, d, q}), dense({d, d, chi, chi, q}), {2, 3, 1, 0, 4}, RB, RBp));
   HS_TRY(zgemm(ctx, dense_gemm(d2, d2, c2 * q), LBp, RBp, R4));                                 // rho4
-  finish_rho_c_kernel<<<1, 256, 0, s>>>(R4.re, R4.im, d, h, out, tr_out);
+  hs_launch(finish_rho_c_kernel, 1, 256, 0, s, R4.re, R4.im, d, h, out, tr_out);
   HS_CUDA(cudaGetLastError());
   ctx->launches += 1;
   return HS_OK;
@@ -433,7 +439,7 @@ hs_status rdm_vjp_complex(hs_ctx ctx, const hs_env* env, const double* A, int d,
   HS_TRY(zgemm(ctx, dense_gemm(d2 * q, q * q * q, c2), gLm, L2pT, g1, true));
   HS_TRY(zgemm(ctx, dense_gemm(d2 * q, q * q * q, c2), gRm, L2pT, g2, true));
   const long long nA = (long long)d * D * D * D * D;
-  open_double_layer_c_vjp_kernel<<<grid_for(nA), 256, 0, s>>>(g1.re, g1.im, make_int4(3, 2, 1, 0), g2.re, g2.im,
+  hs_launch(open_double_layer_c_vjp_kernel, grid_for(nA), 256, 0, s, g1.re, g1.im, make_int4(3, 2, 1, 0), g2.re, g2.im,
                                                                make_int4(1, 0, 3, 2), A, d, D, dA_out);
   HS_CUDA(cudaGetLastError());
   ctx->launches += 1;
@@ -502,9 +508,9 @@ hs_status rdm_chain(hs_ctx ctx, const hs_env* env, const double* A, int d, int D
   double *aoL = r[10].d(), *aoR = r[11].d(), *LB = r[12].d(), *RB = r[13].d(), *LBp = r[14].d(),
          *RBp = r[15].d();
   const long long nao = d2 * q * q * q * q;
-  open_double_layer_kernel<<<grid_for(nao), 256, 0, s>>>(A, d, D, true, aoL);
+  hs_launch(open_double_layer_kernel, grid_for(nao), 256, 0, s, A, d, D, true, aoL);
   HS_CUDA(cudaGetLastError());
-  open_double_layer_kernel<<<grid_for(nao), 256, 0, s>>>(A, d, D, false, aoR);
+  hs_launch(open_double_layer_kernel, grid_for(nao), 256, 0, s, A, d, D, false, aoR);
   HS_CUDA(cudaGetLastError());
   // Z2p[(t', b') | (l, u, d)]
   HS_TRY(permute(ctx, dense({q * q, chi, q, chi}), dense({chi, chi, q * q, q}), {1, 3, 0, 2}, Z2, Z2p));
@@ -531,7 +537,7 @@ extern "C" hs_status hs_rdm(hs_ctx ctx, const hs_env* env, const double* A, int 
   if (dtype == HS_C128) return rdm_complex(ctx, env, A, d, D, kind, h, out, tr_out);
   HS_TRY(rdm_chain(ctx, env, A, d, D, kind, out));
   if (kind == HS_RDM_ENV_ONE_SITE) return HS_OK;
-  finish_rho_kernel<<<1, 256, 0, ctx->stream>>>(ctx->r[6].d(), d, env->basis == HS_BASIS_HERMITIAN, h, out,
+  hs_launch(finish_rho_kernel, 1, 256, 0, ctx->stream, ctx->r[6].d(), d, env->basis == HS_BASIS_HERMITIAN, h, out,
                                                 tr_out);
   HS_CUDA(cudaGetLastError());
   return HS_OK;
@@ -583,7 +589,7 @@ extern "C" hs_status hs_rdm_vjp(hs_ctx ctx, const hs_env* env, const double* A, 
   HS_TRY(gemm(ctx, be, dense_gemm(d2 * q, q * q * q, c2), dLBm, Z2p, ctx->hb[7].d()));
   HS_TRY(gemm(ctx, be, dense_gemm(d2 * q, q * q * q, c2), dRBm, Z2p, ctx->hb[8].d()));
   const long long nA = (long long)d * D * D * D * D;
-  open_double_layer_vjp_kernel<<<grid_for(nA), 256, 0, s>>>(ctx->hb[7].d(), ctx->hb[8].d(), A, d, D, dA_out);
+  hs_launch(open_double_layer_vjp_kernel, grid_for(nA), 256, 0, s, ctx->hb[7].d(), ctx->hb[8].d(), A, d, D, dA_out);
   HS_CUDA(cudaGetLastError());
   return HS_OK;
 }

@@ -52,6 +52,7 @@ __device__ __forceinline__ int traced_local(int k, int D, bool hermitian) {
 
 __global__ void init_T_kernel(const double* __restrict__ a, int D, bool hermitian,
                               double* __restrict__ T) {
+  hs_pdl_enter();
   const int q = D * D;
   const int qe = hermitian ? D * (D + 1) / 2 : q;
   const Sect s = make_sect(qe, q - qe);
@@ -74,6 +75,7 @@ __global__ void init_T_kernel(const double* __restrict__ a, int D, bool hermitia
 
 __global__ void init_C_kernel(const double* __restrict__ a, int D, bool hermitian,
                               double* __restrict__ C) {
+  hs_pdl_enter();
   const int q = D * D;
   const int qe = hermitian ? D * (D + 1) / 2 : q;
   const Sect s = make_sect(qe, q - qe);
@@ -100,6 +102,7 @@ __global__ void init_C_kernel(const double* __restrict__ a, int D, bool hermitia
 __global__ void select_kernel(const double* __restrict__ w0g, int n0, const double* __restrict__ w1g,
                               int n1, int chi, int* __restrict__ idx, double* __restrict__ lam,
                               SelectOut* out, bool staged) {
+  hs_pdl_enter();
   // both spectra staged in shared memory (the merge below is a serial walk),
   // followed by the picked values and their blocks. The walk compares
   // magnitudes as integers (IEEE bit patterns without the sign order like
@@ -188,6 +191,7 @@ __global__ void select_kernel(const double* __restrict__ w0g, int n0, const doub
 __global__ void gather_pt_kernel(const double* __restrict__ V0, int n0, const double* __restrict__ V1,
                                  int n1, const int* __restrict__ idx, int chi,
                                  const SelectOut* __restrict__ sel, double* __restrict__ PT) {
+  hs_pdl_enter();
   const int b = blockIdx.y, j = blockIdx.x;
   if (j >= sel->chi_new[b]) return;
   const int n = b ? n1 : n0;
@@ -198,6 +202,7 @@ __global__ void gather_pt_kernel(const double* __restrict__ V0, int n0, const do
 
 __global__ void diag_corner_kernel(const double* __restrict__ lam, SelectOut* sel, double* C,
                                    int chi) {
+  hs_pdl_enter();
   const int c0 = sel->chi_new[0], c1 = sel->chi_new[1];
   const long long total = (long long)c0 * c0 + (long long)c1 * c1;
   // one FP64 division per block (it is a long sequence on the FP64 pipe)
@@ -224,6 +229,7 @@ __global__ void diag_corner_kernel(const double* __restrict__ lam, SelectOut* se
 }
 
 __global__ void absmax_kernel(const double* __restrict__ x, long long n, unsigned long long* m) {
+  hs_pdl_enter();
   double v = 0.0;
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n;
        e += (long long)gridDim.x * blockDim.x)
@@ -234,6 +240,7 @@ __global__ void absmax_kernel(const double* __restrict__ x, long long n, unsigne
 
 __global__ void scale_kernel(double* __restrict__ x, long long n, const unsigned long long* m,
                              SelectOut* sel) {
+  hs_pdl_enter();
   const double mx = __longlong_as_double((long long)*m);
   // one FP64 division per block (it is a long sequence on the FP64 pipe)
   __shared__ double s_inv;
@@ -247,11 +254,13 @@ __global__ void scale_kernel(double* __restrict__ x, long long n, const unsigned
 }
 
 __global__ void cast_f64_f32_kernel(const double* __restrict__ a, float* __restrict__ b, long long n) {
+  hs_pdl_enter();
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
     b[e] = (float)a[e];
 }
 
 __global__ void cast_f32_f64_kernel(const float* __restrict__ a, double* __restrict__ b, long long n) {
+  hs_pdl_enter();
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
     b[e] = (double)a[e];
 }
@@ -260,6 +269,7 @@ __global__ void cast_f32_f64_kernel(const float* __restrict__ a, double* __restr
 __global__ void gather_p32_kernel(const float* __restrict__ V0, int n0, const float* __restrict__ V1, int n1,
                                   const int* __restrict__ idx, int chi, const SelectOut* __restrict__ sel,
                                   double* __restrict__ PT, double* __restrict__ P) {
+  hs_pdl_enter();
   const int b = blockIdx.y, j = blockIdx.x;
   const int cb = sel->chi_new[b];
   if (j >= cb) return;
@@ -276,6 +286,7 @@ __global__ void gather_p32_kernel(const float* __restrict__ V0, int n0, const fl
 }
 
 __global__ void lowdin_kernel(double* __restrict__ G, int k0, int k1) {
+  hs_pdl_enter();
   const long long total = (long long)k0 * k0 + (long long)k1 * k1;
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
        e += (long long)gridDim.x * blockDim.x) {
@@ -293,6 +304,7 @@ __global__ void lowdin_kernel(double* __restrict__ G, int k0, int k1) {
 }
 
 __global__ void scale_to_kernel(double* __restrict__ x, long long n, const unsigned long long* m, double* log_out) {
+  hs_pdl_enter();
   const double mx = __longlong_as_double((long long)*m);
   __shared__ double s_inv;
   if (threadIdx.x == 0) s_inv = 1.0 / mx;
@@ -311,6 +323,7 @@ __device__ __forceinline__ int pair_index(int k, int l, int D) {
 __global__ void env_to_dense_kernel(const double* __restrict__ C, const double* __restrict__ T, int D,
                                     int c0, int c1, bool hermitian, double* __restrict__ Cd,
                                     double* __restrict__ Td) {
+  hs_pdl_enter();
   const int q = D * D, chi = c0 + c1;
   const int qe = hermitian ? D * (D + 1) / 2 : q;
   const Sect cs = make_sect(c0, c1), qs = make_sect(qe, q - qe);
@@ -367,6 +380,7 @@ __global__ void env_to_dense_kernel(const double* __restrict__ C, const double* 
 // of odd total parity is i times the stored number.
 __global__ void env_to_dense_graded_kernel(const double* __restrict__ C, const double* __restrict__ T, int D,
                                            int c0, int c1, double* __restrict__ Cd, double* __restrict__ Td) {
+  hs_pdl_enter();
   const int q = D * D, chi = c0 + c1;
   const int qe = D * (D + 1) / 2, qo = q - qe;
   const Fused fr = fused2(make_sect(c0, c1), make_sect(qe, qo));
@@ -423,15 +437,15 @@ __global__ void env_to_dense_graded_kernel(const double* __restrict__ C, const d
 cudaError_t launch_env_to_dense_graded(const double* C, const double* T, int D, int c0, int c1, double* Cd,
                                        double* Td, cudaStream_t s) {
   const long long chi = c0 + c1, q = (long long)D * D;
-  env_to_dense_graded_kernel<<<grid_for(chi * q * chi + chi * chi), 256, 0, s>>>(C, T, D, c0, c1, Cd, Td);
+  hs_launch(env_to_dense_graded_kernel, grid_for(chi * q * chi + chi * chi), 256, 0, s, C, T, D, c0, c1, Cd, Td);
   return cudaGetLastError();
 }
 
 cudaError_t launch_ctmrg_init(const double* a_blocks, int D, bool hermitian, double* C, double* T,
                               cudaStream_t s) {
   const long long q = (long long)D * D;
-  init_T_kernel<<<grid_for(q * q * q), 256, 0, s>>>(a_blocks, D, hermitian, T);
-  init_C_kernel<<<grid_for(q * q), 256, 0, s>>>(a_blocks, D, hermitian, C);
+  hs_launch(init_T_kernel, grid_for(q * q * q), 256, 0, s, a_blocks, D, hermitian, T);
+  hs_launch(init_C_kernel, grid_for(q * q), 256, 0, s, a_blocks, D, hermitian, C);
   return cudaGetLastError();
 }
 
@@ -450,21 +464,21 @@ cudaError_t launch_select(const double* w0, int n0, const double* w1, int n1, in
         cudaFuncSetAttribute(select_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax);
     if (attr_err != cudaSuccess) return attr_err;
   }
-  select_kernel<<<1, 256, smem, s>>>(w0, n0, w1, n1, chi, idx, lam, out, staged);
+  hs_launch(select_kernel, 1, 256, smem, s, w0, n0, w1, n1, chi, idx, lam, out, staged);
   return cudaGetLastError();
 }
 
 cudaError_t launch_gather_pt(const double* V0, int n0, const double* V1, int n1, const int* idx,
                                  int chi, const SelectOut* sel, double* PT, cudaStream_t s) {
   dim3 grid((unsigned)chi, 2);
-  gather_pt_kernel<<<grid, 256, 0, s>>>(V0, n0, V1, n1, idx, chi, sel, PT);
+  hs_launch(gather_pt_kernel, grid, 256, 0, s, V0, n0, V1, n1, idx, chi, sel, PT);
   return cudaGetLastError();
 }
 
 cudaError_t launch_diag_corner(const double* lam, int c0, int c1, SelectOut* sel, double* C,
                                cudaStream_t s) {
   const long long n = (long long)c0 * c0 + (long long)c1 * c1;
-  diag_corner_kernel<<<grid_for(n), 256, 0, s>>>(lam, sel, C, c0 + c1);
+  hs_launch(diag_corner_kernel, grid_for(n), 256, 0, s, lam, sel, C, c0 + c1);
   return cudaGetLastError();
 }
 
@@ -472,31 +486,31 @@ cudaError_t launch_normalize_max(double* T, long long n, unsigned long long* scr
                                  SelectOut* sel, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(scratch, 0, sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
-  absmax_kernel<<<grid_for(n), 256, 0, s>>>(T, n, scratch);
-  scale_kernel<<<grid_for(n), 256, 0, s>>>(T, n, scratch, sel);
+  hs_launch(absmax_kernel, grid_for(n), 256, 0, s, T, n, scratch);
+  hs_launch(scale_kernel, grid_for(n), 256, 0, s, T, n, scratch, sel);
   return cudaGetLastError();
 }
 
 cudaError_t launch_cast_f64_f32(const double* src, float* dst, long long n, cudaStream_t s) {
-  cast_f64_f32_kernel<<<grid_for(n), 256, 0, s>>>(src, dst, n);
+  hs_launch(cast_f64_f32_kernel, grid_for(n), 256, 0, s, src, dst, n);
   return cudaGetLastError();
 }
 
 cudaError_t launch_cast_f32_f64(const float* src, double* dst, long long n, cudaStream_t s) {
-  cast_f32_f64_kernel<<<grid_for(n), 256, 0, s>>>(src, dst, n);
+  hs_launch(cast_f32_f64_kernel, grid_for(n), 256, 0, s, src, dst, n);
   return cudaGetLastError();
 }
 
 cudaError_t launch_gather_p32(const float* V0, int n0, const float* V1, int n1, const int* idx, int chi,
                               const SelectOut* sel, double* PT, double* P, cudaStream_t s) {
   dim3 grid((unsigned)chi, 2);
-  gather_p32_kernel<<<grid, 256, 0, s>>>(V0, n0, V1, n1, idx, chi, sel, PT, P);
+  hs_launch(gather_p32_kernel, grid, 256, 0, s, V0, n0, V1, n1, idx, chi, sel, PT, P);
   return cudaGetLastError();
 }
 
 cudaError_t launch_lowdin(double* G, int k0, int k1, cudaStream_t s) {
   const long long n = (long long)k0 * k0 + (long long)k1 * k1;
-  lowdin_kernel<<<grid_for(n), 256, 0, s>>>(G, k0, k1);
+  hs_launch(lowdin_kernel, grid_for(n), 256, 0, s, G, k0, k1);
   return cudaGetLastError();
 }
 
@@ -504,12 +518,13 @@ cudaError_t launch_normalize_max_to(double* x, long long n, unsigned long long* 
                                     cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(scratch, 0, sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
-  absmax_kernel<<<grid_for(n), 256, 0, s>>>(x, n, scratch);
-  scale_to_kernel<<<grid_for(n), 256, 0, s>>>(x, n, scratch, log_out);
+  hs_launch(absmax_kernel, grid_for(n), 256, 0, s, x, n, scratch);
+  hs_launch(scale_to_kernel, grid_for(n), 256, 0, s, x, n, scratch, log_out);
   return cudaGetLastError();
 }
 
 __global__ void block_trace_kernel(const double* __restrict__ x, int n0, int n1, double* out) {
+  hs_pdl_enter();
   double v = 0.0;
   for (int i = threadIdx.x; i < n0 + n1; i += blockDim.x)
     v += i < n0 ? x[(long long)i * n0 + i] : x[(long long)n0 * n0 + (long long)(i - n0) * n1 + (i - n0)];
@@ -524,14 +539,14 @@ __global__ void block_trace_kernel(const double* __restrict__ x, int n0, int n1,
 }
 
 cudaError_t launch_block_trace(const double* x, int n0, int n1, double* out, cudaStream_t s) {
-  block_trace_kernel<<<1, 256, 0, s>>>(x, n0, n1, out);
+  hs_launch(block_trace_kernel, 1, 256, 0, s, x, n0, n1, out);
   return cudaGetLastError();
 }
 
 cudaError_t launch_env_to_dense(const double* C, const double* T, int D, int c0, int c1,
                                 bool hermitian, double* Cd, double* Td, cudaStream_t s) {
   const long long chi = c0 + c1, q = (long long)D * D;
-  env_to_dense_kernel<<<grid_for(chi * q * chi + chi * chi), 256, 0, s>>>(C, T, D, c0, c1, hermitian,
+  hs_launch(env_to_dense_kernel, grid_for(chi * q * chi + chi * chi), 256, 0, s, C, T, D, c0, c1, hermitian,
                                                                          Cd, Td);
   return cudaGetLastError();
 }

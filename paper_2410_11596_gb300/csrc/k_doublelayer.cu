@@ -81,6 +81,7 @@ __device__ __forceinline__ long long fso4(int Xu, int Xl, int Xd, int Xr, int qe
 
 __global__ void double_layer_blocks_kernel(const double* __restrict__ A, int d, int D,
                                            bool hermitian, double* __restrict__ out) {
+  hs_pdl_enter();
   const int q = D * D;
   const int qe = hermitian ? D * (D + 1) / 2 : q;
   const int qo = q - qe;
@@ -114,6 +115,7 @@ __global__ void double_layer_blocks_kernel(const double* __restrict__ A, int d, 
 // [(u,l)|(d,r)] matrix (Sec. II.C): the real part of every even-total entry,
 // the imaginary part of every odd-total one (the other part vanishes).
 __global__ void double_layer_graded_kernel(const double* __restrict__ A, int d, int D, double* __restrict__ out) {
+  hs_pdl_enter();
   const int q = D * D;
   const int qe = D * (D + 1) / 2, qo = q - qe;
   const Fused f = fused2(make_sect(qe, qo), make_sect(qe, qo));
@@ -156,6 +158,7 @@ __global__ void double_layer_graded_kernel(const double* __restrict__ A, int d, 
 
 __global__ void double_layer_dense_kernel(const double* __restrict__ A, int d, int D, bool cplx,
                                           double* __restrict__ out) {
+  hs_pdl_enter();
   const int q = D * D;
   const long long total = (long long)q * q * q * q;
   const long long D4 = (long long)D * D * D * D;
@@ -185,6 +188,7 @@ __global__ void double_layer_dense_kernel(const double* __restrict__ A, int d, i
 
 __global__ void rotate_dense_kernel(const double* __restrict__ a, int D, double* __restrict__ out,
                                     unsigned long long* maxes) {
+  hs_pdl_enter();
   const int q = D * D;
   const int qe = D * (D + 1) / 2, qo = q - qe;
   const long long total = (long long)q * q * q * q;
@@ -227,7 +231,7 @@ unsigned grid_for(long long n) {
 cudaError_t launch_double_layer_blocks(const double* A, int d, int D, bool hermitian, double* out,
                                        cudaStream_t s) {
   const long long q = (long long)D * D;
-  double_layer_blocks_kernel<<<grid_for(q * q * q * q), 256, 0, s>>>(A, d, D, hermitian, out);
+  hs_launch(double_layer_blocks_kernel, grid_for(q * q * q * q), 256, 0, s, A, d, D, hermitian, out);
   return cudaGetLastError();
 }
 
@@ -235,21 +239,21 @@ cudaError_t launch_double_layer_graded(const double* A, int d, int D, double* ou
   const long long q = (long long)D * D, total = q * q * q * q;
   long long g = (total + 255) / 256;
   if (g > 4096) g = 4096;
-  double_layer_graded_kernel<<<(unsigned)g, 256, 0, s>>>(A, d, D, out);
+  hs_launch(double_layer_graded_kernel, (unsigned)g, 256, 0, s, A, d, D, out);
   return cudaGetLastError();
 }
 
 cudaError_t launch_double_layer_dense(const double* A, int d, int D, bool cplx, double* out,
                                       cudaStream_t s) {
   const long long q = (long long)D * D;
-  double_layer_dense_kernel<<<grid_for(q * q * q * q), 256, 0, s>>>(A, d, D, cplx, out);
+  hs_launch(double_layer_dense_kernel, grid_for(q * q * q * q), 256, 0, s, A, d, D, cplx, out);
   return cudaGetLastError();
 }
 
 cudaError_t launch_rotate_dense_to_blocks(const double* a, int D, double* out,
                                           unsigned long long* maxes, cudaStream_t s) {
   const long long q = (long long)D * D;
-  rotate_dense_kernel<<<grid_for(q * q * q * q), 256, 0, s>>>(a, D, out, maxes);
+  hs_launch(rotate_dense_kernel, grid_for(q * q * q * q), 256, 0, s, a, D, out, maxes);
   return cudaGetLastError();
 }
 

@@ -24,6 +24,7 @@ __global__ void __launch_bounds__(NT) gemm_f64_nt_kernel(GemmGroup g, const doub
                                                          const double* __restrict__ B,
                                                          double* __restrict__ C, double alpha, bool accumulate,
                                                          SplitK sk, double* __restrict__ part) {
+  hs_pdl_enter();
   int t = blockIdx.x / sk.nsplit;
   const int split = blockIdx.x % sk.nsplit;
   int pi = 0;
@@ -100,6 +101,7 @@ __global__ void __launch_bounds__(NT) gemm_f64_nt_kernel(GemmGroup g, const doub
 
 __global__ void splitk_reduce_kernel(GemmGroup g, SplitK sk, const double* __restrict__ part,
                                      double* __restrict__ C, bool accumulate) {
+  hs_pdl_enter();
   for (int pi = 0; pi < g.n; ++pi) {
     const GemmProblem P = g.p[pi];
     const long long mn = (long long)P.M * P.N;
@@ -145,13 +147,13 @@ cudaError_t launch_gemm_f64(const GemmGroup& g, const double* A, const double* B
       }
     }
   }
-  gemm_f64_nt_kernel<<<(unsigned)(tiles * sk.nsplit), NT, 0, s>>>(g, A, B, C, alpha, accumulate, sk, part);
+  hs_launch(gemm_f64_nt_kernel, (unsigned)(tiles * sk.nsplit), NT, 0, s, g, A, B, C, alpha, accumulate, sk, part);
   if (sk.nsplit > 1) {
     long long mn = 0;
     for (int i = 0; i < g.n; ++i) mn = (long long)g.p[i].M * g.p[i].N > mn ? (long long)g.p[i].M * g.p[i].N : mn;
     long long gx = (mn + 255) / 256;
     if (gx > 4096) gx = 4096;
-    splitk_reduce_kernel<<<(unsigned)gx, 256, 0, s>>>(g, sk, part, C, accumulate);
+    hs_launch(splitk_reduce_kernel, (unsigned)gx, 256, 0, s, g, sk, part, C, accumulate);
   }
   return cudaGetLastError();
 }

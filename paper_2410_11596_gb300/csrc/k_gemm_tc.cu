@@ -221,6 +221,7 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
 template <int NPASS, int EB, int NM>
 __global__ void __launch_bounds__(NT, 1) gemm_tc_kernel(const __grid_constant__ MapsN<NM> maps, const Group g,
                                                         int total_tiles, int* __restrict__ err) {
+  hs_pdl_enter();
   using K = Cfg<NPASS, EB>;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -538,6 +539,7 @@ struct SplitReds {
 };
 
 __global__ void tc_splitk_reduce_kernel(const SplitReds reds) {
+  hs_pdl_enter();
   const SplitRed& r = reds.r[blockIdx.y];
   const long long mn = (long long)r.M * r.N;
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < mn;
@@ -568,7 +570,7 @@ cudaError_t launch_tc(const Maps& all, const Group& g, int grid, int tiles, int*
       maps.a[j][h] = all.a[j][h];
       maps.b[j][h] = all.b[j][h];
     }
-  gemm_tc_kernel<NPASS, EB, NM><<<grid, NT, K::SMEM, s>>>(maps, g, tiles, err);
+  hs_launch(gemm_tc_kernel<NPASS, EB, NM>, grid, NT, K::SMEM, s, maps, g, tiles, err);
   return cudaGetLastError();
 }
 
@@ -653,7 +655,7 @@ cudaError_t run(const TcProblem* probs, int nprob, int* err, cudaStream_t s, dou
     for (int r = 0; r < nred; ++r) mn = std::max(mn, (long long)red[r].M * red[r].N);
     long long gx = (mn + 255) / 256;
     if (gx > 4096) gx = 4096;
-    tc_splitk_reduce_kernel<<<dim3((unsigned)gx, (unsigned)nred), 256, 0, s>>>(reds);
+    hs_launch(tc_splitk_reduce_kernel, dim3((unsigned)gx, (unsigned)nred), 256, 0, s, reds);
   }
   return cudaGetLastError();
 }

@@ -20,6 +20,7 @@ unsigned grid_for(long long n) {
 
 __global__ void graded_sign_kernel(const double* __restrict__ src, double* __restrict__ dst, long long r0,
                                    long long r1, long long c0, long long c1, long long ld, int mode) {
+  hs_pdl_enter();
   const long long cols = c0 + c1, total = (r0 + r1) * cols;
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
        e += (long long)gridDim.x * blockDim.x) {
@@ -45,6 +46,7 @@ __device__ __forceinline__ long long pair_fso(int Xa, int Xb, int qe, int qo) {
 // first D even states of a leg.
 __global__ void init_graded_kernel(const double* __restrict__ a, int D, double* __restrict__ C,
                                    double* __restrict__ T) {
+  hs_pdl_enter();
   const int q = D * D, qe = D * (D + 1) / 2, qo = q - qe;
   const long long q2 = (long long)q * q, nT = (long long)q * q * q;
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < nT + q2;
@@ -93,6 +95,7 @@ __global__ void init_graded_kernel(const double* __restrict__ a, int D, double* 
 template <typename F>
 __global__ void graded_select_kernel(const F* __restrict__ w, const F* __restrict__ V, int n, int chi,
                                      double* __restrict__ PT, SelectOut* sel) {
+  hs_pdl_enter();
   const int k = chi < n ? chi : n;
   const int j = blockIdx.x;
   if (j >= k) return;
@@ -118,13 +121,13 @@ cudaError_t launch_graded_sign(const double* src, double* dst, long long r0, lon
                                long long c1, long long ld, int mode, cudaStream_t s) {
   const long long total = (r0 + r1) * (c0 + c1);
   if (total == 0) return cudaSuccess;
-  graded_sign_kernel<<<grid_for(total), 256, 0, s>>>(src, dst, r0, r1, c0, c1, ld, mode);
+  hs_launch(graded_sign_kernel, grid_for(total), 256, 0, s, src, dst, r0, r1, c0, c1, ld, mode);
   return cudaGetLastError();
 }
 
 cudaError_t launch_ctmrg_init_graded(const double* a, int D, double* C, double* T, cudaStream_t s) {
   const long long q = (long long)D * D;
-  init_graded_kernel<<<grid_for(q * q * q + q * q), 256, 0, s>>>(a, D, C, T);
+  hs_launch(init_graded_kernel, grid_for(q * q * q + q * q), 256, 0, s, a, D, C, T);
   return cudaGetLastError();
 }
 
@@ -132,7 +135,7 @@ cudaError_t launch_graded_select(const double* w, const double* V, int n, int ch
                                  cudaStream_t s) {
   const int k = chi < n ? chi : n;
   if (k <= 0) return cudaErrorInvalidValue;
-  graded_select_kernel<double><<<k, 256, 0, s>>>(w, V, n, chi, PT, sel);
+  hs_launch(graded_select_kernel<double>, k, 256, 0, s, w, V, n, chi, PT, sel);
   return cudaGetLastError();
 }
 
@@ -140,7 +143,7 @@ cudaError_t launch_graded_select32(const float* w, const float* V, int n, int ch
                                    cudaStream_t s) {
   const int k = chi < n ? chi : n;
   if (k <= 0) return cudaErrorInvalidValue;
-  graded_select_kernel<float><<<k, 256, 0, s>>>(w, V, n, chi, PT, sel);
+  hs_launch(graded_select_kernel<float>, k, 256, 0, s, w, V, n, chi, PT, sel);
   return cudaGetLastError();
 }
 

@@ -415,6 +415,7 @@ struct PlanArg {
 // 32-bit range go element by element. T: double or float (scale 1 only).
 template <int NB, class T, bool SCALE>
 __global__ void permute_kernel(PlanArg<NB> plan, const T* __restrict__ in, T* __restrict__ out, double scale) {
+  hs_pdl_enter();
   const Box& b = plan.box[blockIdx.y];
   // plain copies (SCALE false) keep off the FP64 pipe entirely
   auto put = [&](unsigned long long o, T v) {
@@ -498,6 +499,7 @@ __device__ __forceinline__ void store_split(double x, void* hi, void* lo, long l
 template <int MODE, int NB, class T>
 __global__ void permute_split_kernel(PlanArg<NB> plan, const T* __restrict__ in, void* __restrict__ hi,
                                      void* __restrict__ lo) {
+  hs_pdl_enter();
   const Box& b = plan.box[blockIdx.y];
   if (b.plane > 0) {
     permute_planes(b, in, [&](unsigned o, T v) { store_split<MODE>(v, hi, lo, (long long)o); });
@@ -549,9 +551,9 @@ cudaError_t launch_permute_split_t(const PermPlan& plan, const T* in, void* hi, 
     PlanArg<NB> arg;
     for (int i = 0; i < plan.nbox; ++i) arg.box[i] = plan.box[i];
     if (mode == 1)
-      permute_split_kernel<1, NB, T><<<grid, 256, 0, s>>>(arg, in, hi, lo);
+      hs_launch(permute_split_kernel<1, NB, T>, grid, 256, 0, s, arg, in, hi, lo);
     else
-      permute_split_kernel<2, NB, T><<<grid, 256, 0, s>>>(arg, in, hi, lo);
+      hs_launch(permute_split_kernel<2, NB, T>, grid, 256, 0, s, arg, in, hi, lo);
   };
   if (plan.nbox <= 2)
     go(std::integral_constant<int, 2>{});
@@ -575,6 +577,7 @@ cudaError_t launch_permute_split_f32(const PermPlan& plan, const float* in, void
 template <int MODE>
 __global__ void split_pad_kernel(const double* __restrict__ src, long long rows, int cols, long long ld_src,
                                  void* __restrict__ hi, void* __restrict__ lo, long long ld_dst) {
+  hs_pdl_enter();
   const long long total = rows * ld_dst;
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
        e += (long long)gridDim.x * blockDim.x) {
@@ -591,9 +594,9 @@ cudaError_t launch_split_pad(const double* src, long long rows, int cols, long l
   long long gx = (total + 255) / 256;
   if (gx > 4096) gx = 4096;
   if (mode == 1)
-    split_pad_kernel<1><<<(unsigned)gx, 256, 0, s>>>(src, rows, cols, ld_src, hi, lo, ld_dst);
+    hs_launch(split_pad_kernel<1>, (unsigned)gx, 256, 0, s, src, rows, cols, ld_src, hi, lo, ld_dst);
   else
-    split_pad_kernel<2><<<(unsigned)gx, 256, 0, s>>>(src, rows, cols, ld_src, hi, lo, ld_dst);
+    hs_launch(split_pad_kernel<2>, (unsigned)gx, 256, 0, s, src, rows, cols, ld_src, hi, lo, ld_dst);
   return cudaGetLastError();
 }
 
@@ -609,9 +612,9 @@ cudaError_t launch_permute_t(const PermPlan& plan, const T* in, T* out, double s
     PlanArg<NB> arg;
     for (int i = 0; i < plan.nbox; ++i) arg.box[i] = plan.box[i];
     if (scale != 1.0)
-      permute_kernel<NB, T, true><<<grid, 256, 0, s>>>(arg, in, out, scale);
+      hs_launch(permute_kernel<NB, T, true>, grid, 256, 0, s, arg, in, out, scale);
     else
-      permute_kernel<NB, T, false><<<grid, 256, 0, s>>>(arg, in, out, scale);
+      hs_launch(permute_kernel<NB, T, false>, grid, 256, 0, s, arg, in, out, scale);
   };
   if (plan.nbox <= 2)
     go(std::integral_constant<int, 2>{});

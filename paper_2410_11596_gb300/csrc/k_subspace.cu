@@ -27,6 +27,7 @@ __device__ __forceinline__ double hash_uniform(unsigned long long x) {
 
 // rows [r0, m) of X (m x n, row-major) get seeded pseudo-random entries
 __global__ void fill_random_rows_kernel(double* __restrict__ X, int r0, int m, int n, unsigned long long seed) {
+  hs_pdl_enter();
   const long long total = (long long)(m - r0) * n;
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
        e += (long long)gridDim.x * blockDim.x)
@@ -45,6 +46,7 @@ constexpr int kMaxSub = 160;
 __global__ void __launch_bounds__(1024) chol_inv_kernel(const double* __restrict__ G0, int m0,
                                                         double* __restrict__ Linv0, const double* __restrict__ G1,
                                                         int m1, double* __restrict__ Linv1, int* __restrict__ status) {
+  hs_pdl_enter();
   // one CTA per matrix (blockIdx.x)
   const double* G = blockIdx.x ? G1 : G0;
   double* Linv = blockIdx.x ? Linv1 : Linv0;
@@ -95,6 +97,7 @@ __global__ void __launch_bounds__(1024) chol_inv_kernel(const double* __restrict
 // res[i] = || Zr_i - theta_i Xr_i || for the m rows (theta from FP32 values).
 __global__ void residual_kernel(const double* __restrict__ Zr, const double* __restrict__ Xr,
                                 const float* __restrict__ theta, int m, int n, double* __restrict__ res) {
+  hs_pdl_enter();
   const int i = blockIdx.x;
   if (i >= m) return;
   const double t = (double)theta[i];
@@ -115,6 +118,7 @@ __global__ void residual_kernel(const double* __restrict__ Zr, const double* __r
 
 // Canonical sign: the entry of largest modulus of each row is made positive.
 __global__ void row_sign_kernel(double* __restrict__ X, int m, int n) {
+  hs_pdl_enter();
   const int i = blockIdx.x;
   if (i >= m) return;
   double best = -1.0, val = 0.0;
@@ -166,6 +170,7 @@ __device__ __forceinline__ void pair_row(int i, int m0, int n0, int n1, long lon
 // magnitudes compare as integers (IEEE bits without the sign) and the sign
 // flips as a bit: FP64 compares and negations would take the FP64 pipe.
 __global__ void row_sign_pair_kernel(double* __restrict__ X, int m0, int n0, int n1) {
+  hs_pdl_enter();
   long long off;
   int n;
   pair_row(blockIdx.x, m0, n0, n1, off, n);
@@ -207,6 +212,7 @@ __global__ void row_sign_pair_kernel(double* __restrict__ X, int m0, int n0, int
 __global__ void residual_pair_kernel(const double* __restrict__ Zr, const double* __restrict__ Xr,
                                      const float* __restrict__ theta, int m0, int n0, int n1,
                                      double* __restrict__ res) {
+  hs_pdl_enter();
   const int i = blockIdx.x;
   long long off;
   int n;
@@ -231,6 +237,7 @@ __global__ void residual_pair_kernel(const double* __restrict__ Zr, const double
 __global__ void gather_rows_kernel(const double* __restrict__ X0, int n0, const double* __restrict__ X1, int n1,
                                    const int* __restrict__ idx, int chi, const SelectOut* __restrict__ sel,
                                    double* __restrict__ PT, double* __restrict__ P) {
+  hs_pdl_enter();
   const int b = blockIdx.y, j = blockIdx.x;
   const int cb = sel->chi_new[b];
   if (j >= cb) return;
@@ -249,6 +256,7 @@ __global__ void gather_rows_kernel(const double* __restrict__ X0, int n0, const 
 // Indices of the m eigenvalues of largest modulus of one ascending spectrum
 // (both ends of the array), in descending modulus.
 __global__ void top_abs_kernel(const float* __restrict__ w, int n, int m, int* __restrict__ idx) {
+  hs_pdl_enter();
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   int lo = 0, hi = n - 1;
   for (int j = 0; j < m && lo <= hi; ++j) {
@@ -260,6 +268,7 @@ __global__ void top_abs_kernel(const float* __restrict__ w, int n, int m, int* _
 // row j of X (FP64, m x n) = column idx[j] of V (FP32, column-major n x n)
 __global__ void rows_from_columns_kernel(const float* __restrict__ V, int n, const int* __restrict__ idx,
                                          double* __restrict__ X) {
+  hs_pdl_enter();
   const int j = blockIdx.x;
   const float* src = V + (long long)idx[j] * n;
   for (int i = threadIdx.x; i < n; i += blockDim.x) X[(long long)j * n + i] = (double)src[i];
@@ -267,6 +276,7 @@ __global__ void rows_from_columns_kernel(const float* __restrict__ V, int n, con
 
 // Each row of X (m x n) scaled to unit Euclidean norm (zero rows untouched).
 __global__ void row_normalize_kernel(double* __restrict__ X, int m, int n) {
+  hs_pdl_enter();
   const int i = blockIdx.x;
   if (i >= m) return;
   double s = 0.0;
@@ -291,6 +301,7 @@ __global__ void row_normalize_kernel(double* __restrict__ X, int m, int n) {
 // out row i = X row idx[i], i < m (rows of n doubles).
 __global__ void gather_rows_idx_kernel(const double* __restrict__ X, const int* __restrict__ idx, int n,
                                        double* __restrict__ out) {
+  hs_pdl_enter();
   const long long src = (long long)idx[blockIdx.x] * n, dst = (long long)blockIdx.x * n;
   for (int j = threadIdx.x; j < n; j += blockDim.x) out[dst + j] = X[src + j];
 }
@@ -299,6 +310,7 @@ __global__ void gather_rows_idx_kernel(const double* __restrict__ X, const int* 
 // Y = alpha (Z - T) + beta Yold, T and Yold optional (null: zero).
 __global__ void cheb_step_kernel(double* __restrict__ Y, const double* __restrict__ Z, const double* __restrict__ T,
                                  const double* __restrict__ Yold, long long count, double alpha, double beta) {
+  hs_pdl_enter();
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < count;
        e += (long long)gridDim.x * blockDim.x) {
     double v = Z[e];
@@ -314,6 +326,7 @@ __global__ void cheb_step_kernel(double* __restrict__ Y, const double* __restric
 __global__ void gather_rows_idx_pair_kernel(const double* __restrict__ X, long long src_off1, int n0, int n1,
                                             const int* __restrict__ idx, int cnt0, double* __restrict__ out,
                                             long long dst_off1) {
+  hs_pdl_enter();
   const int j = blockIdx.x, b = j >= cnt0;
   const int n = b ? n1 : n0;
   const long long src = (b ? src_off1 : 0) + (long long)idx[j] * n;
@@ -325,6 +338,7 @@ __global__ void gather_rows_idx_pair_kernel(const double* __restrict__ X, long l
 __global__ void cheb_step_pair_kernel(double* __restrict__ Y, const double* __restrict__ Z,
                                       const double* __restrict__ T, const double* __restrict__ Yold, long long count,
                                       long long count0, double alpha0, double alpha1, double beta) {
+  hs_pdl_enter();
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < count;
        e += (long long)gridDim.x * blockDim.x) {
     double v = Z[e];
@@ -357,6 +371,7 @@ constexpr int kBlkPerThread = 4;
 __global__ void __launch_bounds__(1024) jacobi_eig_kernel(float* __restrict__ A0, int m0, float* __restrict__ w0,
                                                          float* __restrict__ A1, int m1, float* __restrict__ w1,
                                                          int* __restrict__ status) {
+  hs_pdl_enter();
   float* Ag = blockIdx.x ? A1 : A0;
   float* wg = blockIdx.x ? w1 : w0;
   const int m = blockIdx.x ? m1 : m0;
@@ -515,53 +530,53 @@ cudaError_t launch_jacobi_eig_pair(float* A0, int m0, float* w0, float* A1, int 
   static const cudaError_t attr_err = cudaFuncSetAttribute(jacobi_eig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)jacobi_smem_bytes(kMaxSub));
   if (attr_err != cudaSuccess) return attr_err;
-  jacobi_eig_kernel<<<2, 1024, jacobi_smem_bytes(m), s>>>(A0, m0, w0, A1, m1, w1, status);
+  hs_launch(jacobi_eig_kernel, 2, 1024, jacobi_smem_bytes(m), s, A0, m0, w0, A1, m1, w1, status);
   return cudaGetLastError();
 }
 
 cudaError_t launch_row_normalize(double* X, int m, int n, cudaStream_t s) {
   if (m <= 0) return cudaSuccess;
-  row_normalize_kernel<<<m, 256, 0, s>>>(X, m, n);
+  hs_launch(row_normalize_kernel, m, 256, 0, s, X, m, n);
   return cudaGetLastError();
 }
 
 cudaError_t launch_gather_rows_idx(const double* X, const int* idx, int m, int n, double* out, cudaStream_t s) {
   if (m <= 0) return cudaSuccess;
-  gather_rows_idx_kernel<<<m, 256, 0, s>>>(X, idx, n, out);
+  hs_launch(gather_rows_idx_kernel, m, 256, 0, s, X, idx, n, out);
   return cudaGetLastError();
 }
 
 cudaError_t launch_cheb_step(double* Y, const double* Z, const double* T, const double* Yold, long long count,
                              double alpha, double beta, cudaStream_t s) {
   if (count <= 0) return cudaSuccess;
-  cheb_step_kernel<<<grid_for(count), 256, 0, s>>>(Y, Z, T, Yold, count, alpha, beta);
+  hs_launch(cheb_step_kernel, grid_for(count), 256, 0, s, Y, Z, T, Yold, count, alpha, beta);
   return cudaGetLastError();
 }
 
 cudaError_t launch_gather_rows_idx_pair(const double* X, long long src_off1, int n0, int n1, const int* idx,
                                         int cnt0, int cnt1, double* out, long long dst_off1, cudaStream_t s) {
   if (cnt0 + cnt1 <= 0) return cudaSuccess;
-  gather_rows_idx_pair_kernel<<<cnt0 + cnt1, 256, 0, s>>>(X, src_off1, n0, n1, idx, cnt0, out, dst_off1);
+  hs_launch(gather_rows_idx_pair_kernel, cnt0 + cnt1, 256, 0, s, X, src_off1, n0, n1, idx, cnt0, out, dst_off1);
   return cudaGetLastError();
 }
 
 cudaError_t launch_cheb_step_pair(double* Y, const double* Z, const double* T, const double* Yold, long long count,
                                   long long count0, double alpha0, double alpha1, double beta, cudaStream_t s) {
   if (count <= 0) return cudaSuccess;
-  cheb_step_pair_kernel<<<grid_for(count), 256, 0, s>>>(Y, Z, T, Yold, count, count0, alpha0, alpha1, beta);
+  hs_launch(cheb_step_pair_kernel, grid_for(count), 256, 0, s, Y, Z, T, Yold, count, count0, alpha0, alpha1, beta);
   return cudaGetLastError();
 }
 
 cudaError_t launch_top_rows(const float* w, const float* V, int n, int m, int* idx, double* X, cudaStream_t s) {
   if (m <= 0) return cudaSuccess;
-  top_abs_kernel<<<1, 32, 0, s>>>(w, n, m, idx);
-  rows_from_columns_kernel<<<m, 256, 0, s>>>(V, n, idx, X);
+  hs_launch(top_abs_kernel, 1, 32, 0, s, w, n, m, idx);
+  hs_launch(rows_from_columns_kernel, m, 256, 0, s, V, n, idx, X);
   return cudaGetLastError();
 }
 
 cudaError_t launch_fill_random_rows(double* X, int r0, int m, int n, unsigned long long seed, cudaStream_t s) {
   if (r0 >= m) return cudaSuccess;
-  fill_random_rows_kernel<<<grid_for((long long)(m - r0) * n), 256, 0, s>>>(X, r0, m, n, seed);
+  hs_launch(fill_random_rows_kernel, grid_for((long long)(m - r0) * n), 256, 0, s, X, r0, m, n, seed);
   return cudaGetLastError();
 }
 
@@ -575,40 +590,40 @@ cudaError_t launch_chol_inv(const double* G0, int m0, double* Linv0, const doubl
   static const cudaError_t attr_err = cudaFuncSetAttribute(chol_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          kMaxSub * (kMaxSub + 1) * (int)sizeof(double));
   if (attr_err != cudaSuccess) return attr_err;
-  chol_inv_kernel<<<2, 1024, smem, s>>>(G0, m0, Linv0, G1, m1, Linv1, status);
+  hs_launch(chol_inv_kernel, 2, 1024, smem, s, G0, m0, Linv0, G1, m1, Linv1, status);
   return cudaGetLastError();
 }
 
 cudaError_t launch_residual(const double* Zr, const double* Xr, const float* theta, int m, int n, double* res,
                             cudaStream_t s) {
   if (m <= 0) return cudaSuccess;
-  residual_kernel<<<m, 256, 0, s>>>(Zr, Xr, theta, m, n, res);
+  hs_launch(residual_kernel, m, 256, 0, s, Zr, Xr, theta, m, n, res);
   return cudaGetLastError();
 }
 
 cudaError_t launch_row_sign_pair(double* X, int m0, int n0, int m1, int n1, cudaStream_t s) {
   if (m0 + m1 <= 0) return cudaSuccess;
-  row_sign_pair_kernel<<<m0 + m1, 256, 0, s>>>(X, m0, n0, n1);
+  hs_launch(row_sign_pair_kernel, m0 + m1, 256, 0, s, X, m0, n0, n1);
   return cudaGetLastError();
 }
 
 cudaError_t launch_residual_pair(const double* Zr, const double* Xr, const float* theta, int m0, int n0, int m1,
                                  int n1, double* res, cudaStream_t s) {
   if (m0 + m1 <= 0) return cudaSuccess;
-  residual_pair_kernel<<<m0 + m1, 256, 0, s>>>(Zr, Xr, theta, m0, n0, n1, res);
+  hs_launch(residual_pair_kernel, m0 + m1, 256, 0, s, Zr, Xr, theta, m0, n0, n1, res);
   return cudaGetLastError();
 }
 
 cudaError_t launch_row_sign(double* X, int m, int n, cudaStream_t s) {
   if (m <= 0) return cudaSuccess;
-  row_sign_kernel<<<m, 256, 0, s>>>(X, m, n);
+  hs_launch(row_sign_kernel, m, 256, 0, s, X, m, n);
   return cudaGetLastError();
 }
 
 cudaError_t launch_gather_rows(const double* X0, int n0, const double* X1, int n1, const int* idx, int chi,
                                const SelectOut* sel, double* PT, double* P, cudaStream_t s) {
   dim3 grid((unsigned)chi, 2);
-  gather_rows_kernel<<<grid, 256, 0, s>>>(X0, n0, X1, n1, idx, chi, sel, PT, P);
+  hs_launch(gather_rows_kernel, grid, 256, 0, s, X0, n0, X1, n1, idx, chi, sel, PT, P);
   return cudaGetLastError();
 }
 
