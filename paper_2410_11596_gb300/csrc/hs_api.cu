@@ -903,7 +903,7 @@ hs_status subspace_projector(hs_ctx ctx, hs_env* env, int chi, int n0, int n1, d
     double* const Xco[2] = {ctx->sxc.d(0), ctx->sxc.d(1)};
     HS_TRY(orthonormalise_rows(ctx, prec, Xo, m, n, Xco, bad));
   }
-  if (tc) {
+  if (tc && !(ctx->sH_fresh && ctx->sH_n[0] == n0 && ctx->sH_n[1] == n1)) {
     const size_t es = ctx->cp_f32 ? sizeof(float) : sizeof(double);
     if (reinterpret_cast<const char*>(H1) != reinterpret_cast<const char*>(H0) + (size_t)n0 * n0 * es)
       return fail(HS_ERR_INVALID_ARG, "corner blocks not stacked");
@@ -1407,7 +1407,12 @@ hs_status hs_ctmrg_move(hs_ctx ctx, const hs_z2_tensor* a, hs_env* env, int chi,
     PhaseScope ps(ctx, HS_PHASE_GEMM);
     HS_TRY(gemm(ctx, be, g3, B2, a->data, B1));
   }
-  {
+  // C' = X3 with legs (a,e,d,r) -> (a,d,e,r). With the subspace solver and
+  // tensor cores, X3 goes straight into the split C' operand; the FP32 C'
+  // itself is formed only when a fallback eigensolver needs it
+  bool cp_ready = false;
+  auto form_corner = [&]() -> hs_status {
+    if (cp_ready) return HS_OK;
     PhaseScope ps(ctx, HS_PHASE_PERMUTE);
     if (f32c) {
       const int pm[kMaxLegs] = {0, 2, 1, 3, 0, 0};
@@ -1415,8 +1420,19 @@ hs_status hs_ctmrg_move(hs_ctx ctx, const hs_z2_tensor* a, hs_env* env, int chi,
                                  reinterpret_cast<float*>(B2), s));
       ctx->launches += 1;
     } else {
-      HS_TRY(permute(ctx, X3, Cp, {0, 2, 1, 3}, B1, B2));  // (a,e,d,r) -> (a,d,e,r)
+      HS_TRY(permute(ctx, X3, Cp, {0, 2, 1, 3}, B1, B2));
     }
+    cp_ready = true;
+    return HS_OK;
+  };
+  if (f32c && env->eig_mode == HS_EIG_SUBSPACE) {
+    HS_TRY(tc_split_f32(ctx, env->precision, X3, Cp, {0, 2, 1, 3}, reinterpret_cast<const float*>(B1), ctx->sH_hi,
+                        ctx->sH_lo));
+    ctx->sH_n[0] = (int)z2_rows(Cp, 0);
+    ctx->sH_n[1] = (int)z2_rows(Cp, 1);
+    ctx->sH_fresh = true;
+  } else {
+    HS_TRY(form_corner());
   }
 
   // one eigen-decomposition per parity block (C' blocks stacked in B2: FP32
@@ -1462,6 +1478,7 @@ hs_status hs_ctmrg_move(hs_ctx ctx, const hs_z2_tensor* a, hs_env* env, int chi,
     V1f = V0f + (long long)n0 * n0;
     float* w32 = static_cast<float*>(ctx->w32.p);
     PhaseScope ps(ctx, HS_PHASE_EIG);
+    HS_TRY(form_corner());
     if (f32c)
       HS_CUDA(cudaMemcpyAsync(V0f, V0, nn * sizeof(float), cudaMemcpyDeviceToDevice, s));
     else
