@@ -188,6 +188,86 @@ __global__ void select_kernel(const double* __restrict__ w0g, int n0, const doub
   }
 }
 
+// select_kernel for small spectra (n0 + n1 <= kRankMax), by ranks instead of
+// a serial merge: element e's rank is the number of elements that come before
+// it in the merge order (larger |w| first; on equal |w| block 0 first, then
+// the low end of a block before its high end, then the element nearer its end),
+// so the kept states, their pick order and every output equal the merge's.
+// One CTA of kRankMax threads.
+constexpr int kRankMax = 1024;
+
+__global__ void __launch_bounds__(kRankMax) select_rank_kernel(const double* __restrict__ w0g, int n0,
+                                                               const double* __restrict__ w1g, int n1, int chi,
+                                                               int* __restrict__ idx, double* __restrict__ lam,
+                                                               SelectOut* out) {
+  hs_pdl_enter();
+  __shared__ unsigned long long mag[kRankMax];
+  __shared__ unsigned tie[kRankMax];  // block << 31 | side << 30 | distance from the end
+  __shared__ short inv[kRankMax];     // element of each rank
+  __shared__ int pre[kRankMax];       // block-1 picks among ranks < r (inclusive scan, then shifted)
+  __shared__ double part[kRankMax / 32];
+  constexpr unsigned long long kMag = 0x7FFFFFFFFFFFFFFFull;
+  const int N = n0 + n1, keep = min(chi, N), t = threadIdx.x;
+  double wv = 0.0;
+  if (t < N) {
+    const int b = t >= n0, i = b ? t - n0 : t, nb = b ? n1 : n0;
+    wv = b ? w1g[i] : w0g[i];
+    const unsigned long long u = (unsigned long long)__double_as_longlong(wv);
+    const int side = (u >> 63) ? 0 : 1;  // negative values come off the low end
+    mag[t] = u & kMag;
+    tie[t] = ((unsigned)b << 31) | ((unsigned)side << 30) | (unsigned)(side ? nb - 1 - i : i);
+  }
+  __syncthreads();
+  int rank = 0;
+  if (t < N) {
+    const unsigned long long me = mag[t];
+    const unsigned mt = tie[t];
+    for (int f = 0; f < N; ++f) {
+      const unsigned long long o = mag[f];
+      rank += (o > me) || (o == me && tie[f] < mt);
+    }
+    inv[rank] = (short)t;
+  }
+  // sum of |w| over both spectra minus the kept ones: the discarded weight
+  double dw = (t < N && rank >= keep) ? fabs(wv) : 0.0;
+  for (int o = 16; o > 0; o >>= 1) dw += __shfl_xor_sync(0xffffffffu, dw, o);
+  if ((t & 31) == 0) part[t >> 5] = dw;
+  __syncthreads();
+  // block-1 flags in pick order, inclusive scan
+  pre[t] = (t < keep && inv[t] >= n0) ? 1 : 0;
+  __syncthreads();
+  for (int o = 1; o < kRankMax; o <<= 1) {
+    const int v = t >= o ? pre[t - o] : 0;
+    __syncthreads();
+    pre[t] += v;
+    __syncthreads();
+  }
+  const int ones = keep > 0 ? pre[keep - 1] : 0, cnt0 = keep - ones;
+  if (t < keep) {
+    const int e = inv[t], b = e >= n0, i = b ? e - n0 : e;
+    const int before1 = pre[t] - b;  // block-1 picks among ranks < t
+    const double v = b ? w1g[i] : w0g[i];
+    if (b) {
+      idx[chi + before1] = i;
+      lam[cnt0 + before1] = v;
+    } else {
+      const int p0 = t - before1;
+      idx[p0] = i;
+      lam[p0] = v;
+    }
+  }
+  if (t == 0) {
+    double disc = 0.0;
+    for (int w = 0; w < kRankMax / 32; ++w) disc += part[w];
+    out->discarded = disc;
+    out->chi_new[0] = cnt0;
+    out->chi_new[1] = ones;
+    out->lam_max = keep > 0 ? __longlong_as_double((long long)mag[inv[0]]) : 0.0;
+    out->lam_cut = keep > 0 ? __longlong_as_double((long long)mag[inv[keep - 1]]) : 0.0;
+    out->lam_next = keep < N ? __longlong_as_double((long long)mag[inv[keep]]) : 0.0;
+  }
+}
+
 __global__ void gather_pt_kernel(const double* __restrict__ V0, int n0, const double* __restrict__ V1,
                                  int n1, const int* __restrict__ idx, int chi,
                                  const SelectOut* __restrict__ sel, double* __restrict__ PT) {
@@ -451,6 +531,10 @@ cudaError_t launch_ctmrg_init(const double* a_blocks, int D, bool hermitian, dou
 
 cudaError_t launch_select(const double* w0, int n0, const double* w1, int n1, int chi, int* idx,
                           double* lam, SelectOut* out, cudaStream_t s) {
+  if (n0 + n1 <= kRankMax) {
+    hs_launch(select_rank_kernel, 1, kRankMax, 0, s, w0, n0, w1, n1, chi, idx, lam, out);
+    return cudaGetLastError();
+  }
   constexpr size_t kSmemMax = 160 * 1024;
   const int keep = chi < n0 + n1 ? chi : n0 + n1;
   const size_t picks = (size_t)keep * (sizeof(double) + 1);
