@@ -349,51 +349,95 @@ __global__ void cheb_step_pair_kernel(double* __restrict__ Y, const double* __re
   }
 }
 
-// Symmetric eigen-decomposition of one small FP32 matrix per CTA by the
-// cyclic Jacobi method (Golub and Van Loan, Sec. 8.5) with the round-robin
-// ordering, so that the m/2 rotations of a round touch disjoint rows and
-// columns and are applied together: A <- J^T A J, V <- V J. The Rayleigh
-// matrices of the warm-started subspace iteration are nearly diagonal, where
-// Jacobi converges quadratically in a few sweeps. Output as cuSOLVER's syevd:
-// eigenvalues ascending in w, eigenvectors as the columns of the column-major
-// m x m array A (overwritten). A rotation is skipped when |A_pq| <= tol
-// sqrt|A_pp A_qq|, tol = max(4e-7, sqrt(m) eps_32) (the relative criterion of
-// Demmel and Veselic, SIAM J. Matrix Anal. Appl. 13, 1992), or when |A_pq| is
-// below 1e-7 max|A_ii| (FP32 rounding noise of the input); converged after a
-// sweep without rotations.
-// After kMaxSweeps without that, *status = 1.
+// Symmetric eigen-decomposition of one small FP32 matrix by the cyclic Jacobi
+// method (Golub and Van Loan, Sec. 8.5) with the round-robin ordering, so that
+// the m/2 rotations of a round touch disjoint rows and columns and are applied
+// together: A <- J^T A J, V <- V J. The Rayleigh matrices of the warm-started
+// subspace iteration are nearly diagonal, where Jacobi converges
+// quadratically in a few sweeps. Output as cuSOLVER's syevd: eigenvalues
+// ascending in w, eigenvectors as the columns of the column-major m x m array
+// A (overwritten). A rotation is skipped when |A_pq| <= tol sqrt|A_pp A_qq|,
+// tol = max(4e-7, sqrt(m) eps_32) (the relative criterion of Demmel and
+// Veselic, SIAM J. Matrix Anal. Appl. 13, 1992), or when |A_pq| is below
+// 1e-7 max|A_ii| (FP32 rounding noise of the input); converged after a sweep
+// without rotations. After kMaxSweeps without that, *status = 1.
+//
+// One cluster of kJacobiCtas CTAs per matrix. Every CTA of the cluster runs
+// the same rotations on its own copy of A (identical arithmetic on identical
+// data, so the copies and the convergence decision agree bit for bit) and
+// accumulates V only for its slice of the eigenvector components: the work of
+// a round is shared-memory bound, and V is the larger half of it. A is kept as
+// its upper triangle, so a 2 x 2 block of a round is read and written once.
 constexpr int kMaxSweeps = 40;
+constexpr int kJacobiCtas = 4;
 
-// Blocks (a, b), a <= b, of the 2 x 2 block grid that thread `t` updates in
-// every round, packed a << 16 | b (at most kBlkPerThread per thread).
+// Blocks (a, b), a <= b, of the pair grid that a thread updates in every
+// round, packed a << 16 | b, and V entries (pair, component) packed the same
+// way (at most kBlkPerThread and kVPerThread per thread).
 constexpr int kBlkPerThread = 4;
+constexpr int kVPerThread = 4;
+
+// Pair k of round r in the round-robin ordering of M players (player M-1
+// fixed, the others rotating), as (p, q) with p < q.
+__device__ __forceinline__ int2 rr_pair(int k, int r, int M) {
+  int p, q;
+  if (k == 0) {
+    p = r;
+    q = M - 1;
+  } else {
+    p = r + k;
+    if (p >= M - 1) p -= M - 1;
+    q = r - k;
+    if (q < 0) q += M - 1;
+    if (p > q) {
+      const int t = p;
+      p = q;
+      q = t;
+    }
+  }
+  return make_int2(p, q);
+}
+
+__device__ __forceinline__ int cluster_rank() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return (int)r;
+}
 
 __global__ void __launch_bounds__(1024) jacobi_eig_kernel(float* __restrict__ A0, int m0, float* __restrict__ w0,
                                                          float* __restrict__ A1, int m1, float* __restrict__ w1,
                                                          int* __restrict__ status) {
   hs_pdl_enter();
-  float* Ag = blockIdx.x ? A1 : A0;
-  float* wg = blockIdx.x ? w1 : w0;
-  const int m = blockIdx.x ? m1 : m0;
-  if (m <= 0) return;
+  const int mat = blockIdx.x / kJacobiCtas, g = cluster_rank();
+  float* Ag = mat ? A1 : A0;
+  float* wg = mat ? w1 : w0;
+  const int m = mat ? m1 : m0;
+  if (m <= 0) return;  // the whole cluster returns
   extern __shared__ float shj[];
   const int ld = m + 1;
-  float* A = shj;                 // m x ld
-  float* Vt = A + m * ld;         // m x ld, Vt[j * ld + i] = component i of vector j
-  float2* cs = reinterpret_cast<float2*>(Vt + m * ld);  // (cos, sin) per pair
-  int2* pq = reinterpret_cast<int2*>(cs + ((m + 1) / 2 + 1));
-  const int M = (m + 1) & ~1;     // even player count (index m is a dummy when m is odd)
+  const int mc = (m + kJacobiCtas - 1) / kJacobiCtas;  // components per CTA
+  const int i0 = g * mc, nc = max(0, min(m, i0 + mc) - i0);
+  float* A = shj;                                           // upper triangle of m x ld
+  float* Vt = A + m * ld;                                   // m x mc: Vt[j * mc + i] = component i0 + i of vector j
+  float2* cs = reinterpret_cast<float2*>(Vt + ((m * mc + 1) & ~1));  // (cos, sin) per pair (8-byte aligned)
+  const int M = (m + 1) & ~1;  // even player count (index m is a dummy when m is odd)
   const int npair = M / 2;
   const float kRelTol = fmaxf(4e-7f, sqrtf((float)m) * 6e-8f);
   __shared__ float dmax_part[32];
   float dm = 0.f;
   for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
     const int i = e / m, j = e % m;
+    if (j < i) continue;
     const float v = 0.5f * (Ag[i * m + j] + Ag[j * m + i]);
     A[i * ld + j] = v;
-    Vt[i * ld + j] = i == j ? 1.f : 0.f;
     if (i == j) dm = fmaxf(dm, fabsf(v));
   }
+  for (int e = threadIdx.x; e < m * mc; e += blockDim.x) {
+    const int j = e / mc, i = e % mc;
+    Vt[e] = i0 + i == j ? 1.f : 0.f;
+  }
+  // every CTA of the cluster has read Ag before any of them overwrites it
+  asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
   for (int o = 16; o > 0; o >>= 1) dm = fmaxf(dm, __shfl_xor_sync(0xffffffffu, dm, o));
   if ((threadIdx.x & 31) == 0) dmax_part[threadIdx.x >> 5] = dm;
   // this thread's blocks of the upper block triangle, in row-major order
@@ -415,31 +459,35 @@ __global__ void __launch_bounds__(1024) jacobi_eig_kernel(float* __restrict__ A0
       }
     }
   }
+  // this thread's V entries: pair b, local component i (consecutive threads
+  // take consecutive components)
+  int ven[kVPerThread];
+  int nven = 0;
+#pragma unroll
+  for (int t = 0; t < kVPerThread; ++t) {
+    const int f = threadIdx.x + t * blockDim.x;
+    ven[t] = -1;
+    if (nc > 0 && f < npair * nc) {
+      ven[t] = ((f / nc) << 16) | (f % nc);
+      nven = t + 1;
+    }
+  }
   __syncthreads();
   float dmax = 0.f;
   for (int w = 0; w < (int)(blockDim.x >> 5); ++w) dmax = fmaxf(dmax, dmax_part[w]);
   // off-diagonal entries below this are rounding noise of the FP32 matrix
   const float abs_floor = 1e-7f * dmax;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   bool converged = false;
   for (int sweep = 0; sweep < kMaxSweeps && !converged; ++sweep) {
     int nrot = 0;  // rotations in this sweep (the same in every thread)
     for (int r = 0; r < M - 1; ++r) {
       int rotates = 0;
-      // round-robin pairing: player M-1 fixed, the others rotate
       for (int k = threadIdx.x; k < npair; k += blockDim.x) {
-        int p = k == 0 ? M - 1 : (r + k) % (M - 1);
-        int q = (r + M - 1 - k) % (M - 1);
-        if (k == 0) q = r;
-        if (p > q) {
-          const int t = p;
-          p = q;
-          q = t;
-        }
+        const int2 pq = rr_pair(k, r, M);
         float c = 1.f, sn = 0.f;
-        if (q < m) {
-          const float apq = A[p * ld + q];
-          const float app = A[p * ld + p], aqq = A[q * ld + q];
+        if (pq.y < m) {
+          const float apq = A[pq.x * ld + pq.y];
+          const float app = A[pq.x * ld + pq.x], aqq = A[pq.y * ld + pq.y];
           // rotate unless A_pq is negligible against its diagonal pair
           if (fabsf(apq) > abs_floor && fabsf(apq) > 1e-30f && fabsf(apq) > kRelTol * sqrtf(fabsf(app * aqq))) {
             const float th = (aqq - app) / (2.f * apq);
@@ -449,57 +497,58 @@ __global__ void __launch_bounds__(1024) jacobi_eig_kernel(float* __restrict__ A0
             rotates = 1;
           }
         }
-        pq[k] = make_int2(p, q);
         cs[k] = make_float2(c, sn);
       }
       const int rrot = __syncthreads_count(rotates);
       if (rrot == 0) continue;  // nothing rotates in this round (block-uniform)
       nrot += rrot;
       // A <- J^T A J: the rotations act on disjoint pairs, so every 2 x 2 block
-      // (rows of pair a, columns of pair b) transforms on its own; A stays
-      // symmetric, so only blocks a <= b are computed and mirrored
+      // (rows of pair a, columns of pair b) transforms on its own; an entry
+      // lives at its upper-triangle position (min, max)
 #pragma unroll
       for (int t = 0; t < kBlkPerThread; ++t) {
         if (t >= nblk) break;
         const int a = blk[t] >> 16, b = blk[t] & 0xffff;
-        const int2 ia = pq[a], ib = pq[b];
+        const int2 ia = rr_pair(a, r, M), ib = rr_pair(b, r, M);
         const float2 ra_ = cs[a], rb_ = cs[b];
         const bool ra = ia.y < m, rb = ib.y < m;
-        const float a00 = A[ia.x * ld + ib.x];
-        const float a01 = rb ? A[ia.x * ld + ib.y] : 0.f;
-        const float a10 = ra ? A[ia.y * ld + ib.x] : 0.f;
-        const float a11 = (ra && rb) ? A[ia.y * ld + ib.y] : 0.f;
+        // (pa, pb), (pa, qb), (qa, pb), (qa, qb) at their upper positions
+        const int e00 = min(ia.x, ib.x) * ld + max(ia.x, ib.x);
+        const int e01 = min(ia.x, ib.y) * ld + max(ia.x, ib.y);
+        const int e10 = min(ia.y, ib.x) * ld + max(ia.y, ib.x);
+        const int e11 = min(ia.y, ib.y) * ld + max(ia.y, ib.y);
+        const float a00 = A[e00];
+        const float a01 = rb ? A[e01] : 0.f;
+        const float a10 = ra ? A[e10] : 0.f;
+        const float a11 = (ra && rb) ? A[e11] : 0.f;
         const float t00 = ra_.x * a00 - ra_.y * a10, t01 = ra_.x * a01 - ra_.y * a11;
         const float t10 = ra_.y * a00 + ra_.x * a10, t11 = ra_.y * a01 + ra_.x * a11;
         const float n00 = rb_.x * t00 - rb_.y * t01, n01 = rb_.y * t00 + rb_.x * t01;
         const float n10 = rb_.x * t10 - rb_.y * t11, n11 = rb_.y * t10 + rb_.x * t11;
-        A[ia.x * ld + ib.x] = n00;
-        if (rb) A[ia.x * ld + ib.y] = n01;
-        if (ra) A[ia.y * ld + ib.x] = n10;
-        if (ra && rb) A[ia.y * ld + ib.y] = n11;
-        if (a != b) {
-          A[ib.x * ld + ia.x] = n00;
-          if (rb) A[ib.y * ld + ia.x] = n01;
-          if (ra) A[ib.x * ld + ia.y] = n10;
-          if (ra && rb) A[ib.y * ld + ia.y] = n11;
-        }
+        A[e00] = n00;
+        if (rb) A[e01] = n01;
+        // on the diagonal block (a == b) entry (qa, pa) is (pa, qa) again
+        if (ra && a != b) A[e10] = n10;
+        if (ra && rb) A[e11] = n11;
       }
-      // V <- V J on the rows of Vt: one pair per warp, lanes along the vector
-      for (int b = warp; b < npair; b += nw) {
-        const int2 ib = pq[b];
+      // V <- V J on this CTA's components
+#pragma unroll
+      for (int t = 0; t < kVPerThread; ++t) {
+        if (t >= nven) break;
+        const int b = ven[t] >> 16, i = ven[t] & 0xffff;
         const float2 rb_ = cs[b];
-        if (ib.y >= m || (rb_.x == 1.f && rb_.y == 0.f)) continue;  // warp-uniform
-        for (int i = lane; i < m; i += 32) {
-          const float vp = Vt[ib.x * ld + i], vq = Vt[ib.y * ld + i];
-          Vt[ib.x * ld + i] = rb_.x * vp - rb_.y * vq;
-          Vt[ib.y * ld + i] = rb_.y * vp + rb_.x * vq;
-        }
+        if (rb_.x == 1.f && rb_.y == 0.f) continue;  // no rotation (or the dummy pair)
+        const int2 ib = rr_pair(b, r, M);
+        const float vp = Vt[ib.x * mc + i], vq = Vt[ib.y * mc + i];
+        Vt[ib.x * mc + i] = rb_.x * vp - rb_.y * vq;
+        Vt[ib.y * mc + i] = rb_.y * vp + rb_.x * vq;
       }
       __syncthreads();
     }
     converged = nrot == 0;  // a sweep without a rotation: every A_pq is negligible
   }
-  if (!converged && threadIdx.x == 0) atomicExch(status, 1);
+  if (!converged && g == 0 && threadIdx.x == 0) atomicExch(status, 1);
+  asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
   // ascending order by rank (ties by index); vectors as columns, column-major
   for (int j = threadIdx.x; j < m; j += blockDim.x) {
     const float lj = A[j * ld + j];
@@ -508,15 +557,16 @@ __global__ void __launch_bounds__(1024) jacobi_eig_kernel(float* __restrict__ A0
       const float li = A[i * ld + i];
       rank += (li < lj) || (li == lj && i < j);
     }
-    wg[rank] = lj;
-    for (int i = 0; i < m; ++i) Ag[(long long)rank * m + i] = Vt[j * ld + i];
+    if (g == 0) wg[rank] = lj;
+    for (int i = 0; i < nc; ++i) Ag[(long long)rank * m + i0 + i] = Vt[j * mc + i];
   }
 }
 
 }  // namespace
 
 size_t jacobi_smem_bytes(int m) {
-  return (size_t)(2 * m * (m + 1) + 2 * ((m + 1) / 2 + 1)) * sizeof(float) + (size_t)((m + 1) / 2 + 1) * 2 * sizeof(int);
+  const int mc = (m + kJacobiCtas - 1) / kJacobiCtas;
+  return (size_t)(m * (m + 1) + ((m * mc + 1) & ~1)) * sizeof(float) + (size_t)((m + 1) / 2 + 1) * sizeof(float2);
 }
 
 cudaError_t launch_jacobi_eig_pair(float* A0, int m0, float* w0, float* A1, int m1, float* w1, int* status,
@@ -524,13 +574,17 @@ cudaError_t launch_jacobi_eig_pair(float* A0, int m0, float* w0, float* A1, int 
   const int m = m0 > m1 ? m0 : m1;
   if (m <= 0) return cudaSuccess;
   // m <= kMaxSub keeps the (m/2)(m/2 + 1)/2 blocks of a round within kBlkPerThread per thread
+  // and the (m/2) ceil(m / kJacobiCtas) V entries within kVPerThread
   static_assert((kMaxSub / 2 + 1) * (kMaxSub / 2 + 2) / 2 <= kBlkPerThread * 1024, "block grid too large");
+  static_assert((kMaxSub / 2 + 1) * ((kMaxSub + kJacobiCtas - 1) / kJacobiCtas) <= kVPerThread * 1024,
+                "V slice too large");
   if (m > kMaxSub) return cudaErrorInvalidValue;
   // set once per process (thread-safe static initialisation)
   static const cudaError_t attr_err = cudaFuncSetAttribute(jacobi_eig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)jacobi_smem_bytes(kMaxSub));
   if (attr_err != cudaSuccess) return attr_err;
-  hs_launch(jacobi_eig_kernel, 2, 1024, jacobi_smem_bytes(m), s, A0, m0, w0, A1, m1, w1, status);
+  hs_launch_cluster(jacobi_eig_kernel, 2 * kJacobiCtas, 1024, jacobi_smem_bytes(m), s, kJacobiCtas, A0, m0, w0, A1,
+                    m1, w1, status);
   return cudaGetLastError();
 }
 
