@@ -245,28 +245,41 @@ hs_status tc_split_f32(hs_ctx ctx, hs_precision prec, const Z2Mat& src_layout, c
   return tc_split_any(ctx, prec, src_layout, layout, perm, src, true, hi, lo);
 }
 
-hs_status tc_split_any(hs_ctx ctx, hs_precision prec, const Z2Mat& src_layout, const Z2Mat& layout,
-                       std::initializer_list<int> perm, const void* src, bool src_f32, DBuf& hi, DBuf& lo) {
-  const int pad = tc_pad(prec), eb = tc_elem_bytes(prec);
-  const Z2Mat P = mat(layout.r, layout.c, pad);
+// Sizes the split buffers of the padded operand layout P and zeroes their K
+// padding unless the last split into them had the same layout (a split
+// writes every entry of the layout but none of the padding).
+hs_status split_dest(hs_ctx ctx, hs_precision prec, const Z2Mat& P, DBuf& hi, DBuf& lo) {
+  const int eb = tc_elem_bytes(prec);
   const size_t nb = (size_t)z2_elems(P) * eb;
   HS_TRY(hi.ensure(nb));
   HS_TRY(lo.ensure(nb));
-  PhaseScope ps(ctx, HS_PHASE_PERMUTE);
-  int pm[kMaxLegs] = {0}, i = 0;
-  for (int v : perm) pm[i++] = v;
-  // the split writes every entry of the layout but none of the K padding:
-  // zero the buffers only when the last split into them had another layout
   unsigned long long key = 0x9E3779B97F4A7C15ull ^ (unsigned long long)eb;
   for (int p = 0; p < 2; ++p)
     for (long long v : {z2_rows(P, p), z2_cols(P, p), z2_ld(P, p)})
       key = (key ^ (unsigned long long)v) * 0x100000001B3ull;
   key |= 1;
   if (hi.zkey != key || lo.zkey != key) {
-    HS_CUDA(cudaMemsetAsync(hi.p, 0, nb, ctx->stream));
-    HS_CUDA(cudaMemsetAsync(lo.p, 0, nb, ctx->stream));
+    // only the K padding of each block row (the rest is written below)
+    for (int p = 0; p < 2; ++p) {
+      const long long rows = z2_rows(P, p), cols = z2_cols(P, p), ld = z2_ld(P, p);
+      if (rows == 0 || ld == cols) continue;
+      const size_t off = (size_t)(z2_block_off(P, p) + cols) * eb;
+      for (DBuf* b : {&hi, &lo})
+        HS_CUDA(cudaMemset2DAsync(static_cast<char*>(b->p) + off, (size_t)ld * eb, 0, (size_t)(ld - cols) * eb,
+                                  (size_t)rows, ctx->stream));
+    }
     hi.zkey = lo.zkey = key;
   }
+  return HS_OK;
+}
+
+hs_status tc_split_any(hs_ctx ctx, hs_precision prec, const Z2Mat& src_layout, const Z2Mat& layout,
+                       std::initializer_list<int> perm, const void* src, bool src_f32, DBuf& hi, DBuf& lo) {
+  const Z2Mat P = mat(layout.r, layout.c, tc_pad(prec));
+  PhaseScope ps(ctx, HS_PHASE_PERMUTE);
+  HS_TRY(split_dest(ctx, prec, P, hi, lo));
+  int pm[kMaxLegs] = {0}, i = 0;
+  for (int v : perm) pm[i++] = v;
   const PermPlan& plan = cached_plan(ctx, src_layout, P, pm);
   if (src_f32)
     HS_CUDA(launch_permute_split_f32(plan, static_cast<const float*>(src), hi.p, lo.p, tc_mode(prec), ctx->stream));
@@ -308,6 +321,107 @@ hs_status tc_run(hs_ctx ctx, hs_precision prec, const Z2Mat& A, const DBuf& ahi,
   HS_TRY(ctx->splitk.ensure(kSplitKElems * sizeof(double)));
   PhaseScope ps(ctx, HS_PHASE_GEMM_TC);
   HS_CUDA(launch_gemm_tc(prec, pr, n, static_cast<int*>(ctx->tc_err.p), ctx->stream, ctx->splitk.d(), kSplitKElems));
+  if (n > 0) ctx->launches += 1;
+  return HS_OK;
+}
+
+// Destination map of a GEMM output block of parity p (layout Cm: two-leg
+// rows L0 L1, two-leg columns L2 L3) written as the padded split operand P,
+// whose legs are Cm's permuted by perm. False when the epilogue cannot write
+// it (other leg counts, a destination whose innermost leg is neither L1 nor
+// L3, offsets beyond 32 bits).
+bool make_ps_desc(const Z2Mat& Cm, const Z2Mat& P, const int perm[4], int p, void* hi, void* lo, PsDesc& d) {
+  if (Cm.r.k != 2 || Cm.c.k != 2 || P.r.k != 2 || P.c.k != 2) return false;
+  if (perm[3] != 1 && perm[3] != 3) return false;
+  if (z2_elems(P) >= (1ll << 31)) return false;
+  const Sect L[4] = {Cm.r.leg[0], Cm.r.leg[1], Cm.c.leg[0], Cm.c.leg[1]};
+  // the destination's legs must be the source's permuted
+  const Sect Dl[4] = {P.r.leg[0], P.r.leg[1], P.c.leg[0], P.c.leg[1]};
+  for (int k = 0; k < 4; ++k)
+    if (Dl[k].n[0] != L[perm[k]].n[0] || Dl[k].n[1] != L[perm[k]].n[1]) return false;
+  memset(&d, 0, sizeof d);
+  d.hi = hi;
+  d.lo = lo;
+  d.limit = (int)z2_elems(P);
+  d.mode = perm[3] == 1 ? 1 : 2;
+  int rt[2], ct[2], nr = 0, nc = 0;
+  for (int t = 0; t < 4; ++t)
+    if (tuple_parity(t) == p) rt[nr++] = ct[nc++] = t;
+  d.rsplit = (int)tuple_size(Cm.r, rt[0]);
+  d.csplit = (int)tuple_size(Cm.c, ct[0]);
+  for (int a = 0; a < 2; ++a) {
+    const int nri = L[1].n[tuple_bit(rt[a], 2, 1)], nci = L[3].n[tuple_bit(ct[a], 2, 1)];
+    d.rin[a] = nri > 0 ? nri : 1;
+    d.cin[a] = nci > 0 ? nci : 1;
+  }
+  for (int a = 0; a < 2; ++a)
+    for (int b = 0; b < 2; ++b) {
+      const int par[4] = {tuple_bit(rt[a], 2, 0), tuple_bit(rt[a], 2, 1), tuple_bit(ct[b], 2, 0),
+                          tuple_bit(ct[b], 2, 1)};
+      const int tr = (par[perm[0]] << 1) | par[perm[1]], tc = (par[perm[2]] << 1) | par[perm[3]];
+      const int q = tuple_parity(tr);
+      const long long ld = z2_ld(P, q);
+      const long long base = z2_block_off(P, q) + tuple_offset(P.r, tr) * ld + tuple_offset(P.c, tc);
+      long long co[4];
+      co[perm[0]] = (long long)L[perm[1]].n[par[perm[1]]] * ld;
+      co[perm[1]] = ld;
+      co[perm[2]] = L[perm[3]].n[par[perm[3]]];
+      co[perm[3]] = 1;
+      d.base[a][b] = (int)base;
+      for (int k = 0; k < 4; ++k) d.co[a][b][k] = (int)co[k];
+    }
+  return true;
+}
+
+// As tc_run, with the output (layout Cm) written straight as the split
+// operand `layout` (Cm's legs permuted by perm) into hi/lo by the GEMM's
+// epilogue. Where the epilogue cannot (BF16 split, an empty contraction,
+// unsupported leg order) the output goes through the FP32 buffer tmp and
+// the permute/split kernel instead.
+hs_status tc_run_split(hs_ctx ctx, hs_precision prec, const Z2Mat& A, const DBuf& ahi, const DBuf& alo,
+                       const Z2Mat& B, const DBuf& bhi, const DBuf& blo, const Z2Mat& Cm, const Z2Mat& layout,
+                       std::initializer_list<int> perm, DBuf& hi, DBuf& lo, float* tmp) {
+  const int pad = tc_pad(prec), eb = tc_elem_bytes(prec);
+  const Z2Mat Ap = mat(A.r, A.c, pad), Bp = mat(B.r, B.c, pad), P = mat(layout.r, layout.c, pad);
+  int pm[4] = {0, 0, 0, 0}, i = 0;
+  for (int v : perm) {
+    if (i < 4) pm[i] = v;
+    ++i;
+  }
+  bool fused = eb == 4 && i == 4;
+  for (int p = 0; p < 2 && fused; ++p)
+    if (z2_rows(Ap, p) > 0 && z2_rows(Bp, p) > 0 && z2_cols(Ap, p) == 0) fused = false;
+  PsDesc desc[2];
+  TcProblem pr[2];
+  int n = 0;
+  if (fused) {
+    HS_TRY(split_dest(ctx, prec, P, hi, lo));
+    for (int p = 0; p < 2 && fused; ++p) {
+      TcProblem& t = pr[n];
+      t.M = (int)z2_rows(Ap, p);
+      t.N = (int)z2_rows(Bp, p);
+      t.Kp = (int)z2_ld(Ap, p);
+      if (t.M == 0 || t.N == 0) continue;
+      if (!make_ps_desc(Cm, P, pm, p, hi.p, lo.p, desc[n])) {
+        fused = false;
+        break;
+      }
+      t.ldc = t.N;
+      t.a_hi = static_cast<const char*>(ahi.p) + z2_block_off(Ap, p) * eb;
+      t.a_lo = static_cast<const char*>(alo.p) + z2_block_off(Ap, p) * eb;
+      t.b_hi = static_cast<const char*>(bhi.p) + z2_block_off(Bp, p) * eb;
+      t.b_lo = static_cast<const char*>(blo.p) + z2_block_off(Bp, p) * eb;
+      t.c = nullptr;
+      t.ps = &desc[n];
+      ++n;
+    }
+  }
+  if (!fused) {
+    HS_TRY(tc_run(ctx, prec, A, ahi, alo, B, bhi, blo, Cm, reinterpret_cast<double*>(tmp), true));
+    return tc_split_any(ctx, prec, Cm, layout, perm, tmp, true, hi, lo);
+  }
+  PhaseScope ps(ctx, HS_PHASE_GEMM_TC);
+  HS_CUDA(launch_gemm_tc(prec, pr, n, static_cast<int*>(ctx->tc_err.p), ctx->stream, nullptr, 0));
   if (n > 0) ctx->launches += 1;
   return HS_OK;
 }
@@ -1393,11 +1507,32 @@ hs_status hs_ctmrg_move(hs_ctx ctx, const hs_z2_tensor* a, hs_env* env, int chi,
     HS_TRY(tc_run(ctx, env->precision, Tcr, ctx->tc_b_hi, ctx->tc_b_lo, Cm, ctx->sy_hi, ctx->sy_lo, X1,
                   ctx->x1.d()));
     HS_TRY(tc_split(ctx, env->precision, X1, X1, {0, 1, 2}, ctx->x1.d(), ctx->tc_x_hi, ctx->tc_x_lo));
-    HS_TRY(tc_run(ctx, env->precision, X1, ctx->tc_x_hi, ctx->tc_x_lo, Tcr, ctx->tc_b_hi, ctx->tc_b_lo, X2, B1,
-                  f32c));
+    if (f32c) {
+      // X2 goes straight from G2's accumulators into the permuted split A of G3
+      HS_TRY(tc_run_split(ctx, env->precision, X1, ctx->tc_x_hi, ctx->tc_x_lo, Tcr, ctx->tc_b_hi, ctx->tc_b_lo, X2,
+                          X2p, {0, 2, 3, 1}, ctx->ps_hi, ctx->ps_lo, reinterpret_cast<float*>(B1)));
+    } else {
+      HS_TRY(tc_run(ctx, env->precision, X1, ctx->tc_x_hi, ctx->tc_x_lo, Tcr, ctx->tc_b_hi, ctx->tc_b_lo, X2, B1));
+    }
   }
-  if (tc) {
-    HS_TRY(tc_a_gemm(ctx, env->precision, X2, X2p, {0, 2, 3, 1}, B1, Am, X3, B2, f32c));
+  // C' = X3 with legs (a,e,d,r) -> (a,d,e,r). With the subspace solver and
+  // tensor cores, G3 writes X3 straight into the split C' operand; the FP32
+  // C' itself is formed (from that split) only when a fallback eigensolver
+  // needs it
+  const bool cp_fused = f32c && env->eig_mode == HS_EIG_SUBSPACE;
+  // the split C' is TF32x3 (FP32 pairs): a fallback joins it; a BF16x3 split
+  // went through X3 in B1
+  const bool cp_join = cp_fused && tc_elem_bytes(env->precision) == 4;
+  if (cp_fused) {
+    HS_TRY(tc_run_split(ctx, env->precision, X2p, ctx->ps_hi, ctx->ps_lo, Am, ctx->tc_a_hi, ctx->tc_a_lo, X3, Cp,
+                        {0, 2, 1, 3}, ctx->sH_hi, ctx->sH_lo, reinterpret_cast<float*>(B1)));
+    ctx->sH_n[0] = (int)z2_rows(Cp, 0);
+    ctx->sH_n[1] = (int)z2_rows(Cp, 1);
+    ctx->sH_fresh = true;
+  } else if (tc && f32c) {
+    HS_TRY(tc_run(ctx, env->precision, X2p, ctx->ps_hi, ctx->ps_lo, Am, ctx->tc_a_hi, ctx->tc_a_lo, X3, B1, true));
+  } else if (tc) {
+    HS_TRY(tc_a_gemm(ctx, env->precision, X2, X2p, {0, 2, 3, 1}, B1, Am, X3, B2, false));
     std::swap(B1, B2);  // X3 now in B1, as on the FP64 path
   } else {
     {
@@ -1407,14 +1542,17 @@ hs_status hs_ctmrg_move(hs_ctx ctx, const hs_z2_tensor* a, hs_env* env, int chi,
     PhaseScope ps(ctx, HS_PHASE_GEMM);
     HS_TRY(gemm(ctx, be, g3, B2, a->data, B1));
   }
-  // C' = X3 with legs (a,e,d,r) -> (a,d,e,r). With the subspace solver and
-  // tensor cores, X3 goes straight into the split C' operand; the FP32 C'
-  // itself is formed only when a fallback eigensolver needs it
   bool cp_ready = false;
   auto form_corner = [&]() -> hs_status {
     if (cp_ready) return HS_OK;
     PhaseScope ps(ctx, HS_PHASE_PERMUTE);
-    if (f32c) {
+    if (cp_join) {
+      const Z2Mat Pc = mat(Cp.r, Cp.c, tc_pad(env->precision));
+      HS_CUDA(launch_join_split_f32(ctx->sH_hi.p, ctx->sH_lo.p, z2_rows(Pc, 0), z2_cols(Pc, 0), z2_ld(Pc, 0),
+                                    z2_block_off(Pc, 1), z2_rows(Pc, 1), z2_cols(Pc, 1), z2_ld(Pc, 1),
+                                    reinterpret_cast<float*>(B2), s));
+      ctx->launches += 1;
+    } else if (f32c) {
       const int pm[kMaxLegs] = {0, 2, 1, 3, 0, 0};
       HS_CUDA(launch_permute_f32(cached_plan(ctx, X3, Cp, pm), reinterpret_cast<const float*>(B1),
                                  reinterpret_cast<float*>(B2), s));
@@ -1425,15 +1563,7 @@ hs_status hs_ctmrg_move(hs_ctx ctx, const hs_z2_tensor* a, hs_env* env, int chi,
     cp_ready = true;
     return HS_OK;
   };
-  if (f32c && env->eig_mode == HS_EIG_SUBSPACE) {
-    HS_TRY(tc_split_f32(ctx, env->precision, X3, Cp, {0, 2, 1, 3}, reinterpret_cast<const float*>(B1), ctx->sH_hi,
-                        ctx->sH_lo));
-    ctx->sH_n[0] = (int)z2_rows(Cp, 0);
-    ctx->sH_n[1] = (int)z2_rows(Cp, 1);
-    ctx->sH_fresh = true;
-  } else {
-    HS_TRY(form_corner());
-  }
+  if (!cp_fused) HS_TRY(form_corner());
 
   // one eigen-decomposition per parity block (C' blocks stacked in B2: FP32
   // values when f32c, else FP64)
@@ -1512,6 +1642,7 @@ hs_status hs_ctmrg_move(hs_ctx ctx, const hs_z2_tensor* a, hs_env* env, int chi,
   const Z2Mat Zm = mat(fused2(cn, c), fused2(q, q));
   const Z2Mat Zp = mat(fused2(cn, q), fused2(c, q));
   const Z2Mat Tn = mat(fused2(cn, q), fused1(cn));
+  const Z2Mat Zpq = mat(fused2(cn, q), fused2(q, c)), PTq = mat(fused1(cn), fused2(q, c));
   if (sub_done) {
     const long long npt = (long long)cn.n[0] * n0 + (long long)cn.n[1] * n1;
     HS_TRY(ctx->pcol.ensure(npt * sizeof(double)));
@@ -1574,37 +1705,36 @@ hs_status hs_ctmrg_move(hs_ctx ctx, const hs_z2_tensor* a, hs_env* env, int chi,
     HS_TRY(permute(ctx, PT, Pp, {2, 0, 1}, ctx->pt.d(), ctx->pp.d()));  // (a',a,d) -> (d,a',a)
   }
   if (!tc) {
-    PhaseScope ps(ctx, HS_PHASE_GEMM);
-    HS_TRY(gemm(ctx, be, g4, ctx->pp.d(), env->T, B1));
-  } else {
-    HS_TRY(tc_split(ctx, env->precision, Pp, Pp, {0, 1, 2}, ctx->pp.d(), ctx->tc_x_hi, ctx->tc_x_lo));
-    // Y and Z stay FP32 (the accumulators' values): they only feed splits
-    HS_TRY(tc_run(ctx, env->precision, Pp, ctx->tc_x_hi, ctx->tc_x_lo, Tcr, ctx->tc_b_hi, ctx->tc_b_lo, Y, B1,
-                  true));
-  }
-  if (tc) {
-    HS_TRY(tc_a_gemm(ctx, env->precision, Y, Yp, {1, 2, 0, 3}, B1, Am, Zm, B2, true));
-    std::swap(B1, B2);  // Z now in B1
-  } else {
     {
-      PhaseScope ps(ctx, HS_PHASE_PERMUTE);
-      HS_TRY(permute(ctx, Y, Yp, {1, 2, 0, 3}, B1, B2));    // (d,a',b,x) -> (a',b,d,x)
+      PhaseScope ps(ctx, HS_PHASE_GEMM);
+      HS_TRY(gemm(ctx, be, g4, ctx->pp.d(), env->T, B1));
     }
-    PhaseScope ps(ctx, HS_PHASE_GEMM);
-    HS_TRY(gemm(ctx, be, g5, B2, a->data, B1));
-  }
-  if (!tc) {
     {
       PhaseScope ps(ctx, HS_PHASE_PERMUTE);
-      HS_TRY(permute(ctx, Zm, Zp, {0, 3, 1, 2}, B1, B2));   // (a',b,u,r) -> (a',r,b,u)
+      HS_TRY(permute(ctx, Y, Yp, {1, 2, 0, 3}, B1, B2));  // (d,a',b,x) -> (a',b,d,x)
+    }
+    {
+      PhaseScope ps(ctx, HS_PHASE_GEMM);
+      HS_TRY(gemm(ctx, be, g5, B2, a->data, B1));
+    }
+    {
+      PhaseScope ps(ctx, HS_PHASE_PERMUTE);
+      HS_TRY(permute(ctx, Zm, Zp, {0, 3, 1, 2}, B1, B2));  // (a',b,u,r) -> (a',r,b,u)
     }
     PhaseScope ps(ctx, HS_PHASE_GEMM);
     HS_TRY(gemm(ctx, be, g6, B2, ctx->pt.d(), env->T));
   } else {
-    HS_TRY(tc_split_f32(ctx, env->precision, Zm, Zp, {0, 3, 1, 2}, reinterpret_cast<const float*>(B1), ctx->tc_x_hi,
-                        ctx->tc_x_lo));
-    HS_TRY(tc_split(ctx, env->precision, PT, PT, {0, 1, 2}, ctx->pt.d(), ctx->tc_b_hi, ctx->tc_b_lo));
-    HS_TRY(tc_run(ctx, env->precision, Zp, ctx->tc_x_hi, ctx->tc_x_lo, PT, ctx->tc_b_hi, ctx->tc_b_lo, Tn, env->T));
+    HS_TRY(tc_split(ctx, env->precision, Pp, Pp, {0, 1, 2}, ctx->pp.d(), ctx->tc_x_hi, ctx->tc_x_lo));
+    // Y and Z only feed the next GEMM: the epilogues of G4 and G5 write them
+    // as its permuted split A operand. Z's contraction legs (b,u) are taken
+    // in the order (u,b) (PT's columns alike), so that its destination runs
+    // along the rows of G5's output
+    HS_TRY(tc_run_split(ctx, env->precision, Pp, ctx->tc_x_hi, ctx->tc_x_lo, Tcr, ctx->tc_b_hi, ctx->tc_b_lo, Y, Yp,
+                        {1, 2, 0, 3}, ctx->ps_hi, ctx->ps_lo, reinterpret_cast<float*>(B1)));
+    HS_TRY(tc_run_split(ctx, env->precision, Yp, ctx->ps_hi, ctx->ps_lo, Am, ctx->tc_a_hi, ctx->tc_a_lo, Zm, Zpq,
+                        {0, 3, 2, 1}, ctx->tc_x_hi, ctx->tc_x_lo, reinterpret_cast<float*>(B1)));
+    HS_TRY(tc_split(ctx, env->precision, PT, PTq, {0, 2, 1}, ctx->pt.d(), ctx->tc_b_hi, ctx->tc_b_lo));
+    HS_TRY(tc_run(ctx, env->precision, Zpq, ctx->tc_x_hi, ctx->tc_x_lo, PTq, ctx->tc_b_hi, ctx->tc_b_lo, Tn, env->T));
   }
 
   // C <- diag(lambda)/max|lambda|, T <- T/max|T|

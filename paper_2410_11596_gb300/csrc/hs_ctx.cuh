@@ -141,6 +141,8 @@ struct hs_ctx_s {
   // tensor-core operands: split double layer (cached per source/precision),
   // split A operand of the current GEMM, split B for hs_gemm, error word
   hs::DBuf tc_a_hi, tc_a_lo, tc_x_hi, tc_x_lo, tc_b_hi, tc_b_lo, tc_err;
+  // split operands written by a GEMM epilogue (X2 permuted, then Y permuted)
+  hs::DBuf ps_hi, ps_lo;
   const double* tc_a_src = nullptr;
   int tc_a_prec = -1;
   int* h_tc_err = nullptr;  // pinned

@@ -294,6 +294,11 @@ cudaError_t launch_permute_f64(const PermPlan& plan, const double* in, double* o
 cudaError_t launch_permute_f32(const PermPlan& plan, const float* in, float* out, cudaStream_t s);
 cudaError_t launch_permute_split_f32(const PermPlan& plan, const float* in, void* hi, void* lo, int mode,
                                      cudaStream_t s);
+// FP32 values of a TF32x3-split block pair (padded rows of ld0/ld1 elements,
+// block 1 at element off1) into out, tightly packed, block 1 after block 0.
+cudaError_t launch_join_split_f32(const void* hi, const void* lo, long long rows0, long long cols0, long long ld0,
+                                  long long off1, long long rows1, long long cols1, long long ld1, float* out,
+                                  cudaStream_t s);
 cudaError_t launch_permute_split(const PermPlan& plan, const double* in, void* hi, void* lo, int mode,
                                  cudaStream_t s);
 
@@ -306,6 +311,26 @@ cudaError_t launch_split_pad(const double* src, long long rows, int cols, long l
 
 // One block problem: C[M, N] (FP64, row stride ldc) = A[M, Kp] B[N, Kp]^T with
 // A and B given as hi/lo splits (FP32 for TF32, BF16 for BF16), rows Kp apart.
+// Output of a tensor-core GEMM written straight as the split (TF32 hi, FP32
+// lo) operand of the next GEMM, with its four legs permuted. The output block
+// has rows (L0, L1) and columns (L2, L3), each fused from two parity tuples:
+// rows [0, rsplit) are tuple 0, the rest tuple 1, with inner leg extents
+// rin[t] (columns likewise). Entry (i0, i1 | j0, j1) of row tuple tr and
+// column tuple tc goes to element base[tr][tc] + co[tr][tc] . (i0, i1, j0, j1)
+// of hi and lo (4-byte elements, fewer than limit). mode 1: the destination's
+// innermost leg is L1 (a warp stores 32 consecutive rows); mode 2: it is L3
+// (stores run along the columns, staged through shared memory).
+struct PsDesc {
+  void* hi;
+  void* lo;
+  int limit;
+  int rsplit, csplit;
+  int rin[2], cin[2];
+  int base[2][2];
+  int co[2][2][4];
+  int mode;
+};
+
 struct TcProblem {
   int M, N, Kp, ldc;
   const void* a_hi;
@@ -314,6 +339,7 @@ struct TcProblem {
   const void* b_lo;
   double* c;        // FP64 output, or FP32 (c read as float*, ldc in floats) when out_f32
   int out_f32 = 0;  // the accumulators are FP32, so an FP32 output loses nothing (one split-K sum rounds once)
+  const PsDesc* ps = nullptr;  // when set, the output goes there instead of c (never split along K)
 };
 
 // Up to four problems per launch. precision: HS_PREC_TF32X3, HS_PREC_TF32 or HS_PREC_BF16X3. err receives a

@@ -69,6 +69,7 @@ struct Prob {
   int M, N, Kp, ldc;
   int k0, map;
   int f32;  // output FP32 (c read as float*)
+  int psi;  // index of the permuted split output in Group::ps, or -1
   double* c;
   int tile_start, tiles_n;
 };
@@ -76,7 +77,17 @@ struct Prob {
 struct Group {
   int n;
   Prob p[kMaxUnits];
+  PsDesc ps[kMaxPairs];
 };
+
+// PsDesc fields of row tuple tr (0 or 1, runtime) without indexing the
+// parameter arrays by it.
+__device__ __forceinline__ int ps_base(const PsDesc& D, int tr, int tc) {
+  return tr ? D.base[1][tc] : D.base[0][tc];
+}
+__device__ __forceinline__ int ps_co(const PsDesc& D, int tr, int tc, int k) {
+  return tr ? D.co[1][tc][k] : D.co[0][tc][k];
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -218,7 +229,7 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
-template <int NPASS, int EB, int NM>
+template <int NPASS, int EB, int NM, bool PS>
 __global__ void __launch_bounds__(NT, 1) gemm_tc_kernel(const __grid_constant__ MapsN<NM> maps, const Group g,
                                                         int total_tiles, int* __restrict__ err) {
   hs_pdl_enter();
@@ -361,12 +372,118 @@ __global__ void __launch_bounds__(NT, 1) gemm_tc_kernel(const __grid_constant__ 
       // 16-byte stores (FP64) / 8-byte stores (FP32) when every row start is aligned
       const bool vec = P.f32 ? (P.ldc % 2 == 0) && ((reinterpret_cast<uintptr_t>(P.c) & 7) == 0)
                              : (P.ldc % 2 == 0) && ((reinterpret_cast<uintptr_t>(P.c) & 15) == 0);
+      // permuted split output: this lane's row (row0 + lane) as its row tuple
+      // and its destination offsets for column tuples 0 and 1; in mode 2 also
+      // those of the four rows (lane / 4) + 8 k this lane stores
+      const int psi = (PS && EB == 4) ? P.psi : -1;
+      int ps_tr = 0, ps_r0 = 0, ps_r1 = 0;
+      if (psi >= 0) {
+        const PsDesc& D = g.ps[psi];
+        const int row = row0 + lane;
+        if (row < P.M) {
+          ps_tr = row >= D.rsplit ? 1 : 0;
+          const int rin = ps_tr ? D.rin[1] : D.rin[0];
+          const int rr = row - (ps_tr ? D.rsplit : 0);
+          const int i0 = rr / rin, i1 = rr - i0 * rin;
+          ps_r0 = ps_base(D, ps_tr, 0) + ps_co(D, ps_tr, 0, 0) * i0 + ps_co(D, ps_tr, 0, 1) * i1;
+          ps_r1 = ps_base(D, ps_tr, 1) + ps_co(D, ps_tr, 1, 0) * i0 + ps_co(D, ps_tr, 1, 1) * i1;
+        }
+      }
       for (int c = 64 * half; c < 64 * half + 64 && r.n0 + c < P.N; c += 32) {
         uint32_t r0[32], r1[32];
         if (ktiles > 0) {
           tmem_ld32(d + c, r0);
           if (NPASS == 3) tmem_ld32(d + BN + c, r1);
           tmem_wait_ld();
+        }
+        if (psi >= 0 && g.ps[psi].mode == 1) {
+          // destination innermost along the rows: lane = row, one column per step
+          const PsDesc& D = g.ps[psi];
+          uint32_t* hi = static_cast<uint32_t*>(D.hi);
+          uint32_t* lo = static_cast<uint32_t*>(D.lo);
+          const bool rok = row0 + lane < P.M;
+          const int cA0 = ps_co(D, ps_tr, 0, 2), cB0 = ps_co(D, ps_tr, 0, 3);
+          const int cA1 = ps_co(D, ps_tr, 1, 2), cB1 = ps_co(D, ps_tr, 1, 3);
+          const int col = r.n0 + c;
+          int tc = col >= D.csplit ? 1 : 0;
+          int cin = tc ? D.cin[1] : D.cin[0];
+          const int cc = col - (tc ? D.csplit : 0);
+          int j0 = cc / cin, j1 = cc - (cc / cin) * cin;
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            if (col + j >= P.N) break;  // warp-uniform
+            float f = 0.f;
+            if (ktiles > 0) {
+              f = __uint_as_float(r0[j]);
+              if (NPASS == 3) f += __uint_as_float(r1[j]);
+            }
+            const int o = tc ? ps_r1 + cA1 * j0 + cB1 * j1 : ps_r0 + cA0 * j0 + cB0 * j1;
+            if (rok && (unsigned)o < (unsigned)D.limit) {
+              uint32_t h, l;
+              split_f32_tf32x3(__float_as_uint(f), h, l);
+              hi[o] = h;
+              lo[o] = l;
+            }
+            if (++j1 == cin) {
+              j1 = 0;
+              ++j0;
+            }
+            if (col + j + 1 == D.csplit) {
+              tc = 1;
+              j0 = 0;
+              j1 = 0;
+              cin = D.cin[1];
+            }
+          }
+          continue;
+        }
+        if (psi >= 0) {
+          // destination innermost along the columns: 16 columns of the 32
+          // rows staged at a time; each half-warp then stores 16 consecutive
+          // columns of one row
+          const PsDesc& D = g.ps[psi];
+          uint32_t* hi = static_cast<uint32_t*>(D.hi);
+          uint32_t* lo = static_cast<uint32_t*>(D.lo);
+          float* stf = reinterpret_cast<float*>(stg);  // 32 rows x 17
+          const int cl = lane & 15, hw = lane >> 4;
+#pragma unroll
+          for (int hf = 0; hf < 2; ++hf) {
+#pragma unroll
+            for (int t = 0; t < 16; ++t) {
+              float f = 0.f;
+              if (ktiles > 0) {
+                f = __uint_as_float(r0[16 * hf + t]);
+                if (NPASS == 3) f += __uint_as_float(r1[16 * hf + t]);
+              }
+              stf[lane * 17 + t] = f;
+            }
+            __syncwarp();
+            // this lane's column: tuple and offsets for row tuples 0 and 1
+            const int col = r.n0 + c + 16 * hf + cl;
+            const bool cok = col < P.N;
+            const int tc = col >= D.csplit ? 1 : 0;
+            const int cin = tc ? D.cin[1] : D.cin[0];
+            const int cc = col - (tc ? D.csplit : 0);
+            const int j0 = cc / cin, j1 = cc - j0 * cin;
+            const int cp0 = (tc ? D.co[0][1][2] : D.co[0][0][2]) * j0 + (tc ? D.co[0][1][3] : D.co[0][0][3]) * j1;
+            const int cp1 = (tc ? D.co[1][1][2] : D.co[1][0][2]) * j0 + (tc ? D.co[1][1][3] : D.co[1][0][3]) * j1;
+#pragma unroll 4
+            for (int st = 0; st < 16; ++st) {
+              const int i = 2 * st + hw;
+              const int R0 = __shfl_sync(0xffffffffu, ps_r0, i);
+              const int R1 = __shfl_sync(0xffffffffu, ps_r1, i);
+              const int tr = __shfl_sync(0xffffffffu, ps_tr, i);
+              const int o = (tc ? R1 : R0) + (tr ? cp1 : cp0);
+              if (cok && row0 + i < P.M && (unsigned)o < (unsigned)D.limit) {
+                uint32_t hh, ll;
+                split_f32_tf32x3(__float_as_uint(stf[i * 17 + cl]), hh, ll);
+                hi[o] = hh;
+                lo[o] = ll;
+              }
+            }
+            __syncwarp();
+          }
+          continue;
         }
         if (P.f32) {
           // FP32 output: the accumulator sums as they are, staged as above
@@ -557,11 +674,11 @@ __global__ void tc_splitk_reduce_kernel(const SplitReds reds) {
 // Launch with the tensor maps of the first NM operand pairs only: the maps
 // are kernel parameters (512 bytes per pair), and a smaller parameter block
 // launches faster.
-template <int NPASS, int EB, int NM>
+template <int NPASS, int EB, int NM, bool PS>
 cudaError_t launch_tc(const Maps& all, const Group& g, int grid, int tiles, int* err, cudaStream_t s) {
   using K = Cfg<NPASS, EB>;
   // set once per process and instantiation (thread-safe static initialisation)
-  static const cudaError_t attr_err = cudaFuncSetAttribute(gemm_tc_kernel<NPASS, EB, NM>,
+  static const cudaError_t attr_err = cudaFuncSetAttribute(gemm_tc_kernel<NPASS, EB, NM, PS>,
                                                            cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM);
   if (attr_err != cudaSuccess) return attr_err;
   MapsN<NM> maps;
@@ -570,7 +687,7 @@ cudaError_t launch_tc(const Maps& all, const Group& g, int grid, int tiles, int*
       maps.a[j][h] = all.a[j][h];
       maps.b[j][h] = all.b[j][h];
     }
-  hs_launch(gemm_tc_kernel<NPASS, EB, NM>, grid, NT, K::SMEM, s, maps, g, tiles, err);
+  hs_launch(gemm_tc_kernel<NPASS, EB, NM, PS>, grid, NT, K::SMEM, s, maps, g, tiles, err);
   return cudaGetLastError();
 }
 
@@ -599,10 +716,17 @@ cudaError_t run(const TcProblem* probs, int nprob, int* err, cudaStream_t s, dou
     const int tiles_n = (p.N + BN - 1) / BN;
     const int ptiles = ((p.M + BM - 1) / BM) * tiles_n;
     const int ktiles = p.Kp / K::K_PER_TILE;
+    int psi = -1;
+    if (p.ps) {
+      if (EB != 4 || p.ps->mode < 1 || p.ps->mode > 2) return cudaErrorInvalidValue;
+      psi = j;
+      g.ps[j] = *p.ps;
+    }
     // split K when this problem's tiles cannot fill the 152 SMs and each
-    // split keeps at least 4 K steps; partials go to `part`
+    // split keeps at least 4 K steps; partials go to `part` (not for a
+    // permuted split output)
     int ns = 1;
-    if (part && ptiles < 152) {
+    if (part && ptiles < 152 && psi < 0) {
       ns = (152 + ptiles - 1) / ptiles;
       ns = ns < ktiles / 4 ? ns : ktiles / 4;
       ns = ns < 8 ? ns : 8;
@@ -620,6 +744,7 @@ cudaError_t run(const TcProblem* probs, int nprob, int* err, cudaStream_t s, dou
       q.k0 = kb * K::K_PER_TILE;
       q.Kp = (ke > kb ? ke - kb : 0) * K::K_PER_TILE;
       q.map = j;
+      q.psi = psi;
       if (ns > 1) {
         q.c = part + part_used + (long long)sidx * p.M * p.N;
         q.ldc = p.N;
@@ -646,9 +771,16 @@ cudaError_t run(const TcProblem* probs, int nprob, int* err, cudaStream_t s, dou
     return n;
   }();
   const int grid = tiles < sms ? tiles : sms;
-  cudaError_t e = nmap <= 1   ? launch_tc<NPASS, EB, 1>(maps, g, grid, tiles, err, s)
-                  : nmap <= 2 ? launch_tc<NPASS, EB, 2>(maps, g, grid, tiles, err, s)
-                              : launch_tc<NPASS, EB, kMaxPairs>(maps, g, grid, tiles, err, s);
+  // launches with a permuted split output take their own instantiation (the
+  // split epilogue; at most two operand pairs), the others the plain one
+  bool ps = false;
+  for (int u = 0; u < g.n; ++u) ps = ps || g.p[u].psi >= 0;
+  if (ps && (EB != 4 || nmap > 2)) return cudaErrorInvalidValue;
+  cudaError_t e = ps           ? (nmap <= 1 ? launch_tc<NPASS, EB, 1, true>(maps, g, grid, tiles, err, s)
+                                            : launch_tc<NPASS, EB, 2, true>(maps, g, grid, tiles, err, s))
+                  : nmap <= 1 ? launch_tc<NPASS, EB, 1, false>(maps, g, grid, tiles, err, s)
+                  : nmap <= 2 ? launch_tc<NPASS, EB, 2, false>(maps, g, grid, tiles, err, s)
+                              : launch_tc<NPASS, EB, kMaxPairs, false>(maps, g, grid, tiles, err, s);
   if (e != cudaSuccess) return e;
   if (nred > 0) {
     long long mn = 0;

@@ -634,4 +634,38 @@ cudaError_t launch_permute_f32(const PermPlan& plan, const float* in, float* out
   return launch_permute_t(plan, in, out, 1.0, s);
 }
 
+namespace {
+
+// out[r * cols + c] = hi[r * ld + c] + lo[r * ld + c] for both blocks of a
+// TF32x3-split pair (hi a TF32 value, lo the FP32 remainder: the sum is the
+// split FP32 value exactly).
+__global__ void join_split_f32_kernel(const uint32_t* __restrict__ hi, const uint32_t* __restrict__ lo,
+                                      long long rows0, long long cols0, long long ld0, long long off1,
+                                      long long rows1, long long cols1, long long ld1, float* __restrict__ out) {
+  hs_pdl_enter();
+  const long long n0 = rows0 * cols0, total = n0 + rows1 * cols1;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const bool b = e >= n0;
+    const long long f = b ? e - n0 : e, cols = b ? cols1 : cols0;
+    const long long r = f / cols, c = f - r * cols;
+    const long long src = (b ? off1 : 0) + r * (b ? ld1 : ld0) + c;
+    out[e] = __uint_as_float(hi[src]) + __uint_as_float(lo[src]);
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_join_split_f32(const void* hi, const void* lo, long long rows0, long long cols0, long long ld0,
+                                  long long off1, long long rows1, long long cols1, long long ld1, float* out,
+                                  cudaStream_t s) {
+  const long long total = rows0 * cols0 + rows1 * cols1;
+  if (total <= 0) return cudaSuccess;
+  long long blocks = (total + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  hs_launch(join_split_f32_kernel, (unsigned)blocks, 256, 0, s, static_cast<const uint32_t*>(hi),
+            static_cast<const uint32_t*>(lo), rows0, cols0, ld0, off1, rows1, cols1, ld1, out);
+  return cudaGetLastError();
+}
+
 }  // namespace hs
