@@ -236,6 +236,26 @@ HS_HD void split_f32_tf32x3(uint32_t u, uint32_t& hi, uint32_t& lo) {
   if ((ld & 0x7FFFFFFFu) == 0u) lo = 0u;
 }
 
+// split_f32_tf32x3 with selects in place of branches (the GEMM epilogue's
+// form; the same bits for every input).
+HS_HD void split_f32_tf32x3_sel(uint32_t u, uint32_t& hi, uint32_t& lo) {
+  const uint32_t sign = u & 0x80000000u, ex = u & 0x7F800000u;
+  const uint32_t h = (u + 0x1000u) & 0xFFFFE000u;
+  float fv, fh;
+  std::memcpy(&fv, &u, 4);
+  std::memcpy(&fh, &h, 4);
+  const float t = sign ? -1.7014118346046923e38f : 1.7014118346046923e38f;
+  // rounded up to 2^128: v - 2^128 = (v - 2^127) - 2^127, both steps exact
+  const float d = (h & 0x7F800000u) == 0x7F800000u ? (fv - t) - t : fv - fh;
+  uint32_t ld;
+  std::memcpy(&ld, &d, 4);
+  uint32_t l = (ld & 0x7F800000u) == 0u ? (ld & 0x80000000u) : ld;
+  l = (ld & 0x7FFFFFFFu) == 0u ? 0u : l;
+  const uint32_t special = (u & 0x007FFFFFu) ? 0x7FC00000u : u;  // NaN, infinity
+  hi = ex == 0u ? sign : (ex == 0x7F800000u ? special : h);
+  lo = ex == 0u ? sign : (ex == 0x7F800000u ? special : l);
+}
+
 // The FP64 value of the IEEE single bit pattern f (exact). Subnormal singles
 // are widened by the FP64 conversion (`slow` is called for them).
 HS_HD bool f32_widen_fast(uint32_t f, unsigned long long& out) {

@@ -397,55 +397,72 @@ __global__ void __launch_bounds__(NT, 1) gemm_tc_kernel(const __grid_constant__ 
           tmem_wait_ld();
         }
         if (psi >= 0 && g.ps[psi].mode == 1) {
-          // destination innermost along the rows: lane = row, one column per step
+          // destination innermost along the rows: lane = row, one column per
+          // step; the columns' destination offsets (for row tuples 0 and 1)
+          // computed once per chunk, one column per lane, into a table
           const PsDesc& D = g.ps[psi];
           uint32_t* hi = static_cast<uint32_t*>(D.hi);
           uint32_t* lo = static_cast<uint32_t*>(D.lo);
+          int* ctab = reinterpret_cast<int*>(stg);  // [row tuple][32 columns]
+          const int col0 = r.n0 + c;
+          int ctc = 0, co0 = 0, co1 = 0;
+          if (col0 + lane < P.N) {
+            const int col = col0 + lane;
+            ctc = col >= D.csplit ? 1 : 0;
+            const int cin = ctc ? D.cin[1] : D.cin[0];
+            const int cc = col - (ctc ? D.csplit : 0);
+            const int j0 = cc / cin, j1 = cc - j0 * cin;
+            co0 = ps_co(D, 0, 0, 2) * j0 + ps_co(D, 0, 0, 3) * j1;
+            co1 = ps_co(D, 1, 0, 2) * j0 + ps_co(D, 1, 0, 3) * j1;
+            if (ctc) {
+              co0 = ps_co(D, 0, 1, 2) * j0 + ps_co(D, 0, 1, 3) * j1;
+              co1 = ps_co(D, 1, 1, 2) * j0 + ps_co(D, 1, 1, 3) * j1;
+            }
+          }
+          const unsigned tcmask = __ballot_sync(0xffffffffu, ctc);
+          __syncwarp();  // the previous chunk's readers are done
+          ctab[lane] = co0;
+          ctab[32 + lane] = co1;
+          __syncwarp();
+          const int* mytab = ctab + (ps_tr ? 32 : 0);
+          const int nvalid = P.N - col0;
           const bool rok = row0 + lane < P.M;
-          const int cA0 = ps_co(D, ps_tr, 0, 2), cB0 = ps_co(D, ps_tr, 0, 3);
-          const int cA1 = ps_co(D, ps_tr, 1, 2), cB1 = ps_co(D, ps_tr, 1, 3);
-          const int col = r.n0 + c;
-          int tc = col >= D.csplit ? 1 : 0;
-          int cin = tc ? D.cin[1] : D.cin[0];
-          const int cc = col - (tc ? D.csplit : 0);
-          int j0 = cc / cin, j1 = cc - (cc / cin) * cin;
+          // join the accumulators first (frees the correction's registers)
 #pragma unroll
           for (int j = 0; j < 32; ++j) {
-            if (col + j >= P.N) break;  // warp-uniform
             float f = 0.f;
             if (ktiles > 0) {
               f = __uint_as_float(r0[j]);
               if (NPASS == 3) f += __uint_as_float(r1[j]);
             }
-            const int o = tc ? ps_r1 + cA1 * j0 + cB1 * j1 : ps_r0 + cA0 * j0 + cB0 * j1;
+            r0[j] = __float_as_uint(f);
+          }
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            if (j >= nvalid) break;  // warp-uniform
+            uint32_t h, l;
+            split_f32_tf32x3_sel(r0[j], h, l);
+            const int o = ((tcmask >> j) & 1u ? ps_r1 : ps_r0) + mytab[j];
             if (rok && (unsigned)o < (unsigned)D.limit) {
-              uint32_t h, l;
-              split_f32_tf32x3(__float_as_uint(f), h, l);
               hi[o] = h;
               lo[o] = l;
-            }
-            if (++j1 == cin) {
-              j1 = 0;
-              ++j0;
-            }
-            if (col + j + 1 == D.csplit) {
-              tc = 1;
-              j0 = 0;
-              j1 = 0;
-              cin = D.cin[1];
             }
           }
           continue;
         }
         if (psi >= 0) {
           // destination innermost along the columns: 16 columns of the 32
-          // rows staged at a time; each half-warp then stores 16 consecutive
-          // columns of one row
+          // rows staged at a time (row i's columns rotated by (i / 2) % 16,
+          // so that neither the row writes nor the column reads conflict);
+          // each half-warp then stores 16 consecutive columns of one row
           const PsDesc& D = g.ps[psi];
           uint32_t* hi = static_cast<uint32_t*>(D.hi);
           uint32_t* lo = static_cast<uint32_t*>(D.lo);
-          float* stf = reinterpret_cast<float*>(stg);  // 32 rows x 17
-          const int cl = lane & 15, hw = lane >> 4;
+          float* stf = reinterpret_cast<float*>(stg);         // 32 x 16
+          int4* rinfo = reinterpret_cast<int4*>(stf + 512);  // per row: offsets for column tuples 0, 1; row tuple
+          const int cl = lane & 15, hw = lane >> 4, sw = (lane >> 1) & 15;
+          __syncwarp();  // the previous chunk's readers are done
+          rinfo[lane] = make_int4(ps_r0, ps_r1, ps_tr, 0);
 #pragma unroll
           for (int hf = 0; hf < 2; ++hf) {
 #pragma unroll
@@ -455,7 +472,7 @@ __global__ void __launch_bounds__(NT, 1) gemm_tc_kernel(const __grid_constant__ 
                 f = __uint_as_float(r0[16 * hf + t]);
                 if (NPASS == 3) f += __uint_as_float(r1[16 * hf + t]);
               }
-              stf[lane * 17 + t] = f;
+              stf[lane * 16 + (t ^ sw)] = f;
             }
             __syncwarp();
             // this lane's column: tuple and offsets for row tuples 0 and 1
@@ -467,16 +484,14 @@ __global__ void __launch_bounds__(NT, 1) gemm_tc_kernel(const __grid_constant__ 
             const int j0 = cc / cin, j1 = cc - j0 * cin;
             const int cp0 = (tc ? D.co[0][1][2] : D.co[0][0][2]) * j0 + (tc ? D.co[0][1][3] : D.co[0][0][3]) * j1;
             const int cp1 = (tc ? D.co[1][1][2] : D.co[1][0][2]) * j0 + (tc ? D.co[1][1][3] : D.co[1][0][3]) * j1;
-#pragma unroll 4
+#pragma unroll 2
             for (int st = 0; st < 16; ++st) {
               const int i = 2 * st + hw;
-              const int R0 = __shfl_sync(0xffffffffu, ps_r0, i);
-              const int R1 = __shfl_sync(0xffffffffu, ps_r1, i);
-              const int tr = __shfl_sync(0xffffffffu, ps_tr, i);
-              const int o = (tc ? R1 : R0) + (tr ? cp1 : cp0);
+              const int4 ri = rinfo[i];
+              const int o = (tc ? ri.y : ri.x) + (ri.z ? cp1 : cp0);
+              uint32_t hh, ll;
+              split_f32_tf32x3_sel(__float_as_uint(stf[i * 16 + (cl ^ ((i >> 1) & 15))]), hh, ll);
               if (cok && row0 + i < P.M && (unsigned)o < (unsigned)D.limit) {
-                uint32_t hh, ll;
-                split_f32_tf32x3(__float_as_uint(stf[i * 17 + cl]), hh, ll);
                 hi[o] = hh;
                 lo[o] = ll;
               }

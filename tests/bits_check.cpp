@@ -133,6 +133,20 @@ int main() {
         return 1;
       }
     }
+  // 2d. the select form of that split gives the same bits for every pattern
+  // (all exponents, zeros, subnormals, infinities, NaNs)
+  for (uint64_t k = 0; k < (1ull << 32); k += 4093) {
+    const uint32_t uu = (uint32_t)k;
+    for (uint32_t v : {uu, uu | 0x7F800000u, uu & 0x807FFFFFu, uu | 0x7FFFF000u, uu & 0x80000000u}) {
+      uint32_t h2, l2, h3, l3;
+      split_f32_tf32x3(v, h2, l2);
+      split_f32_tf32x3_sel(v, h3, l3);
+      if (h2 != h3 || l2 != l3) {
+        std::printf("select split of %08x: %08x %08x vs %08x %08x\n", v, h3, l3, h2, l2);
+        return 1;
+      }
+    }
+  }
   // zero, tiny, NaN
   uint32_t h, l;
   split_f64(0.0, 11, 24, true, h, l);
