@@ -38,7 +38,7 @@ NCU_TRAFFIC = {
     # profiles/gemm_f64_d6_chi144.md: mean of the G3/G4/G5 launches
     "gemm_f64": {"bytes_per_launch": 143.3e6, "source_sha": "ac07f1d8a4d24d63"},
     # profiles/gemm_tc_tf32x3_d6_chi144.md: mean over the 32 launches of two steady-state moves
-    "gemm_tc_tf32x3": {"bytes_per_launch": 41.9e6, "source_sha": "c1075a93c7e37fbe"},
+    "gemm_tc_tf32x3": {"bytes_per_launch": 56.1e6, "source_sha": "f36631a7cedc423b"},
 }
 
 
