@@ -369,7 +369,7 @@ __global__ void cheb_step_pair_kernel(double* __restrict__ Y, const double* __re
 // a round is shared-memory bound, and V is the larger half of it. A is kept as
 // its upper triangle, so a 2 x 2 block of a round is read and written once.
 constexpr int kMaxSweeps = 40;
-constexpr int kJacobiCtas = 4;
+constexpr int kJacobiCtas = 8;
 
 // Blocks (a, b), a <= b, of the pair grid that a thread updates in every
 // round, packed a << 16 | b, and V entries (pair, component) packed the same
@@ -509,8 +509,10 @@ __global__ void __launch_bounds__(1024) jacobi_eig_kernel(float* __restrict__ A0
       for (int t = 0; t < kBlkPerThread; ++t) {
         if (t >= nblk) break;
         const int a = blk[t] >> 16, b = blk[t] & 0xffff;
-        const int2 ia = rr_pair(a, r, M), ib = rr_pair(b, r, M);
         const float2 ra_ = cs[a], rb_ = cs[b];
+        // neither pair rotates: the block stays as it is
+        if (ra_.x == 1.f && ra_.y == 0.f && rb_.x == 1.f && rb_.y == 0.f) continue;
+        const int2 ia = rr_pair(a, r, M), ib = rr_pair(b, r, M);
         const bool ra = ia.y < m, rb = ib.y < m;
         // (pa, pb), (pa, qb), (qa, pb), (qa, qb) at their upper positions
         const int e00 = min(ia.x, ib.x) * ld + max(ia.x, ib.x);
