@@ -1090,6 +1090,17 @@ hs_status subspace_projector(hs_ctx ctx, hs_env* env, int chi, int n0, int n1, d
     }
     HS_CUDA(launch_residual_pair(ctx->szr.d(0), ctx->sxr.d(0), th, m[0], n[0], m[1], n[1], ctx->sres.d(0), s));
     ctx->launches += 1;
+    // this round's selection, issued ahead of the readback: when the round
+    // converges it is the move's selection, and the move needs no second
+    // round trip to the host for it
+    HS_CUDA(launch_cast_f32_f64(th, w, m[0] + m[1], s));
+    {
+      PhaseScope ps(ctx, HS_PHASE_SELECT);
+      HS_CUDA(launch_select(w, m[0], w + m[0], m[1], chi, static_cast<int*>(ctx->idx.p), ctx->lam.d(),
+                            static_cast<SelectOut*>(ctx->sel.p), s));
+    }
+    HS_CUDA(cudaMemcpyAsync(ctx->h_sel, ctx->sel.p, sizeof(SelectOut), cudaMemcpyDeviceToHost, s));
+    ctx->launches += 2;
     HS_CUDA(cudaMemcpyAsync(hth, th, (size_t)mt * sizeof(float), cudaMemcpyDeviceToHost, s));
     HS_CUDA(cudaMemcpyAsync(hres, ctx->sres.d(0), (size_t)mt * sizeof(double), cudaMemcpyDeviceToHost, s));
     // info[0], info[1]: Jacobi status; info[2]: Cholesky status (bad)
@@ -1128,7 +1139,7 @@ hs_status subspace_projector(hs_ctx ctx, hs_env* env, int chi, int n0, int n1, d
     if (ok) {
       *reason = 0;
       for (int b = 0; b < 2; ++b) m_out[b] = m[b];
-      HS_CUDA(launch_cast_f32_f64(th, w, m[0] + m[1], s));
+      ctx->sel_ready = true;  // w, the selection and its host copy are this round's
       *done = true;
       return HS_OK;
     }
@@ -1471,6 +1482,7 @@ hs_status hs_ctmrg_move(hs_ctx ctx, const hs_z2_tensor* a, hs_env* env, int chi,
   const hs_gemm_backend be = env->gemm_backend;
   const bool tc = env->precision != HS_PREC_F64;
   ctx->sH_fresh = false;
+  ctx->sel_ready = false;
   // with tensor-core GEMMs the corner chain stays in FP32 (the accumulators'
   // values, so nothing is lost), except for the FP64 eigensolver
   ctx->cp_f32 = tc && env->eig_mode != HS_EIG_F64;
@@ -1619,16 +1631,19 @@ hs_status hs_ctmrg_move(hs_ctx ctx, const hs_z2_tensor* a, hs_env* env, int chi,
   }
   SelectOut* dsel = static_cast<SelectOut*>(ctx->sel.p);
   int* didx = static_cast<int*>(ctx->idx.p);
-  {
-    PhaseScope ps(ctx, HS_PHASE_SELECT);
-    HS_CUDA(launch_select(w0, ns0, w1, ns1, chi, didx, ctx->lam.d(), dsel, s));
-    ctx->launches += 1;
+  if (!(sub_done && ctx->sel_ready)) {
+    // (a converged subspace round has issued the selection and read it back)
+    {
+      PhaseScope ps(ctx, HS_PHASE_SELECT);
+      HS_CUDA(launch_select(w0, ns0, w1, ns1, chi, didx, ctx->lam.d(), dsel, s));
+      ctx->launches += 1;
+    }
+    HS_CUDA(cudaMemcpyAsync(ctx->h_sel, dsel, sizeof(SelectOut), cudaMemcpyDeviceToHost, s));
+    HS_CUDA(cudaMemcpyAsync(ctx->h_info, ctx->info.p, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+    HS_CUDA(cudaStreamSynchronize(s));
+    if (ctx->h_info[0] != 0 || ctx->h_info[1] != 0)
+      return fail(HS_ERR_SOLVER, "syevd info = (%d, %d)", ctx->h_info[0], ctx->h_info[1]);
   }
-  HS_CUDA(cudaMemcpyAsync(ctx->h_sel, dsel, sizeof(SelectOut), cudaMemcpyDeviceToHost, s));
-  HS_CUDA(cudaMemcpyAsync(ctx->h_info, ctx->info.p, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
-  HS_CUDA(cudaStreamSynchronize(s));
-  if (ctx->h_info[0] != 0 || ctx->h_info[1] != 0)
-    return fail(HS_ERR_SOLVER, "syevd info = (%d, %d)", ctx->h_info[0], ctx->h_info[1]);
   if (!std::isfinite(ctx->h_sel->lam_max) || ctx->h_sel->lam_max <= 0)
     return fail(HS_ERR_NONFINITE, "enlarged corner has no finite non-zero eigenvalue");
   const SelectOut sel = *ctx->h_sel;

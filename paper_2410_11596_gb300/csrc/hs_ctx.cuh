@@ -175,6 +175,7 @@ struct hs_ctx_s {
   int ws_k[2] = {0, 0}, ws_n[2] = {0, 0}, ws_m[2] = {0, 0};  // kept counts, block sizes, stored rows
   long long ws_moves = 0;
   bool sH_fresh = false;  // sH_hi/lo hold the split blocks of this move's C'
+  bool sel_ready = false; // this move's selection is done and its host copy read back
   // this move's enlarged corner C' (and the GEMM outputs before it) are FP32
   // (the tensor-core accumulators' values) rather than FP64
   bool cp_f32 = false;
