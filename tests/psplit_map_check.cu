@@ -84,6 +84,25 @@ int main() {
     { const int pm[4] = {1, 2, 0, 3}; fails += check(mat(fused2(q, cn), fused2(c, q), 1), mat(fused2(cn, c), fused2(q, q), 1), pm, "Y->Yp"); }
     { const int pm[4] = {0, 3, 2, 1}; fails += check(mat(fused2(cn, c), fused2(q, q), 1), mat(fused2(cn, q), fused2(q, c), 1), pm, "Z->Zpq"); }
   }
+  // layouts the epilogue cannot write are refused (the GEMM then goes through
+  // the FP32 output and the permute/split kernel): a destination whose
+  // innermost leg is a row or column outer leg, and legs that do not match
+  {
+    const Sect c = {{5, 3}}, q = {{2, 3}}, cn = {{4, 2}};
+    const int pz[4] = {0, 3, 1, 2};  // Z -> Zp with contraction legs (b, u): innermost is L2
+    PsDesc d;
+    if (make_ps_desc(mat(fused2(cn, c), fused2(q, q), 1), mat(fused2(cn, q), fused2(c, q), 32), pz, 0, nullptr,
+                     nullptr, d)) {
+      printf("accepted an L2-innermost destination\n");
+      ++fails;
+    }
+    const int px[4] = {0, 2, 3, 1};
+    if (make_ps_desc(mat(fused2(c, q), fused2(c, q), 1), mat(fused2(c, c), fused2(q, cn), 32), px, 0, nullptr,
+                     nullptr, d)) {
+      printf("accepted mismatched legs\n");
+      ++fails;
+    }
+  }
   printf(fails ? "FAIL\n" : "ok\n");
   return fails != 0;
 }
