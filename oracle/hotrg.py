@@ -36,7 +36,11 @@ def stack_vertical(Ttop: np.ndarray, Tbot: np.ndarray) -> np.ndarray:
 
 
 def isometry(M: np.ndarray, chi: int):
-    """Top-chi eigenvectors of the left or right Gram matrix of M (whichever discards less)."""
+    """Top-chi eigenvectors of the left or right Gram matrix of M (whichever discards less).
+
+    Returns (V, w, side): the kept eigenvectors as columns, the Gram matrix's
+    eigenvalues in descending order, and side = 0 (left) or 1 (right).
+    """
     u, l1, l2, d, r1, r2 = M.shape
     ML = M.transpose(1, 2, 0, 3, 4, 5).reshape(l1 * l2, -1)
     MR = M.transpose(4, 5, 0, 1, 2, 3).reshape(r1 * r2, -1)
@@ -48,7 +52,7 @@ def isometry(M: np.ndarray, chi: int):
         keep = min(chi, len(w))
         out.append((float(np.sum(w[order[keep:]])), V[:, order[:keep]], w[order]))
     (eL, VL, wL), (eR, VR, wR) = out
-    return (VL, wL) if eL <= eR else (VR, wR)
+    return (VL, wL, 0) if eL <= eR else (VR, wR, 1)
 
 
 def contract_step(M: np.ndarray, V: np.ndarray) -> np.ndarray:
@@ -67,6 +71,7 @@ class HOTRGResult:
     impurity: np.ndarray | None = None
     impurity_abs: np.ndarray | None = None
     spectra: list = field(default_factory=list)
+    sides: list = field(default_factory=list)
 
 
 def run(a: np.ndarray, chi: int, steps: int, impurity=None, impurity_abs=None) -> HOTRGResult:
@@ -86,8 +91,9 @@ def run(a: np.ndarray, chi: int, steps: int, impurity=None, impurity_abs=None) -
         Tw = rotate(T) if horizontal else T
         impw = [rotate(x) if (x is not None and horizontal) else x for x in imps]
         M = stack_vertical(Tw, Tw)
-        V, w = isometry(M, chi)
+        V, w, side = isometry(M, chi)
         res.spectra.append(w)
+        res.sides.append(side)
         Tn = contract_step(M, V)
         c = np.abs(Tn).max()
         Tn = Tn / c

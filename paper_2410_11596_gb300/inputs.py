@@ -56,6 +56,18 @@ def random_ipeps(d: int, D: int, seed: int, complex_valued: bool = False) -> np.
     return np.ascontiguousarray(A / np.abs(A).max())
 
 
+def lopsided_ipeps(D: int = 3, seed: int = 21, eps: float = 0.3) -> np.ndarray:
+    """A tensor that is NOT mirror symmetric: A[p,u,l,d,r] = X[p,u,l,d] y[r] + eps N(0,1),
+    so its right leg is close to rank one. X, y and the noise are N(0,1) from
+    ``default_rng(seed)`` (X, then y, then the noise); scaled to max|A| = 1.
+    Used to exercise the left/right choice of the HOTRG truncation."""
+    rng = np.random.default_rng(seed)
+    X = rng.standard_normal((2, D, D, D))
+    y = rng.standard_normal(D)
+    A = np.einsum("puld,r->puldr", X, y) + eps * rng.standard_normal((2, D, D, D, D))
+    return np.ascontiguousarray(A / np.abs(A).max())
+
+
 def product_state_ipeps(phi: np.ndarray, D: int = 1) -> np.ndarray:
     """Product state |phi>^N embedded at bond dimension D: A[p, 0, 0, 0, 0] = phi[p]."""
     phi = np.asarray(phi)

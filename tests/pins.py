@@ -79,3 +79,33 @@ def contract_patch(site_tensor, rows: int, cols: int, D: int):
     for c in range(cols):
         psi = np.tensordot(v, psi, axes=([0], [0]))      # close bottom legs
     return psi
+
+
+def contract_quadrant(a: np.ndarray, m: int, D: int) -> np.ndarray:
+    """Q[(x_0..x_{m-1}), (y_0..y_{m-1})]: an m x m patch of double-layer tensors
+    a[u, l, d, r] whose top and left outer legs are closed with delta(i, ibar)
+    and whose bottom legs x_j and right legs y_i stay open (the upper-left
+    corner of the lattice as a matrix between its two cuts).
+
+    Built on contract_patch: a site on the bottom row (right column) gets its
+    d (r) leg re-routed into an open leg and its boundary leg fed the dual of
+    the traced vector, w = delta / D, so that closing it there contributes 1.
+    """
+    q = D * D
+    w = _traced(D) / D
+
+    def site(i, j):
+        bottom, right = i == m - 1, j == m - 1
+        if bottom and right:
+            return ("open", np.einsum("ulxy,d,r->xyuldr", a, w, w))
+        if bottom:
+            return ("open", np.einsum("ulxr,d->xuldr", a, w))
+        if right:
+            return ("open", np.einsum("uldy,r->yuldr", a, w))
+        return a
+
+    out = contract_patch(site, m, m, D)
+    # open legs in visiting order: y_0 .. y_{m-2}, x_0 .. x_{m-2}, x_{m-1}, y_{m-1}
+    ys = list(range(m - 1)) + [2 * m - 1]
+    xs = list(range(m - 1, 2 * m - 1))
+    return out.transpose(xs + ys).reshape(q ** m, q ** m)

@@ -57,3 +57,23 @@ def test_sector_bookkeeping(ctx):
     assert info["h_even"] + info["h_odd"] == 12
     info = h.step()                                     # horizontal step truncates the vertical legs
     assert (h.t.v_even + h.t.v_odd) == 12
+
+
+@pytest.mark.parametrize("basis", ["hermitian", "dense"])
+@pytest.mark.parametrize("mirror", [False, True])
+def test_side_choice_on_lopsided_network(ctx, basis, mirror):
+    """A network that is not mirror symmetric: the first step takes the right Gram matrix
+    (the left one when the tensor is mirrored), as the oracle does, and ln Z per site after
+    four steps matches the oracle."""
+    from paper_2410_11596_gb300.api import HOTRG
+    A = inputs.lopsided_ipeps()
+    if mirror:
+        A = np.ascontiguousarray(A.transpose(0, 1, 4, 3, 2))
+    h = HOTRG(ctx, A, 4, basis=basis)
+    h.run(4)
+    r = oh.run(dl.double_layer(A), 4, 4)
+    assert [i["side"] for i in h.infos] == r.sides
+    assert r.sides[0] == (0 if mirror else 1)
+    assert h.infos[0]["discarded_right" if not mirror else "discarded_left"] < \
+        h.infos[0]["discarded_left" if not mirror else "discarded_right"]
+    assert h.log_z_per_site() == pytest.approx(oh.log_z_per_site(r), rel=1e-10, abs=1e-12)

@@ -161,3 +161,46 @@ def test_complex_truncation_preserves_hermiticity(D, chi):
     assert r.min_gap > 1e-6
     assert ob.hermiticity_error(ob.two_site_rdm(r.C, r.T, A)) < 1e-11
     assert ob.symmetry_error(ob.one_site_environment(r.C, r.T), D) < 1e-11
+
+
+def test_corner_spectrum_known_signed_values():
+    """A symmetric corner with eigenvalues of both signs: the spectrum is |lambda| in
+    descending order over the largest (a sign, an ordering or a missing division fails)."""
+    lam = np.array([-3.0, 2.0, -0.5, 1.0, 0.25, -1.5])
+    Q, _ = np.linalg.qr(np.random.default_rng(3).standard_normal((6, 6)))
+    C = Q @ np.diag(lam) @ Q.T
+    expect = np.array([3.0, 2.0, 1.5, 1.0, 0.5, 0.25]) / 3.0
+    np.testing.assert_allclose(ob.corner_spectrum(C), expect, atol=1e-14)
+
+
+@pytest.mark.parametrize("cplx", [False, True])
+def test_corner_spectrum_known_singular_values_non_normal(cplx):
+    """An oriented (complex or non-symmetric) corner C = U diag(s) V^dagger: the spectrum is
+    s / s_max; the moduli of its eigenvalues are different numbers here."""
+    rng = np.random.default_rng(4)
+    n = 7
+    X = rng.standard_normal((n, n)) + (1j * rng.standard_normal((n, n)) if cplx else 0)
+    Y = rng.standard_normal((n, n)) + (1j * rng.standard_normal((n, n)) if cplx else 0)
+    U, _ = np.linalg.qr(X)
+    V, _ = np.linalg.qr(Y)
+    s = np.array([5.0, 4.0, 2.5, 1.0, 0.7, 0.2, 0.01])
+    C = U @ np.diag(s) @ V.conj().T
+    np.testing.assert_allclose(ob.corner_spectrum(C), s / 5.0, atol=1e-13)
+    mags = np.sort(np.abs(np.linalg.eigvals(C)))[::-1]
+    assert np.abs(mags / mags[0] - s / 5.0).max() > 1e-3
+
+
+@pytest.mark.parametrize("cplx", [False, True])
+@pytest.mark.parametrize("n", [1, 2])
+def test_corner_spectrum_equals_quadrant_without_truncation(n, cplx):
+    """chi >= q^(n+1): after n moves the corner is the (n+1) x (n+1) upper-left quadrant,
+    traced on its outer legs, up to unitary changes of the boundary basis, so its spectrum is
+    that of the brute-force quadrant matrix between the two cuts."""
+    from pins import contract_quadrant
+    A = inputs.random_ipeps(2, 2, 9, complex_valued=cplx)
+    a = dl.double_layer(A)
+    r = ctmrg.run(a, 64, n)
+    Q = contract_quadrant(a, n + 1, 2)
+    s = np.linalg.svd(Q, compute_uv=False)
+    assert r.C.shape == Q.shape
+    np.testing.assert_allclose(ob.corner_spectrum(r.C), s / s[0], atol=1e-12)

@@ -48,3 +48,28 @@ def test_b_probe_detects_a_non_hermitian_network():
     e2 = hotrg.symmetry_error(a + 2 * odd, 2, 16, 1)
     assert e1 > 1e-8
     assert e2 / e1 == pytest.approx(2.0, rel=1e-2)
+
+
+@pytest.mark.parametrize("mirror", [False, True])
+def test_isometry_takes_the_side_that_discards_less(mirror):
+    """The side rule on a network that is not mirror symmetric: the chosen isometry's
+    truncation error ||M - V V^T M||^2 equals the smaller of the two best rank-chi errors
+    (discarded squared singular values of the fused left and right matricisations, from an
+    SVD), and the side is the right one unless the tensor is mirrored (l <-> r)."""
+    chi = 4
+    A = inputs.lopsided_ipeps()
+    if mirror:
+        A = A.transpose(0, 1, 4, 3, 2)
+    a = dl.double_layer(A)
+    a = a / np.abs(a).max()
+    M = hotrg.stack_vertical(a, a)
+    u, l1, l2, d, r1, r2 = M.shape
+    mats = (M.transpose(1, 2, 0, 3, 4, 5).reshape(l1 * l2, -1), M.transpose(4, 5, 0, 1, 2, 3).reshape(r1 * r2, -1))
+    best = [float(np.sum(np.linalg.svd(Mx, compute_uv=False)[chi:] ** 2)) for Mx in mats]
+    assert best[0] > 10 * best[1] if not mirror else best[1] > 10 * best[0]
+    V, _, side = hotrg.isometry(M, chi)
+    assert side == (0 if mirror else 1)
+    Mx = mats[side]
+    resid = float(np.linalg.norm(Mx - V @ (V.T @ Mx)) ** 2)
+    assert resid == pytest.approx(min(best), rel=1e-9)
+    assert hotrg.run(dl.double_layer(A), chi, 2).sides[0] == side
