@@ -46,7 +46,7 @@
 extern "C" {
 #endif
 
-#define HS_ABI_VERSION 2
+#define HS_ABI_VERSION 3
 
 typedef enum {
   HS_OK = 0,
@@ -64,8 +64,11 @@ typedef enum {
 
 typedef enum { HS_F64 = 0, HS_C128 = 1 } hs_dtype;
 
-/* Arithmetic of the block contractions. The eigen-decomposition, the
- * normalisation and the traces are FP64 in every mode. */
+/* Arithmetic of the block contractions (Sec. II.B). The normalisation, the
+ * RDM traces and the projection of the new corner are FP64 in every mode;
+ * the eigenvalues that choose the kept states are FP64 only with HS_EIG_F64
+ * (HS_EIG_F32_PROJECTED and HS_EIG_SUBSPACE choose them from FP32
+ * eigenvalues or FP32 Ritz values, see hs_eig_mode). */
 typedef enum {
   HS_PREC_F64 = 0,    /* FP64 block GEMMs */
   HS_PREC_TF32X3 = 1, /* 3-pass split TF32 on tcgen05, FP32 accumulate */
@@ -107,7 +110,11 @@ typedef struct hs_ctx_s* hs_ctx;
 
 /* The double-layer tensor a[u, l, d, r] (Sec. II.A, Fig. 1(b)) in FSO storage
  * with row legs (u, l) and column legs (d, r), all four legs of dimension D^2
- * split (n_even, n_odd). Only the even-total blocks exist for real A.
+ * split (n_even, n_odd). Only the even-total blocks exist for real A. There is
+ * no block-offset table: the FSO order fixes every block's position (block 1
+ * starts after the rows(0) x cols(0) entries of block 0, and inside a block the
+ * parity tuples follow in lexicographic order), so the sector sizes are the
+ * whole descriptor.
  *
  * Complex A (dtype HS_C128, Hermitian basis only; Sec. II.C): every block of a
  * in the eigenbasis of S is purely real (even total parity) or purely
@@ -120,7 +127,7 @@ typedef struct {
   int D;                 /* bond dimension of A */
   int n_even, n_odd;     /* per-leg sector sizes: (D(D+1)/2, D(D-1)/2) or (D^2, 0) */
   hs_basis basis;
-  hs_dtype dtype;        /* HS_F64 only in this version */
+  hs_dtype dtype;        /* HS_F64 (Z2 blocks) or HS_C128 (graded dense matrix, below) */
   double* data;          /* device, caller-owned */
   size_t capacity_bytes; /* size of data */
   /* HOTRG tensors: sectors of the vertical legs (u, d) and of the horizontal
@@ -174,7 +181,7 @@ typedef struct {
   double subspace_resid; /* largest residual / max|theta| over the candidates in the last round */
 } hs_move_info;
 
-typedef enum { HS_RDM_TWO_SITE = 0, HS_RDM_ENV_ONE_SITE = 1 } hs_rdm_kind;
+typedef enum { HS_RDM_TWO_SITE = 0, HS_RDM_ENV_ONE_SITE = 1, HS_RDM_ONE_SITE = 2 } hs_rdm_kind;
 
 /* Per-step record of hs_hotrg_step (host memory). */
 typedef struct {
@@ -219,8 +226,17 @@ size_t hs_z2_tensor_bytes(int D, hs_basis basis, hs_dtype dtype);
 hs_status hs_to_hermitian_basis(hs_ctx ctx, const double* a_dense, int D, hs_dtype dtype,
                                 double herm_tol, hs_z2_tensor* out);
 
-/* Fused form of the two calls above: from A (device, real) straight to the
- * stored blocks of a~ in `basis` (HS_BASIS_DENSE gives the plain layout).
+/* Inverse of hs_to_hermitian_basis (Sec. II.B): a = U^{x4} a~ from the stored
+ * blocks of a double layer in the Hermitian basis (t: HS_F64 Z2 blocks, or a
+ * HS_C128 graded tensor) into a_dense (device, caller-owned, (D^2)^4 doubles
+ * in the layout of hs_make_double_layer; interleaved complex128 for
+ * HS_C128). HS_ERR_SHAPE if t's sectors are not those of a double layer of
+ * bond dimension t->D (a HOTRG tensor after truncation). Asynchronous. */
+hs_status hs_from_hermitian_basis(hs_ctx ctx, const hs_z2_tensor* t, double* a_dense);
+
+/* Fused form of the two calls above: from A (device; real, or interleaved
+ * complex128 with dtype HS_C128) straight to the stored blocks of a~ in
+ * `basis` (HS_BASIS_DENSE gives the plain layout).
  * dtype HS_C128 (A interleaved complex128, Hermitian basis only) writes the
  * graded a~ (Sec. II.C). Asynchronous. */
 hs_status hs_double_layer_hermitian(hs_ctx ctx, const double* A, int d, int D, hs_dtype dtype,
@@ -299,19 +315,32 @@ hs_status hs_hotrg_step(hs_ctx ctx, hs_z2_tensor* t, int chi, int direction, hs_
 /* ---- observables (Sec. III.A) ----------------------------------------- */
 
 /* HS_RDM_TWO_SITE: rho[(s1 s2), (s1' s2')] of a horizontal bond from the
- * environment and A (device, real), not normalised, into out (device, d^4
- * doubles); then tr_out[0] = Tr rho and tr_out[1] = Tr(rho h) with h a d^2 x
- * d^2 real matrix (device). In the Hermitian basis only the S-even part of the
+ * environment and A (device; real, or interleaved complex128 with HS_C128),
+ * not normalised, into out (device, d^4 doubles); then tr_out[0] = Tr rho and
+ * tr_out[1] = Tr(rho h) with h a d^2 x d^2 real matrix (device). In the Hermitian basis only the S-even part of the
  * open double layer meets the Z2-even environment, so rho is Hermitian by
  * construction; the entries are computed for (row <= col) and mirrored.
  * HS_RDM_ENV_ONE_SITE: the one-site environment eps[u, l, d, r] (Eq. (4)),
  * (D^2)^4 doubles in the plain combined basis; h and tr_out unused.
+ * HS_RDM_ONE_SITE: the one-site reduced density matrix rho1[s, s'] =
+ * sum eps[x_u, x_l, x_d, x_r] A[s, ket(x)] conj(A[s', bra(x)]) (d^2 doubles,
+ * not normalised); tr_out[0] = Tr rho1, tr_out[1] = Tr(rho1 h) with h a d x d
+ * real matrix (device, may be NULL).
  * HS_C128 (complex A, interleaved; graded environment): rho, eps and the
  * traces are interleaved complex128 (tr_out: Re/Im of Tr rho, then of
  * Tr(rho h)), computed in complex arithmetic on the clockwise boundary ring.
  * Asynchronous. */
 hs_status hs_rdm(hs_ctx ctx, const hs_env* env, const double* A, int d, int D, hs_dtype dtype,
                  hs_rdm_kind kind, const double* h, double* out, double* tr_out);
+
+/* Normalised corner spectrum (Sec. III.A): the singular values of the corner
+ * C of env divided by the largest, in descending order, into out (device,
+ * chi_even + chi_odd doubles). Real environments: one FP64 SVD per parity
+ * block of the block-diagonal C, merged. Complex (graded) environments: C =
+ * J M J with J = diag(1, i) by parity, so the values are those of the real M
+ * (the stored matrix with its odd-odd block negated). Synchronises (to check
+ * the solver's status). */
+hs_status hs_corner_spectrum(hs_ctx ctx, const hs_env* env, double* out);
 
 /* Correlation length of a real C4v environment: xi = -1/ln|lambda_2/lambda_1|
  * of the column transfer matrix E[(alpha,l,beta),(alpha',r,beta')] =
@@ -398,9 +427,22 @@ hs_status hs_gemm_static(hs_precision precision, int M, int N, int K, const doub
  * dA[p,u,l,d,r] = sum_{IJ} drho[I,J] d rho[I,J] / d A[p,u,l,d,r] for the rho
  * of hs_rdm(HS_RDM_TWO_SITE) before any mirroring (its exact mathematical
  * derivative). drho: device, d^4 doubles, layout of rho; dA_out: device,
- * d*D^4 doubles. Real A only. Asynchronous. */
+ * d*D^4 doubles. Complex A (HS_C128, graded environment): A, drho and dA_out
+ * interleaved complex128, drho the cotangent dE/dRe rho + i dE/dIm rho and
+ * dA_out = dE/dRe A + i dE/dIm A. Asynchronous. */
 hs_status hs_rdm_vjp(hs_ctx ctx, const hs_env* env, const double* A, int d, int D, hs_dtype dtype,
                      const double* drho, double* dA_out);
+
+/* Gradient of the bond energy E = Re Tr(rho h) / Tr rho (rho of
+ * hs_rdm(HS_RDM_TWO_SITE), environment held fixed): dA_out = dE * dE/dA for
+ * real A, dE * (dE/dRe A + i dE/dIm A) for complex A (interleaved). The
+ * cotangent of rho, dE (conj(1/Tr rho) h^T - conj(Tr(rho h)/(Tr rho)^2) I), is
+ * formed on the device from the traces of the same forward contraction, then
+ * the reverse pass of hs_rdm_vjp runs. h: device, d^2 x d^2 real (required).
+ * The paper has no formula for it (differentiation of the hot path).
+ * Asynchronous. */
+hs_status hs_energy_vjp(hs_ctx ctx, const hs_env* env, const double* A, int d, int D, hs_dtype dtype,
+                        const double* h, double dE, double* dA_out);
 
 /* Workspace the context will allocate for (D, chi): reported for planning. */
 hs_status hs_workspace_query(int D, int chi, hs_precision precision, size_t* bytes);

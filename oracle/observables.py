@@ -53,7 +53,14 @@ def symmetry_error(eps: np.ndarray, D: int) -> float:
     return float(np.linalg.norm(eps - ed) / np.linalg.norm(eps + ed))
 
 
-def two_site_rdm(C: np.ndarray, T: np.ndarray, A: np.ndarray) -> np.ndarray:
+def one_site_rdm(C: np.ndarray, T: np.ndarray, A: np.ndarray) -> np.ndarray:
+    """rho1[s, s'] of one site, not normalised: the one-site environment eps
+    closed with the open double layer A_s (x) conj(A_s') (Sec. III.A)."""
+    eps = one_site_environment(C, T)
+    return np.einsum("stuldr,uldr->st", open_double_layer(A), eps)
+
+
+def two_site_rdm(C: np.ndarray, T: np.ndarray, A: np.ndarray, chunk: int | None = None) -> np.ndarray:
     """rho[(s1 s2), (s1' s2')] of a horizontal bond, not normalised.
 
     The boundary ring, clockwise: corner, top edges above site 1 and site 2,
@@ -64,19 +71,27 @@ def two_site_rdm(C: np.ndarray, T: np.ndarray, A: np.ndarray) -> np.ndarray:
     edge above site 1; the right chain runs from t to b. Each chain is closed
     with its site's open double layer; the two halves share t, b and the bond
     m between the sites.
+
+    chunk: the sum over the bottom bond b taken in slices of that many values
+    (the same sum; it only bounds the memory of the chi^2 D^6 intermediates).
     """
     d = A.shape[0]
+    chi = T.shape[0]
     a_open = open_double_layer(A)                        # [s, s', u, l, d, r]
     H = half_ring(C, T)                                  # [a, x, b]
-    # left chain L[b, d1, l1, u1, t] = T[b, d1, c] H[c, l1, e] T[e, u1, t]
-    L1 = np.tensordot(T, H, axes=([2], [0]))             # [b, d1, l1, e]
-    L2 = np.tensordot(L1, T, axes=([3], [0]))            # [b, d1, l1, u1, t]
-    LB = np.tensordot(L2, a_open, axes=([1, 2, 3], [4, 3, 2]))   # [b, t, s1, s1', m]
-    # right chain R[t, u2, r2, d2, b] = T[t, u2, c] H[c, r2, e] T[e, d2, b]
     R1 = np.tensordot(T, H, axes=([2], [0]))             # [t, u2, r2, e]
-    R2 = np.tensordot(R1, T, axes=([3], [0]))            # [t, u2, r2, d2, b]
-    RB = np.tensordot(R2, a_open, axes=([1, 2, 3], [2, 5, 4]))   # [t, b, s2, s2', m]
-    rho = np.tensordot(LB, RB, axes=([0, 1, 4], [1, 0, 4]))      # [s1, s1', s2, s2']
+    rho = 0
+    step = chi if chunk is None else chunk
+    for b0 in range(0, chi, step):
+        bs = slice(b0, min(chi, b0 + step))
+        # left chain L[b, d1, l1, u1, t] = T[b, d1, c] H[c, l1, e] T[e, u1, t]
+        L1 = np.tensordot(T[bs], H, axes=([2], [0]))     # [b, d1, l1, e]
+        L2 = np.tensordot(L1, T, axes=([3], [0]))        # [b, d1, l1, u1, t]
+        LB = np.tensordot(L2, a_open, axes=([1, 2, 3], [4, 3, 2]))   # [b, t, s1, s1', m]
+        # right chain R[t, u2, r2, d2, b] = T[t, u2, c] H[c, r2, e] T[e, d2, b]
+        R2 = np.tensordot(R1, T[:, :, bs], axes=([3], [0]))          # [t, u2, r2, d2, b]
+        RB = np.tensordot(R2, a_open, axes=([1, 2, 3], [2, 5, 4]))   # [t, b, s2, s2', m]
+        rho = rho + np.tensordot(LB, RB, axes=([0, 1, 4], [1, 0, 4]))  # [s1, s1', s2, s2']
     return rho.transpose(0, 2, 1, 3).reshape(d * d, d * d)
 
 

@@ -25,7 +25,7 @@ HS_F64, HS_C128 = 0, 1
 HS_PREC_F64, HS_PREC_TF32X3, HS_PREC_TF32, HS_PREC_BF16X3 = 0, 1, 2, 3
 HS_BASIS_DENSE, HS_BASIS_HERMITIAN = 0, 1
 HS_GEMM_OWN, HS_GEMM_CUBLAS = 0, 1
-HS_RDM_TWO_SITE, HS_RDM_ENV_ONE_SITE = 0, 1
+HS_RDM_TWO_SITE, HS_RDM_ENV_ONE_SITE, HS_RDM_ONE_SITE = 0, 1, 2
 HS_EIG_F64, HS_EIG_F32_PROJECTED, HS_EIG_SUBSPACE = 0, 1, 2
 
 
@@ -85,6 +85,8 @@ _PROTOS = {
     "hs_ctmrg_move_batched": (c_int, [POINTER(c_void_p), c_int, POINTER(POINTER(Z2Tensor)), POINTER(POINTER(Env)),
                                       POINTER(c_int), POINTER(MoveInfo), POINTER(c_double), c_int]),
     "hs_env_to_dense": (c_int, [c_void_p, POINTER(Env), c_void_p, c_void_p]),
+    "hs_corner_spectrum": (c_int, [c_void_p, POINTER(Env), c_void_p]),
+    "hs_from_hermitian_basis": (c_int, [c_void_p, POINTER(Z2Tensor), c_void_p]),
     "hs_correlation_length": (c_int, [c_void_p, POINTER(Env), c_void_p, c_int, c_int, c_int, c_double,
                                       POINTER(c_double), POINTER(c_double)]),
     "hs_rdm": (c_int, [c_void_p, POINTER(Env), c_void_p, c_int, c_int, c_int, c_int, c_void_p, c_void_p,
@@ -96,6 +98,8 @@ _PROTOS = {
                                 POINTER(ctypes.c_longlong)]),
     "hs_gemm": (c_int, [c_void_p, c_int, c_int, c_int, c_int, c_void_p, c_int, c_void_p, c_int, c_void_p, c_int]),
     "hs_rdm_vjp": (c_int, [c_void_p, POINTER(Env), c_void_p, c_int, c_int, c_int, c_void_p, c_void_p]),
+    "hs_energy_vjp": (c_int, [c_void_p, POINTER(Env), c_void_p, c_int, c_int, c_int, c_void_p, c_double,
+                              c_void_p]),
     "hs_hotrg_tensor_bytes": (c_size_t, [c_int, c_int]),
     "hs_hotrg_init": (c_int, [c_void_p, POINTER(Z2Tensor), POINTER(Z2Tensor), POINTER(c_double)]),
     "hs_hotrg_step": (c_int, [c_void_p, POINTER(Z2Tensor), c_int, c_int, POINTER(HotrgInfo)]),
@@ -223,6 +227,14 @@ def hs_env_to_dense(ctx: int, env: Env, C_dense, T_dense) -> None:
     check(load().hs_env_to_dense(ctx, ctypes.byref(env), ptr(C_dense), ptr(T_dense)))
 
 
+def hs_corner_spectrum(ctx: int, env: Env, out) -> None:
+    check(load().hs_corner_spectrum(ctx, ctypes.byref(env), ptr(out)))
+
+
+def hs_from_hermitian_basis(ctx: int, t: Z2Tensor, a_dense) -> None:
+    check(load().hs_from_hermitian_basis(ctx, ctypes.byref(t), ptr(a_dense)))
+
+
 def hs_rdm(ctx: int, env: Env, A, d: int, D: int, dtype: int, kind: int, h, out, tr_out) -> None:
     check(load().hs_rdm(ctx, ctypes.byref(env), ptr(A), d, D, dtype, kind,
                         ptr(h) if h is not None else None, ptr(out),
@@ -287,3 +299,7 @@ def hs_hotrg_step(ctx: int, t: Z2Tensor, chi: int, direction: int) -> dict:
 
 def hs_rdm_vjp(ctx: int, env: Env, A, d: int, D: int, drho, dA, dtype: int = HS_F64) -> None:
     check(load().hs_rdm_vjp(ctx, ctypes.byref(env), ptr(A), d, D, dtype, ptr(drho), ptr(dA)))
+
+
+def hs_energy_vjp(ctx: int, env: Env, A, d: int, D: int, dtype: int, h, dE: float, dA) -> None:
+    check(load().hs_energy_vjp(ctx, ctypes.byref(env), ptr(A), d, D, dtype, ptr(h), float(dE), ptr(dA)))

@@ -130,11 +130,44 @@ class CTMRG:
     def chi_now(self) -> int:
         return self.env.chi_even + self.env.chi_odd
 
-    def corner_spectrum(self) -> np.ndarray:
-        """Singular values of C divided by the largest (host-side post-processing of C)."""
-        C, _ = self.dense_env()
-        sv = np.linalg.svd(C.cpu().numpy(), compute_uv=False)
-        return sv / sv[0]
+    @on_ctx_stream
+    def corner_spectrum(self) -> torch.Tensor:
+        """Singular values of C divided by the largest, descending (hs_corner_spectrum, on the GPU)."""
+        out = torch.empty(self.chi_now, dtype=torch.float64, device=self.A.device)
+        L.hs_corner_spectrum(self.ctx.handle, self.env, out)
+        return out
+
+    @on_ctx_stream
+    def double_layer_dense(self) -> torch.Tensor:
+        """The double layer back in the plain combined basis, a[u, l, d, r] (hs_from_hermitian_basis);
+        complex128 for complex A. Hermitian basis only."""
+        q = self.D * self.D
+        if self.complex:
+            a = torch.empty((q, q, q, q, 2), dtype=torch.float64, device=self.A.device)
+            L.hs_from_hermitian_basis(self.ctx.handle, self.a, a)
+            return torch.view_as_complex(a)
+        a = torch.empty((q, q, q, q), dtype=torch.float64, device=self.A.device)
+        L.hs_from_hermitian_basis(self.ctx.handle, self.a, a)
+        return a
+
+    @on_ctx_stream
+    def rdm1(self, h1: np.ndarray | None = None):
+        """(rho1, Tr rho1, Tr rho1 h1) of one site (HS_RDM_ONE_SITE); h1 a d x d real matrix.
+        For complex A, rho1 is complex128 and the traces are complex."""
+        dev = self.A.device
+        d = self.d
+        hd = None if h1 is None else torch.from_numpy(np.ascontiguousarray(np.real(h1), dtype=np.float64)).to(dev)
+        if self.complex:
+            rho = torch.empty((d, d, 2), dtype=torch.float64, device=dev)
+            tr = torch.empty(4, dtype=torch.float64, device=dev)
+            L.hs_rdm(self.ctx.handle, self.env, self.A, d, self.D, L.HS_C128, L.HS_RDM_ONE_SITE, hd, rho, tr)
+            t = tr.cpu().numpy()
+            return torch.view_as_complex(rho), complex(t[0], t[1]), complex(t[2], t[3])
+        rho = torch.empty((d, d), dtype=torch.float64, device=dev)
+        tr = torch.empty(2, dtype=torch.float64, device=dev)
+        L.hs_rdm(self.ctx.handle, self.env, self.A, d, self.D, L.HS_F64, L.HS_RDM_ONE_SITE, hd, rho, tr)
+        t = tr.cpu().numpy()
+        return rho, float(t[0]), float(t[1])
 
     @on_ctx_stream
     def dense_env(self) -> tuple[torch.Tensor, torch.Tensor]:
@@ -203,6 +236,18 @@ class CTMRG:
             return torch.view_as_complex(dA)
         dA = torch.empty_like(A)
         L.hs_rdm_vjp(self.ctx.handle, self.env, A.contiguous(), self.d, self.D, drho.contiguous(), dA)
+        return dA
+
+    @on_ctx_stream
+    def energy_vjp(self, A: torch.Tensor, h: torch.Tensor, dE: float) -> torch.Tensor:
+        """dE * gradient of E = Re Tr(rho h) / Tr rho with respect to A, environment fixed (hs_energy_vjp)."""
+        if self.complex:
+            Ai = torch.view_as_real(A.to(torch.complex128)).contiguous()
+            dA = torch.empty_like(Ai)
+            L.hs_energy_vjp(self.ctx.handle, self.env, Ai, self.d, self.D, L.HS_C128, h.contiguous(), dE, dA)
+            return torch.view_as_complex(dA)
+        dA = torch.empty_like(A)
+        L.hs_energy_vjp(self.ctx.handle, self.env, A.contiguous(), self.d, self.D, L.HS_F64, h.contiguous(), dE, dA)
         return dA
 
     def correlation_length(self, max_iter: int = 200, tol: float = 1e-12) -> float:
@@ -301,25 +346,22 @@ class BatchedCTMRG:
 class EnergyFn(torch.autograd.Function):
     """E(A) = Re Tr(rho(A) h) / Tr rho(A) with the environment of `ctm` held fixed.
 
-    forward: hs_rdm; backward: the cotangent of rho, d E / d rho = conj(1 / Tr rho) h^T
-    - conj(Tr rho h / (Tr rho)^2) I (dE/dRe + i dE/dIm for complex rho), then the
-    hand-written adjoint hs_rdm_vjp. For complex A the gradient is dE/dRe A + i dE/dIm A.
+    forward: hs_rdm; backward: hs_energy_vjp (the cotangent of rho and the
+    hand-written adjoint, both in the library). For complex A the gradient is
+    dE/dRe A + i dE/dIm A.
     """
 
     @staticmethod
     def forward(fctx, A: torch.Tensor, ctm: "CTMRG", h: torch.Tensor):
         rho, tr = ctm.rdm2_of(A.detach(), h)
         fctx.ctm = ctm
-        fctx.save_for_backward(A.detach(), h, tr)
+        fctx.save_for_backward(A.detach(), h)
         return torch.real(tr[1] / tr[0])
 
     @staticmethod
     def backward(fctx, g):
-        A, h, tr = fctx.saved_tensors
-        n = h.shape[0]
-        eye = torch.eye(n, dtype=tr.dtype, device=h.device)
-        drho = g * (torch.conj(1.0 / tr[0]) * h.t().to(tr.dtype) - torch.conj(tr[1] / tr[0] ** 2) * eye)
-        return fctx.ctm.rdm2_vjp(A, drho), None, None
+        A, h = fctx.saved_tensors
+        return fctx.ctm.energy_vjp(A, h, float(g)), None, None
 
 
 def bond_energy(ctm: CTMRG, A: torch.Tensor, h: np.ndarray | torch.Tensor) -> torch.Tensor:

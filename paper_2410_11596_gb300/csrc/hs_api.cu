@@ -965,7 +965,7 @@ hs_status subspace_projector(hs_ctx ctx, hs_env* env, int chi, int n0, int n1, d
   if (!(ctx->ws_valid && ctx->ws_env == env)) return HS_OK;
   *reason = 2;
   if (!(ctx->ws_n[0] == n0 && ctx->ws_n[1] == n1)) return HS_OK;
-  constexpr int kOver = 24, kMaxIt = 5;
+  constexpr int kOver = 24, kMinOver = 8, kMaxIt = 5;
   cudaStream_t s = ctx->stream;
   const bool tc = env->precision != HS_PREC_F64;
   // residual tolerance relative to max|theta|: above the rounding floor of
@@ -974,9 +974,11 @@ hs_status subspace_projector(hs_ctx ctx, hs_env* env, int chi, int n0, int n1, d
   const hs_precision prec = env->precision;
   int m[2];
   for (int b = 0; b < 2; ++b) {
-    m[b] = n[b] == 0 ? 0 : (ctx->ws_k[b] + kOver < n[b] ? ctx->ws_k[b] + kOver : n[b]);
+    // k + 24 rows, at most the block and the Rayleigh-Ritz kernels' limit;
+    // at least 8 rows beyond the kept ones unless the subspace is the block
+    m[b] = n[b] == 0 ? 0 : std::min(std::min(ctx->ws_k[b] + kOver, n[b]), max_subspace());
     *reason = 3;
-    if (m[b] > max_subspace()) return HS_OK;
+    if (m[b] < n[b] && m[b] < ctx->ws_k[b] + kMinOver) return HS_OK;
   }
   int* bad = static_cast<int*>(ctx->info.p) + 2;
   HS_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), s));
@@ -1684,7 +1686,7 @@ hs_status hs_ctmrg_move(hs_ctx ctx, const hs_z2_tensor* a, hs_env* env, int chi,
     int mnext[2];
     for (int b = 0; b < 2; ++b) {
       const int nb = b ? n1 : n0;
-      mnext[b] = cn.n[b] + 24 < nb ? cn.n[b] + 24 : nb;
+      mnext[b] = std::min(std::min(cn.n[b] + 24, nb), max_subspace());
       if (sub_done) mnext[b] = b ? ns1 : ns0;
     }
     const long long nws = (long long)mnext[0] * n0 + (long long)mnext[1] * n1;
@@ -1835,7 +1837,7 @@ hs_status hs_profile_read(hs_ctx ctx, double* phase_ms, double* phase_flops, int
 hs_status hs_gemm(hs_ctx ctx, hs_precision precision, int M, int N, int K, const double* A, int lda,
                   const double* B, int ldb, double* C, int ldc) {
   HS_TRY(check_ctx(ctx));
-  if (M < 0 || N < 0 || K < 0 || lda < K || ldb < K || ldc < N || (M * N > 0 && (!A || !B || !C)))
+  if (M < 0 || N < 0 || K < 0 || lda < K || ldb < K || ldc < N || (M > 0 && N > 0 && (!A || !B || !C)))
     return fail(HS_ERR_INVALID_ARG, "bad arguments");
   if (M == 0 || N == 0) return HS_OK;
   if (precision == HS_PREC_F64) {

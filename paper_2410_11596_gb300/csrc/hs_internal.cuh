@@ -11,6 +11,9 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <mutex>
+#include <set>
+#include <tuple>
 #include <utility>
 #include <cuda_runtime.h>
 
@@ -70,6 +73,36 @@ inline cudaError_t hs_launch_cluster(void (*kernel)(KArgs...), dim3 grid, dim3 b
   cfg.attrs = attr;
   cfg.numAttrs = 2;
   return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
+// Opt a kernel in to `bytes` of dynamic shared memory on the current device.
+// The attribute belongs to the device's context, so it is set once per
+// (kernel, device, size) rather than once per process.
+inline cudaError_t ensure_smem_attr(const void* func, int bytes) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  static std::mutex mu;
+  static std::set<std::tuple<const void*, int, int>> done;
+  std::lock_guard<std::mutex> lk(mu);
+  const auto key = std::make_tuple(func, dev, bytes);
+  if (done.count(key)) return cudaSuccess;
+  e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess) done.insert(key);
+  return e;
+}
+
+// Number of SMs of the current device (cached per device; 148 if unknown).
+inline int device_sms() {
+  constexpr int kDevs = 64;
+  static int cache[kDevs] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) return 148;
+  if (dev < kDevs && cache[dev] > 0) return cache[dev];
+  int n = 0;
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 148;
+  if (dev < kDevs) cache[dev] = n;
+  return n;
 }
 
 struct Sect {
@@ -366,6 +399,11 @@ cudaError_t launch_double_layer_dense(const double* A, int d, int D, bool cplx, 
 // even-total ones (FSO) and atomically maxes |odd| and |all| into maxes[0..1].
 cudaError_t launch_rotate_dense_to_blocks(const double* a, int D, double* out,
                                           unsigned long long* maxes, cudaStream_t s);
+
+// Inverse rotation: the stored blocks of a~ (real FSO [(u,l)|(d,r)], or a
+// graded complex matrix) back to the dense plain combined basis (D^2)^4
+// (interleaved complex128 when graded).
+cudaError_t launch_from_hermitian(const double* t, int D, bool graded, double* out, cudaStream_t s);
 
 // Traced-boundary initial C0 and T0 (FSO) from the stored blocks of a.
 cudaError_t launch_ctmrg_init(const double* a_blocks, int D, bool hermitian, double* C, double* T,

@@ -61,7 +61,7 @@ using namespace hs;
 extern "C" hs_status hs_gemm_static(hs_precision precision, int M, int N, int K, const double* A, int lda,
                                     const double* B, int ldb, double* C, int ldc, int* status_out,
                                     void* stream) {
-  if (M < 0 || N < 0 || K < 0 || lda < K || ldb < K || ldc < N || (M * N > 0 && (!A || !B || !C)) ||
+  if (M < 0 || N < 0 || K < 0 || lda < K || ldb < K || ldc < N || (M > 0 && N > 0 && (!A || !B || !C)) ||
       !status_out)
     return fail(HS_ERR_INVALID_ARG, "bad arguments");
   if (precision != HS_PREC_TF32X3 && precision != HS_PREC_TF32 && precision != HS_PREC_BF16X3)

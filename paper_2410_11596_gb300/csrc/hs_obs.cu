@@ -119,6 +119,114 @@ __global__ void finish_rho_kernel(const double* __restrict__ rho4, int d, bool m
   }
 }
 
+// One-site reduced density matrix from the one-site environment eps (plain
+// combined basis, legs (u, l, d, r), x = ket + D * bra on every leg):
+//   rho1[s, s'] = sum_x eps[x_u, x_l, x_d, x_r] A[s, ket(x)] conj(A[s', bra(x)]),
+// one CTA per (s, s'); complex eps, A and rho1 interleaved.
+__global__ void one_site_rho_kernel(const double* __restrict__ eps, const double* __restrict__ A, int d, int D,
+                                    bool cplx, double* __restrict__ rho) {
+  hs_pdl_enter();
+  const int sk = blockIdx.x / d, sb = blockIdx.x % d;
+  const int q = D * D;
+  const long long D4 = (long long)D * D * D * D;
+  const long long total = (long long)q * q * q * q;
+  double re = 0.0, im = 0.0;
+  for (long long e = threadIdx.x; e < total; e += blockDim.x) {
+    const int xr = (int)(e % q), xd = (int)((e / q) % q), xl = (int)((e / q / q) % q), xu = (int)(e / q / q / q);
+    const long long ik = (((long long)(xu % D) * D + xl % D) * D + xd % D) * D + xr % D;
+    const long long ib = (((long long)(xu / D) * D + xl / D) * D + xd / D) * D + xr / D;
+    if (!cplx) {
+      re += eps[e] * A[sk * D4 + ik] * A[sb * D4 + ib];
+      continue;
+    }
+    const double kr = A[2 * (sk * D4 + ik)], ki = A[2 * (sk * D4 + ik) + 1];
+    const double br = A[2 * (sb * D4 + ib)], bi = -A[2 * (sb * D4 + ib) + 1];  // conj
+    const double pr = kr * br - ki * bi, pi = kr * bi + ki * br;
+    const double er = eps[2 * e], ei = eps[2 * e + 1];
+    re += er * pr - ei * pi;
+    im += er * pi + ei * pr;
+  }
+  __shared__ double red[2][32];
+  for (int o = 16; o > 0; o >>= 1) {
+    re += __shfl_down_sync(0xffffffffu, re, o);
+    im += __shfl_down_sync(0xffffffffu, im, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x / 32] = re;
+    red[1][threadIdx.x / 32] = im;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0;
+    for (int w = 0; w < (int)(blockDim.x / 32); ++w) {
+      a += red[0][w];
+      b += red[1][w];
+    }
+    if (cplx) {
+      rho[2 * blockIdx.x] = a;
+      rho[2 * blockIdx.x + 1] = b;
+    } else {
+      rho[blockIdx.x] = a;
+    }
+  }
+}
+
+// tr[0] = Tr rho1, tr[1] = Tr(rho1 h) (h a real d x d matrix, may be null);
+// complex: tr = (Re, Im) of each.
+__global__ void finish_rho1_kernel(const double* __restrict__ rho, int d, bool cplx, const double* __restrict__ h,
+                                   double* __restrict__ tr) {
+  hs_pdl_enter();
+  if (threadIdx.x != 0) return;
+  double t0r = 0.0, t0i = 0.0, t1r = 0.0, t1i = 0.0;
+  for (int i = 0; i < d; ++i) {
+    t0r += cplx ? rho[2 * (i * d + i)] : rho[i * d + i];
+    t0i += cplx ? rho[2 * (i * d + i) + 1] : 0.0;
+    if (h)
+      for (int j = 0; j < d; ++j) {
+        t1r += (cplx ? rho[2 * (i * d + j)] : rho[i * d + j]) * h[j * d + i];
+        t1i += cplx ? rho[2 * (i * d + j) + 1] * h[j * d + i] : 0.0;
+      }
+  }
+  if (cplx) {
+    tr[0] = t0r;
+    tr[1] = t0i;
+    tr[2] = t1r;
+    tr[3] = t1i;
+  } else {
+    tr[0] = t0r;
+    tr[1] = t1r;
+  }
+}
+
+// Cotangent of rho for E = Re Tr(rho h) / Tr rho:
+//   drho[I, J] = dE (conj(1 / t0) h[J, I] - conj(t1 / t0^2) delta_IJ),
+// t0 = Tr rho, t1 = Tr(rho h) as written by the finish kernels (real: tr =
+// (t0, t1); complex: tr = (Re t0, Im t0, Re t1, Im t1), drho interleaved).
+__global__ void energy_cotangent_kernel(const double* __restrict__ tr, const double* __restrict__ h, int n,
+                                        bool cplx, double dE, double* __restrict__ drho) {
+  hs_pdl_enter();
+  const double t0r = tr[0], t0i = cplx ? tr[1] : 0.0;
+  const double t1r = cplx ? tr[2] : tr[1], t1i = cplx ? tr[3] : 0.0;
+  // a = 1 / t0, b = t1 / t0^2 (complex division by |t0|^2)
+  const double m2 = t0r * t0r + t0i * t0i;
+  const double ar = t0r / m2, ai = -t0i / m2;
+  const double sr = ar * ar - ai * ai, si = 2.0 * ar * ai;  // 1 / t0^2
+  const double br = t1r * sr - t1i * si, bi = t1r * si + t1i * sr;
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+    const int I = e / n, J = e % n;
+    const double hv = h ? h[J * n + I] : 0.0;
+    // conj(a) hv - conj(b) delta
+    const double re = ar * hv - (I == J ? br : 0.0);
+    const double im = -ai * hv + (I == J ? bi : 0.0);
+    if (cplx) {
+      drho[2 * e] = dE * re;
+      drho[2 * e + 1] = dE * im;
+    } else {
+      drho[e] = dE * re;
+    }
+  }
+}
+
 unsigned grid_for(long long n) {
   long long g = (n + 255) / 256;
   if (g > 4096) g = 4096;
@@ -524,16 +632,36 @@ hs_status rdm_chain(hs_ctx ctx, const hs_env* env, const double* A, int d, int D
   return HS_OK;
 }
 
+static hs_status rdm_vjp_after_chain(hs_ctx ctx, const hs_env* env, const double* A, int d, int D, const double* drho,
+                                     double* dA_out);
+
 extern "C" hs_status hs_rdm(hs_ctx ctx, const hs_env* env, const double* A, int d, int D,
                             hs_dtype dtype, hs_rdm_kind kind, const double* h, double* out,
                             double* tr_out) {
   HS_TRY(check_ctx(ctx));
   if (!env || !A || !out || d <= 0 || D != env->D) return fail(HS_ERR_INVALID_ARG, "bad arguments");
   if (dtype != HS_F64 && dtype != HS_C128) return fail(HS_ERR_DTYPE, "unknown dtype");
-  if (kind != HS_RDM_TWO_SITE && kind != HS_RDM_ENV_ONE_SITE)
+  if (kind != HS_RDM_TWO_SITE && kind != HS_RDM_ENV_ONE_SITE && kind != HS_RDM_ONE_SITE)
     return fail(HS_ERR_INVALID_ARG, "unknown rdm kind");
-  if (kind == HS_RDM_TWO_SITE && !tr_out) return fail(HS_ERR_INVALID_ARG, "tr_out is required");
+  if (kind != HS_RDM_ENV_ONE_SITE && !tr_out) return fail(HS_ERR_INVALID_ARG, "tr_out is required");
   if ((dtype == HS_C128) != (env->dtype == HS_C128)) return fail(HS_ERR_DTYPE, "A and environment disagree on dtype");
+  if (kind == HS_RDM_ONE_SITE) {
+    // eps first (workspace), then the contraction with A and conj(A)
+    const bool cplx = dtype == HS_C128;
+    const long long q = (long long)D * D, n4 = q * q * q * q;
+    DBuf& eps = ctx->hb[11];
+    HS_TRY(eps.ensure((size_t)n4 * (cplx ? 2 : 1) * sizeof(double)));
+    if (cplx)
+      HS_TRY(rdm_complex(ctx, env, A, d, D, HS_RDM_ENV_ONE_SITE, nullptr, eps.d(), nullptr));
+    else
+      HS_TRY(rdm_chain(ctx, env, A, d, D, HS_RDM_ENV_ONE_SITE, eps.d()));
+    hs_launch(one_site_rho_kernel, d * d, 256, 0, ctx->stream, eps.d(), A, d, D, cplx, out);
+    HS_CUDA(cudaGetLastError());
+    hs_launch(finish_rho1_kernel, 1, 32, 0, ctx->stream, out, d, cplx, h, tr_out);
+    HS_CUDA(cudaGetLastError());
+    ctx->launches += 2;
+    return HS_OK;
+  }
   if (dtype == HS_C128) return rdm_complex(ctx, env, A, d, D, kind, h, out, tr_out);
   HS_TRY(rdm_chain(ctx, env, A, d, D, kind, out));
   if (kind == HS_RDM_ENV_ONE_SITE) return HS_OK;
@@ -551,6 +679,42 @@ extern "C" hs_status hs_rdm_vjp(hs_ctx ctx, const hs_env* env, const double* A, 
   if ((dtype == HS_C128) != (env->dtype == HS_C128)) return fail(HS_ERR_DTYPE, "A and environment disagree on dtype");
   if (dtype == HS_C128) return rdm_vjp_complex(ctx, env, A, d, D, drho, dA_out);
   HS_TRY(rdm_chain(ctx, env, A, d, D, HS_RDM_TWO_SITE, nullptr));
+  return rdm_vjp_after_chain(ctx, env, A, d, D, drho, dA_out);
+}
+
+extern "C" hs_status hs_energy_vjp(hs_ctx ctx, const hs_env* env, const double* A, int d, int D, hs_dtype dtype,
+                                   const double* h, double dE, double* dA_out) {
+  HS_TRY(check_ctx(ctx));
+  if (!env || !A || !h || !dA_out || d <= 0 || D != env->D) return fail(HS_ERR_INVALID_ARG, "bad arguments");
+  if (dtype != HS_F64 && dtype != HS_C128) return fail(HS_ERR_DTYPE, "unknown dtype");
+  if ((dtype == HS_C128) != (env->dtype == HS_C128)) return fail(HS_ERR_DTYPE, "A and environment disagree on dtype");
+  const bool cplx = dtype == HS_C128;
+  const int n = d * d;
+  // rho (scratch), its traces, the cotangent
+  DBuf& w = ctx->hb[12];
+  HS_TRY(w.ensure((size_t)(2 * n * n * (cplx ? 2 : 1) + 8) * sizeof(double)));
+  double* rho = w.d();
+  double* drho = rho + (long long)n * n * (cplx ? 2 : 1);
+  double* tr = drho + (long long)n * n * (cplx ? 2 : 1);
+  if (cplx) {
+    HS_TRY(rdm_complex(ctx, env, A, d, D, HS_RDM_TWO_SITE, h, rho, tr));
+  } else {
+    HS_TRY(rdm_chain(ctx, env, A, d, D, HS_RDM_TWO_SITE, nullptr));
+    hs_launch(finish_rho_kernel, 1, 256, 0, ctx->stream, ctx->r[6].d(), d, env->basis == HS_BASIS_HERMITIAN, h, rho,
+              tr);
+    HS_CUDA(cudaGetLastError());
+  }
+  hs_launch(energy_cotangent_kernel, 1, 256, 0, ctx->stream, (const double*)tr, h, n, cplx, dE, drho);
+  HS_CUDA(cudaGetLastError());
+  ctx->launches += 2;
+  if (cplx) return rdm_vjp_complex(ctx, env, A, d, D, drho, dA_out);
+  return rdm_vjp_after_chain(ctx, env, A, d, D, drho, dA_out);
+}
+
+// Reverse pass of the real two-site chain; rdm_chain(HS_RDM_TWO_SITE) must have
+// run on the same environment and A just before (its buffers r[8..15]).
+static hs_status rdm_vjp_after_chain(hs_ctx ctx, const hs_env* env, const double* A, int d, int D, const double* drho,
+                                     double* dA_out) {
   cudaStream_t s = ctx->stream;
   const hs_gemm_backend be = env->gemm_backend;
   const long long chi = env->chi_even + env->chi_odd, q = (long long)D * D, c2 = chi * chi,

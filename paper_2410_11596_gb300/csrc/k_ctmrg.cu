@@ -543,9 +543,8 @@ cudaError_t launch_select(const double* w0, int n0, const double* w1, int n1, in
   if (!staged) smem = picks;
   if (smem > kSmemMax) return cudaErrorInvalidValue;
   if (smem > 48 * 1024) {
-    // opt in beyond the default 48 KB only when needed (once per process)
-    static const cudaError_t attr_err =
-        cudaFuncSetAttribute(select_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax);
+    // opt in beyond the default 48 KB only when needed (once per device)
+    const cudaError_t attr_err = ensure_smem_attr(reinterpret_cast<const void*>(select_kernel), (int)kSmemMax);
     if (attr_err != cudaSuccess) return attr_err;
   }
   hs_launch(select_kernel, 1, 256, smem, s, w0, n0, w1, n1, chi, idx, lam, out, staged);

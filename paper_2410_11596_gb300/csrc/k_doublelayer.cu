@@ -219,6 +219,80 @@ __global__ void rotate_dense_kernel(const double* __restrict__ a, int D, double*
   atomicMax(&maxes[1], (unsigned long long)__double_as_longlong(mall));
 }
 
+// Index of the Hermitian basis state pair (k, l), k < l, lexicographic (the
+// inverse of pair_of).
+__device__ __forceinline__ int pair_index(int k, int l, int D) { return k * (D - 1) - k * (k - 1) / 2 + (l - k - 1); }
+
+// The (at most two) basis states X of one leg that contain the plain state
+// x = i + D*ibar, with the coefficient U[x, X] of x in X (Sec. II.B).
+__device__ __forceinline__ Terms plain_terms(int x, int D) {
+  Terms t;
+  const int i = x % D, ib = x / D;
+  if (i == ib) {
+    t.n = 1;
+    t.ket[0] = i;  // ket[] holds the basis state X here
+    t.c[0] = 1.0;
+    return t;
+  }
+  const int qe = D * (D + 1) / 2;
+  const int k = i < ib ? i : ib, l = i < ib ? ib : i;
+  const int m = pair_index(k, l, D);
+  const double r = 0.70710678118654752440;
+  t.n = 2;
+  t.ket[0] = D + m;  // (k l' + l k')/sqrt2
+  t.c[0] = r;
+  t.ket[1] = qe + m;  // (k l' - l k')/sqrt2: + for (ket k, bra l), - for (ket l, bra k)
+  t.c[1] = i < ib ? r : -r;
+  return t;
+}
+
+// a[x_u, x_l, x_d, x_r] = sum_X U[x_u, X_u] .. U[x_r, X_r] a~[X_u, .., X_r]: the
+// stored blocks of a~ (real FSO, or a graded complex matrix) back to the
+// plain combined basis; complex output interleaved.
+__global__ void from_hermitian_kernel(const double* __restrict__ t, int D, bool graded, double* __restrict__ out) {
+  hs_pdl_enter();
+  const int q = D * D;
+  const int qe = D * (D + 1) / 2, qo = q - qe;
+  const Fused f = fused2(make_sect(qe, qo), make_sect(qe, qo));
+  const long long f0 = fused_size(f, 0);
+  const long long q2 = (long long)q * q;
+  const long long total = q2 * q2;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int xr = (int)(e % q), xd = (int)((e / q) % q), xl = (int)((e / q / q) % q), xu = (int)(e / q / q / q);
+    const Terms tu = plain_terms(xu, D), tl = plain_terms(xl, D), td = plain_terms(xd, D), tr = plain_terms(xr, D);
+    double re = 0.0, im = 0.0;
+    for (int a = 0; a < tu.n; ++a)
+      for (int b = 0; b < tl.n; ++b)
+        for (int c = 0; c < td.n; ++c)
+          for (int g = 0; g < tr.n; ++g) {
+            const int Xu = tu.ket[a], Xl = tl.ket[b], Xd = td.ket[c], Xr = tr.ket[g];
+            const double coef = tu.c[a] * tl.c[b] * td.c[c] * tr.c[g];
+            if (!graded) {
+              const long long pos = fso4(Xu, Xl, Xd, Xr, qe, qo);
+              if (pos >= 0) re += coef * t[pos];
+              continue;
+            }
+            const int pu = Xu >= qe, pl = Xl >= qe, pd = Xd >= qe, pr = Xr >= qe;
+            const long long row = ((pu ^ pl) ? f0 : 0) + tuple_offset(f, (pu << 1) | pl) +
+                                  (long long)(Xu - pu * qe) * (pl ? qo : qe) + (Xl - pl * qe);
+            const long long col = ((pd ^ pr) ? f0 : 0) + tuple_offset(f, (pd << 1) | pr) +
+                                  (long long)(Xd - pd * qe) * (pr ? qo : qe) + (Xr - pr * qe);
+            const double v = t[row * q2 + col];
+            if ((pu + pl + pd + pr) & 1)
+              im += coef * v;
+            else
+              re += coef * v;
+          }
+    if (graded) {
+      out[2 * e] = re;
+      out[2 * e + 1] = im;
+    } else {
+      out[e] = re;
+    }
+  }
+}
+
 unsigned grid_for(long long n) {
   long long g = (n + 255) / 256;
   if (g > 4096) g = 4096;
@@ -247,6 +321,12 @@ cudaError_t launch_double_layer_dense(const double* A, int d, int D, bool cplx, 
                                       cudaStream_t s) {
   const long long q = (long long)D * D;
   hs_launch(double_layer_dense_kernel, grid_for(q * q * q * q), 256, 0, s, A, d, D, cplx, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_from_hermitian(const double* t, int D, bool graded, double* out, cudaStream_t s) {
+  const long long q = (long long)D * D;
+  hs_launch(from_hermitian_kernel, grid_for(q * q * q * q), 256, 0, s, t, D, graded, out);
   return cudaGetLastError();
 }
 

@@ -692,9 +692,9 @@ __global__ void tc_splitk_reduce_kernel(const SplitReds reds) {
 template <int NPASS, int EB, int NM, bool PS>
 cudaError_t launch_tc(const Maps& all, const Group& g, int grid, int tiles, int* err, cudaStream_t s) {
   using K = Cfg<NPASS, EB>;
-  // set once per process and instantiation (thread-safe static initialisation)
-  static const cudaError_t attr_err = cudaFuncSetAttribute(gemm_tc_kernel<NPASS, EB, NM, PS>,
-                                                           cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM);
+  // set once per device and instantiation
+  const cudaError_t attr_err =
+      ensure_smem_attr(reinterpret_cast<const void*>(gemm_tc_kernel<NPASS, EB, NM, PS>), K::SMEM);
   if (attr_err != cudaSuccess) return attr_err;
   MapsN<NM> maps;
   for (int j = 0; j < NM; ++j)
@@ -717,6 +717,7 @@ cudaError_t run(const TcProblem* probs, int nprob, int* err, cudaStream_t s, dou
   SplitRed* red = reds.r;
   int nred = 0;
   long long part_used = 0;
+  const int sms = device_sms();
   for (int i = 0; i < nprob; ++i) {
     const TcProblem& p = probs[i];
     if (p.M <= 0 || p.N <= 0) continue;
@@ -737,12 +738,12 @@ cudaError_t run(const TcProblem* probs, int nprob, int* err, cudaStream_t s, dou
       psi = j;
       g.ps[j] = *p.ps;
     }
-    // split K when this problem's tiles cannot fill the 152 SMs and each
+    // split K when this problem's tiles cannot fill the SMs and each
     // split keeps at least 4 K steps; partials go to `part` (not for a
     // permuted split output)
     int ns = 1;
-    if (part && ptiles < 152 && psi < 0) {
-      ns = (152 + ptiles - 1) / ptiles;
+    if (part && ptiles < sms && psi < 0) {
+      ns = (sms + ptiles - 1) / ptiles;
       ns = ns < ktiles / 4 ? ns : ktiles / 4;
       ns = ns < 8 ? ns : 8;
       const long long need = (long long)ns * p.M * p.N;
@@ -779,12 +780,6 @@ cudaError_t run(const TcProblem* probs, int nprob, int* err, cudaStream_t s, dou
     }
   }
   if (tiles == 0) return cudaSuccess;
-  static const int sms = [] {
-    int dev = 0, n = 0;
-    cudaGetDevice(&dev);
-    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 148;
-    return n;
-  }();
   const int grid = tiles < sms ? tiles : sms;
   // launches with a permuted split output take their own instantiation (the
   // split epilogue; at most two operand pairs), the others the plain one

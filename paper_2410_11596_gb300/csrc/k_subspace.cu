@@ -581,9 +581,9 @@ cudaError_t launch_jacobi_eig_pair(float* A0, int m0, float* w0, float* A1, int 
   static_assert((kMaxSub / 2 + 1) * ((kMaxSub + kJacobiCtas - 1) / kJacobiCtas) <= kVPerThread * 1024,
                 "V slice too large");
   if (m > kMaxSub) return cudaErrorInvalidValue;
-  // set once per process (thread-safe static initialisation)
-  static const cudaError_t attr_err = cudaFuncSetAttribute(jacobi_eig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)jacobi_smem_bytes(kMaxSub));
+  // set once per device
+  const cudaError_t attr_err =
+      ensure_smem_attr(reinterpret_cast<const void*>(jacobi_eig_kernel), (int)jacobi_smem_bytes(kMaxSub));
   if (attr_err != cudaSuccess) return attr_err;
   hs_launch_cluster(jacobi_eig_kernel, 2 * kJacobiCtas, 1024, jacobi_smem_bytes(m), s, kJacobiCtas, A0, m0, w0, A1,
                     m1, w1, status);
@@ -642,9 +642,9 @@ cudaError_t launch_chol_inv(const double* G0, int m0, double* Linv0, const doubl
   if (m0 == 0 && m1 == 0) return cudaSuccess;
   const int mm = m0 > m1 ? m0 : m1;
   const size_t smem = (size_t)mm * (mm + 1) * sizeof(double);
-  // set once per process (thread-safe static initialisation)
-  static const cudaError_t attr_err = cudaFuncSetAttribute(chol_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         kMaxSub * (kMaxSub + 1) * (int)sizeof(double));
+  // set once per device
+  const cudaError_t attr_err = ensure_smem_attr(reinterpret_cast<const void*>(chol_inv_kernel),
+                                                kMaxSub * (kMaxSub + 1) * (int)sizeof(double));
   if (attr_err != cudaSuccess) return attr_err;
   hs_launch(chol_inv_kernel, 2, 1024, smem, s, G0, m0, Linv0, G1, m1, Linv1, status);
   return cudaGetLastError();

@@ -117,6 +117,9 @@ WORKLOADS = {
     5: dict(d=2, D=5, chi=100, moves=40, complex_valued=True),
     # small complex case for parity tests (the oracle finishes it in seconds)
     6: dict(d=2, D=3, chi=27, moves=30, complex_valued=True),
+    # the largest shape of the batched workload (D=7: q=49 = 28 even + 21 odd,
+    # chi = 4 D^2 = 196): its first D=7 instance (instance 1, seed SEED_BASE + 4001)
+    7: dict(d=2, D=7, chi=196, moves=10, complex_valued=False, seed=SEED_BASE + 4001),
 }
 
 
@@ -130,6 +133,6 @@ def batched_workload(n: int = 32, seed: int | None = None) -> list[tuple[int, in
 
 
 def workload_tensor(k: int) -> np.ndarray:
-    """The seeded iPEPS tensor of workload k (seed SEED_BASE + k)."""
+    """The seeded iPEPS tensor of workload k (seed SEED_BASE + k unless the workload names its own)."""
     w = WORKLOADS[k]
-    return random_ipeps(w["d"], w["D"], SEED_BASE + k, w["complex_valued"])
+    return random_ipeps(w["d"], w["D"], w.get("seed", SEED_BASE + k), w["complex_valued"])

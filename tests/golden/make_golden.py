@@ -23,7 +23,10 @@ CHECKPOINTS = (1, 2, 3, 5, 10, 20, 30, 40, 50)
 
 
 def snapshot(C, T, A, D):
-    rho = ob.two_site_rdm(C, T, A)
+    # D >= 7: the two-site network summed over slices of its bottom bond, and no
+    # S_err (the one-site environment's chi^2 D^6 intermediate is tens of GB)
+    big = D >= 7
+    rho = ob.two_site_rdm(C, T, A, chunk=8 if big else None)
     rho = rho / np.trace(rho)
     out = {
         "energy": ob.bond_energy(rho, inputs.heisenberg_bond()),
@@ -31,7 +34,7 @@ def snapshot(C, T, A, D):
         "rho_im": np.imag(rho).tolist(),
         "corner_spectrum": ob.corner_spectrum(C).tolist(),
     }
-    out["s_err"] = ob.symmetry_error(ob.one_site_environment(C, T), D)
+    out["s_err"] = None if big else ob.symmetry_error(ob.one_site_environment(C, T), D)
     return out
 
 
@@ -42,7 +45,7 @@ def main(ks):
         a = dl.double_layer(A)
         C, T = ctmrg.init_environment(a)
         C, T = C / np.abs(C).max(), T / np.abs(T).max()
-        res = {"workload": k, **w, "seed": inputs.SEED_BASE + k, "checkpoints": {}, "gaps": [], "lam_cut": [],
+        res = {"workload": k, **w, "seed": w.get("seed", inputs.SEED_BASE + k), "checkpoints": {}, "gaps": [], "lam_cut": [],
                "n": []}
         t0 = time.time()
         for m in range(1, w["moves"] + 1):

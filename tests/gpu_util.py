@@ -53,11 +53,6 @@ def golden(k):
         return json.load(f)
 
 
-def spectrum_from_corner(C):
-    s = np.linalg.svd(C, compute_uv=False)
-    return s / s[0]
-
-
 def graded_pack(t, row_sects, col_sects):
     """Dense graded matrix of hs.h (complex tensors): all rows in FSO order (both parities),
     all columns likewise; entries of odd total parity give their imaginary part, even ones

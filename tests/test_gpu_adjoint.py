@@ -108,3 +108,23 @@ def test_complex_energy_gradient_full_size(ctx):
     """Complex workload at full size (D=5, chi=100, 40 moves): finite differences on 16
     coordinates (both parts) and four directional derivatives."""
     _complex_gradient_checks(ctx, 5, 100, 40, 16, False)
+
+
+@pytest.mark.parametrize("cplx", [False, True])
+def test_rdm_vjp_with_the_energy_cotangent_equals_energy_vjp(ctx, cplx):
+    """hs_rdm_vjp fed the cotangent of E = Re Tr(rho h)/Tr rho gives hs_energy_vjp's gradient."""
+    from paper_2410_11596_gb300.api import CTMRG
+    A = inputs.workload_tensor(6 if cplx else 1)
+    ctm = CTMRG(ctx, A, 27 if cplx else 16)
+    ctm.run(8)
+    h = torch.from_numpy(inputs.heisenberg_bond()).cuda()
+    if cplx:
+        At = torch.from_numpy(A).cuda()
+    else:
+        At = torch.from_numpy(A.copy()).cuda()
+    _, tr = ctm.rdm2_of(At, h)
+    eye = torch.eye(4, dtype=tr.dtype, device="cuda")
+    drho = 0.7 * (torch.conj(1.0 / tr[0]) * h.t().to(tr.dtype) - torch.conj(tr[1] / tr[0] ** 2) * eye)
+    g1 = ctm.rdm2_vjp(At, drho).cpu().numpy()
+    g2 = ctm.energy_vjp(At, h, 0.7).cpu().numpy()
+    assert np.abs(g1 - g2).max() <= 1e-12 * np.abs(g1).max()

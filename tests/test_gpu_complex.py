@@ -64,7 +64,7 @@ def test_graded_ctmrg_matches_oracle(ctx, precision, eig, tol_e, tol_s):
         ref = g["checkpoints"][str(m)]
         e = ob.bond_energy(rho, h)
         assert abs(e - ref["energy"]) <= tol_e, (m, e, ref["energy"])
-        sp = ob.corner_spectrum(C)
+        sp = c.corner_spectrum().cpu().numpy()               # hs_corner_spectrum, on the GPU
         rs = np.array(ref["corner_spectrum"])
         n = min(len(sp), len(rs))
         assert np.abs(sp[:n] - rs[:n]).max() <= tol_s, m
@@ -93,7 +93,8 @@ def test_graded_real_input_matches_real_path(ctx):
     cc.run(20)
     Cc, Tc, rho = _env_observables(cc, A.astype(complex))
     assert abs(ob.bond_energy(rho, h) - cr.energy(h)) < 1e-12
-    np.testing.assert_allclose(ob.corner_spectrum(Cc)[:12], cr.corner_spectrum()[:12], atol=1e-11)
+    np.testing.assert_allclose(ob.corner_spectrum(Cc)[:12], cr.corner_spectrum().cpu().numpy()[:12], atol=1e-11)
+    np.testing.assert_allclose(cc.corner_spectrum().cpu().numpy(), cr.corner_spectrum().cpu().numpy(), atol=1e-11)
 
 
 def test_graded_rdm_on_gpu(ctx):
@@ -149,4 +150,21 @@ def test_graded_ctmrg_full_size_tensor_cores(ctx):
     c.run(g["moves"])
     e = c.energy(inputs.heisenberg_bond())
     print(f"w5 tf32x3 |dE| = {abs(e - g['checkpoints'][str(g['moves'])]['energy']):.3e}")
-    assert abs(e - g["checkpoints"][str(g["moves"])]["energy"]) < 1e-6
+    assert abs(e - g["checkpoints"][str(g["moves"])]["energy"]) <= 1e-7   # the mixed-precision energy gate
+
+
+def test_graded_one_site_rdm_and_inverse_rotation(ctx):
+    """HS_RDM_ONE_SITE and hs_from_hermitian_basis on a complex tensor against the oracle."""
+    from paper_2410_11596_gb300.api import CTMRG
+    from oracle import ctmrg as octmrg
+    A = inputs.workload_tensor(6)
+    c = CTMRG(ctx, A, 27)
+    c.run(8)
+    r = octmrg.run(dl.double_layer(A), 27, 8)
+    rho, t0, t1 = c.rdm1(np.diag([0.5, -0.5]))
+    ref = ob.one_site_rdm(r.C, r.T, A)
+    np.testing.assert_allclose(rho.cpu().numpy() / t0, ref / np.trace(ref), atol=1e-11)
+    assert abs(t1 / t0 - np.trace(ref @ np.diag([0.5, -0.5])) / np.trace(ref)) < 1e-11
+    a = c.double_layer_dense().cpu().numpy()
+    want = dl.double_layer(A)
+    np.testing.assert_allclose(a, want, rtol=0, atol=1e-14 * np.abs(want).max())

@@ -4,7 +4,7 @@ import pytest
 
 torch = pytest.importorskip("torch")
 
-from gpu_util import ensure_library, fso_pack, golden, spectrum_from_corner  # noqa: E402
+from gpu_util import ensure_library, fso_pack, golden  # noqa: E402
 from oracle import basis as ob_basis, ctmrg as octmrg, doublelayer as dl, observables as ob  # noqa: E402
 from paper_2410_11596_gb300 import _lib as L, inputs  # noqa: E402
 from pins import onsager_log_z, onsager_nn  # noqa: E402
@@ -73,9 +73,9 @@ def test_to_hermitian_basis_and_rejection(ctx):
     assert e.value.status == -4
 
 
-def _run(ctx, A, chi, moves, basis="hermitian", backend="own"):
+def _run(ctx, A, chi, moves, basis="hermitian", backend="own", precision="f64", eig="f64"):
     from paper_2410_11596_gb300.api import CTMRG
-    c = CTMRG(ctx, A, chi, basis=basis, backend=backend)
+    c = CTMRG(ctx, A, chi, basis=basis, backend=backend, precision=precision, eig=eig)
     c.run(moves)
     return c
 
@@ -98,8 +98,7 @@ def test_ctmrg_matches_oracle(ctx, k, basis, backend):
         rho, t0, t1 = c.rdm2(h)
         assert t1 / t0 == pytest.approx(snap["energy"], rel=1e-10, abs=1e-12), m
         np.testing.assert_allclose(rho.cpu().numpy() / t0, np.array(snap["rho_re"]), atol=1e-10)
-        C, _ = c.dense_env()
-        spec = spectrum_from_corner(C.cpu().numpy())
+        spec = c.corner_spectrum().cpu().numpy()            # hs_corner_spectrum, on the GPU
         np.testing.assert_allclose(spec, np.array(snap["corner_spectrum"]), atol=1e-10)
     gaps = [x for x in g["gaps"] if x is not None]
     assert min(gaps) > 1e-9   # the seed has no near-degenerate cut
@@ -162,3 +161,36 @@ def test_sector_sizes_sum_and_odd_fraction(ctx):
         assert info["n_odd"] == prev["chi_even"] * qo + prev["chi_odd"] * qe
     frac = c.infos[-1]["chi_odd"] / 64
     assert 0.2 < frac < 0.8
+
+
+@pytest.mark.parametrize("basis", ["hermitian", "dense"])
+def test_one_site_rdm_matches_oracle(ctx, basis):
+    """HS_RDM_ONE_SITE: rho1 from eps and A, normalised, against the oracle; Tr(rho1 S^z)."""
+    A = inputs.workload_tensor(1)
+    c = _run(ctx, A, 16, 6, basis=basis)
+    r = octmrg.run(dl.double_layer(A), 16, 6)
+    sz = np.diag([0.5, -0.5])
+    rho, t0, t1 = c.rdm1(sz)
+    ref = ob.one_site_rdm(r.C, r.T, A)
+    np.testing.assert_allclose(rho.cpu().numpy() / t0, ref / np.trace(ref), atol=1e-11)
+    assert t1 / t0 == pytest.approx(np.trace(ref @ sz) / np.trace(ref), abs=1e-11)
+
+
+@pytest.mark.parametrize("D", [1, 2, 3, 4])
+def test_from_hermitian_basis_inverts_the_rotation(ctx, D):
+    """hs_from_hermitian_basis(a~) = a, the oracle's dense double layer (Sec. II.B: U orthogonal)."""
+    from paper_2410_11596_gb300.api import CTMRG
+    A = inputs.random_ipeps(2, D, 41)
+    c = CTMRG(ctx, A, max(4, D * D))
+    a = c.double_layer_dense().cpu().numpy()
+    want = dl.double_layer(A)
+    np.testing.assert_allclose(a, want, rtol=0, atol=1e-14 * np.abs(want).max())
+
+
+def test_corner_spectrum_on_gpu_of_a_projected_corner(ctx):
+    """With the FP32-projected eigensolver the new corner is P^T C' P (not diagonal): the GPU
+    spectrum equals the oracle's formula applied to the same corner."""
+    A = inputs.workload_tensor(2)
+    c = _run(ctx, A, 64, 10, eig="f32p")
+    C, _ = c.dense_env()
+    np.testing.assert_allclose(c.corner_spectrum().cpu().numpy(), ob.corner_spectrum(C.cpu().numpy()), atol=1e-13)

@@ -95,7 +95,7 @@ def test_fp32_projected_eig(ctx, k, precision, eig, tol_e):
     c.run(50)
     e = c.energy(inputs.heisenberg_bond())
     dE = abs(e - g["checkpoints"]["50"]["energy"])
-    spec = c.corner_spectrum()
+    spec = c.corner_spectrum().cpu().numpy()
     ds = np.abs(spec - np.array(g["checkpoints"]["50"]["corner_spectrum"])).max()
     print(f"w{k} {precision}+{eig}: |dE| = {dE:.3e}, max |d spectrum| = {ds:.3e}")
     assert dE <= tol_e
@@ -114,7 +114,7 @@ def test_subspace_eigensolver(ctx, k, precision, tol_e, min_sub):
     infos = c.run(50)
     e = c.energy(inputs.heisenberg_bond())
     dE = abs(e - g["checkpoints"]["50"]["energy"])
-    spec = c.corner_spectrum()
+    spec = c.corner_spectrum().cpu().numpy()
     ds = np.abs(spec - np.array(g["checkpoints"]["50"]["corner_spectrum"])).max()
     used = [bool(i["flags"] & 2) for i in infos]
     iters = [i["subspace_iters"] for i in infos if i["flags"] & 2]
@@ -124,3 +124,52 @@ def test_subspace_eigensolver(ctx, k, precision, tol_e, min_sub):
     assert sum(used[10:]) >= min_sub        # converged moves once warm
     assert dE <= tol_e
     assert ds <= 1e-5
+
+
+def _rho_spectrum_errors(c, snap):
+    rho, t0, t1 = c.rdm2(inputs.heisenberg_bond())
+    r = rho.cpu().numpy() / t0
+    rho_ref = np.array(snap["rho_re"]) + 1j * np.array(snap["rho_im"])
+    spec = c.corner_spectrum().cpu().numpy()
+    sref = np.array(snap["corner_spectrum"])
+    n = min(len(spec), len(sref))
+    return abs(t1 / t0 - snap["energy"]), float(np.abs(r - rho_ref).max()), float(np.abs(spec[:n] - sref[:n]).max())
+
+
+@pytest.mark.parametrize("eig", ["f64", "subspace"])
+def test_full_size_tf32x3_rho_and_spectrum(ctx, eig):
+    """D=6, chi=144, TF32x3 block GEMMs, 50 moves, with the FP64 eigensolver and with the subspace
+    eigensolver: |dE| <= 1e-7, every entry of the normalised rho within 1e-6 and the normalised
+    corner spectrum within 1e-5 of the oracle. (rho's bound: its entries are energies of order one
+    combined from the same environment as E, so ten times E's gate; the spectrum's is the
+    FP32 Ritz-value level.)"""
+    from paper_2410_11596_gb300.api import CTMRG
+    g = golden(3)
+    c = CTMRG(ctx, inputs.workload_tensor(3), g["chi"], basis="hermitian", precision="tf32x3", eig=eig)
+    c.run(50)
+    dE, drho, ds = _rho_spectrum_errors(c, g["checkpoints"]["50"])
+    print(f"D=6 tf32x3+{eig}: |dE| = {dE:.2e}, max|d rho| = {drho:.2e}, max|d spectrum| = {ds:.2e}")
+    assert dE <= 1e-7
+    assert drho <= 1e-6
+    assert ds <= 1e-5
+
+
+@pytest.mark.parametrize("precision,eig,tol_e,tol_rho,tol_s", [("f64", "f64", 1e-10, 1e-10, 1e-10),
+                                                               ("tf32x3", "subspace", 1e-7, 1e-6, 1e-5)])
+def test_d7_chi196_matches_oracle(ctx, precision, eig, tol_e, tol_rho, tol_s):
+    """The largest shape of the batched workload, D=7 (q=49 = 28 even + 21 odd), chi=196: energy,
+    every entry of rho and the corner spectrum against the oracle at each stored checkpoint."""
+    from paper_2410_11596_gb300.api import CTMRG
+    g = golden(7)
+    assert min(x for x in g["gaps"] if x is not None) > 1e-9
+    c = CTMRG(ctx, inputs.workload_tensor(7), g["chi"], basis="hermitian", precision=precision, eig=eig)
+    done = 0
+    for m in sorted(int(k) for k in g["checkpoints"]):
+        c.run(m - done)
+        done = m
+        dE, drho, ds = _rho_spectrum_errors(c, g["checkpoints"][str(m)])
+        print(f"D=7 {precision}+{eig} move {m}: |dE| = {dE:.2e}, max|d rho| = {drho:.2e}, max|d spec| = {ds:.2e}")
+        assert dE <= tol_e, m
+        assert drho <= tol_rho, m
+        assert ds <= tol_s, m
+    assert (c.env.q_even, c.env.q_odd) == (28, 21)

@@ -204,3 +204,37 @@ def test_corner_spectrum_equals_quadrant_without_truncation(n, cplx):
     s = np.linalg.svd(Q, compute_uv=False)
     assert r.C.shape == Q.shape
     np.testing.assert_allclose(ob.corner_spectrum(r.C), s / s[0], atol=1e-12)
+
+
+@pytest.mark.parametrize("D", [1, 4])
+def test_one_site_rdm_product_state_closed_form(D):
+    """Product state: rho1 / Tr rho1 = |phi><phi| / <phi|phi>, also embedded at D = 4."""
+    phi = np.array([0.6, 0.1 + 0.8j])
+    A = inputs.product_state_ipeps(phi, D)
+    r = ctmrg.run(dl.double_layer(A), 8, 4)
+    rho = ob.one_site_rdm(r.C, r.T, A)
+    np.testing.assert_allclose(rho / np.trace(rho), np.outer(phi, phi.conj()) / np.vdot(phi, phi).real, atol=1e-14)
+
+
+@pytest.mark.parametrize("cplx", [False, True])
+@pytest.mark.parametrize("n", [0, 1])
+def test_one_site_rdm_equals_finite_patch_without_truncation(n, cplx):
+    """chi >= chi0 q^n: rho1 after n moves equals the (2n+3)^2 traced-boundary patch whose
+    centre site keeps its physical legs open."""
+    A = inputs.random_ipeps(2, 2, 10, complex_valued=cplx)
+    a = dl.double_layer(A)
+    r = ctmrg.run(a, 64, n)
+    rho = ob.one_site_rdm(r.C, r.T, A)
+    L = 2 * n + 3
+    ao = dl.open_double_layer(A)
+    ex = contract_patch(lambda i, j: ("open", ao) if (i == n + 1 and j == n + 1) else a, L, L, 2)
+    np.testing.assert_allclose(rho / np.trace(rho), ex / np.trace(ex), atol=1e-13)
+
+
+def test_two_site_rdm_chunked_sum_is_the_same_sum():
+    """Summing the bottom bond in slices gives the same rho (memory bound for large chi D^2)."""
+    A = inputs.random_ipeps(2, 2, 12)
+    r = ctmrg.run(dl.double_layer(A), 12, 6)
+    full = ob.two_site_rdm(r.C, r.T, A)
+    for c in (1, 5, 12):
+        np.testing.assert_allclose(ob.two_site_rdm(r.C, r.T, A, chunk=c), full, rtol=1e-13, atol=1e-15)
