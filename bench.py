@@ -1,17 +1,25 @@
 #!/usr/bin/env python
-"""CTMRG moves/s on one GB300: Hermitian Z2 path vs the dense FP64 path.
+"""CTMRG moves/s on one GB300: Hermitian Z2 path vs the dense path, same GPU.
 
 Workload: real C4v iPEPS, d=2, D=6 (double-layer legs 36 = 21 even + 15 odd),
 chi=144, seeded N(0,1) tensor (seed 1159600+3), D4-symmetrised, max|A|=1.
-One step = one C4v CTMRG move (enlarged corner, per-block eigen-decomposition,
-truncation, renormalisation, normalisation). L2 (129 MB) is flushed between
-timed moves by writing a 512 MB buffer outside the timed events.
+One step = one C4v CTMRG move (enlarged corner, projector, truncation,
+renormalisation, normalisation). L2 (129 MB) is flushed between timed moves
+by writing a 512 MB buffer outside the timed events.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-Prints ONE JSON line (rank 0). With torchrun (N>1) every rank runs an
-independent replica ("replicas only": the method has no exchange step) and
-the value is the sum of moves over ranks / the slowest rank's time.
+Prints ONE JSON line (rank 0). `value` is the Z2 path (TF32x3 block GEMMs,
+subspace eigensolver) over the K moves after W warm-up moves. Beside it:
+the same moves split into the transient (the first four timed moves, while
+the environment still changes) and a steady state (ten moves after move 50);
+a table of moves/s and |dE| for {Z2, dense basis} x {FP64 GEMM + FP64 syevd,
+TF32x3 GEMM + FP64 syevd, TF32x3 GEMM + subspace eigensolver}, with the
+Z2/dense ratio at equal arithmetic; HOTRG steps/s (Z2 vs dense) with the odd
+sector fraction; the complex workload; the batched workload.
+With torchrun (N>1) every rank runs an independent replica ("replicas only":
+the method has no exchange step) and the value is the sum of moves over
+ranks / the slowest rank's time.
 """
 from __future__ import annotations
 
@@ -38,32 +46,34 @@ FLUSH_BYTES = 512 << 20
 NCU_TRAFFIC = {
     # profiles/gemm_f64_d6_chi144.md: mean of the G3/G4/G5 launches
     "gemm_f64": {"bytes_per_launch": 143.3e6, "source_sha": "ac07f1d8a4d24d63"},
-    # profiles/gemm_tc_tf32x3_d6_chi144.md: mean over the 32 launches of two steady-state moves
+    # profiles/gemm_tc_tf32x3_d6_chi144.md: mean over the tensor-core launches of two steady-state moves
     "gemm_tc_tf32x3": {"bytes_per_launch": 56.1e6, "source_sha": "f36631a7cedc423b"},
 }
+
+EIG_LABEL = {"f64": "FP64 syevd per parity block", "f32p": "FP32 syevd + FP64 Loewdin and projection",
+             "subspace": "warm-started subspace iteration (tcgen05 products, FP32 Rayleigh-Ritz), FP64 projection"}
 
 
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=50)
+    p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--precision", default="tf32x3", choices=["f64", "tf32x3", "tf32", "bf16x3"])
-    p.add_argument("--eig", default="subspace", choices=["f64", "f32p", "subspace"],
-                   help="f64: FP64 syevd per block; f32p: FP32 syevd + FP64 re-orthonormalised projection")
-    p.add_argument("--no-dense", action="store_true")
+    p.add_argument("--eig", default="subspace", choices=["f64", "f32p", "subspace"])
+    p.add_argument("--no-table", action="store_true", help="skip the {Z2, dense} x arithmetic table")
     p.add_argument("--no-cpu", action="store_true")
-    p.add_argument("--no-check", action="store_true", help="skip the |dE| run to 50 moves")
-    p.add_argument("--no-complex", action="store_true",
-                   help="skip the complex-tensor line (graded path, D=5 chi=100, 40 moves)")
-    p.add_argument("--no-dtypes", action="store_true",
-                   help="skip the per-dtype |dE| / rho error table (50 moves per dtype)")
-    p.add_argument("--no-batched", action="store_true",
-                   help="skip the batched line (32 instances, D in 3..7, chi = 4 D^2)")
+    p.add_argument("--no-check", action="store_true", help="skip the |dE| run to 50 moves and the steady state")
+    p.add_argument("--no-complex", action="store_true", help="skip the complex workload (D=5, chi=100)")
+    p.add_argument("--no-dtypes", action="store_true", help="skip the per-dtype |dE| / rho errors (50 moves each)")
+    p.add_argument("--no-batched", action="store_true", help="skip the batched workload (32 instances)")
+    p.add_argument("--no-hotrg", action="store_true", help="skip the HOTRG line")
     p.add_argument("--profile-region", action="store_true",
                    help="profiling runs only: W warm-up moves, then K moves inside cudaProfilerStart/Stop "
                         "(for ncu --profile-from-start off); prints a short JSON line, no bench line")
+    p.add_argument("--basis", default="hermitian", choices=["hermitian", "dense"],
+                   help="profiling runs only: the basis of the profiled moves")
     p.add_argument("--workload", type=int, default=WORKLOAD,
                    help="smaller workloads (1, 2) are for profiling runs, not bench lines")
     return p.parse_args()
@@ -77,12 +87,25 @@ def emit(obj):
     print(json.dumps(obj), flush=True)
 
 
-def golden_energy(moves: int):
-    path = os.path.join(ROOT, "tests", "golden", f"ctmrg_w{WORKLOAD}.json")
-    with open(path) as f:
-        g = json.load(f)
-    snap = g["checkpoints"].get(str(moves))
+def golden_snapshot(moves: int, k: int | None = None):
+    path = os.path.join(ROOT, "tests", "golden", f"ctmrg_w{WORKLOAD if k is None else k}.json")
+    try:
+        with open(path) as f:
+            return json.load(f)["checkpoints"].get(str(moves))
+    except OSError:
+        return None
+
+
+def golden_energy(moves: int, k: int | None = None):
+    snap = golden_snapshot(moves, k)
     return None if snap is None else snap["energy"]
+
+
+def r3(x):
+    """Rounded for the JSON line (3 significant digits)."""
+    if x is None:
+        return None
+    return float(f"{x:.3g}")
 
 
 # ---------------------------------------------------------------------------
@@ -112,10 +135,10 @@ def oracle_moves(n: int, state=None):
     return ts, (oc, a, C, T, chi)
 
 
-def cpu_baseline():
-    ts, _ = oracle_moves(1)
-    return {"value": 1.0 / ts[0], "unit": "moves/s", "cores": os.cpu_count(), "kind": "oracle",
-            "sample": "one full-size oracle move (D=6, chi=144, C' 5184x5184 numpy eigh) after an untimed "
+def cpu_baseline(n: int = 3):
+    ts, _ = oracle_moves(n)
+    return {"value": n / float(np.sum(ts)), "unit": "moves/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"{n} full-size oracle moves (D=6, chi=144, C' 5184x5184 numpy eigh) after an untimed "
                       "traced-boundary init and first move; numpy BLAS with its default thread count"}
 
 
@@ -123,25 +146,24 @@ def run_reference(args):
     rank, _, world = dist_env()
     if rank != 0:
         return
-    # each full-size oracle move takes seconds on the host cores: cap the
-    # sample so that the whole run stays within a few minutes
-    args.steps = min(args.steps, 20)
-    args.warmup = min(args.warmup, 3)
+    # a full-size oracle move takes a few seconds on the host cores; K and W
+    # are bounded so that the run ends within a few minutes
+    steps, warmup = min(args.steps, 40), min(args.warmup, 10)
     state = None
-    if args.warmup:
-        _, state = oracle_moves(args.warmup, state)
-    ts, _ = oracle_moves(args.steps, state)
+    if warmup:
+        _, state = oracle_moves(warmup, state)
+    ts, _ = oracle_moves(steps, state)
     sec = float(np.sum(ts))
-    val = args.steps / sec
+    val = steps / sec
     cores = os.cpu_count()
     emit({"impl": "reference", "metric": METRIC, "value": val, "unit": "moves/s", "n_gpus": args.gpus,
-          "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec / args.steps,
+          "steps": steps, "warmup": warmup, "ms_per_step": 1e3 * sec / steps,
           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
           "data": "synthetic",
           "config": {"workload": "real C4v iPEPS d=2 D=6 chi=144, seeded N(0,1), D4-symmetrised", "D": 6,
                      "chi": 144, "path": "dense FP64 oracle (numpy eigh, tensordot) on host cores"},
           "cpu_baseline": {"value": val, "unit": "moves/s", "cores": cores, "kind": "oracle",
-                           "sample": f"{args.steps} full-size oracle moves after {args.warmup} warm-up moves"},
+                           "sample": f"{steps} full-size oracle moves after {warmup} warm-up moves"},
           "e2e": {"value": val, "unit": "moves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}})
 
 
@@ -203,7 +225,7 @@ class Clocks:
 
 
 def fp64_peak_tflops(torch, dev):
-    """cuBLAS DGEMM 4096^3, best of 3 (the FP64 pipe's measured rate on this GPU)."""
+    """cuBLAS DGEMM 4096^3, best of 4 (the FP64 pipe's measured rate on this GPU)."""
     a = torch.randn(4096, 4096, dtype=torch.float64, device=dev)
     b = torch.randn(4096, 4096, dtype=torch.float64, device=dev)
     best = 1e9
@@ -221,9 +243,9 @@ def measured_bf16_tflops():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
         with open(path) as f:
-            return float(json.load(f)["bf16_tflops"])
+            return float(json.load(f)["bf16_tflops"]), "measured"
     except Exception:
-        return 1900.0   # profiling recipe fallback (bf16 burst)
+        return 1900.0, "fallback"   # profiling recipe fallback (bf16 burst)
 
 
 def source_sha(rel):
@@ -255,7 +277,7 @@ def run_profile_region(args):
         build.build()
     w = inputs.WORKLOADS[WORKLOAD]
     ctx = Context(0)
-    c = CTMRG(ctx, inputs.workload_tensor(WORKLOAD), w["chi"], basis="hermitian", precision=args.precision,
+    c = CTMRG(ctx, inputs.workload_tensor(WORKLOAD), w["chi"], basis=args.basis, precision=args.precision,
               backend="own", eig=args.eig)
     c.run(args.warmup)
     torch.cuda.synchronize()
@@ -263,8 +285,54 @@ def run_profile_region(args):
     infos = c.run(args.steps)
     torch.cuda.synchronize()
     torch.cuda.profiler.stop()
-    emit({"profile_region": True, "workload": WORKLOAD, "warmup": args.warmup, "steps": args.steps,
-          "subspace_converged": sum(1 for i in infos if i["flags"] & 2)})
+    emit({"profile_region": True, "workload": WORKLOAD, "basis": args.basis, "warmup": args.warmup,
+          "steps": args.steps, "subspace_converged": sum(1 for i in infos if i["flags"] & 2)})
+
+
+def arm(torch, ctx, A, chi, flush, basis, precision, eig, nwarm, ntimed, check_move, h):
+    """moves/s of one {basis, arithmetic} combination (ntimed moves after nwarm), and |dE| against
+    the oracle at move check_move (run on to it if needed)."""
+    from paper_2410_11596_gb300.api import CTMRG
+    c = CTMRG(ctx, A, chi, basis=basis, precision=precision, backend="own", eig=eig)
+    c.run(nwarm)
+    ms = timed_moves(torch, c, ctx, ntimed, flush)
+    done = nwarm + ntimed
+    dE = None
+    ref = golden_energy(check_move)
+    if ref is not None and check_move >= done:
+        c.run(check_move - done)
+        dE = abs(c.energy(h) - ref)
+    conv = sum(1 for i in c.infos[nwarm:nwarm + ntimed] if i.get("flags", 0) & 2)
+    del c
+    return {"moves_per_s": r3(ntimed / (np.sum(ms) / 1e3)), "abs_dE": r3(dE), "moves": f"{nwarm + 1}-{done}",
+            "dE_at": check_move, **({"subspace_converged": conv} if eig == "subspace" else {})}
+
+
+def hotrg_line(torch, ctx):
+    """HOTRG steps/s, Z2 vs dense basis, with FP64 and with TF32x3 block GEMMs (FP64 Gram eig
+    in both), and the odd fraction of the kept states per step (Z2, TF32x3)."""
+    from paper_2410_11596_gb300 import inputs
+    from paper_2410_11596_gb300.api import HOTRG
+    out = []
+    for D, chi in ((2, 16), (2, 32), (4, 16), (4, 24), (4, 32)):
+        A = inputs.random_ipeps(2, D, inputs.SEED_BASE + 40 + D)
+        row = {"D": D, "chi": chi}
+        for prec in ("f64", "tf32x3"):
+            for basis in ("hermitian", "dense"):
+                hg = HOTRG(ctx, A, chi, basis=basis, precision=prec)
+                hg.run(4)                      # the tensor reaches chi on every leg
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                n = 6
+                infos = hg.run(n)
+                torch.cuda.synchronize()
+                row[f"{'z2' if basis == 'hermitian' else 'dense'}_{prec}"] = r3(n / (time.perf_counter() - t0))
+                if basis == "hermitian" and prec == "tf32x3":
+                    row["odd_fraction"] = [round(i["h_odd"] / (i["h_even"] + i["h_odd"]), 3) for i in infos]
+                del hg
+            row[f"speedup_{prec}"] = r3(row[f"z2_{prec}"] / row[f"dense_{prec}"])
+        out.append(row)
+    return {"unit": "steps/s", "rows": out}
 
 
 def run_ours(args):
@@ -285,13 +353,14 @@ def run_ours(args):
         cpu = cpu_baseline()
 
     w = inputs.WORKLOADS[WORKLOAD]
+    chi = w["chi"]
     A = inputs.workload_tensor(WORKLOAD)
     h = inputs.heisenberg_bond()
     ctx = Context(local)
     flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-    peak64 = fp64_peak_tflops(torch, dev)
 
-    c = CTMRG(ctx, A, w["chi"], basis="hermitian", precision=args.precision, backend="own", eig=args.eig)
+    # ---- the headline: W warm-up moves, K timed moves ----
+    c = CTMRG(ctx, A, chi, basis="hermitian", precision=args.precision, backend="own", eig=args.eig)
     c.run(args.warmup)
     L.hs_profile_enable(ctx.handle, True)
     # in the timed moves only the block GEMMs carry events (the roofline
@@ -315,17 +384,18 @@ def run_ours(args):
         torch.distributed.barrier()
         sec = float(t.item())
     value = world * args.steps / sec
+    ntr = min(4, args.steps)
+    transient = ntr / (np.sum(ms[:ntr]) / 1e3)
+    conv_timed = sum(1 for i in c.infos[args.warmup:] if i.get("flags", 0) & 2)
 
-    # |dE| against the oracle after 50 moves, then the same path at steady
-    # state (ten moves after move 50, every warm start in place)
+    # |dE| against the oracle after 50 moves, then the steady state (ten moves
+    # after move 50, every warm start in place) and its phase split
     dE = None
     steady = None
     if not args.no_check:
         done = args.warmup + args.steps
         if done < 50:
             c.run(50 - done)
-        # the stored oracle run ends at move 50; it is converged to 1e-15 from
-        # move 30 on, so later moves compare against it too
         ref = golden_energy(50)
         dE = abs(c.energy(h) - ref) if ref is not None else None
         nst = 10
@@ -338,95 +408,73 @@ def run_ours(args):
         msp = timed_moves(torch, c, ctx, nst, flush)
         ps = L.hs_profile_read(ctx.handle)
         L.hs_profile_enable(ctx.handle, False)
-        steady = {"moves": "%d-%d" % (first, first + nst - 1), "moves_per_s": nst / (np.sum(mss) / 1e3),
-                  "ms_per_step": float(np.mean(mss)), "subspace_converged": conv,
-                  "time_split_ms": {k: v / nst for k, v in ps["phase_ms"].items()},
-                  "time_split_moves": "%d-%d (with phase events: %.3f ms per move)" % (
-                      first + nst, first + 2 * nst - 1, float(np.mean(msp)))}
+        steady = {"moves": "%d-%d" % (first, first + nst - 1), "moves_per_s": r3(nst / (np.sum(mss) / 1e3)),
+                  "subspace_converged": conv,
+                  "phase_ms": {k: r3(v / nst) for k, v in ps["phase_ms"].items() if v > 0},
+                  "phase_moves_ms": r3(float(np.mean(msp)))}
+    del c
 
-    # dense FP64 path (cuBLAS DGEMM + cuSOLVER on the full chi*D^2 corner)
-    dense = None
-    if not args.no_dense:
-        cd = CTMRG(ctx, A, w["chi"], basis="dense", precision="f64", backend="cublas")
-        cd.run(args.warmup)
-        msd = timed_moves(torch, cd, ctx, args.steps, flush)
-        dense = {"moves_per_s": args.steps / (np.sum(msd) / 1e3), "ms_per_step": float(np.mean(msd)),
-                 "path": "dense basis, cuBLAS DGEMM, cuSOLVER Xsyevd on the full 5184x5184 corner"}
-        if not args.no_check:
-            cd.run(50 - args.warmup - args.steps)
-            ref = golden_energy(50)
-            dense["abs_dE_vs_oracle"] = abs(cd.energy(h) - ref) if ref is not None else None
-        del cd
+    # ---- {Z2, dense} x {FP64+syevd, TF32x3+syevd, TF32x3+subspace} ----
+    table = None
+    speedup = None
+    if not args.no_table:
+        table = {"z2": {}, "dense": {}}
+        for basis, key in (("hermitian", "z2"), ("dense", "dense")):
+            # the eigen-decomposition arms: every move costs the same, 5 timed moves after W
+            table[key]["f64_syevd"] = arm(torch, ctx, A, chi, flush, basis, "f64", "f64", args.warmup, 5, 10, h)
+            table[key]["tf32x3_syevd"] = arm(torch, ctx, A, chi, flush, basis, "tf32x3", "f64", args.warmup, 5, 10, h)
+            # the subspace arm: the headline's own moves (W warm-up, K timed), |dE| at move 30
+            if key == "z2":
+                table[key]["tf32x3_subspace"] = {"moves_per_s": r3(value / world), "abs_dE": r3(dE),
+                                                 "moves": f"{args.warmup + 1}-{args.warmup + args.steps}",
+                                                 "dE_at": 50, "subspace_converged": conv_timed}
+            else:
+                table[key]["tf32x3_subspace"] = arm(torch, ctx, A, chi, flush, basis, "tf32x3", "subspace",
+                                                    args.warmup, args.steps, 30, h)
+        speedup = {k: r3(table["z2"][k]["moves_per_s"] / table["dense"][k]["moves_per_s"])
+                   for k in table["z2"]}
 
-    # the same Z2 path with the FP64 eigen-decomposition, for comparison
-    alt = None
-    if not args.no_dense:
-        other = "f64" if args.eig != "f64" else "f32p"
-        ca = CTMRG(ctx, A, w["chi"], basis="hermitian", precision=args.precision, backend="own", eig=other)
-        ca.run(args.warmup)
-        msa = timed_moves(torch, ca, ctx, args.steps, flush)
-        alt = {"eig": other, "moves_per_s": args.steps / (np.sum(msa) / 1e3), "ms_per_step": float(np.mean(msa))}
-        del ca
-
-    # accuracy per dtype of the block GEMMs (same eigensolver): |dE| and the
-    # largest |d rho| of the normalised two-site RDM against the oracle after 50 moves
+    # ---- accuracy per dtype (same eigensolver): |dE| and max |d rho| after 50 moves ----
     per_dtype = None
     if not args.no_dtypes and rank == 0:
-        g3 = None
-        try:
-            with open(os.path.join(ROOT, "tests", "golden", f"ctmrg_w{WORKLOAD}.json")) as f:
-                g3 = json.load(f)["checkpoints"]["50"]
-        except Exception:
-            pass
+        g3 = golden_snapshot(50)
         if g3 is not None:
             rho_ref = np.array(g3["rho_re"]) + 1j * np.array(g3["rho_im"])
             per_dtype = {}
             for prec_ in ("tf32", "bf16x3", "tf32x3", "f64"):
-                cp = CTMRG(ctx, A, w["chi"], basis="hermitian", precision=prec_, backend="own", eig=args.eig)
+                cp = CTMRG(ctx, A, chi, basis="hermitian", precision=prec_, backend="own", eig=args.eig)
                 cp.run(50)
                 rho_, t0_, t1_ = cp.rdm2(h)
                 rho_ = rho_.cpu().numpy() / t0_
-                per_dtype[prec_] = {"abs_dE": abs(t1_ / t0_ - g3["energy"]),
-                                    "max_abs_drho": float(np.abs(rho_ - rho_ref).max())}
+                per_dtype[prec_] = [r3(abs(t1_ / t0_ - g3["energy"])), r3(float(np.abs(rho_ - rho_ref).max()))]
                 del cp
 
-    # complex tensors (Sec. II.C): the graded path on the complex workload, FP64,
-    # every move timed; |dE| against the stored oracle energy after 40 moves
+    # ---- complex tensors (Sec. II.C): graded path, D=5 chi=100, 40 moves ----
     cplx = None
     if not args.no_complex and rank == 0:
-        from paper_2410_11596_gb300 import inputs as _inp
-        w5 = _inp.WORKLOADS[5]
-        ref5 = None
-        try:
-            with open(os.path.join(ROOT, "tests", "golden", "ctmrg_w5.json")) as f:
-                ref5 = json.load(f)["checkpoints"][str(w5["moves"])]["energy"]
-        except Exception:
-            pass
-        cplx = {"workload": "complex C4v iPEPS d=2 D=5 chi=100 (q=25: 15 even/10 odd), seeded, Re/Im ~ N(0,1/2)",
-                "path": "graded real storage (Re of even-total, Im of odd-total entries), sign rule of Eq. (2)-(3), "
-                        "SVD truncation via the eigenvectors of M M^T (n = 2500)", "moves": w5["moves"]}
-        for label, prec_, eig_ in (("f64", "f64", "f64"), ("tf32x3_f32eig", "tf32x3", "f32p")):
-            cc = CTMRG(ctx, _inp.workload_tensor(5), w5["chi"], precision=prec_, eig=eig_)
-            msc = timed_moves(torch, cc, ctx, w5["moves"], flush)
-            e5 = cc.energy(h)
-            cplx[label] = {"gemm": prec_, "eig": {"f64": "FP64 syevd", "f32p": "FP32 syevd + FP64 Loewdin"}[eig_],
-                           "moves_per_s_all": w5["moves"] / (np.sum(msc) / 1e3),
-                           "moves_per_s_last10": 10 / (np.sum(msc[-10:]) / 1e3),
-                           "abs_dE_vs_oracle": abs(e5 - ref5) if ref5 is not None else None}
-            del cc
+        w5 = inputs.WORKLOADS[5]
+        ref5 = golden_energy(w5["moves"], 5)
+        cplx = {"workload": "complex C4v iPEPS d=2 D=5 chi=100, Re/Im ~ N(0,1/2)", "moves": w5["moves"]}
+        for label, prec_, eig_ in (("f64_syevd", "f64", "f64"), ("tf32x3_f32p", "tf32x3", "f32p"),
+                                   ("tf32x3_subspace", "tf32x3", "subspace")):
+            try:
+                cc = CTMRG(ctx, inputs.workload_tensor(5), w5["chi"], precision=prec_, eig=eig_)
+                msc = timed_moves(torch, cc, ctx, w5["moves"], flush)
+                e5 = cc.energy(h)
+                cplx[label] = {"moves_per_s_last10": r3(10 / (np.sum(msc[-10:]) / 1e3)),
+                               "moves_per_s_all": r3(w5["moves"] / (np.sum(msc) / 1e3)),
+                               "abs_dE": r3(abs(e5 - ref5) if ref5 is not None else None)}
+                del cc
+            except L.HsError as e:
+                cplx[label] = {"error": str(e)[:120]}
 
-    # many independent instances (32 real iPEPS, D uniform in 3..7, chi = 4 D^2):
-    # one batched call per move, instances on their own streams driven by a
-    # host thread pool; per-instance latency and the same moves one by one
+    # ---- many independent instances (32 real iPEPS, D uniform in 3..7, chi = 4 D^2) ----
     batched = None
     if not args.no_batched and rank == 0:
         from paper_2410_11596_gb300.api import BatchedCTMRG
-        from paper_2410_11596_gb300 import inputs as _inp
-        wl = _inp.batched_workload()
+        wl = inputs.batched_workload()
         bt = BatchedCTMRG([A_ for _, _, A_ in wl], [chi_ for _, chi_, _ in wl], device=local,
                           precision=args.precision, eig=args.eig)
-        # past the transient (sector sizes settle, warm starts converge), then
-        # 10 batched moves and 10 more moves of the same instances one at a time
         nwarm = max(args.warmup, 15)
         bt.run(nwarm)
         torch.cuda.synchronize()
@@ -442,26 +490,25 @@ def run_ours(args):
                 m_.move()
         torch.cuda.synchronize()
         ts = time.perf_counter() - t0
-        batched = {"workload": "32 real C4v iPEPS, D uniform in {3..7} (seed 1159604), chi = 4 D^2, "
-                               "seeded N(0,1), D4-symmetrised",
-                   "Ds": [int(D_) for D_, _, _ in wl], "moves_timed": nb, "warmup_moves": nwarm,
-                   "instance_moves_per_s": len(wl) * nb / tb, "wall_s": tb,
-                   "latency_ms_p50": float(np.percentile(lat, 50)), "latency_ms_p99": float(np.percentile(lat, 99)),
-                   "one_by_one_instance_moves_per_s": len(wl) * nb / ts,
-                   "threads": bt.nthreads, "note": "wall clock (host) around the batched calls (moves "
-                                                   f"{nwarm + 1}-{nwarm + nb}), then the same instances moved one "
-                                                   "at a time; each instance has its own stream and workspace"}
+        batched = {"instance_moves_per_s": r3(len(wl) * nb / tb), "one_by_one": r3(len(wl) * nb / ts),
+                   "latency_ms_p50": r3(float(np.percentile(lat, 50))),
+                   "latency_ms_p99": r3(float(np.percentile(lat, 99))),
+                   "moves": f"{nwarm + 1}-{nwarm + nb}", "mode": bt.mode}
         bt.close()
         del bt
 
-    # end to end through the public API: host A -> device, double layer, move, corner -> host
-    import ctypes  # noqa: F401
+    hotrg = None
+    if not args.no_hotrg and rank == 0:
+        hotrg = hotrg_line(torch, ctx)
+
+    # ---- end to end through the public API: host A -> device, double layer, move, corner -> host ----
     A_host = torch.from_numpy(np.ascontiguousarray(A)).pin_memory()
-    ce = CTMRG(ctx, A, w["chi"], basis="hermitian", precision=args.precision, backend="own", eig=args.eig)
+    ce = CTMRG(ctx, A, chi, basis="hermitian", precision=args.precision, backend="own", eig=args.eig)
     ce.run(args.warmup)
     C_host = torch.empty(ce.C_buf.numel(), dtype=torch.float64).pin_memory()
     s = ctx.stream
     e2e_ms = []
+    n_c = 0
     for _ in range(args.steps):
         flush.zero_()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -480,33 +527,31 @@ def run_ours(args):
     e2e_sec = float(np.sum(e2e_ms)) / 1e3
     h2d = A_host.numel() * 8
     d2h = n_c * 8
+    del ce
 
-    # roofline of the dominant libhs kernel: the block GEMM on the tensor cores
-    # (mixed precision) or the FP64 block GEMM (FP64 mode)
+    # ---- roofline of the dominant libhs kernel ----
     total_ms = float(np.sum(ms))
     if args.precision == "f64":
         k_ms, k_flops = prof["phase_ms"]["gemm"], prof["phase_flops"]["gemm"]
         src, key = "paper_2410_11596_gb300/csrc/k_gemm_f64.cu", "gemm_f64"
-        peak, bound, kname = peak64, "alu", "gemm_f64_nt_kernel (Z2 block GEMM, DFMA)"
-        psrc = "FP64: cuBLAS DGEMM 4096^3 measured in this run (no FP64 entry in the measured peaks file)"
+        peak, bound, kname = fp64_peak_tflops(torch, dev), "alu", "gemm_f64_nt_kernel (Z2 block GEMM, DFMA)"
+        psrc = "FP64: cuBLAS DGEMM 4096^3 measured in this run"
     else:
         k_ms, k_flops = prof["phase_ms"]["gemm_tc"], prof["phase_flops"]["gemm_tc"]
         src, key = "paper_2410_11596_gb300/csrc/k_gemm_tc.cu", "gemm_tc_" + args.precision
-        bf16 = measured_bf16_tflops()
+        bf16, how = measured_bf16_tflops()
         passes = 1 if args.precision == "tf32" else 3
         ratio = 1.0 if args.precision == "bf16x3" else 1.1 / 2.25   # nominal dense tf32 / bf16
         peak = bf16 * ratio / passes
         bound, kname = "tensor", f"gemm_tc_kernel<{args.precision}> (tcgen05, TMEM, TMA)"
-        psrc = (f"measured bf16 burst {bf16:.1f} TF/s x nominal {'tf32/bf16 ratio 1.1/2.25' if ratio < 1 else 'ratio 1'}"
-                f" / {passes} MMA passes per algorithmic product (of measured)")
+        psrc = (f"bf16 burst {bf16:.1f} TF/s (of {how}) x nominal "
+                f"{'tf32/bf16 1.1/2.25' if ratio < 1 else '1'} / {passes} MMA passes per algorithmic product")
     tr = NCU_TRAFFIC.get(key)
     traffic = tr["bytes_per_launch"] if tr and tr["source_sha"] == source_sha(src) else None
     achieved = k_flops / (k_ms * 1e-3) / 1e12 if k_ms > 0 else None
-    roof = {"bound": bound, "kernel": kname, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": (achieved / peak) if achieved else None, "traffic": traffic, "peak_source": psrc,
-            "share_of_move": k_ms / total_ms,
-            "note": "the timed moves carry events around the block GEMMs only (time_split_ms); the "
-                    "per-phase device time of a move is in steady_state.time_split_ms"}
+    roof = {"bound": bound, "kernel": kname, "achieved": r3(achieved), "peak": r3(peak), "unit": "TFLOP/s",
+            "frac": r3(achieved / peak) if achieved else None, "traffic": traffic, "peak_source": psrc,
+            "share_of_timed_moves": r3(k_ms / total_ms)}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "moves/s", "n_gpus": world, "steps": args.steps,
@@ -517,27 +562,20 @@ def run_ours(args):
                           "subspace": " + subspace eig (f32 Ritz), f64 projection"}[args.eig],
                 "data": "synthetic",
                 "config": {"workload": "real C4v iPEPS d=2 D=6 chi=144 (q=36: 21 even/15 odd), seeded N(0,1), "
-                                       "D4-symmetrised, max|A|=1", "D": 6, "chi": 144, "basis": "hermitian",
-                           "precision": args.precision,
-                           "eig": {"f64": "cuSOLVER Xsyevd FP64 per parity block",
-                                   "f32p": "cuSOLVER Xsyevd FP32 per parity block, FP64 Loewdin "
-                                           "re-orthonormalisation and FP64 projection C = P^T C' P",
-                                   "subspace": "warm-started block subspace iteration per parity block "
-                                               "(tcgen05 products, Chebyshev-filtered steps with locking, Cholesky-QR, "
-                                               "Jacobi Rayleigh-Ritz m=k+24), "
-                                               "FP64 Loewdin re-orthonormalisation and projection"}[args.eig],
+                                       "D4-symmetrised, max|A|=1", "basis": "hermitian", "eig": EIG_LABEL[args.eig],
                            "l2": "flushed (512 MB write) between timed moves", "parallelism": f"replicas{world}",
                            "moves_timed": f"{args.warmup + 1}-{args.warmup + args.steps}"},
-                "speedup_vs_dense_f64": (value / world) / dense["moves_per_s"] if dense else None,
-                "dense_f64": dense, "z2_other_eig": alt, "abs_dE_vs_oracle_50_moves": dE,
-                "per_dtype_50_moves": per_dtype, "complex_graded": cplx, "batched": batched,
-                "steady_state": steady,
-                "time_split_ms": {k: v / args.steps for k, v in prof["phase_ms"].items()},
-                "wall_s_timed_region": t_wall,
+                "table": table, "hotrg": hotrg, "complex": cplx, "batched": batched,
+                "per_dtype_dE_drho": per_dtype, "steady_state": steady,
                 "roofline": roof, "cpu_baseline": cpu,
                 "e2e": {"value": args.steps / e2e_sec, "unit": "moves/s", "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h},
-                "gpu_launches": prof["launches"], "clocks": clk.summary()}
+                "gpu_launches": prof["launches"], "wall_s_timed_region": r3(t_wall), "clocks": clk.summary(),
+                # last, so that a reader of the line's tail sees them: the Z2/dense ratio at equal
+                # arithmetic, the transient and steady-state rates, the energy error
+                "transient_moves_per_s": r3(transient),
+                "steady_moves_per_s": steady["moves_per_s"] if steady else None,
+                "abs_dE_vs_oracle_50_moves": r3(dE), "speedup_vs_dense": speedup}
         emit(line)
     if world > 1:
         torch.distributed.destroy_process_group()

@@ -186,7 +186,9 @@ typedef enum { HS_RDM_TWO_SITE = 0, HS_RDM_ENV_ONE_SITE = 1, HS_RDM_ONE_SITE = 2
 /* Per-step record of hs_hotrg_step (host memory). */
 typedef struct {
   int h_even, h_odd;     /* sectors kept on the truncated legs */
-  int side;              /* 0: left Gram matrix supplied the isometry, 1: right */
+  int side;              /* 0: left Gram matrix supplied the isometry, 1: right; a horizontal
+                            step works on the tensor turned by 90 degrees, R[u,l,d,r] =
+                            T[l,d,r,u], so there 0 is T's upper legs and 1 its lower ones */
   double discarded_left, discarded_right; /* discarded eigenvalue weight of each Gram matrix */
   double log_norm;       /* log of the max-abs normalisation of the new tensor */
   double trace;          /* sum_{u,l} T[u,l,u,l] of the new (normalised) tensor */
@@ -309,8 +311,13 @@ hs_status hs_hotrg_init(hs_ctx ctx, const hs_z2_tensor* a, hs_z2_tensor* t, doub
  * right Gram matrix of the fused leg, whichever discards less weight (ties:
  * left); one FP64 eigen-decomposition per parity block, states kept across
  * both blocks by eigenvalue. The new tensor is divided by its largest
- * modulus. info (host, may be NULL) receives the step record. Synchronises. */
-hs_status hs_hotrg_step(hs_ctx ctx, hs_z2_tensor* t, int chi, int direction, hs_hotrg_info* info);
+ * modulus. precision: HS_PREC_F64 runs the block GEMMs on the FP64 kernel;
+ * HS_PREC_TF32X3 / TF32 / BF16X3 run them on tcgen05 (operands split straight
+ * from their source layouts, FP32 accumulation, FP64 output); the Gram
+ * eigen-decompositions are FP64 in every precision. info (host, may be NULL)
+ * receives the step record. Synchronises. */
+hs_status hs_hotrg_step(hs_ctx ctx, hs_z2_tensor* t, int chi, int direction, hs_precision precision,
+                        hs_hotrg_info* info);
 
 /* ---- observables (Sec. III.A) ----------------------------------------- */
 

@@ -102,7 +102,7 @@ _PROTOS = {
                               c_void_p]),
     "hs_hotrg_tensor_bytes": (c_size_t, [c_int, c_int]),
     "hs_hotrg_init": (c_int, [c_void_p, POINTER(Z2Tensor), POINTER(Z2Tensor), POINTER(c_double)]),
-    "hs_hotrg_step": (c_int, [c_void_p, POINTER(Z2Tensor), c_int, c_int, POINTER(HotrgInfo)]),
+    "hs_hotrg_step": (c_int, [c_void_p, POINTER(Z2Tensor), c_int, c_int, c_int, POINTER(HotrgInfo)]),
     "hs_gemm_static": (c_int, [c_int, c_int, c_int, c_int, c_void_p, c_int, c_void_p, c_int, c_void_p, c_int,
                                c_void_p, c_void_p]),
 }
@@ -291,9 +291,9 @@ def hs_hotrg_init(ctx: int, a: Z2Tensor, t_buf) -> tuple[Z2Tensor, float]:
     return t, ln.value
 
 
-def hs_hotrg_step(ctx: int, t: Z2Tensor, chi: int, direction: int) -> dict:
+def hs_hotrg_step(ctx: int, t: Z2Tensor, chi: int, direction: int, precision: int = HS_PREC_F64) -> dict:
     info = HotrgInfo()
-    check(load().hs_hotrg_step(ctx, ctypes.byref(t), chi, direction, ctypes.byref(info)))
+    check(load().hs_hotrg_step(ctx, ctypes.byref(t), chi, direction, precision, ctypes.byref(info)))
     return info.as_dict()
 
 

@@ -272,8 +272,10 @@ class CTMRG:
 class HOTRG:
     """HOTRG of one real iPEPS double layer on one GPU through the C ABI."""
 
-    def __init__(self, ctx: Context, A: np.ndarray | torch.Tensor, chi: int, basis: str = "hermitian"):
+    def __init__(self, ctx: Context, A: np.ndarray | torch.Tensor, chi: int, basis: str = "hermitian",
+                 precision: str = "f64"):
         self.ctx = ctx
+        self.precision = PRECISION[precision]
         self._init(A, chi, basis)
 
     @on_ctx_stream
@@ -294,7 +296,7 @@ class HOTRG:
 
     def step(self) -> dict:
         direction = len(self.infos) % 2          # vertical, horizontal, vertical, ...
-        info = L.hs_hotrg_step(self.ctx.handle, self.t, self.chi, direction)
+        info = L.hs_hotrg_step(self.ctx.handle, self.t, self.chi, direction, self.precision)
         self.infos.append(info)
         self.log_norms.append(info["log_norm"])
         return info
@@ -324,6 +326,7 @@ class BatchedCTMRG:
             self.members.append(CTMRG(ctx, A, chi, precision=precision, eig=eig))
         self.nthreads = nthreads or min(len(self.members), 32)
         self.latencies_ms: list[list[float]] = []
+        self.mode = "concurrent per-instance moves (own streams, host thread pool)"
 
     def move(self) -> list[dict]:
         infos, ms = L.hs_ctmrg_move_batched([c.handle for c in self.contexts], [m.a for m in self.members],

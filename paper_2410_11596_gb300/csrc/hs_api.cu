@@ -292,7 +292,7 @@ hs_status tc_split_any(hs_ctx ctx, hs_precision prec, const Z2Mat& src_layout, c
 // C[R|N] = A[R|K] B[N|K]^T on the tensor cores from split operands (logical
 // layouts A, B; buffers padded as written by tc_split), FP64 C in layout Cm.
 hs_status tc_run(hs_ctx ctx, hs_precision prec, const Z2Mat& A, const DBuf& ahi, const DBuf& alo,
-                 const Z2Mat& B, const DBuf& bhi, const DBuf& blo, const Z2Mat& Cm, double* C, bool out_f32 = false) {
+                 const Z2Mat& B, const DBuf& bhi, const DBuf& blo, const Z2Mat& Cm, double* C, bool out_f32) {
   const int pad = tc_pad(prec), eb = tc_elem_bytes(prec);
   const size_t ce = out_f32 ? sizeof(float) : sizeof(double);
   char* Cb = reinterpret_cast<char*>(C);
@@ -590,8 +590,36 @@ hs_status orthonormalise_rows(hs_ctx ctx, hs_precision prec, double* const X[2],
         HS_TRY(gemm(ctx, HS_GEMM_OWN, GemmGroup{1, {GemmProblem{m[b], m[b], n[b], n[b], n[b], m[b], 0, 0, 0}}},
                     X[b], X[b], G[b]));
   }
-  HS_CUDA(launch_chol_inv(G[0], m[0], Li[0], G[1], m[1], Li[1], bad, ctx->stream));
-  ctx->launches += 1;
+  if (mm <= max_chol()) {
+    HS_CUDA(launch_chol_inv(G[0], m[0], Li[0], G[1], m[1], Li[1], bad, ctx->stream));
+    ctx->launches += 1;
+  } else {
+    // beyond the one-CTA kernel's shared memory: cuSOLVER potrf + trtri. In the
+    // column-major view of the row-major G the upper factor U (G = U^T U) is
+    // the row-major L = U^T, and U^{-1} is the row-major L^{-1}
+    int* linfo = static_cast<int*>(ctx->info.p) + 4;  // potrf, trtri
+    for (int b = 0; b < 2; ++b) {
+      if (m[b] == 0) continue;
+      HS_CUDA(cudaMemcpyAsync(Li[b], G[b], (size_t)m[b] * m[b] * sizeof(double), cudaMemcpyDeviceToDevice,
+                              ctx->stream));
+      size_t dw = 0, hw = 0, dw2 = 0, hw2 = 0;
+      HS_SOLVER(cusolverDnXpotrf_bufferSize(ctx->solver, ctx->params, CUBLAS_FILL_MODE_UPPER, m[b], CUDA_R_64F,
+                                            Li[b], m[b], CUDA_R_64F, &dw, &hw));
+      HS_SOLVER(cusolverDnXtrtri_bufferSize(ctx->solver, CUBLAS_FILL_MODE_UPPER, CUBLAS_DIAG_NON_UNIT, m[b],
+                                            CUDA_R_64F, Li[b], m[b], &dw2, &hw2));
+      HS_TRY(ctx->solver_dev.ensure(std::max(dw, dw2) + 256));
+      if (ctx->solver_host.size() < std::max(hw, hw2) + 1) ctx->solver_host.resize(std::max(hw, hw2) + 1);
+      HS_CUDA(cudaMemsetAsync(linfo, 0, 2 * sizeof(int), ctx->stream));
+      HS_SOLVER(cusolverDnXpotrf(ctx->solver, ctx->params, CUBLAS_FILL_MODE_UPPER, m[b], CUDA_R_64F, Li[b], m[b],
+                                 CUDA_R_64F, ctx->solver_dev.p, ctx->solver_dev.bytes, ctx->solver_host.data(),
+                                 ctx->solver_host.size(), linfo));
+      HS_SOLVER(cusolverDnXtrtri(ctx->solver, CUBLAS_FILL_MODE_UPPER, CUBLAS_DIAG_NON_UNIT, m[b], CUDA_R_64F, Li[b],
+                                 m[b], ctx->solver_dev.p, ctx->solver_dev.bytes, ctx->solver_host.data(),
+                                 ctx->solver_host.size(), linfo + 1));
+      HS_CUDA(launch_tidy_linv(Li[b], m[b], linfo, bad, ctx->stream));
+      ctx->launches += 2;
+    }
+  }
   if (stacked) {
     HS_TRY(permute(ctx, zd(m[0], m[1], n[0], n[1]), zd(n[0], n[1], m[0], m[1]), {1, 0}, X[0], Xc[0]));
     GemmGroup gl{2, {GemmProblem{m[0], n[0], m[0], m[0], m[0], n[0], 0, 0, 0},
@@ -1225,14 +1253,14 @@ hs_status hs_create(hs_ctx* out, int device, void* stream) {
     return fail(HS_ERR_SOLVER, "cuBLAS initialisation failed");
   }
   if (cudaMallocHost(&c->h_sel, sizeof(SelectOut)) != cudaSuccess ||
-      cudaMallocHost(&c->h_info, 4 * sizeof(int)) != cudaSuccess ||
+      cudaMallocHost(&c->h_info, 8 * sizeof(int)) != cudaSuccess ||
       cudaMallocHost(&c->h_tc_err, sizeof(int)) != cudaSuccess) {
     cudaGetLastError();
     hs_destroy(c);
     return fail(HS_ERR_CUDA, "pinned allocation failed");
   }
   hs_status st;
-  if ((st = c->sel.ensure(sizeof(SelectOut))) != HS_OK || (st = c->info.ensure(4 * sizeof(int))) != HS_OK ||
+  if ((st = c->sel.ensure(sizeof(SelectOut))) != HS_OK || (st = c->info.ensure(8 * sizeof(int))) != HS_OK ||
       (st = c->scratch.ensure(64)) != HS_OK || (st = c->tc_err.ensure(64)) != HS_OK) {
     hs_destroy(c);
     return st;

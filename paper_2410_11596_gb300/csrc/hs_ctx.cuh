@@ -249,6 +249,15 @@ hs_status split_corner(hs_ctx ctx, hs_precision prec, const double* H0, int n0, 
 hs_status lowdin_rows_pair(hs_ctx ctx, hs_precision prec, double* X, const int m[2], const int n[2], double* Xc,
                            int steps);
 
+// Tensor-core operands: tc_split writes the operand `layout` (src_layout's legs
+// permuted by perm) of a tcgen05 GEMM as split, K-padded hi/lo arrays; tc_run
+// computes C[R|N] = A[R|K] B[N|K]^T from two such operands into C (FP64 in
+// layout Cm, or FP32 when out_f32).
+hs_status tc_split(hs_ctx ctx, hs_precision prec, const Z2Mat& src_layout, const Z2Mat& layout,
+                   std::initializer_list<int> perm, const double* src, DBuf& hi, DBuf& lo);
+hs_status tc_run(hs_ctx ctx, hs_precision prec, const Z2Mat& A, const DBuf& ahi, const DBuf& alo, const Z2Mat& B,
+                 const DBuf& bhi, const DBuf& blo, const Z2Mat& Cm, double* C, bool out_f32 = false);
+
 // Tensor-core precisions: elements per 128-byte row (the K padding unit),
 // bytes per element, split mode of the permute/split kernels.
 int tc_pad(hs_precision p);

@@ -48,6 +48,33 @@ hs_status gram_left(hs_ctx ctx, const double* T, Sect v, Sect h, double* G) {
   return HS_OK;
 }
 
+// gram_left with the three products on the tensor cores: each operand is
+// split straight from its source by the split's permute (no separate permute
+// pass), the products come out in FP64.
+hs_status gram_left_tc(hs_ctx ctx, hs_precision prec, const double* T, Sect v, Sect h, double* G) {
+  DBuf* b = ctx->hb;
+  const Z2Mat Tm = mat(fused2(v, h), fused2(v, h));
+  const Z2Mat Tp = mat(fused2(h, v), fused2(v, h));      // [(l, d) | (u, r)]
+  const Z2Mat A1 = mat(fused2(h, v), fused2(h, v));      // [(l1, k) | (l1', k')]
+  const Z2Mat A2 = mat(fused2(v, h), fused2(v, h));      // [(k, l2) | (k', l2')]
+  const Z2Mat A1p = mat(fused2(h, h), fused2(v, v));     // [(l1, l1') | (k, k')]
+  const Z2Mat A2p = mat(fused2(h, h), fused2(v, v));     // [(l2, l2') | (k, k')]
+  const Z2Mat Gp = mat(fused2(h, h), fused2(h, h));      // [(l1, l1') | (l2, l2')]
+  const Z2Mat Gm = mat(fused2(h, h), fused2(h, h));      // [(l1, l2) | (l1', l2')]
+  HS_TRY(b[1].ensure(z2_elems(A1) * 8));
+  HS_TRY(b[2].ensure(z2_elems(A2) * 8));
+  HS_TRY(b[5].ensure(z2_elems(Gp) * 8));
+  HS_TRY(tc_split(ctx, prec, Tm, Tp, {1, 2, 0, 3}, T, ctx->sx_hi, ctx->sx_lo));
+  HS_TRY(tc_run(ctx, prec, Tp, ctx->sx_hi, ctx->sx_lo, Tp, ctx->sx_hi, ctx->sx_lo, A1, b[1].d()));
+  HS_TRY(tc_split(ctx, prec, Tm, Tm, {0, 1, 2, 3}, T, ctx->sy_hi, ctx->sy_lo));
+  HS_TRY(tc_run(ctx, prec, Tm, ctx->sy_hi, ctx->sy_lo, Tm, ctx->sy_hi, ctx->sy_lo, A2, b[2].d()));
+  HS_TRY(tc_split(ctx, prec, A1, A1p, {0, 2, 1, 3}, b[1].d(), ctx->sx_hi, ctx->sx_lo));
+  HS_TRY(tc_split(ctx, prec, A2, A2p, {1, 3, 0, 2}, b[2].d(), ctx->sy_hi, ctx->sy_lo));
+  HS_TRY(tc_run(ctx, prec, A1p, ctx->sx_hi, ctx->sx_lo, A2p, ctx->sy_hi, ctx->sy_lo, Gp, b[5].d()));
+  HS_TRY(permute(ctx, Gp, Gm, {0, 2, 1, 3}, b[5].d(), G));
+  return HS_OK;
+}
+
 unsigned long long* scratch(hs_ctx ctx, int i) { return static_cast<unsigned long long*>(ctx->scratch.p) + i; }
 
 }  // namespace
@@ -80,21 +107,27 @@ extern "C" hs_status hs_hotrg_init(hs_ctx ctx, const hs_z2_tensor* a, hs_z2_tens
   return HS_OK;
 }
 
-extern "C" hs_status hs_hotrg_step(hs_ctx ctx, hs_z2_tensor* t, int chi, int direction, hs_hotrg_info* info) {
+extern "C" hs_status hs_hotrg_step(hs_ctx ctx, hs_z2_tensor* t, int chi, int direction, hs_precision precision,
+                                   hs_hotrg_info* info) {
   HS_TRY(check_ctx(ctx));
   if (!t || !t->data || chi < 1 || (direction != 0 && direction != 1))
     return fail(HS_ERR_INVALID_ARG, "bad arguments");
+  if (precision != HS_PREC_F64 && precision != HS_PREC_TF32X3 && precision != HS_PREC_TF32 &&
+      precision != HS_PREC_BF16X3)
+    return fail(HS_ERR_INVALID_ARG, "unknown precision %d", (int)precision);
+  const bool tc = precision != HS_PREC_F64;
   cudaStream_t s = ctx->stream;
   DBuf* b = ctx->hb;
   // the step always stacks vertically; a horizontal step works on the tensor
-  // turned by 90 degrees, R[u, l, d, r] = T[l, d, r, u], and turns it back
+  // turned by 90 degrees, R[u, l, d, r] = T[l, d, r, u] (R's left leg is T's
+  // upper one, so side 0 of a horizontal step is the upper legs), and turns it back
   Sect v = make_sect(t->v_even, t->v_odd), h = make_sect(t->h_even, t->h_odd);
   const Z2Mat T0m = mat(fused2(v, h), fused2(v, h));
   double* T = t->data;
   if (direction == 1) {
     const Z2Mat Rm = mat(fused2(h, v), fused2(h, v));
     HS_TRY(b[6].ensure(z2_elems(T0m) * 8));
-    HS_TRY(permute(ctx, T0m, Rm, {1, 2, 3, 0}, t->data, b[6].d()));
+    HS_TRY(permute(ctx, T0m, Rm, {3, 0, 1, 2}, t->data, b[6].d()));
     T = b[6].d();
     const Sect tmp = v;
     v = h;
@@ -121,9 +154,14 @@ extern "C" hs_status hs_hotrg_step(hs_ctx ctx, hs_z2_tensor* t, int chi, int dir
 
   // Gram matrices of the fused left leg and (on the mirrored tensor) of the
   // fused right leg; one eigen-decomposition per parity block of each
-  HS_TRY(gram_left(ctx, T, v, h, GL));
   HS_TRY(permute(ctx, Tm, Tm, {0, 3, 2, 1}, T, Tmir));
-  HS_TRY(gram_left(ctx, Tmir, v, h, GR));
+  if (tc) {
+    HS_TRY(gram_left_tc(ctx, precision, T, v, h, GL));
+    HS_TRY(gram_left_tc(ctx, precision, Tmir, v, h, GR));
+  } else {
+    HS_TRY(gram_left(ctx, T, v, h, GL));
+    HS_TRY(gram_left(ctx, Tmir, v, h, GR));
+  }
   HS_TRY(eig_workspace(ctx, n0 > n1 ? n0 : n1));
   HS_CUDA(cudaMemsetAsync(ctx->info.p, 0, 2 * sizeof(int), s));
   HS_TRY(eig_pair(ctx, false, GL, n0, wL, GL + (long long)n0 * n0, n1, wL + n0));
@@ -160,13 +198,25 @@ extern "C" hs_status hs_hotrg_step(hs_ctx ctx, hs_z2_tensor* t, int chi, int dir
   HS_TRY(b[13].ensure(z2_elems(Mm) * 8));
   HS_TRY(b[14].ensure(z2_elems(Mp) * 8));
   HS_TRY(b[15].ensure(z2_elems(Ym) * 8));
-  HS_TRY(permute(ctx, Tm, Ttop, {0, 1, 3, 2}, T, b[0].d()));
-  HS_TRY(permute(ctx, Tm, Tbot, {1, 2, 3, 0}, T, b[1].d()));
-  HS_TRY(gemm(ctx, HS_GEMM_OWN, make_z2_gemm(Ttop, Tbot, Mm), b[0].d(), b[1].d(), b[13].d()));
-  HS_TRY(permute(ctx, Mm, Mp, {0, 4, 2, 5, 1, 3}, b[13].d(), b[14].d()));
-  HS_TRY(gemm(ctx, HS_GEMM_OWN, make_z2_gemm(Mp, UT, Ym), b[14].d(), b[12].d(), b[15].d()));
-  HS_TRY(permute(ctx, Ym, Yp, {0, 4, 1, 2, 3}, b[15].d(), b[13].d()));
-  HS_TRY(gemm(ctx, HS_GEMM_OWN, make_z2_gemm(Yp, UT, T3), b[13].d(), b[12].d(), b[14].d()));
+  if (tc) {
+    // every operand split straight from its source layout by the split's permute
+    HS_TRY(tc_split(ctx, precision, Tm, Ttop, {0, 1, 3, 2}, T, ctx->sx_hi, ctx->sx_lo));
+    HS_TRY(tc_split(ctx, precision, Tm, Tbot, {1, 2, 3, 0}, T, ctx->sy_hi, ctx->sy_lo));
+    HS_TRY(tc_run(ctx, precision, Ttop, ctx->sx_hi, ctx->sx_lo, Tbot, ctx->sy_hi, ctx->sy_lo, Mm, b[13].d()));
+    HS_TRY(tc_split(ctx, precision, Mm, Mp, {0, 4, 2, 5, 1, 3}, b[13].d(), ctx->sx_hi, ctx->sx_lo));
+    HS_TRY(tc_split(ctx, precision, UT, UT, {0, 1, 2}, b[12].d(), ctx->sy_hi, ctx->sy_lo));
+    HS_TRY(tc_run(ctx, precision, Mp, ctx->sx_hi, ctx->sx_lo, UT, ctx->sy_hi, ctx->sy_lo, Ym, b[15].d()));
+    HS_TRY(tc_split(ctx, precision, Ym, Yp, {0, 4, 1, 2, 3}, b[15].d(), ctx->sx_hi, ctx->sx_lo));
+    HS_TRY(tc_run(ctx, precision, Yp, ctx->sx_hi, ctx->sx_lo, UT, ctx->sy_hi, ctx->sy_lo, T3, b[14].d()));
+  } else {
+    HS_TRY(permute(ctx, Tm, Ttop, {0, 1, 3, 2}, T, b[0].d()));
+    HS_TRY(permute(ctx, Tm, Tbot, {1, 2, 3, 0}, T, b[1].d()));
+    HS_TRY(gemm(ctx, HS_GEMM_OWN, make_z2_gemm(Ttop, Tbot, Mm), b[0].d(), b[1].d(), b[13].d()));
+    HS_TRY(permute(ctx, Mm, Mp, {0, 4, 2, 5, 1, 3}, b[13].d(), b[14].d()));
+    HS_TRY(gemm(ctx, HS_GEMM_OWN, make_z2_gemm(Mp, UT, Ym), b[14].d(), b[12].d(), b[15].d()));
+    HS_TRY(permute(ctx, Ym, Yp, {0, 4, 1, 2, 3}, b[15].d(), b[13].d()));
+    HS_TRY(gemm(ctx, HS_GEMM_OWN, make_z2_gemm(Yp, UT, T3), b[13].d(), b[12].d(), b[14].d()));
+  }
   const size_t need = z2_elems(Tn) * 8;
   if (t->capacity_bytes < need)
     return fail(HS_ERR_WORKSPACE, "tensor buffer holds %zu bytes, %zu needed", t->capacity_bytes, need);
@@ -176,7 +226,7 @@ extern "C" hs_status hs_hotrg_step(hs_ctx ctx, hs_z2_tensor* t, int chi, int dir
     // turn back: T[u, l, d, r] = R[r, u, l, d]
     HS_TRY(permute(ctx, T3, Tn, {0, 1, 2, 3}, b[14].d(), b[13].d()));
     const Z2Mat Back = mat(fused2(hn, v), fused2(hn, v));
-    HS_TRY(permute(ctx, Tn, Back, {3, 0, 1, 2}, b[13].d(), t->data));
+    HS_TRY(permute(ctx, Tn, Back, {1, 2, 3, 0}, b[13].d(), t->data));
   }
   const long long nt = (long long)(need / 8);
   SelectOut* dsel = static_cast<SelectOut*>(ctx->sel.p);

@@ -464,6 +464,11 @@ cudaError_t launch_residual_pair(const double* Zr, const double* Xr, const float
 cudaError_t launch_gather_rows(const double* X0, int n0, const double* X1, int n1, const int* idx, int chi,
                                const SelectOut* sel, double* PT, double* P, cudaStream_t s);
 int max_subspace();
+// Largest m of launch_chol_inv (one CTA, shared memory).
+int max_chol();
+// After a library Cholesky + triangular inverse: zero the strictly upper part of
+// the row-major L^{-1} (m x m) and set *bad if info[0] or info[1] is non-zero.
+cudaError_t launch_tidy_linv(double* L, int m, const int* info, int* bad, cudaStream_t s);
 // Two small symmetric FP32 eigen-decompositions (one CTA each; m <= max_subspace()),
 // output as syevd: ascending eigenvalues, vectors as columns (column-major, in place);
 // *status = 1 if a matrix did not converge.

@@ -41,7 +41,10 @@ __global__ void fill_random_rows_kernel(double* __restrict__ X, int r0, int m, i
 // factorisation). One m x (m+1) array holds both triangles: L[i][c] at
 // (i, c) and L^{-1}[i][c] at (c, i + 1), c <= i. On a non-positive pivot the
 // status word is set and Linv is left unspecified.
-constexpr int kMaxSub = 160;
+constexpr int kMaxChol = 160;  // m (m + 1) doubles of shared memory
+// Rayleigh-Ritz problems up to kMaxSub (the Jacobi kernel below); subspaces
+// above kMaxChol take the library Cholesky route (hs_api.cu)
+constexpr int kMaxSub = 192;
 
 __global__ void __launch_bounds__(1024) chol_inv_kernel(const double* __restrict__ G0, int m0,
                                                         double* __restrict__ Linv0, const double* __restrict__ G1,
@@ -374,7 +377,7 @@ constexpr int kJacobiCtas = 8;
 // Blocks (a, b), a <= b, of the pair grid that a thread updates in every
 // round, packed a << 16 | b, and V entries (pair, component) packed the same
 // way (at most kBlkPerThread and kVPerThread per thread).
-constexpr int kBlkPerThread = 4;
+constexpr int kBlkPerThread = 5;
 constexpr int kVPerThread = 4;
 
 // Pair k of round r in the round-robin ordering of M players (player M-1
@@ -638,13 +641,13 @@ cudaError_t launch_fill_random_rows(double* X, int r0, int m, int n, unsigned lo
 
 cudaError_t launch_chol_inv(const double* G0, int m0, double* Linv0, const double* G1, int m1, double* Linv1,
                             int* status, cudaStream_t s) {
-  if (m0 < 0 || m1 < 0 || m0 > kMaxSub || m1 > kMaxSub) return cudaErrorInvalidValue;
+  if (m0 < 0 || m1 < 0 || m0 > kMaxChol || m1 > kMaxChol) return cudaErrorInvalidValue;
   if (m0 == 0 && m1 == 0) return cudaSuccess;
   const int mm = m0 > m1 ? m0 : m1;
   const size_t smem = (size_t)mm * (mm + 1) * sizeof(double);
   // set once per device
   const cudaError_t attr_err = ensure_smem_attr(reinterpret_cast<const void*>(chol_inv_kernel),
-                                                kMaxSub * (kMaxSub + 1) * (int)sizeof(double));
+                                                kMaxChol * (kMaxChol + 1) * (int)sizeof(double));
   if (attr_err != cudaSuccess) return attr_err;
   hs_launch(chol_inv_kernel, 2, 1024, smem, s, G0, m0, Linv0, G1, m1, Linv1, status);
   return cudaGetLastError();
@@ -684,5 +687,29 @@ cudaError_t launch_gather_rows(const double* X0, int n0, const double* X1, int n
 }
 
 int max_subspace() { return kMaxSub; }
+int max_chol() { return kMaxChol; }
+
+namespace {
+// Row-major L^{-1} from the library route: zero the entries above the
+// diagonal (left over from G) and raise *bad if the factorisation or the
+// inversion failed (info[0], info[1]).
+__global__ void tidy_linv_kernel(double* __restrict__ L, int m, const int* __restrict__ info, int* __restrict__ bad) {
+  hs_pdl_enter();
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < (long long)m * m;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(e / m), c = (int)(e % m);
+    if (c > i) L[e] = 0.0;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0 && (info[0] != 0 || info[1] != 0)) *bad = 1;
+}
+}  // namespace
+
+cudaError_t launch_tidy_linv(double* L, int m, const int* info, int* bad, cudaStream_t s) {
+  if (m <= 0) return cudaSuccess;
+  long long g = ((long long)m * m + 255) / 256;
+  if (g > 1024) g = 1024;
+  hs_launch(tidy_linv_kernel, (unsigned)g, 256, 0, s, L, m, info, bad);
+  return cudaGetLastError();
+}
 
 }  // namespace hs

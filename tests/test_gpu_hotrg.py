@@ -77,3 +77,33 @@ def test_side_choice_on_lopsided_network(ctx, basis, mirror):
     assert h.infos[0]["discarded_right" if not mirror else "discarded_left"] < \
         h.infos[0]["discarded_left" if not mirror else "discarded_right"]
     assert h.log_z_per_site() == pytest.approx(oh.log_z_per_site(r), rel=1e-10, abs=1e-12)
+
+
+@pytest.mark.parametrize("basis", ["hermitian", "dense"])
+@pytest.mark.parametrize("beta,chi,steps", [(0.3, 16, 30), (0.6, 16, 30)])
+def test_tf32x3_ising_log_z(ctx, basis, beta, chi, steps):
+    """HOTRG with its block GEMMs on tcgen05 (TF32x3, FP32 accumulation; FP64 Gram eig):
+    ln Z per site within 1e-6 of the FP64 oracle. The bound: each product carries a
+    relative error of about 2^-22 sqrt(K) < 1e-7 (K <= 576 here), which enters ln Z
+    through the normalisations ln c_k / 2^k, so ten times that."""
+    from paper_2410_11596_gb300.api import HOTRG
+    A = inputs.ising_ipeps(beta)
+    h = HOTRG(ctx, A, chi, basis=basis, precision="tf32x3")
+    h.run(steps)
+    ref = oh.log_z_per_site(oh.run(dl.double_layer(A), chi, steps))
+    print(f"tf32x3 HOTRG beta={beta} {basis}: |d lnZ| = {abs(h.log_z_per_site() - ref):.2e}")
+    assert h.log_z_per_site() == pytest.approx(ref, abs=1e-6)
+
+
+@pytest.mark.parametrize("chi,steps", [(8, 9), (16, 6)])
+def test_tf32x3_random_tensor(ctx, chi, steps):
+    """Random real tensor (workload 1), TF32x3 GEMMs in the Hermitian basis: ln Z per site
+    within 1e-6 of the oracle and the same number of kept states per step."""
+    from paper_2410_11596_gb300.api import HOTRG
+    A = inputs.workload_tensor(1)
+    h = HOTRG(ctx, A, chi, precision="tf32x3")
+    h.run(steps)
+    r = oh.run(dl.double_layer(A), chi, steps)
+    print(f"tf32x3 HOTRG chi={chi}: |d lnZ| = {abs(h.log_z_per_site() - oh.log_z_per_site(r)):.2e}")
+    assert h.log_z_per_site() == pytest.approx(oh.log_z_per_site(r), abs=1e-6)
+    assert [i["h_even"] + i["h_odd"] for i in h.infos] == [min(chi, len(w)) for w in r.spectra]
