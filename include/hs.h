@@ -91,17 +91,27 @@ typedef enum { HS_BASIS_DENSE = 0, HS_BASIS_HERMITIAN = 1 } hs_basis;
  *   rounding already.
  * HS_EIG_SUBSPACE: as HS_EIG_F32_PROJECTED, but the kept vectors come from a
  *   warm-started block subspace iteration on each parity block (tensor-core
- *   products H X; the warm rows re-orthonormalised by a Loewdin step, power
- *   steps by Cholesky-QR twice; Rayleigh-Ritz of size m = k + 24 by an FP32
- *   Jacobi eigensolver, at most 4 rounds, fewer when the residual stalls) seeded with the previous move's
- *   subspace (kept plus oversampled vectors). Converged when every Ritz pair that can be kept
+ *   products H X; the warm rows re-orthonormalised by a Loewdin step;
+ *   unconverged rounds take a Chebyshev-filtered step, orthonormalised by
+ *   Cholesky-QR and a Loewdin step; Rayleigh-Ritz of size m = k + max(24, k/3),
+ *   at most 192, by an FP32 Jacobi eigensolver; at most 5 rounds, fewer when
+ *   the residual stalls) seeded with the previous move's subspace (kept plus
+ *   oversampled vectors). Converged when every Ritz pair that can be kept
  *   has residual |H x - theta x| <= tol max|theta| (tol = 1e-6 with FP64
  *   products, 1e-5 with tensor-core products, above their rounding floor);
  *   otherwise, on the first move, or when the sector sizes changed, the move
  *   falls back to HS_EIG_F32_PROJECTED. Kept vectors carry
  *   a canonical sign (largest entry positive) so that the gauge, and with it
- *   the warm start, is stationary at the fixed point. */
-typedef enum { HS_EIG_F64 = 0, HS_EIG_F32_PROJECTED = 1, HS_EIG_SUBSPACE = 2 } hs_eig_mode;
+ *   the warm start, is stationary at the fixed point.
+ * HS_EIG_SUBSPACE_ADAPTIVE: as HS_EIG_SUBSPACE, with the residual tolerance of
+ *   each move set by how much the environment still changes: tol = 0.1 delta
+ *   clamped to [1e-5 (1e-6 with FP64 products), 1e-3], delta the largest change
+ *   of a kept |eigenvalue| / max|eigenvalue| since the previous move. While
+ *   the environment moves (the first moves after the start) the projector is
+ *   found only to that accuracy; at the fixed point delta vanishes and the
+ *   tolerance is HS_EIG_SUBSPACE's. Intermediate environments then differ from
+ *   an exact-eigensolver run by about delta; the fixed point does not. */
+typedef enum { HS_EIG_F64 = 0, HS_EIG_F32_PROJECTED = 1, HS_EIG_SUBSPACE = 2, HS_EIG_SUBSPACE_ADAPTIVE = 3 } hs_eig_mode;
 
 /* Which library runs the FP64 block GEMMs (HS_PREC_F64 only). */
 typedef enum { HS_GEMM_OWN = 0, HS_GEMM_CUBLAS = 1 } hs_gemm_backend;

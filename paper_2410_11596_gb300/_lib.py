@@ -26,7 +26,7 @@ HS_PREC_F64, HS_PREC_TF32X3, HS_PREC_TF32, HS_PREC_BF16X3 = 0, 1, 2, 3
 HS_BASIS_DENSE, HS_BASIS_HERMITIAN = 0, 1
 HS_GEMM_OWN, HS_GEMM_CUBLAS = 0, 1
 HS_RDM_TWO_SITE, HS_RDM_ENV_ONE_SITE, HS_RDM_ONE_SITE = 0, 1, 2
-HS_EIG_F64, HS_EIG_F32_PROJECTED, HS_EIG_SUBSPACE = 0, 1, 2
+HS_EIG_F64, HS_EIG_F32_PROJECTED, HS_EIG_SUBSPACE, HS_EIG_SUBSPACE_ADAPTIVE = 0, 1, 2, 3
 
 
 class HsError(RuntimeError):

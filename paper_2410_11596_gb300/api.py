@@ -15,7 +15,8 @@ BASIS = {"dense": L.HS_BASIS_DENSE, "hermitian": L.HS_BASIS_HERMITIAN}
 PRECISION = {"f64": L.HS_PREC_F64, "tf32x3": L.HS_PREC_TF32X3, "tf32": L.HS_PREC_TF32,
              "bf16x3": L.HS_PREC_BF16X3}
 BACKEND = {"own": L.HS_GEMM_OWN, "cublas": L.HS_GEMM_CUBLAS}
-EIG = {"f64": L.HS_EIG_F64, "f32p": L.HS_EIG_F32_PROJECTED, "subspace": L.HS_EIG_SUBSPACE}
+EIG = {"f64": L.HS_EIG_F64, "f32p": L.HS_EIG_F32_PROJECTED, "subspace": L.HS_EIG_SUBSPACE,
+       "adaptive": L.HS_EIG_SUBSPACE_ADAPTIVE}
 
 
 class Context:

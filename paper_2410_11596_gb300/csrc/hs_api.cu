@@ -977,6 +977,11 @@ hs_status cheb_filter_pair(hs_ctx ctx, hs_precision prec, const int m[2], const 
   return HS_OK;
 }
 
+// Spare rows of the subspace beyond k kept states: 24, or k/3 when that is
+// more, so that a block of many kept states (the dense basis, whose spectrum
+// interleaves both parity sectors) keeps the same relative margin past the cut.
+int oversample(int k) { return std::max(24, (k + 2) / 3); }
+
 // Subspace iteration on both parity blocks H_b (n_b x n_b, FP64 in place in
 // the C' buffer), warm-started from the previous move's kept rows. On success
 // (*done) w[0 .. m0+m1) holds the Ritz values of block 0 then block 1
@@ -993,18 +998,25 @@ hs_status subspace_projector(hs_ctx ctx, hs_env* env, int chi, int n0, int n1, d
   if (!(ctx->ws_valid && ctx->ws_env == env)) return HS_OK;
   *reason = 2;
   if (!(ctx->ws_n[0] == n0 && ctx->ws_n[1] == n1)) return HS_OK;
-  constexpr int kOver = 24, kMinOver = 8, kMaxIt = 5;
+  constexpr int kMinOver = 8, kMaxIt = 5;
   cudaStream_t s = ctx->stream;
   const bool tc = env->precision != HS_PREC_F64;
   // residual tolerance relative to max|theta|: above the rounding floor of
   // the products H X (about 2e-6 with 3-pass TF32 at n ~ 2600)
   const double kTol = tc ? 1e-5 : 1e-6;
+  // adaptive mode: while the environment still changes from move to move, the
+  // projector needs no more accuracy than that change; the tolerance follows
+  // the change of the kept spectrum since the previous move (delta, the
+  // largest change of a normalised kept |eigenvalue|): tol = 0.1 delta,
+  // between kTol and 1e-3, so that it is kTol again at the fixed point
+  const bool adaptive = env->eig_mode == HS_EIG_SUBSPACE_ADAPTIVE && ctx->prev_spec_env == env &&
+                        !ctx->prev_spec.empty();
   const hs_precision prec = env->precision;
   int m[2];
   for (int b = 0; b < 2; ++b) {
-    // k + 24 rows, at most the block and the Rayleigh-Ritz kernels' limit;
+    // k + oversample(k) rows, at most the block and the Rayleigh-Ritz kernels' limit;
     // at least 8 rows beyond the kept ones unless the subspace is the block
-    m[b] = n[b] == 0 ? 0 : std::min(std::min(ctx->ws_k[b] + kOver, n[b]), max_subspace());
+    m[b] = n[b] == 0 ? 0 : std::min(std::min(ctx->ws_k[b] + oversample(ctx->ws_k[b]), n[b]), max_subspace());
     *reason = 3;
     if (m[b] < n[b] && m[b] < ctx->ws_k[b] + kMinOver) return HS_OK;
   }
@@ -1160,9 +1172,18 @@ hs_status subspace_projector(hs_ctx ctx, hs_env* env, int chi, int n0, int n1, d
     }
     *resid = worst;
     *reason = 5;
-    if (worst > kTol) ok = false;
+    double tol = kTol;
+    if (adaptive) {
+      // this round's normalised kept spectrum against the previous move's
+      const int nk = std::min(keep, (int)ctx->prev_spec.size());
+      double delta = nk > 0 ? 0.0 : INFINITY;
+      for (int r = 0; r < nk; ++r)
+        delta = std::max(delta, std::fabs(cand[r].first / tmax - ctx->prev_spec[r]));
+      tol = std::min(1e-3, std::max(kTol, 0.1 * delta));
+    }
+    if (worst > tol) ok = false;
     for (int b = 0; b < 2; ++b)
-      if (m[b] < n[b] && kept[b] > m[b] - kOver / 2) {
+      if (m[b] < n[b] && kept[b] > m[b] - oversample(ctx->ws_k[b]) / 2) {
         ok = false;
         *reason = 6;
       }
@@ -1301,6 +1322,7 @@ hs_status hs_destroy(hs_ctx ctx) {
   if (ctx->h_tc_err) cudaFreeHost(ctx->h_tc_err);
   ctx->h_sub.release();
   ctx->h_idx.release();
+  ctx->h_lam.release();
   if (ctx->stream2) cudaStreamSynchronize(ctx->stream2);
   DBuf* s2b[] = {&ctx->solver2_dev, &ctx->solver2_32_dev};
   for (DBuf* b : s2b) b->release();
@@ -1448,6 +1470,7 @@ hs_status hs_ctmrg_init(hs_ctx ctx, const hs_z2_tensor* a, int chi_max, hs_preci
   env->eig_mode = HS_EIG_F64;
   env->dtype = a->dtype;
   ctx->ws_valid = false;  // no warm start for the subspace eigensolver yet
+  ctx->prev_spec.clear();
   if (a->dtype == HS_C128) {
     if (!herm) return fail(HS_ERR_UNSUPPORTED, "complex double layers are stored in the Hermitian basis only");
     return graded_init(ctx, a, chi_max, env);
@@ -1561,7 +1584,8 @@ hs_status hs_ctmrg_move(hs_ctx ctx, const hs_z2_tensor* a, hs_env* env, int chi,
   // tensor cores, G3 writes X3 straight into the split C' operand; the FP32
   // C' itself is formed (from that split) only when a fallback eigensolver
   // needs it
-  const bool cp_fused = f32c && env->eig_mode == HS_EIG_SUBSPACE;
+  const bool subspace_mode = env->eig_mode == HS_EIG_SUBSPACE || env->eig_mode == HS_EIG_SUBSPACE_ADAPTIVE;
+  const bool cp_fused = f32c && subspace_mode;
   // the split C' is TF32x3 (FP32 pairs): a fallback joins it; a BF16x3 split
   // went through X3 in B1
   const bool cp_join = cp_fused && tc_elem_bytes(env->precision) == 4;
@@ -1616,14 +1640,14 @@ hs_status hs_ctmrg_move(hs_ctx ctx, const hs_z2_tensor* a, hs_env* env, int chi,
   double* w0 = ctx->w.d();
   double* w1 = w0 + n0;
   HS_CUDA(cudaMemsetAsync(ctx->info.p, 0, 2 * sizeof(int), s));
-  if (env->eig_mode != HS_EIG_F64 && env->eig_mode != HS_EIG_F32_PROJECTED && env->eig_mode != HS_EIG_SUBSPACE)
+  if (env->eig_mode != HS_EIG_F64 && env->eig_mode != HS_EIG_F32_PROJECTED && !subspace_mode)
     return fail(HS_ERR_INVALID_ARG, "unknown eig mode");
   // subspace eigensolver first (when a warm start exists); its Ritz values
   // replace the spectra, ns0/ns1 are the sizes passed to the selection
   bool sub_done = false;
   int sub_iters = 0, ns0 = n0, ns1 = n1, sub_reason = -1;
   double sub_resid = 0.0;
-  if (env->eig_mode == HS_EIG_SUBSPACE) {
+  if (subspace_mode) {
     int msub[2] = {0, 0};
     HS_TRY(subspace_projector(ctx, env, chi, n0, n1, V0, V1, w0, msub, &sub_done, &sub_iters, &flops, &sub_reason,
                               &sub_resid));
@@ -1633,7 +1657,7 @@ hs_status hs_ctmrg_move(hs_ctx ctx, const hs_z2_tensor* a, hs_env* env, int chi,
       w1 = w0 + ns0;
     }
   }
-  const bool f32eig = env->eig_mode == HS_EIG_F32_PROJECTED || (env->eig_mode == HS_EIG_SUBSPACE && !sub_done);
+  const bool f32eig = env->eig_mode == HS_EIG_F32_PROJECTED || (subspace_mode && !sub_done);
   float* V0f = nullptr;
   float* V1f = nullptr;
   if (sub_done) {
@@ -1707,14 +1731,14 @@ hs_status hs_ctmrg_move(hs_ctx ctx, const hs_z2_tensor* a, hs_env* env, int chi,
   } else {
     HS_TRY(project_f32(ctx, V0f, n0, V1f, n1, didx, chi, dsel, c, q, cn, V0, V1, env, &flops));
   }
-  if (env->eig_mode == HS_EIG_SUBSPACE) {
+  if (subspace_mode) {
     // the next move starts from the whole subspace of each block: the Ritz
     // vectors of this move, or after a fallback the m largest-|lambda| FP32
     // eigenvectors, m = kept + 24 (at most the block size)
     int mnext[2];
     for (int b = 0; b < 2; ++b) {
       const int nb = b ? n1 : n0;
-      mnext[b] = std::min(std::min(cn.n[b] + 24, nb), max_subspace());
+      mnext[b] = std::min(std::min(cn.n[b] + oversample(cn.n[b]), nb), max_subspace());
       if (sub_done) mnext[b] = b ? ns1 : ns0;
     }
     const long long nws = (long long)mnext[0] * n0 + (long long)mnext[1] * n1;
@@ -1797,8 +1821,26 @@ hs_status hs_ctmrg_move(hs_ctx ctx, const hs_z2_tensor* a, hs_env* env, int chi,
   HS_CUDA(cudaMemcpyAsync(&ctx->h_sel->log_norm_C, &dsel->log_norm_C, 2 * sizeof(double),
                           cudaMemcpyDeviceToHost, s));
   HS_CUDA(cudaMemcpyAsync(ctx->h_tc_err, ctx->tc_err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+  const int nkept = cn.n[0] + cn.n[1];
+  if (env->eig_mode == HS_EIG_SUBSPACE_ADAPTIVE) {
+    // the kept eigenvalues (or Ritz values) of this move, for the next move's tolerance
+    HS_TRY(ctx->h_lam.ensure((size_t)(nkept + 1) * sizeof(double)));
+    HS_CUDA(cudaMemcpyAsync(ctx->h_lam.p, ctx->lam.p, (size_t)nkept * sizeof(double), cudaMemcpyDeviceToHost, s));
+  }
   HS_CUDA(cudaStreamSynchronize(s));
   harvest_profile(ctx);
+  if (env->eig_mode == HS_EIG_SUBSPACE_ADAPTIVE) {
+    const double* hl = static_cast<const double*>(ctx->h_lam.p);
+    ctx->prev_spec.assign(nkept, 0.0);
+    double mx = 0.0;
+    for (int i = 0; i < nkept; ++i) {
+      ctx->prev_spec[i] = std::fabs(hl[i]);
+      mx = std::max(mx, ctx->prev_spec[i]);
+    }
+    std::sort(ctx->prev_spec.begin(), ctx->prev_spec.end(), [](double x, double y) { return x > y; });
+    for (double& v : ctx->prev_spec) v = mx > 0.0 ? v / mx : 0.0;
+    ctx->prev_spec_env = env;
+  }
   if (*ctx->h_tc_err != 0) {
     const int code = *ctx->h_tc_err;
     HS_CUDA(cudaMemsetAsync(ctx->tc_err.p, 0, sizeof(int), s));
@@ -1825,7 +1867,7 @@ hs_status hs_ctmrg_move(hs_ctx ctx, const hs_z2_tensor* a, hs_env* env, int chi,
     info->log_norm_T = env->log_norm_T;
     info->gemm_flops = flops;
     info->flags = ((discarded && info->gap < 1e-9) ? 1 : 0) |
-                  (env->eig_mode == HS_EIG_SUBSPACE ? (sub_done ? 2 : 4) : 0);
+                  (subspace_mode ? (sub_done ? 2 : 4) : 0);
     info->subspace_iters = sub_iters;
     info->subspace_reason = sub_reason;
     info->subspace_resid = sub_resid;

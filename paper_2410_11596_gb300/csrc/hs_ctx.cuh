@@ -192,6 +192,12 @@ struct hs_ctx_s {
   // pinned staging: Ritz values, residuals and status words (device to
   // host), the filter's row order (host to device)
   hs::PinnedBuf h_sub, h_idx;
+  // adaptive subspace tolerance: the previous move's kept |eigenvalues|,
+  // normalised and sorted (host), the environment they belong to, and their
+  // pinned staging
+  std::vector<double> prev_spec;
+  const void* prev_spec_env = nullptr;
+  hs::PinnedBuf h_lam;
   // permute plans by layout pair and permutation (building one takes a few
   // microseconds of host time, and every move repeats the same few dozen)
   std::unordered_map<std::string, hs::PermPlan> plan_cache;
