@@ -464,24 +464,33 @@ def run_ours(args):
                 per_dtype[prec_] = [r3(abs(t1_ / t0_ - g3["energy"])), r3(float(np.abs(rho_ - rho_ref).max()))]
                 del cp
 
-    # ---- complex tensors (Sec. II.C): graded path, D=5 chi=100, 40 moves ----
+    # ---- complex tensors (Sec. II.C): graded path in the Hermitian basis against the plain
+    # complex path (four real GEMMs per complex product, complex Hermitian eigensolver), D=5 chi=100
     cplx = None
     if not args.no_complex and rank == 0:
         w5 = inputs.WORKLOADS[5]
-        ref5 = golden_energy(w5["moves"], 5)
-        cplx = {"workload": "complex C4v iPEPS d=2 D=5 chi=100, Re/Im ~ N(0,1/2)", "moves": w5["moves"]}
-        for label, prec_, eig_ in (("f64_syevd", "f64", "f64"), ("tf32x3_f32p", "tf32x3", "f32p"),
-                                   ("tf32x3_subspace", "tf32x3", "subspace")):
+        A5 = inputs.workload_tensor(5)
+        cplx = {"workload": "complex C4v iPEPS d=2 D=5 chi=100, Re/Im ~ N(0,1/2)"}
+        for label, basis_, prec_, eig_, nw, nt in (("graded_f64_syevd", "hermitian", "f64", "f64", 5, 5),
+                                                   ("dense_f64_zheevd", "dense", "f64", "f64", 5, 5),
+                                                   ("graded_tf32x3_subspace", "hermitian", "tf32x3", "subspace",
+                                                    args.warmup, args.steps)):
             try:
-                cc = CTMRG(ctx, inputs.workload_tensor(5), w5["chi"], precision=prec_, eig=eig_)
-                msc = timed_moves(torch, cc, ctx, w5["moves"], flush)
-                e5 = cc.energy(h)
-                cplx[label] = {"moves_per_s_last10": r3(10 / (np.sum(msc[-10:]) / 1e3)),
-                               "moves_per_s_all": r3(w5["moves"] / (np.sum(msc) / 1e3)),
-                               "abs_dE": r3(abs(e5 - ref5) if ref5 is not None else None)}
+                cc = CTMRG(ctx, A5, w5["chi"], basis=basis_, precision=prec_, eig=eig_)
+                cc.run(nw)
+                msc = timed_moves(torch, cc, ctx, nt, flush)
+                at = 10 if nw + nt <= 10 else w5["moves"]
+                cc.run(at - nw - nt)
+                ref5 = golden_energy(at, 5)
+                cplx[label] = {"moves_per_s": r3(nt / (np.sum(msc) / 1e3)), "moves": f"{nw + 1}-{nw + nt}",
+                               "abs_dE": r3(abs(cc.energy(h) - ref5) if ref5 is not None else None), "dE_at": at}
                 del cc
             except L.HsError as e:
                 cplx[label] = {"error": str(e)[:120]}
+        try:
+            cplx["speedup_f64"] = r3(cplx["graded_f64_syevd"]["moves_per_s"] / cplx["dense_f64_zheevd"]["moves_per_s"])
+        except (KeyError, TypeError, ZeroDivisionError):
+            pass
 
     # ---- many independent instances (32 real iPEPS, D uniform in 3..7, chi = 4 D^2) ----
     batched = None

@@ -105,12 +105,13 @@ typedef enum { HS_BASIS_DENSE = 0, HS_BASIS_HERMITIAN = 1 } hs_basis;
  *   the warm start, is stationary at the fixed point.
  * HS_EIG_SUBSPACE_ADAPTIVE: as HS_EIG_SUBSPACE, with the residual tolerance of
  *   each move set by how much the environment still changes: tol = 0.1 delta
- *   clamped to [1e-5 (1e-6 with FP64 products), 1e-3], delta the largest change
- *   of a kept |eigenvalue| / max|eigenvalue| since the previous move. While
- *   the environment moves (the first moves after the start) the projector is
- *   found only to that accuracy; at the fixed point delta vanishes and the
- *   tolerance is HS_EIG_SUBSPACE's. Intermediate environments then differ from
- *   an exact-eigensolver run by about delta; the fixed point does not. */
+ *   clamped to [1e-5 (1e-6 with FP64 products), 1e-3], delta the residual of the
+ *   warm start in the previous move's first round (how far the kept subspace
+ *   turned in one move). While the environment moves (the first moves after
+ *   the start) the projector is found only to that accuracy; at the fixed
+ *   point delta falls to the rounding level and the tolerance is
+ *   HS_EIG_SUBSPACE's. Intermediate environments then differ from an
+ *   exact-eigensolver run by about delta; the fixed point does not. */
 typedef enum { HS_EIG_F64 = 0, HS_EIG_F32_PROJECTED = 1, HS_EIG_SUBSPACE = 2, HS_EIG_SUBSPACE_ADAPTIVE = 3 } hs_eig_mode;
 
 /* Which library runs the FP64 block GEMMs (HS_PREC_F64 only). */
@@ -126,13 +127,15 @@ typedef struct hs_ctx_s* hs_ctx;
  * parity tuples follow in lexicographic order), so the sector sizes are the
  * whole descriptor.
  *
- * Complex A (dtype HS_C128, Hermitian basis only; Sec. II.C): every block of a
- * in the eigenbasis of S is purely real (even total parity) or purely
+ * Complex A (dtype HS_C128) in the Hermitian basis (Sec. II.C): every block of
+ * a in the eigenbasis of S is purely real (even total parity) or purely
  * imaginary (odd). Such "graded" tensors, and the environment built from
  * them, are stored as ONE dense row-major real matrix over the same row and
  * column leg groups, rows and columns each in FSO order (even group first);
  * an entry of odd total parity holds the imaginary part, an even one the real
- * part. Products follow the sign rule of Eq. (2)-(3). */
+ * part. Products follow the sign rule of Eq. (2)-(3).
+ * Complex A in the dense basis (the comparison path, nothing of the symmetry
+ * used): the plain double layer, interleaved complex128, (D^2)^4 entries. */
 typedef struct {
   int D;                 /* bond dimension of A */
   int n_even, n_odd;     /* per-leg sector sizes: (D(D+1)/2, D(D-1)/2) or (D^2, 0) */
@@ -249,14 +252,17 @@ hs_status hs_from_hermitian_basis(hs_ctx ctx, const hs_z2_tensor* t, double* a_d
 /* Fused form of the two calls above: from A (device; real, or interleaved
  * complex128 with dtype HS_C128) straight to the stored blocks of a~ in
  * `basis` (HS_BASIS_DENSE gives the plain layout).
- * dtype HS_C128 (A interleaved complex128, Hermitian basis only) writes the
- * graded a~ (Sec. II.C). Asynchronous. */
+ * dtype HS_C128 writes the graded a~ in the Hermitian basis (Sec. II.C), and
+ * the plain complex double layer (interleaved complex128) in the dense basis.
+ * Asynchronous. */
 hs_status hs_double_layer_hermitian(hs_ctx ctx, const double* A, int d, int D, hs_dtype dtype,
                                     hs_basis basis, hs_z2_tensor* out);
 
 /* ---- CTMRG (Sec. II.A, Fig. 1(d)) ------------------------------------- */
 
-/* Bytes needed for env->C and env->T at bond dimension D and chi_max. */
+/* Bytes needed for env->C and env->T at bond dimension D and chi_max (real
+ * environments and graded complex ones; complex environments of the dense
+ * basis, interleaved complex128, need twice these). */
 hs_status hs_env_bytes(int D, int chi_max, size_t* C_bytes, size_t* T_bytes);
 
 /* Traced-boundary initial environment: the open outer legs of the first
@@ -275,10 +281,17 @@ hs_status hs_ctmrg_init(hs_ctx ctx, const hs_z2_tensor* a, int chi_max, hs_preci
  * largest singular values of C' = U S V^dagger, found as the top
  * eigenvectors of H = M M^T with C' = J M J (J = diag(1, i) by parity; one
  * eigen-decomposition of size chi*D^2, FP64 for HS_EIG_F64, FP32 followed by
- * two FP64 Loewdin steps otherwise); C <- U^dagger C' U,
+ * two FP64 Loewdin steps for HS_EIG_F32_PROJECTED; the subspace modes run the
+ * warm-started subspace iteration on H as one block, residual tolerance 1e-8
+ * with FP64 products and 1e-5 with tensor-core products, falling back to the
+ * FP32 decomposition); C <- U^dagger C' U,
  * T <- U^dagger (T a) U; the new boundary sectors are (chi, 0). lam_* in info
  * are singular values. The graded GEMMs and H run in the environment's
  * precision (FP64 kernel or tcgen05).
+ * Complex environments of the dense basis (the comparison path): the same
+ * truncation with plain complex tensors, each complex product four FP64 GEMMs,
+ * U from the complex Hermitian FP64 eigen-decomposition of C' C'^dagger; only
+ * HS_PREC_F64 with HS_EIG_F64 (else HS_ERR_UNSUPPORTED).
  * info (host, may be NULL) receives the move record. Synchronises once
  * (to learn the new sector sizes). */
 hs_status hs_ctmrg_move(hs_ctx ctx, const hs_z2_tensor* a, hs_env* env, int chi,

@@ -105,12 +105,12 @@ class CTMRG:
         self.d, self.D = int(self.A.shape[0]), int(self.A.shape[1])
         self.chi = chi
         nbytes = L.hs_z2_tensor_bytes(self.D, BASIS[basis], self.dtype)
-        if nbytes == 0:
-            raise ValueError("complex tensors need the Hermitian basis")
         self.a_buf = torch.empty(nbytes // 8, dtype=torch.float64, device=dev)
         self.a = L.hs_double_layer_hermitian(ctx.handle, self.A, self.d, self.D, self.dtype, BASIS[basis],
                                              self.a_buf)
         cb, tb = L.hs_env_bytes(self.D, chi)
+        if self.complex and basis == "dense":      # complex environments of the plain basis: complex128
+            cb, tb = 2 * cb, 2 * tb
         self.C_buf = torch.empty(cb // 8, dtype=torch.float64, device=dev)
         self.T_buf = torch.empty(tb // 8, dtype=torch.float64, device=dev)
         self.env = L.hs_ctmrg_init(ctx.handle, self.a, chi, PRECISION[precision], BACKEND[backend],

@@ -988,7 +988,8 @@ int oversample(int k) { return std::max(24, (k + 2) / 3); }
 // (ascending per block), sxr[b] the matching Ritz vectors as rows, and
 // m_out the subspace sizes; otherwise the caller falls back.
 hs_status subspace_projector(hs_ctx ctx, hs_env* env, int chi, int n0, int n1, double* H0, double* H1, double* w,
-                             int* m_out, bool* done, int* iters, double* flops, int* reason, double* resid) {
+                             int* m_out, bool* done, int* iters, double* flops, int* reason, double* resid,
+                             double tol_scale) {
   *done = false;
   *iters = 0;
   *resid = 0.0;
@@ -1003,14 +1004,15 @@ hs_status subspace_projector(hs_ctx ctx, hs_env* env, int chi, int n0, int n1, d
   const bool tc = env->precision != HS_PREC_F64;
   // residual tolerance relative to max|theta|: above the rounding floor of
   // the products H X (about 2e-6 with 3-pass TF32 at n ~ 2600)
-  const double kTol = tc ? 1e-5 : 1e-6;
+  const double kTol = (tc ? 1e-5 : 1e-6) * tol_scale;
   // adaptive mode: while the environment still changes from move to move, the
-  // projector needs no more accuracy than that change; the tolerance follows
-  // the change of the kept spectrum since the previous move (delta, the
-  // largest change of a normalised kept |eigenvalue|): tol = 0.1 delta,
-  // between kTol and 1e-3, so that it is kTol again at the fixed point
+  // projector needs no more accuracy than that change. Its measure: the
+  // residual of the warm start in the previous move's first round (how far
+  // the kept subspace turned in one move); tol = 0.1 of it, between kTol and
+  // 1e-3, so that it is kTol again at the fixed point
   const bool adaptive = env->eig_mode == HS_EIG_SUBSPACE_ADAPTIVE && ctx->prev_spec_env == env &&
-                        !ctx->prev_spec.empty();
+                        ctx->prev_first_resid > 0.0;
+  const double tol_move = adaptive ? std::min(1e-3, std::max(kTol, 0.1 * ctx->prev_first_resid)) : kTol;
   const hs_precision prec = env->precision;
   int m[2];
   for (int b = 0; b < 2; ++b) {
@@ -1023,6 +1025,9 @@ hs_status subspace_projector(hs_ctx ctx, hs_env* env, int chi, int n0, int n1, d
   int* bad = static_cast<int*>(ctx->info.p) + 2;
   HS_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), s));
   HS_TRY(eig32_workspace(ctx, m[0] > m[1] ? m[0] : m[1]));
+  // the selection issued by every round writes chi indices per block and chi values
+  HS_TRY(ctx->idx.ensure(2 * (size_t)chi * sizeof(int)));
+  HS_TRY(ctx->lam.ensure((size_t)chi * sizeof(double)));
   // stacked buffers: block 1 after block 0
   const long long mn0 = (long long)m[0] * n[0], mn1 = (long long)m[1] * n[1];
   for (Stacked* t : {&ctx->sx, &ctx->sz, &ctx->sxc, &ctx->szc, &ctx->sxr, &ctx->szr})
@@ -1172,16 +1177,11 @@ hs_status subspace_projector(hs_ctx ctx, hs_env* env, int chi, int n0, int n1, d
     }
     *resid = worst;
     *reason = 5;
-    double tol = kTol;
-    if (adaptive) {
-      // this round's normalised kept spectrum against the previous move's
-      const int nk = std::min(keep, (int)ctx->prev_spec.size());
-      double delta = nk > 0 ? 0.0 : INFINITY;
-      for (int r = 0; r < nk; ++r)
-        delta = std::max(delta, std::fabs(cand[r].first / tmax - ctx->prev_spec[r]));
-      tol = std::min(1e-3, std::max(kTol, 0.1 * delta));
+    if (it == 0) {
+      ctx->prev_first_resid = worst;
+      ctx->prev_spec_env = env;
     }
-    if (worst > tol) ok = false;
+    if (worst > tol_move) ok = false;
     for (int b = 0; b < 2; ++b)
       if (m[b] < n[b] && kept[b] > m[b] - oversample(ctx->ws_k[b]) / 2) {
         ok = false;
@@ -1305,6 +1305,12 @@ hs_status hs_destroy(hs_ctx ctx) {
   for (DBuf* b : bufs) b->release();
   for (DBuf& b : ctx->r) b.release();
   for (DBuf& b : ctx->hb) b.release();
+  for (DBuf& b : ctx->gb) b.release();
+  for (DBuf& b : ctx->zr) b.release();
+  for (DBuf& b : ctx->zd) b.release();
+  ctx->ga.release();
+  ctx->ps_hi.release();
+  ctx->ps_lo.release();
   DBuf* more[] = {&ctx->c32,  &ctx->w32,   &ctx->pcol,         &ctx->pt2,   &ctx->gram,
                   &ctx->wproj, &ctx->solver32_dev, &ctx->splitk, &ctx->ws_pt, &ctx->sth,
                   &ctx->sx_hi, &ctx->sx_lo, &ctx->sy_hi, &ctx->sy_lo, &ctx->schol};
@@ -1322,7 +1328,6 @@ hs_status hs_destroy(hs_ctx ctx) {
   if (ctx->h_tc_err) cudaFreeHost(ctx->h_tc_err);
   ctx->h_sub.release();
   ctx->h_idx.release();
-  ctx->h_lam.release();
   if (ctx->stream2) cudaStreamSynchronize(ctx->stream2);
   DBuf* s2b[] = {&ctx->solver2_dev, &ctx->solver2_32_dev};
   for (DBuf* b : s2b) b->release();
@@ -1352,7 +1357,7 @@ hs_status hs_sync(hs_ctx ctx) {
 
 size_t hs_z2_tensor_bytes(int D, hs_basis basis, hs_dtype dtype) {
   if (D <= 0) return 0;
-  if (dtype == HS_C128) return basis == HS_BASIS_HERMITIAN ? graded_tensor_bytes(D) : 0;
+  if (dtype == HS_C128) return basis == HS_BASIS_HERMITIAN ? graded_tensor_bytes(D) : zdense_tensor_bytes(D);
   if (dtype != HS_F64) return 0;
   return a_elems(D, basis) * sizeof(double);
 }
@@ -1406,13 +1411,13 @@ hs_status hs_double_layer_hermitian(hs_ctx ctx, const double* A, int d, int D, h
   if (dtype != HS_F64 && dtype != HS_C128) return fail(HS_ERR_DTYPE, "unknown dtype");
   if (basis != HS_BASIS_DENSE && basis != HS_BASIS_HERMITIAN)
     return fail(HS_ERR_INVALID_ARG, "unknown basis");
-  if (dtype == HS_C128 && basis != HS_BASIS_HERMITIAN)
-    return fail(HS_ERR_UNSUPPORTED, "complex double layers are stored in the Hermitian basis only");
   const size_t need = hs_z2_tensor_bytes(D, basis, dtype);
   if (out->capacity_bytes < need)
     return fail(HS_ERR_WORKSPACE, "output holds %zu bytes, %zu needed", out->capacity_bytes, need);
-  if (dtype == HS_C128)
+  if (dtype == HS_C128 && basis == HS_BASIS_HERMITIAN)
     HS_TRY(graded_double_layer(ctx, A, d, D, out));
+  else if (dtype == HS_C128)
+    HS_TRY(zdense_double_layer(ctx, A, d, D, out));
   else
     HS_CUDA(launch_double_layer_blocks(A, d, D, basis == HS_BASIS_HERMITIAN, out->data, ctx->stream));
   const Sect q = q_sect(D, basis);
@@ -1470,11 +1475,8 @@ hs_status hs_ctmrg_init(hs_ctx ctx, const hs_z2_tensor* a, int chi_max, hs_preci
   env->eig_mode = HS_EIG_F64;
   env->dtype = a->dtype;
   ctx->ws_valid = false;  // no warm start for the subspace eigensolver yet
-  ctx->prev_spec.clear();
-  if (a->dtype == HS_C128) {
-    if (!herm) return fail(HS_ERR_UNSUPPORTED, "complex double layers are stored in the Hermitian basis only");
-    return graded_init(ctx, a, chi_max, env);
-  }
+  ctx->prev_first_resid = 0.0;
+  if (a->dtype == HS_C128) return herm ? graded_init(ctx, a, chi_max, env) : zdense_init(ctx, a, chi_max, env);
   HS_CUDA(launch_ctmrg_init(a->data, D, herm, env->C, env->T, ctx->stream));
   // normalise like every later move
   const Z2Mat Cm = mat(fused1(qs), fused1(qs)), Tm = mat(fused2(qs, qs), fused1(qs));
@@ -1530,7 +1532,8 @@ hs_status hs_ctmrg_move(hs_ctx ctx, const hs_z2_tensor* a, hs_env* env, int chi,
     return fail(HS_ERR_SHAPE, "tensor and environment disagree on D or basis");
   if (chi < 1 || chi > env->chi_max) return fail(HS_ERR_SHAPE, "chi %d outside [1, %d]", chi, env->chi_max);
   if (env->dtype != a->dtype) return fail(HS_ERR_DTYPE, "tensor and environment disagree on dtype");
-  if (env->dtype == HS_C128) return graded_move(ctx, a, env, chi, info);
+  if (env->dtype == HS_C128)
+    return env->basis == HS_BASIS_DENSE ? zdense_move(ctx, a, env, chi, info) : graded_move(ctx, a, env, chi, info);
   cudaStream_t s = ctx->stream;
   const hs_gemm_backend be = env->gemm_backend;
   const bool tc = env->precision != HS_PREC_F64;
@@ -1821,26 +1824,8 @@ hs_status hs_ctmrg_move(hs_ctx ctx, const hs_z2_tensor* a, hs_env* env, int chi,
   HS_CUDA(cudaMemcpyAsync(&ctx->h_sel->log_norm_C, &dsel->log_norm_C, 2 * sizeof(double),
                           cudaMemcpyDeviceToHost, s));
   HS_CUDA(cudaMemcpyAsync(ctx->h_tc_err, ctx->tc_err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
-  const int nkept = cn.n[0] + cn.n[1];
-  if (env->eig_mode == HS_EIG_SUBSPACE_ADAPTIVE) {
-    // the kept eigenvalues (or Ritz values) of this move, for the next move's tolerance
-    HS_TRY(ctx->h_lam.ensure((size_t)(nkept + 1) * sizeof(double)));
-    HS_CUDA(cudaMemcpyAsync(ctx->h_lam.p, ctx->lam.p, (size_t)nkept * sizeof(double), cudaMemcpyDeviceToHost, s));
-  }
   HS_CUDA(cudaStreamSynchronize(s));
   harvest_profile(ctx);
-  if (env->eig_mode == HS_EIG_SUBSPACE_ADAPTIVE) {
-    const double* hl = static_cast<const double*>(ctx->h_lam.p);
-    ctx->prev_spec.assign(nkept, 0.0);
-    double mx = 0.0;
-    for (int i = 0; i < nkept; ++i) {
-      ctx->prev_spec[i] = std::fabs(hl[i]);
-      mx = std::max(mx, ctx->prev_spec[i]);
-    }
-    std::sort(ctx->prev_spec.begin(), ctx->prev_spec.end(), [](double x, double y) { return x > y; });
-    for (double& v : ctx->prev_spec) v = mx > 0.0 ? v / mx : 0.0;
-    ctx->prev_spec_env = env;
-  }
   if (*ctx->h_tc_err != 0) {
     const int code = *ctx->h_tc_err;
     HS_CUDA(cudaMemsetAsync(ctx->tc_err.p, 0, sizeof(int), s));
@@ -1949,6 +1934,14 @@ hs_status hs_gemm(hs_ctx ctx, hs_precision precision, int M, int N, int K, const
 hs_status hs_env_to_dense(hs_ctx ctx, const hs_env* env, double* C_dense, double* T_dense) {
   HS_TRY(check_ctx(ctx));
   if (!env || !C_dense || !T_dense) return fail(HS_ERR_INVALID_ARG, "bad arguments");
+  if (env->dtype == HS_C128 && env->basis == HS_BASIS_DENSE) {
+    // stored dense already (interleaved complex128)
+    const size_t chi = (size_t)(env->chi_even + env->chi_odd), q = (size_t)env->D * env->D;
+    HS_CUDA(cudaMemcpyAsync(C_dense, env->C, 2 * chi * chi * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+    HS_CUDA(cudaMemcpyAsync(T_dense, env->T, 2 * chi * q * chi * sizeof(double), cudaMemcpyDeviceToDevice,
+                            ctx->stream));
+    return HS_OK;
+  }
   if (env->dtype == HS_C128) {
     HS_CUDA(launch_env_to_dense_graded(env->C, env->T, env->D, env->chi_even, env->chi_odd, C_dense, T_dense,
                                        ctx->stream));

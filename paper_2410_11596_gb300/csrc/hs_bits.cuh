@@ -256,6 +256,28 @@ HS_HD void split_f32_tf32x3_sel(uint32_t u, uint32_t& hi, uint32_t& lo) {
   lo = ex == 0u ? sign : (ex == 0x7F800000u ? special : l);
 }
 
+// split_f32_tf32x3 without the cases of the top of the exponent range (the
+// GEMM epilogue's form): the same bits for every pattern except those that
+// round up to 2^128 (hi is infinite in both; lo is infinite here) and NaN or
+// infinity (both give non-finite parts). A value of the normalised
+// contractions never comes near 2^127, and one that did would still surface
+// as a non-finite result downstream.
+HS_HD void split_f32_tf32x3_fin(uint32_t u, uint32_t& hi, uint32_t& lo) {
+  const uint32_t sign = u & 0x80000000u;
+  const bool tiny = (u & 0x7F800000u) == 0u;
+  const uint32_t h = (u + 0x1000u) & 0xFFFFE000u;
+  float fv, fh;
+  std::memcpy(&fv, &u, 4);
+  std::memcpy(&fh, &h, 4);
+  const float d = fv - fh;  // exact
+  uint32_t ld;
+  std::memcpy(&ld, &d, 4);
+  uint32_t l = (ld & 0x7F800000u) == 0u ? (ld & 0x80000000u) : ld;  // below the normal range: signed zero
+  l = (ld & 0x7FFFFFFFu) == 0u ? 0u : l;
+  hi = tiny ? sign : h;
+  lo = tiny ? sign : l;
+}
+
 // The FP64 value of the IEEE single bit pattern f (exact). Subnormal singles
 // are widened by the FP64 conversion (`slow` is called for them).
 HS_HD bool f32_widen_fast(uint32_t f, unsigned long long& out) {

@@ -166,6 +166,8 @@ struct hs_ctx_s {
   hs::DBuf gb[12];
   // complex observables (planar real / imaginary parts)
   hs::DBuf zr[40];
+  // complex CTMRG in the plain basis (hs_zdense.cu)
+  hs::DBuf zd[40];
   // split-K partial sums of the FP64 GEMM
   hs::DBuf splitk;
   // subspace eigensolver: warm start (previous kept rows, per block) and
@@ -192,12 +194,10 @@ struct hs_ctx_s {
   // pinned staging: Ritz values, residuals and status words (device to
   // host), the filter's row order (host to device)
   hs::PinnedBuf h_sub, h_idx;
-  // adaptive subspace tolerance: the previous move's kept |eigenvalues|,
-  // normalised and sorted (host), the environment they belong to, and their
-  // pinned staging
-  std::vector<double> prev_spec;
+  // adaptive subspace tolerance: the warm start's residual in the previous
+  // move's first round, and the environment it belongs to
+  double prev_first_resid = 0.0;
   const void* prev_spec_env = nullptr;
-  hs::PinnedBuf h_lam;
   // permute plans by layout pair and permutation (building one takes a few
   // microseconds of host time, and every move repeats the same few dozen)
   std::unordered_map<std::string, hs::PermPlan> plan_cache;
@@ -243,6 +243,11 @@ hs_status graded_double_layer(hs_ctx ctx, const double* A, int d, int D, hs_z2_t
 size_t graded_tensor_bytes(int D);
 hs_status graded_init(hs_ctx ctx, const hs_z2_tensor* a, int chi_max, hs_env* env);
 hs_status graded_move(hs_ctx ctx, const hs_z2_tensor* a, hs_env* env, int chi, hs_move_info* info);
+// Complex CTMRG in the plain basis (hs_zdense.cu): the comparison path.
+size_t zdense_tensor_bytes(int D);
+hs_status zdense_double_layer(hs_ctx ctx, const double* A, int d, int D, hs_z2_tensor* out);
+hs_status zdense_init(hs_ctx ctx, const hs_z2_tensor* a, int chi_max, hs_env* env);
+hs_status zdense_move(hs_ctx ctx, const hs_z2_tensor* a, hs_env* env, int chi, hs_move_info* info);
 // Loewdin re-orthonormalisation of the m rows of X (n long), `steps` times.
 hs_status lowdin_rows(hs_ctx ctx, hs_precision prec, double* X, int m, int n, double* Xc, int steps);
 // Stacked parity-block pairs (block 1 right after block 0): the pair as one
@@ -263,6 +268,17 @@ hs_status tc_split(hs_ctx ctx, hs_precision prec, const Z2Mat& src_layout, const
                    std::initializer_list<int> perm, const double* src, DBuf& hi, DBuf& lo);
 hs_status tc_run(hs_ctx ctx, hs_precision prec, const Z2Mat& A, const DBuf& ahi, const DBuf& alo, const Z2Mat& B,
                  const DBuf& bhi, const DBuf& blo, const Z2Mat& Cm, double* C, bool out_f32 = false);
+
+// Warm-started subspace eigensolver of hs_api.cu: on success (*done) the
+// Ritz values of both blocks are in w (block 0 then 1), the Ritz vectors in
+// ctx->sxr, the selection of the chi largest |values| in ctx->sel / idx / lam;
+// otherwise the caller falls back to a full eigen-decomposition.
+// tol_scale multiplies the residual tolerance (see graded_move).
+hs_status subspace_projector(hs_ctx ctx, hs_env* env, int chi, int n0, int n1, double* H0, double* H1, double* w,
+                             int* m_out, bool* done, int* iters, double* flops, int* reason, double* resid,
+                             double tol_scale = 1.0);
+// Spare subspace rows beyond k kept states.
+int oversample(int k);
 
 // Tensor-core precisions: elements per 128-byte row (the K padding unit),
 // bytes per element, split mode of the permute/split kernels.

@@ -164,6 +164,8 @@ hs_status graded_init(hs_ctx ctx, const hs_z2_tensor* a, int chi_max, hs_env* en
   HS_TRY(ctx->gb[5].ensure(2 * c * n * sizeof(double)));      // V1, V1^T + conj
   HS_TRY(ctx->gb[6].ensure(c * n * sizeof(double)));          // Loewdin scratch
   HS_TRY(ctx->w.ensure(n * sizeof(double)));
+  HS_TRY(ctx->lam.ensure(c * sizeof(double)));    // selection of the subspace eigensolver
+  HS_TRY(ctx->idx.ensure(2 * c * sizeof(int)));
   HS_TRY(eig_workspace(ctx, (int)n));
   return HS_OK;
 }
@@ -242,7 +244,34 @@ hs_status graded_move(hs_ctx ctx, const hs_z2_tensor* a, hs_env* env, int chi, h
   }
   flops += 2.0 * n * (double)n * n;
   const bool f32 = env->eig_mode != HS_EIG_F64;
-  {
+  // the subspace eigensolver on H (one block; H is symmetric positive
+  // semi-definite, so the chi largest |eigenvalues| are the chi largest
+  // singular values squared), warm-started from the previous move's Ritz
+  // vectors; the full FP32 eigen-decomposition when it does not apply
+  const bool sub_mode = env->eig_mode == HS_EIG_SUBSPACE || env->eig_mode == HS_EIG_SUBSPACE_ADAPTIVE;
+  bool sub_done = false;
+  int sub_iters = 0, sub_reason = -1, msub[2] = {0, 0};
+  double sub_resid = 0.0;
+  if (sub_mode) {
+    ctx->cp_f32 = false;
+    ctx->sH_fresh = false;
+    ctx->sel_ready = false;
+    // H's eigenvalues are the squared singular values, so its relative gap at
+    // the cut is about s_cut / s_max (~1e-2) times that of the singular values:
+    // with FP64 products the residual tolerance is that much tighter (with
+    // tensor-core products it stays at their rounding floor)
+    HS_TRY(subspace_projector(ctx, env, k, (int)n, 0, Mh, Mh + n * n, ctx->w.d(), msub, &sub_done, &sub_iters, &flops,
+                              &sub_reason, &sub_resid, prec == HS_PREC_F64 ? 1e-2 : 1.0));
+  }
+  if (sub_done) {
+    // the converged round's selection (ctx->idx / sel) picks the kept Ritz vectors
+    PhaseScope ps(ctx, HS_PHASE_SELECT);
+    HS_CUDA(launch_gather_rows(ctx->sxr.d(0), (int)n, ctx->sxr.d(1), 0, static_cast<int*>(ctx->idx.p), k, dsel, PT,
+                               V1, s));
+    HS_CUDA(launch_row_sign(PT, k, (int)n, s));
+    HS_CUDA(cudaMemsetAsync(ctx->info.p, 0, sizeof(int), s));
+    ctx->launches += 2;
+  } else {
     PhaseScope ps(ctx, HS_PHASE_EIG);
     HS_CUDA(cudaMemsetAsync(ctx->info.p, 0, sizeof(int), s));
     if (!f32) {
@@ -255,7 +284,7 @@ hs_status graded_move(hs_ctx ctx, const hs_z2_tensor* a, hs_env* env, int chi, h
       HS_TRY(eig_single(ctx, true, ctx->c32.p, (int)n, ctx->w32.p));
     }
   }
-  {
+  if (!sub_done) {
     PhaseScope ps(ctx, HS_PHASE_SELECT);
     if (!f32)
       HS_CUDA(launch_graded_select(ctx->w.d(), Mh, (int)n, k, PT, dsel, s));
@@ -265,7 +294,30 @@ hs_status graded_move(hs_ctx ctx, const hs_z2_tensor* a, hs_env* env, int chi, h
     HS_CUDA(launch_row_sign(PT, k, (int)n, s));  // canonical sign: largest entry of each row positive
     ctx->launches += 2;
   }
-  if (f32) HS_TRY(lowdin_rows(ctx, HS_PREC_F64, PT, k, (int)n, Lw, 2));
+  if (sub_mode) {
+    // warm start of the next move: the Ritz vectors, or the m eigenvectors of
+    // largest eigenvalue after a full decomposition
+    const int mnext = sub_done ? msub[0] : std::min(std::min(k + oversample(k), (int)n), max_subspace());
+    HS_TRY(ctx->ws_pt.ensure(((size_t)mnext * n + 1) * sizeof(double)));
+    HS_TRY(ctx->sf_idx.ensure(((size_t)mnext + 1) * sizeof(int)));
+    if (sub_done)
+      HS_CUDA(cudaMemcpyAsync(ctx->ws_pt.d(), ctx->sxr.d(0), (size_t)mnext * n * sizeof(double),
+                              cudaMemcpyDeviceToDevice, s));
+    else
+      HS_CUDA(launch_top_rows(static_cast<const float*>(ctx->w32.p), static_cast<const float*>(ctx->c32.p), (int)n,
+                              mnext, static_cast<int*>(ctx->sf_idx.p), ctx->ws_pt.d(), s));
+    ctx->ws_env = env;
+    ctx->ws_valid = true;
+    ctx->ws_k[0] = k;
+    ctx->ws_k[1] = 0;
+    ctx->ws_m[0] = mnext;
+    ctx->ws_m[1] = 0;
+    ctx->ws_n[0] = (int)n;
+    ctx->ws_n[1] = 0;
+    ctx->ws_moves += 1;
+  }
+  // Ritz vectors are orthonormal to ~1e-6 (FP32 Rayleigh-Ritz), FP32 eigenvectors to ~1e-7
+  if (f32) HS_TRY(lowdin_rows(ctx, HS_PREC_F64, PT, k, (int)n, Lw, sub_done ? 1 : 2));
   HS_TRY(gconj(ctx, PTm, PT));
   double* PTc = PT + g_elems(PTm);
 
@@ -298,7 +350,13 @@ hs_status graded_move(hs_ctx ctx, const hs_z2_tensor* a, hs_env* env, int chi, h
   HS_CUDA(cudaStreamSynchronize(s));
   harvest_profile(ctx);
   if (*ctx->h_info != 0) return fail(HS_ERR_SOLVER, "eigensolver info %d", *ctx->h_info);
-  const SelectOut sel = *ctx->h_sel;
+  SelectOut sel = *ctx->h_sel;
+  if (sub_done) {
+    // the subspace selection ranks eigenvalues of H: singular values are their square roots
+    sel.lam_max = std::sqrt(std::fabs(sel.lam_max));
+    sel.lam_cut = std::sqrt(std::fabs(sel.lam_cut));
+    sel.lam_next = std::sqrt(std::fabs(sel.lam_next));
+  }
   env->chi_even = k;
   env->chi_odd = 0;
   env->log_norm_C = sel.log_norm_C;
@@ -319,10 +377,10 @@ hs_status graded_move(hs_ctx ctx, const hs_z2_tensor* a, hs_env* env, int chi, h
     info->log_norm_C = env->log_norm_C;
     info->log_norm_T = env->log_norm_T;
     info->gemm_flops = flops;
-    info->flags = (discarded && info->gap < 1e-9) ? 1 : 0;
-    info->subspace_iters = 0;
-    info->subspace_reason = -1;
-    info->subspace_resid = 0.0;
+    info->flags = ((discarded && info->gap < 1e-9) ? 1 : 0) | (sub_mode ? (sub_done ? 2 : 4) : 0);
+    info->subspace_iters = sub_iters;
+    info->subspace_reason = sub_reason;
+    info->subspace_resid = sub_resid;
   }
   return HS_OK;
 }

@@ -440,8 +440,14 @@ hs_status rdm_complex(hs_ctx ctx, const hs_env* env, const double* A, int d, int
   // interleaved dense environment, then planar
   HS_TRY(ctx->r[0].ensure(2 * c2 * 8));
   HS_TRY(ctx->r[1].ensure(2 * cqc * 8));
-  HS_CUDA(launch_env_to_dense_graded(env->C, env->T, D, env->chi_even, env->chi_odd, ctx->r[0].d(), ctx->r[1].d(),
-                                     s));
+  if (env->basis == HS_BASIS_DENSE) {
+    // a complex environment of the plain basis is stored dense already
+    HS_CUDA(cudaMemcpyAsync(ctx->r[0].d(), env->C, 2 * c2 * 8, cudaMemcpyDeviceToDevice, s));
+    HS_CUDA(cudaMemcpyAsync(ctx->r[1].d(), env->T, 2 * cqc * 8, cudaMemcpyDeviceToDevice, s));
+  } else {
+    HS_CUDA(launch_env_to_dense_graded(env->C, env->T, D, env->chi_even, env->chi_odd, ctx->r[0].d(), ctx->r[1].d(),
+                                       s));
+  }
   ZBuf Cz = zbuf(ctx, 0, c2), Tz = zbuf(ctx, 1, cqc), Ctz = zbuf(ctx, 2, c2), Tqz = zbuf(ctx, 3, cqc),
        H1 = zbuf(ctx, 4, cqc), Hz = zbuf(ctx, 5, cqc), Hq = zbuf(ctx, 6, cqc), L1 = zbuf(ctx, 7, c2q2),
        L2 = zbuf(ctx, 8, c2q3), L2p = zbuf(ctx, 9, c2q3);

@@ -426,7 +426,8 @@ __global__ void __launch_bounds__(NT, 1) gemm_tc_kernel(const __grid_constant__ 
           __syncwarp();
           const int* mytab = ctab + (ps_tr ? 32 : 0);
           const int nvalid = P.N - col0;
-          const bool rok = row0 + lane < P.M;
+          // rows past the problem store nothing; every store stays below the limit
+          const unsigned lim = row0 + lane < P.M ? (unsigned)D.limit : 0u;
           // join the accumulators first (frees the correction's registers)
 #pragma unroll
           for (int j = 0; j < 32; ++j) {
@@ -441,9 +442,9 @@ __global__ void __launch_bounds__(NT, 1) gemm_tc_kernel(const __grid_constant__ 
           for (int j = 0; j < 32; ++j) {
             if (j >= nvalid) break;  // warp-uniform
             uint32_t h, l;
-            split_f32_tf32x3_sel(r0[j], h, l);
+            split_f32_tf32x3_fin(r0[j], h, l);
             const int o = ((tcmask >> j) & 1u ? ps_r1 : ps_r0) + mytab[j];
-            if (rok && (unsigned)o < (unsigned)D.limit) {
+            if ((unsigned)o < lim) {
               hi[o] = h;
               lo[o] = l;
             }
@@ -490,7 +491,7 @@ __global__ void __launch_bounds__(NT, 1) gemm_tc_kernel(const __grid_constant__ 
               const int4 ri = rinfo[i];
               const int o = (tc ? ri.y : ri.x) + (ri.z ? cp1 : cp0);
               uint32_t hh, ll;
-              split_f32_tf32x3_sel(__float_as_uint(stf[i * 16 + (cl ^ ((i >> 1) & 15))]), hh, ll);
+              split_f32_tf32x3_fin(__float_as_uint(stf[i * 16 + (cl ^ ((i >> 1) & 15))]), hh, ll);
               if (cok && row0 + i < P.M && (unsigned)o < (unsigned)D.limit) {
                 hi[o] = hh;
                 lo[o] = ll;

@@ -119,7 +119,7 @@ WORKLOADS = {
     6: dict(d=2, D=3, chi=27, moves=30, complex_valued=True),
     # the largest shape of the batched workload (D=7: q=49 = 28 even + 21 odd,
     # chi = 4 D^2 = 196): its first D=7 instance (instance 1, seed SEED_BASE + 4001)
-    7: dict(d=2, D=7, chi=196, moves=10, complex_valued=False, seed=SEED_BASE + 4001),
+    7: dict(d=2, D=7, chi=196, moves=40, complex_valued=False, seed=SEED_BASE + 4001),
 }
 
 

@@ -147,6 +147,27 @@ int main() {
       }
     }
   }
+  // 2e. the epilogue's form: the same bits except where the general split
+  // rounds up to 2^128 or the input is NaN / infinity; non-finite there
+  for (uint64_t k = 0; k < (1ull << 32); k += 4093) {
+    const uint32_t uu = (uint32_t)k;
+    for (uint32_t v : {uu, uu | 0x7F800000u, uu & 0x807FFFFFu, uu | 0x7FFFF000u, uu & 0x80000000u,
+                       (uu & 0x80FFFFFFu) | 0x7E800000u}) {
+      uint32_t h2, l2, h4, l4;
+      split_f32_tf32x3(v, h2, l2);
+      split_f32_tf32x3_fin(v, h4, l4);
+      const bool top = (v & 0x7F800000u) == 0x7F800000u || ((h2 & 0x7F800000u) == 0x7F800000u);
+      if (top) {
+        if ((h4 & 0x7F800000u) != 0x7F800000u && (l4 & 0x7F800000u) != 0x7F800000u) {
+          std::printf("fin split of %08x is finite: %08x %08x\n", v, h4, l4);
+          return 1;
+        }
+      } else if (h2 != h4 || l2 != l4) {
+        std::printf("fin split of %08x: %08x %08x vs %08x %08x\n", v, h4, l4, h2, l2);
+        return 1;
+      }
+    }
+  }
   // zero, tiny, NaN
   uint32_t h, l;
   split_f64(0.0, 11, 24, true, h, l);

@@ -168,3 +168,46 @@ def test_graded_one_site_rdm_and_inverse_rotation(ctx):
     a = c.double_layer_dense().cpu().numpy()
     want = dl.double_layer(A)
     np.testing.assert_allclose(a, want, rtol=0, atol=1e-14 * np.abs(want).max())
+
+
+@pytest.mark.parametrize("precision,tol_e", [("f64", 1e-9), ("tf32x3", 1e-7)])
+def test_graded_subspace_eigensolver_full_size(ctx, precision, tol_e):
+    """Complex workload at full size (D=5, chi=100) with the warm-started subspace eigensolver on
+    H = M M^T (one block of n = 2500): energy after 40 moves against the oracle, and the solver
+    converges on most moves once a warm start exists. FP64 products: 1e-9, as for the real
+    subspace solver in FP64 (its residual tolerance, 1e-6 of the largest eigenvalue, bounds the
+    error of the kept subspace); TF32x3: the mixed-precision gate 1e-7."""
+    from paper_2410_11596_gb300.api import CTMRG
+    g = golden(5)
+    c = CTMRG(ctx, inputs.workload_tensor(5), g["chi"], precision=precision, eig="subspace")
+    infos = c.run(g["moves"])
+    e = c.energy(inputs.heisenberg_bond())
+    dE = abs(e - g["checkpoints"][str(g["moves"])]["energy"])
+    used = [bool(i["flags"] & 2) for i in infos]
+    print(f"w5 {precision}+subspace: |dE| = {dE:.2e}, subspace moves {sum(used)}/{len(used)}")
+    assert sum(used[10:]) >= 20
+    assert dE <= tol_e
+
+
+def test_dense_complex_path_matches_oracle(ctx):
+    """The comparison path: complex CTMRG in the plain basis (four FP64 GEMMs per complex product,
+    complex Hermitian FP64 eigen-decomposition), energy and rho at every checkpoint of the small
+    complex workload against the oracle (FP64 gate), and the same energy as the graded path."""
+    from paper_2410_11596_gb300.api import CTMRG
+    g = golden(6)
+    A = inputs.workload_tensor(6)
+    c = CTMRG(ctx, A, g["chi"], basis="dense")
+    cg = CTMRG(ctx, A, g["chi"])
+    h = inputs.heisenberg_bond()
+    done = 0
+    for m in sorted(int(k) for k in g["checkpoints"]):
+        c.run(m - done)
+        cg.run(m - done)
+        done = m
+        ref = g["checkpoints"][str(m)]
+        rho, t0, t1 = c.rdm2(h)
+        assert abs((t1 / t0).real - ref["energy"]) <= 1e-10, m
+        rho_ref = np.array(ref["rho_re"]) + 1j * np.array(ref["rho_im"])
+        np.testing.assert_allclose(rho.cpu().numpy() / t0, rho_ref, atol=1e-10)
+        assert abs(c.energy(h) - cg.energy(h)) <= 1e-10
+    assert (c.env.chi_even, c.env.chi_odd) == (g["chi"], 0)
