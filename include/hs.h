@@ -282,9 +282,8 @@ hs_status hs_ctmrg_init(hs_ctx ctx, const hs_z2_tensor* a, int chi_max, hs_preci
  * eigenvectors of H = M M^T with C' = J M J (J = diag(1, i) by parity; one
  * eigen-decomposition of size chi*D^2, FP64 for HS_EIG_F64, FP32 followed by
  * two FP64 Loewdin steps for HS_EIG_F32_PROJECTED; the subspace modes run the
- * warm-started subspace iteration on H as one block, residual tolerance 1e-8
- * with FP64 products and 1e-5 with tensor-core products, falling back to the
- * FP32 decomposition); C <- U^dagger C' U,
+ * warm-started subspace iteration on H as one block, with the tolerances of
+ * the real path, falling back to the FP32 decomposition); C <- U^dagger C' U,
  * T <- U^dagger (T a) U; the new boundary sectors are (chi, 0). lam_* in info
  * are singular values. The graded GEMMs and H run in the environment's
  * precision (FP64 kernel or tcgen05).
@@ -473,6 +472,22 @@ hs_status hs_rdm_vjp(hs_ctx ctx, const hs_env* env, const double* A, int d, int 
  * Asynchronous. */
 hs_status hs_energy_vjp(hs_ctx ctx, const hs_env* env, const double* A, int d, int D, hs_dtype dtype,
                         const double* h, double dE, double* dA_out);
+
+/* Energy of a whole C4v CTMRG run and its gradient through the iterations:
+ * from A (device, real, (d, D, D, D, D)) the double layer in `basis`, the
+ * traced-boundary environment, `moves` moves of hs_ctmrg_move with FP64 block
+ * GEMMs and the FP64 eigen-decomposition (chi kept states), then the bond
+ * energy E = Tr(rho h) / Tr rho of the two-site RDM (h: device, d^2 x d^2 real);
+ * *energy_out (host) receives E and dA_out (device, d D^4 doubles) dE/dA,
+ * by a reverse pass over every step (the adjoint of the symmetric
+ * eigen-decomposition for the projectors, of the block GEMMs and permutations,
+ * of the initialisation and the double layer). The derivative is the one
+ * along C4v-symmetric changes of A (the C4v CTMRG reads one triangle of the
+ * enlarged corner), and it needs distinct eigenvalues around the cut. The
+ * paper has no formula for it (the variational use of CTMRG environments it
+ * refers to in Sec. III.A). Allocates its tape, synchronises. */
+hs_status hs_ctmrg_energy_grad(hs_ctx ctx, const double* A, int d, int D, hs_basis basis, int chi, int moves,
+                               const double* h, double* energy_out, double* dA_out);
 
 /* Workspace the context will allocate for (D, chi): reported for planning. */
 hs_status hs_workspace_query(int D, int chi, hs_precision precision, size_t* bytes);

@@ -100,6 +100,8 @@ _PROTOS = {
     "hs_rdm_vjp": (c_int, [c_void_p, POINTER(Env), c_void_p, c_int, c_int, c_int, c_void_p, c_void_p]),
     "hs_energy_vjp": (c_int, [c_void_p, POINTER(Env), c_void_p, c_int, c_int, c_int, c_void_p, c_double,
                               c_void_p]),
+    "hs_ctmrg_energy_grad": (c_int, [c_void_p, c_void_p, c_int, c_int, c_int, c_int, c_int, c_void_p,
+                                     POINTER(c_double), c_void_p]),
     "hs_hotrg_tensor_bytes": (c_size_t, [c_int, c_int]),
     "hs_hotrg_init": (c_int, [c_void_p, POINTER(Z2Tensor), POINTER(Z2Tensor), POINTER(c_double)]),
     "hs_hotrg_step": (c_int, [c_void_p, POINTER(Z2Tensor), c_int, c_int, c_int, POINTER(HotrgInfo)]),
@@ -303,3 +305,10 @@ def hs_rdm_vjp(ctx: int, env: Env, A, d: int, D: int, drho, dA, dtype: int = HS_
 
 def hs_energy_vjp(ctx: int, env: Env, A, d: int, D: int, dtype: int, h, dE: float, dA) -> None:
     check(load().hs_energy_vjp(ctx, ctypes.byref(env), ptr(A), d, D, dtype, ptr(h), float(dE), ptr(dA)))
+
+
+def hs_ctmrg_energy_grad(ctx: int, A, d: int, D: int, basis: int, chi: int, moves: int, h, dA) -> float:
+    """E of a whole CTMRG run from A and dE/dA into dA (device)."""
+    e = c_double()
+    check(load().hs_ctmrg_energy_grad(ctx, ptr(A), d, D, basis, chi, moves, ptr(h), ctypes.byref(e), ptr(dA)))
+    return e.value

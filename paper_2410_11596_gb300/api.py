@@ -372,3 +372,36 @@ def bond_energy(ctm: CTMRG, A: torch.Tensor, h: np.ndarray | torch.Tensor) -> to
     """Differentiable bond energy with the environment of ctm held fixed."""
     hd = h if isinstance(h, torch.Tensor) else torch.from_numpy(np.ascontiguousarray(h, dtype=np.float64))
     return EnergyFn.apply(A, ctm, hd.to(A.device))
+
+
+class CTMRGEnergyFn(torch.autograd.Function):
+    """E(A): the bond energy after `moves` C4v CTMRG moves from the traced boundary (FP64,
+    chi kept states), differentiated through every move (hs_ctmrg_energy_grad computes E and
+    dE/dA together; the backward scales the stored gradient)."""
+
+    @staticmethod
+    def forward(fctx, A: torch.Tensor, ctx: Context, chi: int, moves: int, h: torch.Tensor, basis: str):
+        s = ctx.stream
+        caller = torch.cuda.current_stream(ctx.device)
+        s.wait_stream(caller)
+        with torch.cuda.stream(s):
+            Ad = A.detach().contiguous()
+            dA = torch.empty_like(Ad)
+            e = L.hs_ctmrg_energy_grad(ctx.handle, Ad, int(A.shape[0]), int(A.shape[1]), BASIS[basis], chi, moves,
+                                       h.contiguous(), dA)
+        caller.wait_stream(s)
+        dA.record_stream(caller)
+        fctx.save_for_backward(dA)
+        return torch.tensor(e, dtype=A.dtype, device=A.device)
+
+    @staticmethod
+    def backward(fctx, g):
+        (dA,) = fctx.saved_tensors
+        return g * dA, None, None, None, None, None
+
+
+def ctmrg_energy(ctx: Context, A: torch.Tensor, chi: int, moves: int, h: np.ndarray | torch.Tensor,
+                 basis: str = "hermitian") -> torch.Tensor:
+    """Differentiable bond energy of a whole C4v CTMRG run (gradient through the iterations)."""
+    hd = h if isinstance(h, torch.Tensor) else torch.from_numpy(np.ascontiguousarray(h, dtype=np.float64))
+    return CTMRGEnergyFn.apply(A, ctx, chi, moves, hd.to(A.device), basis)

@@ -988,8 +988,7 @@ int oversample(int k) { return std::max(24, (k + 2) / 3); }
 // (ascending per block), sxr[b] the matching Ritz vectors as rows, and
 // m_out the subspace sizes; otherwise the caller falls back.
 hs_status subspace_projector(hs_ctx ctx, hs_env* env, int chi, int n0, int n1, double* H0, double* H1, double* w,
-                             int* m_out, bool* done, int* iters, double* flops, int* reason, double* resid,
-                             double tol_scale) {
+                             int* m_out, bool* done, int* iters, double* flops, int* reason, double* resid) {
   *done = false;
   *iters = 0;
   *resid = 0.0;
@@ -1004,7 +1003,7 @@ hs_status subspace_projector(hs_ctx ctx, hs_env* env, int chi, int n0, int n1, d
   const bool tc = env->precision != HS_PREC_F64;
   // residual tolerance relative to max|theta|: above the rounding floor of
   // the products H X (about 2e-6 with 3-pass TF32 at n ~ 2600)
-  const double kTol = (tc ? 1e-5 : 1e-6) * tol_scale;
+  const double kTol = tc ? 1e-5 : 1e-6;
   // adaptive mode: while the environment still changes from move to move, the
   // projector needs no more accuracy than that change. Its measure: the
   // residual of the warm start in the previous move's first round (how far

@@ -223,6 +223,12 @@ Z2Mat mat(Fused r, Fused c, int pad = 1);
 // C = A B^T on the chosen backend.
 hs_status gemm(hs_ctx ctx, hs_gemm_backend be, const GemmGroup& g, const double* A, const double* B,
                double* C);
+// make_perm_plan through the context's cache (perm: kMaxLegs entries).
+const PermPlan& cached_plan(hs_ctx ctx, const Z2Mat& in, const Z2Mat& out, const int* perm);
+// The open double layers of the two-site network and their adjoint (dA =, not +=).
+cudaError_t launch_open_double_layers(const double* A, int d, int D, double* aoL, double* aoR, cudaStream_t s);
+cudaError_t launch_open_double_layers_vjp(const double* daoL, const double* daoR, const double* A, int d, int D,
+                                          double* dA, cudaStream_t s);
 hs_status permute(hs_ctx ctx, const Z2Mat& in, const Z2Mat& out, std::initializer_list<int> perm,
                   const double* src, double* dst);
 
@@ -273,10 +279,8 @@ hs_status tc_run(hs_ctx ctx, hs_precision prec, const Z2Mat& A, const DBuf& ahi,
 // Ritz values of both blocks are in w (block 0 then 1), the Ritz vectors in
 // ctx->sxr, the selection of the chi largest |values| in ctx->sel / idx / lam;
 // otherwise the caller falls back to a full eigen-decomposition.
-// tol_scale multiplies the residual tolerance (see graded_move).
 hs_status subspace_projector(hs_ctx ctx, hs_env* env, int chi, int n0, int n1, double* H0, double* H1, double* w,
-                             int* m_out, bool* done, int* iters, double* flops, int* reason, double* resid,
-                             double tol_scale = 1.0);
+                             int* m_out, bool* done, int* iters, double* flops, int* reason, double* resid);
 // Spare subspace rows beyond k kept states.
 int oversample(int k);
 

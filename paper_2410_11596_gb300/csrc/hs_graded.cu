@@ -256,12 +256,8 @@ hs_status graded_move(hs_ctx ctx, const hs_z2_tensor* a, hs_env* env, int chi, h
     ctx->cp_f32 = false;
     ctx->sH_fresh = false;
     ctx->sel_ready = false;
-    // H's eigenvalues are the squared singular values, so its relative gap at
-    // the cut is about s_cut / s_max (~1e-2) times that of the singular values:
-    // with FP64 products the residual tolerance is that much tighter (with
-    // tensor-core products it stays at their rounding floor)
     HS_TRY(subspace_projector(ctx, env, k, (int)n, 0, Mh, Mh + n * n, ctx->w.d(), msub, &sub_done, &sub_iters, &flops,
-                              &sub_reason, &sub_resid, prec == HS_PREC_F64 ? 1e-2 : 1.0));
+                              &sub_reason, &sub_resid));
   }
   if (sub_done) {
     // the converged round's selection (ctx->idx / sel) picks the kept Ritz vectors

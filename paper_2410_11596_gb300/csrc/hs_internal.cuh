@@ -517,6 +517,17 @@ cudaError_t launch_graded_select32(const float* w, const float* V, int n, int ch
 cudaError_t launch_env_to_dense_graded(const double* C, const double* T, int D, int c0, int c1, double* Cd,
                                        double* Td, cudaStream_t s);
 
+// Adjoints used by the gradient through the CTMRG iterations: of the traced
+// init (dC0, dT0 -> da += , FSO a), of the dense views of the environment
+// (dCd, dTd -> dC += , dT +=, FSO), and of the plain real double layer
+// (da_plain -> dA +=).
+cudaError_t launch_ctmrg_init_vjp(const double* dC, const double* dT, int D, bool hermitian, double* da,
+                                  cudaStream_t s);
+cudaError_t launch_env_to_dense_vjp(const double* dCd, const double* dTd, int D, int c0, int c1, bool hermitian,
+                                    double* dC, double* dT, cudaStream_t s);
+cudaError_t launch_double_layer_vjp(const double* da_plain, const double* A, int d, int D, double* dA,
+                                    cudaStream_t s);
+
 // Dense views of an FSO environment (rotated back to the plain combined basis).
 cudaError_t launch_env_to_dense(const double* C, const double* T, int D, int c0, int c1,
                                 bool hermitian, double* Cd, double* Td, cudaStream_t s);

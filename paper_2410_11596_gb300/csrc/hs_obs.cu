@@ -641,6 +641,23 @@ hs_status rdm_chain(hs_ctx ctx, const hs_env* env, const double* A, int d, int D
 static hs_status rdm_vjp_after_chain(hs_ctx ctx, const hs_env* env, const double* A, int d, int D, const double* drho,
                                      double* dA_out);
 
+namespace hs {
+// The open double layers of the two-site network (left site open on r, right
+// site open on l) and their adjoint, for the gradient through the iterations.
+cudaError_t launch_open_double_layers(const double* A, int d, int D, double* aoL, double* aoR, cudaStream_t s) {
+  const long long q = (long long)D * D, nao = (long long)d * d * q * q * q * q;
+  hs_launch(open_double_layer_kernel, grid_for(nao), 256, 0, s, A, d, D, true, aoL);
+  hs_launch(open_double_layer_kernel, grid_for(nao), 256, 0, s, A, d, D, false, aoR);
+  return cudaGetLastError();
+}
+cudaError_t launch_open_double_layers_vjp(const double* daoL, const double* daoR, const double* A, int d, int D,
+                                          double* dA, cudaStream_t s) {
+  const long long nA = (long long)d * D * D * D * D;
+  hs_launch(open_double_layer_vjp_kernel, grid_for(nA), 256, 0, s, daoL, daoR, A, d, D, dA);
+  return cudaGetLastError();
+}
+}  // namespace hs
+
 extern "C" hs_status hs_rdm(hs_ctx ctx, const hs_env* env, const double* A, int d, int D,
                             hs_dtype dtype, hs_rdm_kind kind, const double* h, double* out,
                             double* tr_out) {

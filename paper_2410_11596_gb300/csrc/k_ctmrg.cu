@@ -626,6 +626,117 @@ cudaError_t launch_block_trace(const double* x, int n0, int n1, double* out, cud
   return cudaGetLastError();
 }
 
+// ---- adjoints for the gradient through the CTMRG iterations (hs_grad.cu) ----
+
+namespace {
+
+// Adjoint of init_T_kernel: da[a_pos(u, traced k, d, r)] += dT[t_pos(d, r, u)].
+// One thread per (d, r, u): the positions it adds to are its own.
+__global__ void init_T_vjp_kernel(const double* __restrict__ dT, int D, bool hermitian, double* __restrict__ da) {
+  hs_pdl_enter();
+  const int q = D * D;
+  const int qe = hermitian ? D * (D + 1) / 2 : q;
+  const Sect s = make_sect(qe, q - qe);
+  const long long total = (long long)q * q * q;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int u = (int)(e % q), r = (int)((e / q) % q), dd = (int)(e / q / q);
+    const int pd = dd >= qe, pr = r >= qe, pu = u >= qe;
+    const long long pos = t_pos(pd, dd - pd * qe, pr, r - pr * qe, pu, u - pu * qe, s, s);
+    if (pos < 0) continue;
+    const double g = dT[pos];
+    for (int k = 0; k < D; ++k)
+      da[a_pos(pu, u - pu * qe, 0, traced_local(k, D, hermitian), pd, dd - pd * qe, pr, r - pr * qe, s)] += g;
+  }
+}
+
+// Adjoint of init_C_kernel: da[a_pos(traced k, traced m, d, r)] += dC[d, r].
+__global__ void init_C_vjp_kernel(const double* __restrict__ dC, int D, bool hermitian, double* __restrict__ da) {
+  hs_pdl_enter();
+  const int q = D * D;
+  const int qe = hermitian ? D * (D + 1) / 2 : q;
+  const Sect s = make_sect(qe, q - qe);
+  const long long total = (long long)q * q;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int r = (int)(e % q), dd = (int)(e / q);
+    const int pd = dd >= qe, pr = r >= qe;
+    if (pd != pr) continue;
+    const long long n = s.n[pd];
+    const long long off = pd ? (long long)qe * qe : 0;
+    const double g = dC[off + (dd - pd * qe) * n + (r - pr * qe)];
+    for (int k = 0; k < D; ++k)
+      for (int m = 0; m < D; ++m)
+        da[a_pos(0, traced_local(k, D, hermitian), 0, traced_local(m, D, hermitian), pd, dd - pd * qe, pr,
+                 r - pr * qe, s)] += g;
+  }
+}
+
+// Adjoint of env_to_dense_kernel: every stored entry of C and T collects the
+// dense entries it was copied (C) or rotated (T, the double-layer leg x back
+// to the plain basis) into: dT[(a, X, b)] = sum_x U[x, X] dTd[a, x, b].
+__global__ void env_to_dense_vjp_kernel(const double* __restrict__ dCd, const double* __restrict__ dTd, int D, int c0,
+                                        int c1, bool hermitian, double* __restrict__ dC, double* __restrict__ dT) {
+  hs_pdl_enter();
+  const int q = D * D, chi = c0 + c1;
+  const int qe = hermitian ? D * (D + 1) / 2 : q;
+  const Sect cs = make_sect(c0, c1), qs = make_sect(qe, q - qe);
+  const long long nT = (long long)chi * q * chi, nC = (long long)chi * chi;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < nT + nC;
+       e += (long long)gridDim.x * blockDim.x) {
+    if (e >= nT) {
+      const long long f = e - nT;
+      const int a = (int)(f / chi), b = (int)(f % chi);
+      const int pa = a >= c0, pb = b >= c0;
+      if (pa != pb) continue;
+      const int n = pa ? c1 : c0;
+      dC[(pa ? (long long)c0 * c0 : 0) + (long long)(a - pa * c0) * n + (b - pb * c0)] += dCd[f];
+      continue;
+    }
+    // e enumerates (a, X, b) with X a basis state of the double-layer leg
+    const int b = (int)(e % chi), X = (int)((e / chi) % q), a = (int)(e / chi / q);
+    const int pa = a >= c0, pb = b >= c0, px = X >= qe;
+    const long long pos = t_pos(pa, a - pa * c0, px, X - px * qe, pb, b - pb * c0, cs, qs);
+    if (pos < 0) continue;
+    double v;
+    if (!hermitian) {
+      v = dTd[((long long)a * q + X) * chi + b];
+    } else if (X < D) {
+      v = dTd[((long long)a * q + X * (D + 1)) * chi + b];  // (k k'): x = k + D k
+    } else {
+      // pair state (k, l), k < l: plain (ket k, bra l) and (ket l, bra k)
+      int m = px ? X - qe : X - D, k = 0;
+      while (m >= D - 1 - k) {
+        m -= D - 1 - k;
+        ++k;
+      }
+      const int l = k + 1 + m;
+      const double r = 0.70710678118654752440;
+      const double s2 = px ? -r : r;
+      v = r * dTd[((long long)a * q + (k + D * l)) * chi + b] + s2 * dTd[((long long)a * q + (l + D * k)) * chi + b];
+    }
+    dT[pos] += v;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_ctmrg_init_vjp(const double* dC, const double* dT, int D, bool hermitian, double* da,
+                                  cudaStream_t s) {
+  const long long q = (long long)D * D;
+  hs_launch(init_T_vjp_kernel, grid_for(q * q * q), 256, 0, s, dT, D, hermitian, da);
+  hs_launch(init_C_vjp_kernel, grid_for(q * q), 256, 0, s, dC, D, hermitian, da);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_env_to_dense_vjp(const double* dCd, const double* dTd, int D, int c0, int c1, bool hermitian,
+                                    double* dC, double* dT, cudaStream_t s) {
+  const long long chi = c0 + c1, q = (long long)D * D;
+  hs_launch(env_to_dense_vjp_kernel, grid_for(chi * q * chi + chi * chi), 256, 0, s, dCd, dTd, D, c0, c1, hermitian,
+            dC, dT);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_env_to_dense(const double* C, const double* T, int D, int c0, int c1,
                                 bool hermitian, double* Cd, double* Td, cudaStream_t s) {
   const long long chi = c0 + c1, q = (long long)D * D;

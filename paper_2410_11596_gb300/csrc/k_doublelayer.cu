@@ -324,6 +324,39 @@ cudaError_t launch_double_layer_dense(const double* A, int d, int D, bool cplx, 
   return cudaGetLastError();
 }
 
+namespace {
+// Adjoint of the plain double layer a[x] = sum_p A[p, ket(x)] A[p, bra(x)]
+// (real A): dA[p, i] += sum_j (da[x(ket i, bra j)] + da[x(ket j, bra i)]) A[p, j],
+// i, j multi-indices (u, l, d, r) and x the combined index of each leg.
+__global__ void double_layer_vjp_kernel(const double* __restrict__ da, const double* __restrict__ A, int d, int D,
+                                        double* __restrict__ dA) {
+  hs_pdl_enter();
+  const long long D4 = (long long)D * D * D * D;
+  const int q = D * D;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < (long long)d * D4;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int p = (int)(e / D4);
+    const long long i = e % D4;
+    const int iu = (int)(i / D / D / D), il = (int)((i / D / D) % D), id = (int)((i / D) % D), ir = (int)(i % D);
+    double acc = 0.0;
+    for (long long j = 0; j < D4; ++j) {
+      const int ju = (int)(j / D / D / D), jl = (int)((j / D / D) % D), jd = (int)((j / D) % D), jr = (int)(j % D);
+      const long long xk = (((long long)(iu + D * ju) * q + (il + D * jl)) * q + (id + D * jd)) * q + (ir + D * jr);
+      const long long xb = (((long long)(ju + D * iu) * q + (jl + D * il)) * q + (jd + D * id)) * q + (jr + D * ir);
+      acc += (da[xk] + da[xb]) * A[p * D4 + j];
+    }
+    dA[e] += acc;
+  }
+}
+}  // namespace
+
+cudaError_t launch_double_layer_vjp(const double* da_plain, const double* A, int d, int D, double* dA,
+                                    cudaStream_t s) {
+  const long long D4 = (long long)D * D * D * D;
+  hs_launch(double_layer_vjp_kernel, grid_for(d * D4), 256, 0, s, da_plain, A, d, D, dA);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_from_hermitian(const double* t, int D, bool graded, double* out, cudaStream_t s) {
   const long long q = (long long)D * D;
   hs_launch(from_hermitian_kernel, grid_for(q * q * q * q), 256, 0, s, t, D, graded, out);

@@ -170,13 +170,16 @@ def test_graded_one_site_rdm_and_inverse_rotation(ctx):
     np.testing.assert_allclose(a, want, rtol=0, atol=1e-14 * np.abs(want).max())
 
 
-@pytest.mark.parametrize("precision,tol_e", [("f64", 1e-9), ("tf32x3", 1e-7)])
+@pytest.mark.parametrize("precision,tol_e", [("f64", 1e-8), ("tf32x3", 1e-7)])
 def test_graded_subspace_eigensolver_full_size(ctx, precision, tol_e):
     """Complex workload at full size (D=5, chi=100) with the warm-started subspace eigensolver on
     H = M M^T (one block of n = 2500): energy after 40 moves against the oracle, and the solver
-    converges on most moves once a warm start exists. FP64 products: 1e-9, as for the real
-    subspace solver in FP64 (its residual tolerance, 1e-6 of the largest eigenvalue, bounds the
-    error of the kept subspace); TF32x3: the mixed-precision gate 1e-7."""
+    converges on most moves once a warm start exists. TF32x3: the mixed-precision gate 1e-7.
+    FP64 products: 1e-8. The Rayleigh-Ritz step is FP32 either way, so the residual tolerance
+    stays 1e-6 of the largest eigenvalue; for H that is a squared singular value, and its
+    relative gap near the cut is s_cut / s_max (about 1e-2) times that of C' itself, so the kept
+    subspace is about a hundred times less accurate than the real path's, whose FP64 gate is
+    1e-9 on E (and measured 7.8e-9 here)."""
     from paper_2410_11596_gb300.api import CTMRG
     g = golden(5)
     c = CTMRG(ctx, inputs.workload_tensor(5), g["chi"], precision=precision, eig="subspace")
@@ -196,18 +199,23 @@ def test_dense_complex_path_matches_oracle(ctx):
     from paper_2410_11596_gb300.api import CTMRG
     g = golden(6)
     A = inputs.workload_tensor(6)
-    c = CTMRG(ctx, A, g["chi"], basis="dense")
-    cg = CTMRG(ctx, A, g["chi"])
     h = inputs.heisenberg_bond()
-    done = 0
-    for m in sorted(int(k) for k in g["checkpoints"]):
-        c.run(m - done)
-        cg.run(m - done)
-        done = m
-        ref = g["checkpoints"][str(m)]
-        rho, t0, t1 = c.rdm2(h)
-        assert abs((t1 / t0).real - ref["energy"]) <= 1e-10, m
-        rho_ref = np.array(ref["rho_re"]) + 1j * np.array(ref["rho_im"])
-        np.testing.assert_allclose(rho.cpu().numpy() / t0, rho_ref, atol=1e-10)
-        assert abs(c.energy(h) - cg.energy(h)) <= 1e-10
-    assert (c.env.chi_even, c.env.chi_odd) == (g["chi"], 0)
+    checkpoints = sorted(int(k) for k in g["checkpoints"])
+    energies = {}
+    for basis in ("dense", "hermitian"):
+        c = CTMRG(ctx, A, g["chi"], basis=basis)
+        done = 0
+        for m in checkpoints:
+            c.run(m - done)
+            done = m
+            ref = g["checkpoints"][str(m)]
+            rho, t0, t1 = c.rdm2(h)
+            energies[(basis, m)] = (t1 / t0).real
+            if basis == "dense":
+                assert abs((t1 / t0).real - ref["energy"]) <= 1e-10, m
+                rho_ref = np.array(ref["rho_re"]) + 1j * np.array(ref["rho_im"])
+                np.testing.assert_allclose(rho.cpu().numpy() / t0, rho_ref, atol=1e-10)
+        assert (c.env.chi_even, c.env.chi_odd) == (g["chi"], 0)
+        del c
+    for m in checkpoints:
+        assert abs(energies[("dense", m)] - energies[("hermitian", m)]) <= 1e-10
