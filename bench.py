@@ -390,19 +390,6 @@ def run_ours(args):
     transient = ntr / (np.sum(ms[:ntr]) / 1e3)
     conv_timed = sum(1 for i in c.infos[args.warmup:] if i.get("flags", 0) & 2)
 
-    # the same W + K moves again (deterministic: the same kernels on the same
-    # data), now with events around each block GEMM launch: the roofline
-    # kernel's device time and flops over the timed moves
-    cr = CTMRG(ctx, A, chi, basis="hermitian", precision=args.precision, backend="own", eig=args.eig)
-    cr.run(args.warmup)
-    L.hs_profile_enable(ctx.handle, True)
-    L.hs_profile_phases(ctx.handle, ("gemm", "gemm_tc"))
-    ms_r = timed_moves(torch, cr, ctx, args.steps, flush)
-    prof_r = L.hs_profile_read(ctx.handle)
-    L.hs_profile_enable(ctx.handle, False)
-    L.hs_profile_phases(ctx.handle, None)
-    del cr
-
     # |dE| against the oracle after 50 moves, then the steady state (ten moves
     # after move 50, every warm start in place) and its phase split
     dE = None
@@ -428,6 +415,20 @@ def run_ours(args):
                   "phase_ms": {k: r3(v / nst) for k, v in ps["phase_ms"].items() if v > 0},
                   "phase_moves_ms": r3(float(np.mean(msp)))}
     del c
+
+    # the same W + K moves again (deterministic: the same kernels on the same
+    # data), now with events around each block GEMM launch: the roofline
+    # kernel's device time and flops over the timed moves
+    cr = CTMRG(ctx, A, chi, basis="hermitian", precision=args.precision, backend="own", eig=args.eig)
+    cr.run(args.warmup)
+    L.hs_profile_enable(ctx.handle, True)
+    L.hs_profile_phases(ctx.handle, ("gemm", "gemm_tc"))
+    ms_r = timed_moves(torch, cr, ctx, args.steps, flush)
+    prof_r = L.hs_profile_read(ctx.handle)
+    L.hs_profile_enable(ctx.handle, False)
+    L.hs_profile_phases(ctx.handle, None)
+    del cr
+
 
     # ---- {Z2, dense} x {FP64+syevd, TF32x3+syevd, TF32x3+subspace} ----
     table = None

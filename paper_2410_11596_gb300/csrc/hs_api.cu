@@ -997,7 +997,13 @@ hs_status subspace_projector(hs_ctx ctx, hs_env* env, int chi, int n0, int n1, d
   *reason = 1;
   if (!(ctx->ws_valid && ctx->ws_env == env)) return HS_OK;
   *reason = 2;
-  if (!(ctx->ws_n[0] == n0 && ctx->ws_n[1] == n1)) return HS_OK;
+  // sector sizes changed since the stored rows: carry them over to the new
+  // boundary sectors (the states both boundaries have), then orthonormalise
+  const Sect c_now = make_sect(env->chi_even, env->chi_odd), q_now = make_sect(env->q_even, env->q_odd);
+  const bool remap = !(ctx->ws_n[0] == n0 && ctx->ws_n[1] == n1);
+  if (remap && (ctx->ws_c[0] < 0 || n0 != c_now.n[0] * q_now.n[0] + c_now.n[1] * q_now.n[1] ||
+                n1 != c_now.n[0] * q_now.n[1] + c_now.n[1] * q_now.n[0]))
+    return HS_OK;
   constexpr int kMinOver = 8, kMaxIt = 5;
   cudaStream_t s = ctx->stream;
   const bool tc = env->precision != HS_PREC_F64;
@@ -1041,7 +1047,18 @@ hs_status subspace_projector(hs_ctx ctx, hs_env* env, int chi, int n0, int n1, d
   const long long wsoff[2] = {0, (long long)ctx->ws_m[0] * ctx->ws_n[0]};
   const int kb[2] = {std::min(ctx->ws_m[0], m[0]), std::min(ctx->ws_m[1], m[1])};
   bool all_warm = true;
-  if (kb[0] == m[0] && kb[1] == m[1] && ctx->ws_m[0] == m[0]) {
+  if (remap) {
+    const Sect c_old = make_sect(ctx->ws_c[0], ctx->ws_c[1]);
+    for (int b = 0; b < 2; ++b) {
+      if (m[b] == 0) continue;
+      if (kb[b] > 0)
+        HS_CUDA(launch_remap_rows(ctx->ws_pt.d() + wsoff[b], kb[b], ctx->ws_n[b], ctx->sx.d(b), n[b], b, c_old, c_now,
+                                  q_now, 0x7e3a0000ull + 2 * (unsigned long long)env->moves + b, s));
+      HS_CUDA(launch_fill_random_rows(ctx->sx.d(b), kb[b], m[b], n[b],
+                                      0x5eed0000ull + 2 * (unsigned long long)env->moves + b, s));
+    }
+    all_warm = false;
+  } else if (kb[0] == m[0] && kb[1] == m[1] && ctx->ws_m[0] == m[0]) {
     HS_CUDA(cudaMemcpyAsync(ctx->sx.d(0), ctx->ws_pt.d(), (size_t)(mn0 + mn1) * sizeof(double),
                             cudaMemcpyDeviceToDevice, s));
   } else {
@@ -1051,7 +1068,7 @@ hs_status subspace_projector(hs_ctx ctx, hs_env* env, int chi, int n0, int n1, d
         HS_CUDA(cudaMemcpyAsync(ctx->sx.d(b), ctx->ws_pt.d() + wsoff[b], (size_t)kb[b] * n[b] * sizeof(double),
                                 cudaMemcpyDeviceToDevice, s));
       HS_CUDA(launch_fill_random_rows(ctx->sx.d(b), kb[b], m[b], n[b],
-                                      0x5eed0000ull + 2 * (unsigned long long)ctx->ws_moves + b, s));
+                                      0x5eed0000ull + 2 * (unsigned long long)env->moves + b, s));
       if (kb[b] < m[b]) all_warm = false;
     }
   }
@@ -1760,6 +1777,8 @@ hs_status hs_ctmrg_move(hs_ctx ctx, const hs_z2_tensor* a, hs_env* env, int chi,
     }
     ctx->ws_env = env;
     ctx->ws_valid = sub_done || f32eig;
+    ctx->ws_c[0] = c.n[0];
+    ctx->ws_c[1] = c.n[1];
     ctx->ws_k[0] = cn.n[0];
     ctx->ws_k[1] = cn.n[1];
     ctx->ws_m[0] = mnext[0];

@@ -175,6 +175,7 @@ struct hs_ctx_s {
   const void* ws_env = nullptr;
   bool ws_valid = false;
   int ws_k[2] = {0, 0}, ws_n[2] = {0, 0}, ws_m[2] = {0, 0};  // kept counts, block sizes, stored rows
+  int ws_c[2] = {-1, -1};  // boundary sectors of the C' the stored rows belong to (-1: not remappable)
   long long ws_moves = 0;
   bool sH_fresh = false;  // sH_hi/lo hold the split blocks of this move's C'
   bool sel_ready = false; // this move's selection is done and its host copy read back

@@ -304,6 +304,7 @@ hs_status graded_move(hs_ctx ctx, const hs_z2_tensor* a, hs_env* env, int chi, h
                               mnext, static_cast<int*>(ctx->sf_idx.p), ctx->ws_pt.d(), s));
     ctx->ws_env = env;
     ctx->ws_valid = true;
+    ctx->ws_c[0] = ctx->ws_c[1] = -1;  // graded rows are not remapped
     ctx->ws_k[0] = k;
     ctx->ws_k[1] = 0;
     ctx->ws_m[0] = mnext;

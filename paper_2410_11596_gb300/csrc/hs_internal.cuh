@@ -464,6 +464,12 @@ cudaError_t launch_residual_pair(const double* Zr, const double* Xr, const float
 cudaError_t launch_gather_rows(const double* X0, int n0, const double* X1, int n1, const int* idx, int chi,
                                const SelectOut* sel, double* PT, double* P, cudaStream_t s);
 int max_subspace();
+// Warm-start rows of parity block b of C' moved from boundary sectors c_old to
+// c_new (same double-layer sectors q): entries of states both boundaries have
+// are kept, the others zero; then seeded noise of about 1% of an entry of a
+// unit row, so that no row is left (nearly) zero.
+cudaError_t launch_remap_rows(const double* src, int rows, int old_n, double* dst, int new_n, int b, Sect c_old,
+                              Sect c_new, Sect q, unsigned long long seed, cudaStream_t s);
 // Largest m of launch_chol_inv (one CTA, shared memory).
 int max_chol();
 // After a library Cholesky + triangular inverse: zero the strictly upper part of

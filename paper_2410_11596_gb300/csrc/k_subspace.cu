@@ -686,6 +686,57 @@ cudaError_t launch_gather_rows(const double* X0, int n0, const double* X1, int n
   return cudaGetLastError();
 }
 
+namespace {
+// Rows of a parity block of C' over [(alpha, x)] (FSO order of fused2(c, q),
+// parity b) carried from boundary sectors c_old to c_new: entry (alpha, x) of
+// sector tuple (p_alpha, p_x) keeps its value when alpha < c_old[p_alpha] (the
+// kept states of a sector are in pick order, largest |eigenvalue| first, so
+// the first ones correspond), and is zero for a state the old boundary did not
+// have.
+__global__ void remap_rows_kernel(const double* __restrict__ src, int rows, int old_n, double* __restrict__ dst,
+                                  int new_n, int b, Sect c_old, Sect c_new, Sect q) {
+  hs_pdl_enter();
+  const Fused fo = fused2(c_old, q), fn = fused2(c_new, q);
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < (long long)rows * new_n;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int r = (int)(e / new_n), j = (int)(e % new_n);
+    double v = 0.0;
+    for (int t = 0; t < 4; ++t) {
+      if (tuple_parity(t) != b) continue;
+      const long long off = tuple_offset(fn, t), size = tuple_size(fn, t);
+      if (j < off || j >= off + size) continue;
+      const int pa = tuple_bit(t, 2, 0), px = tuple_bit(t, 2, 1);
+      const int al = (int)((j - off) / q.n[px]), xl = (int)((j - off) % q.n[px]);
+      if (al < c_old.n[pa]) v = src[(long long)r * old_n + tuple_offset(fo, t) + (long long)al * q.n[px] + xl];
+    }
+    dst[e] = v;
+  }
+}
+}  // namespace
+
+namespace {
+// X (rows x n) += amp * seeded uniform noise in (-1, 1)
+__global__ void perturb_rows_kernel(double* __restrict__ X, int rows, int n, double amp, unsigned long long seed) {
+  hs_pdl_enter();
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < (long long)rows * n;
+       e += (long long)gridDim.x * blockDim.x)
+    X[e] += amp * hash_uniform(seed * 0x100000001B3ull + (unsigned long long)e);
+}
+}  // namespace
+
+cudaError_t launch_remap_rows(const double* src, int rows, int old_n, double* dst, int new_n, int b, Sect c_old,
+                              Sect c_new, Sect q, unsigned long long seed, cudaStream_t s) {
+  if (rows <= 0 || new_n <= 0) return cudaSuccess;
+  hs_launch(remap_rows_kernel, grid_for((long long)rows * new_n), 256, 0, s, src, rows, old_n, dst, new_n, b, c_old,
+            c_new, q);
+  // a row that lived mostly on states the new boundary lacks is left nearly
+  // zero: a little noise (about 1% of an entry of a unit row) keeps the rows
+  // independent for the Cholesky-QR that follows
+  hs_launch(perturb_rows_kernel, grid_for((long long)rows * new_n), 256, 0, s, dst, rows, new_n,
+            0.01 / sqrt((double)new_n), seed);
+  return cudaGetLastError();
+}
+
 int max_subspace() { return kMaxSub; }
 int max_chol() { return kMaxChol; }
 
