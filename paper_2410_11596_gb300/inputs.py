@@ -90,6 +90,26 @@ def ising_ipeps(beta: float) -> np.ndarray:
     return np.einsum("pu,pl,pd,pr->puldr", M, M, M, M)
 
 
+def anisotropic_ising_ipeps(beta_x: float, beta_y: float) -> np.ndarray:
+    """As ising_ipeps, with coupling beta_x on the horizontal legs (l, r) and beta_y on the
+    vertical legs (u, d): the norm network is the anisotropic 2D Ising partition function."""
+    def root(beta):
+        g = np.array([[np.exp(beta / 2), np.exp(-beta / 2)],
+                      [np.exp(-beta / 2), np.exp(beta / 2)]])
+        w, v = np.linalg.eigh(g)
+        return (v * np.sqrt(w)) @ v.T
+    Mx, My = root(beta_x), root(beta_y)
+    return np.einsum("pu,pl,pd,pr->puldr", My, Mx, My, Mx)
+
+
+def asymmetric_ipeps(d: int, D: int, seed: int) -> np.ndarray:
+    """Seeded random real iPEPS tensor with no lattice symmetry: N(0, 1) entries from
+    ``default_rng(seed)`` (not averaged over D4), scaled to max|A| = 1. Input of the
+    directional CTMRG, which assumes no C4v symmetry."""
+    A = np.random.default_rng(seed).standard_normal((d, D, D, D, D))
+    return np.ascontiguousarray(A / np.abs(A).max())
+
+
 def heisenberg_bond() -> np.ndarray:
     """Two-site h = S^x S^x + S^y S^y + S^z S^z (S = sigma/2, J = 1) as a real 4x4.
 
