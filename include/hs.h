@@ -46,7 +46,7 @@
 extern "C" {
 #endif
 
-#define HS_ABI_VERSION 3
+#define HS_ABI_VERSION 4
 
 typedef enum {
   HS_OK = 0,
@@ -315,6 +315,73 @@ hs_status hs_ctmrg_move_batched(hs_ctx* ctxs, int n, const hs_z2_tensor* const* 
  * sector first) and the double-layer leg rotated back to the plain combined
  * basis. Asynchronous. */
 hs_status hs_env_to_dense(hs_ctx ctx, const hs_env* env, double* C_dense, double* T_dense);
+
+/* ---- Directional CTMRG: four corners, four edges, no lattice symmetry -----
+ *
+ * Sec. II.A runs CTMRG with C4v symmetry "for simplicity". Without it the
+ * environment of a one-site unit cell has four corners and four edges, and a
+ * directional move grows one side by a column of double-layer tensors and
+ * truncates its bonds back with oblique projectors from the SVD of the two
+ * quarters (enlarged corners) on that side: X = Q1^T Q4^T = U S V^T, keep the
+ * chi largest singular values (and only those above 1e-12 s_max),
+ * P_a = Q4^T V S^-1/2 above each truncated bond, P_b = Q1 U S^-1/2 below it.
+ * In the Hermitian basis every tensor is Z2 block-sparse (Sec. II.B) and the
+ * SVD splits into one per parity block; the kept states are the chi largest
+ * over both blocks. FP64 GEMMs and FP64 SVD (one-sided Jacobi). Real double
+ * layers only (HS_F64).
+ *
+ * Bonds: 0 top, 1 right, 2 bottom, 3 left side of the boundary. Corner k
+ * (C1 upper left, C2 upper right, C3 lower right, C4 lower left) joins bond
+ * k-1 (mod 4, its incoming leg) to bond k (outgoing); edge k (T1 top, T2 right,
+ * T3 bottom, T4 left) has both ends on bond k and its bulk leg on the
+ * double-layer leg facing it (up, right, down, left). Legs run clockwise
+ * around the lattice: T1[alpha, x, beta] left to right, T2 top to bottom, T3
+ * right to left, T4 bottom to top. Storage: C[k] is the Z2 matrix
+ * [in | out], T[k] the Z2 matrix [(alpha, x) | beta], both in FSO block
+ * order (hs_z2_tensor). */
+typedef struct {
+  int D, chi_max;
+  int chi_even[4], chi_odd[4]; /* sectors of the four boundary bonds (host copy) */
+  int q_even, q_odd;           /* sectors of the double-layer legs */
+  hs_basis basis;
+  int moves;                   /* directional moves since hs_ctmrg4_init (a sweep is four) */
+  double* C[4];                /* device, caller-owned; C_bytes each */
+  double* T[4];                /* device, caller-owned; T_bytes each */
+  size_t C_bytes, T_bytes;     /* at least hs_env_bytes(D, chi_max) */
+  double log_norm_C[4], log_norm_T[4]; /* logs of the last normalisation factors */
+} hs_env4;
+
+typedef struct {
+  int direction;          /* side moved: 0 left, 1 top, 2 right, 3 bottom */
+  int chi_even, chi_odd;  /* sectors kept on the moved side's bond */
+  int m_even, m_odd;      /* rows of the two SVD blocks (the side's first neighbour bond x bulk leg) */
+  int n_even, n_odd;      /* columns (the side's other neighbour bond x bulk leg) */
+  double s_max, s_cut, s_next; /* largest, smallest kept and largest discarded singular value */
+  double gap;             /* (s_cut - s_next) / s_max, +inf if nothing discarded */
+  double gemm_flops;      /* sum over block GEMMs of 2 M N K in this move */
+} hs_move4_info;
+
+/* Traced-boundary initialisation of all eight tensors from the double layer a
+ * (HS_F64, either basis; every bond starts at the double-layer leg's sectors),
+ * each divided by its largest modulus. Caches the four rotated copies of a in
+ * the context; a must not change until the next hs_ctmrg4_init. */
+hs_status hs_ctmrg4_init(hs_ctx ctx, const hs_z2_tensor* a, int chi_max, hs_env4* env);
+
+/* One directional move of side `direction` (0 left, 1 top, 2 right, 3 bottom;
+ * a sweep is 0, 1, 2, 3): updates the side's two corners and its edge, with
+ * chi (<= env->chi_max) states kept on its bond. sv_out (host, may be NULL,
+ * at least chi entries) receives the kept singular values divided by the
+ * largest, descending. Synchronises the stream once (the kept sector sizes
+ * fix the shapes that follow). HS_ERR_SOLVER if the SVD does not converge,
+ * HS_ERR_NONFINITE if a normalisation factor is not finite. */
+hs_status hs_ctmrg4_move(hs_ctx ctx, const hs_z2_tensor* a, hs_env4* env, int chi, int direction,
+                         hs_move4_info* info, double* sv_out);
+
+/* Dense copies of the eight tensors (device, caller-owned, FP64): C_dense[k]
+ * [in bond, out bond] and T_dense[k] [bond, D^2, bond], boundary legs ordered
+ * as stored (even sector first), the bulk leg rotated back to the plain
+ * combined basis. Asynchronous. */
+hs_status hs_env4_to_dense(hs_ctx ctx, const hs_env4* env, double* const* C_dense, double* const* T_dense);
 
 /* ---- HOTRG (Sec. II.A, Ref. xie12) ------------------------------------ */
 

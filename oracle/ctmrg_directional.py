@@ -198,8 +198,12 @@ def run(a: np.ndarray, chi: int, sweeps: int) -> Result:
 def one_site_environment(E: list) -> np.ndarray:
     """eps[u, l, d, r]: the boundary ring around one site, Fig. 1(d) with the centre removed."""
     C1, T1, C2, T2, C3, T3, C4, T4 = E
-    return np.einsum("ab,buc,ce,erf,fg,gdh,hi,ila->uldr", C1, T1, C2, T2, C3, T3, C4, T4,
-                     optimize=True)
+    top = np.tensordot(np.tensordot(C1, T1, axes=([1], [0])), C2, axes=([2], [0]))   # [a, u, e]
+    top = np.tensordot(top, T2, axes=([2], [0]))                                    # [a, u, r, f]
+    bot = np.tensordot(np.tensordot(C3, T3, axes=([1], [0])), C4, axes=([2], [0]))   # [f, d, i]
+    ring = np.tensordot(top, bot, axes=([3], [0]))                                  # [a, u, r, d, i]
+    eps = np.tensordot(ring, T4, axes=([4, 0], [0, 2]))                             # [u, r, d, l]
+    return np.ascontiguousarray(eps.transpose(0, 3, 2, 1))
 
 
 def one_site_rdm(E: list, A: np.ndarray) -> np.ndarray:

@@ -68,6 +68,22 @@ class MoveInfo(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class Env4(ctypes.Structure):
+    _fields_ = [("D", c_int), ("chi_max", c_int), ("chi_even", c_int * 4), ("chi_odd", c_int * 4),
+                ("q_even", c_int), ("q_odd", c_int), ("basis", c_int), ("moves", c_int),
+                ("C", c_void_p * 4), ("T", c_void_p * 4), ("C_bytes", c_size_t), ("T_bytes", c_size_t),
+                ("log_norm_C", c_double * 4), ("log_norm_T", c_double * 4)]
+
+
+class Move4Info(ctypes.Structure):
+    _fields_ = [("direction", c_int), ("chi_even", c_int), ("chi_odd", c_int), ("m_even", c_int),
+                ("m_odd", c_int), ("n_even", c_int), ("n_odd", c_int), ("s_max", c_double), ("s_cut", c_double),
+                ("s_next", c_double), ("gap", c_double), ("gemm_flops", c_double)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 _PROTOS = {
     "hs_create": (c_int, [POINTER(c_void_p), c_int, c_void_p]),
     "hs_destroy": (c_int, [c_void_p]),
@@ -102,6 +118,10 @@ _PROTOS = {
                               c_void_p]),
     "hs_ctmrg_energy_grad": (c_int, [c_void_p, c_void_p, c_int, c_int, c_int, c_int, c_int, c_void_p,
                                      POINTER(c_double), c_void_p]),
+    "hs_ctmrg4_init": (c_int, [c_void_p, POINTER(Z2Tensor), c_int, POINTER(Env4)]),
+    "hs_ctmrg4_move": (c_int, [c_void_p, POINTER(Z2Tensor), POINTER(Env4), c_int, c_int, POINTER(Move4Info),
+                               POINTER(c_double)]),
+    "hs_env4_to_dense": (c_int, [c_void_p, POINTER(Env4), POINTER(c_void_p), POINTER(c_void_p)]),
     "hs_hotrg_tensor_bytes": (c_size_t, [c_int, c_int]),
     "hs_hotrg_init": (c_int, [c_void_p, POINTER(Z2Tensor), POINTER(Z2Tensor), POINTER(c_double)]),
     "hs_hotrg_step": (c_int, [c_void_p, POINTER(Z2Tensor), c_int, c_int, c_int, POINTER(HotrgInfo)]),
@@ -227,6 +247,27 @@ def hs_correlation_length(ctx: int, env: Env, A, d: int, D: int, max_iter: int =
 
 def hs_env_to_dense(ctx: int, env: Env, C_dense, T_dense) -> None:
     check(load().hs_env_to_dense(ctx, ctypes.byref(env), ptr(C_dense), ptr(T_dense)))
+
+
+def hs_ctmrg4_init(ctx: int, a: Z2Tensor, chi_max: int, C_bufs, T_bufs) -> Env4:
+    env = Env4(C=(c_void_p * 4)(*[ptr(b) for b in C_bufs]), T=(c_void_p * 4)(*[ptr(b) for b in T_bufs]),
+               C_bytes=min(b.numel() for b in C_bufs) * 8, T_bytes=min(b.numel() for b in T_bufs) * 8)
+    check(load().hs_ctmrg4_init(ctx, ctypes.byref(a), chi_max, ctypes.byref(env)))
+    return env
+
+
+def hs_ctmrg4_move(ctx: int, a: Z2Tensor, env: Env4, chi: int, direction: int) -> tuple[dict, list]:
+    """One directional move; returns (move record, kept singular values / largest)."""
+    info = Move4Info()
+    sv = (c_double * chi)()
+    check(load().hs_ctmrg4_move(ctx, ctypes.byref(a), ctypes.byref(env), chi, direction, ctypes.byref(info), sv))
+    d = info.as_dict()
+    return d, [sv[i] for i in range(d["chi_even"] + d["chi_odd"])]
+
+
+def hs_env4_to_dense(ctx: int, env: Env4, C_dense, T_dense) -> None:
+    check(load().hs_env4_to_dense(ctx, ctypes.byref(env), (c_void_p * 4)(*[ptr(x) for x in C_dense]),
+                                  (c_void_p * 4)(*[ptr(x) for x in T_dense])))
 
 
 def hs_corner_spectrum(ctx: int, env: Env, out) -> None:

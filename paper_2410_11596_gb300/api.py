@@ -270,6 +270,60 @@ class CTMRG:
         return eps
 
 
+class DirectionalCTMRG:
+    """CTMRG without lattice symmetry (four corners, four edges) of one real iPEPS tensor on one
+    GPU through the C ABI: a sweep moves the left, top, right and bottom sides in turn."""
+
+    def __init__(self, ctx: Context, A: np.ndarray | torch.Tensor, chi: int, basis: str = "hermitian"):
+        self.ctx = ctx
+        self._init(A, chi, basis)
+
+    @on_ctx_stream
+    def _init(self, A, chi, basis):
+        ctx = self.ctx
+        dev = f"cuda:{ctx.device}"
+        self.A = A if isinstance(A, torch.Tensor) else to_device(A, ctx.device)
+        self.d, self.D = int(self.A.shape[0]), int(self.A.shape[1])
+        self.chi = chi
+        nbytes = L.hs_z2_tensor_bytes(self.D, BASIS[basis], L.HS_F64)
+        self.a_buf = torch.empty(nbytes // 8, dtype=torch.float64, device=dev)
+        self.a = L.hs_double_layer_hermitian(ctx.handle, self.A, self.d, self.D, L.HS_F64, BASIS[basis], self.a_buf)
+        cb, tb = L.hs_env_bytes(self.D, chi)
+        self.C_bufs = [torch.empty(cb // 8, dtype=torch.float64, device=dev) for _ in range(4)]
+        self.T_bufs = [torch.empty(tb // 8, dtype=torch.float64, device=dev) for _ in range(4)]
+        self.env = L.hs_ctmrg4_init(ctx.handle, self.a, chi, self.C_bufs, self.T_bufs)
+        self.infos: list[dict] = []
+        self.spectra: list[list] = []
+
+    @on_ctx_stream
+    def move(self, direction: int) -> dict:
+        info, sv = L.hs_ctmrg4_move(self.ctx.handle, self.a, self.env, self.chi, direction)
+        self.infos.append(info)
+        self.spectra.append(sv)
+        return info
+
+    def sweep(self) -> list[dict]:
+        return [self.move(k) for k in range(4)]
+
+    def run(self, sweeps: int) -> list[dict]:
+        for _ in range(sweeps):
+            self.sweep()
+        return self.infos
+
+    def bond(self, b: int) -> int:
+        return self.env.chi_even[b] + self.env.chi_odd[b]
+
+    @on_ctx_stream
+    def dense_env(self) -> list[torch.Tensor]:
+        """[C1, T1, C2, T2, C3, T3, C4, T4] as dense FP64 device tensors in the plain basis."""
+        q = self.D * self.D
+        dev = self.A.device
+        C = [torch.empty(self.bond((k + 3) % 4), self.bond(k), dtype=torch.float64, device=dev) for k in range(4)]
+        T = [torch.empty(self.bond(k), q, self.bond(k), dtype=torch.float64, device=dev) for k in range(4)]
+        L.hs_env4_to_dense(self.ctx.handle, self.env, C, T)
+        return [x for k in range(4) for x in (C[k], T[k])]
+
+
 class HOTRG:
     """HOTRG of one real iPEPS double layer on one GPU through the C ABI."""
 

@@ -1324,6 +1324,9 @@ hs_status hs_destroy(hs_ctx ctx) {
   for (DBuf& b : ctx->gb) b.release();
   for (DBuf& b : ctx->zr) b.release();
   for (DBuf& b : ctx->zd) b.release();
+  for (DBuf& b : ctx->d4) b.release();
+  ctx->d4_h.release();
+  if (ctx->gesvdj) cusolverDnDestroyGesvdjInfo(ctx->gesvdj);
   ctx->ga.release();
   ctx->ps_hi.release();
   ctx->ps_lo.release();

@@ -168,6 +168,12 @@ struct hs_ctx_s {
   hs::DBuf zr[40];
   // complex CTMRG in the plain basis (hs_zdense.cu)
   hs::DBuf zd[40];
+  // directional CTMRG (hs_ctmrg4.cu): the rotated double layers in their two
+  // operand layouts, move scratch, SVD workspace and its host staging
+  hs::DBuf d4[40];
+  hs::PinnedBuf d4_h;
+  const double* d4_src = nullptr;
+  gesvdjInfo_t gesvdj = nullptr;
   // split-K partial sums of the FP64 GEMM
   hs::DBuf splitk;
   // subspace eigensolver: warm start (previous kept rows, per block) and

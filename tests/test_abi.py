@@ -28,7 +28,7 @@ def test_binding_covers_header():
 
 
 def test_abi_version(lib):
-    assert lib.hs_abi_version() == 3
+    assert lib.hs_abi_version() == 4
 
 
 @pytest.mark.parametrize("D", [1, 2, 3, 4, 5, 6, 7])
