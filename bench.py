@@ -71,6 +71,7 @@ def parse():
     p.add_argument("--no-dtypes", action="store_true", help="skip the per-dtype |dE| / rho errors (50 moves each)")
     p.add_argument("--no-batched", action="store_true", help="skip the batched workload (32 instances)")
     p.add_argument("--no-hotrg", action="store_true", help="skip the HOTRG line")
+    p.add_argument("--no-directional", action="store_true", help="skip the directional (non-C4v) CTMRG line")
     p.add_argument("--profile-region", action="store_true",
                    help="profiling runs only: W warm-up moves, then K moves inside cudaProfilerStart/Stop "
                         "(for ncu --profile-from-start off); prints a short JSON line, no bench line")
@@ -337,6 +338,38 @@ def hotrg_line(torch, ctx):
     return {"unit": "steps/s", "rows": out}
 
 
+def directional_line(torch, ctx):
+    """Directional CTMRG (four corners and edges, no lattice symmetry) on seeded asymmetric
+    tensors: directional moves/s in the Z2 and the plain basis (FP64 GEMMs and FP64 Jacobi SVD in
+    both), after two warm-up sweeps, and the odd fraction of the kept states."""
+    from paper_2410_11596_gb300 import inputs
+    from paper_2410_11596_gb300.api import DirectionalCTMRG
+    rows = []
+    for D, chi in ((3, 36), (4, 64), (5, 100)):
+        A = inputs.asymmetric_ipeps(2, D, inputs.SEED_BASE + 5200 + D)
+        row = {"D": D, "chi": chi}
+        for svd in (("jacobi", "polar") if D < 5 else ("polar",)):   # the Jacobi SVD takes ~9 s per dense move at D=5
+            for basis in ("hermitian", "dense"):
+                c = DirectionalCTMRG(ctx, A, chi, basis=basis, svd=svd)
+                c.run(2)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                infos = c.run(1)[-4:]
+                torch.cuda.synchronize()
+                key = ("z2" if basis == "hermitian" else "dense") + "_" + svd
+                row[f"{key}_moves_per_s"] = r3(4 / (time.perf_counter() - t0))
+                if svd == "jacobi":
+                    row[f"{key.split('_')[0]}_gflop_per_move"] = r3(sum(i["gemm_flops"] for i in infos) / 4 / 1e9)
+                if basis == "hermitian" and svd == "jacobi":
+                    row["odd_fraction"] = r3(float(np.mean([i["chi_odd"] / (i["chi_even"] + i["chi_odd"])
+                                                            for i in infos])))
+                del c
+            row[f"speedup_{svd}"] = r3(row[f"z2_{svd}_moves_per_s"] / row[f"dense_{svd}_moves_per_s"])
+        rows.append(row)
+    return {"unit": "directional moves/s (one side each), moves 9-12",
+            "arith": "f64 GEMM + f64 SVD (jacobi: gesvdj; polar: Xgesvdp)", "rows": rows}
+
+
 def run_ours(args):
     import torch
     from paper_2410_11596_gb300 import _lib as L, build, inputs
@@ -525,6 +558,9 @@ def run_ours(args):
     hotrg = None
     if not args.no_hotrg and rank == 0:
         hotrg = hotrg_line(torch, ctx)
+    directional = None
+    if not args.no_directional and rank == 0:
+        directional = directional_line(torch, ctx)
 
     # ---- end to end through the public API: host A -> device, double layer, move, corner -> host ----
     A_host = torch.from_numpy(np.ascontiguousarray(A)).pin_memory()
@@ -594,7 +630,7 @@ def run_ours(args):
                                        "D4-symmetrised, max|A|=1", "basis": "hermitian", "eig": EIG_LABEL[args.eig],
                            "l2": "flushed (512 MB write) between timed moves", "parallelism": f"replicas{world}",
                            "moves_timed": f"{args.warmup + 1}-{args.warmup + args.steps}"},
-                "table": table, "hotrg": hotrg, "complex": cplx, "batched": batched,
+                "table": table, "hotrg": hotrg, "directional": directional, "complex": cplx, "batched": batched,
                 "per_dtype_dE_drho": per_dtype, "steady_state": steady,
                 "roofline": roof, "cpu_baseline": cpu,
                 "e2e": {"value": args.steps / e2e_sec, "unit": "moves/s", "h2d_bytes_per_step": h2d,

@@ -327,7 +327,7 @@ hs_status hs_env_to_dense(hs_ctx ctx, const hs_env* env, double* C_dense, double
  * P_a = Q4^T V S^-1/2 above each truncated bond, P_b = Q1 U S^-1/2 below it.
  * In the Hermitian basis every tensor is Z2 block-sparse (Sec. II.B) and the
  * SVD splits into one per parity block; the kept states are the chi largest
- * over both blocks. FP64 GEMMs and FP64 SVD (one-sided Jacobi). Real double
+ * over both blocks. FP64 GEMMs and FP64 SVD (hs_svd_mode). Real double
  * layers only (HS_F64).
  *
  * Bonds: 0 top, 1 right, 2 bottom, 3 left side of the boundary. Corner k
@@ -339,6 +339,12 @@ hs_status hs_env_to_dense(hs_ctx ctx, const hs_env* env, double* C_dense, double
  * right to left, T4 bottom to top. Storage: C[k] is the Z2 matrix
  * [in | out], T[k] the Z2 matrix [(alpha, x) | beta], both in FSO block
  * order (hs_z2_tensor). */
+/* SVD of the directional move's parity blocks: one-sided Jacobi (cuSOLVER
+ * gesvdj; singular values to about 1e-14 of the largest) or the polar-
+ * decomposition SVD (cuSOLVER Xgesvdp; 4-8 times faster on these blocks,
+ * singular values to about 1e-11..1e-9 of the largest). */
+typedef enum { HS_SVD_JACOBI = 0, HS_SVD_POLAR = 1 } hs_svd_mode;
+
 typedef struct {
   int D, chi_max;
   int chi_even[4], chi_odd[4]; /* sectors of the four boundary bonds (host copy) */
@@ -349,6 +355,7 @@ typedef struct {
   double* T[4];                /* device, caller-owned; T_bytes each */
   size_t C_bytes, T_bytes;     /* at least hs_env_bytes(D, chi_max) */
   double log_norm_C[4], log_norm_T[4]; /* logs of the last normalisation factors */
+  hs_svd_mode svd;             /* set to HS_SVD_JACOBI by hs_ctmrg4_init; may change between moves */
 } hs_env4;
 
 typedef struct {
@@ -558,6 +565,16 @@ hs_status hs_ctmrg_energy_grad(hs_ctx ctx, const double* A, int d, int D, hs_bas
 
 /* Workspace the context will allocate for (D, chi): reported for planning. */
 hs_status hs_workspace_query(int D, int chi, hs_precision precision, size_t* bytes);
+
+/* Diagnostic: runs the tensor-core GEMM's bounded mbarrier wait (the wait
+ * every pipeline stage of that kernel uses, which gives up after a fixed
+ * number of try_wait rounds, raises the kernel's abort flag and records an
+ * error code) on barriers whose outcome is known, with `limit` rounds
+ * (1 <= limit <= the kernel's own limit). result (host, 7 ints): wait on a
+ * barrier nothing completes -> {0 (gave up), 7 (code recorded), 1 (abort
+ * raised)}; wait with the abort flag raised -> {0, 0 (nothing recorded)};
+ * wait on a barrier completed by one arrival -> {1, 0}. Synchronises. */
+hs_status hs_selftest_bounded_wait(hs_ctx ctx, long long limit, int* result);
 
 #ifdef __cplusplus
 }

@@ -27,6 +27,7 @@ HS_BASIS_DENSE, HS_BASIS_HERMITIAN = 0, 1
 HS_GEMM_OWN, HS_GEMM_CUBLAS = 0, 1
 HS_RDM_TWO_SITE, HS_RDM_ENV_ONE_SITE, HS_RDM_ONE_SITE = 0, 1, 2
 HS_EIG_F64, HS_EIG_F32_PROJECTED, HS_EIG_SUBSPACE, HS_EIG_SUBSPACE_ADAPTIVE = 0, 1, 2, 3
+HS_SVD_JACOBI, HS_SVD_POLAR = 0, 1
 
 
 class HsError(RuntimeError):
@@ -72,7 +73,7 @@ class Env4(ctypes.Structure):
     _fields_ = [("D", c_int), ("chi_max", c_int), ("chi_even", c_int * 4), ("chi_odd", c_int * 4),
                 ("q_even", c_int), ("q_odd", c_int), ("basis", c_int), ("moves", c_int),
                 ("C", c_void_p * 4), ("T", c_void_p * 4), ("C_bytes", c_size_t), ("T_bytes", c_size_t),
-                ("log_norm_C", c_double * 4), ("log_norm_T", c_double * 4)]
+                ("log_norm_C", c_double * 4), ("log_norm_T", c_double * 4), ("svd", c_int)]
 
 
 class Move4Info(ctypes.Structure):
@@ -122,6 +123,7 @@ _PROTOS = {
     "hs_ctmrg4_move": (c_int, [c_void_p, POINTER(Z2Tensor), POINTER(Env4), c_int, c_int, POINTER(Move4Info),
                                POINTER(c_double)]),
     "hs_env4_to_dense": (c_int, [c_void_p, POINTER(Env4), POINTER(c_void_p), POINTER(c_void_p)]),
+    "hs_selftest_bounded_wait": (c_int, [c_void_p, ctypes.c_longlong, POINTER(c_int)]),
     "hs_hotrg_tensor_bytes": (c_size_t, [c_int, c_int]),
     "hs_hotrg_init": (c_int, [c_void_p, POINTER(Z2Tensor), POINTER(Z2Tensor), POINTER(c_double)]),
     "hs_hotrg_step": (c_int, [c_void_p, POINTER(Z2Tensor), c_int, c_int, c_int, POINTER(HotrgInfo)]),
@@ -268,6 +270,12 @@ def hs_ctmrg4_move(ctx: int, a: Z2Tensor, env: Env4, chi: int, direction: int) -
 def hs_env4_to_dense(ctx: int, env: Env4, C_dense, T_dense) -> None:
     check(load().hs_env4_to_dense(ctx, ctypes.byref(env), (c_void_p * 4)(*[ptr(x) for x in C_dense]),
                                   (c_void_p * 4)(*[ptr(x) for x in T_dense])))
+
+
+def hs_selftest_bounded_wait(ctx: int, limit: int) -> list[int]:
+    out = (c_int * 7)()
+    check(load().hs_selftest_bounded_wait(ctx, limit, out))
+    return list(out)
 
 
 def hs_corner_spectrum(ctx: int, env: Env, out) -> None:

@@ -274,12 +274,13 @@ class DirectionalCTMRG:
     """CTMRG without lattice symmetry (four corners, four edges) of one real iPEPS tensor on one
     GPU through the C ABI: a sweep moves the left, top, right and bottom sides in turn."""
 
-    def __init__(self, ctx: Context, A: np.ndarray | torch.Tensor, chi: int, basis: str = "hermitian"):
+    def __init__(self, ctx: Context, A: np.ndarray | torch.Tensor, chi: int, basis: str = "hermitian",
+                 svd: str = "jacobi"):
         self.ctx = ctx
-        self._init(A, chi, basis)
+        self._init(A, chi, basis, svd)
 
     @on_ctx_stream
-    def _init(self, A, chi, basis):
+    def _init(self, A, chi, basis, svd):
         ctx = self.ctx
         dev = f"cuda:{ctx.device}"
         self.A = A if isinstance(A, torch.Tensor) else to_device(A, ctx.device)
@@ -292,6 +293,7 @@ class DirectionalCTMRG:
         self.C_bufs = [torch.empty(cb // 8, dtype=torch.float64, device=dev) for _ in range(4)]
         self.T_bufs = [torch.empty(tb // 8, dtype=torch.float64, device=dev) for _ in range(4)]
         self.env = L.hs_ctmrg4_init(ctx.handle, self.a, chi, self.C_bufs, self.T_bufs)
+        self.env.svd = {"jacobi": L.HS_SVD_JACOBI, "polar": L.HS_SVD_POLAR}[svd]
         self.infos: list[dict] = []
         self.spectra: list[list] = []
 

@@ -1458,6 +1458,17 @@ hs_status hs_env_bytes(int D, int chi_max, size_t* C_bytes, size_t* T_bytes) {
   return HS_OK;
 }
 
+hs_status hs_selftest_bounded_wait(hs_ctx ctx, long long limit, int* result) {
+  HS_TRY(check_ctx(ctx));
+  if (!result || limit < 1) return fail(HS_ERR_INVALID_ARG, "bad arguments");
+  HS_TRY(ctx->info.ensure(8 * sizeof(int)));
+  int* d = static_cast<int*>(ctx->info.p);
+  HS_CUDA(launch_wait_selftest(limit, d, ctx->stream));
+  HS_CUDA(cudaMemcpyAsync(result, d, 7 * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  HS_CUDA(cudaStreamSynchronize(ctx->stream));
+  return HS_OK;
+}
+
 hs_status hs_workspace_query(int D, int chi, hs_precision precision, size_t* bytes) {
   if (D <= 0 || chi <= 0 || !bytes) return fail(HS_ERR_INVALID_ARG, "bad arguments");
   (void)precision;

@@ -143,6 +143,61 @@ hs_status ensure_workspace(hs_ctx ctx, int chi_max, int q) {
   return HS_OK;
 }
 
+// SVD of the row-major block X (m x n, tightly packed): the min(m, n)
+// singular values to S, the left singular vectors as contiguous columns of L
+// (m long), the right ones of R (n long); status to *dinfo. Both methods work
+// on the tall orientation. polar: cuSOLVER Xgesvdp (polar factor, then a
+// symmetric eigensolver), falling back to the Jacobi SVD where it reports a
+// failure; else the one-sided Jacobi SVD (gesvdj).
+hs_status block_svd(hs_ctx ctx, bool polar, double* X, int m, int n, double* S, double* L, double* R, int* dinfo) {
+  cudaStream_t s = ctx->stream;
+  HS_SOLVER(cusolverDnSetStream(ctx->solver, s));
+  // column-major view of the tall orientation: X^T (n x m) when n >= m,
+  // else X itself (m x n, a transposed copy)
+  const bool tall_t = n >= m;
+  const int rows = tall_t ? n : m, cols = tall_t ? m : n;
+  double* A = X;
+  if (!tall_t) {
+    A = ctx->d4[kW1].d();
+    HS_TRY(permute(ctx, mat(fused1(make_sect(m, 0)), fused1(make_sect(n, 0))),
+                   mat(fused1(make_sect(n, 0)), fused1(make_sect(m, 0))), {1, 0}, X, A));
+  }
+  double* U = tall_t ? R : L;  // rows long
+  double* V = tall_t ? L : R;  // cols long
+  size_t dbytes = 0, hbytes = 0;
+  const cusolverStatus_t q = !polar ? CUSOLVER_STATUS_NOT_SUPPORTED :
+      cusolverDnXgesvdp_bufferSize(ctx->solver, ctx->params, CUSOLVER_EIG_MODE_VECTOR, 1, rows, cols, CUDA_R_64F, A,
+                                   rows, CUDA_R_64F, S, CUDA_R_64F, U, rows, CUDA_R_64F, V, cols, CUDA_R_64F, &dbytes,
+                                   &hbytes);
+  if (q == CUSOLVER_STATUS_SUCCESS) {
+    HS_TRY(ctx->d4[kWork].ensure(std::max<size_t>(dbytes, 8)));
+    if (ctx->d4_work_host.size() < hbytes) ctx->d4_work_host.resize(hbytes);
+    // the polar path overwrites A; keep X for the fallback
+    double* A2 = ctx->d4[kW2].d();
+    HS_CUDA(cudaMemcpyAsync(A2, A, (size_t)rows * cols * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    double err_sigma = 0.0;
+    const cusolverStatus_t st = cusolverDnXgesvdp(
+        ctx->solver, ctx->params, CUSOLVER_EIG_MODE_VECTOR, 1, rows, cols, CUDA_R_64F, A2, rows, CUDA_R_64F, S,
+        CUDA_R_64F, U, rows, CUDA_R_64F, V, cols, CUDA_R_64F, ctx->d4[kWork].p, dbytes,
+        hbytes ? ctx->d4_work_host.data() : nullptr, hbytes, dinfo, &err_sigma);
+    int hinfo = 0;
+    if (st == CUSOLVER_STATUS_SUCCESS) {
+      HS_CUDA(cudaMemcpyAsync(&hinfo, dinfo, sizeof(int), cudaMemcpyDeviceToHost, s));
+      HS_CUDA(cudaStreamSynchronize(s));
+      if (hinfo == 0 && std::isfinite(err_sigma)) return HS_OK;
+    }
+    HS_CUDA(cudaMemsetAsync(dinfo, 0, sizeof(int), s));
+  }
+  int lwork = 0;
+  HS_SOLVER(cusolverDnDgesvdj_bufferSize(ctx->solver, CUSOLVER_EIG_MODE_VECTOR, 1, rows, cols, A, rows, S, U, rows,
+                                         V, cols, &lwork, ctx->gesvdj));
+  HS_TRY(ctx->d4[kWork].ensure((size_t)std::max(lwork, 1) * sizeof(double)));
+  HS_SOLVER(cusolverDnDgesvdj(ctx->solver, CUSOLVER_EIG_MODE_VECTOR, 1, rows, cols, A, rows, S, U, rows, V, cols,
+                              ctx->d4[kWork].d(), lwork, dinfo, ctx->gesvdj));
+  ctx->d4_svd_fallbacks += polar;
+  return HS_OK;
+}
+
 // Normalise x (n entries) by its largest modulus; the log goes to device slot k of kLog.
 hs_status normalise(hs_ctx ctx, double* x, long long n, int k) {
   HS_CUDA(launch_normalize_max_to(x, n, static_cast<unsigned long long*>(ctx->scratch.p) + k,
@@ -182,6 +237,7 @@ hs_status hs_ctmrg4_init(hs_ctx ctx, const hs_z2_tensor* a, int chi_max, hs_env4
   }
   env->basis = a->basis;
   env->moves = 0;
+  env->svd = HS_SVD_JACOBI;
   HS_TRY(ensure_workspace(ctx, env->chi_max, q));
   HS_TRY(ctx->scratch.ensure(64 * sizeof(unsigned long long)));
   const Z2Mat Am = mat(fused2(qs, qs), fused2(qs, qs));
@@ -221,6 +277,7 @@ hs_status hs_ctmrg4_move(hs_ctx ctx, const hs_z2_tensor* a, hs_env4* env, int ch
   if (!a || !env || !a->data) return fail(HS_ERR_INVALID_ARG, "bad arguments");
   if (direction < 0 || direction > 3) return fail(HS_ERR_INVALID_ARG, "direction must be 0..3");
   if (chi < 1 || chi > env->chi_max) return fail(HS_ERR_SHAPE, "chi must be in [1, chi_max]");
+  if (env->svd != HS_SVD_JACOBI && env->svd != HS_SVD_POLAR) return fail(HS_ERR_INVALID_ARG, "unknown SVD mode");
   if (a->data != ctx->d4_src || a->D != env->D)
     return fail(HS_ERR_INVALID_ARG, "the double layer is not the one given to hs_ctmrg4_init");
   const int f = direction;
@@ -241,11 +298,9 @@ hs_status hs_ctmrg4_move(hs_ctx ctx, const hs_z2_tensor* a, hs_env4* env, int ch
   HS_TRY(permute(ctx, Q4m, Q4t, {2, 3, 0, 1}, Q4, ctx->d4[kQ4t].d()));
   HS_TRY(gemm4(ctx, fl, Q1t, Q4m, Xm, ctx->d4[kQ1t].d(), Q4, ctx->d4[kX].d()));
 
-  // one SVD per parity block. The row-major block X_p (m x n) read
-  // column-major is X_p^T, whose Jacobi SVD W S Z^T gives X_p = Z S W^T: the
-  // columns of Z (buffer Lv) are the left singular vectors of X_p (over its
-  // rows j), those of W (buffer Rv) the right ones (over its columns j'),
-  // each contiguous.
+  // one SVD per parity block, into contiguous columns: Lv the left singular
+  // vectors of X_p (over its rows j, m_p long), Rv the right ones (over its
+  // columns j', n_p long).
   int m[2], n[2], r[2];
   long long roff[2], loff[2], soff[2];
   for (int p = 0; p < 2; ++p) {
@@ -257,29 +312,15 @@ hs_status hs_ctmrg4_move(hs_ctx ctx, const hs_z2_tensor* a, hs_env4* env, int ch
   roff[1] = (long long)n[0] * r[0];
   loff[1] = (long long)m[0] * r[0];
   soff[1] = r[0];
-  double* X = ctx->d4[kX].d();
   double* Rv = ctx->d4[kU].d();
   double* Lv = ctx->d4[kV].d();
   double* S = ctx->d4[kS].d();
   int* dinfo = static_cast<int*>(ctx->d4[kInfo].p);
   HS_CUDA(cudaMemsetAsync(dinfo, 0, 2 * sizeof(int), s));
-  HS_SOLVER(cusolverDnSetStream(ctx->solver, s));
-  int lwork = 0;
-  for (int p = 0; p < 2; ++p) {
-    if (r[p] == 0) continue;
-    int lw = 0;
-    HS_SOLVER(cusolverDnDgesvdj_bufferSize(ctx->solver, CUSOLVER_EIG_MODE_VECTOR, 1, n[p], m[p],
-                                           X + z2_block_off(Xm, p), n[p], S + soff[p], Rv + roff[p], n[p],
-                                           Lv + loff[p], m[p], &lw, ctx->gesvdj));
-    lwork = std::max(lwork, lw);
-  }
-  HS_TRY(ctx->d4[kWork].ensure((size_t)std::max(lwork, 1) * sizeof(double)));
-  for (int p = 0; p < 2; ++p) {
-    if (r[p] == 0) continue;
-    HS_SOLVER(cusolverDnDgesvdj(ctx->solver, CUSOLVER_EIG_MODE_VECTOR, 1, n[p], m[p], X + z2_block_off(Xm, p), n[p],
-                                S + soff[p], Rv + roff[p], n[p], Lv + loff[p], m[p], ctx->d4[kWork].d(), lwork,
-                                dinfo + p, ctx->gesvdj));
-  }
+  for (int p = 0; p < 2; ++p)
+    if (r[p] > 0)
+      HS_TRY(block_svd(ctx, env->svd == HS_SVD_POLAR, ctx->d4[kX].d() + z2_block_off(Xm, p), m[p], n[p],
+                       S + soff[p], Lv + loff[p], Rv + roff[p], dinfo + p));
   // singular values and status to the host: the kept sectors fix every shape below
   const int rt = r[0] + r[1];
   if (rt == 0) return fail(HS_ERR_SHAPE, "empty SVD");
@@ -288,7 +329,7 @@ hs_status hs_ctmrg4_move(hs_ctx ctx, const hs_z2_tensor* a, hs_env4* env, int ch
   HS_CUDA(cudaMemcpyAsync(hs_, S, rt * sizeof(double), cudaMemcpyDeviceToHost, s));
   HS_CUDA(cudaMemcpyAsync(hinfo, dinfo, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
   HS_CUDA(cudaStreamSynchronize(s));
-  if (hinfo[0] != 0 || hinfo[1] != 0) return fail(HS_ERR_SOLVER, "gesvdj info = (%d, %d)", hinfo[0], hinfo[1]);
+  if (hinfo[0] != 0 || hinfo[1] != 0) return fail(HS_ERR_SOLVER, "SVD info = (%d, %d)", hinfo[0], hinfo[1]);
 
   // keep the chi largest over both blocks (ties: block 0, then lower index)
   struct Cand {

@@ -174,6 +174,8 @@ struct hs_ctx_s {
   hs::PinnedBuf d4_h;
   const double* d4_src = nullptr;
   gesvdjInfo_t gesvdj = nullptr;
+  std::vector<char> d4_work_host;
+  long long d4_svd_fallbacks = 0;  // blocks that took the Jacobi SVD
   // split-K partial sums of the FP64 GEMM
   hs::DBuf splitk;
   // subspace eigensolver: warm start (previous kept rows, per block) and

@@ -534,6 +534,10 @@ cudaError_t launch_env_to_dense_vjp(const double* dCd, const double* dTd, int D,
 cudaError_t launch_double_layer_vjp(const double* da_plain, const double* A, int d, int D, double* dA,
                                     cudaStream_t s);
 
+// The tensor-core GEMM's bounded mbarrier wait on barriers with known outcomes
+// (7 ints to the device array out; k_gemm_tc.cu).
+cudaError_t launch_wait_selftest(long long limit, int* out, cudaStream_t s);
+
 // Dense views of an FSO environment (rotated back to the plain combined basis).
 cudaError_t launch_env_to_dense(const double* C, const double* T, int D, int c0, int c1,
                                 bool hermitian, double* Cd, double* Td, cudaStream_t s);

@@ -103,16 +103,22 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Bounded wait; on timeout records the code and raises the abort flag.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag,
-                                          int* err, int code) {
-  for (long long i = 0; i < WAIT_LIMIT; ++i) {
+// Bounded wait (limit try_wait rounds); on timeout records the code and
+// raises the abort flag.
+__device__ __forceinline__ bool mbar_wait_n(uint32_t bar, uint32_t parity, volatile int* abort_flag,
+                                            int* err, int code, long long limit) {
+  for (long long i = 0; i < limit; ++i) {
     if (mbar_try(bar, parity)) return true;
     if (*abort_flag) return false;
   }
   *abort_flag = 1;
   atomicExch(err, code);
   return false;
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag,
+                                          int* err, int code) {
+  return mbar_wait_n(bar, parity, abort_flag, err, code, WAIT_LIMIT);
 }
 
 // Drain wait after an abort: bounded, never raises anything.
@@ -803,7 +809,42 @@ cudaError_t run(const TcProblem* probs, int nprob, int* err, cudaStream_t s, dou
   return cudaGetLastError();
 }
 
+// The GEMM kernel's bounded wait, run on barriers whose outcome is known:
+// out[0..2] a wait (limit rounds) on a barrier nothing completes: the result
+// (0), the recorded code (7) and the abort flag (1); out[3..4] a second wait
+// with the abort flag raised: returns at once (0) and records nothing (0);
+// out[5..6] a wait on a barrier completed by one arrival: 1 and nothing
+// recorded. One thread; no copy or MMA is in flight.
+__global__ void wait_selftest_kernel(long long limit, int* out) {
+  __shared__ __align__(8) uint64_t bar[2];
+  __shared__ int abort_flag, err[3];
+  if (threadIdx.x != 0) return;
+  abort_flag = 0;
+  err[0] = err[1] = err[2] = 0;
+  mbar_init(smem_u32(&bar[0]), 1);
+  mbar_init(smem_u32(&bar[1]), 1);
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  const bool w0 = mbar_wait_n(smem_u32(&bar[0]), 0, &abort_flag, &err[0], 7, limit);
+  out[0] = w0;
+  out[1] = err[0];
+  out[2] = abort_flag;
+  const bool w1 = mbar_wait_n(smem_u32(&bar[0]), 0, &abort_flag, &err[1], 9, limit);
+  out[3] = w1;
+  out[4] = err[1];
+  abort_flag = 0;
+  mbar_arrive(smem_u32(&bar[1]));
+  const bool w2 = mbar_wait_n(smem_u32(&bar[1]), 0, &abort_flag, &err[2], 11, limit);
+  out[5] = w2;
+  out[6] = err[2];
+}
+
 }  // namespace
+
+cudaError_t launch_wait_selftest(long long limit, int* out, cudaStream_t s) {
+  if (limit < 1 || limit > WAIT_LIMIT) return cudaErrorInvalidValue;
+  wait_selftest_kernel<<<1, 32, 0, s>>>(limit, out);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_gemm_tc(int precision, const TcProblem* probs, int nprob, int* err, cudaStream_t s,
                            double* part, long long part_elems) {

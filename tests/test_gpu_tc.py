@@ -192,3 +192,22 @@ def test_d7_chi196_matches_oracle(ctx, precision, eig):
         assert drho <= tol[1], m
         assert ds <= tol[2], m
     assert (c.env.q_even, c.env.q_odd) == (28, 21)
+
+
+def test_bounded_wait_gives_up_and_reports(ctx):
+    """The GEMM kernel's mbarrier wait on a barrier that nothing completes gives up after its
+    round limit, raises the abort flag and records its code; with the flag raised a wait returns
+    at once; a completed barrier passes. The context stays usable afterwards."""
+    import time
+    from paper_2410_11596_gb300 import _lib as L
+    t0 = time.perf_counter()
+    assert L.hs_selftest_bounded_wait(ctx.handle, 20000) == [0, 7, 1, 0, 0, 1, 0]
+    assert time.perf_counter() - t0 < 10.0
+    with pytest.raises(L.HsError):
+        L.hs_selftest_bounded_wait(ctx.handle, 0)
+    a = torch.randn(256, 128, dtype=torch.float64, device="cuda")
+    c = torch.empty(256, 256, dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    L.hs_gemm(ctx.handle, L.HS_PREC_TF32X3, a, a, c)
+    torch.cuda.synchronize()
+    assert torch.allclose(c, a @ a.T, rtol=1e-5, atol=1e-4)
