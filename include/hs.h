@@ -470,7 +470,9 @@ typedef enum {
   HS_PHASE_SELECT = 3,    /* choice of kept states, projector gather, new corner */
   HS_PHASE_NORMALIZE = 4, /* max-abs normalisation of the edge */
   HS_PHASE_GEMM_TC = 5,   /* block GEMMs on the tensor cores (TF32/BF16 modes) */
-  HS_PHASE_COUNT = 6
+  HS_PHASE_GEMM_TC_SPLIT = 6, /* those of them whose epilogue writes the next GEMM's permuted split
+                                 operand (the enlarged corner and edge products); also in phase 5 */
+  HS_PHASE_COUNT = 7
 } hs_phase;
 
 /* Turn per-phase timing on (1) or off (0); either way the counters reset.

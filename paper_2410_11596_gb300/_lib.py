@@ -131,7 +131,7 @@ _PROTOS = {
                                c_void_p, c_void_p]),
 }
 
-PHASES = ("gemm", "permute", "eig", "select", "normalize", "gemm_tc")
+PHASES = ("gemm", "permute", "eig", "select", "normalize", "gemm_tc", "gemm_tc_split")
 
 _lib = None
 

@@ -420,7 +420,10 @@ hs_status tc_run_split(hs_ctx ctx, hs_precision prec, const Z2Mat& A, const DBuf
     HS_TRY(tc_run(ctx, prec, A, ahi, alo, B, bhi, blo, Cm, reinterpret_cast<double*>(tmp), true));
     return tc_split_any(ctx, prec, Cm, layout, perm, tmp, true, hi, lo);
   }
+  for (int p = 0; p < 2; ++p)
+    ctx->phase_flops[HS_PHASE_GEMM_TC_SPLIT] += 2.0 * z2_rows(A, p) * (double)z2_rows(B, p) * z2_cols(A, p);
   PhaseScope ps(ctx, HS_PHASE_GEMM_TC);
+  PhaseScope ps2(ctx, HS_PHASE_GEMM_TC_SPLIT);
   HS_CUDA(launch_gemm_tc(prec, pr, n, static_cast<int*>(ctx->tc_err.p), ctx->stream, nullptr, 0));
   if (n > 0) ctx->launches += 1;
   return HS_OK;

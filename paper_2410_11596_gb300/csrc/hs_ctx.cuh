@@ -219,8 +219,8 @@ struct hs_ctx_s {
     int phase, e0, e1;
   };
   std::vector<Rec> recs;
-  double phase_ms[HS_PHASE_COUNT] = {0, 0, 0, 0, 0, 0};
-  double phase_flops[HS_PHASE_COUNT] = {0, 0, 0, 0, 0, 0};
+  double phase_ms[HS_PHASE_COUNT] = {};
+  double phase_flops[HS_PHASE_COUNT] = {};
   long long launches = 0;
 };
 

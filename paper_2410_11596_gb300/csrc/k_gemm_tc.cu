@@ -64,7 +64,7 @@ using Maps = MapsN<kMaxPairs>;
 // One launch unit: a K range [k0, k0 + Kp) of an operand pair (map); with
 // split-K every range writes its own FP64 partial (c, row stride ldc) and a
 // reduction kernel sums them.
-constexpr int kMaxUnits = 16;
+constexpr int kMaxUnits = 32;
 struct Prob {
   int M, N, Kp, ldc;
   int k0, map;
@@ -747,12 +747,14 @@ cudaError_t run(const TcProblem* probs, int nprob, int* err, cudaStream_t s, dou
     }
     // split K when this problem's tiles cannot fill the SMs and each
     // split keeps at least 4 K steps; partials go to `part` (not for a
-    // permuted split output)
+    // permuted split output). Up to 16 splits: a narrow product with a long
+    // contraction (the subspace steps: M, N ~ 100, K ~ 2600) otherwise
+    // streams its whole K through a handful of SMs
     int ns = 1;
     if (part && ptiles < sms && psi < 0) {
       ns = (sms + ptiles - 1) / ptiles;
       ns = ns < ktiles / 4 ? ns : ktiles / 4;
-      ns = ns < 8 ? ns : 8;
+      ns = ns < 16 ? ns : 16;
       const long long need = (long long)ns * p.M * p.N;
       if (ns < 2 || part_used + need > part_elems || g.n + ns > kMaxUnits) ns = 1;
     }
