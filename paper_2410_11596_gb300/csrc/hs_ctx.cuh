@@ -206,6 +206,9 @@ struct hs_ctx_s {
   // adaptive subspace tolerance: the warm start's residual in the previous
   // move's first round, and the environment it belongs to
   double prev_first_resid = 0.0;
+  // the subspace residual at which a previous move stalled on the rounding
+  // of its products (0: none yet); the tolerance of later moves follows it
+  double resid_floor = 0.0;
   const void* prev_spec_env = nullptr;
   // permute plans by layout pair and permutation (building one takes a few
   // microseconds of host time, and every move repeats the same few dozen)
