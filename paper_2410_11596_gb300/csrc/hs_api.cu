@@ -448,7 +448,7 @@ Z2Mat dense2(long long r, long long c) { return mat(fused1(make_sect((int)r, 0))
 // the new corner is the projection C = PT C' PT^T of each block (FP64, or on
 // the tensor cores in the TF32/BF16 precisions), normalised by its largest entry.
 hs_status finish_projector(hs_ctx ctx, int n0, int n1, SelectOut* dsel, Sect c, Sect q, Sect cn, const double* C0,
-                           const double* C1, hs_env* env, double* flops, int lowdin) {
+                           const double* C1, hs_env* env, double* flops, int lowdin, bool canonical_sign = true) {
   cudaStream_t s = ctx->stream;
   const int k[2] = {cn.n[0], cn.n[1]};
   const int n[2] = {n0, n1};
@@ -477,9 +477,12 @@ hs_status finish_projector(hs_ctx ctx, int n0, int n1, SelectOut* dsel, Sect c, 
   const Z2Mat PTm = mat(fused1(cn), fused2(c, q)), Pm = mat(fused2(c, q), fused1(cn));
   {
     PhaseScope ps(ctx, HS_PHASE_SELECT);
-    HS_CUDA(launch_row_sign_pair(PT, k[0], n[0], k[1], n[1], s));
+    if (canonical_sign) {
+      HS_CUDA(launch_row_sign_pair(PT, k[0], n[0], k[1], n[1], s));
+      ctx->launches += 1;
+    }
     HS_TRY(permute(ctx, PTm, Pm, {1, 2, 0}, PT, P));
-    ctx->launches += 2;
+    ctx->launches += 1;
   }
   if (env->precision != HS_PREC_F64) {
     // tensor-core precisions: the projection below runs on tcgen05 with FP32
@@ -545,6 +548,100 @@ hs_status finish_projector(hs_ctx ctx, int n0, int n1, SelectOut* dsel, Sect c, 
   HS_CUDA(launch_normalize_max_to(env->C, goff[1] + (long long)k[1] * k[1],
                                   static_cast<unsigned long long*>(ctx->scratch.p) + 2, &dsel->log_norm_C, s));
   ctx->launches += 4;
+  return HS_OK;
+}
+
+// Order the kept rows PT of this move (k_b rows of length n_b per block,
+// stacked) like the previous move's: the new boundary states are a gauge
+// choice, and the warm start of the next move's subspace iteration is only
+// valid when that choice is stationary. Kept states come ordered by |lambda|;
+// where two of them have nearly equal |lambda| (D = 7: the spectrum drifts by
+// ~0.5% per move and close pairs change order) the order, and with it the
+// coordinates of the next C', changes from move to move. Here each new row
+// takes the position of the previous row it overlaps most (|O_ij|, O = PT
+// PT_prev^T, FP64), when that is a one-to-one match with every overlap above
+// 1/2; otherwise the block keeps its order. *moved: rows that moved.
+hs_status align_kept_rows(hs_ctx ctx, const int k[2], const int n[2], int* moved) {
+  cudaStream_t s = ctx->stream;
+  *moved = 0;
+  const long long off1 = (long long)k[0] * n[0];
+  const long long npt = off1 + (long long)k[1] * n[1];
+  const long long no = (long long)k[0] * k[0] + (long long)k[1] * k[1];
+  HS_TRY(ctx->ovl.ensure((size_t)(no + 1) * sizeof(double)));
+  HS_TRY(ctx->ovl_idx.ensure((size_t)(k[0] + k[1] + 1) * sizeof(int)));
+  HS_TRY(ctx->pt_tmp.ensure((size_t)(npt + 1) * sizeof(double)));
+  HS_TRY(ctx->h_ovl.ensure((size_t)(no + 1) * sizeof(double) + (size_t)(k[0] + k[1] + 1) * (sizeof(int) + sizeof(double))));
+  HS_TRY(ctx->splitk.ensure(kSplitKElems * sizeof(double)));
+  const long long poff[2] = {0, off1}, ooff[2] = {0, (long long)k[0] * k[0]};
+  GemmGroup g{};
+  for (int b = 0; b < 2; ++b)
+    if (k[b] > 0) g.p[g.n++] = GemmProblem{k[b], k[b], n[b], n[b], n[b], k[b], poff[b], poff[b], ooff[b]};
+  HS_CUDA(launch_gemm_f64(g, ctx->pt.d(), ctx->pt_prev.d(), ctx->ovl.d(), 1.0, s, ctx->splitk.d(), kSplitKElems));
+  ctx->launches += 1;
+  double* ho = static_cast<double*>(ctx->h_ovl.p);
+  double* hsgn = ho + no + 1;
+  int* hidx = reinterpret_cast<int*>(hsgn + k[0] + k[1] + 1);
+  HS_CUDA(cudaMemcpyAsync(ho, ctx->ovl.p, (size_t)no * sizeof(double), cudaMemcpyDeviceToHost, s));
+  HS_CUDA(cudaStreamSynchronize(s));
+  for (int b = 0; b < 2; ++b) {
+    const int kb = k[b];
+    const double* O = ho + ooff[b];
+    int* ib = hidx + (b ? k[0] : 0);
+    // each new row's best previous row; rows with the clearest match first,
+    // each taking its previous row's position when that is still free and
+    // the overlap is above 1/2; the rest fill the free positions in order
+    std::vector<int> best(kb, 0), pos(kb, -1), order(kb);
+    std::vector<double> ov(kb, 0.0);
+    for (int i = 0; i < kb; ++i) {
+      for (int j = 1; j < kb; ++j)
+        if (std::fabs(O[(long long)i * kb + j]) > std::fabs(O[(long long)i * kb + best[i]])) best[i] = j;
+      ov[i] = std::fabs(O[(long long)i * kb + best[i]]);
+      order[i] = i;
+    }
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return ov[x] > ov[y]; });
+    std::vector<char> taken(kb, 0);
+    for (int i : order)
+      if (ov[i] > 0.5 && !taken[best[i]]) {
+        pos[i] = best[i];
+        taken[best[i]] = 1;
+      }
+    int free_j = 0;
+    for (int i = 0; i < kb; ++i) {
+      if (pos[i] >= 0) continue;
+      while (taken[free_j]) ++free_j;
+      pos[i] = free_j;
+      taken[free_j] = 1;
+    }
+    double* sb = hsgn + (b ? k[0] : 0);
+    for (int i = 0; i < kb; ++i) {
+      ib[pos[i]] = i;
+      // a matched row takes the sign of the previous row it continues
+      sb[pos[i]] = (pos[i] == best[i] && O[(long long)i * kb + best[i]] < 0.0) ? -1.0 : 1.0;
+      *moved += pos[i] != i || sb[pos[i]] < 0.0;
+    }
+  }
+  if (*moved == 0) return HS_OK;
+  HS_TRY(ctx->ovl_sgn.ensure((size_t)(k[0] + k[1] + 1) * sizeof(double)));
+  HS_CUDA(cudaMemcpyAsync(ctx->ovl_idx.p, hidx, (size_t)(k[0] + k[1]) * sizeof(int), cudaMemcpyHostToDevice, s));
+  HS_CUDA(cudaMemcpyAsync(ctx->ovl_sgn.p, hsgn, (size_t)(k[0] + k[1]) * sizeof(double), cudaMemcpyHostToDevice, s));
+  HS_CUDA(launch_gather_rows_idx_sign_pair(ctx->pt.d(), off1, n[0], n[1], static_cast<const int*>(ctx->ovl_idx.p),
+                                           ctx->ovl_sgn.d(), k[0], k[1], ctx->pt_tmp.d(), off1, s));
+  HS_CUDA(cudaMemcpyAsync(ctx->pt.d(), ctx->pt_tmp.d(), (size_t)npt * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  ctx->launches += 1;
+  return HS_OK;
+}
+
+// Keep this move's final kept rows for the next move's align_kept_rows.
+hs_status keep_pt(hs_ctx ctx, const int k[2], const int n[2]) {
+  const long long npt = (long long)k[0] * n[0] + (long long)k[1] * n[1];
+  HS_TRY(ctx->pt_prev.ensure((size_t)(npt + 1) * sizeof(double)));
+  HS_CUDA(cudaMemcpyAsync(ctx->pt_prev.d(), ctx->pt.d(), (size_t)npt * sizeof(double), cudaMemcpyDeviceToDevice,
+                          ctx->stream));
+  ctx->pt_prev_valid = true;
+  for (int b = 0; b < 2; ++b) {
+    ctx->pt_prev_k[b] = k[b];
+    ctx->pt_prev_n[b] = n[b];
+  }
   return HS_OK;
 }
 
@@ -1342,6 +1439,8 @@ hs_status hs_destroy(hs_ctx ctx) {
   for (DBuf& b : ctx->zr) b.release();
   for (DBuf& b : ctx->zd) b.release();
   for (DBuf& b : ctx->d4) b.release();
+  for (DBuf* b : {&ctx->pt_prev, &ctx->ovl, &ctx->ovl_idx, &ctx->ovl_sgn, &ctx->pt_tmp}) b->release();
+  ctx->h_ovl.release();
   ctx->d4_h.release();
   if (ctx->gesvdj) cusolverDnDestroyGesvdjInfo(ctx->gesvdj);
   ctx->ga.release();
@@ -1524,6 +1623,7 @@ hs_status hs_ctmrg_init(hs_ctx ctx, const hs_z2_tensor* a, int chi_max, hs_preci
   ctx->ws_valid = false;  // no warm start for the subspace eigensolver yet
   ctx->prev_first_resid = 0.0;
   ctx->resid_floor = 0.0;
+  ctx->pt_prev_valid = false;
   if (a->dtype == HS_C128) return herm ? graded_init(ctx, a, chi_max, env) : zdense_init(ctx, a, chi_max, env);
   HS_CUDA(launch_ctmrg_init(a->data, D, herm, env->C, env->T, ctx->stream));
   // normalise like every later move
@@ -1772,15 +1872,31 @@ hs_status hs_ctmrg_move(hs_ctx ctx, const hs_z2_tensor* a, hs_env* env, int chi,
                                  ctx->pcol.d(), s));
       ctx->launches += 1;
     }
+    // a poor warm start (this move's first round far from converged) means
+    // the boundary gauge moved: order the kept rows like the previous move's
+    const int kk[2] = {cn.n[0], cn.n[1]}, nn[2] = {n0, n1};
+    bool aligned = false;
+    if (ctx->pt_prev_valid && ctx->pt_prev_k[0] == kk[0] && ctx->pt_prev_k[1] == kk[1] &&
+        ctx->pt_prev_n[0] == n0 && ctx->pt_prev_n[1] == n1 && ctx->prev_first_resid > 1e-3) {
+      // canonical signs first (the rows no previous row matches keep them)
+      HS_CUDA(launch_row_sign_pair(ctx->pt.d(), kk[0], n0, kk[1], n1, s));
+      ctx->launches += 1;
+      int moved = 0;
+      HS_TRY(align_kept_rows(ctx, kk, nn, &moved));
+      aligned = true;
+    }
     // converged Ritz vectors are orthonormal to ~1e-6 (FP32 Rayleigh-Ritz):
     // one FP64 Loewdin step brings them to ~1e-12
-    HS_TRY(finish_projector(ctx, n0, n1, dsel, c, q, cn, V0, V1, env, &flops, 1));
+    HS_TRY(finish_projector(ctx, n0, n1, dsel, c, q, cn, V0, V1, env, &flops, 1, !aligned));
+    HS_TRY(keep_pt(ctx, kk, nn));
   } else if (!f32eig) {
     PhaseScope ps(ctx, HS_PHASE_SELECT);
     HS_CUDA(launch_gather_pt(V0, n0, V1, n1, didx, chi, dsel, ctx->pt.d(), s));
     ctx->launches += 1;
   } else {
     HS_TRY(project_f32(ctx, V0f, n0, V1f, n1, didx, chi, dsel, c, q, cn, V0, V1, env, &flops));
+    const int kk[2] = {cn.n[0], cn.n[1]}, nn[2] = {n0, n1};
+    HS_TRY(keep_pt(ctx, kk, nn));
   }
   if (subspace_mode) {
     // the next move starts from the whole subspace of each block: the Ritz

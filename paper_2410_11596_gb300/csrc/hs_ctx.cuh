@@ -206,6 +206,12 @@ struct hs_ctx_s {
   // adaptive subspace tolerance: the warm start's residual in the previous
   // move's first round, and the environment it belongs to
   double prev_first_resid = 0.0;
+  // the previous move's kept rows (final PT, both blocks stacked), for
+  // ordering this move's kept rows like them (align_kept_rows)
+  hs::DBuf pt_prev, ovl, ovl_idx, ovl_sgn, pt_tmp;
+  hs::PinnedBuf h_ovl;
+  bool pt_prev_valid = false;
+  int pt_prev_k[2] = {0, 0}, pt_prev_n[2] = {0, 0};
   // the subspace residual at which a previous move stalled on the rounding
   // of its products (0: none yet); the tolerance of later moves follows it
   double resid_floor = 0.0;

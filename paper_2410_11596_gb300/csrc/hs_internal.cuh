@@ -488,6 +488,10 @@ cudaError_t launch_gather_rows_idx(const double* X, const int* idx, int m, int n
 // Chebyshev term with alpha0 on the first count0 entries, alpha1 after.
 cudaError_t launch_gather_rows_idx_pair(const double* X, long long src_off1, int n0, int n1, const int* idx,
                                         int cnt0, int cnt1, double* out, long long dst_off1, cudaStream_t s);
+// As launch_gather_rows_idx_pair, output row j scaled by sgn[j] (device, cnt0 + cnt1 entries).
+cudaError_t launch_gather_rows_idx_sign_pair(const double* X, long long src_off1, int n0, int n1, const int* idx,
+                                             const double* sgn, int cnt0, int cnt1, double* out, long long dst_off1,
+                                             cudaStream_t s);
 cudaError_t launch_cheb_step_pair(double* Y, const double* Z, const double* T, const double* Yold, long long count,
                                   long long count0, double alpha0, double alpha1, double beta, cudaStream_t s);
 // Y = alpha (Z - T) + beta Yold over count entries; T and Yold may be null.

@@ -337,6 +337,19 @@ __global__ void gather_rows_idx_pair_kernel(const double* __restrict__ X, long l
   for (int k = threadIdx.x; k < n; k += blockDim.x) out[dst + k] = X[src + k];
 }
 
+// As gather_rows_idx_pair_kernel, each output row j multiplied by sgn[j].
+__global__ void gather_rows_idx_sign_pair_kernel(const double* __restrict__ X, long long src_off1, int n0, int n1,
+                                                 const int* __restrict__ idx, const double* __restrict__ sgn,
+                                                 int cnt0, double* __restrict__ out, long long dst_off1) {
+  hs_pdl_enter();
+  const int j = blockIdx.x, b = j >= cnt0;
+  const int n = b ? n1 : n0;
+  const long long src = (b ? src_off1 : 0) + (long long)idx[j] * n;
+  const long long dst = (b ? dst_off1 : 0) + (long long)(j - (b ? cnt0 : 0)) * n;
+  const double f = sgn[j];
+  for (int k = threadIdx.x; k < n; k += blockDim.x) out[dst + k] = f * X[src + k];
+}
+
 // cheb_step_kernel over a stacked pair: entries below count0 use alpha0.
 __global__ void cheb_step_pair_kernel(double* __restrict__ Y, const double* __restrict__ Z,
                                       const double* __restrict__ T, const double* __restrict__ Yold, long long count,
@@ -616,6 +629,15 @@ cudaError_t launch_gather_rows_idx_pair(const double* X, long long src_off1, int
                                         int cnt0, int cnt1, double* out, long long dst_off1, cudaStream_t s) {
   if (cnt0 + cnt1 <= 0) return cudaSuccess;
   hs_launch(gather_rows_idx_pair_kernel, cnt0 + cnt1, 256, 0, s, X, src_off1, n0, n1, idx, cnt0, out, dst_off1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather_rows_idx_sign_pair(const double* X, long long src_off1, int n0, int n1, const int* idx,
+                                             const double* sgn, int cnt0, int cnt1, double* out, long long dst_off1,
+                                             cudaStream_t s) {
+  if (cnt0 + cnt1 <= 0) return cudaSuccess;
+  hs_launch(gather_rows_idx_sign_pair_kernel, cnt0 + cnt1, 256, 0, s, X, src_off1, n0, n1, idx, sgn, cnt0, out,
+            dst_off1);
   return cudaGetLastError();
 }
 
