@@ -98,13 +98,17 @@ typedef enum { HS_BASIS_DENSE = 0, HS_BASIS_HERMITIAN = 1 } hs_basis;
  *   the residual stalls far from the tolerance) seeded with the previous
  *   move's subspace (kept plus oversampled vectors). Converged when every
  *   Ritz pair that can be kept has residual |H x - theta x| <= tol max|theta|
- *   (tol = 1e-6 with FP64 products, 1e-5 with tensor-core products), or when
- *   a round has stalled below 10 tol (less than a factor 2 better than the
- *   previous round: the rounding floor of the products, 1e-5..3e-5 at D = 7);
+ *   (tol = 1e-6 with FP64 products, 1e-5 with tensor-core products), or, with
+ *   tensor-core products, when a round has stalled below 10 tol (less than a
+ *   factor 2 better than the previous round: the rounding floor of the
+ *   products, 1e-5..3e-5 at D = 7);
  *   such a floor then serves as the tolerance of the following moves (times
  *   1.5) until a round gets below tol again. Otherwise, on the first move, or
  *   when the sector sizes cannot be carried over, the move falls back to
- *   HS_EIG_F32_PROJECTED. Kept vectors carry
+ *   HS_EIG_F32_PROJECTED. With tensor-core products, where the Cholesky-QR
+ *   of a filtered basis breaks down, the round is run again on a
+ *   Householder-QR basis instead. Kept
+ *   vectors carry
  *   a canonical sign (largest entry positive) so that the gauge, and with it
  *   the warm start, is stationary at the fixed point.
  * HS_EIG_SUBSPACE_ADAPTIVE: as HS_EIG_SUBSPACE, with the residual tolerance of

@@ -738,6 +738,34 @@ hs_status orthonormalise_rows(hs_ctx ctx, hs_precision prec, double* const X[2],
   return HS_OK;
 }
 
+// Orthonormal rows spanning the rows of Xsrc (stacked blocks, m_b x n_b
+// row-major, overwritten) into X, by Householder QR of each block (cuSOLVER
+// geqrf + orgqr on the column-major n_b x m_b view, whose Q is the row-major
+// m_b x n_b result). Backward stable for any conditioning, but about four
+// times the time of the Cholesky-QR pass on these shapes with GB300's FP64
+// rate, so it serves only where that pass broke down.
+hs_status orthonormalise_rows_qr(hs_ctx ctx, double* Xsrc, const int m[2], const int n[2], double* X) {
+  cudaStream_t s = ctx->stream;
+  HS_SOLVER(cusolverDnSetStream(ctx->solver, s));
+  const long long off1 = (long long)m[0] * n[0];
+  int* qinfo = static_cast<int*>(ctx->info.p) + 6;
+  for (int b = 0; b < 2; ++b) {
+    if (m[b] == 0) continue;
+    double* A = Xsrc + (b ? off1 : 0);
+    int lw1 = 0, lw2 = 0;
+    HS_TRY(ctx->lam.ensure(((size_t)m[b] + 1) * sizeof(double)));  // tau (the selection is rebuilt later)
+    double* tau = ctx->lam.d();
+    HS_SOLVER(cusolverDnDgeqrf_bufferSize(ctx->solver, n[b], m[b], A, n[b], &lw1));
+    HS_SOLVER(cusolverDnDorgqr_bufferSize(ctx->solver, n[b], m[b], m[b], A, n[b], tau, &lw2));
+    HS_TRY(ctx->solver_dev.ensure((size_t)std::max(std::max(lw1, lw2), 1) * sizeof(double)));
+    HS_SOLVER(cusolverDnDgeqrf(ctx->solver, n[b], m[b], A, n[b], tau, ctx->solver_dev.d(), std::max(lw1, 1), qinfo));
+    HS_SOLVER(cusolverDnDorgqr(ctx->solver, n[b], m[b], m[b], A, n[b], tau, ctx->solver_dev.d(), std::max(lw2, 1),
+                               qinfo + 1));
+    HS_CUDA(cudaMemcpyAsync(X + (b ? off1 : 0), A, (size_t)m[b] * n[b] * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  }
+  return HS_OK;
+}
+
 // C[M x N] = A[M x K] B[N x K]^T for dense FP64 row-major operands: on the
 // tensor cores (operands split into sx / sy) in the TF32/BF16 precisions,
 // with the FP64 kernel otherwise.
@@ -1196,6 +1224,7 @@ hs_status subspace_projector(hs_ctx ctx, hs_env* env, int chi, int n0, int n1, d
   float* hth = reinterpret_cast<float*>(hres + mt);
   int* hstat = reinterpret_cast<int*>(hth + mt);  // Jacobi status of both blocks, Cholesky status
   double prev_worst = INFINITY;
+  ctx->sx_save_valid = false;
   for (int it = 0; it < kMaxIt; ++it) {
     *iters = it + 1;
     // Z = X H (H symmetric), Rayleigh matrix B = X Z^T (symmetric); with
@@ -1270,6 +1299,20 @@ hs_status subspace_projector(hs_ctx ctx, hs_env* env, int chi, int n0, int n1, d
     HS_CUDA(cudaMemcpyAsync(hstat, ctx->info.p, 3 * sizeof(int), cudaMemcpyDeviceToHost, s));
     HS_CUDA(cudaStreamSynchronize(s));
     const int hbad = hstat[2];
+    if (hbad && tc && ctx->sx_save_valid && it + 1 < kMaxIt) {
+      // the last Cholesky-QR broke down (the filtered rows were numerically
+      // dependent): this round ran on a broken basis. Orthonormalise the
+      // rows it started from by Householder QR and run the round again.
+      // (Tensor-core products only: with FP64 products the fallback's FP32
+      // eigenvectors with two FP64 Loewdin steps are the more accurate
+      // projector, and that mode is about accuracy)
+      HS_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), s));
+      HS_TRY(orthonormalise_rows_qr(ctx, ctx->sx_save.d(), m, n, ctx->sx.d(0)));
+      ctx->sx_save_valid = false;
+      ctx->qr_redos += 1;
+      prev_worst = INFINITY;
+      continue;
+    }
     *reason = hbad ? 4 : 7;
     if (hbad || hstat[0] || hstat[1]) return HS_OK;  // fall back
     // the states the selection can keep: the chi largest |theta| across both
@@ -1303,7 +1346,8 @@ hs_status subspace_projector(hs_ctx ctx, hs_env* env, int chi, int n0, int n1, d
     // there (less than a factor 2 better than the previous round, within
     // kFloorMax) is accepted as converged, and the floor it found serves as
     // the tolerance of the next moves (times kFloorMargin)
-    const double kFloorMax = 10.0 * kTol, kFloorMargin = 1.5;
+    // (tensor-core products only: with FP64 products the floor lies below kTol)
+    const double kFloorMax = tc ? 10.0 * kTol : kTol, kFloorMargin = 1.5;
     const double accept = std::max(tol_move, std::min(kFloorMax, kFloorMargin * ctx->resid_floor));
     bool at_floor = false;
     if (worst > accept) {
@@ -1349,7 +1393,12 @@ hs_status subspace_projector(hs_ctx ctx, hs_env* env, int chi, int n0, int n1, d
     }
     {
       // far from convergence the rows can be far from orthogonal (the Loewdin
-      // iteration alone diverges there): Cholesky-QR first
+      // iteration alone diverges there): Cholesky-QR first, its input kept in
+      // case it breaks down
+      HS_TRY(ctx->sx_save.ensure((size_t)(mn0 + mn1 + 2) * sizeof(double)));
+      HS_CUDA(cudaMemcpyAsync(ctx->sx_save.d(), ctx->sx.d(0), (size_t)(mn0 + mn1) * sizeof(double),
+                              cudaMemcpyDeviceToDevice, s));
+      ctx->sx_save_valid = ctx->sx.d(1) == ctx->sx.d(0) + mn0;
       double* const Xo[2] = {ctx->sx.d(0), ctx->sx.d(1)};
       double* const Xco[2] = {ctx->sxc.d(0), ctx->sxc.d(1)};
       HS_TRY(orthonormalise_rows(ctx, prec, Xo, m, n, Xco, bad));
@@ -1439,7 +1488,7 @@ hs_status hs_destroy(hs_ctx ctx) {
   for (DBuf& b : ctx->zr) b.release();
   for (DBuf& b : ctx->zd) b.release();
   for (DBuf& b : ctx->d4) b.release();
-  for (DBuf* b : {&ctx->pt_prev, &ctx->ovl, &ctx->ovl_idx, &ctx->ovl_sgn, &ctx->pt_tmp}) b->release();
+  for (DBuf* b : {&ctx->pt_prev, &ctx->ovl, &ctx->ovl_idx, &ctx->ovl_sgn, &ctx->pt_tmp, &ctx->sx_save}) b->release();
   ctx->h_ovl.release();
   ctx->d4_h.release();
   if (ctx->gesvdj) cusolverDnDestroyGesvdjInfo(ctx->gesvdj);

@@ -209,6 +209,11 @@ struct hs_ctx_s {
   // the previous move's kept rows (final PT, both blocks stacked), for
   // ordering this move's kept rows like them (align_kept_rows)
   hs::DBuf pt_prev, ovl, ovl_idx, ovl_sgn, pt_tmp;
+  // the subspace rows before the last Cholesky-QR (for the Householder redo
+  // when that breaks down) and the count of such redos
+  hs::DBuf sx_save;
+  bool sx_save_valid = false;
+  long long qr_redos = 0;
   hs::PinnedBuf h_ovl;
   bool pt_prev_valid = false;
   int pt_prev_k[2] = {0, 0}, pt_prev_n[2] = {0, 0};
