@@ -92,6 +92,20 @@ def emit(obj):
     print(json.dumps(obj), flush=True)
 
 
+def replica_throughput(sec: float, steps: int, world: int, device) -> tuple[float, float]:
+    """Whole-job moves/s of `world` independent replicas (one per GPU, no exchange between them):
+    world * steps moves in the slowest rank's time, taken as the max over ranks after the timed
+    region. Returns (moves/s, seconds)."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([sec], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.barrier()
+        sec = float(t.item())
+    return world * steps / sec, sec
+
+
 def golden_snapshot(moves: int, k: int | None = None):
     path = os.path.join(ROOT, "tests", "golden", f"ctmrg_w{WORKLOAD if k is None else k}.json")
     try:
@@ -414,13 +428,7 @@ def run_ours(args):
         t_wall = time.perf_counter() - t_wall
     prof = L.hs_profile_read(ctx.handle)
     L.hs_profile_enable(ctx.handle, False)
-    sec = float(np.sum(ms)) / 1e3
-    if world > 1:
-        t = torch.tensor([sec], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        torch.distributed.barrier()
-        sec = float(t.item())
-    value = world * args.steps / sec
+    value, sec = replica_throughput(float(np.sum(ms)) / 1e3, args.steps, world, dev)
     ntr = min(4, args.steps)
     transient = ntr / (np.sum(ms[:ntr]) / 1e3)
     conv_timed = sum(1 for i in c.infos[args.warmup:] if i.get("flags", 0) & 2)

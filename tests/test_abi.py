@@ -65,3 +65,25 @@ def test_missing_library_fails_loudly(tmp_path):
             L.load(str(tmp_path / "nope.so"))
         finally:
             L._lib = saved
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """Every ctypes struct of the binding has the size and field offsets the C compiler gives the
+    struct of include/hs.h (tests/abi_layout.c, built with the host compiler)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no host C compiler")
+    here = os.path.dirname(os.path.abspath(__file__))
+    exe = str(tmp_path / "abi_layout")
+    subprocess.run([cc, "-std=c99", "-I", os.path.join(os.path.dirname(here), "include"),
+                    os.path.join(here, "abi_layout.c"), "-o", exe], check=True)
+    lines = subprocess.run([exe], check=True, capture_output=True, text=True).stdout.split("\n")
+    c_side = {ln.split()[0]: [int(x) for x in ln.split()[1:]] for ln in lines if ln.strip()}
+    structs = {"hs_z2_tensor": L.Z2Tensor, "hs_env": L.Env, "hs_move_info": L.MoveInfo,
+               "hs_hotrg_info": L.HotrgInfo, "hs_env4": L.Env4, "hs_move4_info": L.Move4Info}
+    for name, cls in structs.items():
+        size, *offsets = c_side[name]
+        assert ctypes.sizeof(cls) == size, name
+        assert [getattr(cls, f).offset for f, _ in cls._fields_] == offsets, name
