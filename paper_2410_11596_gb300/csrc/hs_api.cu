@@ -1234,7 +1234,10 @@ hs_status subspace_projector(hs_ctx ctx, hs_env* env, int chi, int n0, int n1, d
       HS_TRY(tc_split(ctx, prec, XL, XL, {0, 1}, ctx->sx.d(0), ctx->sx_hi, ctx->sx_lo));
       HS_TRY(tc_run(ctx, prec, XL, ctx->sx_hi, ctx->sx_lo, HL, ctx->sH_hi, ctx->sH_lo, XL, ctx->sz.d(0)));
       HS_TRY(tc_split(ctx, prec, XL, XL, {0, 1}, ctx->sz.d(0), ctx->sy_hi, ctx->sy_lo));
-      HS_TRY(tc_run(ctx, prec, XL, ctx->sx_hi, ctx->sx_lo, XL, ctx->sy_hi, ctx->sy_lo, BL, ctx->sbm.d(0)));
+      // the Rayleigh matrix straight in FP32, the Jacobi eigensolver's input
+      // (the tensor-core accumulators are FP32: nothing is lost)
+      HS_TRY(tc_run(ctx, prec, XL, ctx->sx_hi, ctx->sx_lo, XL, ctx->sy_hi, ctx->sy_lo, BL,
+                    reinterpret_cast<double*>(ctx->sbw.as<float>(0)), true));
       for (int b = 0; b < 2; ++b)
         ctx->phase_flops[HS_PHASE_GEMM_TC] += 2.0 * m[b] * (double)n[b] * n[b] + 2.0 * m[b] * (double)m[b] * n[b];
     } else {
@@ -1248,9 +1251,11 @@ hs_status subspace_projector(hs_ctx ctx, hs_env* env, int chi, int n0, int n1, d
       }
     }
     for (int b = 0; b < 2; ++b) *flops += 2.0 * m[b] * (double)n[b] * n[b];
-    HS_CUDA(launch_cast_f64_f32(ctx->sbm.d(0), ctx->sbw.as<float>(0),
-                                (long long)m[0] * m[0] + (long long)m[1] * m[1], s));
-    ctx->launches += 1;
+    if (!tc) {
+      HS_CUDA(launch_cast_f64_f32(ctx->sbm.d(0), ctx->sbw.as<float>(0),
+                                  (long long)m[0] * m[0] + (long long)m[1] * m[1], s));
+      ctx->launches += 1;
+    }
     {
       // Rayleigh-Ritz: both m x m FP32 problems by one-CTA Jacobi kernels
       PhaseScope ps(ctx, HS_PHASE_EIG);

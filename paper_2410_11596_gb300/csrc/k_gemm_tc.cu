@@ -667,9 +667,12 @@ bool make_map_cached(CUtensorMap* m, const void* base, int rows, int Kp, int eb)
 
 // Split-K sums of every split problem of one launch (blockIdx.y = problem),
 // partials added in split order (deterministic).
+// The partials are FP32 (each is one FP32 accumulator's sum, so FP32 storage
+// loses nothing and halves the epilogue's stores), rows padded to an even
+// length ldp for 8-byte stores; they are summed in FP64.
 struct SplitRed {
-  const double* part;
-  int nsplit, M, N, ldc;
+  const float* part;
+  int nsplit, M, N, ldc, ldp;
   double* c;
   int f32;  // write FP32 (c read as float*)
 };
@@ -680,16 +683,16 @@ struct SplitReds {
 __global__ void tc_splitk_reduce_kernel(const SplitReds reds) {
   hs_pdl_enter();
   const SplitRed& r = reds.r[blockIdx.y];
-  const long long mn = (long long)r.M * r.N;
+  const long long mn = (long long)r.M * r.N, stride = (long long)r.M * r.ldp;
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < mn;
        e += (long long)gridDim.x * blockDim.x) {
+    const long long row = e / r.N, col = e - row * r.N;
     double v = 0.0;
-    for (int s = 0; s < r.nsplit; ++s) v += r.part[s * mn + e];
-    const long long row = e / r.N;
+    for (int s = 0; s < r.nsplit; ++s) v += (double)r.part[s * stride + row * r.ldp + col];
     if (r.f32)
-      reinterpret_cast<float*>(r.c)[row * r.ldc + (e - row * r.N)] = (float)v;
+      reinterpret_cast<float*>(r.c)[row * r.ldc + col] = (float)v;
     else
-      r.c[row * r.ldc + (e - row * r.N)] = v;
+      r.c[row * r.ldc + col] = v;
   }
 }
 
@@ -723,6 +726,9 @@ cudaError_t run(const TcProblem* probs, int nprob, int* err, cudaStream_t s, dou
   SplitReds reds{};  // one reduction per split problem (at most one per operand pair)
   SplitRed* red = reds.r;
   int nred = 0;
+  // split-K partials in FP32 (part holds part_elems doubles = 2 part_elems floats)
+  float* partf = reinterpret_cast<float*>(part);
+  const long long part_felems = 2 * part_elems;
   long long part_used = 0;
   const int sms = device_sms();
   for (int i = 0; i < nprob; ++i) {
@@ -755,8 +761,8 @@ cudaError_t run(const TcProblem* probs, int nprob, int* err, cudaStream_t s, dou
       ns = (sms + ptiles - 1) / ptiles;
       ns = ns < ktiles / 4 ? ns : ktiles / 4;
       ns = ns < 16 ? ns : 16;
-      const long long need = (long long)ns * p.M * p.N;
-      if (ns < 2 || part_used + need > part_elems || g.n + ns > kMaxUnits) ns = 1;
+      const long long need = (long long)ns * p.M * ((p.N + 1) & ~1);
+      if (ns < 2 || part_used + need > part_felems || g.n + ns > kMaxUnits) ns = 1;
     }
     const int kper = (ktiles + ns - 1) / ns;
     ns = (ktiles + kper - 1) / kper;  // no empty K range
@@ -771,8 +777,10 @@ cudaError_t run(const TcProblem* probs, int nprob, int* err, cudaStream_t s, dou
       q.map = j;
       q.psi = psi;
       if (ns > 1) {
-        q.c = part + part_used + (long long)sidx * p.M * p.N;
-        q.ldc = p.N;
+        const int ldp = (p.N + 1) & ~1;
+        q.c = reinterpret_cast<double*>(partf + part_used + (long long)sidx * p.M * ldp);
+        q.ldc = ldp;
+        q.f32 = 1;
       } else {
         q.c = p.c;
         q.ldc = p.ldc;
@@ -784,8 +792,9 @@ cudaError_t run(const TcProblem* probs, int nprob, int* err, cudaStream_t s, dou
     }
     if (ns > 1) {
       if (nred >= kMaxPairs) return cudaErrorInvalidValue;
-      red[nred++] = {part + part_used, ns, p.M, p.N, p.ldc, p.c, p.out_f32};
-      part_used += (long long)ns * p.M * p.N;
+      const int ldp = (p.N + 1) & ~1;
+      red[nred++] = {partf + part_used, ns, p.M, p.N, p.ldc, ldp, p.c, p.out_f32};
+      part_used += (long long)ns * p.M * ldp;
     }
   }
   if (tiles == 0) return cudaSuccess;
