@@ -47,9 +47,9 @@ NCU_TRAFFIC = {
     # profiles/gemm_f64_d6_chi144.md: mean of the G3/G4/G5 launches
     "gemm_f64": {"bytes_per_launch": 143.3e6, "source_sha": "ac07f1d8a4d24d63"},
     # profiles/gemm_tc_tf32x3_d6_chi144.md: mean over the tensor-core launches of two steady-state moves
-    "gemm_tc_tf32x3": {"bytes_per_launch": 56.6e6, "source_sha": "15b12cce6367d12a"},
+    "gemm_tc_tf32x3": {"bytes_per_launch": 56.6e6, "source_sha": "c3b7279478e6ad5a"},
     # the same capture, mean over its split-output launches (G2-G5, the dominant kernel)
-    "gemm_tc_split_tf32x3": {"bytes_per_launch": 131.6e6, "source_sha": "15b12cce6367d12a"},
+    "gemm_tc_split_tf32x3": {"bytes_per_launch": 131.5e6, "source_sha": "c3b7279478e6ad5a"},
 }
 
 EIG_LABEL = {"f64": "FP64 syevd per parity block", "f32p": "FP32 syevd + FP64 Loewdin and projection",

@@ -1157,6 +1157,7 @@ hs_status subspace_projector(hs_ctx ctx, hs_env* env, int chi, int n0, int n1, d
   }
   int* bad = static_cast<int*>(ctx->info.p) + 2;
   HS_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), s));
+  HS_CUDA(cudaMemsetAsync(static_cast<int*>(ctx->info.p) + 6, 0, 2 * sizeof(int), s));  // Householder QR status
   HS_TRY(eig32_workspace(ctx, m[0] > m[1] ? m[0] : m[1]));
   // the selection issued by every round writes chi indices per block and chi values
   HS_TRY(ctx->idx.ensure(2 * (size_t)chi * sizeof(int)));
@@ -1219,7 +1220,7 @@ hs_status subspace_projector(hs_ctx ctx, hs_env* env, int chi, int n0, int n1, d
   // pinned read-back of the Ritz values, residuals and status words (a copy
   // into pageable memory would block the host before the stream drains)
   const int mt = m[0] + m[1];
-  HS_TRY(ctx->h_sub.ensure((size_t)mt * (sizeof(double) + sizeof(float)) + 4 * sizeof(int)));
+  HS_TRY(ctx->h_sub.ensure((size_t)mt * (sizeof(double) + sizeof(float)) + 8 * sizeof(int)));
   double* hres = static_cast<double*>(ctx->h_sub.p);
   float* hth = reinterpret_cast<float*>(hres + mt);
   int* hstat = reinterpret_cast<int*>(hth + mt);  // Jacobi status of both blocks, Cholesky status
@@ -1300,10 +1301,15 @@ hs_status subspace_projector(hs_ctx ctx, hs_env* env, int chi, int n0, int n1, d
     ctx->launches += 2;
     HS_CUDA(cudaMemcpyAsync(hth, th, (size_t)mt * sizeof(float), cudaMemcpyDeviceToHost, s));
     HS_CUDA(cudaMemcpyAsync(hres, ctx->sres.d(0), (size_t)mt * sizeof(double), cudaMemcpyDeviceToHost, s));
-    // info[0], info[1]: Jacobi status; info[2]: Cholesky status (bad)
-    HS_CUDA(cudaMemcpyAsync(hstat, ctx->info.p, 3 * sizeof(int), cudaMemcpyDeviceToHost, s));
+    // info[0], info[1]: Jacobi status; info[2]: Cholesky status (bad);
+    // info[6], info[7]: status of a Householder redo's geqrf, orgqr
+    HS_CUDA(cudaMemcpyAsync(hstat, ctx->info.p, 8 * sizeof(int), cudaMemcpyDeviceToHost, s));
     HS_CUDA(cudaStreamSynchronize(s));
     const int hbad = hstat[2];
+    if (hstat[6] != 0 || hstat[7] != 0) {  // a Householder redo reported an error: fall back
+      *reason = 4;
+      return HS_OK;
+    }
     if (hbad && tc && ctx->sx_save_valid && it + 1 < kMaxIt) {
       // the last Cholesky-QR broke down (the filtered rows were numerically
       // dependent): this round ran on a broken basis. Orthonormalise the

@@ -688,7 +688,13 @@ __global__ void tc_splitk_reduce_kernel(const SplitReds reds) {
        e += (long long)gridDim.x * blockDim.x) {
     const long long row = e / r.N, col = e - row * r.N;
     double v = 0.0;
-    for (int s = 0; s < r.nsplit; ++s) v += (double)r.part[s * stride + row * r.ldp + col];
+    for (int s = 0; s < r.nsplit; ++s) {
+      // widened on the bit pattern (the FP64 pipe, which a conversion would use, is GB300's scarce one)
+      const uint32_t x = __float_as_uint(r.part[s * stride + row * r.ldp + col]);
+      unsigned long long w;
+      if (!f32_widen_fast(x, w)) w = f64_bits((double)__uint_as_float(x));  // subnormal
+      v += f64_from_bits(w);
+    }
     if (r.f32)
       reinterpret_cast<float*>(r.c)[row * r.ldc + col] = (float)v;
     else
