@@ -77,6 +77,9 @@ def parse():
     p.add_argument("--profile-region", action="store_true",
                    help="profiling runs only: W warm-up moves, then K moves inside cudaProfilerStart/Stop "
                         "(for ncu --profile-from-start off); prints a short JSON line, no bench line")
+    p.add_argument("--profile-directional", action="store_true",
+                   help="profiling runs only: the directional CTMRG (D=4, chi=64, seeded asymmetric tensor, "
+                        "polar SVD), two sweeps, then one sweep inside cudaProfilerStart/Stop")
     p.add_argument("--basis", default="hermitian", choices=["hermitian", "dense"],
                    help="profiling runs only: the basis of the profiled moves")
     p.add_argument("--workload", type=int, default=WORKLOAD,
@@ -285,6 +288,26 @@ def timed_moves(torch, c, ctx, n, flush):
         e1.synchronize()
         ms.append(e0.elapsed_time(e1))
     return ms
+
+
+def run_profile_directional(args):
+    """One directional sweep (four moves) inside cudaProfilerStart/Stop, for ncu --profile-from-start off."""
+    import torch
+    from paper_2410_11596_gb300 import build, inputs, _lib as L
+    from paper_2410_11596_gb300.api import Context, DirectionalCTMRG
+    if not os.path.exists(L.LIB_PATH):
+        build.build()
+    ctx = Context(0)
+    A = inputs.asymmetric_ipeps(2, 4, inputs.SEED_BASE + 5204)
+    c = DirectionalCTMRG(ctx, A, 64, basis=args.basis, svd="polar")
+    c.run(2)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.start()
+    c.sweep()
+    torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
+    emit({"profile_directional": True, "D": 4, "chi": 64, "basis": args.basis, "svd": "polar",
+          "bonds": [c.bond(b) for b in range(4)]})
 
 
 def run_profile_region(args):
@@ -677,6 +700,8 @@ def main():
         run_reference(args)
     elif args.profile_region:
         run_profile_region(args)
+    elif args.profile_directional:
+        run_profile_directional(args)
     else:
         run_ours(args)
 
