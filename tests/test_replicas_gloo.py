@@ -26,7 +26,7 @@ def _rank(rank: int, world: int, port: int, out):
 
 def test_replica_throughput_two_ranks():
     world = 2
-    with mp.Manager() as m:
+    with mp.get_context("spawn").Manager() as m:
         out = m.dict()
         mp.spawn(_rank, args=(world, _free_port(), out), nprocs=world, join=True)
         res = dict(out)
