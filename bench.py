@@ -123,6 +123,15 @@ def golden_energy(moves: int, k: int | None = None):
     return None if snap is None else snap["energy"]
 
 
+def workload_name(k: int) -> str:
+    """The config.workload string of real workload k, the same on both arms."""
+    from paper_2410_11596_gb300 import inputs
+    w = inputs.WORKLOADS[k]
+    D = w["D"]
+    return (f"real C4v iPEPS d={w['d']} D={D} chi={w['chi']} (q={D * D}: {D * (D + 1) // 2} even/"
+            f"{D * (D - 1) // 2} odd), seeded N(0,1), D4-symmetrised, max|A|=1")
+
+
 def r3(x):
     """Rounded for the JSON line (3 significant digits)."""
     if x is None:
@@ -157,11 +166,19 @@ def oracle_moves(n: int, state=None):
     return ts, (oc, a, C, T, chi)
 
 
+def oracle_sample(n: int, warmup: int) -> str:
+    from paper_2410_11596_gb300 import inputs
+    w = inputs.WORKLOADS[WORKLOAD]
+    n_c = w["chi"] * w["D"] ** 2
+    return (f"{n} full-size oracle moves (D={w['D']}, chi={w['chi']}, C' {n_c}x{n_c} numpy eigh) after an "
+            f"untimed traced-boundary init, first move and {warmup} warm-up moves; numpy BLAS with its default "
+            "thread count")
+
+
 def cpu_baseline(n: int = 3):
     ts, _ = oracle_moves(n)
     return {"value": n / float(np.sum(ts)), "unit": "moves/s", "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"{n} full-size oracle moves (D=6, chi=144, C' 5184x5184 numpy eigh) after an untimed "
-                      "traced-boundary init and first move; numpy BLAS with its default thread count"}
+            "sample": oracle_sample(n, 0)}
 
 
 def run_reference(args):
@@ -182,10 +199,10 @@ def run_reference(args):
           "steps": steps, "warmup": warmup, "ms_per_step": 1e3 * sec / steps,
           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
           "data": "synthetic",
-          "config": {"workload": "real C4v iPEPS d=2 D=6 chi=144, seeded N(0,1), D4-symmetrised", "D": 6,
-                     "chi": 144, "path": "dense FP64 oracle (numpy eigh, tensordot) on host cores"},
+          "config": {"workload": workload_name(WORKLOAD), "basis": "dense (the oracle works in the plain basis)",
+                     "path": "dense FP64 oracle (numpy eigh, tensordot) on host cores"},
           "cpu_baseline": {"value": val, "unit": "moves/s", "cores": cores, "kind": "oracle",
-                           "sample": f"{steps} full-size oracle moves after {warmup} warm-up moves"},
+                           "sample": oracle_sample(steps, warmup)},
           "e2e": {"value": val, "unit": "moves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}})
 
 
@@ -672,8 +689,7 @@ def run_ours(args):
                           "subspace": " + subspace eig (f32 Ritz), f64 projection",
                           "adaptive": " + subspace eig (f32 Ritz, adaptive tolerance), f64 projection"}[args.eig],
                 "data": "synthetic",
-                "config": {"workload": "real C4v iPEPS d=2 D=6 chi=144 (q=36: 21 even/15 odd), seeded N(0,1), "
-                                       "D4-symmetrised, max|A|=1", "basis": "hermitian", "eig": EIG_LABEL[args.eig],
+                "config": {"workload": workload_name(WORKLOAD), "basis": "hermitian", "eig": EIG_LABEL[args.eig],
                            "l2": "flushed (512 MB write) between timed moves", "parallelism": f"replicas{world}",
                            "moves_timed": f"{args.warmup + 1}-{args.warmup + args.steps}"},
                 "table": table, "hotrg": hotrg, "directional": directional, "complex": cplx, "batched": batched,
