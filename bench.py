@@ -489,6 +489,7 @@ def run_ours(args):
         conv = int(sum(1 for i in c.infos[-nst:] if i.get("flags", 0) & 2))
         # the phase split from the next moves: the events between phases
         # cost time of their own, so they stay out of the timed moves above
+        L.hs_profile_phases(ctx.handle, None)
         L.hs_profile_enable(ctx.handle, True)
         msp = timed_moves(torch, c, ctx, nst, flush)
         ps = L.hs_profile_read(ctx.handle)
