@@ -1,0 +1,82 @@
+// Host dump of the permute plan's element map: for each case read from
+// stdin, build make_perm_plan(in, out, perm) and print, for every element of
+// the input matrix (flat index in its block storage), the flat index its
+// boxes send it to in the output matrix (-1 if no box covers it). The test
+// compares the map with the one the block layout's definition gives.
+//
+// A case is one line of integers:
+//   kr kc  e_0 o_0 ... e_{n-1} o_{n-1}  kr_out  perm_0 ... perm_{n-1}  pad_out
+// n = kr + kc legs; the input's first kr legs are its rows, the output's leg
+// j is input leg perm[j] and its first kr_out legs are its rows.
+#include <cstdio>
+#include <vector>
+#include "hs_internal.cuh"
+
+using namespace hs;
+
+static Fused group(const Sect* s, int k) {
+  Fused f = fused0();
+  f.k = k;
+  for (int j = 0; j < k; ++j) f.leg[j] = s[j];
+  return f;
+}
+
+int main() {
+  int kr, kc;
+  while (std::scanf("%d %d", &kr, &kc) == 2) {
+    const int n = kr + kc;
+    if (kr < 1 || kc < 1 || kr > kMaxFused || kc > kMaxFused || n > kMaxLegs) {
+      std::printf("bad case\n");
+      return 1;
+    }
+    Sect s[kMaxLegs], so[kMaxLegs];
+    for (int j = 0; j < n; ++j)
+      if (std::scanf("%d %d", &s[j].n[0], &s[j].n[1]) != 2) return 1;
+    int kro, perm[kMaxLegs] = {0, 0, 0, 0, 0, 0}, pad;
+    if (std::scanf("%d", &kro) != 1) return 1;
+    for (int j = 0; j < n; ++j)
+      if (std::scanf("%d", &perm[j]) != 1 || perm[j] < 0 || perm[j] >= n) return 1;
+    if (std::scanf("%d", &pad) != 1) return 1;
+    if (kro < 1 || n - kro < 1 || kro > kMaxFused || n - kro > kMaxFused) {
+      std::printf("bad case\n");
+      return 1;
+    }
+    for (int j = 0; j < n; ++j) so[j] = s[perm[j]];
+    Z2Mat in, out;
+    in.r = group(s, kr);
+    in.c = group(s + kr, kc);
+    in.pad = 1;
+    out.r = group(so, kro);
+    out.c = group(so + kro, n - kro);
+    out.pad = pad;
+    const PermPlan plan = make_perm_plan(in, out, perm);
+    std::vector<long long> map(z2_elems(in), -1);
+    const long long nout = z2_elems(out);
+    bool inside = true;
+    for (int b = 0; b < plan.nbox; ++b) {
+      const Box& x = plan.box[b];
+      for (long long e = 0; e < x.count; ++e) {
+        long long rem = e, i = x.in_off, o = x.out_off;
+        for (int j = kMaxLegs - 1; j >= 0; --j) {
+          const long long t = rem % x.dim[j];
+          rem /= x.dim[j];
+          i += t * x.in_stride[j];
+          o += t * x.out_stride[j];
+        }
+        if (i < 0 || i >= (long long)map.size() || o < 0 || o >= nout) {
+          inside = false;
+          continue;
+        }
+        map[i] = o;
+      }
+    }
+    if (!inside) {
+      std::printf("out of range\n");
+      return 1;
+    }
+    std::printf("%lld %lld", (long long)map.size(), nout);
+    for (long long v : map) std::printf(" %lld", v);
+    std::printf("\n");
+  }
+  return 0;
+}

@@ -1,0 +1,166 @@
+"""Host check of the Z2 permute plan (the block bookkeeping behind every leg permutation): the boxes
+that make_perm_plan builds must send each element of the input's block storage to the position
+the sector-ordered block layout gives it in the output (tests/perm_plan_check.cu prints the plan's
+map; the expected map is computed here from the layout's definition).
+
+The layout (Sec. II.B: a Z2-symmetric tensor is block diagonal in the parity of its fused legs):
+a fused group of legs enumerates its parity tuples grouped by total parity, even group first,
+tuples in lexicographic order, local indices row-major inside a tuple; block p holds the rows of
+parity p times the columns of parity p, row-major, rows padded to `pad` elements, block 0 first."""
+import itertools
+import os
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+from paper_2410_11596_gb300 import _lib as L, build
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+CSRC = os.path.join(HERE, "..", "paper_2410_11596_gb300", "csrc")
+
+
+def _group_index(sects, idx):
+    """(parity, position in its parity group) of the leg indices idx of one fused group."""
+    bits = [int(i >= e) for (e, _), i in zip(sects, idx)]
+    loc = [i - b * e for (e, _), i, b in zip(sects, idx, bits)]
+    par = sum(bits) % 2
+    off = 0
+    for t in itertools.product((0, 1), repeat=len(sects)):
+        if sum(t) % 2 != par:
+            continue
+        if list(t) == bits:
+            break
+        off += int(np.prod([s[b] for s, b in zip(sects, t)]))
+    ext = [s[b] for s, b in zip(sects, bits)]
+    return par, off + int(np.ravel_multi_index(loc, ext)) if ext else off
+
+
+def _group_size(sects, par):
+    return sum(int(np.prod([s[b] for s, b in zip(sects, t)]))
+               for t in itertools.product((0, 1), repeat=len(sects)) if sum(t) % 2 == par)
+
+
+def _flat(rows, cols, pad, idx):
+    """Flat position of the element with leg indices idx in the block storage, or None if its
+    total parity is odd (no such block)."""
+    pr, ri = _group_index(rows, idx[:len(rows)])
+    pc, ci = _group_index(cols, idx[len(rows):])
+    if pr != pc:
+        return None
+    ld = [-(-_group_size(cols, p) // pad) * pad for p in (0, 1)]
+    off = 0 if pr == 0 else _group_size(rows, 0) * ld[0]
+    return off + ri * ld[pr] + ci
+
+
+def _elems(rows, cols, pad):
+    return sum(_group_size(rows, p) * (-(-_group_size(cols, p) // pad) * pad) for p in (0, 1))
+
+
+def _expected(kr, sects, kro, perm, pad):
+    rows, cols = sects[:kr], sects[kr:]
+    so = [sects[p] for p in perm]
+    orows, ocols = so[:kro], so[kro:]
+    m = np.full(_elems(rows, cols, 1), -1, dtype=np.int64)
+    for idx in itertools.product(*[range(e + o) for e, o in sects]):
+        fi = _flat(rows, cols, 1, idx)
+        if fi is None:
+            continue
+        m[fi] = _flat(orows, ocols, pad, [idx[p] for p in perm])
+    return m, _elems(orows, ocols, pad)
+
+
+# (kr, sectors, kr_out, perm, pad_out). The permutations of the C4v and directional moves
+# ([(a, x) | (y, b)] -> [(a, b) | (y, x)], [(a, b) | (d, r)] -> [(a, d) | (b, r)], the transposes,
+# the edge's [(b, x) | a] -> [(x, a) | b], the split operands' padded rows); empty odd sectors
+# (D = 1, a boundary with no odd states) and empty even ones; three- to six-leg groupings.
+CASES = [
+    (2, [(3, 2), (2, 1), (2, 1), (3, 2)], 2, [0, 3, 2, 1], 1),
+    (2, [(3, 2), (2, 1), (2, 1), (3, 2)], 2, [0, 2, 1, 3], 1),
+    (2, [(3, 2), (2, 1), (3, 2), (2, 1)], 2, [2, 3, 0, 1], 1),
+    (2, [(3, 2), (2, 1), (3, 2), (2, 1)], 2, [0, 3, 1, 2], 32),
+    (1, [(4, 3), (5, 2)], 1, [1, 0], 1),
+    (2, [(4, 3), (3, 1), (4, 3)], 2, [1, 2, 0], 1),
+    (2, [(4, 3), (3, 1), (4, 3)], 1, [0, 2, 1], 32),
+    (2, [(3, 0), (1, 0), (1, 0), (3, 0)], 2, [0, 3, 2, 1], 1),
+    (2, [(2, 2), (3, 0), (3, 0), (2, 2)], 2, [0, 2, 1, 3], 32),
+    (2, [(0, 3), (2, 1), (2, 1), (0, 3)], 2, [2, 3, 0, 1], 1),
+    (1, [(6, 0), (6, 0)], 1, [1, 0], 32),
+    (3, [(2, 1), (1, 2), (2, 2), (1, 1), (2, 1)], 2, [4, 0, 3, 1, 2], 1),
+    (3, [(2, 1), (1, 1), (2, 1), (1, 2), (1, 1), (2, 1)], 3, [5, 4, 3, 2, 1, 0], 1),
+    (2, [(2, 1), (1, 1), (2, 1), (1, 2), (1, 1), (2, 1)], 4, [1, 3, 5, 0, 2, 4], 32),
+]
+
+
+def _random_cases(n, seed):
+    rng = np.random.default_rng(seed)
+    out = []
+    while len(out) < n:
+        legs = int(rng.integers(2, 7))
+        kr = int(rng.integers(1, min(legs - 1, 4) + 1))
+        if legs - kr > 4:
+            continue
+        kro = int(rng.integers(1, min(legs - 1, 4) + 1))
+        if legs - kro > 4:
+            continue
+        sects = [(int(rng.integers(0, 4)), int(rng.integers(0, 3))) for _ in range(legs)]
+        if any(e + o == 0 for e, o in sects):
+            continue
+        out.append((kr, sects, kro, [int(x) for x in rng.permutation(legs)], int(rng.choice([1, 4, 32]))))
+    return out
+
+
+@pytest.fixture(scope="module")
+def exe(tmp_path_factory):
+    nvcc = shutil.which("nvcc") or ("/usr/local/cuda/bin/nvcc" if os.path.exists("/usr/local/cuda/bin/nvcc") else None)
+    if nvcc is None:
+        pytest.skip("no nvcc")
+    if not os.path.exists(L.LIB_PATH) or any(
+            os.path.getmtime(s) > os.path.getmtime(L.LIB_PATH) for s in build.sources()):
+        build.build()
+    libdir = os.path.dirname(L.LIB_PATH)
+    path = tmp_path_factory.mktemp("perm") / "perm_plan_check"
+    subprocess.run([nvcc, "-std=c++17", "-I", CSRC, os.path.join(HERE, "perm_plan_check.cu"), "-o", str(path),
+                    "-L", libdir, "-lhs", "-Xlinker", "-rpath=" + libdir], check=True, capture_output=True)
+    return path
+
+
+def _plan_maps(exe, cases):
+    text = "".join(f"{kr} {len(s) - kr} " + " ".join(f"{e} {o}" for e, o in s) + f" {kro} " +
+                   " ".join(map(str, perm)) + f" {pad}\n" for kr, s, kro, perm, pad in cases)
+    out = subprocess.run([str(exe)], input=text, capture_output=True, text=True, timeout=300)
+    assert out.returncode == 0, out.stdout[-500:] + out.stderr
+    lines = out.stdout.splitlines()
+    assert len(lines) == len(cases)
+    maps = []
+    for line in lines:
+        v = np.array(line.split(), dtype=np.int64)
+        maps.append((v[2:], int(v[1])))
+        assert len(v) - 2 == v[0]
+    return maps
+
+
+@pytest.mark.parametrize("which", ["move_layouts", "random"])
+def test_perm_plan_matches_the_block_layout(exe, which):
+    cases = CASES if which == "move_layouts" else _random_cases(60, 11596)
+    for case, (got, nout) in zip(cases, _plan_maps(exe, cases)):
+        want, nout_want = _expected(*case)
+        assert nout == nout_want, case
+        np.testing.assert_array_equal(got, want, err_msg=str(case))
+        # a bijection onto the output's non-padding entries
+        assert len(np.unique(got)) == len(got) and (got >= 0).all(), case
+
+
+def test_expected_map_on_a_hand_example():
+    """The layout definition itself on a two-leg matrix small enough to write out: legs (2 even,
+    1 odd) x (1 even, 1 odd). Block 0 = rows {e0, e1} x cols {e0}; block 1 = row {o0} x col {o0};
+    the transpose sends (r, c) to (c, r)."""
+    want, n = _expected(1, [(2, 1), (1, 1)], 1, [1, 0], 1)
+    # input storage: [ (e0,e0), (e1,e0) | (o0,o0) ]; output (transposed) storage:
+    # block 0 = row e0 x cols {e0, e1}: [(e0,e0), (e0,e1)], block 1 = [(o0,o0)]
+    assert n == 3
+    assert list(want) == [0, 1, 2]
+    want, n = _expected(1, [(2, 1), (1, 1)], 1, [1, 0], 4)
+    assert n == 4 + 4       # each block's row padded to 4
+    assert list(want) == [0, 1, 4]
