@@ -1,13 +1,15 @@
-// Host dump of the permute plan's element map: for each case read from
-// stdin, build make_perm_plan(in, out, perm) and print, for every element of
-// the input matrix (flat index in its block storage), the flat index its
-// boxes send it to in the output matrix (-1 if no box covers it). The test
-// compares the map with the one the block layout's definition gives.
+// Host dump of the permute plans' element maps: for each case read from
+// stdin, build the plan (make_perm_plan for Z2 block matrices,
+// make_graded_perm_plan for graded ones) and print, for every element of the
+// input matrix (flat index in its storage), the flat index its boxes send it
+// to in the output matrix (-1 if no box covers it). The test compares the
+// map with the one the layout's definition gives.
 //
 // A case is one line of integers:
-//   kr kc  e_0 o_0 ... e_{n-1} o_{n-1}  kr_out  perm_0 ... perm_{n-1}  pad_out
-// n = kr + kc legs; the input's first kr legs are its rows, the output's leg
-// j is input leg perm[j] and its first kr_out legs are its rows.
+//   mode kr kc  e_0 o_0 ... e_{n-1} o_{n-1}  kr_out  perm_0 ... perm_{n-1}  pad_out
+// mode 0: Z2 block matrices, 1: graded matrices; n = kr + kc legs; the
+// input's first kr legs are its rows, the output's leg j is input leg
+// perm[j] and its first kr_out legs are its rows.
 #include <cstdio>
 #include <vector>
 #include "hs_internal.cuh"
@@ -22,8 +24,8 @@ static Fused group(const Sect* s, int k) {
 }
 
 int main() {
-  int kr, kc;
-  while (std::scanf("%d %d", &kr, &kc) == 2) {
+  int mode, kr, kc;
+  while (std::scanf("%d %d %d", &mode, &kr, &kc) == 3) {
     const int n = kr + kc;
     if (kr < 1 || kc < 1 || kr > kMaxFused || kc > kMaxFused || n > kMaxLegs) {
       std::printf("bad case\n");
@@ -42,16 +44,35 @@ int main() {
       return 1;
     }
     for (int j = 0; j < n; ++j) so[j] = s[perm[j]];
-    Z2Mat in, out;
-    in.r = group(s, kr);
-    in.c = group(s + kr, kc);
-    in.pad = 1;
-    out.r = group(so, kro);
-    out.c = group(so + kro, n - kro);
-    out.pad = pad;
-    const PermPlan plan = make_perm_plan(in, out, perm);
-    std::vector<long long> map(z2_elems(in), -1);
-    const long long nout = z2_elems(out);
+    PermPlan plan{};
+    long long nin, nout;
+    if (mode == 0) {
+      Z2Mat in, out;
+      in.r = group(s, kr);
+      in.c = group(s + kr, kc);
+      in.pad = 1;
+      out.r = group(so, kro);
+      out.c = group(so + kro, n - kro);
+      out.pad = pad;
+      plan = make_perm_plan(in, out, perm);
+      nin = z2_elems(in);
+      nout = z2_elems(out);
+    } else {
+      GMat in, out;
+      in.r = group(s, kr);
+      in.c = group(s + kr, kc);
+      in.pad = 1;
+      out.r = group(so, kro);
+      out.c = group(so + kro, n - kro);
+      out.pad = pad;
+      if (!make_graded_perm_plan(in, out, perm, &plan)) {
+        std::printf("unsupported\n");
+        continue;
+      }
+      nin = g_elems(in);
+      nout = g_elems(out);
+    }
+    std::vector<long long> map(nin, -1);
     bool inside = true;
     for (int b = 0; b < plan.nbox; ++b) {
       const Box& x = plan.box[b];

@@ -1,12 +1,15 @@
-"""Host check of the Z2 permute plan (the block bookkeeping behind every leg permutation): the boxes
-that make_perm_plan builds must send each element of the input's block storage to the position
-the sector-ordered block layout gives it in the output (tests/perm_plan_check.cu prints the plan's
-map; the expected map is computed here from the layout's definition).
+"""Host check of the permute plans (the block bookkeeping behind every leg permutation): the boxes
+that make_perm_plan (Z2 block matrices) and make_graded_perm_plan (graded matrices of complex
+tensors) build must send each element of the input's storage to the position the layout gives it
+in the output (tests/perm_plan_check.cu prints a plan's map; the expected map is computed here
+from the layout's definition).
 
-The layout (Sec. II.B: a Z2-symmetric tensor is block diagonal in the parity of its fused legs):
-a fused group of legs enumerates its parity tuples grouped by total parity, even group first,
-tuples in lexicographic order, local indices row-major inside a tuple; block p holds the rows of
-parity p times the columns of parity p, row-major, rows padded to `pad` elements, block 0 first."""
+The layouts. A fused group of legs enumerates its parity tuples grouped by total parity, even
+group first, tuples in lexicographic order, local indices row-major inside a tuple. Z2 block
+matrix (Sec. II.B: a Z2-symmetric tensor is block diagonal in the parity of its fused legs):
+block p holds the rows of parity p times the columns of parity p, row-major, rows padded to `pad`
+elements, block 0 first. Graded matrix (Sec. II.C): all rows times all columns, each in that
+order, as one dense row-major matrix with rows padded to `pad` elements."""
 import itertools
 import os
 import shutil
@@ -58,46 +61,78 @@ def _elems(rows, cols, pad):
     return sum(_group_size(rows, p) * (-(-_group_size(cols, p) // pad) * pad) for p in (0, 1))
 
 
-def _expected(kr, sects, kro, perm, pad):
+def _graded_ld(cols, pad):
+    return -(-(_group_size(cols, 0) + _group_size(cols, 1)) // pad) * pad
+
+
+def _graded_flat(rows, cols, pad, idx):
+    """Flat position of the element with leg indices idx in a graded matrix."""
+    pr, ri = _group_index(rows, idx[:len(rows)])
+    pc, ci = _group_index(cols, idx[len(rows):])
+    r = (_group_size(rows, 0) if pr else 0) + ri
+    c = (_group_size(cols, 0) if pc else 0) + ci
+    return r * _graded_ld(cols, pad) + c
+
+
+def _graded_elems(rows, cols, pad):
+    return (_group_size(rows, 0) + _group_size(rows, 1)) * _graded_ld(cols, pad)
+
+
+def _expected(mode, kr, sects, kro, perm, pad):
     rows, cols = sects[:kr], sects[kr:]
     so = [sects[p] for p in perm]
     orows, ocols = so[:kro], so[kro:]
-    m = np.full(_elems(rows, cols, 1), -1, dtype=np.int64)
+    flat, elems = (_flat, _elems) if mode == 0 else (_graded_flat, _graded_elems)
+    m = np.full(elems(rows, cols, 1), -1, dtype=np.int64)
     for idx in itertools.product(*[range(e + o) for e, o in sects]):
-        fi = _flat(rows, cols, 1, idx)
+        fi = flat(rows, cols, 1, idx)
         if fi is None:
             continue
-        m[fi] = _flat(orows, ocols, pad, [idx[p] for p in perm])
-    return m, _elems(orows, ocols, pad)
+        m[fi] = flat(orows, ocols, pad, [idx[p] for p in perm])
+    return m, elems(orows, ocols, pad)
 
 
-# (kr, sectors, kr_out, perm, pad_out). The permutations of the C4v and directional moves
-# ([(a, x) | (y, b)] -> [(a, b) | (y, x)], [(a, b) | (d, r)] -> [(a, d) | (b, r)], the transposes,
-# the edge's [(b, x) | a] -> [(x, a) | b], the split operands' padded rows); empty odd sectors
-# (D = 1, a boundary with no odd states) and empty even ones; three- to six-leg groupings.
+# (mode, kr, sectors, kr_out, perm, pad_out); mode 0: Z2 block matrices. The permutations of the
+# C4v and directional moves ([(a, x) | (y, b)] -> [(a, b) | (y, x)], [(a, b) | (d, r)] ->
+# [(a, d) | (b, r)], the transposes, the edge's [(b, x) | a] -> [(x, a) | b], the split operands'
+# padded rows); empty odd sectors (D = 1, a boundary with no odd states) and empty even ones;
+# three- to six-leg groupings.
 CASES = [
-    (2, [(3, 2), (2, 1), (2, 1), (3, 2)], 2, [0, 3, 2, 1], 1),
-    (2, [(3, 2), (2, 1), (2, 1), (3, 2)], 2, [0, 2, 1, 3], 1),
-    (2, [(3, 2), (2, 1), (3, 2), (2, 1)], 2, [2, 3, 0, 1], 1),
-    (2, [(3, 2), (2, 1), (3, 2), (2, 1)], 2, [0, 3, 1, 2], 32),
-    (1, [(4, 3), (5, 2)], 1, [1, 0], 1),
-    (2, [(4, 3), (3, 1), (4, 3)], 2, [1, 2, 0], 1),
-    (2, [(4, 3), (3, 1), (4, 3)], 1, [0, 2, 1], 32),
-    (2, [(3, 0), (1, 0), (1, 0), (3, 0)], 2, [0, 3, 2, 1], 1),
-    (2, [(2, 2), (3, 0), (3, 0), (2, 2)], 2, [0, 2, 1, 3], 32),
-    (2, [(0, 3), (2, 1), (2, 1), (0, 3)], 2, [2, 3, 0, 1], 1),
-    (1, [(6, 0), (6, 0)], 1, [1, 0], 32),
-    (3, [(2, 1), (1, 2), (2, 2), (1, 1), (2, 1)], 2, [4, 0, 3, 1, 2], 1),
-    (3, [(2, 1), (1, 1), (2, 1), (1, 2), (1, 1), (2, 1)], 3, [5, 4, 3, 2, 1, 0], 1),
-    (2, [(2, 1), (1, 1), (2, 1), (1, 2), (1, 1), (2, 1)], 4, [1, 3, 5, 0, 2, 4], 32),
+    (0, 2, [(3, 2), (2, 1), (2, 1), (3, 2)], 2, [0, 3, 2, 1], 1),
+    (0, 2, [(3, 2), (2, 1), (2, 1), (3, 2)], 2, [0, 2, 1, 3], 1),
+    (0, 2, [(3, 2), (2, 1), (3, 2), (2, 1)], 2, [2, 3, 0, 1], 1),
+    (0, 2, [(3, 2), (2, 1), (3, 2), (2, 1)], 2, [0, 3, 1, 2], 32),
+    (0, 1, [(4, 3), (5, 2)], 1, [1, 0], 1),
+    (0, 2, [(4, 3), (3, 1), (4, 3)], 2, [1, 2, 0], 1),
+    (0, 2, [(4, 3), (3, 1), (4, 3)], 1, [0, 2, 1], 32),
+    (0, 2, [(3, 0), (1, 0), (1, 0), (3, 0)], 2, [0, 3, 2, 1], 1),
+    (0, 2, [(2, 2), (3, 0), (3, 0), (2, 2)], 2, [0, 2, 1, 3], 32),
+    (0, 2, [(0, 3), (2, 1), (2, 1), (0, 3)], 2, [2, 3, 0, 1], 1),
+    (0, 1, [(6, 0), (6, 0)], 1, [1, 0], 32),
+    (0, 3, [(2, 1), (1, 2), (2, 2), (1, 1), (2, 1)], 2, [4, 0, 3, 1, 2], 1),
+    (0, 3, [(2, 1), (1, 1), (2, 1), (1, 2), (1, 1), (2, 1)], 3, [5, 4, 3, 2, 1, 0], 1),
+    (0, 2, [(2, 1), (1, 1), (2, 1), (1, 2), (1, 1), (2, 1)], 4, [1, 3, 5, 0, 2, 4], 32),
 ]
 
 
-def _random_cases(n, seed):
+# Graded matrices (mode 1, at most five legs): the complex path's permutations of the corner and
+# edge chains, with empty and uneven sectors.
+GRADED_CASES = [
+    (1, 2, [(3, 2), (2, 1), (2, 1), (3, 2)], 2, [0, 3, 2, 1], 1),
+    (1, 2, [(3, 2), (2, 1), (3, 2), (2, 1)], 2, [0, 2, 1, 3], 32),
+    (1, 2, [(4, 3), (3, 1), (4, 3)], 2, [1, 2, 0], 1),
+    (1, 2, [(4, 3), (3, 1), (4, 3)], 1, [2, 0, 1], 32),
+    (1, 1, [(4, 3), (5, 2)], 1, [1, 0], 1),
+    (1, 2, [(3, 0), (2, 1), (2, 1), (3, 0)], 2, [2, 3, 0, 1], 1),
+    (1, 3, [(2, 1), (1, 2), (2, 2), (1, 1), (2, 1)], 2, [4, 0, 3, 1, 2], 32),
+]
+
+
+def _random_cases(n, seed, mode=0, max_legs=6):
     rng = np.random.default_rng(seed)
     out = []
     while len(out) < n:
-        legs = int(rng.integers(2, 7))
+        legs = int(rng.integers(2, max_legs + 1))
         kr = int(rng.integers(1, min(legs - 1, 4) + 1))
         if legs - kr > 4:
             continue
@@ -107,7 +142,7 @@ def _random_cases(n, seed):
         sects = [(int(rng.integers(0, 4)), int(rng.integers(0, 3))) for _ in range(legs)]
         if any(e + o == 0 for e, o in sects):
             continue
-        out.append((kr, sects, kro, [int(x) for x in rng.permutation(legs)], int(rng.choice([1, 4, 32]))))
+        out.append((mode, kr, sects, kro, [int(x) for x in rng.permutation(legs)], int(rng.choice([1, 4, 32]))))
     return out
 
 
@@ -127,23 +162,25 @@ def exe(tmp_path_factory):
 
 
 def _plan_maps(exe, cases):
-    text = "".join(f"{kr} {len(s) - kr} " + " ".join(f"{e} {o}" for e, o in s) + f" {kro} " +
-                   " ".join(map(str, perm)) + f" {pad}\n" for kr, s, kro, perm, pad in cases)
+    text = "".join(f"{mode} {kr} {len(s) - kr} " + " ".join(f"{e} {o}" for e, o in s) + f" {kro} " +
+                   " ".join(map(str, perm)) + f" {pad}\n" for mode, kr, s, kro, perm, pad in cases)
     out = subprocess.run([str(exe)], input=text, capture_output=True, text=True, timeout=300)
     assert out.returncode == 0, out.stdout[-500:] + out.stderr
     lines = out.stdout.splitlines()
     assert len(lines) == len(cases)
     maps = []
     for line in lines:
+        assert line != "unsupported"
         v = np.array(line.split(), dtype=np.int64)
         maps.append((v[2:], int(v[1])))
         assert len(v) - 2 == v[0]
     return maps
 
 
-@pytest.mark.parametrize("which", ["move_layouts", "random"])
+@pytest.mark.parametrize("which", ["move_layouts", "random", "graded", "graded_random"])
 def test_perm_plan_matches_the_block_layout(exe, which):
-    cases = CASES if which == "move_layouts" else _random_cases(60, 11596)
+    cases = {"move_layouts": CASES, "random": _random_cases(60, 11596), "graded": GRADED_CASES,
+             "graded_random": _random_cases(40, 11597, mode=1, max_legs=5)}[which]
     for case, (got, nout) in zip(cases, _plan_maps(exe, cases)):
         want, nout_want = _expected(*case)
         assert nout == nout_want, case
@@ -156,11 +193,11 @@ def test_expected_map_on_a_hand_example():
     """The layout definition itself on a two-leg matrix small enough to write out: legs (2 even,
     1 odd) x (1 even, 1 odd). Block 0 = rows {e0, e1} x cols {e0}; block 1 = row {o0} x col {o0};
     the transpose sends (r, c) to (c, r)."""
-    want, n = _expected(1, [(2, 1), (1, 1)], 1, [1, 0], 1)
+    want, n = _expected(0, 1, [(2, 1), (1, 1)], 1, [1, 0], 1)
     # input storage: [ (e0,e0), (e1,e0) | (o0,o0) ]; output (transposed) storage:
     # block 0 = row e0 x cols {e0, e1}: [(e0,e0), (e0,e1)], block 1 = [(o0,o0)]
     assert n == 3
     assert list(want) == [0, 1, 2]
-    want, n = _expected(1, [(2, 1), (1, 1)], 1, [1, 0], 4)
+    want, n = _expected(0, 1, [(2, 1), (1, 1)], 1, [1, 0], 4)
     assert n == 4 + 4       # each block's row padded to 4
     assert list(want) == [0, 1, 4]
