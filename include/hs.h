@@ -237,7 +237,8 @@ int hs_abi_version(void);
 hs_status hs_make_double_layer(hs_ctx ctx, const double* A, int d, int D, hs_dtype dtype,
                                double* a_out);
 
-/* Bytes of an hs_z2_tensor for bond dimension D in the given basis. */
+/* Bytes of an hs_z2_tensor for bond dimension D in the given basis; 0 when D < 1 or dtype is
+ * neither HS_F64 nor HS_C128. */
 size_t hs_z2_tensor_bytes(int D, hs_basis basis, hs_dtype dtype);
 
 /* Rotate a dense double layer (layout of hs_make_double_layer, device) into
@@ -400,7 +401,8 @@ hs_status hs_env4_to_dense(hs_ctx ctx, const hs_env4* env, double* const* C_dens
 
 /* ---- HOTRG (Sec. II.A, Ref. xie12) ------------------------------------ */
 
-/* Bytes of a HOTRG tensor buffer for bond dimension D and chi: max(D^2, chi)^4 doubles. */
+/* Bytes of a HOTRG tensor buffer for bond dimension D and chi: max(D^2, chi)^4 doubles; 0 when
+ * D < 1 or chi < 1. */
 size_t hs_hotrg_tensor_bytes(int D, int chi);
 
 /* Start a HOTRG run: copy the double layer a (FSO) into t (caller-owned,

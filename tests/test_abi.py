@@ -87,3 +87,40 @@ def test_struct_layouts_match_the_header(tmp_path):
         size, *offsets = c_side[name]
         assert ctypes.sizeof(cls) == size, name
         assert [getattr(cls, f).offset for f, _ in cls._fields_] == offsets, name
+
+
+def _zero_args(argtypes):
+    out = []
+    for a in argtypes:
+        if a in (ctypes.c_int, ctypes.c_uint, ctypes.c_long, ctypes.c_ulong):
+            out.append(0)
+        elif a is ctypes.c_double:
+            out.append(0.0)
+        else:
+            out.append(None)
+    return out
+
+
+def test_null_context_is_an_error_not_a_crash(lib):
+    """Every call that takes a context, given a null context (and null buffers, zero sizes),
+    returns HS_ERR_INVALID_ARG and leaves a message, before touching any device state; the calls
+    without a context reject null output pointers and empty batches the same way."""
+    taking_ctx = [n for n, (_, args) in L._PROTOS.items() if args and args[0] is ctypes.c_void_p
+                  and n not in ("hs_destroy",)]
+    assert len(taking_ctx) >= 24
+    for name in taking_ctx:
+        _, args = L._PROTOS[name]
+        assert getattr(lib, name)(*_zero_args(args)) == -1, name
+        assert "null context" in lib.hs_last_error().decode(), name
+    for name, msg in (("hs_create", "null output pointer"), ("hs_ctmrg_move_batched", "bad arguments"),
+                      ("hs_workspace_query", "bad arguments"), ("hs_env_bytes", "bad arguments")):
+        assert getattr(lib, name)(*_zero_args(L._PROTOS[name][1])) == -1, name
+        assert msg in lib.hs_last_error().decode(), name
+    assert lib.hs_destroy(None) == 0
+
+
+def test_byte_counts_of_invalid_sizes_are_zero(lib):
+    assert L.hs_z2_tensor_bytes(0, L.HS_BASIS_HERMITIAN) == 0
+    assert lib.hs_z2_tensor_bytes(3, L.HS_BASIS_HERMITIAN, 99) == 0
+    assert lib.hs_hotrg_tensor_bytes(0, 16) == 0 and lib.hs_hotrg_tensor_bytes(2, 0) == 0
+    assert lib.hs_hotrg_tensor_bytes(2, 16) == 16 ** 4 * 8 and lib.hs_hotrg_tensor_bytes(5, 16) == 25 ** 4 * 8
