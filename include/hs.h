@@ -380,7 +380,10 @@ typedef struct {
 /* Traced-boundary initialisation of all eight tensors from the double layer a
  * (HS_F64, either basis; every bond starts at the double-layer leg's sectors),
  * each divided by its largest modulus. Caches the four rotated copies of a in
- * the context; a must not change until the next hs_ctmrg4_init. */
+ * the context; a must not change until the next hs_ctmrg4_init. One context
+ * serves the directional runs of one double layer at a time: after another
+ * hs_ctmrg4_init with a different a, a move given the earlier a fails with
+ * HS_ERR_INVALID_ARG. */
 hs_status hs_ctmrg4_init(hs_ctx ctx, const hs_z2_tensor* a, int chi_max, hs_env4* env);
 
 /* One directional move of side `direction` (0 left, 1 top, 2 right, 3 bottom;
