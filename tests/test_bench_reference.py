@@ -45,3 +45,27 @@ def test_workload_name_of_the_headline():
     import bench
     assert bench.workload_name(3) == ("real C4v iPEPS d=2 D=6 chi=144 (q=36: 21 even/15 odd), seeded N(0,1), "
                                       "D4-symmetrised, max|A|=1")
+
+
+def test_clock_summary_reads_the_samples(tmp_path):
+    """The clock record of the timed region: median SM clock, the maximum, and every throttle reason
+    seen active in any sample (nvidia-smi csv, noheader, nounits); malformed lines are skipped."""
+    import bench
+    c = bench.Clocks(0)
+    c.path = str(tmp_path / "clocks.csv")
+    with open(c.path, "w") as f:
+        f.write("0, 2070, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active\n"
+                "0, 1980, 2070, 1390.5, 0x4, Not Active, Not Active, Not Active, Active\n"
+                "0, 2070, 2070, 1000.0, 0x0, Not Active, Not Active, Not Active, Not Active\n"
+                "garbage line\n"
+                "0, [N/A], 2070, 1000.0, 0x0, Not Active, Not Active, Not Active, Not Active\n")
+    c.proc = object()          # as if the sampler had run
+    s = c.summary()
+    assert s == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+    with open(c.path, "a") as f:
+        f.write("0, 1500, 2070, 1000.0, 0x0, Not Active, Active, Not Active, Not Active\n"
+                "0, 1500, 2070, 1000.0, 0x0, Not Active, Not Active, Not Active, Not Active\n")
+    s = c.summary()
+    assert s["sm_mhz"] == 1980.0 and s["reasons"] == ["hw_thermal_slowdown", "sw_power_cap"]
+    c.proc = None              # no sampler (no nvidia-smi): no record
+    assert c.summary() is None
