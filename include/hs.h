@@ -46,7 +46,7 @@
 extern "C" {
 #endif
 
-#define HS_ABI_VERSION 4
+#define HS_ABI_VERSION 5
 
 typedef enum {
   HS_OK = 0,
@@ -427,6 +427,15 @@ hs_status hs_hotrg_init(hs_ctx ctx, const hs_z2_tensor* a, hs_z2_tensor* t, doub
  * receives the step record. Synchronises. */
 hs_status hs_hotrg_step(hs_ctx ctx, hs_z2_tensor* t, int chi, int direction, hs_precision precision,
                         hs_hotrg_info* info);
+
+/* Free energy per site of a HOTRG run (Sec. II.A, Ref. xie12), host only:
+ *   ln Z / N = ln c_0 + sum_{k=1..steps} ln(c_k) / 2^k + ln Tr(T_steps) / 2^steps,
+ * with log_norms[0] = ln c_0 from hs_hotrg_init, log_norms[k] = ln c_k the
+ * log_norm of step k (host array of steps + 1 values) and trace the `trace`
+ * of the last step's hs_hotrg_info. *log_z (host) receives the value.
+ * HS_ERR_INVALID_ARG on null pointers or steps < 1; HS_ERR_NONFINITE if
+ * trace is not positive and finite, or the result is not finite. */
+hs_status hs_hotrg_log_z(const double* log_norms, int steps, double trace, double* log_z);
 
 /* ---- observables (Sec. III.A) ----------------------------------------- */
 

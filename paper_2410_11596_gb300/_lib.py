@@ -127,6 +127,7 @@ _PROTOS = {
     "hs_hotrg_tensor_bytes": (c_size_t, [c_int, c_int]),
     "hs_hotrg_init": (c_int, [c_void_p, POINTER(Z2Tensor), POINTER(Z2Tensor), POINTER(c_double)]),
     "hs_hotrg_step": (c_int, [c_void_p, POINTER(Z2Tensor), c_int, c_int, c_int, POINTER(HotrgInfo)]),
+    "hs_hotrg_log_z": (c_int, [POINTER(c_double), c_int, c_double, POINTER(c_double)]),
     "hs_gemm_static": (c_int, [c_int, c_int, c_int, c_int, c_void_p, c_int, c_void_p, c_int, c_void_p, c_int,
                                c_void_p, c_void_p]),
 }
@@ -346,6 +347,15 @@ def hs_hotrg_step(ctx: int, t: Z2Tensor, chi: int, direction: int, precision: in
     info = HotrgInfo()
     check(load().hs_hotrg_step(ctx, ctypes.byref(t), chi, direction, precision, ctypes.byref(info)))
     return info.as_dict()
+
+
+def hs_hotrg_log_z(log_norms, trace: float) -> float:
+    """ln Z / N from the log norms of hs_hotrg_init and of every step, and the last step's trace."""
+    n = len(log_norms)
+    arr = (c_double * n)(*[float(x) for x in log_norms])
+    out = c_double()
+    check(load().hs_hotrg_log_z(arr, n - 1, float(trace), ctypes.byref(out)))
+    return out.value
 
 
 def hs_rdm_vjp(ctx: int, env: Env, A, d: int, D: int, drho, dA, dtype: int = HS_F64) -> None:

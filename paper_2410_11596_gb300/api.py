@@ -362,10 +362,8 @@ class HOTRG:
         return [self.step() for _ in range(steps)]
 
     def log_z_per_site(self) -> float:
-        """ln Z / N = ln c_0 + sum_k ln(c_k) / 2^k + ln Tr(T_n) / 2^n (scalars returned by the library)."""
-        n = len(self.infos)
-        val = self.log_norms[0] + sum(self.log_norms[k] / 2.0 ** k for k in range(1, n + 1))
-        return float(val + np.log(self.infos[-1]["trace"]) / 2.0 ** n)
+        """ln Z / N of the steps so far (hs_hotrg_log_z)."""
+        return L.hs_hotrg_log_z(self.log_norms, self.infos[-1]["trace"] if self.infos else 0.0)
 
 
 class BatchedCTMRG:

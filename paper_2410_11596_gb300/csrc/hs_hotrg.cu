@@ -85,6 +85,24 @@ extern "C" size_t hs_hotrg_tensor_bytes(int D, int chi) {
   return x * x * x * x * sizeof(double);
 }
 
+// ln Z / N of a run of `steps` coarse-graining steps. Each step halves the
+// number of tensors, so the normalisation factor of step k is shared by 2^k
+// sites; the last tensor, closed on itself, stands for the rest of the
+// lattice. The terms are added in step order.
+extern "C" hs_status hs_hotrg_log_z(const double* log_norms, int steps, double trace, double* log_z) {
+  if (!log_norms || !log_z || steps < 1) return fail(HS_ERR_INVALID_ARG, "bad arguments");
+  if (!(trace > 0.0) || !std::isfinite(trace)) return fail(HS_ERR_NONFINITE, "trace %g is not positive", trace);
+  double sum = 0.0, w = 1.0;
+  for (int k = 1; k <= steps; ++k) {
+    w *= 0.5;
+    sum += log_norms[k] * w;
+  }
+  const double v = (log_norms[0] + sum) + std::log(trace) * w;
+  if (!std::isfinite(v)) return fail(HS_ERR_NONFINITE, "ln Z is not finite");
+  *log_z = v;
+  return HS_OK;
+}
+
 extern "C" hs_status hs_hotrg_init(hs_ctx ctx, const hs_z2_tensor* a, hs_z2_tensor* t, double* log_norm) {
   HS_TRY(check_ctx(ctx));
   if (!a || !t || !a->data || !t->data || !log_norm) return fail(HS_ERR_INVALID_ARG, "bad arguments");

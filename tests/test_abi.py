@@ -28,7 +28,7 @@ def test_binding_covers_header():
 
 
 def test_abi_version(lib):
-    assert lib.hs_abi_version() == 4
+    assert lib.hs_abi_version() == 5
 
 
 @pytest.mark.parametrize("D", [1, 2, 3, 4, 5, 6, 7])
@@ -124,3 +124,23 @@ def test_byte_counts_of_invalid_sizes_are_zero(lib):
     assert lib.hs_z2_tensor_bytes(3, L.HS_BASIS_HERMITIAN, 99) == 0
     assert lib.hs_hotrg_tensor_bytes(0, 16) == 0 and lib.hs_hotrg_tensor_bytes(2, 0) == 0
     assert lib.hs_hotrg_tensor_bytes(2, 16) == 16 ** 4 * 8 and lib.hs_hotrg_tensor_bytes(5, 16) == 25 ** 4 * 8
+
+
+def test_hotrg_log_z(lib):
+    """hs_hotrg_log_z (host only): ln Z / N from the normalisation logs of a run and the last trace,
+    against the sum written out term by term (the factor of step k is shared by 2^k sites), and
+    its error statuses."""
+    import math
+    ln = [0.7, 1.1, -2.3, 4.9]
+    want = 0.7 + 1.1 / 2 - 2.3 / 4 + 4.9 / 8 + math.log(3.5) / 8
+    assert L.hs_hotrg_log_z(ln, 3.5) == pytest.approx(want, rel=1e-15)
+    assert L.hs_hotrg_log_z([0.2, 0.4], 2.0) == pytest.approx(0.2 + 0.2 + math.log(2.0) / 2, rel=1e-15)
+    # thirty steps: the last trace weighs 2^-30
+    ln30 = [0.5] + [0.25] * 30
+    assert L.hs_hotrg_log_z(ln30, 7.0) == pytest.approx(0.5 + 0.25 * (1 - 2.0 ** -30) + math.log(7.0) * 2.0 ** -30,
+                                                         rel=1e-15)
+    for log_norms, trace, status in (([0.1], 1.0, -1), ([0.1, 0.2], 0.0, -8), ([0.1, 0.2], -1.0, -8),
+                                     ([0.1, float("nan")], 1.0, -8), ([0.1, 0.2], float("inf"), -8)):
+        with pytest.raises(L.HsError) as e:
+            L.hs_hotrg_log_z(log_norms, trace)
+        assert e.value.status == status, (log_norms, trace)
