@@ -38,26 +38,33 @@ def snapshot(C, T, A, D):
     return out
 
 
-def main(ks):
-    for k in ks:
-        w = inputs.WORKLOADS[k]
-        A = inputs.workload_tensor(k)
-        a = dl.double_layer(A)
-        C, T = ctmrg.init_environment(a)
-        C, T = C / np.abs(C).max(), T / np.abs(T).max()
-        res = {"workload": k, **w, "seed": w.get("seed", inputs.SEED_BASE + k), "checkpoints": {}, "gaps": [], "lam_cut": [],
-               "n": []}
-        t0 = time.time()
-        for m in range(1, w["moves"] + 1):
-            C, T, info = ctmrg.move(C, T, a, w["chi"])
-            res["gaps"].append(float(info.gap) if np.isfinite(info.gap) else None)
-            res["lam_cut"].append(info.lam_cut)
-            res["n"].append(info.n)
-            if m in CHECKPOINTS or m == w["moves"]:
-                res["checkpoints"][str(m)] = snapshot(C, T, A, w["D"])
+def compute(k, verbose=False):
+    """The stored record of workload k, computed by the oracle."""
+    w = inputs.WORKLOADS[k]
+    A = inputs.workload_tensor(k)
+    a = dl.double_layer(A)
+    C, T = ctmrg.init_environment(a)
+    C, T = C / np.abs(C).max(), T / np.abs(T).max()
+    res = {"workload": k, **w, "seed": w.get("seed", inputs.SEED_BASE + k), "checkpoints": {}, "gaps": [], "lam_cut": [],
+           "n": []}
+    t0 = time.time()
+    for m in range(1, w["moves"] + 1):
+        C, T, info = ctmrg.move(C, T, a, w["chi"])
+        res["gaps"].append(float(info.gap) if np.isfinite(info.gap) else None)
+        res["lam_cut"].append(info.lam_cut)
+        res["n"].append(info.n)
+        if m in CHECKPOINTS or m == w["moves"]:
+            res["checkpoints"][str(m)] = snapshot(C, T, A, w["D"])
+            if verbose:
                 print(f"w{k} move {m} E={res['checkpoints'][str(m)]['energy']:.15f} t={time.time()-t0:.1f}s",
                       flush=True)
-        res["oracle_seconds"] = time.time() - t0
+    res["oracle_seconds"] = time.time() - t0
+    return res
+
+
+def main(ks):
+    for k in ks:
+        res = compute(k, verbose=True)
         path = os.path.join(os.path.dirname(os.path.abspath(__file__)), f"ctmrg_w{k}.json")
         with open(path, "w") as f:
             json.dump(res, f)
