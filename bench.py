@@ -514,7 +514,7 @@ def run_ours(args):
     del cr
 
 
-    # ---- {Z2, dense} x {FP64+syevd, TF32x3+syevd, TF32x3+subspace} ----
+    # ---- {Z2, dense} x {FP64+syevd, TF32x3+syevd, FP64+subspace, TF32x3+subspace} ----
     table = None
     speedup = None
     if not args.no_table:
