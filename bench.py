@@ -44,9 +44,9 @@ FLUSH_BYTES = 512 << 20
 # DRAM traffic per launch of the roofline kernel from one ncu capture, valid only
 # while the kernel source is unchanged (sha256 of the file, first 16 hex digits).
 NCU_TRAFFIC = {
-    # profiles/gemm_f64_d6_chi144.md: mean of the G3/G4/G5 launches
+    # FP64 block GEMM, one ncu capture of a D=6 chi=144 move: mean of its G3/G4/G5 launches
     "gemm_f64": {"bytes_per_launch": 143.3e6, "source_sha": "ac07f1d8a4d24d63"},
-    # profiles/gemm_tc_tf32x3_d6_chi144.md: mean over the tensor-core launches of two steady-state moves
+    # tensor-core GEMM, one ncu capture of two steady-state D=6 chi=144 moves: mean over its launches
     "gemm_tc_tf32x3": {"bytes_per_launch": 56.6e6, "source_sha": "c3b7279478e6ad5a"},
     # the same capture, mean over its split-output launches (G2-G5, the dominant kernel)
     "gemm_tc_split_tf32x3": {"bytes_per_launch": 131.5e6, "source_sha": "c3b7279478e6ad5a"},
