@@ -10,6 +10,11 @@
 // mode 0: Z2 block matrices, 1: graded matrices; n = kr + kc legs; the
 // input's first kr legs are its rows, the output's leg j is input leg
 // perm[j] and its first kr_out legs are its rows.
+//
+// Mode 2 prints the block GEMMs of a Z2 product C[R|N] = A[R|K] B[N|K]^T
+// (make_z2_gemm) instead:
+//   2 kr kk kn  e_0 o_0 ... (kr + kk + kn legs: R, then K, then N)  padA padB padC
+// as "n elemsA elemsB elemsC" and per problem "M N K lda ldb ldc a_off b_off c_off".
 #include <cstdio>
 #include <vector>
 #include "hs_internal.cuh"
@@ -26,6 +31,38 @@ static Fused group(const Sect* s, int k) {
 int main() {
   int mode, kr, kc;
   while (std::scanf("%d %d %d", &mode, &kr, &kc) == 3) {
+    if (mode == 2) {
+      int kn, pa, pb, pc;
+      if (std::scanf("%d", &kn) != 1) return 1;
+      const int n = kr + kc + kn;
+      if (kr < 1 || kc < 1 || kn < 1 || kr > kMaxFused || kc > kMaxFused || kn > kMaxFused || n > 12) {
+        std::printf("bad case\n");
+        return 1;
+      }
+      Sect s[12];
+      for (int j = 0; j < n; ++j)
+        if (std::scanf("%d %d", &s[j].n[0], &s[j].n[1]) != 2) return 1;
+      if (std::scanf("%d %d %d", &pa, &pb, &pc) != 3) return 1;
+      Z2Mat A, B, C;
+      A.r = group(s, kr);
+      A.c = group(s + kr, kc);
+      A.pad = pa;
+      B.r = group(s + kr + kc, kn);
+      B.c = group(s + kr, kc);
+      B.pad = pb;
+      C.r = group(s, kr);
+      C.c = group(s + kr + kc, kn);
+      C.pad = pc;
+      const GemmGroup g = make_z2_gemm(A, B, C);
+      std::printf("%d %lld %lld %lld", g.n, z2_elems(A), z2_elems(B), z2_elems(C));
+      for (int i = 0; i < g.n; ++i) {
+        const GemmProblem& q = g.p[i];
+        std::printf(" %d %d %d %d %d %d %lld %lld %lld", q.M, q.N, q.K, q.lda, q.ldb, q.ldc, q.a_off, q.b_off,
+                    q.c_off);
+      }
+      std::printf("\n");
+      continue;
+    }
     const int n = kr + kc;
     if (kr < 1 || kc < 1 || kr > kMaxFused || kc > kMaxFused || n > kMaxLegs) {
       std::printf("bad case\n");

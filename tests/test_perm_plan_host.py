@@ -201,3 +201,67 @@ def test_expected_map_on_a_hand_example():
     want, n = _expected(0, 1, [(2, 1), (1, 1)], 1, [1, 0], 4)
     assert n == 4 + 4       # each block's row padded to 4
     assert list(want) == [0, 1, 4]
+
+
+def _pack(tensor, rows, cols, pad):
+    """Z2 block storage of a tensor whose first len(rows) legs are the rows (odd-total entries
+    dropped), by the layout definition."""
+    out = np.zeros(_elems(rows, cols, pad))
+    for idx in itertools.product(*[range(e + o) for e, o in rows + cols]):
+        f = _flat(rows, cols, pad, idx)
+        if f is not None:
+            out[f] = tensor[idx]
+    return out
+
+
+def _even_random(sects, rng):
+    t = rng.standard_normal([e + o for e, o in sects])
+    for idx in itertools.product(*[range(e + o) for e, o in sects]):
+        if sum(int(i >= e) for (e, _), i in zip(sects, idx)) % 2:
+            t[idx] = 0.0
+    return t
+
+
+# (R legs, K legs, N legs, pads of A, B, C): the move's corner and edge products (two-leg groups,
+# ragged sectors, an empty odd sector), one-leg groups, three-leg groups, padded operands.
+GEMM_CASES = [
+    ([(3, 2), (2, 1)], [(2, 1), (3, 2)], [(3, 2), (2, 1)], 1, 1, 1),
+    ([(3, 2)], [(3, 2), (2, 1)], [(2, 1), (2, 1)], 32, 32, 1),
+    ([(4, 0), (1, 0)], [(1, 0), (4, 0)], [(2, 0)], 1, 4, 1),
+    ([(2, 1), (1, 1), (1, 2)], [(2, 2)], [(1, 1), (2, 1)], 4, 1, 32),
+    ([(0, 2), (2, 1)], [(1, 2), (2, 0)], [(2, 2)], 1, 1, 4),
+]
+
+
+def test_block_gemm_descriptors_give_the_dense_contraction(exe):
+    """make_z2_gemm's problems (sizes, strides, offsets), applied with numpy to the packed operands,
+    give the packed dense contraction C[R, N] = sum_K A[R, K] B[N, K]; their flop count is the
+    sum over parity blocks of 2 M N K."""
+    rng = np.random.default_rng(2410)
+    text = "".join(f"2 {len(r)} {len(k)} {len(n)} " + " ".join(f"{e} {o}" for e, o in r + k + n) +
+                   f" {pa} {pb} {pc}\n" for r, k, n, pa, pb, pc in GEMM_CASES)
+    out = subprocess.run([str(exe)], input=text, capture_output=True, text=True, timeout=300)
+    assert out.returncode == 0, out.stdout[-500:] + out.stderr
+    lines = out.stdout.splitlines()
+    assert len(lines) == len(GEMM_CASES)
+    for (r, k, n, pa, pb, pc), line in zip(GEMM_CASES, lines):
+        v = [int(x) for x in line.split()]
+        nprob, ea, eb, ec = v[:4]
+        assert (ea, eb, ec) == (_elems(r, k, pa), _elems(n, k, pb), _elems(r, n, pc))
+        a = _even_random(r + k, rng)
+        b = _even_random(n + k, rng)
+        A, B = _pack(a, r, k, pa), _pack(b, n, k, pb)
+        C = np.zeros(ec)
+        flops = 0
+        for i in range(nprob):
+            M, N, K, lda, ldb, ldc, ao, bo, co = v[4 + 9 * i: 13 + 9 * i]
+            Ab = A[ao:ao + M * lda].reshape(M, lda)[:, :K]
+            Bb = B[bo:bo + N * ldb].reshape(N, ldb)[:, :K]
+            C[co:co + M * ldc].reshape(M, ldc)[:, :N] = Ab @ Bb.T
+            flops += 2 * M * N * K
+        dense = np.tensordot(a, b, axes=(list(range(len(r), len(r) + len(k))),
+                                          list(range(len(n), len(n) + len(k)))))
+        np.testing.assert_allclose(C, _pack(dense, r, n, pc), atol=1e-12, err_msg=str((r, k, n)))
+        want = sum(2 * _group_size(r, p) * _group_size(n, p) * _group_size(k, p) for p in (0, 1)
+                   if _group_size(r, p) and _group_size(n, p))
+        assert flops == want
