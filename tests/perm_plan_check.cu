@@ -15,6 +15,8 @@
 // (make_z2_gemm) instead:
 //   2 kr kk kn  e_0 o_0 ... (kr + kk + kn legs: R, then K, then N)  padA padB padC
 // as "n elemsA elemsB elemsC" and per problem "M N K lda ldb ldc a_off b_off c_off".
+// Mode 3 does the same for the graded product of complex tensors
+// (make_graded_gemm, the conjugate copy of B stored right after B).
 #include <cstdio>
 #include <vector>
 #include "hs_internal.cuh"
@@ -31,7 +33,7 @@ static Fused group(const Sect* s, int k) {
 int main() {
   int mode, kr, kc;
   while (std::scanf("%d %d %d", &mode, &kr, &kc) == 3) {
-    if (mode == 2) {
+    if (mode == 2 || mode == 3) {
       int kn, pa, pb, pc;
       if (std::scanf("%d", &kn) != 1) return 1;
       const int n = kr + kc + kn;
@@ -43,18 +45,40 @@ int main() {
       for (int j = 0; j < n; ++j)
         if (std::scanf("%d %d", &s[j].n[0], &s[j].n[1]) != 2) return 1;
       if (std::scanf("%d %d %d", &pa, &pb, &pc) != 3) return 1;
-      Z2Mat A, B, C;
-      A.r = group(s, kr);
-      A.c = group(s + kr, kc);
-      A.pad = pa;
-      B.r = group(s + kr + kc, kn);
-      B.c = group(s + kr, kc);
-      B.pad = pb;
-      C.r = group(s, kr);
-      C.c = group(s + kr + kc, kn);
-      C.pad = pc;
-      const GemmGroup g = make_z2_gemm(A, B, C);
-      std::printf("%d %lld %lld %lld", g.n, z2_elems(A), z2_elems(B), z2_elems(C));
+      GemmGroup g;
+      long long ea, eb, ec;
+      if (mode == 2) {
+        Z2Mat A, B, C;
+        A.r = group(s, kr);
+        A.c = group(s + kr, kc);
+        A.pad = pa;
+        B.r = group(s + kr + kc, kn);
+        B.c = group(s + kr, kc);
+        B.pad = pb;
+        C.r = group(s, kr);
+        C.c = group(s + kr + kc, kn);
+        C.pad = pc;
+        g = make_z2_gemm(A, B, C);
+        ea = z2_elems(A);
+        eb = z2_elems(B);
+        ec = z2_elems(C);
+      } else {
+        GMat A, B, C;
+        A.r = group(s, kr);
+        A.c = group(s + kr, kc);
+        A.pad = pa;
+        B.r = group(s + kr + kc, kn);
+        B.c = group(s + kr, kc);
+        B.pad = pb;
+        C.r = group(s, kr);
+        C.c = group(s + kr + kc, kn);
+        C.pad = pc;
+        g = make_graded_gemm(A, B, C, g_elems(B));
+        ea = g_elems(A);
+        eb = g_elems(B);
+        ec = g_elems(C);
+      }
+      std::printf("%d %lld %lld %lld", g.n, ea, eb, ec);
       for (int i = 0; i < g.n; ++i) {
         const GemmProblem& q = g.p[i];
         std::printf(" %d %d %d %d %d %d %lld %lld %lld", q.M, q.N, q.K, q.lda, q.ldb, q.ldc, q.a_off, q.b_off,

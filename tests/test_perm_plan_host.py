@@ -265,3 +265,64 @@ def test_block_gemm_descriptors_give_the_dense_contraction(exe):
         want = sum(2 * _group_size(r, p) * _group_size(n, p) * _group_size(k, p) for p in (0, 1)
                    if _group_size(r, p) and _group_size(n, p))
         assert flops == want
+
+
+def _block(off, rows, cols, ld):
+    """Flat indices of a rows x cols block with row stride ld starting at off."""
+    return off + np.arange(rows)[:, None] * ld + np.arange(cols)[None, :]
+
+
+def _graded_pack(t, rows, cols, pad):
+    out = np.zeros(_graded_elems(rows, cols, pad))
+    for idx in itertools.product(*[range(e + o) for e, o in rows + cols]):
+        out[_graded_flat(rows, cols, pad, idx)] = t[idx]
+    return out
+
+
+def _parity(sects, idx):
+    return sum(int(i >= e) for (e, _), i in zip(sects, idx)) % 2
+
+
+def test_graded_gemm_descriptors_give_the_complex_product(exe):
+    """make_graded_gemm's four sub-GEMMs per product, with the diagonal blocks reading the copy of
+    B~ whose odd-total entries are negated (stored right after B~), applied with numpy to packed
+    graded operands, give the graded form of the complex product: for complex X with
+    X[r, c] = i^[p(r) != p(c)] X~[r, c] (X~ real, Sec. II.C), C = A B^T and C~ = C / i^[p(r) != p(k)]."""
+    rng = np.random.default_rng(2411)
+    text = "".join(f"3 {len(r)} {len(k)} {len(n)} " + " ".join(f"{e} {o}" for e, o in r + k + n) +
+                   f" {pa} {pb} {pc}\n" for r, k, n, pa, pb, pc in GEMM_CASES)
+    out = subprocess.run([str(exe)], input=text, capture_output=True, text=True, timeout=300)
+    assert out.returncode == 0, out.stdout[-500:] + out.stderr
+    for (r, k, n, pa, pb, pc), line in zip(GEMM_CASES, out.stdout.splitlines()):
+        v = [int(x) for x in line.split()]
+        nprob, ea, eb, ec = v[:4]
+        assert (ea, eb, ec) == (_graded_elems(r, k, pa), _graded_elems(n, k, pb), _graded_elems(r, n, pc))
+        at = rng.standard_normal([e + o for e, o in r + k])      # A~ over (R, K)
+        bt = rng.standard_normal([e + o for e, o in n + k])      # B~ over (N, K): the operand B^T
+        A = _graded_pack(at, r, k, pa)
+        Bs = _graded_pack(bt, n, k, pb)
+        conj = bt.copy()
+        for idx in itertools.product(*[range(e + o) for e, o in n + k]):
+            if _parity(n, idx[:len(n)]) != _parity(k, idx[len(n):]):
+                conj[idx] = -conj[idx]
+        B = np.concatenate([Bs, _graded_pack(conj, n, k, pb)])
+        C = np.zeros(ec)
+        for i in range(nprob):
+            M, N, K, lda, ldb, ldc, ao, bo, co = v[4 + 9 * i: 13 + 9 * i]
+            C[_block(co, M, N, ldc)] = A[_block(ao, M, K, lda)] @ B[_block(bo, N, K, ldb)].T
+        # the complex product, written out
+        ac = at.astype(complex)
+        for idx in itertools.product(*[range(e + o) for e, o in r + k]):
+            if _parity(r, idx[:len(r)]) != _parity(k, idx[len(r):]):
+                ac[idx] *= 1j
+        bc = bt.astype(complex)
+        for idx in itertools.product(*[range(e + o) for e, o in n + k]):
+            if _parity(n, idx[:len(n)]) != _parity(k, idx[len(n):]):
+                bc[idx] *= 1j
+        cc = np.tensordot(ac, bc, axes=(list(range(len(r), len(r) + len(k))), list(range(len(n), len(n) + len(k)))))
+        ct = np.empty(cc.shape)
+        for idx in itertools.product(*[range(e + o) for e, o in r + n]):
+            z = cc[idx] / (1j if _parity(r, idx[:len(r)]) != _parity(n, idx[len(r):]) else 1)
+            assert abs(z.imag) <= 1e-12
+            ct[idx] = z.real
+        np.testing.assert_allclose(C, _graded_pack(ct, r, n, pc), atol=1e-12, err_msg=str((r, k, n)))
