@@ -587,7 +587,12 @@ hs_status hs_energy_vjp(hs_ctx ctx, const hs_env* env, const double* A, int d, i
 hs_status hs_ctmrg_energy_grad(hs_ctx ctx, const double* A, int d, int D, hs_basis basis, int chi, int moves,
                                const double* h, double* energy_out, double* dA_out);
 
-/* Workspace the context will allocate for (D, chi): reported for planning. */
+/* A planning estimate of a context's largest work buffers for (D, chi): the
+ * two ping-pong buffers of the enlarged-corner and edge chains, sized for the
+ * plain basis ((chi D^2)^2 doubles each, chi at least D^2), and three
+ * chi^2 D^2 buffers. Not counted: solver workspaces, tensor-core split
+ * operands and the subspace solver's buffers. precision is not used yet.
+ * HS_ERR_INVALID_ARG if D or chi is below 1 or bytes is NULL. Host only. */
 hs_status hs_workspace_query(int D, int chi, hs_precision precision, size_t* bytes);
 
 /* Diagnostic: runs the tensor-core GEMM's bounded mbarrier wait (the wait

@@ -144,3 +144,13 @@ def test_hotrg_log_z(lib):
         with pytest.raises(L.HsError) as e:
             L.hs_hotrg_log_z(log_norms, trace)
         assert e.value.status == status, (log_norms, trace)
+
+
+def test_workspace_query_is_the_stated_estimate(lib):
+    """hs_workspace_query (host only): two (chi D^2)^2 ping-pong buffers and three chi^2 D^2 ones,
+    chi at least D^2, in doubles."""
+    for D, chi in ((2, 16), (6, 144), (7, 196), (3, 4)):
+        q, c = D * D, max(chi, D * D)
+        out = ctypes.c_size_t()
+        assert lib.hs_workspace_query(D, chi, 0, ctypes.byref(out)) == 0
+        assert out.value == 8 * (2 * (c * q) ** 2 + 3 * c * c * q)
