@@ -90,8 +90,9 @@ typedef enum { HS_BASIS_DENSE = 0, HS_BASIS_HERMITIAN = 1 } hs_basis;
  *   not diagonal). Meant for the mixed-precision modes, whose C' carries FP32
  *   rounding already.
  * HS_EIG_SUBSPACE: as HS_EIG_F32_PROJECTED, but the kept vectors come from a
- *   warm-started block subspace iteration on each parity block (tensor-core
- *   products H X; the warm rows re-orthonormalised by a Loewdin step;
+ *   warm-started block subspace iteration on each parity block (products H X
+ *   in the environment's precision, on tcgen05 or the FP64 kernel; the warm
+ *   rows re-orthonormalised by a Loewdin step;
  *   unconverged rounds take a Chebyshev-filtered step, orthonormalised by
  *   Cholesky-QR and a Loewdin step; Rayleigh-Ritz of size m = k + max(24, k/3),
  *   at most 192, by an FP32 Jacobi eigensolver; at most 8 rounds, fewer when
@@ -107,10 +108,12 @@ typedef enum { HS_BASIS_DENSE = 0, HS_BASIS_HERMITIAN = 1 } hs_basis;
  *   when the sector sizes cannot be carried over, the move falls back to
  *   HS_EIG_F32_PROJECTED. With tensor-core products, where the Cholesky-QR
  *   of a filtered basis breaks down, the round is run again on a
- *   Householder-QR basis instead. Kept
- *   vectors carry
- *   a canonical sign (largest entry positive) so that the gauge, and with it
- *   the warm start, is stationary at the fixed point.
+ *   Householder-QR basis instead. Kept vectors carry a canonical sign
+ *   (largest entry positive) so that the gauge, and with it the warm start,
+ *   is stationary at the fixed point; while the environment still moves (the
+ *   move's first residual above 1e-3) they are instead ordered and signed
+ *   like the previous move's kept vectors they overlap most (overlap above
+ *   1/2, per parity block).
  * HS_EIG_SUBSPACE_ADAPTIVE: as HS_EIG_SUBSPACE, with the residual tolerance of
  *   each move set by how much the environment still changes: tol = 0.1 delta
  *   clamped to [1e-5 (1e-6 with FP64 products), 1e-3], delta the residual of the

@@ -557,10 +557,12 @@ hs_status finish_projector(hs_ctx ctx, int n0, int n1, SelectOut* dsel, Sect c, 
 // valid when that choice is stationary. Kept states come ordered by |lambda|;
 // where two of them have nearly equal |lambda| (D = 7: the spectrum drifts by
 // ~0.5% per move and close pairs change order) the order, and with it the
-// coordinates of the next C', changes from move to move. Here each new row
-// takes the position of the previous row it overlaps most (|O_ij|, O = PT
-// PT_prev^T, FP64), when that is a one-to-one match with every overlap above
-// 1/2; otherwise the block keeps its order. *moved: rows that moved.
+// coordinates of the next C', changes from move to move. Here, per block,
+// the new rows in order of their clearest overlap each take the position of
+// the previous row they overlap most (|O_ij|, O = PT PT_prev^T, FP64), with
+// that row's sign, when the overlap is above 1/2 and the position is still
+// free; the other rows fill the free positions in their order. *moved: rows
+// that moved or changed sign.
 hs_status align_kept_rows(hs_ctx ctx, const int k[2], const int n[2], int* moved) {
   cudaStream_t s = ctx->stream;
   *moved = 0;
