@@ -127,8 +127,8 @@ cudaError_t launch_gemm_f64(const GemmGroup& g, const double* A, const double* B
   }
   if (tiles == 0) return cudaSuccess;
   // split K when the output tiles cannot fill the GPU (3 resident CTAs on each
-  // of its 152 SMs) and each split still gets several K steps
-  constexpr long long kTarget = 3 * 152;
+  // of its SMs) and each split still gets several K steps
+  const long long kTarget = 3LL * device_sms();
   SplitK sk{};
   sk.nsplit = 1;
   if (part && tiles < kTarget) {
