@@ -34,9 +34,11 @@ constexpr double kSvCutoff = 1e-12;  // singular values below this fraction of t
 
 int mod4(int x) { return ((x % 4) + 4) % 4; }
 
+// Blocks of 256 threads for a grid-stride loop over n elements: one per 256
+// elements, at most 32 per SM.
 unsigned grid_of(long long n) {
   const long long g = (n + 255) / 256;
-  return (unsigned)std::max(1ll, std::min(g, 152ll * 32));
+  return (unsigned)std::max(1ll, std::min(g, 32ll * device_sms()));
 }
 
 // dst row r = scale[r] * (src row idx[r]), rows of n elements.

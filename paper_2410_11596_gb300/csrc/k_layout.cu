@@ -662,7 +662,8 @@ cudaError_t launch_join_split_f32(const void* hi, const void* lo, long long rows
   const long long total = rows0 * cols0 + rows1 * cols1;
   if (total <= 0) return cudaSuccess;
   long long blocks = (total + 255) / 256;
-  if (blocks > 152 * 16) blocks = 152 * 16;
+  const long long cap = 16LL * device_sms();  // grid-stride loop: 16 blocks per SM
+  if (blocks > cap) blocks = cap;
   hs_launch(join_split_f32_kernel, (unsigned)blocks, 256, 0, s, static_cast<const uint32_t*>(hi),
             static_cast<const uint32_t*>(lo), rows0, cols0, ld0, off1, rows1, cols1, ld1, out);
   return cudaGetLastError();
